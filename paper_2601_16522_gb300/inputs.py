@@ -1,0 +1,304 @@
+"""Seeded synthetic inputs: problem descriptions and initial conditions.
+
+This module holds no arithmetic of the time step itself.  It describes a
+problem (grid, phases, raw physical parameters, boundary conditions) and builds
+initial fields from distance functions, exactly as the paper's benchmark set-up
+does (Sec. 4 "Common conditions", Sec. 5).  It is the one piece of code that
+both the CUDA engine's callers and the CPU oracle's tests use; it imports only
+numpy/scipy.
+
+State layout everywhere: ``u`` of shape ``(N + K, V)`` float64, phase-major,
+cell index ``i = (z*ny + y)*nx + x`` (x fastest); row ``N`` is the
+concentration when ``K == 1``.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field, replace
+from typing import Optional
+
+import numpy as np
+
+BC_PERIODIC, BC_NEUMANN, BC_DIRICHLET = 0, 1, 2
+FEULER, SSP2, SSP104, RKL1, RKL2 = 0, 1, 2, 3, 4
+INTEGRATORS = {"feuler": FEULER, "ssp2": SSP2, "ssp104": SSP104, "rkl1": RKL1, "rkl2": RKL2}
+
+
+@dataclass
+class Problem:
+    """Raw parameters of one simulation (Sec. 2 model, Sec. 4 parameters)."""
+    dim: int
+    nx: int
+    ny: int
+    nz: int
+    dx: float
+    n_phases: int
+    phase_type: np.ndarray          # (N,) int32, chemical type 0 (alpha) or 1 (beta)
+    gamma: np.ndarray               # (N, N) interface energies
+    mobility: np.ndarray            # (N, N) interface mobilities M
+    W: float                        # interface parameter (width pi*W)
+    L_override: Optional[np.ndarray] = None   # (N, N) phase-field mobility, e.g. thin-interface L
+    has_conc: int = 0
+    k: tuple = (1.0, 1.0)
+    c0: tuple = (0.0, 0.0)
+    D: tuple = (0.0, 0.0)
+    bc_phi: tuple = (0, 0, 0, 0, 0, 0)
+    bc_c: tuple = (0, 0, 0, 0, 0, 0)
+    c_dirichlet: tuple = (0.0,) * 6
+    name: str = ""
+
+    @property
+    def V(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    @property
+    def nfields(self) -> int:
+        return self.n_phases + self.has_conc
+
+    def with_(self, **kw) -> "Problem":
+        return replace(self, **kw)
+
+
+def uniform_pairs(N: int, value: float) -> np.ndarray:
+    m = np.full((N, N), float(value))
+    np.fill_diagonal(m, 0.0)
+    return m
+
+
+def typed_pairs(ptype, same_beta: float, mixed: float, same_alpha: float = None) -> np.ndarray:
+    """Pairwise matrix depending only on the chemical types of the two phases."""
+    t = np.asarray(ptype)
+    N = len(t)
+    m = np.empty((N, N))
+    for a in range(N):
+        for b in range(N):
+            if t[a] != t[b]:
+                m[a, b] = mixed
+            elif t[a] == 1:
+                m[a, b] = same_beta
+            else:
+                m[a, b] = same_alpha if same_alpha is not None else same_beta
+    np.fill_diagonal(m, 0.0)
+    return m
+
+
+# --------------------------------------------------------------------------
+# initial profile (Eq. profile) and distance fields
+# --------------------------------------------------------------------------
+
+def profile(d, W):
+    """Equilibrium 1D profile of Eq. (profile) evaluated on a distance field d."""
+    d = np.asarray(d, dtype=np.float64)
+    h = math.pi * W / 2.0
+    out = 0.5 * (1.0 + np.sin(np.clip(d, -h, h) / W))
+    out = np.where(d <= -h, 0.0, out)
+    out = np.where(d >= h, 1.0, out)
+    return out
+
+
+def cell_centres(nx, ny, nz, dx):
+    """Cell-centred coordinates x_i = (i + 1/2) dx (Sec. 3)."""
+    z, y, x = np.meshgrid((np.arange(nz) + 0.5) * dx, (np.arange(ny) + 0.5) * dx,
+                          (np.arange(nx) + 0.5) * dx, indexing="ij")
+    return x.ravel(), y.ravel(), z.ravel()
+
+
+# --------------------------------------------------------------------------
+# benchmark problems
+# --------------------------------------------------------------------------
+
+def circle(n=128, R0=40.0, W=5.0 / math.pi, M=1.0, gamma=1.0, dx=1.0, ny=None):
+    """Shrinking circular grain (Sec. 5.2.1): inner grain = phase 1 with
+    distance d = R0 - |X - C| (Eq. centersphere), outer phase 0 = complement.
+    2D periodic, phase field only."""
+    ny = n if ny is None else ny
+    prob = Problem(dim=2, nx=n, ny=ny, nz=1, dx=dx, n_phases=2,
+                   phase_type=np.array([0, 0], np.int32),
+                   gamma=uniform_pairs(2, gamma), mobility=uniform_pairs(2, M), W=W,
+                   name="circle%dx%d" % (n, ny))
+    x, y, _ = cell_centres(n, ny, 1, dx)
+    cx, cy = n * dx / 2.0, ny * dx / 2.0
+    d = R0 - np.sqrt((x - cx) ** 2 + (y - cy) ** 2)
+    g = profile(d, W)
+    u = np.stack([1.0 - g, g])
+    return prob, u
+
+
+def stefan_L(W, k=1.0, dc=0.96, D=1.0, MF=0.3084251):
+    """Thin-interface phase-field mobility for vanishing kinetic coefficient
+    (Eq. thin-interface, Sec. 5.2.2): L = pi^2/(16 W^2) D (dc/dmu) / (dc_eq^2 (M+F)),
+    with dc/dmu = 1/k for the parabolic energies."""
+    return (math.pi ** 2 / (16.0 * W * W)) * D * (1.0 / k) / (dc * dc * MF)
+
+
+def stefan(nx=1024, ny=256, h=200.0, W=5.0 / math.pi, D_liquid=1.0, D_solid=0.01,
+           c_liquid=0.2, c_solid=0.98, k=1.0, c0=(0.02, 0.98), dx=1.0, gamma=1.0):
+    """Solutal Stefan problem (Sec. 5.2.2) on a 2D strip: solid beta (type 1,
+    phase 1) on the left with distance d = h - x, liquid alpha (type 0, phase 0)
+    as complement; c = phi_alpha c_liquid + phi_beta c_solid; phi zero-gradient
+    on x faces, c Dirichlet (left c_solid, right c_liquid); y periodic."""
+    N = 2
+    L = stefan_L(W, k=k, dc=c0[1] - c0[0], D=D_liquid)
+    Lm = uniform_pairs(N, L)
+    prob = Problem(dim=2, nx=nx, ny=ny, nz=1, dx=dx, n_phases=N,
+                   phase_type=np.array([0, 1], np.int32),
+                   gamma=uniform_pairs(N, gamma), mobility=uniform_pairs(N, 1.0), W=W,
+                   L_override=Lm, has_conc=1, k=(k, k), c0=tuple(c0), D=(D_liquid, D_solid),
+                   bc_phi=(BC_NEUMANN, BC_NEUMANN, 0, 0, 0, 0),
+                   bc_c=(BC_DIRICHLET, BC_DIRICHLET, 0, 0, 0, 0),
+                   c_dirichlet=(c_solid, c_liquid, 0.0, 0.0, 0.0, 0.0),
+                   name="stefan%dx%d" % (nx, ny))
+    x, _, _ = cell_centres(nx, ny, 1, dx)
+    solid = profile(h - x, W)
+    liquid = 1.0 - solid
+    c = liquid * c_liquid + solid * c_solid
+    return prob, np.stack([liquid, solid, c])
+
+
+def stefan_growth_constant(D=1.0, c_a=0.2, c_ab=0.02, c_ba=0.98, c_b=0.98):
+    """Root A of Eq. (stefangrowth) by bisection (X(t) = A sqrt(t))."""
+    from math import erf, exp, pi, sqrt
+
+    def g(A):
+        e = exp(-A * A / (4 * D))
+        t1 = (c_a - c_ab) / (c_ba - c_ab) * e / (1 - erf(A / sqrt(4 * D)))
+        t2 = (c_b - c_ba) / (c_ba - c_ab) * e / (1 + erf(A / sqrt(4 * D)))
+        return sqrt(4 * D / pi) * (t1 + t2) - A
+
+    lo, hi = 1e-9, 10.0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if g(lo) * g(mid) <= 0:
+            hi = mid
+        else:
+            lo = mid
+    return 0.5 * (lo + hi)
+
+
+def poisson_disc_seeds(n_cells, count, min_dist, dim, rng, max_tries=200000):
+    """Seeded random points in a periodic box with a minimum (periodic) distance."""
+    pts = []
+    tries = 0
+    L = np.array(n_cells, dtype=np.float64)
+    while len(pts) < count:
+        tries += 1
+        if tries > max_tries:
+            raise ValueError("could not place %d seeds with min distance %g" % (count, min_dist))
+        p = rng.random(dim) * L
+        ok = True
+        for q in pts:
+            dd = np.abs(p - q)
+            dd = np.minimum(dd, L - dd)
+            if np.sqrt((dd * dd).sum()) < min_dist:
+                ok = False
+                break
+        if ok:
+            pts.append(p)
+    return np.array(pts)
+
+
+def _diffuse_voronoi(shape, seeds, W, knn=8, chunk=1 << 18):
+    """Diffuse periodic Voronoi fields: for every grain g among the knn nearest
+    seeds, d_g = min over the other neighbours h of the signed distance to the
+    bisector of (s_g, s_h); trial phi_g = profile(d_g), rescaled to sum 1
+    (the rescaling of Eq. distfix with all trial ratios kept)."""
+    from scipy.spatial import cKDTree
+    dims = len(shape)
+    nz, ny, nx = (shape if dims == 3 else (1,) + tuple(shape))
+    G = len(seeds)
+    box = np.array([nx, ny, nz][:dims], dtype=np.float64)
+    tree = cKDTree(seeds, boxsize=box)
+    V = nx * ny * nz
+    k = min(knn, G)
+    labels_out = np.zeros((k, V), np.int32)
+    phis_out = np.zeros((k, V), np.float64)
+    for s0 in range(0, V, chunk):
+        idx = np.arange(s0, min(V, s0 + chunk))
+        x = idx % nx + 0.5
+        y = (idx // nx) % ny + 0.5
+        z = idx // (nx * ny) + 0.5
+        P = np.stack([x, y, z][:dims], axis=1)
+        _, nn = tree.query(P, k=k)
+        nn = nn.reshape(len(idx), k)
+        S = seeds[nn]                                     # (n, k, dims)
+        Dv = P[:, None, :] - S
+        Dv -= box * np.round(Dv / box)                    # minimum image
+        d2 = (Dv * Dv).sum(-1)                            # (n, k)
+        dist = np.full((len(idx), k), np.inf)
+        for g in range(k):
+            for hh in range(k):
+                if hh == g:
+                    continue
+                sep = S[:, hh, :] - S[:, g, :]
+                sep -= box * np.round(sep / box)
+                ln = np.sqrt((sep * sep).sum(-1))
+                bis = (d2[:, hh] - d2[:, g]) / (2.0 * np.maximum(ln, 1e-12))
+                dist[:, g] = np.minimum(dist[:, g], bis)
+        tr = profile(dist, W)
+        tr /= tr.sum(1, keepdims=True)
+        labels_out[:, idx] = nn.T
+        phis_out[:, idx] = tr.T
+    return labels_out, phis_out
+
+
+def grains(n=256, n_grains=32, min_dist=40.0, seed=2, dim=3, dx=0.005, W_cells=2.5, M=5e-3,
+           gamma=1.0, diffuse=True, dtype=np.float64):
+    """Periodic Voronoi grain structure (Sec. 5.3): seeded Poisson-disc seeds,
+    nearest-seed labelling, dense N = n_grains storage.  diffuse=False gives
+    the sharp one-hot start; diffuse=True gives profile-shaped boundaries."""
+    rng = np.random.default_rng(seed)
+    shape = (n,) * dim
+    seeds = poisson_disc_seeds(shape, n_grains, min_dist, dim, rng)
+    W = W_cells * dx
+    prob = Problem(dim=dim, nx=n, ny=n, nz=n if dim == 3 else 1, dx=dx, n_phases=n_grains,
+                   phase_type=np.ones(n_grains, np.int32),
+                   gamma=uniform_pairs(n_grains, gamma), mobility=uniform_pairs(n_grains, M), W=W,
+                   name="grains%d^%d_N%d" % (n, dim, n_grains))
+    V = prob.V
+    u = np.zeros((n_grains, V), dtype=dtype)
+    if diffuse:
+        lab, ph = _diffuse_voronoi(shape, seeds, W_cells)
+        cols = np.arange(V)
+        for j in range(lab.shape[0]):
+            u[lab[j], cols] += ph[j]
+    else:
+        from scipy.spatial import cKDTree
+        tree = cKDTree(seeds, boxsize=np.full(dim, float(n)))
+        x, y, z = cell_centres(prob.nx, prob.ny, prob.nz, 1.0)
+        P = np.stack([x, y, z][:dim], axis=1)
+        _, lab = tree.query(P, k=1)
+        u[lab, np.arange(V)] = 1.0
+    return prob, u
+
+
+def multiphase_blobs(nx=24, ny=20, nz=1, n_phases=5, seed=0, W=1.6, dx=1.0, has_conc=0,
+                     n_alpha=1, k=(1.0, 1.0), c0=(0.02, 0.98), D=(1.0, 0.5), M=1.0,
+                     gamma=1.0, bc_phi=(0,) * 6, bc_c=(0,) * 6, c_dirichlet=(0.0,) * 6,
+                     min_dist=None):
+    """Small seeded diffuse multi-grain state with triple junctions, used for
+    parity tests on odd grid sizes.  Phases 0..n_alpha-1 have type alpha."""
+    rng = np.random.default_rng(seed)
+    dim = 2 if nz == 1 else 3
+    shape = (nx, ny) if dim == 2 else (nx, ny, nz)
+    md = min_dist if min_dist is not None else 0.5 * (np.prod(shape) / n_phases) ** (1.0 / dim)
+    seeds = poisson_disc_seeds(shape, n_phases, md, dim, rng)
+    lab, ph = _diffuse_voronoi(shape[::-1] if dim == 3 else (ny, nx), seeds, W / dx)
+    V = nx * ny * nz
+    ptype = np.array([0 if a < n_alpha else 1 for a in range(n_phases)], np.int32)
+    gam = typed_pairs(ptype, gamma, 1.3 * gamma)
+    mob = typed_pairs(ptype, M, 0.7 * M)
+    prob = Problem(dim=dim, nx=nx, ny=ny, nz=nz, dx=dx, n_phases=n_phases, phase_type=ptype,
+                   gamma=gam, mobility=mob, W=W, has_conc=has_conc, k=tuple(k), c0=tuple(c0),
+                   D=tuple(D), bc_phi=tuple(bc_phi), bc_c=tuple(bc_c),
+                   c_dirichlet=tuple(c_dirichlet), name="blobs%dx%dx%d_N%d" % (nx, ny, nz, n_phases))
+    u = np.zeros((n_phases + has_conc, V))
+    cols = np.arange(V)
+    for j in range(lab.shape[0]):
+        u[lab[j], cols] += ph[j]
+    if has_conc:
+        # local equilibrium c = sum_a phi_a c0_a plus a seeded smooth perturbation
+        x, y, z = cell_centres(nx, ny, nz, 1.0)
+        pert = 0.02 * np.sin(2 * np.pi * x / nx + rng.random() * 6) * np.cos(2 * np.pi * y / ny)
+        c = sum(u[a] * c0[ptype[a]] for a in range(n_phases)) + pert
+        u[n_phases] = c
+    return prob, u

@@ -1,0 +1,416 @@
+"""Pins of the CPU oracle against things the paper and mathematics fix.
+
+Each test is chosen so that a plausible slip in the oracle (a dropped term, a
+wrong sign, a transposed index, a wrong coefficient table) fails it.  None of
+these tests uses the CUDA engine.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from conftest import golden
+from oracle import ref
+from paper_2601_16522_gb300 import inputs as I
+
+G = golden("paper_numbers.txt")
+TOL = (1e-4, 1e-4, 1e-4, 1e-4)
+
+
+# ---------------------------------------------------------------------------
+# Stable Euler step (Sec. 3.2 Gershgorin reading; printed values in Sec. 5.3)
+# ---------------------------------------------------------------------------
+
+def _particle_problem(M_ab, D_alpha, D_beta=5e-8):
+    dx = 0.005
+    pt = np.array([0, 1, 1], np.int32)
+    return I.Problem(dim=3, nx=4, ny=4, nz=4, dx=dx, n_phases=3, phase_type=pt,
+                     gamma=I.uniform_pairs(3, 1.0), mobility=I.typed_pairs(pt, 5e-3, M_ab),
+                     W=2.5 * dx, has_conc=1, k=(1e5, 1e5), c0=(0.02, 0.98), D=(D_alpha, D_beta))
+
+
+def test_dt_e_reproduces_printed_values():
+    dx = 0.005
+    gg = I.Problem(dim=3, nx=4, ny=4, nz=4, dx=dx, n_phases=2, phase_type=np.array([1, 1], np.int32),
+                   gamma=I.uniform_pairs(2, 1.0), mobility=I.uniform_pairs(2, 5e-3), W=2.5 * dx)
+    cases = [("pure_gg", gg), ("immobile", _particle_problem(5e-8, 5e-8)),
+             ("mobile", _particle_problem(5e-3, 10.0))]
+    for name, prob in cases:
+        dte = ref.Oracle(prob).dt_e()
+        printed = G["dte_" + name]
+        # three printed digits (the paper truncates one value and rounds the
+        # others): agree within one unit of the last printed digit
+        unit = 10.0 ** (math.floor(math.log10(printed)) - 2)
+        assert abs(dte - printed) < unit, (name, dte, printed)
+        count = G["tr_" + name] / dte
+        assert abs(count - G["fe_rhs_" + name]) <= 1.0, (name, count)
+
+
+def test_dt_e_two_phase_closed_form():
+    # For two phases the discrete operator is L A Lap_h + L B; its most negative
+    # eigenvalue is -(L A 4d/dx^2 - L B) = -M gamma (4d/dx^2 - 1/W^2).
+    for dim, dx, W, M, g in [(2, 1.0, 2.5, 1.0, 1.0), (3, 0.5, 1.3, 0.2, 3.0)]:
+        prob = I.Problem(dim=dim, nx=4, ny=4, nz=4 if dim == 3 else 1, dx=dx, n_phases=2,
+                         phase_type=np.array([0, 0], np.int32), gamma=I.uniform_pairs(2, g),
+                         mobility=I.uniform_pairs(2, M), W=W)
+        lam = M * g * (4 * dim / dx ** 2 - 1 / W ** 2)
+        assert ref.Oracle(prob).dt_e() == pytest.approx(2 / lam, rel=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# Integrators on the Dahlquist test equation (footnote of Sec. 5.2.1)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("integ,s,order", [
+    (ref.FEULER, 1, 1), (ref.SSP2, 5, 2), (ref.SSP2, 3, 2), (ref.SSP104, 10, 4),
+    (ref.RKL1, 1, 1), (ref.RKL1, 5, 1), (ref.RKL1, 9, 1),
+    (ref.RKL2, 3, 2), (ref.RKL2, 5, 2), (ref.RKL2, 21, 2)])
+@pytest.mark.parametrize("lam", [-1.0 + 0j, -0.5 + 0.4j])
+def test_dahlquist_order(integ, s, order, lam):
+    if integ in (ref.RKL1, ref.RKL2) and lam.imag != 0:
+        pytest.skip("RKL stability region is a strip along the negative real axis")
+    errs = []
+    for n in (16, 32, 64):
+        u = ref.dahlquist_solve(integ, lam, 1.0, n, s)
+        errs.append(abs(u - np.exp(lam)))
+    p = math.log2(errs[1] / errs[2])
+    assert abs(p - order) < G["dahlquist_order_tol"], (integ, s, p)
+
+
+def _stability_ok(integ, s, zs):
+    return max(abs(ref.dahlquist_step(integ, complex(z, 0.0), s)[0]) for z in zs)
+
+
+@pytest.mark.parametrize("integ,s,bound,tight", [
+    (ref.FEULER, 1, 2.0, True),
+    (ref.SSP2, 5, 2.0 * 4, False),         # (s-1) Delta t_e on the real axis
+    (ref.RKL1, 3, 3 * 3 + 3, True),         # s^2 + s
+    (ref.RKL1, 11, 11 * 11 + 11, True),
+    (ref.RKL2, 5, (25 + 5 - 2) / 2, False),  # (s^2 + s - 2)/2
+    (ref.RKL2, 21, (441 + 21 - 2) / 2, False),
+])
+def test_stability_interval(integ, s, bound, tight):
+    zs = -np.linspace(0.0, bound, 4001)
+    assert _stability_ok(integ, s, zs) <= 1.0 + 1e-12
+    if tight:
+        assert abs(ref.dahlquist_step(integ, complex(-1.02 * bound, 0), s)[0]) > 1.0
+
+
+def test_ssp104_real_axis_limit():
+    # Sec. 3.2 prints Delta t_SSP(10)4 < 6 Delta t_e, i.e. z >= -12 must be stable.
+    limit = G["ssp104_limit"]
+    zs = -np.linspace(0.0, 2.0 * limit, 2001)
+    assert _stability_ok(ref.SSP104, 10, zs) <= 1.0 + 1e-12
+
+
+def test_ssp104_embedded_is_order_three():
+    bh = ref.ssp104_embedded_weights()
+    assert bh.sum() == pytest.approx(1.0, abs=1e-14)
+    assert abs(bh[9]) < 1e-15
+    e_main, e_emb = [], []
+    for z in (0.1, 0.05):
+        R, Rh = ref.dahlquist_step(ref.SSP104, complex(-z, 0.0), 10)
+        e_main.append(abs(R - math.exp(-z)))
+        e_emb.append(abs(Rh - math.exp(-z)))
+    assert math.log2(e_main[0] / e_main[1]) == pytest.approx(5.0, abs=0.1)   # local error h^5
+    assert math.log2(e_emb[0] / e_emb[1]) == pytest.approx(4.0, abs=0.1)     # local error h^4
+
+
+def test_sts_stage_rule():
+    # Sec. 3.2: smallest odd s whose bound with 0.9 dt_e covers dt.
+    # RKL2: (s^2+s-2)/4 * 0.9 >= 10 -> s^2+s-2 >= 44.4 -> s = 7 (5 gives 28).
+    assert ref.sts_stages(ref.RKL2, 10.0, 1.0) == 7
+    # RKL1: (s^2+s)/2 * 0.9 >= 10 -> s^2+s >= 22.2 -> s = 5 (odd; 4 would give 20).
+    assert ref.sts_stages(ref.RKL1, 10.0, 1.0) == 5
+    assert ref.sts_stages(ref.RKL1, 0.9, 1.0) == 1
+    assert ref.sts_stages(ref.RKL2, 0.01, 1.0) == 3
+
+
+def test_sommeijer_estimate_scales_as_local_error():
+    # Sec. 3.3 (sign read so the estimate is a local error): for RKL2 on the
+    # Dahlquist equation e ~ dt^3; the printed sign would give e ~ dt.
+    import ctypes as C
+    lam = np.array([-1.0, 0.0])
+    sysd = ref._Sys()
+    ref.lib().or_sys_dahlquist(C.byref(sysd), lam.ctypes.data_as(ref._dp))
+    es = []
+    for h in (0.1, 0.05, 0.025):
+        u0 = np.array([1.0, 0.0]); u1 = np.zeros(2); rn = np.zeros(2); zz = np.zeros(2)
+        ref.lib().or_step(C.byref(sysd), ref.RKL2, h, 5, u0.ctypes.data_as(ref._dp),
+                          u1.ctypes.data_as(ref._dp), rn.ctypes.data_as(ref._dp),
+                          zz.ctypes.data_as(ref._dp))
+        rn1 = np.array([-u1[0], -u1[1]])
+        t = ref._Tol(0.0, 1.0, 0.0, 1.0)
+        nd = C.c_long()
+        e = ref.lib().or_err_sts(C.byref(sysd), C.byref(t), h, u0.ctypes.data_as(ref._dp),
+                                 u1.ctypes.data_as(ref._dp), rn.ctypes.data_as(ref._dp),
+                                 rn1.ctypes.data_as(ref._dp), C.byref(nd))
+        es.append(e)
+    assert math.log2(es[0] / es[1]) == pytest.approx(3.0, abs=0.1)
+    assert math.log2(es[1] / es[2]) == pytest.approx(3.0, abs=0.1)
+
+
+# ---------------------------------------------------------------------------
+# Model / RHS
+# ---------------------------------------------------------------------------
+
+def test_coefficients_relations():
+    # Sec. 2: L A = M gamma and L B = M gamma / W^2 for L = pi M / (4 W).
+    prob, _ = I.multiphase_blobs(8, 8, 1, 4, seed=1)
+    A, B, L = ref.Oracle(prob).coeffs()
+    Mg = prob.mobility * prob.gamma
+    assert np.allclose(L * A, Mg, rtol=1e-14, atol=0)
+    assert np.allclose(L * B, Mg / prob.W ** 2, rtol=1e-14, atol=0)
+    assert np.allclose(A, prob.W ** 2 * B, rtol=1e-14)
+
+
+def _profile_residual(W, dx):
+    n = int(round(16 * W / dx)) * 2
+    prob = I.Problem(dim=2, nx=n, ny=1, nz=1, dx=dx, n_phases=2,
+                     phase_type=np.array([0, 0], np.int32), gamma=I.uniform_pairs(2, 1.0),
+                     mobility=I.uniform_pairs(2, 1.0), W=W, bc_phi=(1, 1, 0, 0, 0, 0))
+    x = (np.arange(n) + 0.5) * dx - n * dx / 2
+    g = I.profile(x, W)
+    r, nz = ref.Oracle(prob).rhs(np.stack([1 - g, g]))
+    inner = np.abs(x) < math.pi * W / 2 - 1.5   # fixed physical distance from the kinks
+    return np.abs(r[1][inner]).max(), r, nz, x
+
+
+def test_equilibrium_profile_is_stationary():
+    # Eq. profile solves the two-phase equilibrium iff A = B W^2 (Sec. 2); the
+    # FD residual away from the profile's kinks is O(dx^2/W^2) relative to the
+    # curvature scale L A / W^2.
+    res = [_profile_residual(4.0, dx)[0] for dx in (1.0, 0.5, 0.25, 0.125)]
+    scale = 1.0 / 4.0 ** 2  # L A / W^2 with M = gamma = 1
+    assert res[0] / scale < 0.05
+    for i in range(3):
+        assert res[i] / res[i + 1] == pytest.approx(4.0, rel=0.05)
+    # a profile of the wrong width is not stationary
+    W, dx = 4.0, 0.5
+    n = int(round(16 * W / dx)) * 2
+    prob = I.Problem(dim=2, nx=n, ny=1, nz=1, dx=dx, n_phases=2, phase_type=np.array([0, 0], np.int32),
+                     gamma=I.uniform_pairs(2, 1.0), mobility=I.uniform_pairs(2, 1.0), W=W,
+                     bc_phi=(1, 1, 0, 0, 0, 0))
+    x = (np.arange(n) + 0.5) * dx - n * dx / 2
+    g = I.profile(x, 0.7 * W)
+    r, _ = ref.Oracle(prob).rhs(np.stack([1 - g, g]))
+    assert np.abs(r[1]).max() > 50 * res[1]
+
+
+def test_activity_and_nz():
+    _, r, nz, x = _profile_residual(2.0, 1.0)
+    # bulk (trivial) cells have N_z = 0 and zero RHS; interface cells N_z = 2
+    edge = math.pi * 2.0 / 2
+    assert np.all(nz[np.abs(x) > edge + 1.5] == 0)
+    assert np.all(nz[np.abs(x) < edge - 1.0] == 2)
+    assert np.all(r[:, nz == 0] == 0.0)
+
+
+def test_pairwise_rhs_sums_to_zero_and_mass_is_conserved():
+    prob, u = I.multiphase_blobs(17, 13, 1, 5, seed=3, has_conc=1, n_alpha=2)
+    o = ref.Oracle(prob)
+    r, nz = o.rhs(u)
+    N = prob.n_phases
+    s = r[:N].sum(0)
+    assert np.abs(s).max() <= 1e-13 * np.abs(r[:N]).max()
+    assert nz.max() >= 3
+    # periodic flux-difference form: total concentration change is zero
+    assert abs(r[N].sum()) <= 1e-13 * np.abs(r[N]).sum()
+    # 3D as well
+    prob3, u3 = I.multiphase_blobs(9, 7, 6, 4, seed=5, has_conc=1, n_alpha=1)
+    r3, _ = ref.Oracle(prob3).rhs(u3)
+    assert np.abs(r3[:4].sum(0)).max() <= 1e-13 * np.abs(r3[:4]).max()
+    assert abs(r3[4].sum()) <= 1e-13 * np.abs(r3[4]).sum()
+
+
+def test_uniform_two_phase_reduces_to_closed_form():
+    # Uniform state: Lap = 0 and the pairwise equation reduces to
+    # dphi_1/dt = L B (phi_1 - 1/2) - (L/2)(psi_1 - psi_0)   (two phases),
+    # with psi_a = -mu^2/(2 k_a) - mu c0_a and c built from a chosen mu by the
+    # forward map c = sum phi_a (c0_a + mu/k_a)  (Sec. 2).
+    k, c0 = (2.0, 5.0), (0.1, 0.8)
+    prob = I.Problem(dim=2, nx=3, ny=3, nz=1, dx=1.0, n_phases=2, phase_type=np.array([0, 1], np.int32),
+                     gamma=I.uniform_pairs(2, 0.7), mobility=I.uniform_pairs(2, 1.3), W=1.7,
+                     has_conc=1, k=k, c0=c0, D=(1.0, 1.0))
+    o = ref.Oracle(prob)
+    _, B, L = o.coeffs()
+    for phi1, mu in [(0.3, 0.05), (0.8, -0.2)]:
+        phi = np.array([1 - phi1, phi1])
+        c = sum(phi[a] * (c0[a] + mu / k[a]) for a in range(2))
+        u = np.zeros((3, 9))
+        u[0], u[1], u[2] = phi[0], phi[1], c
+        r, nz = o.rhs(u)
+        psi = [-mu * mu / (2 * k[a]) - mu * c0[a] for a in range(2)]
+        expect = L[0, 1] * B[0, 1] * (phi1 - 0.5) - 0.5 * L[0, 1] * (psi[1] - psi[0])
+        assert np.allclose(r[1], expect, rtol=1e-12, atol=1e-15)
+        assert np.all(nz == 2)
+        assert np.allclose(r[2], 0.0, atol=1e-15)
+
+
+def test_dirichlet_linear_concentration_is_steady():
+    # Bulk single phase, c linear between two Dirichlet faces: the ghost
+    # 2 c_b - c_i puts the face value at c_b, so the FD flux divergence is 0.
+    nx, ny = 12, 3
+    prob = I.Problem(dim=2, nx=nx, ny=ny, nz=1, dx=0.5, n_phases=2, phase_type=np.array([0, 1], np.int32),
+                     gamma=I.uniform_pairs(2, 1.0), mobility=I.uniform_pairs(2, 1.0), W=1.0,
+                     has_conc=1, k=(1.0, 3.0), c0=(0.02, 0.98), D=(2.0, 1.0),
+                     bc_phi=(1, 1, 0, 0, 0, 0), bc_c=(2, 2, 0, 0, 0, 0), c_dirichlet=(0.3, 0.9, 0, 0, 0, 0))
+    x = (np.arange(nx) + 0.5) * 0.5
+    c = 0.3 + (0.9 - 0.3) * x / (nx * 0.5)
+    u = np.zeros((3, nx * ny))
+    u[0] = 1.0
+    u[2] = np.tile(c, ny)
+    r, _ = ref.Oracle(prob).rhs(u)
+    assert np.abs(r[2]).max() < 1e-13
+    # a non-linear profile is not steady, and its net change equals the boundary fluxes
+    u[2] = np.tile(0.3 + 0.6 * (x / (nx * 0.5)) ** 2, ny)
+    r, _ = ref.Oracle(prob).rhs(u)
+    assert np.abs(r[2]).max() > 1e-3
+
+
+def test_projection_special_cases():
+    prob = I.Problem(dim=2, nx=4, ny=1, nz=1, dx=1.0, n_phases=3, phase_type=np.zeros(3, np.int32),
+                     gamma=I.uniform_pairs(3, 1.0), mobility=I.uniform_pairs(3, 1.0), W=1.0)
+    o = ref.Oracle(prob)
+    u = np.array([[-0.1, 1.2, 1.0, 0.2],
+                  [0.6, -0.1, 1.0, 0.3],
+                  [0.5, 0.3, 0.0, 0.5]])
+    p, acted, st = o.project(u)
+    assert st == 0
+    np.testing.assert_allclose(p[:, 0], [0.0, 0.6 / 1.1, 0.5 / 1.1], rtol=1e-15)
+    np.testing.assert_array_equal(p[:, 1], [1.0, 0.0, 0.0])   # >= 1 wins, others zeroed
+    np.testing.assert_array_equal(p[:, 2], [1.0, 0.0, 0.0])   # tie -> lowest id
+    np.testing.assert_allclose(p[:, 3], [0.2, 0.3, 0.5], rtol=1e-15)
+    np.testing.assert_array_equal(acted, [1, 1, 1, 0])
+
+
+def test_controller_bias_and_direction():
+    # Sec. 3.3: bias starts at 0.9, is squared on rejection down to 0.1 and
+    # square-rooted on acceptance up to 0.98; a rejection never enlarges dt.
+    seq = ref.ctrl_sequence([2.0, 3.0, 5.0, 9.0, 2.0], [1.0] * 5, 2)
+    bs = [b for _, _, b in seq]
+    assert bs == pytest.approx([0.81, 0.6561, 0.43046721, 0.1853020188851841, 0.1], rel=1e-14)
+    assert all(nxt < 1.0 for nxt, acc, _ in seq)
+    assert all(acc == 0 for _, acc, _ in seq)
+    seq = ref.ctrl_sequence([0.1] * 6, [1.0] * 6, 2)
+    assert all(acc == 1 for _, acc, _ in seq)
+    assert seq[-1][2] == 0.98
+    assert all(nxt > 1.0 for nxt, _, _ in seq)
+    # first step, no history: F = (e/b)^(-k1/(P+1)), dt' = dt (1 + 5 atan((F-1)/5)).
+    # e = 0.5, b = 0.9, P = 2:  E = 0.5555..., F = E^(-5/12) = 1.2775078,
+    # dt' = 1 + 5 atan(0.0555016) = 1.2772233 (worked out separately)
+    nxt, acc, b = ref.ctrl_sequence([0.5], [1.0], 2)[0]
+    assert nxt == pytest.approx(1.2772233, abs=2e-7)
+    assert acc == 1 and b == pytest.approx(math.sqrt(0.9), rel=1e-15)
+    # the step factor saturates: 1 + 5 atan(inf) = 1 + 5 pi/2
+    nxt, _, _ = ref.ctrl_sequence([0.0], [1.0], 2)[0]
+    assert nxt < 1 + 5 * math.pi / 2
+
+
+def test_error_norm_dof_count():
+    # Sec. 3.3: phase entries count only where e != 0, an all-zero phase cell
+    # counts as 2 DoF, every concentration entry counts.  3 cells, N=2, K=1.
+    prob = I.Problem(dim=2, nx=3, ny=1, nz=1, dx=1.0, n_phases=2, phase_type=np.array([0, 1], np.int32),
+                     gamma=I.uniform_pairs(2, 1.0), mobility=I.uniform_pairs(2, 1.0), W=1.0,
+                     has_conc=1, k=(1.0, 1.0), c0=(0.0, 1.0), D=(1.0, 1.0))
+    o = ref.Oracle(prob)
+    un = np.array([[0.5, 1.0, 0.4], [0.5, 0.0, 0.6], [0.3, 0.3, 0.3]])
+    unew = un.copy()
+    z = un.copy()
+    z[0, 0] += 0.01; z[1, 0] -= 0.01          # cell 0: two nonzero phase errors
+    z[0, 2] += 0.02                            # cell 2: one nonzero phase error
+    z[2, 1] += 0.001                           # a concentration error in cell 1
+    z[1, 1] = -0.5                             # outside [0,1]: filtered to zero error
+    tol = (0.0, 0.01, 0.0, 0.001)
+    e, nd = o.err_embedded(tol, un, unew, z)
+    assert nd == 2 + 2 + 1 + 3
+    expect = math.sqrt((1 + 1 + 4 + 1) / 8.0)
+    assert e == pytest.approx(expect, rel=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Integrator invariants on the PDE
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("integ,s", [(ref.FEULER, 1), (ref.SSP2, 5), (ref.SSP104, 10),
+                                     (ref.RKL1, 7), (ref.RKL2, 7)])
+def test_step_keeps_simplex_and_mass(integ, s):
+    prob, u = I.multiphase_blobs(13, 11, 1, 4, seed=7, has_conc=1, n_alpha=1)
+    o = ref.Oracle(prob)
+    dt = 3.0 * o.dt_e() if integ in (ref.RKL1, ref.RKL2) else 0.5 * o.dt_e()
+    un, rn, z, ev = o.step(integ, dt, s, u)
+    N = prob.n_phases
+    assert ev == {ref.FEULER: 1, ref.SSP2: s, ref.SSP104: 10}.get(integ, s)
+    assert un[:N].min() >= 0.0
+    assert np.abs(un[:N].sum(0) - 1.0).max() < 1e-14
+    assert abs(un[N].sum() - u[N].sum()) < 1e-12 * abs(u[N].sum())
+
+
+def test_rkl2_first_stage_fix_lands_inside_simplex():
+    # Sec. 3.2: where S acts on stage 1, F(u^n) is replaced by
+    # (S(u^{n,1}) - u^n)/(mu~_1 dt), so that u^n + mu~_1 dt F_eff is the
+    # projected first stage.  With a step large enough to trigger S we check
+    # that identity on the effective RHS returned by the oracle.
+    prob, u = I.circle(24, 6.0, W=1.2)
+    o = ref.Oracle(prob)
+    dt = 200 * o.dt_e()
+    s = ref.sts_stages(ref.RKL2, dt, o.dt_e())
+    un, rn, _, _ = o.step(ref.RKL2, dt, s, u)
+    r0, _ = o.rhs(u)
+    w1 = 4.0 / (s * s + s - 2)
+    mt1 = w1 / 3.0
+    y1 = u + (mt1 * dt) * rn
+    changed = np.any(np.abs(rn - r0) > 1e-12, axis=0)
+    assert changed.any()
+    y1p, _, _ = o.project(y1)
+    np.testing.assert_allclose(y1p, y1, atol=1e-12)
+    assert y1[:2].min() >= -1e-12
+
+
+# ---------------------------------------------------------------------------
+# Full model against the sharp-interface laws (Sec. 5.2)
+# ---------------------------------------------------------------------------
+
+def test_circle_area_law():
+    # Sec. 5.2.1: A(t) - A(0) = -2 pi M gamma t; error of dA/dt for t > 0
+    # (average of 2nd-order FD derivatives).  W = 2.5 as in the paper.
+    prob, u = I.circle(128, 40.0, W=2.5)
+    o = ref.Oracle(prob)
+    ts, A = [0.0], [u[1].sum()]
+    t = 0.0
+    for k in range(8):
+        st, u, t, _ = o.run(ref.FEULER, u, t, t + 25.0, dt_mult=0.9)
+        assert st == 0
+        ts.append(t); A.append(u[1].sum())
+    dA = np.gradient(np.array(A), np.array(ts))[1:].mean()
+    rel = abs(dA + 2 * math.pi) / (2 * math.pi)
+    assert rel < 1.5 * G["grain_rel_err"], rel
+    assert dA < 0
+
+
+def test_stefan_growth_constant_and_front():
+    # Eq. stefangrowth with the Sec. 5.2.2 values gives A = 0.2412.
+    A = I.stefan_growth_constant()
+    assert A == pytest.approx(G["stefan_A"], abs=6e-5)
+    prob, u = I.stefan(nx=512, ny=1, h=150.0, W=2.5, D_solid=1.0)
+    o = ref.Oracle(prob)
+
+    def front(v):
+        liq = v[0]
+        j = int(np.argmax(liq >= 0.5))
+        xs = (np.arange(j - 2, j + 2) + 0.5)
+        r = np.roots(np.polyfit(xs, liq[j - 2:j + 2] - 0.5, 3))
+        r = r[np.isreal(r)].real
+        return r[(r >= xs[0]) & (r <= xs[-1])][0]
+
+    x0 = front(u)
+    t, ts, X = 0.0, [], []
+    for T in np.linspace(1000.0, 6000.0, 6):
+        st, u, t, _ = o.run(ref.RKL2, u, t, T, tol=(1e-4, 1e-2, 1e-4, 1e-4))
+        assert st == 0 and t == T
+        ts.append(t); X.append(front(u) - x0)
+    ts, X = np.array(ts), np.array(X)
+    Afit = (np.sqrt(ts) * X).sum() / ts.sum()
+    assert abs(Afit - A) / A < 0.03, Afit
+    # concentration is not conserved here (Dirichlet faces) but phases are on the simplex
+    assert np.abs(u[:2].sum(0) - 1).max() < 1e-13
