@@ -653,6 +653,14 @@ int or_run(const or_params *p, int integ, double t_end, const or_tol *tol,
            *rn1 = malloc(sizeof(double) * n), *z = malloc(sizeof(double) * n);
     int status = OR_OK, ntr = 0, attempt = 0;
     double dt = adaptive ? (st->dt_next > 0.0 ? st->dt_next : (dt0 > 0.0 ? dt0 : 0.9 * dte)) : dt_mult * dte;
+    /* fixed steps: the k-th step ends at t0 + k dt (no accumulated drift) and
+       the last one is shortened to land on t_end (Sec. 5) */
+    double t0 = *t;
+    long nfix = 0, kfix = 0;
+    if (!adaptive) {
+        nfix = (long)ceil((t_end - t0) / dt - 1e-9);
+        if (nfix < 1) nfix = 1;
+    }
     while (*t < t_end) {
         double rem = t_end - *t, h;
         int s, last = 0;
@@ -660,11 +668,17 @@ int or_run(const or_params *p, int integ, double t_end, const or_tol *tol,
             if (attempt >= replay_n) break;
             h = replay_dt[attempt];
             s = replay_s[attempt];
-            last = (h >= rem * (1.0 - 1e-12));
+            last = (h >= rem * (1.0 - 1e-9));
         } else {
-            h = dt;
-            if (h >= rem * (1.0 - 1e-12)) { h = rem; last = 1; }
+            if (adaptive) {
+                h = dt;
+                if (h >= rem * (1.0 - 1e-9)) { h = rem; last = 1; }
+            } else {
+                last = (kfix + 1 >= nfix);
+                h = last ? rem : dt;
+            }
             s = sts ? or_sts_stages(integ, h, dte) : (integ == OR_SSP2 ? ssp_stages : (integ == OR_SSP104 ? 10 : 1));
+            if (sts && s > max_stages && !adaptive) { status = OR_EINVAL; break; }
             if (sts && s > max_stages) {
                 s = max_stages | 1;
                 double ds = (double)s;
@@ -704,7 +718,8 @@ int or_run(const or_params *p, int integ, double t_end, const or_tol *tol,
         attempt++;
         if (acc) {
             memcpy(u, unew, sizeof(double) * n);
-            *t = last ? t_end : *t + h;
+            if (!adaptive && replay_n == 0) { kfix++; *t = last ? t_end : t0 + (double)kfix * dt; }
+            else *t = last ? t_end : *t + h;
             st->accepted++;
         } else {
             st->rejected++;
