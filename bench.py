@@ -1,0 +1,333 @@
+#!/usr/bin/env python
+"""Benchmark: GCell-updates/s of the explicit phase-field step on one GB300.
+
+Workload (default ``grains256``): 3D grain growth, 256^3 periodic cells, 32
+grains from a seeded periodic Voronoi tessellation with diffuse boundaries,
+dense N = 32 phase storage in FP32 (FP64 time, coefficients and reductions),
+paper units dx = 0.005, W = 2.5 dx, M = 5e-3, gamma = 1.  One step = one
+attempted adaptive RKL2 step (Sec. 3.2-3.3): s fused stage passes (RHS, stage
+combination, simplex projection, first-stage fix), the error sweep with the
+weighted norm, and the PID controller.  Every state vector (2.1 GB) is larger
+than L2, so no flush is needed between steps.
+
+value = cells x RHS sweeps / device time (max over ranks, summed over ranks),
+e2e   = the same through the C ABI with host buffers (pinned) copied in and out
+        every step.
+
+``--impl reference`` times the CPU oracle (the only reference this method has)
+on a bounded sample of the same workload and prints the same line.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+TOL = (1e-4, 1e-2, 1e-4, 1e-3)          # r_phi, a_phi, r_c, a_c (Sec. 5.3 runs)
+METRIC = "GCell-updates/s"
+UNIT = "GCell/s"
+
+
+def workload_problem(name, device):
+    from paper_2601_16522_gb300 import inputs as I
+    if name == "grains256":
+        prob, u = I.grains_device(n=256, n_grains=32, min_dist=40.0, seed=2, dim=3, device=device)
+        return prob, u, 32
+    if name == "grains128":
+        prob, u = I.grains_device(n=128, n_grains=32, min_dist=20.0, seed=2, dim=3, device=device)
+        return prob, u, 32
+    raise SystemExit("unknown workload %s" % name)
+
+
+# algorithmic vectors moved per pass kind (reads + writes of whole state vectors)
+PASS_VECTORS = {"rkl2": 5, "rkl1": 3, "sts_first": 3, "sts_err": 3, "euler": 2, "ssp": 2, "rhs": 1}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.out = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thr = threading.Thread(target=self._read, daemon=True)
+            self.thr.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.out.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.out:
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world, device=None):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def oracle_sample(u_host_sub, prob_sub, s=5):
+    """Time the CPU oracle on one RKL2 step (s stages + error sweep) of a sub-box."""
+    from oracle import ref
+    o = ref.Oracle(prob_sub)
+    dte = o.dt_e()
+    dt = 0.9 * dte * ((s * s + s - 2) / 4.0) * 0.999
+    t0 = time.perf_counter()
+    _, e, _ = o.step_error(ref.RKL2, dt, s, u_host_sub, TOL)
+    el = time.perf_counter() - t0
+    sweeps = s + 1
+    return prob_sub.V * sweeps / el / 1e9, el, sweeps
+
+
+def sub_box(prob, u_dev, m):
+    """Periodic m^3 sub-box (corner at the origin) of a 3D state, on the host."""
+    import numpy as np
+    n = prob.nx
+    N = prob.n_phases
+    u3 = u_dev.reshape(N, n, n, n)[:, :m, :m, :m].contiguous().cpu().numpy().reshape(N, -1)
+    sub = prob.with_(nx=m, ny=m, nz=m, name=prob.name + "_sub%d" % m)
+    return sub, np.ascontiguousarray(u3)
+
+
+def reference_sub_box(name, m):
+    """The corner m^3 block of the workload's state, generated on the host only."""
+    from paper_2601_16522_gb300 import inputs as I
+    kw = dict(n=256, n_grains=32, min_dist=40.0) if name == "grains256" else dict(n=128, n_grains=32, min_dist=20.0)
+    prob, u = I.grains_device(seed=2, dim=3, device="cpu", region=m, **kw)
+    return prob.with_(nx=m, ny=m, nz=m, name=prob.name + "_sub%d" % m), u.numpy()
+
+
+def run_reference(args, world, rank):
+    """CPU oracle arm: each step is one oracle RKL2 step on a bounded sub-box."""
+    if rank != 0:
+        return
+    m = 40
+    sub, us = reference_sub_box(args.workload, m)
+    vals = []
+    tot_el, tot_cells = 0.0, 0.0
+    for k in range(args.warmup + args.steps):
+        v, el, sweeps = oracle_sample(us, sub)
+        if k >= args.warmup:
+            tot_el += el
+            tot_cells += sub.V * sweeps
+    value = tot_cells / tot_el / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload + " (oracle on a %d^3 periodic sub-box)" % m},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "one RKL2 step (s=5) + error sweep on a %d^3 sub-box of the same 32-phase state" % m},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+    from paper_2601_16522_gb300 import build as pkg_build
+    pkg_build.build()
+    from paper_2601_16522_gb300 import pf
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    prob, u, prec = workload_problem(args.workload, dev)
+    V, N = prob.V, prob.n_phases
+    sim = pf.Simulation(prob, precision=prec, stream=stream)
+    torch.cuda.synchronize()
+    sim.set_state(u)
+    torch.cuda.synchronize()
+
+    def one_step():
+        return sim.step(pf.RKL2, 1e30, tol=TOL, max_attempts=1)
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    barrier(world)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    sim.profile(1)
+    l0 = sim.launch_count()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    sweeps, ss, acc = 0, [], 0
+    for _ in range(args.steps):
+        st = one_step()
+        sweeps += st["rhs_evals"]
+        acc += st["steps_accepted"]
+        ss.append(st["rhs_evals"])
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    ms = ev0.elapsed_time(ev1)
+    launches = sim.launch_count() - l0
+    prof = sim.profile(0)
+    clk = clocks.stop()
+    ms_max = max_over_ranks(ms, world, dev)
+    value = world * V * sweeps / (ms_max * 1e-3) / 1e9
+
+    # roofline of the dominant pass kind
+    kinds = {k: v for k, v in prof.items() if v[1] > 0 and k in PASS_VECTORS}
+    dom = max(kinds, key=lambda k: kinds[k][0]) if kinds else None
+    vec_bytes = V * (N + prob.has_conc) * (4 if prec == 32 else 8)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    peak = peaks.get("hbm_gbs", 6800.0)
+    roof = None
+    if dom:
+        ms_k, n_k = kinds[dom]
+        bytes_launch = PASS_VECTORS[dom] * vec_bytes
+        achieved = bytes_launch / (ms_k / n_k * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "cell_kernel<float,32> (%s pass)" % dom,
+                "bytes_per_launch": bytes_launch, "avg_launch_ms": ms_k / n_k,
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+    pass_ms = {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items() if v[1] > 0}
+
+    # end-to-end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        host_in = torch.empty((N + prob.has_conc, V), dtype=torch.float64, pin_memory=True)
+        host_out = torch.empty_like(host_in, pin_memory=True)
+        host_in.copy_(u.to("cpu"))
+        # settled step size: the controller's current proposal
+        st_probe = sim.step(pf.RKL2, 1e30, tol=TOL, max_attempts=1)
+        dt_settled = st_probe["dt_next"]
+        torch.cuda.synchronize()
+        n_e2e = max(1, min(args.steps, 3))
+        e_sweeps = 0
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            sim.set_state(host_in, 0.0)
+            st = sim.step(pf.RKL2, 1e30, tol=TOL, dt0=dt_settled, max_attempts=1)
+            e_sweeps += st["rhs_evals"]
+            sim.get_state(out=host_out.numpy())
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        el = max_over_ranks(el, world, dev)
+        bi = host_in.numel() * 8
+        e2e = {"value": world * V * e_sweeps / el / 1e9, "unit": UNIT, "h2d_bytes_per_step": bi,
+               "d2h_bytes_per_step": bi, "steps": n_e2e}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        m = 48
+        sub, us = sub_box(prob, u, m)
+        v, el, sw = oracle_sample(us, sub)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "one RKL2 step (s=5) + error sweep on a %d^3 sub-box of the same state, %.1f s" % (m, el)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == 32 else "f64",
+            "data": "synthetic",
+            "config": {"workload": "3D grain growth %s: %dx%dx%d periodic, %d dense phases, FP32 storage, "
+                                   "adaptive RKL2 (tol r=%g a_phi=%g)" % (args.workload, prob.nx, prob.ny,
+                                                                           prob.nz, N, TOL[0], TOL[1]),
+                       "cells": V, "phases": N, "integrator": "rkl2-adaptive", "parallelism": "replicas",
+                       "l2": "state vectors %.2f GB each > L2 (no flush needed)" % (vec_bytes / 1e9)},
+            "sweeps": sweeps, "stages_per_step": ss, "accepted": acc,
+            "roofline": roof, "pass_ms": pass_ms,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    sim.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="grains256")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

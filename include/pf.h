@@ -1,0 +1,192 @@
+/*
+ * pf.h -- C ABI of libpf, a GB300 (sm_103a) engine for one explicit time step
+ * of the obstacle-potential multi-phase-field model coupled to a KKS
+ * concentration field, and for the explicit integrators compared by
+ * M. Seiz and T. Takaki, "Numerical efficiency of explicit time integrators
+ * for phase-field models", arXiv 2601.16522 (cited below as "the paper").
+ *
+ * Conventions for every entry point:
+ *  - Every call returns an int status (pf_status).  Nothing throws or aborts
+ *    across the ABI; pf_strerror() gives a short text.
+ *  - The caller owns every pointer it passes; the library copies what it needs
+ *    (set/get) and owns its device buffers, which live until pf_destroy().
+ *  - Work is ordered on the CUDA stream given to pf_create (NULL: the legacy
+ *    default stream).  A handle is not thread-safe; distinct handles are
+ *    independent.  All device memory of a handle belongs to the device that
+ *    was current at pf_create and that device must be current at every call.
+ *  - Field layout at the ABI ("phase-major"): a state holds
+ *    phi[a * V + i] for phases a = 0..N-1 and, when has_conc = 1, the
+ *    concentration c[i], with i = (z * ny + y) * nx + x (x fastest),
+ *    V = nx * ny * nz.  Values cross the ABI as double; in precision 32 the
+ *    library converts on the way in and out.
+ *  - ptr_is_device: 0 = host pointers (pageable or pinned; the call copies and
+ *    synchronises the stream before returning), 1 = device pointers on the
+ *    handle's device (stream-ordered, no synchronisation).
+ */
+#ifndef PF_H
+#define PF_H
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+typedef enum {
+    PF_OK = 0,
+    PF_EINVAL = 1,      /* invalid argument or unsupported combination            */
+    PF_ENOMEM = 2,      /* device or host allocation failed                         */
+    PF_EUNSTABLE = 3,   /* NaN/Inf error norm, non-positive simplex sum, or too
+                           many rejected steps; the last accepted state is kept  */
+    PF_ETIMEOUT = 4,    /* a bounded device wait gave up                            */
+    PF_EDEVICE = 5,     /* a CUDA call failed (launch, copy, no device)             */
+    PF_ESTATE = 6       /* no state has been set yet                                */
+} pf_status;
+
+/* Integrators of Sec. 3.2: forward Euler, SSP(s)2 and SSP(10)4 (Ketcheson
+   2008, the low-storage forms with one extra buffer), and the
+   Runge-Kutta-Legendre super-time-stepping schemes of order 1 and 2
+   (Eq. sts with Legendre coefficients of Meyer et al. 2012/2014). */
+typedef enum { PF_FEULER = 0, PF_SSP2 = 1, PF_SSP104 = 2, PF_RKL1 = 3, PF_RKL2 = 4 } pf_integrator;
+
+/* Boundary conditions per face (Sec. 4: periodic by default; Sec. 5.2.2:
+   zero-gradient phase field and Dirichlet concentration).  A periodic face
+   requires its opposite face to be periodic for both phi and c. */
+typedef enum { PF_BC_PERIODIC = 0, PF_BC_NEUMANN = 1, PF_BC_DIRICHLET = 2 } pf_bc;
+
+/* Problem description (Sec. 2 model, Sec. 3 discretisation).  All arrays are
+   read during pf_create only. */
+typedef struct {
+    int dim;                  /* 2 or 3 */
+    int nx, ny, nz;           /* cells; nz = 1 when dim = 2 */
+    double dx;                /* grid spacing */
+    int n_phases;             /* N >= 2 phases stored densely.  At most 12 of them may be
+                                 nontrivial (the n(phi) filter of Eq. phieq) in any one cell,
+                                 the per-cell capacity N_p = 12 the paper uses (Sec. 3.1);
+                                 more is reported as PF_EINVAL by the call that meets it. */
+    const int *phase_type;    /* N entries, chemical type 0 (alpha) or 1 (beta), Sec. 2 */
+    const double *gamma;      /* N*N interface energies gamma_ab, symmetric (diag ignored) */
+    const double *mobility;   /* N*N interface mobilities M_ab, symmetric (diag ignored) */
+    double W;                 /* interface parameter, interface width pi*W (Eq. profile) */
+    const double *L_override; /* NULL: L_ab = pi M_ab / (4 W) (Sec. 2); else N*N phase-field
+                                 mobilities (e.g. Eq. thin-interface) */
+    int has_conc;             /* K: 0 or 1 concentration field (Eq. ceq) */
+    double k[2], c0[2], D[2]; /* per chemical type: k_t, c_{0,t} (Eq. gibbs-energy), D_t (Eq. ceq) */
+    int bc_phi[6];            /* pf_bc per face x-, x+, y-, y+, z-, z+ (periodic or Neumann) */
+    int bc_c[6];              /* pf_bc per face for c (periodic, Neumann or Dirichlet) */
+    double c_dirichlet[6];    /* Dirichlet value of c per face */
+    int precision;            /* 64: FP64 storage and arithmetic; 32: FP32 storage and stencil
+                                 arithmetic, FP64 time, coefficients and reductions */
+} pf_params;
+
+/* Error tolerances of the weighted norm (Eq. error_norm): relative r and
+   absolute a per field (phase field, concentration). */
+typedef struct { double r_phi, a_phi, r_c, a_c; } pf_tol;
+
+typedef struct {
+    int ssp_stages;    /* s for PF_SSP2 (>= 2); ignored otherwise */
+    double dt_mult;    /* > 0: fixed dt = dt_mult * dt_e; 0: adaptive (SSP104, RKL1, RKL2) */
+    double dt0;        /* first adaptive step (0: 0.9 * dt_e); ignored if a previous adaptive
+                          call left a proposal for the next step */
+    int max_stages;    /* cap on RKL stages (0: 1001) */
+    int max_attempts;  /* stop after this many attempted steps (0: no limit); the call then
+                          returns PF_OK with t < t_end */
+    /* Optional trace of attempted steps (NULL to skip): step size, stages,
+       error norm and accepted flag, up to trace_cap entries. */
+    int trace_cap;
+    double *trace_dt;
+    int *trace_s;
+    double *trace_err;
+    int *trace_acc;
+    int *trace_len;
+} pf_step_opts;
+
+typedef struct {
+    long long rhs_evals;       /* RHS sweeps, including rejected steps and STS error sweeps */
+    long long steps_accepted;
+    long long steps_rejected;
+    double t;                  /* simulated time after the call */
+    double dt_last;            /* size of the last attempted step */
+    double err_last;           /* error norm of the last attempted step (0 for fixed steps) */
+    double dt_e;               /* stable explicit Euler step used (Sec. 3.2) */
+    double dt_next;            /* adaptive proposal for the next step */
+    long long kernel_launches; /* CUDA kernels this call launched */
+} pf_stats;
+
+/* Create a handle for one simulation.  cuda_stream is a cudaStream_t (NULL:
+   default stream).  Allocates the device buffers of every integrator
+   (5 state vectors) plus reduction scratch.  PF_EINVAL on bad parameters,
+   PF_ENOMEM when the device cannot hold the buffers. */
+int pf_create(const pf_params *params, void *cuda_stream, struct pf_handle **out);
+
+/* Set the state u (phase-major, (N + K) * V doubles; c may be NULL when
+   K = 0 and is read from c otherwise) at time t.  Resets the step
+   controller (Sec. 3.3).  PF_EINVAL on NULL phi. */
+int pf_set_state(struct pf_handle *h, const double *phi, const double *c, double t, int ptr_is_device);
+
+/* Semi-discrete RHS of the current state (Eq. phieq with the leading minus
+   sign of the gradient flow, Eq. ceq; Sec. 3 second-order FD with face-flux
+   differences), written phase-major: rhs_phi (N * V) and, when K = 1,
+   rhs_c (V; may be NULL).  nz (V bytes, may be NULL) receives N_z, the
+   number of nontrivial phases per cell (Sec. 3.1).  No state change. */
+int pf_rhs(struct pf_handle *h, double *rhs_phi, double *rhs_c, unsigned char *nz, int ptr_is_device);
+/* (pf_rhs synchronises the stream to read the kernel's status flags.) */
+
+/* Advance to exactly t_end (Sec. 5: output at defined target times) with the
+   given integrator.  Fixed steps (opts->dt_mult > 0): dt = dt_mult * dt_e, the
+   last step shortened to land on t_end; RKL stage count from the rule of
+   Sec. 3.2.  Adaptive (dt_mult = 0; PF_SSP104, PF_RKL1, PF_RKL2 only): the
+   error estimate and norm of Sec. 3.3 and the PID controller with bias.  The
+   simplex projection is applied to every stage.  tol may be NULL for fixed
+   steps; opts may be NULL (defaults: s = 5, adaptive, dt0 = 0.9 dt_e).
+   stats may be NULL.  PF_EUNSTABLE leaves the last accepted state. */
+int pf_step(struct pf_handle *h, pf_integrator integ, double t_end, const pf_tol *tol,
+            const pf_step_opts *opts, pf_stats *stats);
+
+/* Copy the state out (phase-major doubles; c may be NULL), N_z of the
+   current state (nz, V bytes, may be NULL) and the time (t, may be NULL). */
+int pf_get_state(struct pf_handle *h, double *phi, double *c, unsigned char *nz, double *t,
+                 int ptr_is_device);
+
+/* Conserved totals (host outputs, FP64, deterministic): mass_c = sum c dV
+   (0 when K = 0), vol_phi[a] = sum phi_a dV (N entries, may be NULL), and
+   grains_alive = number of phases whose maximum is >= 0.5 (may be NULL). */
+int pf_reduce(struct pf_handle *h, double *mass_c, double *vol_phi, int *grains_alive);
+
+/* Stable explicit Euler step dt_e = 2 / max(lambda_phi, lambda_c) from the
+   Gershgorin reading of Sec. 3.2 (the estimates themselves are in the
+   paper's supplement; the reading reproduces the three values printed in
+   Sec. 5.3). */
+int pf_dt_e(struct pf_handle *h, double *dt_e);
+
+/* Kinds of fused passes, for pf_profile. */
+enum {
+    PF_PASS_EULER = 0,       /* forward Euler stage */
+    PF_PASS_SSP = 1,         /* SSP(s)2 / SSP(10)4 stages */
+    PF_PASS_STS_FIRST = 2,   /* RKL stage 1 (stores F(u^n), RKL2 first-stage fix) */
+    PF_PASS_RKL1 = 3,        /* RKL1 stages j >= 2 */
+    PF_PASS_RKL2 = 4,        /* RKL2 stages j >= 2 */
+    PF_PASS_STS_ERR = 5,     /* RKL error sweep: F(u^{n+1}), estimate and norm partials */
+    PF_PASS_RHS = 6,         /* pf_rhs / N_z */
+    PF_PASS_OTHER = 7,       /* reductions and layout conversion */
+    PF_NPASS_KINDS = 8
+};
+
+/* Per-pass device timing with CUDA events recorded on the handle's stream
+   around each fused pass (not part of the method; for measurement).  Reads
+   the totals accumulated since the last reset into ms[PF_NPASS_KINDS] and
+   launches[PF_NPASS_KINDS] (either may be NULL; synchronises), then
+   enable = 1 resets and starts recording, enable = 0 resets and stops,
+   enable = -1 keeps the totals and the current setting. */
+int pf_profile(struct pf_handle *h, int enable, double *ms, long long *launches);
+
+/* Number of CUDA kernels launched by this handle since pf_create (-1 on NULL). */
+long long pf_launch_count(struct pf_handle *h);
+
+/* Release every device buffer of the handle.  NULL is accepted. */
+int pf_destroy(struct pf_handle *h);
+
+const char *pf_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

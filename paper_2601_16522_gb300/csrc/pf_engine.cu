@@ -1,0 +1,996 @@
+// pf_engine.cu -- host engine and C ABI of libpf (see include/pf.h).
+//
+// The engine owns five device state vectors per handle (cell-record layout,
+// see pf_kernels.cuh) and drives the fused stage pass for every integrator of
+// Sec. 3.2 of Seiz & Takaki (arXiv 2601.16522), the error estimate and norm of
+// Sec. 3.3 (deterministic two-level FP64 reduction) and the PID controller
+// with bias.  Only scalars cross the host/device boundary per adaptive step.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "../../include/pf.h"
+#include "pf_internal.h"
+
+using pfk::Geom;
+using pfk::Pass;
+
+namespace {
+
+const double kPi = 3.14159265358979323846;
+constexpr int NBUF = 5;
+
+// ---------------------------------------------------------------------------
+// auxiliary kernels: layout conversion and reductions
+// ---------------------------------------------------------------------------
+
+// ABI layout (FP64, field stride V) -> engine layout (T, field stride Vs)
+template <typename T>
+__global__ void pack_kernel(const double *__restrict__ src, T *__restrict__ dst, long long V, long long Vs, int NF)
+{
+    const long long n = V * NF;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        const long long f = k / V;
+        const long long i = k - f * V;
+        dst[f * Vs + i] = (T)src[k];
+    }
+}
+
+// engine layout -> ABI layout
+template <typename T>
+__global__ void unpack_kernel(const T *__restrict__ src, double *__restrict__ dst, long long V, long long Vs, int NF)
+{
+    const long long n = V * NF;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        const long long f = k / V;
+        const long long i = k - f * V;
+        dst[k] = (double)src[f * Vs + i];
+    }
+}
+
+// Fixed-order sum of the per-block error partials (one block of 256 threads).
+__global__ void finalize_err_kernel(const double *__restrict__ ps, const long long *__restrict__ pc, int n,
+                                    double *out_sum, long long *out_cnt)
+{
+    __shared__ double ss[256];
+    __shared__ long long sc[256];
+    double s = 0.0;
+    long long c = 0;
+    for (int k = threadIdx.x; k < n; k += 256) { s += ps[k]; c += pc[k]; }
+    ss[threadIdx.x] = s;
+    sc[threadIdx.x] = c;
+    __syncthreads();
+    for (int o = 128; o >= 1; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            ss[threadIdx.x] += ss[threadIdx.x + o];
+            sc[threadIdx.x] += sc[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) { *out_sum = ss[0]; *out_cnt = sc[0]; }
+}
+
+// Per-field totals: block (b, f) sums / maximises field f over a fixed cell range.
+template <typename T>
+__global__ void totals_kernel(const T *__restrict__ u, long long V, long long Vs, double *psum, double *pmax)
+{
+    const int f = blockIdx.y;
+    const long long chunk = (V + gridDim.x - 1) / gridDim.x;
+    const long long lo = blockIdx.x * chunk;
+    const long long hi = lo + chunk < V ? lo + chunk : V;
+    double s = 0.0, m = -1e300;
+    for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        const double v = (double)u[(long long)f * Vs + i];
+        s += v;
+        m = v > m ? v : m;
+    }
+    __shared__ double ss[256], sm[256];
+    ss[threadIdx.x] = s;
+    sm[threadIdx.x] = m;
+    __syncthreads();
+    for (int o = 128; o >= 1; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            ss[threadIdx.x] += ss[threadIdx.x + o];
+            sm[threadIdx.x] = sm[threadIdx.x] > sm[threadIdx.x + o] ? sm[threadIdx.x] : sm[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        psum[(long long)f * gridDim.x + blockIdx.x] = ss[0];
+        pmax[(long long)f * gridDim.x + blockIdx.x] = sm[0];
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// handle
+// ---------------------------------------------------------------------------
+
+struct pf_handle {
+    int dev = 0;
+    cudaStream_t stream = nullptr;
+    int prec = 64;
+    size_t esize = 8;
+    Geom g{};
+    int N = 0, K = 0, NP = 0;
+    long long V = 0, Vs = 0;
+    int grid = 1;                      // blocks per pass (= error partials)
+    std::vector<int> ptype;
+    std::vector<double> A, B, L;
+    void *dA = nullptr, *dB = nullptr, *dL = nullptr;
+    signed char *dptype = nullptr;
+    void *buf[NBUF] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    int iu = 0;                        // buffer holding u^n
+    size_t vec_bytes = 0;
+    double *staging = nullptr;         // (N + K) * V doubles (set/get/rhs)
+    unsigned char *dnz = nullptr;
+    double *part_sum = nullptr;
+    long long *part_cnt = nullptr;
+    double *dres = nullptr;            // [0] error sum
+    long long *dcnt = nullptr;
+    int *dflag = nullptr;
+    double *tot_sum = nullptr, *tot_max = nullptr;
+    int tot_blocks = 0;
+    double t = 0.0;
+    bool has_state = false;
+    double dte = 0.0;
+    double dx = 1.0;
+    // launch accounting and optional per-pass event timing
+    long long launches = 0;
+    bool prof_on = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<int> ev_kind;          // kind of the pass bracketed by events 2k, 2k+1
+    int ev_used = 0;
+    double prof_ms[PF_NPASS_KINDS] = {0};
+    long long prof_n[PF_NPASS_KINDS] = {0};
+    int cur_kind = PF_PASS_OTHER;
+    // controller (Sec. 3.3)
+    double b = 0.9, E1 = 0.0, E2 = 0.0, dt1 = 0.0, dt2 = 0.0;
+    int nhist = 0;
+    double dt_next = 0.0;
+};
+
+namespace {
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? PF_OK : PF_EDEVICE; }
+
+void *vec(pf_handle *h, int k) { return h->buf[k]; }
+
+// Fold recorded event pairs into the per-kind totals (synchronises).
+int prof_flush(pf_handle *h)
+{
+    if (h->ev_used == 0) return PF_OK;
+    if (cudaEventSynchronize(h->ev_pool[2 * (h->ev_used - 1) + 1]) != cudaSuccess) return PF_EDEVICE;
+    for (int k = 0; k < h->ev_used; ++k) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, h->ev_pool[2 * k], h->ev_pool[2 * k + 1]) != cudaSuccess) return PF_EDEVICE;
+        h->prof_ms[h->ev_kind[k]] += ms;
+        h->prof_n[h->ev_kind[k]] += 1;
+    }
+    h->ev_used = 0;
+    return PF_OK;
+}
+
+int prof_begin(pf_handle *h)
+{
+    if (!h->prof_on) return PF_OK;
+    if (h->ev_used * 2 + 2 > (int)h->ev_pool.size()) {
+        int st = prof_flush(h);
+        if (st) return st;
+    }
+    h->ev_kind[h->ev_used] = h->cur_kind;
+    return cudaEventRecord(h->ev_pool[2 * h->ev_used], h->stream) == cudaSuccess ? PF_OK : PF_EDEVICE;
+}
+
+int prof_end(pf_handle *h)
+{
+    if (!h->prof_on) return PF_OK;
+    if (cudaEventRecord(h->ev_pool[2 * h->ev_used + 1], h->stream) != cudaSuccess) return PF_EDEVICE;
+    h->ev_used++;
+    return PF_OK;
+}
+
+template <typename T>
+int run_pass(pf_handle *h, const Pass<T> &P)
+{
+    int st = prof_begin(h);
+    if (st) return st;
+    int e = pfk::launch_stage<T>(h->g, P, h->stream, (const T *)h->dA, (const T *)h->dB, (const T *)h->dL,
+                                 h->dptype);
+    h->launches++;
+    if (e != 0) return PF_EDEVICE;
+    return prof_end(h);
+}
+
+template <typename T>
+Pass<T> blank_pass(pf_handle *h)
+{
+    Pass<T> P;
+    memset(&P, 0, sizeof(P));
+    P.mode = pfk::MODE_STAGE;
+    P.project = 1;
+    P.a1 = 1.0;
+    P.flag = h->dflag;
+    P.part_sum = h->part_sum;
+    P.part_cnt = h->part_cnt;
+    return P;
+}
+
+// ---- Gershgorin reading of the stable Euler step (Sec. 3.2) ---------------
+double gershgorin_dt_e(const pf_handle *h, const pf_params *p)
+{
+    const int N = h->N;
+    const double d4 = 4.0 * p->dim / (p->dx * p->dx);
+    double lphi = 0.0, lmax = 0.0;
+    for (int a = 0; a < N; ++a)
+        for (int b = 0; b < N; ++b) {
+            if (a == b) continue;
+            const double v = h->L[a * N + b] * (h->A[a * N + b] * d4 - h->B[a * N + b]);
+            if (v > lphi) lphi = v;
+            if (h->L[a * N + b] > lmax) lmax = h->L[a * N + b];
+        }
+    double lam = lphi;
+    if (h->K) {
+        bool used[2] = {false, false};
+        for (int a = 0; a < N; ++a) used[h->ptype[a]] = true;
+        double kmax = 0.0, c0max = -1e300, c0min = 1e300, Dmax = 0.0;
+        for (int t = 0; t < 2; ++t) {
+            if (!used[t]) continue;
+            kmax = fmax(kmax, p->k[t]);
+            c0max = fmax(c0max, p->c0[t]);
+            c0min = fmin(c0min, p->c0[t]);
+            Dmax = fmax(Dmax, p->D[t]);
+        }
+        const double dc0 = c0max - c0min;
+        const double chem = lmax * kmax * dc0 * c0max;       // chemical driving-force term
+        const double lc = d4 * Dmax * (1.0 + dc0 / 2.0);     // concentration diffusion
+        lam = fmax(lphi + chem, lc);
+    }
+    return 2.0 / lam;
+}
+
+// ---- RKL coefficients (Meyer et al. 2012/2014, Legendre basis) ------------
+double rkl2_b(int j)
+{
+    if (j < 2) return 1.0 / 3.0;
+    const double jj = (double)j;
+    return (jj * jj + jj - 2.0) / (2.0 * jj * (jj + 1.0));
+}
+
+// Smallest odd stage count whose RKL stability bound with 0.9 dt_e covers dt.
+int sts_stages(int integ, double dt, double dte)
+{
+    const double dte9 = 0.9 * dte;
+    for (int s = (integ == PF_RKL2) ? 3 : 1;; s += 2) {
+        const double ds = (double)s;
+        const double bound = (integ == PF_RKL2) ? (ds * ds + ds - 2.0) / 4.0 * dte9 : (ds * ds + ds) / 2.0 * dte9;
+        if (bound >= dt || s > 1000001) return s;
+    }
+}
+
+double sts_max_dt(int integ, int s, double dte)
+{
+    const double ds = (double)s;
+    return ((integ == PF_RKL2) ? (ds * ds + ds - 2.0) / 4.0 : (ds * ds + ds) / 2.0) * 0.9 * dte;
+}
+
+int method_order(int integ)
+{
+    switch (integ) {
+    case PF_FEULER: return 1;
+    case PF_SSP2: return 2;
+    case PF_SSP104: return 4;
+    case PF_RKL1: return 1;
+    default: return 2;
+    }
+}
+
+// Embedded weights for SSP(10)4: minimum-norm solution of the order-3
+// conditions over the first nine stages (the scheme's own weights are all
+// 1/10 and already minimal, so the last stage is left out of the embedding).
+void ssp104_embedded(double bh[10])
+{
+    double Am[10][10] = {{0}}, c[10];
+    for (int i = 1; i < 5; ++i)
+        for (int j = 0; j < i; ++j) Am[i][j] = 1.0 / 6.0;
+    for (int j = 0; j < 5; ++j) Am[5][j] = 0.4 / 6.0;
+    for (int i = 6; i < 10; ++i) {
+        for (int j = 0; j < 10; ++j) Am[i][j] = Am[i - 1][j];
+        Am[i][i - 1] += 1.0 / 6.0;
+    }
+    for (int i = 0; i < 10; ++i) {
+        c[i] = 0.0;
+        for (int j = 0; j < 10; ++j) c[i] += Am[i][j];
+    }
+    double M[4][10];
+    const double g[4] = {1.0, 0.5, 1.0 / 3.0, 1.0 / 6.0};
+    for (int i = 0; i < 10; ++i) {
+        double ac = 0.0;
+        for (int j = 0; j < 10; ++j) ac += Am[i][j] * c[j];
+        const bool use = i < 9;
+        M[0][i] = use ? 1.0 : 0.0;
+        M[1][i] = use ? c[i] : 0.0;
+        M[2][i] = use ? c[i] * c[i] : 0.0;
+        M[3][i] = use ? ac : 0.0;
+    }
+    double G[4][5];
+    for (int r = 0; r < 4; ++r) {
+        for (int q = 0; q < 4; ++q) {
+            double s = 0.0;
+            for (int i = 0; i < 10; ++i) s += M[r][i] * M[q][i];
+            G[r][q] = s;
+        }
+        G[r][4] = g[r];
+    }
+    for (int col = 0; col < 4; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < 4; ++r) if (fabs(G[r][col]) > fabs(G[piv][col])) piv = r;
+        for (int q = 0; q < 5; ++q) { double t = G[col][q]; G[col][q] = G[piv][q]; G[piv][q] = t; }
+        for (int r = 0; r < 4; ++r) {
+            if (r == col) continue;
+            const double f = G[r][col] / G[col][col];
+            for (int q = 0; q < 5; ++q) G[r][q] -= f * G[col][q];
+        }
+    }
+    double y[4];
+    for (int r = 0; r < 4; ++r) y[r] = G[r][4] / G[r][r];
+    for (int i = 0; i < 10; ++i) {
+        double s = 0.0;
+        for (int r = 0; r < 4; ++r) s += M[r][i] * y[r];
+        bh[i] = s;
+    }
+}
+
+// ---- PID controller with bias (Sec. 3.3, Soderlind 2006 form) --------------
+double controller(pf_handle *h, double err, double dt, int P, int *accept)
+{
+    const double k1 = 1.25, k2 = 0.5, k3 = -0.6, k4 = 0.25, k5 = 0.0;
+    const double ex = 1.0 / (double)(P + 1);
+    double E = err / h->b;
+    if (E < 1e-10) E = 1e-10;
+    double F = pow(E, -k1 * ex);
+    if (h->nhist >= 1) F = F * pow(h->E1, -k2 * ex) * pow(dt / h->dt1, k4);
+    if (h->nhist >= 2) F = F * pow(h->E2, -k3 * ex) * pow(h->dt1 / h->dt2, k5);
+    const int acc = err < 1.0;
+    if (acc) {
+        h->E2 = h->E1;
+        h->E1 = E;
+        h->dt2 = h->dt1;
+        h->dt1 = dt;
+        if (h->nhist < 2) h->nhist++;
+        const double nb = sqrt(h->b);
+        h->b = nb > 0.98 ? 0.98 : nb;
+    } else {
+        const double nb = h->b * h->b;
+        h->b = nb < 0.1 ? 0.1 : nb;
+        if (F > 1.0) F = pow(E, -k1 * ex);
+    }
+    *accept = acc;
+    return dt * (1.0 + 5.0 * atan((F - 1.0) / 5.0));
+}
+
+void reset_controller(pf_handle *h)
+{
+    h->b = 0.9;
+    h->E1 = h->E2 = h->dt1 = h->dt2 = 0.0;
+    h->nhist = 0;
+    h->dt_next = 0.0;
+}
+
+// ---- one step ---------------------------------------------------------------
+// Runs the stages of one step of size dt with s stages from buf[iu].  On
+// return *out is the buffer index holding the candidate u^{n+1}; when
+// want_err is set, the error partials of Sec. 3.3 are in part_sum/part_cnt.
+template <typename T>
+int do_step(pf_handle *h, int integ, double dt, int s, const pf_tol *tol, bool want_err, int *out, long long *evals)
+{
+    const int U = h->iu;
+    int w[NBUF - 1], nw = 0;
+    for (int k = 0; k < NBUF; ++k) if (k != U) w[nw++] = k;
+    int st;
+    auto B = [&](int k) { return (T *)vec(h, k); };
+
+    if (integ == PF_FEULER) {
+        h->cur_kind = PF_PASS_EULER;
+        Pass<T> P = blank_pass<T>(h);
+        P.in = B(U); P.out = B(w[0]); P.a1 = 1.0; P.b1 = dt;
+        if ((st = run_pass<T>(h, P))) return st;
+        *out = w[0];
+        *evals += 1;
+        return PF_OK;
+    }
+    if (integ == PF_SSP2) {
+        // Alg. ssp2: s-1 Euler substeps of dt/(s-1), then the final combination
+        int q1 = w[0], q3 = w[1];
+        h->cur_kind = PF_PASS_SSP;
+        const double hs = dt / (double)(s - 1);
+        int cur = U;
+        for (int k = 1; k <= s - 1; ++k) {
+            Pass<T> P = blank_pass<T>(h);
+            P.in = B(cur); P.out = B(q1); P.a1 = 1.0; P.b1 = hs;
+            if ((st = run_pass<T>(h, P))) return st;
+            cur = q1;
+            int t = q1; q1 = q3; q3 = t;
+        }
+        Pass<T> P = blank_pass<T>(h);
+        P.in = B(cur); P.p0 = B(U);
+        P.a0 = 1.0 / (double)s; P.a1 = (double)(s - 1) / (double)s; P.b1 = dt / (double)s;
+        P.out = B(q1);
+        if ((st = run_pass<T>(h, P))) return st;
+        *out = q1;
+        *evals += s;
+        return PF_OK;
+    }
+    if (integ == PF_SSP104) {
+        // Ketcheson (2008) low-storage SSP(10,4) with an extra stage buffer and
+        // the embedded accumulator z = u^n + dt sum bh_i F_i (Sec. 3.3).
+        double bh[10];
+        ssp104_embedded(bh);
+        int q1 = w[0], q3 = w[1], q2 = w[2], zb = w[3];
+        h->cur_kind = PF_PASS_SSP;
+        const double h6 = dt / 6.0;
+        int cur = U;
+        for (int k = 1; k <= 9; ++k) {
+            Pass<T> P = blank_pass<T>(h);
+            P.in = B(cur); P.a1 = 1.0; P.b1 = h6;
+            if (want_err) { P.zin = (k == 1) ? B(U) : B(zb); P.zout = B(zb); P.bz = dt * bh[k - 1]; }
+            if (k == 5) {
+                P.out2 = B(q2); P.q2in = B(U);
+                P.m25 = 1.0 / 25.0; P.m925 = 9.0 / 25.0; P.m15 = 15.0; P.m5 = -5.0;
+            }
+            P.out = B(q1);
+            if ((st = run_pass<T>(h, P))) return st;
+            cur = q1;
+            int t = q1; q1 = q3; q3 = t;
+        }
+        Pass<T> P = blank_pass<T>(h);
+        P.in = B(cur); P.p0 = B(q2); P.a0 = 1.0; P.a1 = 0.6; P.b1 = dt / 10.0;
+        P.out = B(q1);
+        if (want_err) {
+            P.zin = B(zb); P.zout = B(zb); P.bz = dt * bh[9]; P.embedded_err = 1; P.uw = B(U);
+            P.r_phi = tol->r_phi; P.a_phi = tol->a_phi; P.r_c = tol->r_c; P.a_c = tol->a_c;
+        }
+        if ((st = run_pass<T>(h, P))) return st;
+        *out = q1;
+        *evals += 10;
+        return PF_OK;
+    }
+    // RKL1 / RKL2 (Eq. sts), ring of three stage buffers plus F(u^n)
+    const bool o2 = (integ == PF_RKL2);
+    const int ring[3] = {w[0], w[1], w[2]};
+    const int r0 = w[3];
+    const double ds = (double)s;
+    const double w1 = o2 ? 4.0 / (ds * ds + ds - 2.0) : 2.0 / (ds * ds + ds);
+    const double mt1 = o2 ? rkl2_b(1) * w1 : w1;
+    {
+        h->cur_kind = PF_PASS_STS_FIRST;
+        Pass<T> P = blank_pass<T>(h);
+        P.in = B(U); P.a1 = 1.0; P.b1 = mt1 * dt; P.out = B(ring[0]); P.r0out = B(r0); P.fix_first = o2 ? 1 : 0;
+        if ((st = run_pass<T>(h, P))) return st;
+    }
+    h->cur_kind = o2 ? PF_PASS_RKL2 : PF_PASS_RKL1;
+    for (int j = 2; j <= s; ++j) {
+        const double dj = (double)j;
+        double mu, nu, mt, gt;
+        if (o2) {
+            mu = ((2.0 * dj - 1.0) / dj) * (rkl2_b(j) / rkl2_b(j - 1));
+            nu = -((dj - 1.0) / dj) * (rkl2_b(j) / rkl2_b(j - 2));
+            mt = mu * w1;
+            gt = -(1.0 - rkl2_b(j - 1)) * mt;
+        } else {
+            mu = (2.0 * dj - 1.0) / dj;
+            nu = -(dj - 1.0) / dj;
+            mt = w1 * mu;
+            gt = 0.0;
+        }
+        Pass<T> P = blank_pass<T>(h);
+        P.in = B(ring[(j - 2) % 3]);
+        P.p2 = (j == 2) ? B(U) : B(ring[(j - 3) % 3]);
+        P.a1 = mu; P.a2 = nu; P.b1 = mt * dt;
+        if (o2) { P.p0 = B(U); P.a0 = (1.0 - mu) - nu; P.r0in = B(r0); P.b0 = gt * dt; }
+        P.out = B(ring[(j - 1) % 3]);
+        if ((st = run_pass<T>(h, P))) return st;
+    }
+    const int fin = ring[(s - 1) % 3];
+    *evals += s;
+    if (want_err) {
+        // Sommeijer estimate with F(u^{n+1}) (Sec. 3.3): one more RHS sweep
+        h->cur_kind = PF_PASS_STS_ERR;
+        Pass<T> P = blank_pass<T>(h);
+        P.mode = pfk::MODE_ERR;
+        P.in = B(fin); P.p0 = B(U); P.r0in = B(r0); P.dt = dt; P.project = 0;
+        P.r_phi = tol->r_phi; P.a_phi = tol->a_phi; P.r_c = tol->r_c; P.a_c = tol->a_c;
+        if ((st = run_pass<T>(h, P))) return st;
+        *evals += 1;
+    }
+    *out = fin;
+    return PF_OK;
+}
+
+// Device flags -> status: a non-positive simplex sum is an instability; more
+// nontrivial phases in one cell than the kernel's list holds is unsupported.
+int flag_status(int flag)
+{
+    if (flag & pfk::FLAG_NZ_OVERFLOW) return PF_EINVAL;
+    return PF_EUNSTABLE;
+}
+
+int read_error(pf_handle *h, double *err)
+{
+    h->cur_kind = PF_PASS_OTHER;
+    int pst = prof_begin(h);
+    if (pst) return pst;
+    finalize_err_kernel<<<1, 256, 0, h->stream>>>(h->part_sum, h->part_cnt, h->grid, h->dres, h->dcnt);
+    h->launches++;
+    if (cudaGetLastError() != cudaSuccess) return PF_EDEVICE;
+    if ((pst = prof_end(h))) return pst;
+    double s;
+    long long c;
+    int flag;
+    if (cudaMemcpyAsync(&s, h->dres, sizeof(double), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess) return PF_EDEVICE;
+    if (cudaMemcpyAsync(&c, h->dcnt, sizeof(long long), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess) return PF_EDEVICE;
+    if (cudaMemcpyAsync(&flag, h->dflag, sizeof(int), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess) return PF_EDEVICE;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return PF_EDEVICE;
+    if (flag) return flag_status(flag);
+    *err = c > 0 ? sqrt(s / (double)c) : 0.0;
+    return PF_OK;
+}
+
+int check_flag(pf_handle *h)
+{
+    int flag = 0;
+    if (cudaMemcpyAsync(&flag, h->dflag, sizeof(int), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess) return PF_EDEVICE;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return PF_EDEVICE;
+    return flag ? flag_status(flag) : PF_OK;
+}
+
+template <typename T>
+int step_loop(pf_handle *h, int integ, double t_end, const pf_tol *tol, const pf_step_opts *o, pf_stats *stats)
+{
+    const bool adaptive = !(o->dt_mult > 0.0);
+    const bool sts = (integ == PF_RKL1 || integ == PF_RKL2);
+    if (adaptive && (integ == PF_FEULER || integ == PF_SSP2)) return PF_EINVAL;
+    if (adaptive && !tol) return PF_EINVAL;
+    if (integ == PF_SSP2 && o->ssp_stages < 2) return PF_EINVAL;
+    const int max_stages = o->max_stages > 0 ? o->max_stages : 1001;
+    long long evals = 0, acc_n = 0, rej_n = 0, attempts = 0;
+    const long long launches0 = h->launches;
+    double dt = adaptive ? (h->dt_next > 0.0 ? h->dt_next : (o->dt0 > 0.0 ? o->dt0 : 0.9 * h->dte)) : o->dt_mult * h->dte;
+    double hlast = 0.0, elast = 0.0;
+    int ntr = 0, status = PF_OK;
+    // fixed steps: step k ends at t0 + k dt (no drift); the last is shortened
+    // to land exactly on t_end (Sec. 5, output at target times)
+    const double t0 = h->t;
+    long long nfix = 0, kfix = 0;
+    if (!adaptive) {
+        nfix = (long long)ceil((t_end - t0) / dt - 1e-9);
+        if (nfix < 1) nfix = 1;
+    }
+    if (cudaMemsetAsync(h->dflag, 0, sizeof(int), h->stream) != cudaSuccess) return PF_EDEVICE;
+    while (h->t < t_end) {
+        if (o->max_attempts > 0 && attempts >= o->max_attempts) break;
+        const double rem = t_end - h->t;
+        double hs = dt;
+        bool last = false;
+        if (adaptive) {
+            if (hs >= rem * (1.0 - 1e-9)) { hs = rem; last = true; }
+        } else {
+            last = (kfix + 1 >= nfix);
+            if (last) hs = rem;
+        }
+        int s = 1;
+        if (sts) {
+            s = sts_stages(integ, hs, h->dte);
+            if (s > max_stages && !adaptive) { status = PF_EINVAL; break; }
+            if (s > max_stages) {
+                s = max_stages | 1;
+                hs = sts_max_dt(integ, s, h->dte);
+                last = false;
+            }
+        } else if (integ == PF_SSP2) {
+            s = o->ssp_stages;
+        } else if (integ == PF_SSP104) {
+            s = 10;
+        }
+        int cand = -1;
+        if ((status = do_step<T>(h, integ, hs, s, tol, adaptive, &cand, &evals))) break;
+        attempts++;
+        double err = 0.0;
+        int acc = 1;
+        if (adaptive) {
+            if ((status = read_error(h, &err))) break;
+            if (!isfinite(err)) { status = PF_EUNSTABLE; break; }
+            dt = controller(h, err, hs, method_order(integ), &acc);
+        }
+        if (o->trace_cap > ntr) {
+            if (o->trace_dt) o->trace_dt[ntr] = hs;
+            if (o->trace_s) o->trace_s[ntr] = s;
+            if (o->trace_err) o->trace_err[ntr] = err;
+            if (o->trace_acc) o->trace_acc[ntr] = acc;
+            ntr++;
+        }
+        hlast = hs;
+        elast = err;
+        if (acc) {
+            h->iu = cand;
+            if (!adaptive) { kfix++; h->t = last ? t_end : t0 + (double)kfix * dt; }
+            else h->t = last ? t_end : h->t + hs;
+            acc_n++;
+        } else {
+            rej_n++;
+            if (rej_n > 100000) { status = PF_EUNSTABLE; break; }
+        }
+    }
+    if (status == PF_OK) status = check_flag(h);
+    if (adaptive) h->dt_next = dt;
+    if (o->trace_len) *o->trace_len = ntr;
+    if (stats) {
+        stats->rhs_evals = evals;
+        stats->steps_accepted = acc_n;
+        stats->steps_rejected = rej_n;
+        stats->t = h->t;
+        stats->dt_last = hlast;
+        stats->err_last = elast;
+        stats->dt_e = h->dte;
+        stats->dt_next = h->dt_next;
+        stats->kernel_launches = h->launches - launches0;
+    }
+    return status;
+}
+
+int grid_for(long long n) { long long b = (n + 255) / 256; return (int)(b < 4096 ? (b > 0 ? b : 1) : 4096); }
+
+template <typename T>
+int set_state_t(pf_handle *h, const double *src_dev)
+{
+    pack_kernel<T><<<grid_for(h->V * h->NP), 256, 0, h->stream>>>(src_dev, (T *)h->buf[h->iu], h->V, h->Vs, h->NP);
+    h->launches++;
+    return cuda_status(cudaGetLastError());
+}
+
+template <typename T>
+int get_state_t(pf_handle *h, double *dst_dev)
+{
+    unpack_kernel<T><<<grid_for(h->V * h->NP), 256, 0, h->stream>>>((const T *)h->buf[h->iu], dst_dev, h->V, h->Vs, h->NP);
+    h->launches++;
+    return cuda_status(cudaGetLastError());
+}
+
+template <typename T>
+int rhs_t(pf_handle *h, unsigned char *nz_dev)
+{
+    h->cur_kind = PF_PASS_RHS;
+    Pass<T> P = blank_pass<T>(h);
+    P.mode = pfk::MODE_RHS;
+    P.in = (const T *)h->buf[h->iu];
+    P.rhs_pm = h->staging;
+    P.nz_out = nz_dev;
+    P.project = 0;
+    return run_pass<T>(h, P);
+}
+
+template <typename T>
+int totals_t(pf_handle *h)
+{
+    dim3 grid(h->tot_blocks, h->NP);
+    totals_kernel<T><<<grid, 256, 0, h->stream>>>((const T *)h->buf[h->iu], h->V, h->Vs, h->tot_sum, h->tot_max);
+    h->launches++;
+    return cuda_status(cudaGetLastError());
+}
+
+int ensure_staging(pf_handle *h)
+{
+    if (h->staging) return PF_OK;
+    if (cudaMalloc(&h->staging, sizeof(double) * (size_t)h->NP * h->V) != cudaSuccess) return PF_ENOMEM;
+    return PF_OK;
+}
+
+void free_all(pf_handle *h)
+{
+    for (cudaEvent_t ev : h->ev_pool) cudaEventDestroy(ev);
+    h->ev_pool.clear();
+    for (int k = 0; k < NBUF; ++k) if (h->buf[k]) cudaFree(h->buf[k]);
+    void *ps[] = {h->dA, h->dB, h->dL, h->dptype, h->staging, h->dnz, h->part_sum, h->part_cnt,
+                  h->dres, h->dcnt, h->dflag, h->tot_sum, h->tot_max};
+    for (void *p : ps) if (p) cudaFree(p);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+
+extern "C" {
+
+const char *pf_strerror(int s)
+{
+    switch (s) {
+    case PF_OK: return "ok";
+    case PF_EINVAL: return "invalid argument";
+    case PF_ENOMEM: return "out of memory";
+    case PF_EUNSTABLE: return "unstable (non-finite error norm, bad simplex sum or too many rejections)";
+    case PF_ETIMEOUT: return "device wait timed out";
+    case PF_EDEVICE: return "CUDA error";
+    case PF_ESTATE: return "no state set";
+    default: return "unknown status";
+    }
+}
+
+int pf_create(const pf_params *p, void *cuda_stream, pf_handle **out)
+{
+    if (!p || !out) return PF_EINVAL;
+    *out = nullptr;
+    if (p->dim != 2 && p->dim != 3) return PF_EINVAL;
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1 || (p->dim == 2 && p->nz != 1)) return PF_EINVAL;
+    if (!(p->dx > 0.0) || !(p->W > 0.0)) return PF_EINVAL;
+    if (p->n_phases < 2 || !p->phase_type || !p->gamma || (!p->mobility && !p->L_override)) return PF_EINVAL;
+    if (p->has_conc != 0 && p->has_conc != 1) return PF_EINVAL;
+    if (p->precision != 32 && p->precision != 64) return PF_EINVAL;
+    const int NP = p->n_phases + p->has_conc;
+    if (NP > 128) return PF_EINVAL;
+    for (int f = 0; f < 6; ++f) {
+        if (f >= 2 * p->dim) break;
+        const int o = f ^ 1;
+        if (p->bc_phi[f] != PF_BC_PERIODIC && p->bc_phi[f] != PF_BC_NEUMANN) return PF_EINVAL;
+        if (p->bc_c[f] < 0 || p->bc_c[f] > 2) return PF_EINVAL;
+        const bool per = p->bc_phi[f] == PF_BC_PERIODIC;
+        if (per != (p->bc_phi[o] == PF_BC_PERIODIC)) return PF_EINVAL;
+        if (p->has_conc && per != (p->bc_c[f] == PF_BC_PERIODIC)) return PF_EINVAL;
+    }
+    for (int a = 0; a < p->n_phases; ++a)
+        if (p->phase_type[a] != 0 && p->phase_type[a] != 1) return PF_EINVAL;
+    if (p->has_conc)
+        for (int t = 0; t < 2; ++t) if (!(p->k[t] > 0.0)) return PF_EINVAL;
+
+    pf_handle *h = new (std::nothrow) pf_handle();
+    if (!h) return PF_ENOMEM;
+    if (cudaGetDevice(&h->dev) != cudaSuccess) { delete h; return PF_EDEVICE; }
+    h->stream = (cudaStream_t)cuda_stream;
+    h->prec = p->precision;
+    h->esize = p->precision == 64 ? 8 : 4;
+    const int N = p->n_phases;
+    h->N = N;
+    h->K = p->has_conc;
+    h->NP = NP;
+    h->V = (long long)p->nx * p->ny * p->nz;
+    h->ptype.assign(p->phase_type, p->phase_type + N);
+    h->A.resize(N * N);
+    h->B.resize(N * N);
+    h->L.resize(N * N);
+    for (int a = 0; a < N; ++a)
+        for (int b = 0; b < N; ++b) {
+            const double g = p->gamma[a * N + b];
+            // Sec. 2: A = 4 W gamma / pi, B = 4 gamma / (pi W), L = pi M / (4 W)
+            h->A[a * N + b] = 4.0 * p->W * g / kPi;
+            h->B[a * N + b] = 4.0 * g / (kPi * p->W);
+            h->L[a * N + b] = p->L_override ? p->L_override[a * N + b] : kPi * p->mobility[a * N + b] / (4.0 * p->W);
+        }
+    Geom &g = h->g;
+    g.nx = p->nx; g.ny = p->ny; g.nz = p->nz; g.dim = p->dim;
+    h->Vs = (h->V + 63) / 64 * 64;
+    g.V = h->V; g.Vs = h->Vs; g.N = N; g.K = h->K; g.NF = NP;
+    g.tiles_x = (p->nx + pfk::TX - 1) / pfk::TX;
+    g.tiles_y = (p->ny + pfk::TY - 1) / pfk::TY;
+    for (int f = 0; f < 6; ++f) {
+        g.bc_phi[f] = p->bc_phi[f];
+        g.bc_c[f] = p->bc_c[f];
+        g.cdir[f] = p->c_dirichlet[f];
+    }
+    g.dx2 = p->dx * p->dx;
+    h->dx = p->dx;
+    for (int t = 0; t < 2; ++t) {
+        const double k = h->K ? p->k[t] : 1.0;
+        g.k[t] = k;
+        g.c0[t] = p->c0[t];
+        g.invk[t] = 1.0 / k;
+        g.Dk[t] = p->D[t] / k;
+    }
+    h->dte = gershgorin_dt_e(h, p);
+
+    int st = PF_OK;
+    int bps = (h->prec == 64) ? pfk::prepare_stage<double>() : pfk::prepare_stage<float>();
+    if (bps <= 0) { delete h; return PF_EINVAL; }
+    if ((long long)g.tiles_x * g.tiles_y * p->nz > 0x7fffffffLL || p->nz > 65535) { delete h; return PF_EINVAL; }
+    h->grid = g.tiles_x * g.tiles_y * p->nz;
+    h->tot_blocks = (int)((h->V + 4095) / 4096 < 1024 ? (h->V + 4095) / 4096 : 1024);
+    if (h->tot_blocks < 1) h->tot_blocks = 1;
+
+    h->vec_bytes = (size_t)h->Vs * NP * h->esize;
+    bool ok = true;
+    for (int k = 0; k < NBUF && ok; ++k) ok = cudaMalloc(&h->buf[k], h->vec_bytes) == cudaSuccess;
+    ok = ok && cudaMalloc(&h->dA, h->esize * N * N) == cudaSuccess;
+    ok = ok && cudaMalloc(&h->dB, h->esize * N * N) == cudaSuccess;
+    ok = ok && cudaMalloc(&h->dL, h->esize * N * N) == cudaSuccess;
+    ok = ok && cudaMalloc(&h->dptype, N) == cudaSuccess;
+    ok = ok && cudaMalloc(&h->part_sum, sizeof(double) * h->grid) == cudaSuccess;
+    ok = ok && cudaMalloc(&h->part_cnt, sizeof(long long) * h->grid) == cudaSuccess;
+    ok = ok && cudaMalloc(&h->dres, sizeof(double)) == cudaSuccess;
+    ok = ok && cudaMalloc(&h->dcnt, sizeof(long long)) == cudaSuccess;
+    ok = ok && cudaMalloc(&h->dflag, sizeof(int)) == cudaSuccess;
+    ok = ok && cudaMalloc(&h->tot_sum, sizeof(double) * h->tot_blocks * NP) == cudaSuccess;
+    ok = ok && cudaMalloc(&h->tot_max, sizeof(double) * h->tot_blocks * NP) == cudaSuccess;
+    if (!ok) { cudaGetLastError(); free_all(h); delete h; return PF_ENOMEM; }
+    // coefficient tables in the storage precision
+    std::vector<signed char> pt(N);
+    for (int a = 0; a < N; ++a) pt[a] = (signed char)h->ptype[a];
+    if (h->prec == 64) {
+        st |= cudaMemcpy(h->dA, h->A.data(), 8 * N * N, cudaMemcpyHostToDevice);
+        st |= cudaMemcpy(h->dB, h->B.data(), 8 * N * N, cudaMemcpyHostToDevice);
+        st |= cudaMemcpy(h->dL, h->L.data(), 8 * N * N, cudaMemcpyHostToDevice);
+    } else {
+        std::vector<float> fa(h->A.begin(), h->A.end()), fb(h->B.begin(), h->B.end()), fl(h->L.begin(), h->L.end());
+        st |= cudaMemcpy(h->dA, fa.data(), 4 * N * N, cudaMemcpyHostToDevice);
+        st |= cudaMemcpy(h->dB, fb.data(), 4 * N * N, cudaMemcpyHostToDevice);
+        st |= cudaMemcpy(h->dL, fl.data(), 4 * N * N, cudaMemcpyHostToDevice);
+    }
+    st |= cudaMemcpy(h->dptype, pt.data(), N, cudaMemcpyHostToDevice);
+    st |= cudaMemset(h->dflag, 0, sizeof(int));
+    if (st != 0) { free_all(h); delete h; return PF_EDEVICE; }
+    *out = h;
+    return PF_OK;
+}
+
+int pf_destroy(pf_handle *h)
+{
+    if (!h) return PF_OK;
+    cudaStreamSynchronize(h->stream);
+    free_all(h);
+    delete h;
+    return PF_OK;
+}
+
+int pf_dt_e(pf_handle *h, double *dte)
+{
+    if (!h || !dte) return PF_EINVAL;
+    *dte = h->dte;
+    return PF_OK;
+}
+
+int pf_set_state(pf_handle *h, const double *phi, const double *c, double t, int ptr_is_device)
+{
+    if (!h || !phi || (h->K && !c)) return PF_EINVAL;
+    int st;
+    if ((st = ensure_staging(h))) return st;
+    const size_t nphi = sizeof(double) * (size_t)h->N * h->V;
+    const cudaMemcpyKind kind = ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (cudaMemcpyAsync(h->staging, phi, nphi, kind, h->stream) != cudaSuccess) return PF_EDEVICE;
+    if (h->K && cudaMemcpyAsync(h->staging + (size_t)h->N * h->V, c, sizeof(double) * h->V, kind, h->stream) != cudaSuccess)
+        return PF_EDEVICE;
+    st = (h->prec == 64) ? set_state_t<double>(h, h->staging) : set_state_t<float>(h, h->staging);
+    if (st) return st;
+    if (!ptr_is_device && cudaStreamSynchronize(h->stream) != cudaSuccess) return PF_EDEVICE;
+    h->t = t;
+    h->has_state = true;
+    reset_controller(h);
+    return PF_OK;
+}
+
+int pf_get_state(pf_handle *h, double *phi, double *c, unsigned char *nz, double *t, int ptr_is_device)
+{
+    if (!h) return PF_EINVAL;
+    if (!h->has_state) return PF_ESTATE;
+    int st;
+    if ((st = ensure_staging(h))) return st;
+    const cudaMemcpyKind kind = ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (phi || c) {
+        st = (h->prec == 64) ? get_state_t<double>(h, h->staging) : get_state_t<float>(h, h->staging);
+        if (st) return st;
+        if (phi && cudaMemcpyAsync(phi, h->staging, sizeof(double) * (size_t)h->N * h->V, kind, h->stream) != cudaSuccess)
+            return PF_EDEVICE;
+        if (c && h->K &&
+            cudaMemcpyAsync(c, h->staging + (size_t)h->N * h->V, sizeof(double) * h->V, kind, h->stream) != cudaSuccess)
+            return PF_EDEVICE;
+    }
+    if (nz) {
+        if (!h->dnz && cudaMalloc(&h->dnz, h->V) != cudaSuccess) return PF_ENOMEM;
+        st = (h->prec == 64) ? rhs_t<double>(h, h->dnz) : rhs_t<float>(h, h->dnz);
+        if (st) return st;
+        if (cudaMemcpyAsync(nz, h->dnz, h->V, kind, h->stream) != cudaSuccess) return PF_EDEVICE;
+    }
+    if (t) *t = h->t;
+    if (!ptr_is_device && cudaStreamSynchronize(h->stream) != cudaSuccess) return PF_EDEVICE;
+    return PF_OK;
+}
+
+int pf_rhs(pf_handle *h, double *rhs_phi, double *rhs_c, unsigned char *nz, int ptr_is_device)
+{
+    if (!h || !rhs_phi) return PF_EINVAL;
+    if (!h->has_state) return PF_ESTATE;
+    int st;
+    if ((st = ensure_staging(h))) return st;
+    if (nz && !h->dnz && cudaMalloc(&h->dnz, h->V) != cudaSuccess) return PF_ENOMEM;
+    if (cudaMemsetAsync(h->dflag, 0, sizeof(int), h->stream) != cudaSuccess) return PF_EDEVICE;
+    st = (h->prec == 64) ? rhs_t<double>(h, nz ? h->dnz : nullptr) : rhs_t<float>(h, nz ? h->dnz : nullptr);
+    if (st) return st;
+    const cudaMemcpyKind kind = ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (cudaMemcpyAsync(rhs_phi, h->staging, sizeof(double) * (size_t)h->N * h->V, kind, h->stream) != cudaSuccess)
+        return PF_EDEVICE;
+    if (rhs_c && h->K &&
+        cudaMemcpyAsync(rhs_c, h->staging + (size_t)h->N * h->V, sizeof(double) * h->V, kind, h->stream) != cudaSuccess)
+        return PF_EDEVICE;
+    if (nz && cudaMemcpyAsync(nz, h->dnz, h->V, kind, h->stream) != cudaSuccess) return PF_EDEVICE;
+    return check_flag(h);
+}
+
+int pf_step(pf_handle *h, pf_integrator integ, double t_end, const pf_tol *tol, const pf_step_opts *opts,
+            pf_stats *stats)
+{
+    if (!h) return PF_EINVAL;
+    if (!h->has_state) return PF_ESTATE;
+    if ((int)integ < PF_FEULER || (int)integ > PF_RKL2) return PF_EINVAL;
+    if (!(t_end >= h->t)) return PF_EINVAL;
+    pf_step_opts o;
+    memset(&o, 0, sizeof(o));
+    o.ssp_stages = 5;
+    if (opts) o = *opts;
+    return (h->prec == 64) ? step_loop<double>(h, integ, t_end, tol, &o, stats)
+                           : step_loop<float>(h, integ, t_end, tol, &o, stats);
+}
+
+int pf_profile(pf_handle *h, int enable, double *ms, long long *launches)
+{
+    if (!h) return PF_EINVAL;
+    if (enable && h->ev_pool.empty()) {
+        const int cap = 4096;
+        h->ev_pool.resize(2 * cap);
+        h->ev_kind.resize(cap);
+        for (auto &ev : h->ev_pool)
+            if (cudaEventCreate(&ev) != cudaSuccess) return PF_EDEVICE;
+    }
+    int st = prof_flush(h);
+    if (st) return st;
+    if (ms)
+        for (int k = 0; k < PF_NPASS_KINDS; ++k) ms[k] = h->prof_ms[k];
+    if (launches)
+        for (int k = 0; k < PF_NPASS_KINDS; ++k) launches[k] = h->prof_n[k];
+    if (enable >= 0) {
+        for (int k = 0; k < PF_NPASS_KINDS; ++k) { h->prof_ms[k] = 0.0; h->prof_n[k] = 0; }
+        h->prof_on = enable != 0;
+    }
+    return PF_OK;
+}
+
+long long pf_launch_count(pf_handle *h) { return h ? h->launches : -1; }
+
+int pf_reduce(pf_handle *h, double *mass_c, double *vol_phi, int *grains_alive)
+{
+    if (!h) return PF_EINVAL;
+    if (!h->has_state) return PF_ESTATE;
+    int st = (h->prec == 64) ? totals_t<double>(h) : totals_t<float>(h);
+    if (st) return st;
+    std::vector<double> s((size_t)h->tot_blocks * h->NP), m((size_t)h->tot_blocks * h->NP);
+    if (cudaMemcpyAsync(s.data(), h->tot_sum, sizeof(double) * s.size(), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+        return PF_EDEVICE;
+    if (cudaMemcpyAsync(m.data(), h->tot_max, sizeof(double) * m.size(), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+        return PF_EDEVICE;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return PF_EDEVICE;
+    const double dv = pow(h->dx, h->g.dim);
+    int alive = 0;
+    for (int f = 0; f < h->NP; ++f) {
+        double tot = 0.0, mx = -1e300;
+        for (int b = 0; b < h->tot_blocks; ++b) {
+            tot += s[(size_t)f * h->tot_blocks + b];
+            mx = fmax(mx, m[(size_t)f * h->tot_blocks + b]);
+        }
+        if (f < h->N) {
+            if (vol_phi) vol_phi[f] = tot * dv;
+            if (mx >= 0.5) alive++;
+        } else if (mass_c) {
+            *mass_c = tot * dv;
+        }
+    }
+    if (mass_c && !h->K) *mass_c = 0.0;
+    if (grains_alive) *grains_alive = alive;
+    return PF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,784 @@
+// pf_kernels.cuh -- sm_103a device code for one explicit stage of the
+// obstacle-potential multi-phase-field + KKS model (Seiz & Takaki,
+// arXiv 2601.16522, Sec. 2-3).
+//
+// Layout in HBM: a state vector holds NF = N + K fields, field f at
+// u + f * Vs (Vs = V rounded up to 64 cells, so every field starts 256-byte
+// aligned); inside a field cells are x-fastest.  One thread owns one cell:
+// every load of a warp is 32 consecutive cells of one field (coalesced), and
+// the per-cell loops over phases run over phase planes with stage values of a
+// chunk of phases held in shared memory.  The nontrivial phases of a cell (the n(phi) filter of Eq. phieq,
+// at most MAXACT of them) are gathered into a small static-index list in
+// ascending phase order (per-thread slots in shared memory), so the pairwise
+// sums run over the N_z entries only, in the same order as a plain loop over
+// all phases.
+//
+// One pass computes the RHS of its stencil input and, fused, the stage
+// combination, the simplex projection (Sec. 3.1), the RKL2 first-stage fix
+// (Sec. 3.2), the SSP(10)4 embedded accumulator and the per-thread partials
+// of the error norm (Sec. 3.3).  With more phases than one chunk holds the
+// unnormalised stage values are written and re-read (L2-resident) for the
+// projection's normalisation.  The hot passes are compiled per signature
+// (which inputs and outputs they use); everything else takes the generic
+// instantiation that reads the options at run time.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pfk {
+
+enum { BC_PERIODIC = 0, BC_NEUMANN = 1, BC_DIRICHLET = 2 };
+constexpr int MAXACT = 12;      // nontrivial phases per cell handled by the list
+constexpr int TX = 32, TY = 8;  // cells per block: 32 (x) by 8 (y), one z plane
+constexpr int BLOCK = TX * TY;
+
+// Problem constants shared by every pass (passed by value).
+struct Geom {
+    int nx, ny, nz, dim;
+    long long V, Vs;                    // cells, field stride
+    int N, K, NF;
+    int bc_phi[6], bc_c[6];
+    double cdir[6];
+    double dx2;                         // dx * dx
+    double k[2], c0[2], invk[2], Dk[2]; // per chemical type: k, c0, 1/k, D/k
+    int tiles_x, tiles_y;               // block tiling of the x-y plane
+};
+
+// What one pass does (passed by value).
+template <typename T>
+struct Pass {
+    int mode;            // MODE_RHS, MODE_STAGE or MODE_ERR
+    const T *in;         // stencil input (the RHS is evaluated on it)
+    const T *p0;         // pointwise input with coefficient a0 (may be null)
+    const T *p2;         // pointwise input with coefficient a2 (may be null)
+    const T *r0in;       // pointwise RHS with coefficient b0 (may be null)
+    T *out;              // stage output
+    T *r0out;            // store the RHS of `in` (RKL stage 1); may be null
+    int fix_first;       // RKL2 first-stage replacement where S acted (Sec. 3.2)
+    const T *zin;        // SSP(10)4 embedded accumulator input (may be null)
+    T *zout;             // SSP(10)4 embedded accumulator output (may be null)
+    T *out2;             // SSP(10)4 after stage 5: q2 output (with q2in)
+    const T *q2in;
+    const T *uw;         // u^n for the error weights (SSP(10)4 final stage)
+    int project;         // apply the simplex projection to the phases
+    int embedded_err;    // final SSP(10)4 stage: e = u - z into the error partials
+    double a0, a1, a2, b1, b0, bz;   // combination coefficients (dt folded into b*)
+    double m25, m925, m15, m5;       // SSP(10)4 mid-stage combination coefficients
+    double dt;                       // step size (error sweep)
+    double r_phi, a_phi, r_c, a_c;   // tolerances (error partials)
+    double *part_sum;    // per-block partial sums of (e/w)^2
+    long long *part_cnt; // per-block partial DoF counts
+    double *rhs_pm;      // MODE_RHS: FP64 output, field f at rhs_pm + f * V
+    unsigned char *nz_out; // MODE_RHS: N_z per cell (may be null)
+    int *flag;           // device status flags
+};
+
+enum { MODE_RHS = 0, MODE_STAGE = 1, MODE_ERR = 2 };
+enum { FLAG_SIMPLEX = 1, FLAG_NZ_OVERFLOW = 2 };
+
+template <typename T>
+__device__ __forceinline__ T ldg(const T *p) { return __ldg(p); }
+
+template <typename T>
+__device__ __forceinline__ T tabs(T v) { return v < (T)0 ? -v : v; }
+
+// Offsets (in cells) of the 2d face neighbours of (x,y,z); ghost[f] = 1 for a
+// non-periodic domain face (the caller builds the ghost value), else 0.
+__device__ __forceinline__ void face_offsets(const Geom &g, int x, int y, int z, long long off[6], int ghost[6])
+{
+    const long long sx = 1, sy = g.nx, sz = (long long)g.nx * g.ny;
+    const int c[3] = {x, y, z};
+    const int n[3] = {g.nx, g.ny, g.nz};
+    const long long s[3] = {sx, sy, sz};
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+        const int ax = f >> 1;
+        const bool plus = f & 1;
+        ghost[f] = 0;
+        if (!plus) {
+            if (c[ax] > 0) off[f] = -s[ax];
+            else if (g.bc_phi[f] == BC_PERIODIC) off[f] = (long long)(n[ax] - 1) * s[ax];
+            else { off[f] = 0; ghost[f] = 1; }
+        } else {
+            if (c[ax] < n[ax] - 1) off[f] = s[ax];
+            else if (g.bc_phi[f] == BC_PERIODIC) off[f] = -(long long)(n[ax] - 1) * s[ax];
+            else { off[f] = 0; ghost[f] = 1; }
+        }
+    }
+}
+
+// Fixed-order block reduction of (sum, count) into the per-block partials.
+__device__ __forceinline__ void block_partials(double esum, long long ecnt, double *ps, long long *pc, int bid)
+{
+    __shared__ double rs_sum[BLOCK / 32];
+    __shared__ long long rs_cnt[BLOCK / 32];
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        esum += __shfl_xor_sync(0xffffffffu, esum, o);
+        ecnt += __shfl_xor_sync(0xffffffffu, ecnt, o);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) { rs_sum[wid] = esum; rs_cnt[wid] = ecnt; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        long long c = 0;
+        for (int w = 0; w < BLOCK / 32; ++w) { s += rs_sum[w]; c += rs_cnt[w]; }
+        ps[bid] = s;
+        pc[bid] = c;
+    }
+}
+
+// Compile-time pass signature: which optional inputs/outputs a pass uses.
+// SIG_GENERIC reads every option from the Pass at run time.
+enum : unsigned {
+    SIG_P0 = 1u, SIG_P2 = 2u, SIG_R0IN = 4u, SIG_R0OUT = 8u, SIG_PROJECT = 16u,
+    SIG_ERR = 32u, SIG_RHS = 64u, SIG_GENERIC = 1u << 30
+};
+
+template <typename T>
+struct Smem {
+    static constexpr int NV = sizeof(T) == 4 ? 32 : 16;   // stage values held per chunk
+    unsigned char id[MAXACT][BLOCK];
+    T lap[MAXACT][BLOCK];    // Laplacian, later the RHS of the listed phase
+    T cen[MAXACT][BLOCK];    // phi at the cell
+    T dl[MAXACT][BLOCK];     // variational derivative
+    T nv[NV][BLOCK];         // stage values of the current chunk
+};
+
+template <typename T, int DIM, int KC, unsigned SIG>
+__global__ void __launch_bounds__(BLOCK)
+cell_kernel(const Geom g, const Pass<T> P, const T *__restrict__ tabA, const T *__restrict__ tabB,
+            const T *__restrict__ tabL, const signed char *__restrict__ ptype)
+{
+    constexpr int NFACE = 2 * DIM;
+    constexpr bool GEN = (SIG & SIG_GENERIC) != 0;
+    constexpr int NV = Smem<T>::NV;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem<T> &S = *reinterpret_cast<Smem<T> *>(smem_raw);
+    const int tid = threadIdx.x;
+
+    // pass options: compile-time for the specialised signatures, run time for GENERIC
+    const int mode = GEN ? P.mode : ((SIG & SIG_ERR) ? MODE_ERR : (SIG & SIG_RHS) ? MODE_RHS : MODE_STAGE);
+    const bool has_p0 = GEN ? P.p0 != nullptr : (SIG & SIG_P0) != 0;
+    const bool has_p2 = GEN ? P.p2 != nullptr : (SIG & SIG_P2) != 0;
+    const bool has_r0in = GEN ? P.r0in != nullptr : (SIG & SIG_R0IN) != 0;
+    const bool has_r0out = GEN ? P.r0out != nullptr : (SIG & SIG_R0OUT) != 0;
+    const bool project = GEN ? P.project != 0 : (SIG & SIG_PROJECT) != 0;
+    const bool has_z = GEN && P.zout != nullptr;
+    const bool emb = GEN && P.embedded_err != 0;
+    const bool has_out2 = GEN && P.out2 != nullptr;
+
+    const int N = g.N;
+    const int K = KC;
+    const long long Vs = g.Vs;
+    const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    const int x = blockIdx.x * TX + (tid % TX);
+    const int y = blockIdx.y * TY + (tid / TX);
+    const int z = blockIdx.z;
+    const bool valid = x < g.nx && y < g.ny;
+    const long long i = valid ? ((long long)z * g.ny + y) * g.nx + x : 0;
+    const T dx2 = (T)g.dx2;
+
+    double esum = 0.0;
+    long long ecnt = 0;
+
+    if (valid) {
+        long long off[6];
+        int ghost[6];
+        face_offsets(g, x, y, z, off, ghost);
+        // a zero-gradient ghost of phi is the cell itself: offset 0
+#pragma unroll
+        for (int f = 0; f < 6; ++f) if (ghost[f]) off[f] = 0;
+
+        // ---- concentration at the cell and its face neighbours -------------
+        T cc = (T)0, num_c = (T)0, den_c = (T)0, num_n[NFACE], den_n[NFACE], mf[NFACE];
+#pragma unroll
+        for (int f = 0; f < NFACE; ++f) { num_n[f] = (T)0; den_n[f] = (T)0; mf[f] = (T)0; }
+        if (K) {
+            const T *cf = P.in + (long long)N * Vs + i;
+            cc = ldg(cf);
+            num_c = cc;
+#pragma unroll
+            for (int f = 0; f < NFACE; ++f) {
+                T v = ldg(cf + off[f]);
+                if (ghost[f] && g.bc_c[f] == BC_DIRICHLET) v = (T)2 * (T)g.cdir[f] - cc;
+                num_n[f] = v;
+            }
+        }
+
+        // ---- pass 1: activity, Laplacian, chemistry sums (Sec. 2-3) --------
+        int nz = 0;
+        {
+            const T *fp = P.in + i;
+#pragma unroll 4
+            for (int a = 0; a < N; ++a, fp += Vs) {
+                const T v0 = ldg(fp);
+                T nb[NFACE];
+#pragma unroll
+                for (int f = 0; f < NFACE; ++f) nb[f] = ldg(fp + off[f]);
+                T mx = v0, mn = v0;
+#pragma unroll
+                for (int f = 0; f < NFACE; ++f) {
+                    mx = nb[f] > mx ? nb[f] : mx;
+                    mn = nb[f] < mn ? nb[f] : mn;
+                }
+                if (K) {
+                    const int t = ptype[a];
+                    const T c0t = (T)g.c0[t], ikt = (T)g.invk[t], dkt = (T)g.Dk[t];
+                    num_c = num_c - v0 * c0t;
+                    den_c = den_c + v0 * ikt;
+#pragma unroll
+                    for (int f = 0; f < NFACE; ++f) {
+                        num_n[f] = num_n[f] - nb[f] * c0t;
+                        den_n[f] = den_n[f] + nb[f] * ikt;
+                        mf[f] = mf[f] + dkt * ((T)0.5 * (v0 + nb[f]));
+                    }
+                }
+                if (mx > (T)0 && mn < (T)1) {
+                    T l = (T)0;
+#pragma unroll
+                    for (int f = 0; f < NFACE; ++f) l = l + (nb[f] - v0);
+                    if (nz < MAXACT) {
+                        S.id[nz][tid] = (unsigned char)a;
+                        S.lap[nz][tid] = l / dx2;
+                        S.cen[nz][tid] = v0;
+                    }
+                    nz++;
+                }
+            }
+        }
+        if (nz > MAXACT) {
+            atomicOr(P.flag, FLAG_NZ_OVERFLOW);
+            nz = MAXACT;
+        }
+
+        // ---- grand potential and concentration RHS -------------------------
+        T mu = (T)0, rc = (T)0;
+        if (K) {
+            mu = num_c / den_c;
+            T acc = (T)0;
+#pragma unroll
+            for (int f = 0; f < NFACE; ++f) {
+                const T mun = num_n[f] / den_n[f];
+                acc = acc + mf[f] * (mun - mu);
+            }
+            rc = acc / dx2;
+        }
+
+        // ---- variational derivative and pairwise sum over the list ---------
+        for (int k = 0; k < nz; ++k) {
+            const int a = S.id[k][tid];
+            const T *Aa = tabA + a * N, *Ba = tabB + a * N;
+            T d = (T)0;
+            for (int k2 = 0; k2 < nz; ++k2) {
+                if (k2 == k) continue;
+                const int b = S.id[k2][tid];
+                d = d + (ldg(Aa + b) * S.lap[k2][tid] + ldg(Ba + b) * S.cen[k2][tid]);
+            }
+            T psi = (T)0;
+            if (K) {
+                const int t = ptype[a];
+                psi = -(mu * mu) / ((T)2 * (T)g.k[t]) - mu * (T)g.c0[t];
+            }
+            S.dl[k][tid] = d + psi;
+        }
+        for (int k = 0; k < nz; ++k) {
+            T rk = (T)0;
+            if (nz > 1) {
+                const int a = S.id[k][tid];
+                const T *La = tabL + a * N;
+                const T dk = S.dl[k][tid];
+                T s = (T)0;
+                for (int k2 = 0; k2 < nz; ++k2) {
+                    if (k2 == k) continue;
+                    s = s + ldg(La + S.id[k2][tid]) * (dk - S.dl[k2][tid]);
+                }
+                rk = -(s / (T)nz);
+            }
+            S.lap[k][tid] = rk;                  // the list now holds the RHS
+        }
+
+        // list cursor: phases are visited in ascending order
+        int kk = 0;
+        int curid = nz > 0 ? S.id[0][tid] : -1;
+#define PF_NEXT_RHS(a_, r_)                                          \
+    if ((a_) == curid) {                                             \
+        r_ = S.lap[kk][tid];                                         \
+        kk++;                                                        \
+        curid = kk < nz ? S.id[kk][tid] : -1;                        \
+    }
+
+        if (mode == MODE_RHS) {
+            // ---- RHS only (pf_rhs) -------------------------------------------
+            for (int a = 0; a < N; ++a) {
+                T r = (T)0;
+                PF_NEXT_RHS(a, r)
+                P.rhs_pm[(long long)a * g.V + i] = (double)r;
+            }
+            if (K) P.rhs_pm[(long long)N * g.V + i] = (double)rc;
+            if (P.nz_out) P.nz_out[i] = (unsigned char)nz;
+        } else if (mode == MODE_ERR) {
+            // ---- STS error sweep (Sec. 3.3): in = u^{n+1}, p0 = u^n, r0in = F^n
+            const T dt = (T)P.dt;
+            const T rph = (T)P.r_phi, aph = (T)P.a_phi;
+            int nc = 0;
+            long long o = i;
+#pragma unroll 4
+            for (int a = 0; a < N; ++a, o += Vs) {
+                T r1 = (T)0;
+                PF_NEXT_RHS(a, r1)
+                const T un = ldg(P.p0 + o), un1 = ldg(P.in + o), rn = ldg(P.r0in + o);
+                const T sr = rn + r1;
+                T e = ((T)12 * (un - un1) + ((T)6 * dt) * sr) / (T)15;
+                const T trial = un + (dt / (T)2) * sr;
+                if (trial < (T)0 || trial > (T)1) e = (T)0;
+                if (e != (T)0) {
+                    const T au = tabs(un), av = tabs(un1);
+                    const T w = rph * (au > av ? au : av) + aph;
+                    const T q = e / w;
+                    esum += (double)(q * q);
+                    nc++;
+                }
+            }
+            ecnt += (nc > 0 ? nc : 2);
+            if (K) {
+                const long long oc = (long long)N * Vs + i;
+                const T un = ldg(P.p0 + oc), un1 = ldg(P.in + oc), rn = ldg(P.r0in + oc);
+                const T sr = rn + rc;
+                const T e = ((T)12 * (un - un1) + ((T)6 * dt) * sr) / (T)15;
+                const T au = tabs(un), av = tabs(un1);
+                const T w = (T)P.r_c * (au > av ? au : av) + (T)P.a_c;
+                const T q = e / w;
+                esum += (double)(q * q);
+                ecnt += 1;
+            }
+        } else {
+            // ---- stage combination (Eq. sts / Alg. ssp2 / SSP(10)4) ---------
+            const T a0c = (T)P.a0, a1c = (T)P.a1, a2c = (T)P.a2, b1c = (T)P.b1, b0c = (T)P.b0, bzc = (T)P.bz;
+            const bool chunked = N > NV;
+            bool changed = false;
+            T best = (T)-1;
+            int bestid = -1;
+            T ssum = (T)0;
+            for (int a0 = 0; a0 < N; a0 += NV) {
+                const int an = (N - a0) < NV ? (N - a0) : NV;
+                long long o = (long long)a0 * Vs + i;
+#pragma unroll 4
+                for (int aa = 0; aa < an; ++aa, o += Vs) {
+                    const int a = a0 + aa;
+                    T r = (T)0;
+                    PF_NEXT_RHS(a, r)
+                    const T v = ldg(P.in + o);
+                    T acc;
+                    if (has_p0) { acc = a0c * ldg(P.p0 + o); acc = acc + a1c * v; }
+                    else acc = a1c * v;
+                    if (has_p2) acc = acc + a2c * ldg(P.p2 + o);
+                    acc = acc + b1c * r;
+                    if (has_r0in) acc = acc + b0c * ldg(P.r0in + o);
+                    if (has_r0out) P.r0out[o] = r;      // replaced below where S acts (RKL2)
+                    if (has_z) P.zout[o] = P.zin[o] + bzc * r;   // zin may alias zout
+                    if (project) {
+                        // S step 1: clamp negatives; step 2 candidate: largest >= 1
+                        if (acc < (T)0) { acc = (T)0; changed = true; }
+                        if (acc >= (T)1 && acc > best) { best = acc; bestid = a; }
+                    }
+                    if (chunked) P.out[o] = acc;
+                    else S.nv[aa][tid] = acc;
+                }
+            }
+            // S step 2 (the >= 1 rule) and the sum for step 3, ascending order
+            if (project) {
+                if (bestid >= 0) {
+                    // the winner becomes 1, the others 0; the sum is then exactly 1
+                    if (!chunked) {
+                        for (int aa = 0; aa < N; ++aa) {
+                            const T w = (aa == bestid) ? (T)1 : (T)0;
+                            if (S.nv[aa][tid] != w) changed = true;
+                        }
+                    } else {
+                        changed = true;
+                    }
+                    ssum = (T)1;
+                } else if (!chunked) {
+                    for (int aa = 0; aa < N; ++aa) ssum = ssum + S.nv[aa][tid];
+                } else {
+                    for (int a = 0; a < N; ++a) ssum = ssum + P.out[(long long)a * Vs + i];
+                }
+                if (!(ssum > (T)0)) atomicOr(P.flag, FLAG_SIMPLEX);
+            }
+            const bool fix = has_r0out && P.fix_first && changed;
+            // store pass: S step 3, first-stage fix, embedded error, SSP(10)4 mid combination
+            int nc = 0;
+            {
+                long long o = i;
+#pragma unroll 4
+                for (int a = 0; a < N; ++a, o += Vs) {
+                    T w = chunked ? P.out[o] : S.nv[a][tid];
+                    if (project) {
+                        if (bestid >= 0) w = (a == bestid) ? (T)1 : (T)0;
+                        else if (ssum > (T)0) w = w / ssum;
+                    }
+                    if (fix) P.r0out[o] = (w - ldg(P.in + o)) / b1c;
+                    if (emb) {
+                        const T zv = P.zout[o];
+                        T e = w - zv;
+                        if (zv < (T)0 || zv > (T)1) e = (T)0;
+                        if (e != (T)0) {
+                            const T au = tabs(ldg(P.uw + o)), av = tabs(w);
+                            const T wt = (T)P.r_phi * (au > av ? au : av) + (T)P.a_phi;
+                            const T q = e / wt;
+                            esum += (double)(q * q);
+                            nc++;
+                        }
+                    }
+                    if (has_out2) {
+                        const T q2 = (T)P.m25 * ldg(P.q2in + o) + (T)P.m925 * w;
+                        P.out2[o] = q2;
+                        P.out[o] = (T)P.m15 * q2 + (T)P.m5 * w;
+                    } else {
+                        P.out[o] = w;
+                    }
+                }
+            }
+            if (emb) ecnt += (nc > 0 ? nc : 2);
+            // concentration field (no projection)
+            if (K) {
+                const long long o = (long long)N * Vs + i;
+                T acc;
+                if (has_p0) { acc = a0c * ldg(P.p0 + o); acc = acc + a1c * cc; }
+                else acc = a1c * cc;
+                if (has_p2) acc = acc + a2c * ldg(P.p2 + o);
+                acc = acc + b1c * rc;
+                if (has_r0in) acc = acc + b0c * ldg(P.r0in + o);
+                if (has_r0out) P.r0out[o] = rc;
+                if (has_z) {
+                    const T zv = P.zin[o] + bzc * rc;
+                    P.zout[o] = zv;
+                    if (emb) {
+                        const T e = acc - zv;
+                        const T au = tabs(ldg(P.uw + o)), av = tabs(acc);
+                        const T wt = (T)P.r_c * (au > av ? au : av) + (T)P.a_c;
+                        const T q = e / wt;
+                        esum += (double)(q * q);
+                        ecnt += 1;
+                    }
+                }
+                if (has_out2) {
+                    const T q2 = (T)P.m25 * ldg(P.q2in + o) + (T)P.m925 * acc;
+                    P.out2[o] = q2;
+                    P.out[o] = (T)P.m15 * q2 + (T)P.m5 * acc;
+                } else {
+                    P.out[o] = acc;
+                }
+            }
+        }
+#undef PF_NEXT_RHS
+    }
+
+    if (mode == MODE_ERR || emb) block_partials(esum, ecnt, P.part_sum, P.part_cnt, bid);
+}
+
+// Shared-memory slots of the per-cell active list (no stage values).
+template <typename T>
+struct ListSmem {
+    unsigned char id[MAXACT][BLOCK];
+    T lap[MAXACT][BLOCK];    // Laplacian, later the RHS of the listed phase
+    T cen[MAXACT][BLOCK];    // phi at the cell
+    T dl[MAXACT][BLOCK];     // variational derivative
+};
+
+// FP32 fast path for N <= NMAX phases and the specialised signatures.  The
+// loop over phases is unrolled NMAX times (guarded by a < N) so the stage
+// values stay in registers and every load of a phase (stencil and pointwise)
+// is issued together; a phase that is not nontrivial has a zero RHS, so its
+// stage value (or error term) is final in that first loop.  Only the N_z
+// listed phases receive their RHS term after the pairwise sums.  Rounding
+// order differs from the generic kernel; FP32 is not compared bit for bit.
+template <int DIM, int KC, unsigned SIG, int NMAX>
+__global__ void __launch_bounds__(BLOCK, 4)
+fast_kernel(const Geom g, const Pass<float> P, const float *__restrict__ tabA, const float *__restrict__ tabB,
+            const float *__restrict__ tabL, const signed char *__restrict__ ptype)
+{
+    typedef float T;
+    constexpr int NFACE = 2 * DIM;
+    constexpr bool ERR = (SIG & SIG_ERR) != 0;
+    constexpr bool HP0 = (SIG & SIG_P0) != 0 || ERR;
+    constexpr bool HP2 = (SIG & SIG_P2) != 0;
+    constexpr bool HR0 = (SIG & SIG_R0IN) != 0 || ERR;
+    constexpr bool R0OUT = (SIG & SIG_R0OUT) != 0;
+    constexpr bool PROJ = (SIG & SIG_PROJECT) != 0;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ListSmem<T> &S = *reinterpret_cast<ListSmem<T> *>(smem_raw);
+    const int tid = threadIdx.x;
+    const int N = g.N;
+    const int Vs = (int)g.Vs;
+    const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    const int x = blockIdx.x * TX + (tid % TX);
+    const int y = blockIdx.y * TY + (tid / TX);
+    const int z = blockIdx.z;
+    const bool valid = x < g.nx && y < g.ny;
+    const long long i = valid ? ((long long)z * g.ny + y) * g.nx + x : 0;
+    const T idx2 = (T)(1.0 / g.dx2);
+    double esum = 0.0;
+    long long ecnt = 0;
+
+    if (valid) {
+        long long off64[6];
+        int ghost[6];
+        face_offsets(g, x, y, z, off64, ghost);
+        int off[6];
+#pragma unroll
+        for (int f = 0; f < 6; ++f) off[f] = ghost[f] ? 0 : (int)off64[f];
+
+        const T a0c = (T)P.a0, a1c = (T)P.a1, a2c = (T)P.a2, b1c = (T)P.b1, b0c = (T)P.b0;
+        const T dt = (T)P.dt, rph = (T)P.r_phi, aph = (T)P.a_phi;
+        const T *pin = P.in + i;
+        const T *pp0 = HP0 ? P.p0 + i : nullptr;
+        const T *pp2 = HP2 ? P.p2 + i : nullptr;
+        const T *pr0 = HR0 ? P.r0in + i : nullptr;
+
+        // concentration
+        T cc = (T)0, num_c = (T)0, den_c = (T)0, num_n[NFACE], den_n[NFACE], mf[NFACE];
+#pragma unroll
+        for (int f = 0; f < NFACE; ++f) { num_n[f] = (T)0; den_n[f] = (T)0; mf[f] = (T)0; }
+        if (KC) {
+            const T *cf = pin + (long long)N * Vs;
+            cc = ldg(cf);
+            num_c = cc;
+#pragma unroll
+            for (int f = 0; f < NFACE; ++f) {
+                T v = ldg(cf + off[f]);
+                if (ghost[f] && g.bc_c[f] == BC_DIRICHLET) v = (T)2 * (T)g.cdir[f] - cc;
+                num_n[f] = v;
+            }
+        }
+
+        int nz = 0, nc = 0;
+        bool changed = false;
+        T best = (T)-1, ssum = (T)0;
+        int bestid = -1;
+        T nv[NMAX];
+        unsigned actmask = 0u;
+#pragma unroll
+        for (int a = 0; a < NMAX; ++a) {
+            nv[a] = (T)0;
+            if (a < N) {
+                const long long fo = (long long)a * Vs;
+                const T v0 = ldg(pin + fo);
+                T nb[NFACE];
+#pragma unroll
+                for (int f = 0; f < NFACE; ++f) nb[f] = ldg(pin + fo + off[f]);
+                const T p0v = HP0 ? ldg(pp0 + fo) : (T)0;
+                const T p2v = HP2 ? ldg(pp2 + fo) : (T)0;
+                const T r0v = HR0 ? ldg(pr0 + fo) : (T)0;
+                T mx = v0, mn = v0;
+#pragma unroll
+                for (int f = 0; f < NFACE; ++f) {
+                    mx = fmaxf(mx, nb[f]);
+                    mn = fminf(mn, nb[f]);
+                }
+                if (KC) {
+                    const int t = ptype[a];
+                    const T c0t = (T)g.c0[t], ikt = (T)g.invk[t], dkt = (T)g.Dk[t];
+                    num_c = num_c - v0 * c0t;
+                    den_c = den_c + v0 * ikt;
+#pragma unroll
+                    for (int f = 0; f < NFACE; ++f) {
+                        num_n[f] = num_n[f] - nb[f] * c0t;
+                        den_n[f] = den_n[f] + nb[f] * ikt;
+                        mf[f] = mf[f] + dkt * ((T)0.5 * (v0 + nb[f]));
+                    }
+                }
+                const bool act = mx > (T)0 && mn < (T)1;
+                if (act) {
+                    T l = (T)0;
+#pragma unroll
+                    for (int f = 0; f < NFACE; ++f) l = l + (nb[f] - v0);
+                    if (nz < MAXACT) {
+                        S.id[nz][tid] = (unsigned char)a;
+                        S.lap[nz][tid] = l * idx2;
+                        S.cen[nz][tid] = v0;
+                        actmask |= 1u << a;
+                    }
+                    nz++;
+                }
+                if (ERR) {
+                    // in = u^{n+1}, p0 = u^n, r0in = F^n; a trivial phase has F^{n+1} = 0
+                    if (!act) {
+                        T e = ((T)12 * (p0v - v0) + ((T)6 * dt) * r0v) * ((T)1 / (T)15);
+                        const T trial = p0v + (dt * (T)0.5) * r0v;
+                        if (trial < (T)0 || trial > (T)1) e = (T)0;
+                        if (e != (T)0) {
+                            const T w = rph * fmaxf(fabsf(p0v), fabsf(v0)) + aph;
+                            const T q = e / w;
+                            esum += (double)(q * q);
+                            nc++;
+                        }
+                    }
+                } else {
+                    T acc = HP0 ? a0c * p0v + a1c * v0 : a1c * v0;
+                    if (HP2) acc = acc + a2c * p2v;
+                    if (HR0) acc = acc + b0c * r0v;
+                    if (!act && PROJ) {
+                        if (acc < (T)0) { acc = (T)0; changed = true; }
+                        if (acc >= (T)1 && acc > best) { best = acc; bestid = a; }
+                        ssum = ssum + acc;
+                    }
+                    nv[a] = acc;
+                }
+            }
+        }
+        if (nz > MAXACT) {
+            atomicOr(P.flag, FLAG_NZ_OVERFLOW);
+            nz = MAXACT;
+        }
+
+        T mu = (T)0, rc = (T)0;
+        if (KC) {
+            mu = num_c / den_c;
+            T acc = (T)0;
+#pragma unroll
+            for (int f = 0; f < NFACE; ++f) acc = acc + mf[f] * (num_n[f] / den_n[f] - mu);
+            rc = acc * idx2;
+        }
+        // variational derivative and pairwise sum over the listed phases
+        for (int k = 0; k < nz; ++k) {
+            const int a = S.id[k][tid];
+            const T *Aa = tabA + a * N, *Ba = tabB + a * N;
+            T d = (T)0;
+            for (int k2 = 0; k2 < nz; ++k2) {
+                if (k2 == k) continue;
+                const int b = S.id[k2][tid];
+                d = d + (ldg(Aa + b) * S.lap[k2][tid] + ldg(Ba + b) * S.cen[k2][tid]);
+            }
+            if (KC) {
+                const int t = ptype[a];
+                d = d + (-(mu * mu) / ((T)2 * (T)g.k[t]) - mu * (T)g.c0[t]);
+            }
+            S.dl[k][tid] = d;
+        }
+        const T inz = nz > 1 ? (T)1 / (T)nz : (T)0;
+        for (int k = 0; k < nz; ++k) {
+            T rk = (T)0;
+            if (nz > 1) {
+                const int a = S.id[k][tid];
+                const T *La = tabL + a * N;
+                const T dk = S.dl[k][tid];
+                T s = (T)0;
+                for (int k2 = 0; k2 < nz; ++k2) {
+                    if (k2 == k) continue;
+                    s = s + ldg(La + S.id[k2][tid]) * (dk - S.dl[k2][tid]);
+                }
+                rk = -(s * inz);
+            }
+            S.lap[k][tid] = rk;                 // the list now holds the RHS
+            if (ERR) {
+                const int a = S.id[k][tid];
+                const long long fo = (long long)a * Vs;
+                const T p0v = ldg(pp0 + fo), v0 = S.cen[k][tid], r0v = ldg(pr0 + fo);
+                const T sr = r0v + rk;
+                T e = ((T)12 * (p0v - v0) + ((T)6 * dt) * sr) * ((T)1 / (T)15);
+                const T trial = p0v + (dt * (T)0.5) * sr;
+                if (trial < (T)0 || trial > (T)1) e = (T)0;
+                if (e != (T)0) {
+                    const T w = rph * fmaxf(fabsf(p0v), fabsf(v0)) + aph;
+                    const T q = e / w;
+                    esum += (double)(q * q);
+                    nc++;
+                }
+            }
+        }
+        if (ERR) {
+            ecnt += (nc > 0 ? nc : 2);
+            if (KC) {
+                const long long o = (long long)N * Vs + i;
+                const T un = ldg(P.p0 + o), un1 = cc, rn = ldg(P.r0in + o);
+                const T e = ((T)12 * (un - un1) + ((T)6 * dt) * (rn + rc)) * ((T)1 / (T)15);
+                const T w = (T)P.r_c * fmaxf(fabsf(un), fabsf(un1)) + (T)P.a_c;
+                const T q = e / w;
+                esum += (double)(q * q);
+                ecnt += 1;
+            }
+        } else {
+            // listed phases: add the RHS term, clamp, >= 1 candidates, sum
+            T rr[NMAX];
+            {
+                int kk = 0;
+                int curid = nz > 0 ? S.id[0][tid] : -1;
+#pragma unroll
+                for (int a = 0; a < NMAX; ++a) {
+                    rr[a] = (T)0;
+                    if ((actmask >> a) & 1u) {
+                        const T rk = S.lap[kk][tid];
+                        kk++;
+                        rr[a] = rk;
+                        T acc = nv[a] + b1c * rk;
+                        if (PROJ) {
+                            if (acc < (T)0) { acc = (T)0; changed = true; }
+                            if (acc >= (T)1 && (acc > best || (acc == best && a < bestid))) { best = acc; bestid = a; }
+                            ssum = ssum + acc;
+                        }
+                        nv[a] = acc;
+                    }
+                }
+                (void)curid;
+            }
+            if (PROJ) {
+                if (bestid >= 0) {
+#pragma unroll
+                    for (int a = 0; a < NMAX; ++a)
+                        if (a < N && nv[a] != ((a == bestid) ? (T)1 : (T)0)) changed = true;
+                    ssum = (T)1;
+                }
+                if (!(ssum > (T)0)) atomicOr(P.flag, FLAG_SIMPLEX);
+            }
+            const T inv = (ssum > (T)0) ? (T)1 / ssum : (T)1;
+            const bool fix = R0OUT && P.fix_first && changed;
+            T *pout = P.out + i;
+            T *pr0o = R0OUT ? P.r0out + i : nullptr;
+#pragma unroll
+            for (int a = 0; a < NMAX; ++a) {
+                if (a < N) {
+                    const long long fo = (long long)a * Vs;
+                    T w = nv[a];
+                    if (PROJ) w = (bestid >= 0) ? ((a == bestid) ? (T)1 : (T)0) : w * inv;
+                    if (R0OUT) {
+                        T r = rr[a];
+                        if (fix) r = (w - ldg(pin + fo)) / b1c;
+                        pr0o[fo] = r;
+                    }
+                    pout[fo] = w;
+                }
+            }
+            if (KC) {
+                const long long o = (long long)N * Vs;
+                T acc = HP0 ? a0c * ldg(pp0 + o) + a1c * cc : a1c * cc;
+                if (HP2) acc = acc + a2c * ldg(pp2 + o);
+                acc = acc + b1c * rc;
+                if (HR0) acc = acc + b0c * ldg(pr0 + o);
+                if (R0OUT) pr0o[o] = rc;
+                pout[o] = acc;
+            }
+        }
+    }
+    if (ERR) block_partials(esum, ecnt, P.part_sum, P.part_cnt, bid);
+}
+
+// Signature of a pass as used by the engine's dispatcher.
+template <typename T>
+inline unsigned pass_signature(const Pass<T> &P)
+{
+    if (P.mode == MODE_ERR) return SIG_ERR;
+    if (P.mode == MODE_RHS) return SIG_RHS;
+    if (P.zout || P.embedded_err || P.out2) return SIG_GENERIC;
+    unsigned s = 0;
+    if (P.p0) s |= SIG_P0;
+    if (P.p2) s |= SIG_P2;
+    if (P.r0in) s |= SIG_R0IN;
+    if (P.r0out) s |= SIG_R0OUT;
+    if (P.project) s |= SIG_PROJECT;
+    return s;
+}
+
+}  // namespace pfk

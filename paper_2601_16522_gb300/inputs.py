@@ -197,7 +197,7 @@ def poisson_disc_seeds(n_cells, count, min_dist, dim, rng, max_tries=200000):
     return np.array(pts)
 
 
-def _diffuse_voronoi(shape, seeds, W, knn=8, chunk=1 << 18):
+def _diffuse_voronoi(shape, seeds, W, knn=6, chunk=1 << 17):
     """Diffuse periodic Voronoi fields: for every grain g among the knn nearest
     seeds, d_g = min over the other neighbours h of the signed distance to the
     bisector of (s_g, s_h); trial phi_g = profile(d_g), rescaled to sum 1
@@ -212,6 +212,7 @@ def _diffuse_voronoi(shape, seeds, W, knn=8, chunk=1 << 18):
     k = min(knn, G)
     labels_out = np.zeros((k, V), np.int32)
     phis_out = np.zeros((k, V), np.float64)
+    eye = np.eye(k, dtype=bool)
     for s0 in range(0, V, chunk):
         idx = np.arange(s0, min(V, s0 + chunk))
         x = idx % nx + 0.5
@@ -224,16 +225,12 @@ def _diffuse_voronoi(shape, seeds, W, knn=8, chunk=1 << 18):
         Dv = P[:, None, :] - S
         Dv -= box * np.round(Dv / box)                    # minimum image
         d2 = (Dv * Dv).sum(-1)                            # (n, k)
-        dist = np.full((len(idx), k), np.inf)
-        for g in range(k):
-            for hh in range(k):
-                if hh == g:
-                    continue
-                sep = S[:, hh, :] - S[:, g, :]
-                sep -= box * np.round(sep / box)
-                ln = np.sqrt((sep * sep).sum(-1))
-                bis = (d2[:, hh] - d2[:, g]) / (2.0 * np.maximum(ln, 1e-12))
-                dist[:, g] = np.minimum(dist[:, g], bis)
+        sep = S[:, None, :, :] - S[:, :, None, :]         # (n, g, h, dims)
+        sep -= box * np.round(sep / box)
+        ln = np.sqrt((sep * sep).sum(-1))
+        bis = (d2[:, None, :] - d2[:, :, None]) / (2.0 * np.maximum(ln, 1e-12))
+        bis[:, eye] = np.inf
+        dist = bis.min(-1)                                # (n, g)
         tr = profile(dist, W)
         tr /= tr.sum(1, keepdims=True)
         labels_out[:, idx] = nn.T
@@ -301,4 +298,52 @@ def multiphase_blobs(nx=24, ny=20, nz=1, n_phases=5, seed=0, W=1.6, dx=1.0, has_
         pert = 0.02 * np.sin(2 * np.pi * x / nx + rng.random() * 6) * np.cos(2 * np.pi * y / ny)
         c = sum(u[a] * c0[ptype[a]] for a in range(n_phases)) + pert
         u[n_phases] = c
+    return prob, u
+
+
+def grains_device(n=256, n_grains=32, min_dist=40.0, seed=2, dim=3, dx=0.005, W_cells=2.5, M=5e-3,
+                  gamma=1.0, knn=6, device="cuda", chunk=1 << 20, region=None):
+    """Same structure as grains(diffuse=True), built with torch on a device
+    (brute-force nearest seeds): returns (Problem, u) with u a float64 tensor
+    of shape (n_grains, V) on `device`.  Used for large benchmark inputs.
+    region=m evaluates only the corner m^dim block (u then has m^dim columns,
+    ordered x-fastest within the block) of the full n^dim structure."""
+    import torch
+    rng = np.random.default_rng(seed)
+    shape = (n,) * dim
+    seeds = poisson_disc_seeds(shape, n_grains, min_dist, dim, rng)
+    W = W_cells * dx
+    prob = Problem(dim=dim, nx=n, ny=n, nz=n if dim == 3 else 1, dx=dx, n_phases=n_grains,
+                   phase_type=np.ones(n_grains, np.int32),
+                   gamma=uniform_pairs(n_grains, gamma), mobility=uniform_pairs(n_grains, M), W=W,
+                   name="grains%d^%d_N%d" % (n, dim, n_grains))
+    m = n if region is None else region
+    V = m ** dim
+    S = torch.tensor(seeds, dtype=torch.float64, device=device)
+    box = torch.full((dim,), float(n), dtype=torch.float64, device=device)
+    u = torch.zeros((n_grains, V), dtype=torch.float64, device=device)
+    k = min(knn, n_grains)
+    eye = torch.eye(k, dtype=torch.bool, device=device)
+    h = math.pi * W_cells / 2.0
+    for s0 in range(0, V, chunk):
+        idx = torch.arange(s0, min(V, s0 + chunk), device=device)
+        coords = [idx % m + 0.5, (idx // m) % m + 0.5, idx // (m * m) + 0.5][:dim]
+        P = torch.stack([c.to(torch.float64) for c in coords], dim=1)
+        Dv = P[:, None, :] - S[None]
+        Dv -= box * torch.round(Dv / box)
+        d2all = (Dv * Dv).sum(-1)
+        d2, nn = torch.topk(d2all, k, dim=1, largest=False)
+        Sk = S[nn]
+        sep = Sk[:, None, :, :] - Sk[:, :, None, :]
+        sep -= box * torch.round(sep / box)
+        ln = torch.sqrt((sep * sep).sum(-1)).clamp_min(1e-12)
+        bis = (d2[:, None, :] - d2[:, :, None]) / (2.0 * ln)
+        bis[:, eye] = float("inf")
+        dist = bis.min(-1).values
+        tr = 0.5 * (1.0 + torch.sin(dist.clamp(-h, h) / W_cells))
+        tr = torch.where(dist <= -h, torch.zeros_like(tr), tr)
+        tr = torch.where(dist >= h, torch.ones_like(tr), tr)
+        tr /= tr.sum(1, keepdim=True)
+        for j in range(k):
+            u.index_put_((nn[:, j], idx), tr[:, j], accumulate=True)
     return prob, u

@@ -1,0 +1,257 @@
+"""ctypes binding of libpf (include/pf.h): argument marshalling only.
+
+Every step of the path runs in the CUDA library; this module converts a
+``Problem`` (paper_2601_16522_gb300.inputs) into ``pf_params``, moves numpy
+arrays or torch tensors across the ABI and raises on non-zero status.  If the
+compiled library is missing it raises ImportError: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpf.so")
+
+FEULER, SSP2, SSP104, RKL1, RKL2 = 0, 1, 2, 3, 4
+PASS_KINDS = ["euler", "ssp", "sts_first", "rkl1", "rkl2", "sts_err", "rhs", "other"]
+PF_OK, PF_EINVAL, PF_ENOMEM, PF_EUNSTABLE, PF_ETIMEOUT, PF_EDEVICE, PF_ESTATE = range(7)
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int)
+_ubp = C.POINTER(C.c_ubyte)
+
+
+class PfError(RuntimeError):
+    def __init__(self, status, what):
+        self.status = status
+        super().__init__("%s failed: %s (status %d)" % (what, _lib().pf_strerror(status).decode(), status))
+
+
+class pf_params(C.Structure):
+    _fields_ = [("dim", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("dx", C.c_double), ("n_phases", C.c_int), ("phase_type", _ip),
+                ("gamma", _dp), ("mobility", _dp), ("W", C.c_double), ("L_override", _dp),
+                ("has_conc", C.c_int), ("k", C.c_double * 2), ("c0", C.c_double * 2),
+                ("D", C.c_double * 2), ("bc_phi", C.c_int * 6), ("bc_c", C.c_int * 6),
+                ("c_dirichlet", C.c_double * 6), ("precision", C.c_int)]
+
+
+class pf_tol(C.Structure):
+    _fields_ = [("r_phi", C.c_double), ("a_phi", C.c_double), ("r_c", C.c_double), ("a_c", C.c_double)]
+
+
+class pf_step_opts(C.Structure):
+    _fields_ = [("ssp_stages", C.c_int), ("dt_mult", C.c_double), ("dt0", C.c_double),
+                ("max_stages", C.c_int), ("max_attempts", C.c_int), ("trace_cap", C.c_int),
+                ("trace_dt", _dp), ("trace_s", _ip), ("trace_err", _dp), ("trace_acc", _ip),
+                ("trace_len", _ip)]
+
+
+class pf_stats(C.Structure):
+    _fields_ = [("rhs_evals", C.c_longlong), ("steps_accepted", C.c_longlong),
+                ("steps_rejected", C.c_longlong), ("t", C.c_double), ("dt_last", C.c_double),
+                ("err_last", C.c_double), ("dt_e", C.c_double), ("dt_next", C.c_double),
+                ("kernel_launches", C.c_longlong)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_LIB = None
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libpf.so not built (run paper_2601_16522_gb300.build.build())")
+        L = C.CDLL(LIB_PATH)
+        H = C.c_void_p
+        L.pf_create.argtypes = [C.POINTER(pf_params), C.c_void_p, C.POINTER(H)]
+        L.pf_set_state.argtypes = [H, C.c_void_p, C.c_void_p, C.c_double, C.c_int]
+        L.pf_rhs.argtypes = [H, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
+        L.pf_step.argtypes = [H, C.c_int, C.c_double, C.POINTER(pf_tol), C.POINTER(pf_step_opts),
+                              C.POINTER(pf_stats)]
+        L.pf_get_state.argtypes = [H, C.c_void_p, C.c_void_p, C.c_void_p, _dp, C.c_int]
+        L.pf_reduce.argtypes = [H, _dp, _dp, _ip]
+        L.pf_dt_e.argtypes = [H, _dp]
+        L.pf_destroy.argtypes = [H]
+        L.pf_profile.argtypes = [H, C.c_int, _dp, C.POINTER(C.c_longlong)]
+        L.pf_launch_count.argtypes = [H]
+        L.pf_launch_count.restype = C.c_longlong
+        L.pf_strerror.argtypes = [C.c_int]
+        L.pf_strerror.restype = C.c_char_p
+        _LIB = L
+    return _LIB
+
+
+def lib():
+    """The loaded libpf (ctypes CDLL)."""
+    return _lib()
+
+
+def _check(st, what):
+    if st != PF_OK:
+        raise PfError(st, what)
+
+
+def _ptr(a):
+    """Raw pointer of a numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+def _is_dev(a):
+    """True for a CUDA tensor, False for numpy arrays and (pinned) CPU tensors."""
+    if isinstance(a, np.ndarray):
+        return False
+    return bool(getattr(a, "is_cuda", False))
+
+
+class Simulation:
+    """One simulation handle (pf_create .. pf_destroy)."""
+
+    def __init__(self, prob, precision=64, stream=None):
+        self.prob = prob
+        N = prob.n_phases
+        self._keep = [np.ascontiguousarray(prob.phase_type, np.int32),
+                      np.ascontiguousarray(prob.gamma, np.float64).reshape(-1),
+                      np.ascontiguousarray(prob.mobility, np.float64).reshape(-1)]
+        p = pf_params()
+        p.dim, p.nx, p.ny, p.nz, p.dx = prob.dim, prob.nx, prob.ny, prob.nz, prob.dx
+        p.n_phases = N
+        p.phase_type = self._keep[0].ctypes.data_as(_ip)
+        p.gamma = self._keep[1].ctypes.data_as(_dp)
+        p.mobility = self._keep[2].ctypes.data_as(_dp)
+        p.W = prob.W
+        if prob.L_override is not None:
+            Lm = np.ascontiguousarray(prob.L_override, np.float64).reshape(-1)
+            self._keep.append(Lm)
+            p.L_override = Lm.ctypes.data_as(_dp)
+        p.has_conc = prob.has_conc
+        for t in range(2):
+            p.k[t], p.c0[t], p.D[t] = prob.k[t], prob.c0[t], prob.D[t]
+        for f in range(6):
+            p.bc_phi[f], p.bc_c[f], p.c_dirichlet[f] = prob.bc_phi[f], prob.bc_c[f], prob.c_dirichlet[f]
+        p.precision = precision
+        self.params = p
+        self.precision = precision
+        self._stream = stream
+        sptr = C.c_void_p(stream.cuda_stream) if stream is not None else None
+        h = C.c_void_p()
+        _check(_lib().pf_create(C.byref(p), sptr, C.byref(h)), "pf_create")
+        self.h = h
+        self.V = prob.V
+        self.N = N
+        self.K = prob.has_conc
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib().pf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -------------------------------------------------------------------
+    def dt_e(self):
+        d = C.c_double()
+        _check(_lib().pf_dt_e(self.h, C.byref(d)), "pf_dt_e")
+        return d.value
+
+    def set_state(self, u, t=0.0):
+        """u: (N+K, V) float64 numpy array (host) or torch CUDA tensor (device)."""
+        dev = _is_dev(u)
+        if not dev:
+            u = np.ascontiguousarray(u, np.float64)
+        assert tuple(u.shape) == (self.N + self.K, self.V), tuple(u.shape)
+        phi = _ptr(u)
+        c = phi + 8 * self.N * self.V if self.K else None
+        _check(_lib().pf_set_state(self.h, phi, c, float(t), int(dev)), "pf_set_state")
+        self._last_in = u
+
+    def get_state(self, out=None, with_nz=False):
+        """Returns (u, t[, nz]); out may be a preallocated numpy array or CUDA tensor."""
+        if out is None:
+            out = np.zeros((self.N + self.K, self.V))
+        dev = _is_dev(out)
+        phi = _ptr(out)
+        c = phi + 8 * self.N * self.V if self.K else None
+        nz = None
+        if with_nz:
+            nz = np.zeros(self.V, np.uint8) if not dev else None
+            if dev:
+                import torch
+                nz = torch.zeros(self.V, dtype=torch.uint8, device=out.device)
+        t = C.c_double()
+        _check(_lib().pf_get_state(self.h, phi, c, _ptr(nz), C.byref(t), int(dev)), "pf_get_state")
+        return (out, t.value, nz) if with_nz else (out, t.value)
+
+    def rhs(self):
+        """RHS of the current state -> ((N+K, V) float64, nz uint8) on the host."""
+        r = np.zeros((self.N + self.K, self.V))
+        nz = np.zeros(self.V, np.uint8)
+        phi = r.ctypes.data
+        c = phi + 8 * self.N * self.V if self.K else None
+        _check(_lib().pf_rhs(self.h, phi, c, nz.ctypes.data, 0), "pf_rhs")
+        return r, nz
+
+    def step(self, integ, t_end, tol=None, dt_mult=0.0, ssp_stages=5, dt0=0.0, max_stages=0,
+             max_attempts=0, trace_cap=0):
+        o = pf_step_opts()
+        o.ssp_stages, o.dt_mult, o.dt0, o.max_stages, o.max_attempts = ssp_stages, dt_mult, dt0, max_stages, max_attempts
+        tr = None
+        if trace_cap:
+            tr = dict(dt=np.zeros(trace_cap), s=np.zeros(trace_cap, np.int32), err=np.zeros(trace_cap),
+                      acc=np.zeros(trace_cap, np.int32), n=C.c_int())
+            o.trace_cap = trace_cap
+            o.trace_dt = tr["dt"].ctypes.data_as(_dp)
+            o.trace_s = tr["s"].ctypes.data_as(_ip)
+            o.trace_err = tr["err"].ctypes.data_as(_dp)
+            o.trace_acc = tr["acc"].ctypes.data_as(_ip)
+            o.trace_len = C.pointer(tr["n"])
+        tl = pf_tol(*tol) if tol is not None else None
+        st = pf_stats()
+        s = _lib().pf_step(self.h, int(integ), float(t_end), C.byref(tl) if tl is not None else None,
+                           C.byref(o), C.byref(st))
+        _check(s, "pf_step")
+        out = st.as_dict()
+        if tr is not None:
+            n = tr["n"].value
+            out["trace"] = dict(dt=tr["dt"][:n].copy(), s=tr["s"][:n].copy(),
+                                err=tr["err"][:n].copy(), acc=tr["acc"][:n].copy())
+        return out
+
+    def profile(self, enable):
+        """Read per-pass event timings accumulated so far, then (enable=1)
+        restart or (enable=0) stop recording; enable=-1 only reads.
+        Returns {kind: (ms, launches)}."""
+        ms = (C.c_double * 8)()
+        n = (C.c_longlong * 8)()
+        _check(_lib().pf_profile(self.h, int(enable), ms, n), "pf_profile")
+        return {k: (ms[i], n[i]) for i, k in enumerate(PASS_KINDS)}
+
+    def launch_count(self):
+        return _lib().pf_launch_count(self.h)
+
+    def reduce(self):
+        m = C.c_double()
+        vol = np.zeros(self.N)
+        alive = C.c_int()
+        _check(_lib().pf_reduce(self.h, C.byref(m), vol.ctypes.data_as(_dp), C.byref(alive)), "pf_reduce")
+        return m.value, vol, alive.value

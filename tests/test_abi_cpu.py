@@ -1,0 +1,53 @@
+"""CPU-only checks of the boundary: the library builds, loads without a GPU and
+exports every entry point that include/pf.h declares; the product package
+does not depend on the oracle."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(pf\w+)\s*\(", src))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2601_16522_gb300 import build
+    lib_path = build.build()
+    lib = ctypes.CDLL(lib_path)
+    names = declared_functions()
+    assert "pf_create" in names and "pf_step" in names and "pf_get_state" in names
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_strerror_without_gpu():
+    from paper_2601_16522_gb300 import pf
+    lib = pf.lib()
+    assert lib.pf_strerror(0) == b"ok"
+    assert b"invalid" in lib.pf_strerror(1)
+
+
+def test_product_does_not_import_oracle():
+    pkg = os.path.join(ROOT, "paper_2601_16522_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(from|import)\s+oracle", txt, re.M), f
+                assert "pf_oracle" not in txt, f
+    for f in os.listdir(os.path.join(ROOT, "oracle")):
+        if f.endswith((".py", ".c", ".h")):
+            txt = open(os.path.join(ROOT, "oracle", f)).read()
+            for m in re.findall(r"^\s*(?:from|import)\s+(paper_2601_16522_gb300[\w.]*)", txt, re.M):
+                assert m == "paper_2601_16522_gb300.inputs", (f, m)
+            assert "pf_kernels" not in txt and "include/pf.h" not in txt, f

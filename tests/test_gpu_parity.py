@@ -1,0 +1,263 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+FP64: every field within 1e-12 relative (max |gpu - oracle| / max |oracle|,
+per field), N_z bit-exact.  FP32: the error against the FP64 oracle is bounded
+by a few FP32 roundings of the field scale.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import ref
+from paper_2601_16522_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+REL64 = 1e-12
+
+
+@pytest.fixture(scope="module")
+def pf():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2601_16522_gb300 import build
+    build.build()
+    from paper_2601_16522_gb300 import pf as pfmod
+    return pfmod
+
+
+def relerr(a, b, N, K):
+    """max over fields of max|a-b| / max|b| (phase fields as one block, c separately)."""
+    out = []
+    blocks = [slice(0, N)] + ([slice(N, N + 1)] if K else [])
+    for s in blocks:
+        scale = np.abs(b[s]).max()
+        d = np.abs(a[s] - b[s]).max()
+        out.append(d / scale if scale > 0 else d)
+    return max(out)
+
+
+def cases():
+    c = []
+    prob, u = I.circle(32, 9.0, W=2.5)
+    c.append(("circle32", prob, u))
+    prob, u = I.multiphase_blobs(17, 13, 1, 5, seed=3, has_conc=1, n_alpha=2)
+    c.append(("blobs2d_K1", prob, u))
+    prob, u = I.multiphase_blobs(19, 11, 1, 3, seed=4, has_conc=1, n_alpha=1,
+                                 bc_phi=(1, 1, 0, 0, 0, 0), bc_c=(2, 1, 0, 0, 0, 0),
+                                 c_dirichlet=(0.7, 0.0, 0, 0, 0, 0))
+    c.append(("blobs2d_bc", prob, u))
+    prob, u = I.multiphase_blobs(9, 7, 6, 4, seed=5, has_conc=1, n_alpha=1)
+    c.append(("blobs3d_K1", prob, u))
+    prob, u = I.multiphase_blobs(10, 9, 7, 6, seed=6, has_conc=0,
+                                 bc_phi=(1, 1, 0, 0, 1, 1))
+    c.append(("blobs3d_neumann", prob, u))
+    prob, u = I.multiphase_blobs(32, 30, 28, 33, seed=8, has_conc=1, n_alpha=3, min_dist=8.0)
+    c.append(("blobs3d_N33", prob, u))
+    prob, u = I.multiphase_blobs(30, 28, 26, 70, seed=9, has_conc=1, n_alpha=5, min_dist=5.0)
+    c.append(("blobs3d_N70", prob, u))
+    prob, u = I.stefan(nx=64, ny=3, h=20.0, W=2.5)
+    c.append(("stefan", prob, u))
+    return c
+
+
+CASES = cases()
+
+
+@pytest.mark.parametrize("name,prob,u", CASES, ids=[c[0] for c in CASES])
+def test_rhs_fp64(pf, name, prob, u):
+    o = ref.Oracle(prob)
+    r_ref, nz_ref = o.rhs(u)
+    with pf.Simulation(prob, precision=64) as sim:
+        sim.set_state(u)
+        r, nz = sim.rhs()
+        back, t = sim.get_state()
+    np.testing.assert_array_equal(back, u)
+    np.testing.assert_array_equal(nz, nz_ref)
+    assert relerr(r, r_ref, prob.n_phases, prob.has_conc) <= REL64
+    assert 2 <= nz_ref.max() <= 12
+
+
+INTEG_CASES = [(pf_i, s, mult) for pf_i, s, mult in [
+    (ref.FEULER, 1, 0.9), (ref.SSP2, 5, 2.0), (ref.SSP104, 10, 3.0), (ref.RKL1, 0, 30.0),
+    (ref.RKL2, 0, 60.0)]]
+
+
+@pytest.mark.parametrize("integ,s,mult", INTEG_CASES, ids=["fe", "ssp2", "ssp104", "rkl1", "rkl2"])
+@pytest.mark.parametrize("name,prob,u", [CASES[0], CASES[1], CASES[3], CASES[5]],
+                         ids=["circle32", "blobs2d_K1", "blobs3d_K1", "blobs3d_N33"])
+def test_single_step_fp64(pf, name, prob, u, integ, s, mult):
+    o = ref.Oracle(prob)
+    dte = o.dt_e()
+    dt = mult * dte
+    if integ in (ref.RKL1, ref.RKL2):
+        s = ref.sts_stages(integ, dt, dte)
+    un_ref, _, _, _ = o.step(integ, dt, s, u)
+    with pf.Simulation(prob, precision=64) as sim:
+        assert sim.dt_e() == pytest.approx(dte, rel=1e-15)
+        sim.set_state(u, 0.0)
+        st = sim.step(integ, dt, dt_mult=mult, ssp_stages=s if integ == ref.SSP2 else 5)
+        un, t = sim.get_state()
+    assert t == dt
+    assert st["steps_accepted"] == 1
+    assert relerr(un, un_ref, prob.n_phases, prob.has_conc) <= REL64
+
+
+@pytest.mark.parametrize("integ", [ref.SSP104, ref.RKL1, ref.RKL2], ids=["ssp104", "rkl1", "rkl2"])
+@pytest.mark.parametrize("name,prob,u", [CASES[1], CASES[3], CASES[7]], ids=["blobs2d_K1", "blobs3d_K1", "stefan"])
+def test_error_norm_fp64(pf, name, prob, u, integ):
+    o = ref.Oracle(prob)
+    tol = (1e-4, 1e-3, 1e-4, 1e-4)
+    dte = o.dt_e()
+    dt0 = 8.0 * dte
+    with pf.Simulation(prob, precision=64) as sim:
+        sim.set_state(u)
+        st = sim.step(integ, 1e9, tol=tol, dt0=dt0, max_attempts=1, trace_cap=4)
+        tr = st["trace"]
+    assert len(tr["dt"]) == 1
+    dt, s = tr["dt"][0], tr["s"][0]
+    assert dt == dt0
+    _, e_ref, _ = o.step_error(integ, dt, s, u, tol)
+    assert tr["err"][0] == pytest.approx(e_ref, rel=1e-12)
+    assert tr["acc"][0] == int(e_ref < 1.0)
+
+
+@pytest.mark.parametrize("integ", [ref.RKL1, ref.RKL2, ref.SSP104], ids=["rkl1", "rkl2", "ssp104"])
+def test_adaptive_trajectory_replay_fp64(pf, integ):
+    # The oracle replays the GPU's attempted (dt, s, accept) sequence, so a
+    # 1-ulp difference in an error norm cannot fork the two runs.
+    prob, u = I.multiphase_blobs(21, 17, 1, 4, seed=11, has_conc=1, n_alpha=1)
+    o = ref.Oracle(prob)
+    t_end = 60.0 * o.dt_e()
+    tol = (1e-4, 1e-3, 1e-4, 1e-4)
+    with pf.Simulation(prob, precision=64) as sim:
+        sim.set_state(u)
+        st = sim.step(integ, t_end, tol=tol, trace_cap=10000)
+        ug, tg = sim.get_state()
+    tr = st["trace"]
+    assert tg == t_end
+    assert st["steps_accepted"] >= 3
+    status, ur, t, trace = o.run(integ, u, 0.0, t_end, tol=tol, replay=(tr["dt"], tr["s"], tr["acc"]),
+                                 trace_cap=10000)
+    assert status == 0 and t == t_end
+    np.testing.assert_allclose(trace["err"], tr["err"], rtol=1e-10, atol=0)
+    assert relerr(ug, ur, prob.n_phases, prob.has_conc) <= REL64
+    assert st["rhs_evals"] == o.stats.rhs_evals
+
+
+def test_fe_trajectory_circle_full(pf):
+    # 128^2 circle, R0 = 40, W = 5/pi, forward Euler at 0.9 dt_e for 2000 steps.
+    prob, u = I.circle(128, 40.0)
+    o = ref.Oracle(prob)
+    dt = 0.9 * o.dt_e()
+    t_end = 2000 * dt
+    st_ref, ur, tr_, _ = o.run(ref.FEULER, u, 0.0, t_end, dt_mult=0.9)
+    with pf.Simulation(prob, precision=64) as sim:
+        sim.set_state(u)
+        st = sim.step(ref.FEULER, t_end, dt_mult=0.9)
+        ug, tg, nz = sim.get_state(with_nz=True)
+    assert st["steps_accepted"] == 2000 and tg == t_end
+    assert relerr(ug, ur, 2, 0) <= REL64
+    _, nz_ref = o.rhs(ur)
+    np.testing.assert_array_equal(nz, nz_ref)
+
+
+@pytest.mark.parametrize("name,prob,u", [CASES[1], CASES[3], CASES[6]], ids=["blobs2d_K1", "blobs3d_K1", "N70"])
+def test_reduce_fp64(pf, name, prob, u):
+    o = ref.Oracle(prob)
+    m_ref, vol_ref, alive_ref = o.reduce(u)
+    with pf.Simulation(prob, precision=64) as sim:
+        sim.set_state(u)
+        m, vol, alive = sim.reduce()
+    assert m == pytest.approx(m_ref, rel=1e-12)
+    np.testing.assert_allclose(vol, vol_ref, rtol=1e-12)
+    assert alive == alive_ref
+
+
+@pytest.mark.parametrize("name,prob,u", [CASES[0], CASES[1], CASES[3], CASES[5], CASES[6]],
+                         ids=["circle32", "blobs2d_K1", "blobs3d_K1", "N33", "N70"])
+def test_rhs_fp32(pf, name, prob, u):
+    o = ref.Oracle(prob)
+    r_ref, nz_ref = o.rhs(u)
+    with pf.Simulation(prob, precision=32) as sim:
+        sim.set_state(u)
+        r, nz = sim.rhs()
+    # FP32 storage rounds the inputs to 2^-24 relative; the chemical potential
+    # mu = (c - sum phi c0) / (sum phi / k) sums up to N terms and cancels
+    # O(1) values down to O(1e-2), and the flux takes differences of mu, which
+    # together amplify that rounding by up to ~1e4 relative to the RHS scale:
+    # bound 1e-3, still an order below the O(1e-2) discretisation error.
+    assert relerr(r, r_ref, prob.n_phases, prob.has_conc) < 1e-3
+    assert (nz != nz_ref).mean() < 0.02
+
+
+def test_fp32_trajectory_error_below_discretisation(pf):
+    # FP32 forward Euler on the circle: deviation from the FP64 oracle is far
+    # below the O(1e-2) error against the sharp-interface law (Sec. 5.2.1).
+    prob, u = I.circle(64, 20.0, W=2.5)
+    o = ref.Oracle(prob)
+    dt = 0.9 * o.dt_e()
+    t_end = 300 * dt
+    _, ur, _, _ = o.run(ref.FEULER, u, 0.0, t_end, dt_mult=0.9)
+    with pf.Simulation(prob, precision=32) as sim:
+        sim.set_state(u)
+        sim.step(ref.FEULER, t_end, dt_mult=0.9)
+        ug, _ = sim.get_state()
+    area_ref = ur[1].sum()
+    area = ug[1].sum()
+    assert abs(area - area_ref) / area_ref < 1e-4
+    assert np.abs(ug - ur).max() < 1e-4
+
+
+def test_status_codes(pf):
+    prob, u = I.circle(16, 4.0, W=1.5)
+    with pf.Simulation(prob, precision=64) as sim:
+        with pytest.raises(pf.PfError) as e:
+            sim.step(ref.FEULER, 1.0, dt_mult=0.5)
+        assert e.value.status == pf.PF_ESTATE
+        sim.set_state(u)
+        with pytest.raises(pf.PfError) as e:
+            sim.step(ref.FEULER, 1.0, tol=(1e-4,) * 4)      # FE has no adaptive mode
+        assert e.value.status == pf.PF_EINVAL
+        with pytest.raises(pf.PfError) as e:
+            sim.step(ref.RKL2, -1.0, tol=(1e-4,) * 4)        # t_end before t
+        assert e.value.status == pf.PF_EINVAL
+    bad = prob.with_(bc_phi=(0, 1, 0, 0, 0, 0))          # periodic face opposite a Neumann face
+    with pytest.raises(pf.PfError) as e:
+        pf.Simulation(bad)
+    assert e.value.status == pf.PF_EINVAL
+
+
+def test_active_list_overflow_is_reported(pf):
+    # More than 12 nontrivial phases in one cell exceeds the kernel's per-cell
+    # list (the paper's own per-cell capacity is N_p = 12): PF_EINVAL, no
+    # silent truncation.
+    prob, u = I.multiphase_blobs(9, 9, 8, 40, seed=9, has_conc=0, min_dist=1.5)
+    _, nz_ref = ref.Oracle(prob).rhs(u)
+    assert nz_ref.max() > 12
+    with pf.Simulation(prob, precision=64) as sim:
+        sim.set_state(u)
+        with pytest.raises(pf.PfError) as e:
+            sim.rhs()
+        assert e.value.status == pf.PF_EINVAL
+        with pytest.raises(pf.PfError) as e:
+            sim.step(ref.FEULER, sim.dt_e(), dt_mult=1.0)
+        assert e.value.status == pf.PF_EINVAL
+
+
+def test_bulk_state_is_stationary(pf):
+    # Degenerate case: every cell bulk (one phase = 1): N_z = 0, RHS = 0 and
+    # every integrator leaves the state unchanged.
+    prob, _ = I.multiphase_blobs(8, 8, 4, 3, seed=1)
+    u = np.zeros((3, prob.V))
+    u[1] = 1.0
+    with pf.Simulation(prob, precision=64) as sim:
+        sim.set_state(u)
+        r, nz = sim.rhs()
+        assert np.all(r == 0) and np.all(nz == 0)
+        for integ in (ref.FEULER, ref.RKL2):
+            sim.step(integ, sim.dt_e() * 5 + (0 if integ == ref.FEULER else 10), dt_mult=1.0)
+        ug, _ = sim.get_state()
+    np.testing.assert_array_equal(ug, u)
