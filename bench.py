@@ -198,7 +198,8 @@ def run_ours(args, world, rank, local):
     stream = torch.cuda.Stream(device=dev)
     prob, u, prec = workload_problem(args.workload, dev)
     V, N = prob.V, prob.n_phases
-    sim = pf.Simulation(prob, precision=prec, stream=stream)
+    sim = pf.Simulation(prob, precision=prec, stream=stream,
+                        options=pf.Simulation.OPT_TMA if args.tma else 0)
     torch.cuda.synchronize()
     sim.set_state(u)
     torch.cuda.synchronize()
@@ -318,6 +319,7 @@ def main():
     ap.add_argument("--workload", default="grains256")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tma", action="store_true", help="TMA-staged kernels instead of plain loads")
     args = ap.parse_args()
     world, rank, local = dist_setup(args)
     if args.impl == "reference":

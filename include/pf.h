@@ -75,7 +75,16 @@ typedef struct {
     double c_dirichlet[6];    /* Dirichlet value of c per face */
     int precision;            /* 64: FP64 storage and arithmetic; 32: FP32 storage and stencil
                                  arithmetic, FP64 time, coefficients and reductions */
+    int options;              /* bit set of PF_OPT_* (0: defaults) */
 } pf_params;
+
+/* pf_params.options: PF_OPT_TMA runs the FP32 3D passes (5..32 phases, nx a
+   multiple of 32, ny a multiple of 8) through the warp-specialised kernel
+   that streams phase planes into shared memory with TMA bulk tensor copies
+   instead of the plain-load kernel.  Results are bit-identical; which is
+   faster depends on the problem (on the 256^3, 32-phase grain workload the
+   plain-load kernel is). */
+enum { PF_OPT_TMA = 1 };
 
 /* Error tolerances of the weighted norm (Eq. error_norm): relative r and
    absolute a per field (phase field, concentration). */

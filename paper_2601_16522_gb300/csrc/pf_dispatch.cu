@@ -4,33 +4,33 @@
 namespace pfk {
 
 int launch_f64(const Geom &, const Pass<double> &, unsigned, cudaStream_t, const double *, const double *,
-               const double *, const signed char *, bool *);
+               const double *, const signed char *, const TmaMaps *, bool *);
 int launch_f32k0(const Geom &, const Pass<float> &, unsigned, cudaStream_t, const float *, const float *,
-                 const float *, const signed char *, bool *);
+                 const float *, const signed char *, const TmaMaps *, bool *);
 int launch_f32k1(const Geom &, const Pass<float> &, unsigned, cudaStream_t, const float *, const float *,
-                 const float *, const signed char *, bool *);
+                 const float *, const signed char *, const TmaMaps *, bool *);
 int prepare_f64();
 int prepare_f32k0();
 int prepare_f32k1();
 
 template <>
 int launch_stage<double>(const Geom &g, const Pass<double> &P, cudaStream_t st, const double *A, const double *B,
-                         const double *L, const signed char *ptype)
+                         const double *L, const signed char *ptype, const TmaMaps *)
 {
     bool done = false;
     // FP64 runs every pass through the generic instantiation
-    int e = launch_f64(g, P, SIG_GENERIC, st, A, B, L, ptype, &done);
+    int e = launch_f64(g, P, SIG_GENERIC, st, A, B, L, ptype, nullptr, &done);
     return done ? e : (int)cudaErrorInvalidValue;
 }
 
 template <>
 int launch_stage<float>(const Geom &g, const Pass<float> &P, cudaStream_t st, const float *A, const float *B,
-                        const float *L, const signed char *ptype)
+                        const float *L, const signed char *ptype, const TmaMaps *tma)
 {
     bool done = false;
     auto go = [&](unsigned sig) {
-        return g.K ? launch_f32k1(g, P, sig, st, A, B, L, ptype, &done)
-                   : launch_f32k0(g, P, sig, st, A, B, L, ptype, &done);
+        return g.K ? launch_f32k1(g, P, sig, st, A, B, L, ptype, tma, &done)
+                   : launch_f32k0(g, P, sig, st, A, B, L, ptype, tma, &done);
     };
     int e = go(pass_signature(P));
     if (!done) e = go(SIG_GENERIC);

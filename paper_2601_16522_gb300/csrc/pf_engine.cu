@@ -5,6 +5,8 @@
 // Sec. 3.2 of Seiz & Takaki (arXiv 2601.16522), the error estimate and norm of
 // Sec. 3.3 (deterministic two-level FP64 reduction) and the PID controller
 // with bias.  Only scalars cross the host/device boundary per adaptive step.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -139,6 +141,8 @@ struct pf_handle {
     int *dflag = nullptr;
     double *tot_sum = nullptr, *tot_max = nullptr;
     int tot_blocks = 0;
+    bool tma = false;                  // TMA-staged FP32 kernels usable
+    CUtensorMap m3[NBUF], m1[NBUF];    // per buffer: 3-plane and 1-plane boxes
     double t = 0.0;
     bool has_state = false;
     double dte = 0.0;
@@ -161,6 +165,36 @@ struct pf_handle {
 namespace {
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? PF_OK : PF_EDEVICE; }
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no -lcuda).
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+// 4D map (x, y, z, field) of one FP32 state buffer with a 32 x 8 x boxz x 1 box.
+bool make_map(CUtensorMap *m, void *base, const pfk::Geom &g, int boxz)
+{
+    auto enc = encode_fn();
+    if (!enc) return false;
+    const cuuint64_t dims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz, (cuuint64_t)g.NF};
+    const cuuint64_t strides[3] = {(cuuint64_t)g.nx * 4, (cuuint64_t)g.nx * g.ny * 4, (cuuint64_t)g.Vs * 4};
+    const cuuint32_t box[4] = {(cuuint32_t)pfk::TX, (cuuint32_t)pfk::TY, (cuuint32_t)boxz, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 void *vec(pf_handle *h, int k) { return h->buf[k]; }
 
@@ -198,13 +232,33 @@ int prof_end(pf_handle *h)
     return PF_OK;
 }
 
+int buf_index(const pf_handle *h, const void *p)
+{
+    for (int k = 0; k < NBUF; ++k) if (h->buf[k] == p) return k;
+    return -1;
+}
+
 template <typename T>
 int run_pass(pf_handle *h, const Pass<T> &P)
 {
     int st = prof_begin(h);
     if (st) return st;
+    pfk::TmaMaps tm;
+    const pfk::TmaMaps *tmp = nullptr;
+    if (h->tma && P.mode != pfk::MODE_RHS) {
+        const int ki = buf_index(h, P.in), k0 = P.p0 ? buf_index(h, P.p0) : 0, k2 = P.p2 ? buf_index(h, P.p2) : 0,
+                  kr = P.r0in ? buf_index(h, P.r0in) : 0;
+        if (ki >= 0 && k0 >= 0 && k2 >= 0 && kr >= 0) {
+            tm.in3 = h->m3[ki];
+            tm.in1 = h->m1[ki];
+            tm.p0 = h->m1[k0];
+            tm.p2 = h->m1[k2];
+            tm.r0 = h->m1[kr];
+            tmp = &tm;
+        }
+    }
     int e = pfk::launch_stage<T>(h->g, P, h->stream, (const T *)h->dA, (const T *)h->dB, (const T *)h->dL,
-                                 h->dptype);
+                                 h->dptype, tmp);
     h->launches++;
     if (e != 0) return PF_EDEVICE;
     return prof_end(h);
@@ -520,6 +574,7 @@ int do_step(pf_handle *h, int integ, double dt, int s, const pf_tol *tol, bool w
 int flag_status(int flag)
 {
     if (flag & pfk::FLAG_NZ_OVERFLOW) return PF_EINVAL;
+    if (flag & pfk::FLAG_TIMEOUT) return PF_ETIMEOUT;
     return PF_EUNSTABLE;
 }
 
@@ -835,6 +890,14 @@ int pf_create(const pf_params *p, void *cuda_stream, pf_handle **out)
     st |= cudaMemcpy(h->dptype, pt.data(), N, cudaMemcpyHostToDevice);
     st |= cudaMemset(h->dflag, 0, sizeof(int));
     if (st != 0) { free_all(h); delete h; return PF_EDEVICE; }
+    // TMA-staged FP32 kernels: full 32 x 8 tiles, 3D, 5..32 phases
+    if (h->prec == 32 && p->dim == 3 && N > 4 && N <= 32 && p->nx % pfk::TX == 0 && p->ny % pfk::TY == 0 &&
+        p->nz >= 3 && (p->options & PF_OPT_TMA) && h->Vs * (long long)NP < 0x7fffffffLL) {
+        bool ok = true;
+        for (int k = 0; k < NBUF && ok; ++k)
+            ok = make_map(&h->m3[k], h->buf[k], g, 3) && make_map(&h->m1[k], h->buf[k], g, 1);
+        h->tma = ok;
+    }
     *out = h;
     return PF_OK;
 }

@@ -22,6 +22,7 @@
 // (which inputs and outputs they use); everything else takes the generic
 // instantiation that reads the options at run time.
 #pragma once
+#include <cuda.h>            // CUtensorMap (type only)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -110,8 +111,9 @@ __device__ __forceinline__ void face_offsets(const Geom &g, int x, int y, int z,
 // Fixed-order block reduction of (sum, count) into the per-block partials.
 __device__ __forceinline__ void block_partials(double esum, long long ecnt, double *ps, long long *pc, int bid)
 {
-    __shared__ double rs_sum[BLOCK / 32];
-    __shared__ long long rs_cnt[BLOCK / 32];
+    constexpr int MAXW = 16;                 // blocks of up to 512 threads
+    __shared__ double rs_sum[MAXW];
+    __shared__ long long rs_cnt[MAXW];
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) {
         esum += __shfl_xor_sync(0xffffffffu, esum, o);
@@ -123,7 +125,7 @@ __device__ __forceinline__ void block_partials(double esum, long long ecnt, doub
     if (threadIdx.x == 0) {
         double s = 0.0;
         long long c = 0;
-        for (int w = 0; w < BLOCK / 32; ++w) { s += rs_sum[w]; c += rs_cnt[w]; }
+        for (int w = 0; w < (int)(blockDim.x / 32); ++w) { s += rs_sum[w]; c += rs_cnt[w]; }
         ps[bid] = s;
         pc[bid] = c;
     }
@@ -479,6 +481,88 @@ cell_kernel(const Geom g, const Pass<T> P, const T *__restrict__ tabA, const T *
     if (mode == MODE_ERR || emb) block_partials(esum, ecnt, P.part_sum, P.part_cnt, bid);
 }
 
+// ---------------------------------------------------------------------------
+// TMA staging (sm_90+ bulk tensor copies, used on sm_103a): a block streams
+// the phase planes of its 32x8 tile through a ring of TMA_R shared-memory
+// slots.  Slot r holds, for one phase, the stencil input's planes z-1, z, z+1
+// (one 4D box of 32x8x3 cells) and the pointwise inputs' plane z, and is
+// signalled by an mbarrier with a transaction count.  Every wait is bounded.
+// ---------------------------------------------------------------------------
+constexpr int TMA_R = 4;
+constexpr unsigned TMA_SPIN = 1u << 22;   // bounded mbarrier polls before giving up
+enum { FLAG_TIMEOUT = 4 };
+
+struct TmaMaps {
+    CUtensorMap in3;   // stencil input, box 32 x 8 x 3 planes x 1 field
+    CUtensorMap in1;   // stencil input, box 32 x 8 x 1 (domain z faces)
+    CUtensorMap p0, p2, r0;   // pointwise inputs, box 32 x 8 x 1 x 1
+};
+
+template <typename T>
+struct ListSmem;
+
+struct alignas(1024) TmaSmem {
+    float in[TMA_R][3][TY][TX];
+    float p0[TMA_R][TY][TX];
+    float p2[TMA_R][TY][TX];
+    float r0[TMA_R][TY][TX];
+    unsigned long long full[TMA_R];    // copies of the slot landed (tx count)
+    unsigned long long empty[TMA_R];   // every consumer warp has read the slot
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *b, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *b, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned long long *b)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *b, unsigned parity)
+{
+    unsigned ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok)
+                 : "r"(smem_u32(b)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: false after TMA_SPIN polls (the caller raises FLAG_TIMEOUT).
+__device__ __forceinline__ bool mbar_wait(unsigned long long *b, unsigned parity)
+{
+    for (unsigned k = 0; k < TMA_SPIN; ++k)
+        if (mbar_try_wait(b, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void tma_load4(void *dst, const CUtensorMap *m, int x, int y, int z, int f,
+                                          unsigned long long *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
+        ::"r"(smem_u32(dst)), "l"((unsigned long long)m), "r"(x), "r"(y), "r"(z), "r"(f), "r"(smem_u32(bar))
+        : "memory");
+}
+
 // Shared-memory slots of the per-cell active list (no stage values).
 template <typename T>
 struct ListSmem {
@@ -488,17 +572,73 @@ struct ListSmem {
     T dl[MAXACT][BLOCK];     // variational derivative
 };
 
-// FP32 fast path for N <= NMAX phases and the specialised signatures.  The
-// loop over phases is unrolled NMAX times (guarded by a < N) so the stage
-// values stay in registers and every load of a phase (stencil and pointwise)
-// is issued together; a phase that is not nontrivial has a zero RHS, so its
-// stage value (or error term) is final in that first loop.  Only the N_z
-// listed phases receive their RHS term after the pairwise sums.  Rounding
-// order differs from the generic kernel; FP32 is not compared bit for bit.
-template <int DIM, int KC, unsigned SIG, int NMAX>
-__global__ void __launch_bounds__(BLOCK, 4)
-fast_kernel(const Geom g, const Pass<float> P, const float *__restrict__ tabA, const float *__restrict__ tabB,
-            const float *__restrict__ tabL, const signed char *__restrict__ ptype)
+// Loader policies of the FP32 fast path: where the values of phase a come
+// from.  PlainLoader reads global memory; TmaLoader reads the shared-memory
+// ring filled by the producer warp (and releases the slot afterwards).
+template <int DIM>
+struct PlainLoader {
+    // per-phase base pointers are the same for every thread (uniform); the
+    // per-thread part is a 32-bit cell index (the fast path needs NF*Vs < 2^31)
+    const float *in, *p0, *p2, *r0;
+    int Vs;
+    int ic, inb[6];
+    __device__ __forceinline__ void load(int a, long long, float &v0, float *nb, float &p0v, float &p2v, float &r0v,
+                                         bool hp0, bool hp2, bool hr0)
+    {
+        const float *b = in + (long long)a * Vs;
+        v0 = ldg(b + ic);
+#pragma unroll
+        for (int f = 0; f < 2 * DIM; ++f) nb[f] = ldg(b + inb[f]);
+        if (hp0) p0v = ldg(p0 + (long long)a * Vs + ic);
+        if (hp2) p2v = ldg(p2 + (long long)a * Vs + ic);
+        if (hr0) r0v = ldg(r0 + (long long)a * Vs + ic);
+    }
+    __device__ __forceinline__ void release(int) {}
+};
+
+struct TmaLoader {
+    TmaSmem *Q;
+    const float *pin;
+    int off[6];
+    int tx, ty;
+    bool zin;
+    bool ok;
+    __device__ __forceinline__ void load(int a, long long fo, float &v0, float *nb, float &p0v, float &p2v, float &r0v,
+                                         bool hp0, bool hp2, bool hr0)
+    {
+        const int r = a % TMA_R;
+        if (!mbar_wait(&Q->full[r], (unsigned)((a / TMA_R) & 1))) ok = false;
+        v0 = Q->in[r][1][ty][tx];
+        nb[0] = tx > 0 ? Q->in[r][1][ty][tx - 1] : ldg(pin + fo + off[0]);
+        nb[1] = tx < TX - 1 ? Q->in[r][1][ty][tx + 1] : ldg(pin + fo + off[1]);
+        nb[2] = ty > 0 ? Q->in[r][1][ty - 1][tx] : ldg(pin + fo + off[2]);
+        nb[3] = ty < TY - 1 ? Q->in[r][1][ty + 1][tx] : ldg(pin + fo + off[3]);
+        nb[4] = zin ? Q->in[r][0][ty][tx] : ldg(pin + fo + off[4]);
+        nb[5] = zin ? Q->in[r][2][ty][tx] : ldg(pin + fo + off[5]);
+        if (hp0) p0v = Q->p0[r][ty][tx];
+        if (hp2) p2v = Q->p2[r][ty][tx];
+        if (hr0) r0v = Q->r0[r][ty][tx];
+    }
+    // one arrival per consumer warp once all its lanes have read slot a
+    __device__ __forceinline__ void release(int a)
+    {
+        __syncwarp();
+        if ((threadIdx.x & 31) == 0) mbar_arrive(&Q->empty[a % TMA_R]);
+    }
+};
+
+// Per-cell body of the FP32 fast path (N <= NMAX).  The loop over phases is
+// unrolled NMAX times (guarded by a < N) so the stage values stay in
+// registers and the loads of a phase (stencil and pointwise) issue together.
+// A phase that is not nontrivial has a zero RHS, so its stage value (or error
+// term) is final in that first loop; only the N_z listed phases receive their
+// RHS term after the pairwise sums.  Rounding order differs from the generic
+// kernel; FP32 is not compared bit for bit.
+template <int DIM, int KC, unsigned SIG, int NMAX, class LD>
+__device__ __forceinline__ void fast_cell(const Geom &g, const Pass<float> &P, LD &ld, ListSmem<float> &S, int tid,
+                                          long long i, const int *off, const int *ghost, const float *tabA,
+                                          const float *tabB, const float *tabL, const signed char *ptype,
+                                          double &esum, long long &ecnt)
 {
     typedef float T;
     constexpr int NFACE = 2 * DIM;
@@ -508,260 +648,345 @@ fast_kernel(const Geom g, const Pass<float> P, const float *__restrict__ tabA, c
     constexpr bool HR0 = (SIG & SIG_R0IN) != 0 || ERR;
     constexpr bool R0OUT = (SIG & SIG_R0OUT) != 0;
     constexpr bool PROJ = (SIG & SIG_PROJECT) != 0;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    ListSmem<T> &S = *reinterpret_cast<ListSmem<T> *>(smem_raw);
-    const int tid = threadIdx.x;
     const int N = g.N;
     const int Vs = (int)g.Vs;
+    const int i32 = (int)i;
+    const T idx2 = (T)(1.0 / g.dx2);
+    const T a0c = (T)P.a0, a1c = (T)P.a1, a2c = (T)P.a2, b1c = (T)P.b1, b0c = (T)P.b0;
+    const T dt = (T)P.dt, rph = (T)P.r_phi, aph = (T)P.a_phi;
+
+    // concentration
+    T cc = (T)0, num_c = (T)0, den_c = (T)0, num_n[NFACE], den_n[NFACE], mf[NFACE];
+#pragma unroll
+    for (int f = 0; f < NFACE; ++f) { num_n[f] = (T)0; den_n[f] = (T)0; mf[f] = (T)0; }
+    if (KC) {
+        const T *cf = P.in + (long long)N * Vs + i;
+        cc = ldg(cf);
+        num_c = cc;
+#pragma unroll
+        for (int f = 0; f < NFACE; ++f) {
+            T v = ldg(cf + off[f]);
+            if (ghost[f] && g.bc_c[f] == BC_DIRICHLET) v = (T)2 * (T)g.cdir[f] - cc;
+            num_n[f] = v;
+        }
+    }
+
+    int nz = 0, nc = 0;
+    bool changed = false;
+    T best = (T)-1, ssum = (T)0;
+    int bestid = -1;
+    T nv[NMAX];
+    unsigned actmask = 0u;
+#pragma unroll
+    for (int a = 0; a < NMAX; ++a) {
+        nv[a] = (T)0;
+        if (a < N) {
+            const long long fo = (long long)a * Vs;
+            T v0, nb[NFACE], p0v = (T)0, p2v = (T)0, r0v = (T)0;
+            ld.load(a, fo, v0, nb, p0v, p2v, r0v, HP0, HP2, HR0);
+            ld.release(a);
+            T mx = v0, mn = v0;
+#pragma unroll
+            for (int f = 0; f < NFACE; ++f) {
+                mx = fmaxf(mx, nb[f]);
+                mn = fminf(mn, nb[f]);
+            }
+            if (KC) {
+                const int t = ptype[a];
+                const T c0t = (T)g.c0[t], ikt = (T)g.invk[t], dkt = (T)g.Dk[t];
+                num_c = num_c - v0 * c0t;
+                den_c = den_c + v0 * ikt;
+#pragma unroll
+                for (int f = 0; f < NFACE; ++f) {
+                    num_n[f] = num_n[f] - nb[f] * c0t;
+                    den_n[f] = den_n[f] + nb[f] * ikt;
+                    mf[f] = mf[f] + dkt * ((T)0.5 * (v0 + nb[f]));
+                }
+            }
+            const bool act = mx > (T)0 && mn < (T)1;
+            if (act) {
+                T l = (T)0;
+#pragma unroll
+                for (int f = 0; f < NFACE; ++f) l = l + (nb[f] - v0);
+                if (nz < MAXACT) {
+                    S.id[nz][tid] = (unsigned char)a;
+                    S.lap[nz][tid] = l * idx2;
+                    S.cen[nz][tid] = v0;
+                    actmask |= 1u << a;
+                }
+                nz++;
+            }
+            if (ERR) {
+                // in = u^{n+1}, p0 = u^n, r0in = F^n; a trivial phase has F^{n+1} = 0
+                if (!act) {
+                    T e = ((T)12 * (p0v - v0) + ((T)6 * dt) * r0v) * ((T)1 / (T)15);
+                    const T trial = p0v + (dt * (T)0.5) * r0v;
+                    if (trial < (T)0 || trial > (T)1) e = (T)0;
+                    if (e != (T)0) {
+                        const T w = rph * fmaxf(fabsf(p0v), fabsf(v0)) + aph;
+                        const T q = e / w;
+                        esum += (double)(q * q);
+                        nc++;
+                    }
+                }
+            } else {
+                T acc = HP0 ? a0c * p0v + a1c * v0 : a1c * v0;
+                if (HP2) acc = acc + a2c * p2v;
+                if (HR0) acc = acc + b0c * r0v;
+                if (!act && PROJ) {
+                    if (acc < (T)0) { acc = (T)0; changed = true; }
+                    if (acc >= (T)1 && acc > best) { best = acc; bestid = a; }
+                    ssum = ssum + acc;
+                }
+                nv[a] = acc;
+            }
+        }
+    }
+    if (nz > MAXACT) {
+        atomicOr(P.flag, FLAG_NZ_OVERFLOW);
+        nz = MAXACT;
+    }
+
+    T mu = (T)0, rc = (T)0;
+    if (KC) {
+        mu = num_c / den_c;
+        T acc = (T)0;
+#pragma unroll
+        for (int f = 0; f < NFACE; ++f) acc = acc + mf[f] * (num_n[f] / den_n[f] - mu);
+        rc = acc * idx2;
+    }
+    // variational derivative and pairwise sum over the listed phases
+    for (int k = 0; k < nz; ++k) {
+        const int a = S.id[k][tid];
+        const T *Aa = tabA + a * N, *Ba = tabB + a * N;
+        T d = (T)0;
+        for (int k2 = 0; k2 < nz; ++k2) {
+            if (k2 == k) continue;
+            const int b = S.id[k2][tid];
+            d = d + (ldg(Aa + b) * S.lap[k2][tid] + ldg(Ba + b) * S.cen[k2][tid]);
+        }
+        if (KC) {
+            const int t = ptype[a];
+            d = d + (-(mu * mu) / ((T)2 * (T)g.k[t]) - mu * (T)g.c0[t]);
+        }
+        S.dl[k][tid] = d;
+    }
+    const T inz = nz > 1 ? (T)1 / (T)nz : (T)0;
+    for (int k = 0; k < nz; ++k) {
+        T rk = (T)0;
+        if (nz > 1) {
+            const int a = S.id[k][tid];
+            const T *La = tabL + a * N;
+            const T dk = S.dl[k][tid];
+            T s = (T)0;
+            for (int k2 = 0; k2 < nz; ++k2) {
+                if (k2 == k) continue;
+                s = s + ldg(La + S.id[k2][tid]) * (dk - S.dl[k2][tid]);
+            }
+            rk = -(s * inz);
+        }
+        S.lap[k][tid] = rk;                 // the list now holds the RHS
+        if (ERR) {
+            const int a = S.id[k][tid];
+            const long long fo = (long long)a * Vs;
+            const T p0v = ldg(P.p0 + fo + i), v0 = S.cen[k][tid], r0v = ldg(P.r0in + fo + i);
+            const T sr = r0v + rk;
+            T e = ((T)12 * (p0v - v0) + ((T)6 * dt) * sr) * ((T)1 / (T)15);
+            const T trial = p0v + (dt * (T)0.5) * sr;
+            if (trial < (T)0 || trial > (T)1) e = (T)0;
+            if (e != (T)0) {
+                const T w = rph * fmaxf(fabsf(p0v), fabsf(v0)) + aph;
+                const T q = e / w;
+                esum += (double)(q * q);
+                nc++;
+            }
+        }
+    }
+    if (ERR) {
+        ecnt += (nc > 0 ? nc : 2);
+        if (KC) {
+            const long long o = (long long)N * Vs + i;
+            const T un = ldg(P.p0 + o), un1 = cc, rn = ldg(P.r0in + o);
+            const T e = ((T)12 * (un - un1) + ((T)6 * dt) * (rn + rc)) * ((T)1 / (T)15);
+            const T w = (T)P.r_c * fmaxf(fabsf(un), fabsf(un1)) + (T)P.a_c;
+            const T q = e / w;
+            esum += (double)(q * q);
+            ecnt += 1;
+        }
+        return;
+    }
+    // listed phases: add the RHS term, clamp, >= 1 candidates, sum
+    T rr[R0OUT ? NMAX : 1];
+    {
+        int kk = 0;
+#pragma unroll
+        for (int a = 0; a < NMAX; ++a) {
+            if (R0OUT) rr[a] = (T)0;
+            if ((actmask >> a) & 1u) {
+                const T rk = S.lap[kk][tid];
+                kk++;
+                if (R0OUT) rr[a] = rk;
+                T acc = nv[a] + b1c * rk;
+                if (PROJ) {
+                    if (acc < (T)0) { acc = (T)0; changed = true; }
+                    if (acc >= (T)1 && (acc > best || (acc == best && a < bestid))) { best = acc; bestid = a; }
+                    ssum = ssum + acc;
+                }
+                nv[a] = acc;
+            }
+        }
+    }
+    if (PROJ) {
+        if (bestid >= 0) {
+#pragma unroll
+            for (int a = 0; a < NMAX; ++a)
+                if (a < N && nv[a] != ((a == bestid) ? (T)1 : (T)0)) changed = true;
+            ssum = (T)1;
+        }
+        if (!(ssum > (T)0)) atomicOr(P.flag, FLAG_SIMPLEX);
+    }
+    const T inv = (ssum > (T)0) ? (T)1 / ssum : (T)1;
+    const bool fix = R0OUT && P.fix_first && changed;
+#pragma unroll
+    for (int a = 0; a < NMAX; ++a) {
+        if (a < N) {
+            const long long fo = (long long)a * Vs;
+            T w = nv[a];
+            if (PROJ) w = (bestid >= 0) ? ((a == bestid) ? (T)1 : (T)0) : w * inv;
+            if (R0OUT) {
+                T r = rr[R0OUT ? a : 0];
+                if (fix) r = (w - ldg(P.in + fo + i)) / b1c;
+                (P.r0out + fo)[i32] = r;
+            }
+            (P.out + fo)[i32] = w;
+        }
+    }
+    if (KC) {
+        const long long o = (long long)N * Vs + i;
+        T acc = HP0 ? a0c * ldg(P.p0 + o) + a1c * cc : a1c * cc;
+        if (HP2) acc = acc + a2c * ldg(P.p2 + o);
+        acc = acc + b1c * rc;
+        if (HR0) acc = acc + b0c * ldg(P.r0in + o);
+        if (R0OUT) P.r0out[o] = rc;
+        P.out[o] = acc;
+    }
+}
+
+// FP32 fast path with plain global loads (any grid, 2D or 3D).
+template <int DIM, int KC, unsigned SIG, int NMAX>
+__global__ void __launch_bounds__(BLOCK, 4)
+fast_kernel(const Geom g, const Pass<float> P, const float *__restrict__ tabA, const float *__restrict__ tabB,
+            const float *__restrict__ tabL, const signed char *__restrict__ ptype)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ListSmem<float> &S = *reinterpret_cast<ListSmem<float> *>(smem_raw);
+    const int tid = threadIdx.x;
     const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
     const int x = blockIdx.x * TX + (tid % TX);
     const int y = blockIdx.y * TY + (tid / TX);
     const int z = blockIdx.z;
-    const bool valid = x < g.nx && y < g.ny;
-    const long long i = valid ? ((long long)z * g.ny + y) * g.nx + x : 0;
-    const T idx2 = (T)(1.0 / g.dx2);
     double esum = 0.0;
     long long ecnt = 0;
-
-    if (valid) {
+    if (x < g.nx && y < g.ny) {
+        const long long i = ((long long)z * g.ny + y) * g.nx + x;
         long long off64[6];
         int ghost[6];
         face_offsets(g, x, y, z, off64, ghost);
+        PlainLoader<DIM> ld;
         int off[6];
 #pragma unroll
-        for (int f = 0; f < 6; ++f) off[f] = ghost[f] ? 0 : (int)off64[f];
-
-        const T a0c = (T)P.a0, a1c = (T)P.a1, a2c = (T)P.a2, b1c = (T)P.b1, b0c = (T)P.b0;
-        const T dt = (T)P.dt, rph = (T)P.r_phi, aph = (T)P.a_phi;
-        const T *pin = P.in + i;
-        const T *pp0 = HP0 ? P.p0 + i : nullptr;
-        const T *pp2 = HP2 ? P.p2 + i : nullptr;
-        const T *pr0 = HR0 ? P.r0in + i : nullptr;
-
-        // concentration
-        T cc = (T)0, num_c = (T)0, den_c = (T)0, num_n[NFACE], den_n[NFACE], mf[NFACE];
-#pragma unroll
-        for (int f = 0; f < NFACE; ++f) { num_n[f] = (T)0; den_n[f] = (T)0; mf[f] = (T)0; }
-        if (KC) {
-            const T *cf = pin + (long long)N * Vs;
-            cc = ldg(cf);
-            num_c = cc;
-#pragma unroll
-            for (int f = 0; f < NFACE; ++f) {
-                T v = ldg(cf + off[f]);
-                if (ghost[f] && g.bc_c[f] == BC_DIRICHLET) v = (T)2 * (T)g.cdir[f] - cc;
-                num_n[f] = v;
-            }
+        for (int f = 0; f < 6; ++f) {
+            off[f] = ghost[f] ? 0 : (int)off64[f];
+            ld.inb[f] = (int)i + off[f];
         }
-
-        int nz = 0, nc = 0;
-        bool changed = false;
-        T best = (T)-1, ssum = (T)0;
-        int bestid = -1;
-        T nv[NMAX];
-        unsigned actmask = 0u;
-#pragma unroll
-        for (int a = 0; a < NMAX; ++a) {
-            nv[a] = (T)0;
-            if (a < N) {
-                const long long fo = (long long)a * Vs;
-                const T v0 = ldg(pin + fo);
-                T nb[NFACE];
-#pragma unroll
-                for (int f = 0; f < NFACE; ++f) nb[f] = ldg(pin + fo + off[f]);
-                const T p0v = HP0 ? ldg(pp0 + fo) : (T)0;
-                const T p2v = HP2 ? ldg(pp2 + fo) : (T)0;
-                const T r0v = HR0 ? ldg(pr0 + fo) : (T)0;
-                T mx = v0, mn = v0;
-#pragma unroll
-                for (int f = 0; f < NFACE; ++f) {
-                    mx = fmaxf(mx, nb[f]);
-                    mn = fminf(mn, nb[f]);
-                }
-                if (KC) {
-                    const int t = ptype[a];
-                    const T c0t = (T)g.c0[t], ikt = (T)g.invk[t], dkt = (T)g.Dk[t];
-                    num_c = num_c - v0 * c0t;
-                    den_c = den_c + v0 * ikt;
-#pragma unroll
-                    for (int f = 0; f < NFACE; ++f) {
-                        num_n[f] = num_n[f] - nb[f] * c0t;
-                        den_n[f] = den_n[f] + nb[f] * ikt;
-                        mf[f] = mf[f] + dkt * ((T)0.5 * (v0 + nb[f]));
-                    }
-                }
-                const bool act = mx > (T)0 && mn < (T)1;
-                if (act) {
-                    T l = (T)0;
-#pragma unroll
-                    for (int f = 0; f < NFACE; ++f) l = l + (nb[f] - v0);
-                    if (nz < MAXACT) {
-                        S.id[nz][tid] = (unsigned char)a;
-                        S.lap[nz][tid] = l * idx2;
-                        S.cen[nz][tid] = v0;
-                        actmask |= 1u << a;
-                    }
-                    nz++;
-                }
-                if (ERR) {
-                    // in = u^{n+1}, p0 = u^n, r0in = F^n; a trivial phase has F^{n+1} = 0
-                    if (!act) {
-                        T e = ((T)12 * (p0v - v0) + ((T)6 * dt) * r0v) * ((T)1 / (T)15);
-                        const T trial = p0v + (dt * (T)0.5) * r0v;
-                        if (trial < (T)0 || trial > (T)1) e = (T)0;
-                        if (e != (T)0) {
-                            const T w = rph * fmaxf(fabsf(p0v), fabsf(v0)) + aph;
-                            const T q = e / w;
-                            esum += (double)(q * q);
-                            nc++;
-                        }
-                    }
-                } else {
-                    T acc = HP0 ? a0c * p0v + a1c * v0 : a1c * v0;
-                    if (HP2) acc = acc + a2c * p2v;
-                    if (HR0) acc = acc + b0c * r0v;
-                    if (!act && PROJ) {
-                        if (acc < (T)0) { acc = (T)0; changed = true; }
-                        if (acc >= (T)1 && acc > best) { best = acc; bestid = a; }
-                        ssum = ssum + acc;
-                    }
-                    nv[a] = acc;
-                }
-            }
-        }
-        if (nz > MAXACT) {
-            atomicOr(P.flag, FLAG_NZ_OVERFLOW);
-            nz = MAXACT;
-        }
-
-        T mu = (T)0, rc = (T)0;
-        if (KC) {
-            mu = num_c / den_c;
-            T acc = (T)0;
-#pragma unroll
-            for (int f = 0; f < NFACE; ++f) acc = acc + mf[f] * (num_n[f] / den_n[f] - mu);
-            rc = acc * idx2;
-        }
-        // variational derivative and pairwise sum over the listed phases
-        for (int k = 0; k < nz; ++k) {
-            const int a = S.id[k][tid];
-            const T *Aa = tabA + a * N, *Ba = tabB + a * N;
-            T d = (T)0;
-            for (int k2 = 0; k2 < nz; ++k2) {
-                if (k2 == k) continue;
-                const int b = S.id[k2][tid];
-                d = d + (ldg(Aa + b) * S.lap[k2][tid] + ldg(Ba + b) * S.cen[k2][tid]);
-            }
-            if (KC) {
-                const int t = ptype[a];
-                d = d + (-(mu * mu) / ((T)2 * (T)g.k[t]) - mu * (T)g.c0[t]);
-            }
-            S.dl[k][tid] = d;
-        }
-        const T inz = nz > 1 ? (T)1 / (T)nz : (T)0;
-        for (int k = 0; k < nz; ++k) {
-            T rk = (T)0;
-            if (nz > 1) {
-                const int a = S.id[k][tid];
-                const T *La = tabL + a * N;
-                const T dk = S.dl[k][tid];
-                T s = (T)0;
-                for (int k2 = 0; k2 < nz; ++k2) {
-                    if (k2 == k) continue;
-                    s = s + ldg(La + S.id[k2][tid]) * (dk - S.dl[k2][tid]);
-                }
-                rk = -(s * inz);
-            }
-            S.lap[k][tid] = rk;                 // the list now holds the RHS
-            if (ERR) {
-                const int a = S.id[k][tid];
-                const long long fo = (long long)a * Vs;
-                const T p0v = ldg(pp0 + fo), v0 = S.cen[k][tid], r0v = ldg(pr0 + fo);
-                const T sr = r0v + rk;
-                T e = ((T)12 * (p0v - v0) + ((T)6 * dt) * sr) * ((T)1 / (T)15);
-                const T trial = p0v + (dt * (T)0.5) * sr;
-                if (trial < (T)0 || trial > (T)1) e = (T)0;
-                if (e != (T)0) {
-                    const T w = rph * fmaxf(fabsf(p0v), fabsf(v0)) + aph;
-                    const T q = e / w;
-                    esum += (double)(q * q);
-                    nc++;
-                }
-            }
-        }
-        if (ERR) {
-            ecnt += (nc > 0 ? nc : 2);
-            if (KC) {
-                const long long o = (long long)N * Vs + i;
-                const T un = ldg(P.p0 + o), un1 = cc, rn = ldg(P.r0in + o);
-                const T e = ((T)12 * (un - un1) + ((T)6 * dt) * (rn + rc)) * ((T)1 / (T)15);
-                const T w = (T)P.r_c * fmaxf(fabsf(un), fabsf(un1)) + (T)P.a_c;
-                const T q = e / w;
-                esum += (double)(q * q);
-                ecnt += 1;
-            }
-        } else {
-            // listed phases: add the RHS term, clamp, >= 1 candidates, sum
-            T rr[NMAX];
-            {
-                int kk = 0;
-                int curid = nz > 0 ? S.id[0][tid] : -1;
-#pragma unroll
-                for (int a = 0; a < NMAX; ++a) {
-                    rr[a] = (T)0;
-                    if ((actmask >> a) & 1u) {
-                        const T rk = S.lap[kk][tid];
-                        kk++;
-                        rr[a] = rk;
-                        T acc = nv[a] + b1c * rk;
-                        if (PROJ) {
-                            if (acc < (T)0) { acc = (T)0; changed = true; }
-                            if (acc >= (T)1 && (acc > best || (acc == best && a < bestid))) { best = acc; bestid = a; }
-                            ssum = ssum + acc;
-                        }
-                        nv[a] = acc;
-                    }
-                }
-                (void)curid;
-            }
-            if (PROJ) {
-                if (bestid >= 0) {
-#pragma unroll
-                    for (int a = 0; a < NMAX; ++a)
-                        if (a < N && nv[a] != ((a == bestid) ? (T)1 : (T)0)) changed = true;
-                    ssum = (T)1;
-                }
-                if (!(ssum > (T)0)) atomicOr(P.flag, FLAG_SIMPLEX);
-            }
-            const T inv = (ssum > (T)0) ? (T)1 / ssum : (T)1;
-            const bool fix = R0OUT && P.fix_first && changed;
-            T *pout = P.out + i;
-            T *pr0o = R0OUT ? P.r0out + i : nullptr;
-#pragma unroll
-            for (int a = 0; a < NMAX; ++a) {
-                if (a < N) {
-                    const long long fo = (long long)a * Vs;
-                    T w = nv[a];
-                    if (PROJ) w = (bestid >= 0) ? ((a == bestid) ? (T)1 : (T)0) : w * inv;
-                    if (R0OUT) {
-                        T r = rr[a];
-                        if (fix) r = (w - ldg(pin + fo)) / b1c;
-                        pr0o[fo] = r;
-                    }
-                    pout[fo] = w;
-                }
-            }
-            if (KC) {
-                const long long o = (long long)N * Vs;
-                T acc = HP0 ? a0c * ldg(pp0 + o) + a1c * cc : a1c * cc;
-                if (HP2) acc = acc + a2c * ldg(pp2 + o);
-                acc = acc + b1c * rc;
-                if (HR0) acc = acc + b0c * ldg(pr0 + o);
-                if (R0OUT) pr0o[o] = rc;
-                pout[o] = acc;
-            }
-        }
+        ld.ic = (int)i;
+        ld.Vs = (int)g.Vs;
+        ld.in = P.in;
+        ld.p0 = P.p0;
+        ld.p2 = P.p2;
+        ld.r0 = P.r0in;
+        fast_cell<DIM, KC, SIG, NMAX>(g, P, ld, S, tid, i, off, ghost, tabA, tabB, tabL, ptype, esum, ecnt);
     }
+    if (SIG & SIG_ERR) block_partials(esum, ecnt, P.part_sum, P.part_cnt, bid);
+}
+
+// FP32 fast path with TMA staging, warp-specialised: warps 0..7 compute the
+// 32 x 8 tile, warp 8 is the producer that streams phase planes into the
+// ring (waiting on each slot's "empty" barrier, one arrival per consumer
+// warp) and the consumers wait on the slot's "full" barrier.  3D only, tiles
+// fully inside the domain in x and y (nx % 32 == 0, ny % 8 == 0).
+constexpr int TMA_BLOCK = BLOCK + 32;
+
+template <int KC, unsigned SIG>
+__global__ void __launch_bounds__(TMA_BLOCK, 3)
+tma_kernel(const Geom g, const Pass<float> P, const __grid_constant__ TmaMaps M, const float *__restrict__ tabA,
+           const float *__restrict__ tabB, const float *__restrict__ tabL, const signed char *__restrict__ ptype)
+{
+    constexpr bool ERR = (SIG & SIG_ERR) != 0;
+    constexpr bool HP0 = (SIG & SIG_P0) != 0 || ERR;
+    constexpr bool HP2 = (SIG & SIG_P2) != 0;
+    constexpr bool HR0 = (SIG & SIG_R0IN) != 0 || ERR;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // [pad to 1024 B | TmaSmem | ListSmem]: TMA destinations must be 128-byte
+    // aligned; the launch reserves 1 KB for the pad
+    unsigned char *sbase = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    TmaSmem &Q = *reinterpret_cast<TmaSmem *>(sbase);
+    ListSmem<float> &S = *reinterpret_cast<ListSmem<float> *>(sbase + sizeof(TmaSmem));
+    const int tid = threadIdx.x;
+    const int N = g.N;
+    const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z = blockIdx.z;
+    const bool zin = z > 0 && z < g.nz - 1;
+    if (tid == 0) {
+#pragma unroll
+        for (int r = 0; r < TMA_R; ++r) {
+            mbar_init(&Q.full[r], 1);
+            mbar_init(&Q.empty[r], BLOCK / 32);
+        }
+        mbar_fence_init();
+    }
+    __syncthreads();
+    double esum = 0.0;
+    long long ecnt = 0;
+    int timeout = 0;
+    if (tid >= BLOCK) {
+        // ---- producer warp: one elected lane issues every copy -------------
+        if (tid == BLOCK) {
+            const unsigned pt = (unsigned)(TX * TY * sizeof(float));
+            const unsigned bytes = (zin ? 3u : 1u) * pt + (HP0 ? pt : 0u) + (HP2 ? pt : 0u) + (HR0 ? pt : 0u);
+            for (int a = 0; a < N; ++a) {
+                const int r = a % TMA_R;
+                if (a >= TMA_R && !mbar_wait(&Q.empty[r], (unsigned)(((a / TMA_R) - 1) & 1))) timeout = 1;
+                fence_proxy_async();
+                mbar_expect_tx(&Q.full[r], bytes);
+                if (zin) tma_load4(&Q.in[r][0][0][0], &M.in3, x0, y0, z - 1, a, &Q.full[r]);
+                else tma_load4(&Q.in[r][1][0][0], &M.in1, x0, y0, z, a, &Q.full[r]);
+                if (HP0) tma_load4(&Q.p0[r][0][0], &M.p0, x0, y0, z, a, &Q.full[r]);
+                if (HP2) tma_load4(&Q.p2[r][0][0], &M.p2, x0, y0, z, a, &Q.full[r]);
+                if (HR0) tma_load4(&Q.r0[r][0][0], &M.r0, x0, y0, z, a, &Q.full[r]);
+            }
+        }
+    } else {
+        // ---- consumer warps: one cell per thread ---------------------------
+        const int tx = tid % TX, ty = tid / TX;
+        const int x = x0 + tx, y = y0 + ty;
+        const long long i = ((long long)z * g.ny + y) * g.nx + x;
+        long long off64[6];
+        int ghost[6];
+        face_offsets(g, x, y, z, off64, ghost);
+        TmaLoader ld;
+#pragma unroll
+        for (int f = 0; f < 6; ++f) ld.off[f] = ghost[f] ? 0 : (int)off64[f];
+        ld.Q = &Q;
+        ld.pin = P.in + i;
+        ld.tx = tx;
+        ld.ty = ty;
+        ld.zin = zin;
+        ld.ok = true;
+        fast_cell<3, KC, SIG, 32>(g, P, ld, S, tid, i, ld.off, ghost, tabA, tabB, tabL, ptype, esum, ecnt);
+        if (!ld.ok) timeout = 1;
+    }
+    if (timeout) atomicOr(P.flag, FLAG_TIMEOUT);
     if (ERR) block_partials(esum, ecnt, P.part_sum, P.part_cnt, bid);
 }
 

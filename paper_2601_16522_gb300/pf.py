@@ -36,7 +36,7 @@ class pf_params(C.Structure):
                 ("gamma", _dp), ("mobility", _dp), ("W", C.c_double), ("L_override", _dp),
                 ("has_conc", C.c_int), ("k", C.c_double * 2), ("c0", C.c_double * 2),
                 ("D", C.c_double * 2), ("bc_phi", C.c_int * 6), ("bc_c", C.c_int * 6),
-                ("c_dirichlet", C.c_double * 6), ("precision", C.c_int)]
+                ("c_dirichlet", C.c_double * 6), ("precision", C.c_int), ("options", C.c_int)]
 
 
 class pf_tol(C.Structure):
@@ -117,7 +117,9 @@ def _is_dev(a):
 class Simulation:
     """One simulation handle (pf_create .. pf_destroy)."""
 
-    def __init__(self, prob, precision=64, stream=None):
+    OPT_TMA = 1
+
+    def __init__(self, prob, precision=64, stream=None, options=0):
         self.prob = prob
         N = prob.n_phases
         self._keep = [np.ascontiguousarray(prob.phase_type, np.int32),
@@ -140,6 +142,7 @@ class Simulation:
         for f in range(6):
             p.bc_phi[f], p.bc_c[f], p.c_dirichlet[f] = prob.bc_phi[f], prob.bc_c[f], prob.c_dirichlet[f]
         p.precision = precision
+        p.options = options
         self.params = p
         self.precision = precision
         self._stream = stream
