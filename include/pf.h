@@ -190,6 +190,38 @@ int pf_profile(struct pf_handle *h, int enable, double *ms, long long *launches)
 /* Number of CUDA kernels launched by this handle since pf_create (-1 on NULL). */
 long long pf_launch_count(struct pf_handle *h);
 
+/* Limits of pf_totals_noalloc: fields per call, and per-field partial slots
+   of its fixed scratch (PF_NOALLOC_MAX_FIELDS * PF_NOALLOC_MAX_BLOCKS * 2
+   doubles = 1.06 MB of device memory, reserved on every GPU that loads the
+   library until the process exits). */
+#define PF_NOALLOC_MAX_FIELDS 130
+#define PF_NOALLOC_MAX_BLOCKS 512
+
+/* pf_totals_noalloc -- the paper has no counterpart; this entry point exists
+   for callers that must not allocate device memory.  cudaMalloc and cudaFree
+   may synchronise the whole device, which a caller that keeps other streams
+   busy or works under a latency budget cannot accept, and a caller whose
+   device memory is entirely held by another allocator has none to give.
+   It computes, for every field f < n_fields of a caller-owned FP64 state in
+   the ABI layout (u_dev[f * n_cells + i], device memory of the current
+   device), sum_dev[f] = dv * sum_i u_dev[f * n_cells + i] and max_dev[f] =
+   max_i u_dev[f * n_cells + i] (either output may be NULL; both are device
+   pointers).  It is the allocation-free form of the totals behind pf_reduce
+   (mass = sum of the concentration field, volumes = sums of the phase
+   fields, grains alive = phases whose max is >= 0.5).
+   Scratch: a fixed device array inside the library; nothing is allocated and
+   nothing is freed.  The first call on each device looks up that array's
+   device address (once per device); make that first call before any CUDA
+   stream capture.  Every call shares the array and writes every entry it
+   later reads, so nothing needs clearing, but calls whose kernels overlap on
+   the GPU (different streams without ordering) race on it and must be
+   serialised by the caller.  The work is enqueued on cuda_stream (NULL: the
+   default stream) and the call does not synchronise.
+   Returns PF_EINVAL for NULL u_dev, n_cells < 1, n_fields < 1, both outputs
+   NULL, or n_fields > PF_NOALLOC_MAX_FIELDS; PF_EDEVICE if a launch fails. */
+int pf_totals_noalloc(const double *u_dev, int n_fields, long long n_cells, double dv, double *sum_dev,
+                      double *max_dev, void *cuda_stream);
+
 /* Release every device buffer of the handle.  NULL is accepted. */
 int pf_destroy(struct pf_handle *h);
 
