@@ -156,7 +156,7 @@ cell_kernel(const Geom g, const Pass<T> P, const T *__restrict__ tabA, const T *
     constexpr int NFACE = 2 * DIM;
     constexpr bool GEN = (SIG & SIG_GENERIC) != 0;
     constexpr int NV = Smem<T>::NV;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
     Smem<T> &S = *reinterpret_cast<Smem<T> *>(smem_raw);
     const int tid = threadIdx.x;
 
@@ -878,7 +878,7 @@ __global__ void __launch_bounds__(BLOCK, 4)
 fast_kernel(const Geom g, const Pass<float> P, const float *__restrict__ tabA, const float *__restrict__ tabB,
             const float *__restrict__ tabL, const signed char *__restrict__ ptype)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
     ListSmem<float> &S = *reinterpret_cast<ListSmem<float> *>(smem_raw);
     const int tid = threadIdx.x;
     const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
