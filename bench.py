@@ -47,6 +47,10 @@ def workload_problem(name, device):
 
 # algorithmic vectors moved per pass kind (reads + writes of whole state vectors)
 PASS_VECTORS = {"rkl2": 5, "rkl1": 3, "sts_first": 3, "sts_err": 3, "euler": 2, "ssp": 2, "rhs": 1}
+# DRAM bytes (read + write) per cell of one RKL2 stage pass on this workload's
+# 32-phase FP32 state, from an ncu capture of the 128^3 case (1.339 GB per
+# launch for 2,097,152 cells); traffic grows in proportion to the cells.
+RKL2_TRAFFIC_PER_CELL = {"grains256": 1.339e9 / 2097152, "grains128": 1.339e9 / 2097152}
 
 
 class ClockSampler:
@@ -252,8 +256,11 @@ def run_ours(args, world, rank, local):
         ms_k, n_k = kinds[dom]
         bytes_launch = PASS_VECTORS[dom] * vec_bytes
         achieved = bytes_launch / (ms_k / n_k * 1e-3) / 1e9
+        traffic = None
+        if dom == "rkl2" and args.workload in RKL2_TRAFFIC_PER_CELL and not args.tma:
+            traffic = RKL2_TRAFFIC_PER_CELL[args.workload] * V
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "cell_kernel<float,32> (%s pass)" % dom,
+                "traffic": traffic, "kernel": "fast_kernel<3,0,sig,32> (%s pass)" % dom,
                 "bytes_per_launch": bytes_launch, "avg_launch_ms": ms_k / n_k,
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
     pass_ms = {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items() if v[1] > 0}
