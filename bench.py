@@ -190,6 +190,105 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# time to solution at fixed error (2D sharp-interface benchmarks)
+# ---------------------------------------------------------------------------
+
+def _area_rate_error(ts, areas, M=1.0, gamma=1.0):
+    """|mean dA/dt + 2 pi M gamma| over t > 0, dA/dt by 2nd-order FD of the
+    output series (Sec. 5.2.1); returned relative to 2 pi M gamma."""
+    import numpy as np
+    dA = np.gradient(np.asarray(areas), np.asarray(ts))[1:]
+    exact = 2.0 * np.pi * M * gamma
+    return abs(dA.mean() + exact) / exact
+
+
+def _front(liquid_row):
+    """x of phi_liquid = 0.5 by a cubic through the 4 nearest cell centres (Sec. 5.2.2)."""
+    import numpy as np
+    j = int(np.argmax(liquid_row >= 0.5))
+    j = min(max(j, 2), len(liquid_row) - 2)
+    xs = np.arange(j - 2, j + 2) + 0.5
+    r = np.roots(np.polyfit(xs, liquid_row[j - 2:j + 2] - 0.5, 3))
+    r = r[np.isreal(r)].real
+    r = r[(r >= xs[0]) & (r <= xs[-1])]
+    return float(r[0]) if len(r) else float(j)
+
+
+def time_to_solution(pf, torch, stefan_t_end=4300.0):
+    """Wall time of each integrator/precision to t_end with outputs at exact
+    times, and its error against the sharp-interface law; FP64 forward Euler
+    at 0.9 dt_e sets the target error."""
+    import numpy as np
+    from paper_2601_16522_gb300 import inputs as I
+    res = {}
+    # -- shrinking circle, 128^2, W = 5/pi, 2000 FE steps of 0.9 dt_e ----------
+    prob, u = I.circle(128, 40.0)
+    variants = [("feuler", 64, dict(dt_mult=0.9)), ("feuler", 32, dict(dt_mult=0.9)),
+                ("rkl2", 32, dict(tol=(1e-4, 1e-2, 1e-4, 1e-4))), ("rkl2", 64, dict(tol=(1e-4, 1e-2, 1e-4, 1e-4))),
+                ("rkl1", 32, dict(tol=(1e-4, 1e-2, 1e-4, 1e-4)))]
+    out = []
+    stream = torch.cuda.Stream()
+    for name, prec, kw in variants:
+        sim = pf.Simulation(prob, precision=prec, stream=stream)
+        sim.set_state(u)
+        dte = sim.dt_e()
+        t_end = 2000 * 0.9 * dte
+        times = np.linspace(0.0, t_end, 41)
+        integ = {"feuler": pf.FEULER, "rkl2": pf.RKL2, "rkl1": pf.RKL1}[name]
+        areas = [sim.reduce()[1][1]]
+        evals = 0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for tk in times[1:]:
+            evals += sim.step(integ, float(tk), **kw)["rhs_evals"]
+            areas.append(sim.reduce()[1][1])
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        out.append({"integrator": name, "precision": prec, "wall_ms": 1e3 * el, "rhs_evals": evals,
+                    "rel_error": _area_rate_error(times, areas)})
+        sim.close()
+    res["circle128"] = {"t_end": "2000 x 0.9 dt_e", "error": "|<dA/dt> + 2 pi M gamma| / (2 pi M gamma)",
+                        "variants": out}
+    # -- solutal Stefan strip, 1024 x 256, W = 5/pi, D 1:100 ------------------
+    prob, u = I.stefan(1024, 256, 200.0)
+    A = I.stefan_growth_constant()
+    variants = [("feuler", 64, dict(dt_mult=0.9)), ("rkl2", 32, dict(tol=(1e-4, 1e-2, 1e-4, 1e-4))),
+                ("rkl2", 64, dict(tol=(1e-4, 1e-2, 1e-4, 1e-4))), ("feuler", 32, dict(dt_mult=0.9))]
+    out = []
+    x0 = _front(u[0][:1024])
+    for name, prec, kw in variants:
+        sim = pf.Simulation(prob, precision=prec, stream=stream)
+        sim.set_state(u)
+        times = np.linspace(0.0, stefan_t_end, 11)[1:]
+        integ = {"feuler": pf.FEULER, "rkl2": pf.RKL2}[name]
+        X = []
+        evals = 0
+        host = np.zeros((3, prob.V))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for tk in times:
+            evals += sim.step(integ, float(tk), **kw)["rhs_evals"]
+            sim.get_state(out=host)
+            X.append(_front(host[0][:1024]) - x0)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        Afit = float((np.sqrt(times) * np.array(X)).sum() / times.sum())
+        out.append({"integrator": name, "precision": prec, "wall_ms": 1e3 * el, "rhs_evals": evals,
+                    "A_fit": Afit, "rel_error": abs(Afit - A) / A})
+        sim.close()
+    res["stefan1024x256"] = {"t_end": stefan_t_end, "A_exact": A, "error": "|A* - A| / A", "variants": out}
+    # speedups over FP64 FE among variants whose error is within 1.05x of its error
+    for k, r in res.items():
+        ref = [v for v in r["variants"] if v["integrator"] == "feuler" and v["precision"] == 64][0]
+        r["target_error"] = ref["rel_error"]
+        ok = [v for v in r["variants"] if v["rel_error"] <= 1.05 * ref["rel_error"] + 1e-12]
+        best = min(ok, key=lambda v: v["wall_ms"])
+        r["fastest_at_target"] = {"integrator": best["integrator"], "precision": best["precision"],
+                                  "speedup_vs_fe64": ref["wall_ms"] / best["wall_ms"]}
+    return res
+
+
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
@@ -298,6 +397,10 @@ def run_ours(args, world, rank, local):
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": "one RKL2 step (s=5) + error sweep on a %d^3 sub-box of the same state, %.1f s" % (m, el)}
 
+    tts = None
+    if rank == 0 and not args.no_tts:
+        tts = time_to_solution(pf, torch)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -312,6 +415,7 @@ def run_ours(args, world, rank, local):
             "sweeps": sweeps, "stages_per_step": ss, "accepted": acc,
             "roofline": roof, "pass_ms": pass_ms,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+            "time_to_solution": tts,
         }
         print(json.dumps(line), flush=True)
     sim.close()
@@ -327,6 +431,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tma", action="store_true", help="TMA-staged kernels instead of plain loads")
+    ap.add_argument("--no-tts", action="store_true", help="skip the 2D time-to-solution runs")
     args = ap.parse_args()
     world, rank, local = dist_setup(args)
     if args.impl == "reference":

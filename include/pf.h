@@ -106,7 +106,15 @@ typedef struct {
     double *trace_err;
     int *trace_acc;
     int *trace_len;
+    int flags;         /* PF_STEP_* bit set (0: defaults) */
 } pf_step_opts;
+
+/* pf_step_opts.flags.  By default a fixed-step run on a non-default stream
+   captures the smallest group of full steps after which the buffer rotation
+   repeats into a CUDA graph (cached per handle) and replays it; results are
+   identical to launching the passes one by one.  PF_STEP_NO_GRAPH disables
+   that. */
+enum { PF_STEP_NO_GRAPH = 1 };
 
 typedef struct {
     long long rhs_evals;       /* RHS sweeps, including rejected steps and STS error sweeps */

@@ -45,6 +45,7 @@ def build(force=False, verbose=False, ptxas_info=False):
         return LIB
     nvcc = _nvcc()
     extra = ["-Xptxas", "-v"] if ptxas_info else []
+    extra += os.environ.get("PF_NVCC_EXTRA", "").split()
 
     def compile_unit(unit):
         name, flags = unit

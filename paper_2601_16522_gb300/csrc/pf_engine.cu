@@ -156,6 +156,13 @@ struct pf_handle {
     double prof_ms[PF_NPASS_KINDS] = {0};
     long long prof_n[PF_NPASS_KINDS] = {0};
     int cur_kind = PF_PASS_OTHER;
+    // CUDA graph of `period` full fixed steps (replayed while the step size,
+    // stage count and buffer rotation are unchanged)
+    cudaGraphExec_t gexec = nullptr;
+    int g_integ = -1, g_s = -1, g_iu = -1, g_period = 0;
+    double g_dt = 0.0;
+    long long g_evals = 0, g_launches = 0;
+    long long graph_replays = 0;
     // controller (Sec. 3.3)
     double b = 0.9, E1 = 0.0, E2 = 0.0, dt1 = 0.0, dt2 = 0.0;
     int nhist = 0;
@@ -607,6 +614,54 @@ int check_flag(pf_handle *h)
     return flag ? flag_status(flag) : PF_OK;
 }
 
+// Capture full fixed steps of size dt with s stages into a graph until the
+// buffer holding u^n is the one it started from (so the graph can be
+// replayed); nothing executes during capture.  Returns false (and leaves the
+// handle unchanged) when capture is not possible.
+template <typename T>
+bool capture_fixed_steps(pf_handle *h, int integ, double dt, int s)
+{
+    if (h->gexec && h->g_integ == integ && h->g_s == s && h->g_dt == dt && h->g_iu == h->iu) return true;
+    if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+    const int iu0 = h->iu;
+    const long long l0 = h->launches;
+    long long ev = 0;
+    int period = 0;
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    bool ok = true;
+    do {
+        int cand = -1;
+        if (do_step<T>(h, integ, dt, s, nullptr, false, &cand, &ev) != PF_OK) { ok = false; break; }
+        h->iu = cand;
+        period++;
+    } while (h->iu != iu0 && period < 12);
+    if (cudaStreamEndCapture(h->stream, &graph) != cudaSuccess) ok = false;
+    ok = ok && graph && h->iu == iu0;
+    h->iu = iu0;
+    const long long nl = h->launches - l0;
+    h->launches = l0;
+    cudaGraphExec_t exec = nullptr;
+    if (ok && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) ok = false;
+    if (graph) cudaGraphDestroy(graph);
+    if (!ok) {
+        cudaGetLastError();
+        return false;
+    }
+    h->gexec = exec;
+    h->g_integ = integ;
+    h->g_s = s;
+    h->g_dt = dt;
+    h->g_iu = iu0;
+    h->g_period = period;
+    h->g_evals = ev;
+    h->g_launches = nl;
+    return true;
+}
+
 template <typename T>
 int step_loop(pf_handle *h, int integ, double t_end, const pf_tol *tol, const pf_step_opts *o, pf_stats *stats)
 {
@@ -630,8 +685,30 @@ int step_loop(pf_handle *h, int integ, double t_end, const pf_tol *tol, const pf
         if (nfix < 1) nfix = 1;
     }
     if (cudaMemsetAsync(h->dflag, 0, sizeof(int), h->stream) != cudaSuccess) return PF_EDEVICE;
+    const bool graphs = !adaptive && h->stream != nullptr && !h->prof_on && !(o->flags & PF_STEP_NO_GRAPH) &&
+                        o->max_attempts == 0 && o->trace_cap == 0;
     while (h->t < t_end) {
         if (o->max_attempts > 0 && attempts >= o->max_attempts) break;
+        // replay whole groups of full fixed steps from a CUDA graph
+        if (graphs && nfix - 1 - kfix >= 8) {
+            const int s_full = sts ? sts_stages(integ, dt, h->dte)
+                                   : (integ == PF_SSP2 ? o->ssp_stages : (integ == PF_SSP104 ? 10 : 1));
+            if (!(sts && s_full > max_stages) && capture_fixed_steps<T>(h, integ, dt, s_full)) {
+                const long long groups = (nfix - 1 - kfix) / h->g_period;
+                for (long long r = 0; r < groups; ++r)
+                    if (cudaGraphLaunch(h->gexec, h->stream) != cudaSuccess) { status = PF_EDEVICE; break; }
+                if (status) break;
+                kfix += groups * h->g_period;
+                attempts += groups * h->g_period;
+                acc_n += groups * h->g_period;
+                evals += groups * h->g_evals;
+                h->launches += groups * h->g_launches;
+                h->graph_replays += groups;
+                h->t = t0 + (double)kfix * dt;
+                hlast = dt;
+                continue;
+            }
+        }
         const double rem = t_end - h->t;
         double hs = dt;
         bool last = false;
@@ -750,6 +827,8 @@ int ensure_staging(pf_handle *h)
 
 void free_all(pf_handle *h)
 {
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    h->gexec = nullptr;
     for (cudaEvent_t ev : h->ev_pool) cudaEventDestroy(ev);
     h->ev_pool.clear();
     for (int k = 0; k < NBUF; ++k) if (h->buf[k]) cudaFree(h->buf[k]);

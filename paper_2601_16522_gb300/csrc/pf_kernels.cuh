@@ -83,6 +83,21 @@ __device__ __forceinline__ T ldg(const T *p) { return __ldg(p); }
 template <typename T>
 __device__ __forceinline__ T tabs(T v) { return v < (T)0 ? -v : v; }
 
+// Phases ahead for which the FP32 fast path asks L2 to fetch the lines of the
+// pointwise inputs and of the stencil input's cell (0: off).
+#ifndef PF_PREFETCH_DIST
+#define PF_PREFETCH_DIST 4
+#endif
+// Resident 256-thread blocks per SM the fast kernel's register budget targets.
+#ifndef PF_FAST_MINB
+#define PF_FAST_MINB 4
+#endif
+
+__device__ __forceinline__ void prefetch_l2(const void *p)
+{
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // Offsets (in cells) of the 2d face neighbours of (x,y,z); ghost[f] = 1 for a
 // non-periodic domain face (the caller builds the ghost value), else 0.
 __device__ __forceinline__ void face_offsets(const Geom &g, int x, int y, int z, long long off[6], int ghost[6])
@@ -580,11 +595,18 @@ struct PlainLoader {
     // per-phase base pointers are the same for every thread (uniform); the
     // per-thread part is a 32-bit cell index (the fast path needs NF*Vs < 2^31)
     const float *in, *p0, *p2, *r0;
-    int Vs;
+    int Vs, nph;
     int ic, inb[6];
     __device__ __forceinline__ void load(int a, long long, float &v0, float *nb, float &p0v, float &p2v, float &r0v,
                                          bool hp0, bool hp2, bool hr0)
     {
+        if (PF_PREFETCH_DIST > 0 && a + PF_PREFETCH_DIST < nph) {   // stays inside the phase fields
+            const long long pa = (long long)(a + PF_PREFETCH_DIST) * Vs + ic;
+            prefetch_l2(in + pa);
+            if (hp0) prefetch_l2(p0 + pa);
+            if (hp2) prefetch_l2(p2 + pa);
+            if (hr0) prefetch_l2(r0 + pa);
+        }
         const float *b = in + (long long)a * Vs;
         v0 = ldg(b + ic);
 #pragma unroll
@@ -816,16 +838,13 @@ __device__ __forceinline__ void fast_cell(const Geom &g, const Pass<float> &P, L
         return;
     }
     // listed phases: add the RHS term, clamp, >= 1 candidates, sum
-    T rr[R0OUT ? NMAX : 1];
     {
         int kk = 0;
 #pragma unroll
         for (int a = 0; a < NMAX; ++a) {
-            if (R0OUT) rr[a] = (T)0;
             if ((actmask >> a) & 1u) {
                 const T rk = S.lap[kk][tid];
                 kk++;
-                if (R0OUT) rr[a] = rk;
                 T acc = nv[a] + b1c * rk;
                 if (PROJ) {
                     if (acc < (T)0) { acc = (T)0; changed = true; }
@@ -847,6 +866,7 @@ __device__ __forceinline__ void fast_cell(const Geom &g, const Pass<float> &P, L
     }
     const T inv = (ssum > (T)0) ? (T)1 / ssum : (T)1;
     const bool fix = R0OUT && P.fix_first && changed;
+    int kr = 0;      // list cursor for the RHS of listed phases (R0OUT)
 #pragma unroll
     for (int a = 0; a < NMAX; ++a) {
         if (a < N) {
@@ -854,7 +874,8 @@ __device__ __forceinline__ void fast_cell(const Geom &g, const Pass<float> &P, L
             T w = nv[a];
             if (PROJ) w = (bestid >= 0) ? ((a == bestid) ? (T)1 : (T)0) : w * inv;
             if (R0OUT) {
-                T r = rr[R0OUT ? a : 0];
+                T r = (T)0;
+                if ((actmask >> a) & 1u) { r = S.lap[kr][tid]; kr++; }
                 if (fix) r = (w - ldg(P.in + fo + i)) / b1c;
                 (P.r0out + fo)[i32] = r;
             }
@@ -874,7 +895,7 @@ __device__ __forceinline__ void fast_cell(const Geom &g, const Pass<float> &P, L
 
 // FP32 fast path with plain global loads (any grid, 2D or 3D).
 template <int DIM, int KC, unsigned SIG, int NMAX>
-__global__ void __launch_bounds__(BLOCK, 4)
+__global__ void __launch_bounds__(BLOCK, PF_FAST_MINB)
 fast_kernel(const Geom g, const Pass<float> P, const float *__restrict__ tabA, const float *__restrict__ tabB,
             const float *__restrict__ tabL, const signed char *__restrict__ ptype)
 {
@@ -901,6 +922,7 @@ fast_kernel(const Geom g, const Pass<float> P, const float *__restrict__ tabA, c
         }
         ld.ic = (int)i;
         ld.Vs = (int)g.Vs;
+        ld.nph = g.N;
         ld.in = P.in;
         ld.p0 = P.p0;
         ld.p2 = P.p2;

@@ -47,7 +47,7 @@ class pf_step_opts(C.Structure):
     _fields_ = [("ssp_stages", C.c_int), ("dt_mult", C.c_double), ("dt0", C.c_double),
                 ("max_stages", C.c_int), ("max_attempts", C.c_int), ("trace_cap", C.c_int),
                 ("trace_dt", _dp), ("trace_s", _ip), ("trace_err", _dp), ("trace_acc", _ip),
-                ("trace_len", _ip)]
+                ("trace_len", _ip), ("flags", C.c_int)]
 
 
 class pf_stats(C.Structure):
@@ -214,10 +214,13 @@ class Simulation:
         _check(_lib().pf_rhs(self.h, phi, c, nz.ctypes.data, 0), "pf_rhs")
         return r, nz
 
+    STEP_NO_GRAPH = 1
+
     def step(self, integ, t_end, tol=None, dt_mult=0.0, ssp_stages=5, dt0=0.0, max_stages=0,
-             max_attempts=0, trace_cap=0):
+             max_attempts=0, trace_cap=0, flags=0):
         o = pf_step_opts()
         o.ssp_stages, o.dt_mult, o.dt0, o.max_stages, o.max_attempts = ssp_stages, dt_mult, dt0, max_stages, max_attempts
+        o.flags = flags
         tr = None
         if trace_cap:
             tr = dict(dt=np.zeros(trace_cap), s=np.zeros(trace_cap, np.int32), err=np.zeros(trace_cap),
