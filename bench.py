@@ -289,6 +289,24 @@ def time_to_solution(pf, torch, stefan_t_end=4300.0):
     return res
 
 
+def served_stream(pf, torch, n_requests, rate=50.0):
+    """Poisson stream of mixed simulations through the continuous-batching
+    server; p50/p99 latency and aggregate GCell-updates/s."""
+    from paper_2601_16522_gb300 import serve
+    reqs = serve.poisson_stream(n_requests, rate=rate, seed=4, sizes2d=(64, 128, 256, 512, 1024),
+                                sizes3d=(64, 96), steps=100)
+    serve.finalize_end_times(reqs)
+    free, total = torch.cuda.mem_get_info()
+    srv = serve.Server(mem_budget_bytes=int(0.5 * free), workers=8)
+    finished, makespan = srv.serve(reqs, realtime=True)
+    s = serve.summary(finished, makespan)
+    s.update({"arrival_rate_per_s": rate, "workers": 8, "mem_budget_bytes": srv.budget,
+              "peak_admitted_bytes": srv.peak_used,
+              "mix": "circles, Stefan strips, 2D/3D Voronoi grains (N 2..32), FE/SSP2/RKL1/RKL2, FP32, "
+                     "100 stable-Euler steps of simulated time each"})
+    return s
+
+
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
@@ -400,6 +418,9 @@ def run_ours(args, world, rank, local):
     tts = None
     if rank == 0 and not args.no_tts:
         tts = time_to_solution(pf, torch)
+    served = None
+    if rank == 0 and args.served > 0:
+        served = served_stream(pf, torch, args.served)
 
     if rank == 0:
         line = {
@@ -415,7 +436,7 @@ def run_ours(args, world, rank, local):
             "sweeps": sweeps, "stages_per_step": ss, "accepted": acc,
             "roofline": roof, "pass_ms": pass_ms,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
-            "time_to_solution": tts,
+            "time_to_solution": tts, "served": served,
         }
         print(json.dumps(line), flush=True)
     sim.close()
@@ -432,6 +453,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tma", action="store_true", help="TMA-staged kernels instead of plain loads")
     ap.add_argument("--no-tts", action="store_true", help="skip the 2D time-to-solution runs")
+    ap.add_argument("--served", type=int, default=48, help="requests in the served Poisson stream (0: skip)")
     args = ap.parse_args()
     world, rank, local = dist_setup(args)
     if args.impl == "reference":

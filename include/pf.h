@@ -230,6 +230,12 @@ long long pf_launch_count(struct pf_handle *h);
 int pf_totals_noalloc(const double *u_dev, int n_fields, long long n_cells, double dv, double *sum_dev,
                       double *max_dev, void *cuda_stream);
 
+/* Device bytes a handle for these parameters holds once it has been
+   created and a state has been set (state vectors, ABI staging buffer,
+   tables and reduction partials), without allocating anything.  Used to
+   admit simulations by memory footprint. */
+int pf_footprint(const pf_params *params, long long *bytes);
+
 /* Release every device buffer of the handle.  NULL is accepted. */
 int pf_destroy(struct pf_handle *h);
 

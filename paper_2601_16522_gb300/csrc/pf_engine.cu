@@ -818,10 +818,22 @@ int totals_t(pf_handle *h)
     return cuda_status(cudaGetLastError());
 }
 
+// Device memory comes from the stream-ordered allocator on the handle's
+// stream: creating and destroying handles then does not synchronise the
+// device, so other simulations keep running while one is set up or torn down.
+template <typename P>
+bool dmalloc(pf_handle *h, P **p, size_t bytes)
+{
+    void *q = nullptr;
+    if (cudaMallocAsync(&q, bytes, h->stream) != cudaSuccess) { cudaGetLastError(); return false; }
+    *p = static_cast<P *>(q);
+    return true;
+}
+
 int ensure_staging(pf_handle *h)
 {
     if (h->staging) return PF_OK;
-    if (cudaMalloc(&h->staging, sizeof(double) * (size_t)h->NP * h->V) != cudaSuccess) return PF_ENOMEM;
+    if (!dmalloc(h, &h->staging, sizeof(double) * (size_t)h->NP * h->V)) return PF_ENOMEM;
     return PF_OK;
 }
 
@@ -831,10 +843,11 @@ void free_all(pf_handle *h)
     h->gexec = nullptr;
     for (cudaEvent_t ev : h->ev_pool) cudaEventDestroy(ev);
     h->ev_pool.clear();
-    for (int k = 0; k < NBUF; ++k) if (h->buf[k]) cudaFree(h->buf[k]);
+    for (int k = 0; k < NBUF; ++k) if (h->buf[k]) cudaFreeAsync(h->buf[k], h->stream);
     void *ps[] = {h->dA, h->dB, h->dL, h->dptype, h->staging, h->dnz, h->part_sum, h->part_cnt,
                   h->dres, h->dcnt, h->dflag, h->tot_sum, h->tot_max};
-    for (void *p : ps) if (p) cudaFree(p);
+    for (void *p : ps) if (p) cudaFreeAsync(p, h->stream);
+    cudaStreamSynchronize(h->stream);
 }
 
 }  // namespace
@@ -940,34 +953,32 @@ int pf_create(const pf_params *p, void *cuda_stream, pf_handle **out)
 
     h->vec_bytes = (size_t)h->Vs * NP * h->esize;
     bool ok = true;
-    for (int k = 0; k < NBUF && ok; ++k) ok = cudaMalloc(&h->buf[k], h->vec_bytes) == cudaSuccess;
-    ok = ok && cudaMalloc(&h->dA, h->esize * N * N) == cudaSuccess;
-    ok = ok && cudaMalloc(&h->dB, h->esize * N * N) == cudaSuccess;
-    ok = ok && cudaMalloc(&h->dL, h->esize * N * N) == cudaSuccess;
-    ok = ok && cudaMalloc(&h->dptype, N) == cudaSuccess;
-    ok = ok && cudaMalloc(&h->part_sum, sizeof(double) * h->grid) == cudaSuccess;
-    ok = ok && cudaMalloc(&h->part_cnt, sizeof(long long) * h->grid) == cudaSuccess;
-    ok = ok && cudaMalloc(&h->dres, sizeof(double)) == cudaSuccess;
-    ok = ok && cudaMalloc(&h->dcnt, sizeof(long long)) == cudaSuccess;
-    ok = ok && cudaMalloc(&h->dflag, sizeof(int)) == cudaSuccess;
-    ok = ok && cudaMalloc(&h->tot_sum, sizeof(double) * h->tot_blocks * NP) == cudaSuccess;
-    ok = ok && cudaMalloc(&h->tot_max, sizeof(double) * h->tot_blocks * NP) == cudaSuccess;
+    for (int k = 0; k < NBUF && ok; ++k) ok = dmalloc(h, &h->buf[k], h->vec_bytes);
+    ok = ok && dmalloc(h, &h->dA, h->esize * N * N);
+    ok = ok && dmalloc(h, &h->dB, h->esize * N * N);
+    ok = ok && dmalloc(h, &h->dL, h->esize * N * N);
+    ok = ok && dmalloc(h, &h->dptype, N);
+    ok = ok && dmalloc(h, &h->part_sum, sizeof(double) * h->grid);
+    ok = ok && dmalloc(h, &h->part_cnt, sizeof(long long) * h->grid);
+    ok = ok && dmalloc(h, &h->dres, sizeof(double));
+    ok = ok && dmalloc(h, &h->dcnt, sizeof(long long));
+    ok = ok && dmalloc(h, &h->dflag, sizeof(int));
+    ok = ok && dmalloc(h, &h->tot_sum, sizeof(double) * h->tot_blocks * NP);
+    ok = ok && dmalloc(h, &h->tot_max, sizeof(double) * h->tot_blocks * NP);
     if (!ok) { cudaGetLastError(); free_all(h); delete h; return PF_ENOMEM; }
     // coefficient tables in the storage precision
     std::vector<signed char> pt(N);
     for (int a = 0; a < N; ++a) pt[a] = (signed char)h->ptype[a];
-    if (h->prec == 64) {
-        st |= cudaMemcpy(h->dA, h->A.data(), 8 * N * N, cudaMemcpyHostToDevice);
-        st |= cudaMemcpy(h->dB, h->B.data(), 8 * N * N, cudaMemcpyHostToDevice);
-        st |= cudaMemcpy(h->dL, h->L.data(), 8 * N * N, cudaMemcpyHostToDevice);
-    } else {
-        std::vector<float> fa(h->A.begin(), h->A.end()), fb(h->B.begin(), h->B.end()), fl(h->L.begin(), h->L.end());
-        st |= cudaMemcpy(h->dA, fa.data(), 4 * N * N, cudaMemcpyHostToDevice);
-        st |= cudaMemcpy(h->dB, fb.data(), 4 * N * N, cudaMemcpyHostToDevice);
-        st |= cudaMemcpy(h->dL, fl.data(), 4 * N * N, cudaMemcpyHostToDevice);
-    }
-    st |= cudaMemcpy(h->dptype, pt.data(), N, cudaMemcpyHostToDevice);
-    st |= cudaMemset(h->dflag, 0, sizeof(int));
+    std::vector<float> fa(h->A.begin(), h->A.end()), fb(h->B.begin(), h->B.end()), fl(h->L.begin(), h->L.end());
+    const void *ta = h->prec == 64 ? (const void *)h->A.data() : (const void *)fa.data();
+    const void *tb = h->prec == 64 ? (const void *)h->B.data() : (const void *)fb.data();
+    const void *tl = h->prec == 64 ? (const void *)h->L.data() : (const void *)fl.data();
+    st |= cudaMemcpyAsync(h->dA, ta, h->esize * N * N, cudaMemcpyHostToDevice, h->stream);
+    st |= cudaMemcpyAsync(h->dB, tb, h->esize * N * N, cudaMemcpyHostToDevice, h->stream);
+    st |= cudaMemcpyAsync(h->dL, tl, h->esize * N * N, cudaMemcpyHostToDevice, h->stream);
+    st |= cudaMemcpyAsync(h->dptype, pt.data(), N, cudaMemcpyHostToDevice, h->stream);
+    st |= cudaMemsetAsync(h->dflag, 0, sizeof(int), h->stream);
+    st |= cudaStreamSynchronize(h->stream);
     if (st != 0) { free_all(h); delete h; return PF_EDEVICE; }
     // TMA-staged FP32 kernels: full 32 x 8 tiles, 3D, 5..32 phases
     if (h->prec == 32 && p->dim == 3 && N > 4 && N <= 32 && p->nx % pfk::TX == 0 && p->ny % pfk::TY == 0 &&
@@ -978,6 +989,25 @@ int pf_create(const pf_params *p, void *cuda_stream, pf_handle **out)
         h->tma = ok;
     }
     *out = h;
+    return PF_OK;
+}
+
+int pf_footprint(const pf_params *p, long long *bytes)
+{
+    if (!p || !bytes) return PF_EINVAL;
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1 || p->n_phases < 2 || (p->precision != 32 && p->precision != 64))
+        return PF_EINVAL;
+    const long long V = (long long)p->nx * p->ny * p->nz;
+    const long long Vs = (V + 63) / 64 * 64;
+    const long long NF = p->n_phases + (p->has_conc ? 1 : 0);
+    const long long es = p->precision == 64 ? 8 : 4;
+    const long long tiles = (long long)((p->nx + pfk::TX - 1) / pfk::TX) * ((p->ny + pfk::TY - 1) / pfk::TY) * p->nz;
+    const long long tot_blocks = (V + 4095) / 4096 < 1024 ? ((V + 4095) / 4096 > 0 ? (V + 4095) / 4096 : 1) : 1024;
+    long long b = (long long)NBUF * NF * Vs * es;          // state vectors
+    b += NF * V * 8;                                       // ABI staging buffer (allocated on first set/get)
+    b += 3LL * p->n_phases * p->n_phases * es + p->n_phases;   // coefficient tables, phase types
+    b += tiles * 16 + 2 * tot_blocks * NF * 8 + 64;       // reduction partials
+    *bytes = b;
     return PF_OK;
 }
 
@@ -1033,7 +1063,7 @@ int pf_get_state(pf_handle *h, double *phi, double *c, unsigned char *nz, double
             return PF_EDEVICE;
     }
     if (nz) {
-        if (!h->dnz && cudaMalloc(&h->dnz, h->V) != cudaSuccess) return PF_ENOMEM;
+        if (!h->dnz && !dmalloc(h, &h->dnz, h->V)) return PF_ENOMEM;
         st = (h->prec == 64) ? rhs_t<double>(h, h->dnz) : rhs_t<float>(h, h->dnz);
         if (st) return st;
         if (cudaMemcpyAsync(nz, h->dnz, h->V, kind, h->stream) != cudaSuccess) return PF_EDEVICE;
@@ -1049,7 +1079,7 @@ int pf_rhs(pf_handle *h, double *rhs_phi, double *rhs_c, unsigned char *nz, int 
     if (!h->has_state) return PF_ESTATE;
     int st;
     if ((st = ensure_staging(h))) return st;
-    if (nz && !h->dnz && cudaMalloc(&h->dnz, h->V) != cudaSuccess) return PF_ENOMEM;
+    if (nz && !h->dnz && !dmalloc(h, &h->dnz, h->V)) return PF_ENOMEM;
     if (cudaMemsetAsync(h->dflag, 0, sizeof(int), h->stream) != cudaSuccess) return PF_EDEVICE;
     st = (h->prec == 64) ? rhs_t<double>(h, nz ? h->dnz : nullptr) : rhs_t<float>(h, nz ? h->dnz : nullptr);
     if (st) return st;

@@ -80,6 +80,7 @@ def _lib():
         L.pf_dt_e.argtypes = [H, _dp]
         L.pf_destroy.argtypes = [H]
         L.pf_profile.argtypes = [H, C.c_int, _dp, C.POINTER(C.c_longlong)]
+        L.pf_footprint.argtypes = [C.POINTER(pf_params), C.POINTER(C.c_longlong)]
         L.pf_launch_count.argtypes = [H]
         L.pf_launch_count.restype = C.c_longlong
         L.pf_strerror.argtypes = [C.c_int]
@@ -114,6 +115,41 @@ def _is_dev(a):
     return bool(getattr(a, "is_cuda", False))
 
 
+def make_params(prob, precision=64, options=0):
+    """pf_params for a Problem; returns (params, keep-alive arrays)."""
+    N = prob.n_phases
+    keep = [np.ascontiguousarray(prob.phase_type, np.int32),
+            np.ascontiguousarray(prob.gamma, np.float64).reshape(-1),
+            np.ascontiguousarray(prob.mobility, np.float64).reshape(-1)]
+    p = pf_params()
+    p.dim, p.nx, p.ny, p.nz, p.dx = prob.dim, prob.nx, prob.ny, prob.nz, prob.dx
+    p.n_phases = N
+    p.phase_type = keep[0].ctypes.data_as(_ip)
+    p.gamma = keep[1].ctypes.data_as(_dp)
+    p.mobility = keep[2].ctypes.data_as(_dp)
+    p.W = prob.W
+    if prob.L_override is not None:
+        Lm = np.ascontiguousarray(prob.L_override, np.float64).reshape(-1)
+        keep.append(Lm)
+        p.L_override = Lm.ctypes.data_as(_dp)
+    p.has_conc = prob.has_conc
+    for t in range(2):
+        p.k[t], p.c0[t], p.D[t] = prob.k[t], prob.c0[t], prob.D[t]
+    for f in range(6):
+        p.bc_phi[f], p.bc_c[f], p.c_dirichlet[f] = prob.bc_phi[f], prob.bc_c[f], prob.c_dirichlet[f]
+    p.precision = precision
+    p.options = options
+    return p, keep
+
+
+def footprint(prob, precision=64):
+    """Device bytes a Simulation of this problem holds (pf_footprint)."""
+    p, keep = make_params(prob, precision)
+    b = C.c_longlong()
+    _check(_lib().pf_footprint(C.byref(p), C.byref(b)), "pf_footprint")
+    return b.value
+
+
 class Simulation:
     """One simulation handle (pf_create .. pf_destroy)."""
 
@@ -122,27 +158,7 @@ class Simulation:
     def __init__(self, prob, precision=64, stream=None, options=0):
         self.prob = prob
         N = prob.n_phases
-        self._keep = [np.ascontiguousarray(prob.phase_type, np.int32),
-                      np.ascontiguousarray(prob.gamma, np.float64).reshape(-1),
-                      np.ascontiguousarray(prob.mobility, np.float64).reshape(-1)]
-        p = pf_params()
-        p.dim, p.nx, p.ny, p.nz, p.dx = prob.dim, prob.nx, prob.ny, prob.nz, prob.dx
-        p.n_phases = N
-        p.phase_type = self._keep[0].ctypes.data_as(_ip)
-        p.gamma = self._keep[1].ctypes.data_as(_dp)
-        p.mobility = self._keep[2].ctypes.data_as(_dp)
-        p.W = prob.W
-        if prob.L_override is not None:
-            Lm = np.ascontiguousarray(prob.L_override, np.float64).reshape(-1)
-            self._keep.append(Lm)
-            p.L_override = Lm.ctypes.data_as(_dp)
-        p.has_conc = prob.has_conc
-        for t in range(2):
-            p.k[t], p.c0[t], p.D[t] = prob.k[t], prob.c0[t], prob.D[t]
-        for f in range(6):
-            p.bc_phi[f], p.bc_c[f], p.c_dirichlet[f] = prob.bc_phi[f], prob.bc_c[f], prob.c_dirichlet[f]
-        p.precision = precision
-        p.options = options
+        p, self._keep = make_params(prob, precision, options)
         self.params = p
         self.precision = precision
         self._stream = stream

@@ -1,0 +1,213 @@
+"""Serving loop: continuous batching of simulations by device-memory footprint.
+
+Requests (a problem, an initial state, an integrator and an end time) arrive
+over time.  The scheduler admits a waiting request as soon as its footprint
+(pf_footprint) fits into the memory budget and a worker is free; an admitted
+request gets its own handle on its own CUDA stream and a worker thread drives
+it to its end time through the C ABI (ctypes releases the GIL during the
+call), so the kernels of all resident requests overlap on the GPU.  When a
+request finishes, its state is copied out, its handle and memory are
+released, and the next waiting requests are admitted.  Every result is
+computed by exactly the same passes as a stand-alone run, so a request's
+result does not depend on what it was batched with.
+"""
+from __future__ import annotations
+
+import threading
+import time
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+from . import inputs as I
+from . import pf
+
+
+@dataclass
+class Request:
+    rid: int
+    prob: I.Problem
+    u0: np.ndarray                  # (N + K, V) float64
+    integ: int
+    t_end: float
+    tol: Optional[tuple] = None     # adaptive when set, else fixed dt_mult
+    dt_mult: float = 0.0
+    precision: int = 32
+    arrival: float = 0.0            # seconds after the start of the stream
+    # filled in by the server
+    admitted: float = float("nan")
+    finished: float = float("nan")
+    result: Optional[np.ndarray] = None
+    stats: Optional[dict] = None
+    error: Optional[str] = None
+
+    @property
+    def footprint(self):
+        return pf.footprint(self.prob, self.precision)
+
+    @property
+    def latency(self):
+        return self.finished - self.arrival
+
+
+def run_alone(req: Request, stream=None):
+    """Run one request by itself (reference for the batching invariance)."""
+    import torch
+    stream = stream or torch.cuda.Stream()
+    with pf.Simulation(req.prob, precision=req.precision, stream=stream) as sim:
+        sim.set_state(req.u0)
+        st = _advance(sim, req)
+        out, _ = sim.get_state()
+    return out, st
+
+
+def _advance(sim, req):
+    if req.tol is not None:
+        return sim.step(req.integ, req.t_end, tol=req.tol)
+    return sim.step(req.integ, req.t_end, dt_mult=req.dt_mult)
+
+
+class Server:
+    """Admit by footprint, run on worker threads with one stream each.
+
+    runner(request, stream) -> (state, stats) does the work (default: the C
+    ABI on the GPU); stream_factory() makes one stream per worker; footprint
+    (request) -> bytes.  Tests of the scheduling logic replace all three."""
+
+    def __init__(self, mem_budget_bytes: int, workers: int = 8, runner=None, stream_factory=None,
+                 footprint=None):
+        self.budget = int(mem_budget_bytes)
+        self.workers = int(workers)
+        self.used = 0
+        self.peak_used = 0
+        self.lock = threading.Condition()
+        self.runner = runner or run_alone
+        self.stream_factory = stream_factory
+        self.footprint = footprint or (lambda r: r.footprint)
+
+    def serve(self, requests, realtime=True):
+        """Feed the requests at their arrival times (realtime) or all at once;
+        returns the finished requests and the makespan in seconds."""
+        if self.stream_factory is None:
+            import torch
+            dev = torch.cuda.current_device()
+            make_stream = lambda: torch.cuda.Stream(device=dev)       # noqa: E731
+            set_dev = lambda: torch.cuda.set_device(dev)               # noqa: E731
+        else:
+            make_stream = self.stream_factory
+            set_dev = lambda: None                                      # noqa: E731
+        pending = sorted(requests, key=lambda r: (r.arrival, r.rid))
+        fp = {r.rid: self.footprint(r) for r in pending}
+        for r in pending:
+            if fp[r.rid] > self.budget:
+                r.error = "footprint %d B exceeds the memory budget %d B" % (fp[r.rid], self.budget)
+        waiting = []          # arrived, not admitted (FIFO by arrival)
+        running = []
+        streams = [make_stream() for _ in range(self.workers)]
+        free_streams = list(range(self.workers))
+        t0 = time.perf_counter()
+        nxt = 0
+        finished = []
+
+        def work(req, sidx):
+            set_dev()
+            try:
+                out, st = self.runner(req, streams[sidx])
+                req.result, req.stats = out, st
+            except Exception as exc:                  # reported per request
+                req.error = str(exc)
+            req.finished = time.perf_counter() - t0
+            with self.lock:
+                self.used -= fp[req.rid]
+                free_streams.append(sidx)
+                finished.append(req)
+                self.lock.notify_all()
+
+        while nxt < len(pending) or waiting or running:
+            now = time.perf_counter() - t0
+            while nxt < len(pending) and (not realtime or pending[nxt].arrival <= now):
+                r = pending[nxt]
+                nxt += 1
+                if r.error:
+                    r.finished = now
+                    finished.append(r)
+                else:
+                    waiting.append(r)
+            with self.lock:
+                # admit in arrival order while memory and a worker are available
+                while waiting and free_streams and self.used + fp[waiting[0].rid] <= self.budget:
+                    r = waiting.pop(0)
+                    self.used += fp[r.rid]
+                    self.peak_used = max(self.peak_used, self.used)
+                    r.admitted = time.perf_counter() - t0
+                    sidx = free_streams.pop(0)
+                    th = threading.Thread(target=work, args=(r, sidx), daemon=True)
+                    running.append(th)
+                    th.start()
+                running = [th for th in running if th.is_alive()]
+                if nxt < len(pending):
+                    wait = max(0.0, pending[nxt].arrival - (time.perf_counter() - t0)) if realtime else 0.0
+                    self.lock.wait(timeout=min(wait, 0.05) if wait > 0 else 0.001)
+                elif running or waiting:
+                    self.lock.wait(timeout=0.05)
+        makespan = time.perf_counter() - t0
+        return finished, makespan
+
+
+def poisson_stream(n, rate=50.0, seed=4, sizes2d=(64, 128, 256, 512, 1024), sizes3d=(64, 96, 128),
+                   phases=(2, 3, 8, 16, 32), steps=100, device="cuda"):
+    """Seeded mixed stream shaped like the paper's benchmarks: shrinking
+    circles and Stefan strips (2D, N = 2) and Voronoi grain structures (2D/3D,
+    N up to 32); integrators and tolerances drawn uniformly.  Each request
+    runs for `steps` stable Euler steps of simulated time."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    reqs = []
+    for rid in range(n):
+        t += rng.exponential(1.0 / rate)
+        kind = rng.integers(0, 3)
+        if kind == 0:
+            nn = int(rng.choice(sizes2d))
+            prob, u = I.circle(nn, 0.3 * nn, W=2.5)
+        elif kind == 1:
+            nn = int(rng.choice(sizes2d))
+            prob, u = I.stefan(nx=max(64, nn), ny=max(8, nn // 4), h=0.2 * max(64, nn), W=2.5)
+        else:
+            dim = int(rng.integers(2, 4))
+            nn = int(rng.choice(sizes3d if dim == 3 else sizes2d[:3]))
+            N = int(rng.choice(phases))
+            N = max(2, min(N, max(2, (nn // 16) ** dim)))
+            prob, u = I.grains_device(n=nn, n_grains=N, min_dist=0.5 * nn / N ** (1.0 / dim),
+                                      seed=int(rng.integers(1 << 30)), dim=dim, dx=1.0, W_cells=2.5, M=1.0,
+                                      device=device)
+            u = u.cpu().numpy()
+        integ = int(rng.choice([pf.FEULER, pf.RKL1, pf.RKL2, pf.SSP2]))
+        a_phi = float(rng.choice([1e-2, 1e-3, 1e-4]))
+        req = Request(rid=rid, prob=prob, u0=u, integ=integ, t_end=0.0, arrival=t)
+        if integ in (pf.RKL1, pf.RKL2):
+            req.tol = (1e-4, a_phi, 1e-4, 1e-4)
+        else:
+            req.dt_mult = 0.9 if integ == pf.FEULER else 2.0
+        req.steps = steps
+        reqs.append(req)
+    return reqs
+
+
+def finalize_end_times(reqs):
+    """Set each request's end time to `steps` stable Euler steps (needs dt_e)."""
+    for r in reqs:
+        with pf.Simulation(r.prob, precision=r.precision) as sim:
+            r.t_end = r.steps * sim.dt_e()
+    return reqs
+
+
+def summary(finished, makespan):
+    ok = [r for r in finished if r.error is None]
+    lat = np.array([r.latency for r in ok]) if ok else np.zeros(1)
+    cells = sum(r.prob.V * r.stats["rhs_evals"] for r in ok)
+    errors = sorted({r.error for r in finished if r.error is not None})
+    return {"requests": len(finished), "completed": len(ok), "rejected": len(finished) - len(ok),
+            "errors": errors[:3],
+            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+            "makespan_s": makespan, "gcell_updates_per_s": cells / makespan / 1e9}

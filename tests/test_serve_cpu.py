@@ -1,0 +1,73 @@
+"""Scheduling logic of the serving loop (no GPU): admission by footprint,
+arrival order, budget never exceeded, oversize requests refused, every
+request finished (continuous batching: freed memory is reused at once)."""
+import threading
+import time
+
+import numpy as np
+
+from paper_2601_16522_gb300.serve import Request, Server, summary
+
+
+class FakeProb:
+    def __init__(self, V):
+        self.V = V
+
+
+def make(n, seed=0, budget=100):
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for i in range(n):
+        r = Request(rid=i, prob=FakeProb(int(rng.integers(10, 1000))), u0=None, integ=0, t_end=1.0,
+                    arrival=0.001 * i)
+        r.fp = int(rng.integers(5, 60)) if i != 7 else budget + 1
+        reqs.append(r)
+    return reqs
+
+
+def test_admission_respects_budget_and_order():
+    budget = 100
+    reqs = make(40, budget=budget)
+    live = {"now": 0, "max": 0}
+    lock = threading.Lock()
+    order = []
+
+    def runner(req, stream):
+        with lock:
+            live["now"] += req.fp
+            live["max"] = max(live["max"], live["now"])
+            order.append(req.rid)
+        time.sleep(0.002 + 0.001 * (req.rid % 3))
+        with lock:
+            live["now"] -= req.fp
+        return np.zeros(1), {"rhs_evals": 3}
+
+    srv = Server(budget, workers=4, runner=runner, stream_factory=lambda: None, footprint=lambda r: r.fp)
+    finished, makespan = srv.serve(reqs, realtime=True)
+    assert len(finished) == len(reqs)
+    assert live["max"] <= budget and srv.peak_used <= budget
+    refused = [r for r in finished if r.error]
+    assert [r.rid for r in refused] == [7]
+    # admission follows arrival order (FIFO, no overtaking)
+    assert order == sorted(order)
+    s = summary(finished, makespan)
+    assert s["completed"] == len(reqs) - 1 and s["rejected"] == 1
+    assert s["p99_latency_s"] >= s["p50_latency_s"] > 0
+
+
+def test_memory_freed_is_reused():
+    # three requests of 60 with a budget of 100 run one at a time
+    reqs = [Request(rid=i, prob=FakeProb(10), u0=None, integ=0, t_end=1.0, arrival=0.0) for i in range(3)]
+    spans = []
+
+    def runner(req, stream):
+        t = time.perf_counter()
+        time.sleep(0.01)
+        spans.append((t, time.perf_counter()))
+        return np.zeros(1), {"rhs_evals": 1}
+
+    srv = Server(100, workers=3, runner=runner, stream_factory=lambda: None, footprint=lambda r: 60)
+    finished, _ = srv.serve(reqs, realtime=False)
+    assert len(finished) == 3 and all(r.error is None for r in finished)
+    spans.sort()
+    assert all(spans[i][1] <= spans[i + 1][0] + 1e-3 for i in range(2))
