@@ -324,6 +324,10 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     sim.set_state(u)
     torch.cuda.synchronize()
+    tuned = None
+    if not args.tma:
+        choice, ms_plain, ms_tma = sim.autotune()
+        tuned = {"choice": ["plain", "tma"][choice], "rkl2_pass_ms_plain": ms_plain, "rkl2_pass_ms_tma": ms_tma}
 
     def one_step():
         return sim.step(pf.RKL2, 1e30, tol=TOL, max_attempts=1)
@@ -374,10 +378,12 @@ def run_ours(args, world, rank, local):
         bytes_launch = PASS_VECTORS[dom] * vec_bytes
         achieved = bytes_launch / (ms_k / n_k * 1e-3) / 1e9
         traffic = None
-        if dom == "rkl2" and args.workload in RKL2_TRAFFIC_PER_CELL and not args.tma:
+        if (dom == "rkl2" and args.workload in RKL2_TRAFFIC_PER_CELL and not args.tma
+                and not (tuned and tuned["choice"] == "tma")):
             traffic = RKL2_TRAFFIC_PER_CELL[args.workload] * V
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": "fast_kernel<3,0,sig,32> (%s pass)" % dom,
+                "traffic": traffic, "kernel": ("tma_kernel<0,sig>" if (tuned and tuned["choice"] == "tma") or args.tma
+                           else "fast_kernel<3,0,sig,32>") + " (%s pass)" % dom,
                 "bytes_per_launch": bytes_launch, "avg_launch_ms": ms_k / n_k,
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
     pass_ms = {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items() if v[1] > 0}
@@ -432,7 +438,8 @@ def run_ours(args, world, rank, local):
                                    "adaptive RKL2 (tol r=%g a_phi=%g)" % (args.workload, prob.nx, prob.ny,
                                                                            prob.nz, N, TOL[0], TOL[1]),
                        "cells": V, "phases": N, "integrator": "rkl2-adaptive", "parallelism": "replicas",
-                       "l2": "state vectors %.2f GB each > L2 (no flush needed)" % (vec_bytes / 1e9)},
+                       "l2": "state vectors %.2f GB each > L2 (no flush needed)" % (vec_bytes / 1e9),
+                       "autotune": tuned},
             "sweeps": sweeps, "stages_per_step": ss, "accepted": acc,
             "roofline": roof, "pass_ms": pass_ms,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,

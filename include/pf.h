@@ -195,6 +195,15 @@ enum {
    enable = -1 keeps the totals and the current setting. */
 int pf_profile(struct pf_handle *h, int enable, double *ms, long long *launches);
 
+/* Autotuner: times the RKL2 stage pass of this handle's current state with
+   each available kernel variant (plain loads; TMA-staged phase planes where
+   the problem allows it), switches the handle to the faster one and records
+   the choice for the problem's shape (precision, dims, phases, K) in a
+   process-wide table that later pf_create calls of the same shape apply.
+   *choice = 0 plain, 1 TMA; the average times in ms (or -1 when a variant
+   does not apply).  No state change.  PF_ESTATE without a state. */
+int pf_autotune(struct pf_handle *h, int *choice, double *ms_plain, double *ms_tma);
+
 /* Number of CUDA kernels launched by this handle since pf_create (-1 on NULL). */
 long long pf_launch_count(struct pf_handle *h);
 

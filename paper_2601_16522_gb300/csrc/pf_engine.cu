@@ -13,7 +13,10 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 #include <vector>
 
 #include "../../include/pf.h"
@@ -141,7 +144,8 @@ struct pf_handle {
     int *dflag = nullptr;
     double *tot_sum = nullptr, *tot_max = nullptr;
     int tot_blocks = 0;
-    bool tma = false;                  // TMA-staged FP32 kernels usable
+    bool tma_ok = false;               // tensor maps built: TMA-staged kernels available
+    bool tma = false;                  // TMA-staged FP32 kernels in use
     CUtensorMap m3[NBUF], m1[NBUF];    // per buffer: 3-plane and 1-plane boxes
     double t = 0.0;
     bool has_state = false;
@@ -850,6 +854,56 @@ void free_all(pf_handle *h)
     cudaStreamSynchronize(h->stream);
 }
 
+// Process-wide autotuning results: problem shape -> kernel variant (0 plain
+// loads, 1 TMA staging).
+typedef std::tuple<int, int, int, int, int, int, int> TuneKey;   // prec, dim, nx, ny, nz, N, K
+std::mutex g_tune_lock;
+std::map<TuneKey, int> g_tune;
+
+TuneKey tune_key(const pf_handle *h)
+{
+    return TuneKey(h->prec, h->g.dim, h->g.nx, h->g.ny, h->g.nz, h->N, h->K);
+}
+
+int tuned_choice(const pf_handle *h)
+{
+    std::lock_guard<std::mutex> guard(g_tune_lock);
+    auto it = g_tune.find(tune_key(h));
+    return it == g_tune.end() ? -1 : it->second;
+}
+
+// Average time of the RKL2-body pass signature on the current state (inputs
+// u^n for every operand, output into a work buffer; no state change).
+double time_rkl2_pass(pf_handle *h, bool use_tma, int reps)
+{
+    const bool keep = h->tma;
+    h->tma = use_tma;
+    const int U = h->iu, W = (h->iu + 1) % NBUF;
+    Pass<float> P = blank_pass<float>(h);
+    P.in = (float *)h->buf[U]; P.p0 = (float *)h->buf[U]; P.p2 = (float *)h->buf[U]; P.r0in = (float *)h->buf[U];
+    P.a0 = -0.5; P.a1 = 1.5; P.a2 = 0.0; P.b1 = 0.0; P.b0 = 0.0;
+    P.out = (float *)h->buf[W];
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double ms = -1.0;
+    bool ok = true;
+    for (int r = 0; r < 2 && ok; ++r) ok = run_pass<float>(h, P) == PF_OK;
+    cudaEventRecord(e0, h->stream);
+    for (int r = 0; r < reps && ok; ++r) ok = run_pass<float>(h, P) == PF_OK;
+    cudaEventRecord(e1, h->stream);
+    if (ok && cudaEventSynchronize(e1) == cudaSuccess) {
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        ms = t / reps;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaMemsetAsync(h->dflag, 0, sizeof(int), h->stream);
+    h->tma = keep;
+    return ms;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -982,11 +1036,14 @@ int pf_create(const pf_params *p, void *cuda_stream, pf_handle **out)
     if (st != 0) { free_all(h); delete h; return PF_EDEVICE; }
     // TMA-staged FP32 kernels: full 32 x 8 tiles, 3D, 5..32 phases
     if (h->prec == 32 && p->dim == 3 && N > 4 && N <= 32 && p->nx % pfk::TX == 0 && p->ny % pfk::TY == 0 &&
-        p->nz >= 3 && (p->options & PF_OPT_TMA) && h->Vs * (long long)NP < 0x7fffffffLL) {
+        p->nz >= 3 && h->Vs * (long long)NP < 0x7fffffffLL) {
         bool ok = true;
         for (int k = 0; k < NBUF && ok; ++k)
             ok = make_map(&h->m3[k], h->buf[k], g, 3) && make_map(&h->m1[k], h->buf[k], g, 1);
-        h->tma = ok;
+        h->tma_ok = ok;
+        int tuned = -1;
+        if (ok) tuned = tuned_choice(h);
+        h->tma = ok && ((p->options & PF_OPT_TMA) || tuned == 1);
     }
     *out = h;
     return PF_OK;
@@ -1132,6 +1189,28 @@ int pf_profile(pf_handle *h, int enable, double *ms, long long *launches)
 }
 
 long long pf_launch_count(pf_handle *h) { return h ? h->launches : -1; }
+
+int pf_autotune(pf_handle *h, int *choice, double *ms_plain, double *ms_tma)
+{
+    if (!h) return PF_EINVAL;
+    if (!h->has_state) return PF_ESTATE;
+    if (ms_plain) *ms_plain = -1.0;
+    if (ms_tma) *ms_tma = -1.0;
+    int c = 0;
+    if (h->prec == 32 && h->tma_ok) {
+        const double a = time_rkl2_pass(h, false, 5);
+        const double b = time_rkl2_pass(h, true, 5);
+        if (a < 0.0 || b < 0.0) return PF_EDEVICE;
+        c = b < a ? 1 : 0;
+        if (ms_plain) *ms_plain = a;
+        if (ms_tma) *ms_tma = b;
+        std::lock_guard<std::mutex> guard(g_tune_lock);
+        g_tune[tune_key(h)] = c;
+    }
+    h->tma = h->tma_ok && c == 1;
+    if (choice) *choice = c;
+    return check_flag(h);
+}
 
 int pf_reduce(pf_handle *h, double *mass_c, double *vol_phi, int *grains_alive)
 {

@@ -81,6 +81,7 @@ def _lib():
         L.pf_destroy.argtypes = [H]
         L.pf_profile.argtypes = [H, C.c_int, _dp, C.POINTER(C.c_longlong)]
         L.pf_footprint.argtypes = [C.POINTER(pf_params), C.POINTER(C.c_longlong)]
+        L.pf_autotune.argtypes = [H, _ip, _dp, _dp]
         L.pf_launch_count.argtypes = [H]
         L.pf_launch_count.restype = C.c_longlong
         L.pf_strerror.argtypes = [C.c_int]
@@ -267,6 +268,14 @@ class Simulation:
         n = (C.c_longlong * 8)()
         _check(_lib().pf_profile(self.h, int(enable), ms, n), "pf_profile")
         return {k: (ms[i], n[i]) for i, k in enumerate(PASS_KINDS)}
+
+    def autotune(self):
+        """pf_autotune: returns (choice, ms_plain, ms_tma); choice 0 plain, 1 TMA."""
+        c = C.c_int()
+        a = C.c_double()
+        b = C.c_double()
+        _check(_lib().pf_autotune(self.h, C.byref(c), C.byref(a), C.byref(b)), "pf_autotune")
+        return c.value, a.value, b.value
 
     def launch_count(self):
         return _lib().pf_launch_count(self.h)
