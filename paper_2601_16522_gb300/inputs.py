@@ -347,3 +347,97 @@ def grains_device(n=256, n_grains=32, min_dist=40.0, seed=2, dim=3, dx=0.005, W_
         for j in range(k):
             u.index_put_((nn[:, j], idx), tr[:, j], accumulate=True)
     return prob, u
+
+
+def corrected_radius(r, W, tol=1e-10):
+    """Radius r_c whose diffuse sphere (Eq. profile of r_c - |x|) holds the
+    sharp volume 4/3 pi r^3 (the radius correction of Sec. 5.3, solved here by
+    bisection on the continuous volume integral)."""
+    h = math.pi * W / 2.0
+
+    def vol(rc):
+        rho = np.linspace(0.0, rc + h, 4001)
+        return 4.0 * math.pi * np.trapezoid(rho ** 2 * profile(rc - rho, W), rho)
+
+    target = 4.0 / 3.0 * math.pi * r ** 3
+    lo, hi = 0.0, r + h
+    while hi - lo > tol * max(1.0, r):
+        mid = 0.5 * (lo + hi)
+        if vol(mid) < target:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
+def sintering_device(n=320, n_grains=64, porosity=0.05, r_range=(4.0, 8.0), gap=4.0, seed=3, dx=0.005,
+                     W_cells=2.5, M_gb=5e-3, M_gp=5e-3, D_pore=10.0, D_grain=5e-8, k=1e5, c0=(0.02, 0.98),
+                     gamma=1.0, grain_min_dist=None, device="cuda"):
+    """Final-stage sintering state (Sec. 5.3, mobile pores): a periodic
+    Voronoi grain structure (grains: type beta, phases 0..n_grains-1) with
+    spherical pores (one pore phase of type alpha, last phase) of radii
+    U[r_range] cells placed at seeded sites whose centres are at least
+    r_i + r_j + 2 gap apart, until the sharp pore volume reaches `porosity`.
+    Pores use the corrected radius, grains are rescaled by (1 - phi_pore)
+    (Eq. distfix with the ratios kept), and c is at local equilibrium
+    c = sum_a phi_a c0_a.  Returns (Problem, u) with u a float64 device tensor."""
+    import torch
+    rng = np.random.default_rng(seed)
+    gmd = grain_min_dist if grain_min_dist is not None else 0.8 * n / n_grains ** (1.0 / 3.0)
+    prob_g, ug = grains_device(n=n, n_grains=n_grains, min_dist=gmd, seed=seed, dim=3, dx=dx, W_cells=W_cells,
+                               M=M_gb, gamma=gamma, device=device)
+    V = n ** 3
+    target = porosity * V
+    centres, radii = [], []
+    vol = 0.0
+    tries = 0
+    while vol < target:
+        tries += 1
+        if tries > 2000000:
+            raise ValueError("cannot reach porosity %g" % porosity)
+        c = rng.random(3) * n
+        r = rng.uniform(*r_range)
+        if centres:
+            d = np.abs(np.array(centres) - c)
+            d = np.minimum(d, n - d)
+            if np.any(np.sqrt((d * d).sum(1)) < np.array(radii) + r + 2.0 * gap):
+                continue
+        centres.append(c)
+        radii.append(r)
+        vol += 4.0 / 3.0 * math.pi * r ** 3
+    # pore phase: max over pores of profile(r_c - |x - s|), stamped box by box
+    h = math.pi * W_cells / 2.0
+    phip = torch.zeros(V, dtype=torch.float64, device=device)
+    rc_cache = {}
+    for c, r in zip(centres, radii):
+        rc = corrected_radius(r, W_cells)
+        R = int(math.ceil(rc + h)) + 1
+        off = torch.arange(-R, R + 1, device=device)
+        zz, yy, xx = torch.meshgrid(off, off, off, indexing="ij")
+        ci = np.floor(c).astype(int)
+        X = (ci[0] + xx) % n
+        Y = (ci[1] + yy) % n
+        Z = (ci[2] + zz) % n
+        dxv = (ci[0] + xx + 0.5 - c[0]).double()
+        dyv = (ci[1] + yy + 0.5 - c[1]).double()
+        dzv = (ci[2] + zz + 0.5 - c[2]).double()
+        d = rc - torch.sqrt(dxv * dxv + dyv * dyv + dzv * dzv)
+        val = 0.5 * (1.0 + torch.sin(d.clamp(-h, h) / W_cells))
+        val = torch.where(d <= -h, torch.zeros_like(val), val)
+        val = torch.where(d >= h, torch.ones_like(val), val)
+        idx = ((Z * n + Y) * n + X).reshape(-1)
+        phip.scatter_reduce_(0, idx, val.reshape(-1), reduce="amax")
+    N = n_grains + 1
+    u = torch.empty((N + 1, V), dtype=torch.float64, device=device)
+    u[:n_grains] = ug * (1.0 - phip)[None, :]
+    u[n_grains] = phip
+    u[N] = c0[0] * phip + c0[1] * (1.0 - phip)
+    ptype = np.ones(N, np.int32)
+    ptype[n_grains] = 0
+    prob = Problem(dim=3, nx=n, ny=n, nz=n, dx=dx, n_phases=N, phase_type=ptype,
+                   gamma=uniform_pairs(N, gamma), mobility=typed_pairs(ptype, M_gb, M_gp), W=W_cells * dx,
+                   has_conc=1, k=(k, k), c0=tuple(c0), D=(D_pore, D_grain),
+                   name="sinter%d^3_N%d_pores%d" % (n, N, len(centres)))
+    prob.pores = len(centres)
+    prob.porosity = float(phip.sum().item()) / V
+    return prob, u
