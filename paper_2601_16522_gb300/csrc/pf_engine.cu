@@ -1036,7 +1036,7 @@ int pf_create(const pf_params *p, void *cuda_stream, pf_handle **out)
     if (st != 0) { free_all(h); delete h; return PF_EDEVICE; }
     // TMA-staged FP32 kernels: full 32 x 8 tiles, 3D, 5..32 phases
     if (h->prec == 32 && p->dim == 3 && N > 4 && N <= 32 && p->nx % pfk::TX == 0 && p->ny % pfk::TY == 0 &&
-        p->nz >= 3 && h->Vs * (long long)NP < 0x7fffffffLL) {
+        p->nz >= 3 && h->Vs < 0x7fffffffLL) {
         bool ok = true;
         for (int k = 0; k < NBUF && ok; ++k)
             ok = make_map(&h->m3[k], h->buf[k], g, 3) && make_map(&h->m1[k], h->buf[k], g, 1);

@@ -93,6 +93,22 @@ __device__ __forceinline__ T tabs(T v) { return v < (T)0 ? -v : v; }
 #define PF_FAST_MINB 4
 #endif
 
+// Streaming load that does not allocate in L1 (pointwise stage inputs are
+// used once; L1 is left to the stencil rows shared between warps).
+#ifndef PF_STREAM_NOALLOC
+#define PF_STREAM_NOALLOC 1
+#endif
+__device__ __forceinline__ float ld_stream(const float *p)
+{
+#if PF_STREAM_NOALLOC
+    float v;
+    asm volatile("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+#else
+    return __ldg(p);
+#endif
+}
+
 __device__ __forceinline__ void prefetch_l2(const void *p)
 {
     asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
@@ -585,6 +601,7 @@ struct ListSmem {
     T lap[MAXACT][BLOCK];    // Laplacian, later the RHS of the listed phase
     T cen[MAXACT][BLOCK];    // phi at the cell
     T dl[MAXACT][BLOCK];     // variational derivative
+    T val[MAXACT][BLOCK];    // stage value of the listed phase (N > 32 path)
 };
 
 // Loader policies of the FP32 fast path: where the values of phase a come
@@ -611,9 +628,9 @@ struct PlainLoader {
         v0 = ldg(b + ic);
 #pragma unroll
         for (int f = 0; f < 2 * DIM; ++f) nb[f] = ldg(b + inb[f]);
-        if (hp0) p0v = ldg(p0 + (long long)a * Vs + ic);
-        if (hp2) p2v = ldg(p2 + (long long)a * Vs + ic);
-        if (hr0) r0v = ldg(r0 + (long long)a * Vs + ic);
+        if (hp0) p0v = ld_stream(p0 + (long long)a * Vs + ic);
+        if (hp2) p2v = ld_stream(p2 + (long long)a * Vs + ic);
+        if (hr0) r0v = ld_stream(r0 + (long long)a * Vs + ic);
     }
     __device__ __forceinline__ void release(int) {}
 };
@@ -891,6 +908,267 @@ __device__ __forceinline__ void fast_cell(const Geom &g, const Pass<float> &P, L
         if (R0OUT) P.r0out[o] = rc;
         P.out[o] = acc;
     }
+}
+
+// FP32 path for N > 32 phases: phases are taken in register-unrolled chunks
+// of 32.  A trivial phase's stage value is final in the first sweep and is
+// written, unnormalised, to the output; listed phases get their RHS term
+// after the pairwise sums; a second sweep re-reads the output (written by the
+// same thread moments before, so it is still in L2) and applies the
+// projection's normalisation.  No per-phase register array is needed.
+template <int DIM, int KC, unsigned SIG>
+__device__ __forceinline__ void big_cell(const Geom &g, const Pass<float> &P, PlainLoader<DIM> &ld,
+                                         ListSmem<float> &S, int tid, long long i, const int *off, const int *ghost,
+                                         const float *tabA, const float *tabB, const float *tabL,
+                                         const signed char *ptype, double &esum, long long &ecnt)
+{
+    typedef float T;
+    constexpr int NFACE = 2 * DIM;
+    constexpr int CHK = 32;
+    constexpr bool ERR = (SIG & SIG_ERR) != 0;
+    constexpr bool HP0 = (SIG & SIG_P0) != 0 || ERR;
+    constexpr bool HP2 = (SIG & SIG_P2) != 0;
+    constexpr bool HR0 = (SIG & SIG_R0IN) != 0 || ERR;
+    constexpr bool R0OUT = (SIG & SIG_R0OUT) != 0;
+    constexpr bool PROJ = (SIG & SIG_PROJECT) != 0;
+    const int N = g.N;
+    const long long Vs = g.Vs;
+    const int i32 = (int)i;
+    const T idx2 = (T)(1.0 / g.dx2);
+    const T a0c = (T)P.a0, a1c = (T)P.a1, a2c = (T)P.a2, b1c = (T)P.b1, b0c = (T)P.b0;
+    const T dt = (T)P.dt, rph = (T)P.r_phi, aph = (T)P.a_phi;
+    auto combo = [&](T p0v, T v0, T p2v, T r0v) {
+        T acc = HP0 ? a0c * p0v + a1c * v0 : a1c * v0;
+        if (HP2) acc = acc + a2c * p2v;
+        if (HR0) acc = acc + b0c * r0v;
+        return acc;
+    };
+
+    T cc = (T)0, num_c = (T)0, den_c = (T)0, num_n[NFACE], den_n[NFACE], mf[NFACE];
+#pragma unroll
+    for (int f = 0; f < NFACE; ++f) { num_n[f] = (T)0; den_n[f] = (T)0; mf[f] = (T)0; }
+    if (KC) {
+        const T *cf = P.in + (long long)N * Vs + i;
+        cc = ldg(cf);
+        num_c = cc;
+#pragma unroll
+        for (int f = 0; f < NFACE; ++f) {
+            T v = ldg(cf + off[f]);
+            if (ghost[f] && g.bc_c[f] == BC_DIRICHLET) v = (T)2 * (T)g.cdir[f] - cc;
+            num_n[f] = v;
+        }
+    }
+
+    int nz = 0, nc = 0;
+    bool changed = false;
+    T best = (T)-1, ssum = (T)0;
+    int bestid = -1;
+    for (int a0 = 0; a0 < N; a0 += CHK) {
+#pragma unroll
+        for (int aa = 0; aa < CHK; ++aa) {
+            const int a = a0 + aa;
+            if (a < N) {
+                const long long fo = (long long)a * Vs;
+                T v0, nb[NFACE], p0v = (T)0, p2v = (T)0, r0v = (T)0;
+                ld.load(a, fo, v0, nb, p0v, p2v, r0v, HP0, HP2, HR0);
+                T mx = v0, mn = v0;
+#pragma unroll
+                for (int f = 0; f < NFACE; ++f) {
+                    mx = fmaxf(mx, nb[f]);
+                    mn = fminf(mn, nb[f]);
+                }
+                if (KC) {
+                    const int t = ptype[a];
+                    const T c0t = (T)g.c0[t], ikt = (T)g.invk[t], dkt = (T)g.Dk[t];
+                    num_c = num_c - v0 * c0t;
+                    den_c = den_c + v0 * ikt;
+#pragma unroll
+                    for (int f = 0; f < NFACE; ++f) {
+                        num_n[f] = num_n[f] - nb[f] * c0t;
+                        den_n[f] = den_n[f] + nb[f] * ikt;
+                        mf[f] = mf[f] + dkt * ((T)0.5 * (v0 + nb[f]));
+                    }
+                }
+                const bool act = mx > (T)0 && mn < (T)1;
+                if (act) {
+                    T l = (T)0;
+#pragma unroll
+                    for (int f = 0; f < NFACE; ++f) l = l + (nb[f] - v0);
+                    if (nz < MAXACT) {
+                        S.id[nz][tid] = (unsigned char)a;
+                        S.lap[nz][tid] = l * idx2;
+                        S.cen[nz][tid] = v0;
+                        if (!ERR) S.val[nz][tid] = combo(p0v, v0, p2v, r0v);
+                    }
+                    nz++;
+                } else if (ERR) {
+                    T e = ((T)12 * (p0v - v0) + ((T)6 * dt) * r0v) * ((T)1 / (T)15);
+                    const T trial = p0v + (dt * (T)0.5) * r0v;
+                    if (trial < (T)0 || trial > (T)1) e = (T)0;
+                    if (e != (T)0) {
+                        const T w = rph * fmaxf(fabsf(p0v), fabsf(v0)) + aph;
+                        const T q = e / w;
+                        esum += (double)(q * q);
+                        nc++;
+                    }
+                } else {
+                    T c = combo(p0v, v0, p2v, r0v);
+                    if (PROJ) {
+                        if (c < (T)0) { c = (T)0; changed = true; }
+                        if (c >= (T)1 && c > best) { best = c; bestid = a; }
+                        ssum = ssum + c;
+                    }
+                    (P.out + fo)[i32] = c;
+                }
+            }
+        }
+    }
+    if (nz > MAXACT) {
+        atomicOr(P.flag, FLAG_NZ_OVERFLOW);
+        nz = MAXACT;
+    }
+    T mu = (T)0, rc = (T)0;
+    if (KC) {
+        mu = num_c / den_c;
+        T acc = (T)0;
+#pragma unroll
+        for (int f = 0; f < NFACE; ++f) acc = acc + mf[f] * (num_n[f] / den_n[f] - mu);
+        rc = acc * idx2;
+    }
+    for (int k = 0; k < nz; ++k) {
+        const int a = S.id[k][tid];
+        const T *Aa = tabA + a * N, *Ba = tabB + a * N;
+        T d = (T)0;
+        for (int k2 = 0; k2 < nz; ++k2) {
+            if (k2 == k) continue;
+            const int b = S.id[k2][tid];
+            d = d + (ldg(Aa + b) * S.lap[k2][tid] + ldg(Ba + b) * S.cen[k2][tid]);
+        }
+        if (KC) {
+            const int t = ptype[a];
+            d = d + (-(mu * mu) / ((T)2 * (T)g.k[t]) - mu * (T)g.c0[t]);
+        }
+        S.dl[k][tid] = d;
+    }
+    const T inz = nz > 1 ? (T)1 / (T)nz : (T)0;
+    for (int k = 0; k < nz; ++k) {
+        T rk = (T)0;
+        const int a = S.id[k][tid];
+        if (nz > 1) {
+            const T *La = tabL + a * N;
+            const T dk = S.dl[k][tid];
+            T s = (T)0;
+            for (int k2 = 0; k2 < nz; ++k2) {
+                if (k2 == k) continue;
+                s = s + ldg(La + S.id[k2][tid]) * (dk - S.dl[k2][tid]);
+            }
+            rk = -(s * inz);
+        }
+        S.lap[k][tid] = rk;
+        const long long fo = (long long)a * Vs;
+        if (ERR) {
+            const T p0v = ldg(P.p0 + fo + i), v0 = S.cen[k][tid], r0v = ldg(P.r0in + fo + i);
+            const T sr = r0v + rk;
+            T e = ((T)12 * (p0v - v0) + ((T)6 * dt) * sr) * ((T)1 / (T)15);
+            const T trial = p0v + (dt * (T)0.5) * sr;
+            if (trial < (T)0 || trial > (T)1) e = (T)0;
+            if (e != (T)0) {
+                const T w = rph * fmaxf(fabsf(p0v), fabsf(v0)) + aph;
+                const T q = e / w;
+                esum += (double)(q * q);
+                nc++;
+            }
+        } else {
+            T c = S.val[k][tid] + b1c * rk;
+            if (PROJ) {
+                if (c < (T)0) { c = (T)0; changed = true; }
+                if (c >= (T)1 && (c > best || (c == best && a < bestid))) { best = c; bestid = a; }
+                ssum = ssum + c;
+            }
+            (P.out + fo)[i32] = c;
+        }
+    }
+    if (ERR) {
+        ecnt += (nc > 0 ? nc : 2);
+        if (KC) {
+            const long long o = (long long)N * Vs + i;
+            const T un = ldg(P.p0 + o), un1 = cc, rn = ldg(P.r0in + o);
+            const T e = ((T)12 * (un - un1) + ((T)6 * dt) * (rn + rc)) * ((T)1 / (T)15);
+            const T w = (T)P.r_c * fmaxf(fabsf(un), fabsf(un1)) + (T)P.a_c;
+            const T q = e / w;
+            esum += (double)(q * q);
+            ecnt += 1;
+        }
+        return;
+    }
+    if (PROJ) {
+        if (bestid >= 0) { changed = true; ssum = (T)1; }
+        if (!(ssum > (T)0)) atomicOr(P.flag, FLAG_SIMPLEX);
+    }
+    const T inv = (ssum > (T)0) ? (T)1 / ssum : (T)1;
+    const bool fix = R0OUT && P.fix_first && changed;
+    int kr = 0;
+    int curid = nz > 0 ? S.id[0][tid] : -1;
+#pragma unroll 4
+    for (int a = 0; a < N; ++a) {
+        const long long fo = (long long)a * Vs;
+        T w = (P.out + fo)[i32];
+        if (PROJ) w = (bestid >= 0) ? ((a == bestid) ? (T)1 : (T)0) : w * inv;
+        if (R0OUT) {
+            T r = (T)0;
+            if (a == curid) { r = S.lap[kr][tid]; kr++; curid = kr < nz ? S.id[kr][tid] : -1; }
+            if (fix) r = (w - ldg(P.in + fo + i)) / b1c;
+            (P.r0out + fo)[i32] = r;
+        }
+        (P.out + fo)[i32] = w;
+    }
+    if (KC) {
+        const long long o = (long long)N * Vs + i;
+        T acc = HP0 ? a0c * ldg(P.p0 + o) + a1c * cc : a1c * cc;
+        if (HP2) acc = acc + a2c * ldg(P.p2 + o);
+        acc = acc + b1c * rc;
+        if (HR0) acc = acc + b0c * ldg(P.r0in + o);
+        if (R0OUT) P.r0out[o] = rc;
+        P.out[o] = acc;
+    }
+}
+
+template <int DIM, int KC, unsigned SIG>
+__global__ void __launch_bounds__(BLOCK, 4)
+big_kernel(const Geom g, const Pass<float> P, const float *__restrict__ tabA, const float *__restrict__ tabB,
+           const float *__restrict__ tabL, const signed char *__restrict__ ptype)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    ListSmem<float> &S = *reinterpret_cast<ListSmem<float> *>(smem_raw);
+    const int tid = threadIdx.x;
+    const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    const int x = blockIdx.x * TX + (tid % TX);
+    const int y = blockIdx.y * TY + (tid / TX);
+    const int z = blockIdx.z;
+    double esum = 0.0;
+    long long ecnt = 0;
+    if (x < g.nx && y < g.ny) {
+        const long long i = ((long long)z * g.ny + y) * g.nx + x;
+        long long off64[6];
+        int ghost[6];
+        face_offsets(g, x, y, z, off64, ghost);
+        PlainLoader<DIM> ld;
+        int off[6];
+#pragma unroll
+        for (int f = 0; f < 6; ++f) {
+            off[f] = ghost[f] ? 0 : (int)off64[f];
+            ld.inb[f] = (int)i + off[f];
+        }
+        ld.ic = (int)i;
+        ld.Vs = (int)g.Vs;
+        ld.nph = g.N;
+        ld.in = P.in;
+        ld.p0 = P.p0;
+        ld.p2 = P.p2;
+        ld.r0 = P.r0in;
+        big_cell<DIM, KC, SIG>(g, P, ld, S, tid, i, off, ghost, tabA, tabB, tabL, ptype, esum, ecnt);
+    }
+    if (SIG & SIG_ERR) block_partials(esum, ecnt, P.part_sum, P.part_cnt, bid);
 }
 
 // FP32 fast path with plain global loads (any grid, 2D or 3D).

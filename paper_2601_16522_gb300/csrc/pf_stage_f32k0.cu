@@ -10,7 +10,57 @@ int launch_f32k0(const Geom &g, const Pass<float> &P, unsigned sig, cudaStream_t
     *done = true;
     const size_t smf = sizeof(ListSmem<float>);
     const size_t smt = 1024 + sizeof(TmaSmem) + sizeof(ListSmem<float>);
-    if (g.N <= 32 && g.Vs * (long long)(g.N + g.K) < 0x7fffffffLL) {
+    if (g.N > 32 && g.N <= 250 && g.Vs < 0x7fffffffLL) {
+        if (g.dim == 2 && sig == (SIG_PROJECT)) {
+            big_kernel<2, 0, SIG_PROJECT><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+            return (int)cudaGetLastError();
+        }
+        if (g.dim == 2 && sig == (SIG_P2 | SIG_PROJECT)) {
+            big_kernel<2, 0, SIG_P2 | SIG_PROJECT><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+            return (int)cudaGetLastError();
+        }
+        if (g.dim == 2 && sig == (SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT)) {
+            big_kernel<2, 0, SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+            return (int)cudaGetLastError();
+        }
+        if (g.dim == 2 && sig == (SIG_R0OUT | SIG_PROJECT)) {
+            big_kernel<2, 0, SIG_R0OUT | SIG_PROJECT><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+            return (int)cudaGetLastError();
+        }
+        if (g.dim == 2 && sig == (SIG_ERR)) {
+            big_kernel<2, 0, SIG_ERR><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+            return (int)cudaGetLastError();
+        }
+        if (g.dim == 2 && sig == (SIG_P0 | SIG_PROJECT)) {
+            big_kernel<2, 0, SIG_P0 | SIG_PROJECT><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+            return (int)cudaGetLastError();
+        }
+        if (g.dim == 3 && sig == (SIG_PROJECT)) {
+            big_kernel<3, 0, SIG_PROJECT><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+            return (int)cudaGetLastError();
+        }
+        if (g.dim == 3 && sig == (SIG_P2 | SIG_PROJECT)) {
+            big_kernel<3, 0, SIG_P2 | SIG_PROJECT><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+            return (int)cudaGetLastError();
+        }
+        if (g.dim == 3 && sig == (SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT)) {
+            big_kernel<3, 0, SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+            return (int)cudaGetLastError();
+        }
+        if (g.dim == 3 && sig == (SIG_R0OUT | SIG_PROJECT)) {
+            big_kernel<3, 0, SIG_R0OUT | SIG_PROJECT><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+            return (int)cudaGetLastError();
+        }
+        if (g.dim == 3 && sig == (SIG_ERR)) {
+            big_kernel<3, 0, SIG_ERR><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+            return (int)cudaGetLastError();
+        }
+        if (g.dim == 3 && sig == (SIG_P0 | SIG_PROJECT)) {
+            big_kernel<3, 0, SIG_P0 | SIG_PROJECT><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+            return (int)cudaGetLastError();
+        }
+    }
+    if (g.N <= 32 && g.Vs < 0x7fffffffLL) {
         if (tma && g.dim == 3 && g.N > 4) {
             if (sig == (SIG_PROJECT)) {
                 tma_kernel<0, SIG_PROJECT><<<grid, TMA_BLOCK, smt, st>>>(g, P, *tma, A, B, L, ptype);
@@ -156,6 +206,18 @@ int prepare_f32k0()
 {
     const int smf = (int)sizeof(ListSmem<float>);
     const int smt = (int)(1024 + sizeof(TmaSmem) + sizeof(ListSmem<float>));
+    if (cudaFuncSetAttribute(big_kernel<2, 0, SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(big_kernel<2, 0, SIG_P2 | SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(big_kernel<2, 0, SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(big_kernel<2, 0, SIG_R0OUT | SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(big_kernel<2, 0, SIG_ERR>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(big_kernel<2, 0, SIG_P0 | SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(big_kernel<3, 0, SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(big_kernel<3, 0, SIG_P2 | SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(big_kernel<3, 0, SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(big_kernel<3, 0, SIG_R0OUT | SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(big_kernel<3, 0, SIG_ERR>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(big_kernel<3, 0, SIG_P0 | SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(tma_kernel<0, SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smt) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(tma_kernel<0, SIG_P2 | SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smt) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(tma_kernel<0, SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smt) != cudaSuccess) return -1;

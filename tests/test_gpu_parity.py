@@ -322,3 +322,23 @@ def test_fixed_step_graph_replay_is_identical(pf, integ, mult, prec):
     np.testing.assert_array_equal(res[0][0], res[1][0])
     assert res[0][1:] == res[1][1:]
     assert res[0][3] == 38
+
+
+@pytest.mark.parametrize("case,integ,mult", [(5, ref.FEULER, 0.9), (5, ref.RKL2, 8.0), (5, ref.RKL1, 6.0),
+                                             (5, ref.SSP2, 2.0), (6, ref.FEULER, 0.9)],
+                         ids=["N33-fe", "N33-rkl2", "N33-rkl1", "N33-ssp2", "N70-fe"])
+def test_fp32_step_many_phases(pf, case, integ, mult):
+    # N > 32 takes the chunked FP32 kernel; compared with the FP64 oracle
+    # started from the same FP32-rounded state.
+    name, prob, u = CASES[case]
+    u = u.astype(np.float32).astype(np.float64)
+    o = ref.Oracle(prob)
+    dte = o.dt_e()
+    dt = mult * dte
+    s = ref.sts_stages(integ, dt, dte) if integ in (ref.RKL1, ref.RKL2) else 5
+    un_ref, _, _, _ = o.step(integ, dt, s, u)
+    with pf.Simulation(prob, precision=32) as sim:
+        sim.set_state(u)
+        sim.step(integ, dt, dt_mult=mult)
+        ug, _ = sim.get_state()
+    assert relerr(ug, un_ref, prob.n_phases, prob.has_conc) < 1e-4
