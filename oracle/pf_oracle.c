@@ -239,6 +239,45 @@ double or_dt_e(const or_params *p)
     return 2.0 / lam;
 }
 
+double or_energy(const or_params *p, const double *u)
+{
+    int N = p->N;
+    long V = or_ncells(p);
+    double *A = malloc(sizeof(double) * N * N), *B = malloc(sizeof(double) * N * N),
+           *L = malloc(sizeof(double) * N * N), *phc = malloc(sizeof(double) * N),
+           *grad = malloc(sizeof(double) * N * 3);
+    or_coeffs(p, A, B, L);
+    double dv = pow(p->dx, p->dim), total = 0.0;
+    for (int z = 0; z < p->nz; ++z)
+    for (int y = 0; y < p->ny; ++y)
+    for (int x = 0; x < p->nx; ++x) {
+        long i = ((long)z * p->ny + y) * p->nx + x;
+        for (int a = 0; a < N; ++a) {
+            phc[a] = u[a * V + i];
+            for (int ax = 0; ax < p->dim; ++ax) {
+                long j = neighbour(p, x, y, z, 2 * ax + 1);
+                double vn = j >= 0 ? u[a * V + j] : phc[a];
+                grad[a * 3 + ax] = (vn - phc[a]) / p->dx;
+            }
+        }
+        double e = 0.0;
+        for (int a = 0; a < N; ++a)
+            for (int b = 0; b < a; ++b) {
+                double gg = 0.0;
+                for (int ax = 0; ax < p->dim; ++ax) gg = gg + grad[a * 3 + ax] * grad[b * 3 + ax];
+                e = e - A[a * N + b] * gg;
+                e = e + B[a * N + b] * phc[a] * phc[b];
+            }
+        if (p->K) {
+            double mu = chem_mu(p, u[N * V + i], phc);
+            for (int a = 0; a < N; ++a) e = e + phc[a] * (mu * mu / (2.0 * p->k[p->ptype[a]]));
+        }
+        total = total + e;
+    }
+    free(A); free(B); free(L); free(phc); free(grad);
+    return total * dv;
+}
+
 void or_reduce(const or_params *p, const double *u, double *mass, double *vol, int *alive)
 {
     long V = or_ncells(p);

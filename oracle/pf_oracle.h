@@ -72,6 +72,12 @@ int or_rhs(const or_params *p, const double *u, double *r, unsigned char *nz);
 int or_project(const or_params *p, double *u, unsigned char *acted);
 /* Stable explicit Euler step from the Gershgorin reading (Sec. 3.2). */
 double or_dt_e(const or_params *p);
+/* Energy functional F = int a + w + f dV (Eq. energy) with forward
+   differences across the +x, +y, +z faces of every cell for the gradients:
+   a = -sum_{a>b} A_ab grad phi_a . grad phi_b, w = sum_{a>b} B_ab phi_a phi_b,
+   f = sum_a phi_a g_a(c_a) = sum_a phi_a mu^2/(2 k_a) (K = 1).  The ghost
+   value across a non-periodic face is the cell itself (zero gradient). */
+double or_energy(const or_params *p, const double *u);
 /* Totals (Sec. 5.2 area by integration): sum c dV, sum phi_a dV, #phases with max >= 0.5. */
 void or_reduce(const or_params *p, const double *u, double *mass, double *vol, int *alive);
 

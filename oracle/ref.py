@@ -62,6 +62,8 @@ def lib():
         L.or_dt_e.argtypes = [C.POINTER(_Params)]
         L.or_dt_e.restype = C.c_double
         L.or_reduce.argtypes = [C.POINTER(_Params), _dp, _dp, _dp, _ip]
+        L.or_energy.argtypes = [C.POINTER(_Params), _dp]
+        L.or_energy.restype = C.c_double
         L.or_coeffs.argtypes = [C.POINTER(_Params), _dp, _dp, _dp]
         L.or_sys_pde.argtypes = [C.POINTER(_Sys), C.POINTER(_Params)]
         L.or_sys_dahlquist.argtypes = [C.POINTER(_Sys), _dp]
@@ -153,6 +155,9 @@ class Oracle:
 
     def dt_e(self):
         return lib().or_dt_e(C.byref(self.p))
+
+    def energy(self, u):
+        return lib().or_energy(C.byref(self.p), _d(self._u(u)))
 
     def reduce(self, u):
         u = self._u(u)

@@ -414,3 +414,36 @@ def test_stefan_growth_constant_and_front():
     assert abs(Afit - A) / A < 0.03, Afit
     # concentration is not conserved here (Dirichlet faces) but phases are on the simplex
     assert np.abs(u[:2].sum(0) - 1).max() < 1e-13
+
+
+def test_energy_of_flat_profile_is_gamma():
+    # Sec. 2: A and B are fixed so that the energy of a flat equilibrium
+    # profile integrates to gamma per unit interface area; the FD value
+    # converges to it as dx/W -> 0.
+    errs = []
+    for W, dx, g in [(4.0, 1.0, 1.3), (4.0, 0.5, 1.3), (4.0, 0.25, 1.3)]:
+        n = int(round(24 * W / dx)) * 2
+        prob = I.Problem(dim=2, nx=n, ny=3, nz=1, dx=dx, n_phases=2, phase_type=np.array([0, 0], np.int32),
+                         gamma=I.uniform_pairs(2, g), mobility=I.uniform_pairs(2, 1.0), W=W,
+                         bc_phi=(1, 1, 0, 0, 0, 0))
+        x = (np.arange(n) + 0.5) * dx - n * dx / 2
+        ph = np.tile(I.profile(x, W), 3)
+        F = ref.Oracle(prob).energy(np.stack([1 - ph, ph]))
+        per_area = F / (3 * dx)              # interface area = height of the strip
+        errs.append(abs(per_area - g) / g)
+    assert errs[-1] < 2e-3
+    assert errs[0] > errs[1] > errs[2]
+
+
+def test_energy_decreases_under_curvature_flow():
+    # gradient flow (Q1 sign): the energy of the shrinking circle decreases
+    prob, u = I.circle(48, 14.0, W=2.5)
+    o = ref.Oracle(prob)
+    Fs = [o.energy(u)]
+    t = 0.0
+    for k in range(5):
+        st, u, t, _ = o.run(ref.FEULER, u, t, t + 10.0, dt_mult=0.9)
+        Fs.append(o.energy(u))
+    assert all(b < a for a, b in zip(Fs, Fs[1:]))
+    # a circle of radius R carries about 2 pi R gamma
+    assert Fs[0] == pytest.approx(2 * math.pi * 14.0, rel=0.05)
