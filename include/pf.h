@@ -168,6 +168,18 @@ int pf_get_state(struct pf_handle *h, double *phi, double *c, unsigned char *nz,
    grains_alive = number of phases whose maximum is >= 0.5 (may be NULL). */
 int pf_reduce(struct pf_handle *h, double *mass_c, double *vol_phi, int *grains_alive);
 
+/* Energy functional F = int a + w + f dV of Eq. energy (Sec. 2) of the
+   current state, evaluated in FP64 whatever the storage precision, written to
+   the host double *F (deterministic for a given state and launch shape).
+   a = -sum_{a>b} A_ab grad phi_a . grad phi_b with forward differences across
+   the +x, +y, +z faces of each cell (a zero-gradient ghost across a
+   non-periodic face), w = sum_{a>b} B_ab phi_a phi_b (the state is on the
+   simplex), f = sum_a phi_a g_a(c_a) with the KKS phase concentrations
+   (K = 1; absent when K = 0).  Phases that are zero at a cell and at its
+   three forward neighbours contribute nothing; PF_EINVAL if more than 32
+   phases are present around one cell.  Synchronises the handle's stream. */
+int pf_energy(struct pf_handle *h, double *F);
+
 /* Stable explicit Euler step dt_e = 2 / max(lambda_phi, lambda_c) from the
    Gershgorin reading of Sec. 3.2 (the estimates themselves are in the
    paper's supplement; the reading reproduces the three values printed in

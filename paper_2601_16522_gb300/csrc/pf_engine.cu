@@ -113,6 +113,81 @@ __global__ void totals_kernel(const T *__restrict__ u, long long V, long long Vs
     }
 }
 
+
+// Energy functional of Eq. energy, one cell per thread, accumulated in FP64.
+// The gradients are forward differences across the +x, +y, +z faces (a
+// zero-gradient ghost across a non-periodic face).  Only phases that are
+// nonzero at the cell or at one of those three neighbours contribute (every
+// other term is an exact zero); they are listed in ascending order, up to
+// EMAX of them, and a cell with more counts as an overflow.  Per cell:
+//   e = sum_{a>b} (-A_ab grad phi_a . grad phi_b + B_ab phi_a phi_b)
+//     + sum_a phi_a mu^2 / (2 k_a)                     (K = 1, KKS, Sec. 2)
+constexpr int EMAX = 32;
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+energy_kernel(const Geom g, const T *__restrict__ u, const double *__restrict__ A, const double *__restrict__ B,
+              const signed char *__restrict__ ptype, double dx, double *ps, long long *pc)
+{
+    unsigned char id[EMAX];
+    double ph[EMAX], gr[EMAX][3];
+    double esum = 0.0;
+    long long over = 0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < g.V; i += stride) {
+        const int x = (int)(i % g.nx);
+        const int y = (int)((i / g.nx) % g.ny);
+        const int z = (int)(i / ((long long)g.nx * g.ny));
+        long long off[6];
+        int ghost[6];
+        pfk::face_offsets(g, x, y, z, off, ghost);
+        int n = 0;
+        bool full = false;
+        for (int a = 0; a < g.N; ++a) {
+            const T *f = u + (long long)a * g.Vs + i;
+            const double v = (double)f[0];
+            double d[3] = {0.0, 0.0, 0.0};
+            bool any = v != 0.0;
+            for (int ax = 0; ax < g.dim; ++ax) {
+                const double w = ghost[2 * ax + 1] ? v : (double)f[off[2 * ax + 1]];
+                any = any || w != 0.0;
+                d[ax] = __dsub_rn(w, v) / dx;
+            }
+            if (!any) continue;
+            if (n == EMAX) { full = true; break; }
+            id[n] = (unsigned char)a;
+            ph[n] = v;
+            gr[n][0] = d[0]; gr[n][1] = d[1]; gr[n][2] = d[2];
+            ++n;
+        }
+        if (full) { ++over; continue; }
+        double e = 0.0;
+        for (int p = 0; p < n; ++p) {
+            const long long ra = (long long)id[p] * g.N;
+            for (int q = 0; q < p; ++q) {
+                double gg = 0.0;
+                for (int ax = 0; ax < g.dim; ++ax) gg = __dadd_rn(gg, __dmul_rn(gr[p][ax], gr[q][ax]));
+                e = __dsub_rn(e, __dmul_rn(A[ra + id[q]], gg));
+                e = __dadd_rn(e, __dmul_rn(__dmul_rn(B[ra + id[q]], ph[p]), ph[q]));
+            }
+        }
+        if (g.K) {
+            double num = (double)u[(long long)g.N * g.Vs + i], den = 0.0;
+            for (int p = 0; p < n; ++p) {
+                const int t = ptype[id[p]];
+                num = __dsub_rn(num, __dmul_rn(ph[p], g.c0[t]));
+                den = __dadd_rn(den, __dmul_rn(ph[p], g.invk[t]));
+            }
+            const double mu = num / den;
+            for (int p = 0; p < n; ++p) {
+                const int t = ptype[id[p]];
+                e = __dadd_rn(e, __dmul_rn(ph[p], __dmul_rn(mu, mu) / __dmul_rn(2.0, g.k[t])));
+            }
+        }
+        esum = __dadd_rn(esum, e);
+    }
+    pfk::block_partials(esum, over, ps, pc, blockIdx.x);
+}
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -131,6 +206,7 @@ struct pf_handle {
     std::vector<int> ptype;
     std::vector<double> A, B, L;
     void *dA = nullptr, *dB = nullptr, *dL = nullptr;
+    double *dAB64 = nullptr;           // A then B in FP64 (energy functional)
     signed char *dptype = nullptr;
     void *buf[NBUF] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     int iu = 0;                        // buffer holding u^n
@@ -848,7 +924,7 @@ void free_all(pf_handle *h)
     for (cudaEvent_t ev : h->ev_pool) cudaEventDestroy(ev);
     h->ev_pool.clear();
     for (int k = 0; k < NBUF; ++k) if (h->buf[k]) cudaFreeAsync(h->buf[k], h->stream);
-    void *ps[] = {h->dA, h->dB, h->dL, h->dptype, h->staging, h->dnz, h->part_sum, h->part_cnt,
+    void *ps[] = {h->dA, h->dB, h->dL, h->dAB64, h->dptype, h->staging, h->dnz, h->part_sum, h->part_cnt,
                   h->dres, h->dcnt, h->dflag, h->tot_sum, h->tot_max};
     for (void *p : ps) if (p) cudaFreeAsync(p, h->stream);
     cudaStreamSynchronize(h->stream);
@@ -1012,6 +1088,7 @@ int pf_create(const pf_params *p, void *cuda_stream, pf_handle **out)
     ok = ok && dmalloc(h, &h->dB, h->esize * N * N);
     ok = ok && dmalloc(h, &h->dL, h->esize * N * N);
     ok = ok && dmalloc(h, &h->dptype, N);
+    ok = ok && dmalloc(h, &h->dAB64, sizeof(double) * 2 * N * N);
     ok = ok && dmalloc(h, &h->part_sum, sizeof(double) * h->grid);
     ok = ok && dmalloc(h, &h->part_cnt, sizeof(long long) * h->grid);
     ok = ok && dmalloc(h, &h->dres, sizeof(double));
@@ -1031,6 +1108,9 @@ int pf_create(const pf_params *p, void *cuda_stream, pf_handle **out)
     st |= cudaMemcpyAsync(h->dB, tb, h->esize * N * N, cudaMemcpyHostToDevice, h->stream);
     st |= cudaMemcpyAsync(h->dL, tl, h->esize * N * N, cudaMemcpyHostToDevice, h->stream);
     st |= cudaMemcpyAsync(h->dptype, pt.data(), N, cudaMemcpyHostToDevice, h->stream);
+    st |= cudaMemcpyAsync(h->dAB64, h->A.data(), sizeof(double) * N * N, cudaMemcpyHostToDevice, h->stream);
+    st |= cudaMemcpyAsync(h->dAB64 + (size_t)N * N, h->B.data(), sizeof(double) * N * N, cudaMemcpyHostToDevice,
+                          h->stream);
     st |= cudaMemsetAsync(h->dflag, 0, sizeof(int), h->stream);
     st |= cudaStreamSynchronize(h->stream);
     if (st != 0) { free_all(h); delete h; return PF_EDEVICE; }
@@ -1063,6 +1143,7 @@ int pf_footprint(const pf_params *p, long long *bytes)
     long long b = (long long)NBUF * NF * Vs * es;          // state vectors
     b += NF * V * 8;                                       // ABI staging buffer (allocated on first set/get)
     b += 3LL * p->n_phases * p->n_phases * es + p->n_phases;   // coefficient tables, phase types
+    b += 2LL * p->n_phases * p->n_phases * 8;              // FP64 A and B for the energy functional
     b += tiles * 16 + 2 * tot_blocks * NF * 8 + 64;       // reduction partials
     *bytes = b;
     return PF_OK;
@@ -1241,6 +1322,36 @@ int pf_reduce(pf_handle *h, double *mass_c, double *vol_phi, int *grains_alive)
     }
     if (mass_c && !h->K) *mass_c = 0.0;
     if (grains_alive) *grains_alive = alive;
+    return PF_OK;
+}
+
+int pf_energy(pf_handle *h, double *F)
+{
+    if (!h || !F) return PF_EINVAL;
+    if (!h->has_state) return PF_ESTATE;
+    const long long want = (h->V + 255) / 256;
+    const int nblk = (int)(want < h->grid ? want : h->grid);
+    if (h->prec == 64)
+        energy_kernel<double><<<nblk, 256, 0, h->stream>>>(h->g, (const double *)h->buf[h->iu], h->dAB64,
+                                                          h->dAB64 + (size_t)h->N * h->N, h->dptype, h->dx,
+                                                          h->part_sum, h->part_cnt);
+    else
+        energy_kernel<float><<<nblk, 256, 0, h->stream>>>(h->g, (const float *)h->buf[h->iu], h->dAB64,
+                                                         h->dAB64 + (size_t)h->N * h->N, h->dptype, h->dx,
+                                                         h->part_sum, h->part_cnt);
+    h->launches++;
+    finalize_err_kernel<<<1, 256, 0, h->stream>>>(h->part_sum, h->part_cnt, nblk, h->dres, h->dcnt);
+    h->launches++;
+    if (cudaGetLastError() != cudaSuccess) return PF_EDEVICE;
+    double sum = 0.0;
+    long long over = 0;
+    if (cudaMemcpyAsync(&sum, h->dres, sizeof(double), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+        return PF_EDEVICE;
+    if (cudaMemcpyAsync(&over, h->dcnt, sizeof(long long), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+        return PF_EDEVICE;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return PF_EDEVICE;
+    if (over) return PF_EINVAL;
+    *F = sum * pow(h->dx, h->g.dim);
     return PF_OK;
 }
 

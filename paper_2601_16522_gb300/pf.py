@@ -77,6 +77,7 @@ def _lib():
                               C.POINTER(pf_stats)]
         L.pf_get_state.argtypes = [H, C.c_void_p, C.c_void_p, C.c_void_p, _dp, C.c_int]
         L.pf_reduce.argtypes = [H, _dp, _dp, _ip]
+        L.pf_energy.argtypes = [H, _dp]
         L.pf_dt_e.argtypes = [H, _dp]
         L.pf_destroy.argtypes = [H]
         L.pf_profile.argtypes = [H, C.c_int, _dp, C.POINTER(C.c_longlong)]
@@ -286,3 +287,9 @@ class Simulation:
         alive = C.c_int()
         _check(_lib().pf_reduce(self.h, C.byref(m), vol.ctypes.data_as(_dp), C.byref(alive)), "pf_reduce")
         return m.value, vol, alive.value
+
+    def energy(self):
+        """Energy functional F of the current state (Eq. energy), FP64."""
+        F = C.c_double()
+        _check(_lib().pf_energy(self.h, C.byref(F)), "pf_energy")
+        return F.value
