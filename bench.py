@@ -129,6 +129,18 @@ def barrier(world):
         dist.barrier()
 
 
+def kernel_name(prob, prec, tma):
+    """Which stage kernel the library dispatches for this problem."""
+    K = prob.has_conc
+    if prec == 64:
+        return "cell_kernel<double,%d,%d,generic>" % (prob.dim, K)
+    if prob.n_phases > 32:
+        return "big_kernel<%d,%d,sig>" % (prob.dim, K)
+    if tma and prob.dim == 3 and prob.n_phases > 4:
+        return "tma_kernel<%d,sig>" % K
+    return "fast_kernel<%d,%d,sig,%d>" % (prob.dim, K, 4 if prob.n_phases <= 4 else 32)
+
+
 def max_over_ranks(x, world, device=None):
     """Maximum of a host scalar over the ranks (the timing rule for N > 1)."""
     if world == 1:
@@ -404,8 +416,8 @@ def run_ours(args, world, rank, local):
                 and not (tuned and tuned["choice"] == "tma")):
             traffic = RKL2_TRAFFIC_PER_CELL[args.workload] * V
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": ("tma_kernel<0,sig>" if (tuned and tuned["choice"] == "tma") or args.tma
-                           else "fast_kernel<3,0,sig,32>") + " (%s pass)" % dom,
+                "traffic": traffic, "kernel": kernel_name(prob, prec, (tuned and tuned["choice"] == "tma") or args.tma)
+                + " (%s pass)" % dom,
                 "bytes_per_launch": bytes_launch, "avg_launch_ms": ms_k / n_k,
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
     pass_ms = {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items() if v[1] > 0}
