@@ -341,6 +341,43 @@ def served_stream(pf, torch, n_requests, rate=50.0):
     return s
 
 
+def masked_run(pf, torch, prob, u, stream, args, world, dev, dense_out, dense_pass_ms):
+    """The bench steps again in masked storage (PF_OPT_MASKED) from the same
+    initial state: GCell-updates/s, per-pass times, and whether the final
+    state equals the dense run's."""
+    V, N = prob.V, prob.n_phases
+    sim = pf.Simulation(prob, precision=32, stream=stream, options=pf.Simulation.OPT_MASKED)
+    sim.set_state(u)
+    for _ in range(args.warmup):
+        sim.step(pf.RKL2, 1e30, tol=TOL, max_attempts=1)
+    torch.cuda.synchronize()
+    barrier(world)
+    sim.profile(1)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    sweeps = 0
+    for _ in range(args.steps):
+        sweeps += sim.step(pf.RKL2, 1e30, tol=TOL, max_attempts=1)["rhs_evals"]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(ev0.elapsed_time(ev1), world, dev)
+    prof = sim.profile(0)
+    out = torch.empty_like(dense_out)
+    sim.get_state(out=out)
+    equal = bool(torch.equal(out, dense_out))
+    sim.close()
+    occ = float((u[:N] != 0).sum(0, dtype=torch.float64).mean())
+    pass_ms = {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items() if v[1] > 0}
+    rk = pass_ms.get("rkl2")
+    dk = dense_pass_ms.get("rkl2")
+    return {"value": aggregate_value(V, sweeps, ms, world), "unit": UNIT, "ms_per_step": ms / args.steps,
+            "sweeps": sweeps, "pass_ms": pass_ms, "equal_to_dense": equal,
+            "rkl2_pass_speedup": (dk["ms"] / dk["launches"]) / (rk["ms"] / rk["launches"]) if rk and dk else None,
+            "mean_nonzero_phases_per_cell": occ,
+            "storage": "dense phase planes + one 32-bit occupancy word per cell and vector"}
+
+
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
@@ -422,6 +459,15 @@ def run_ours(args, world, rank, local):
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
     pass_ms = {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items() if v[1] > 0}
 
+    # masked storage (the GPU form of the per-cell phase lists): the same
+    # steps from the same state; its result must equal the dense one
+    masked = None
+    if not args.no_masked and prec == 32 and N <= 32:
+        dense_out = torch.empty((N + prob.has_conc, V), dtype=torch.float64, device=dev)
+        sim.get_state(out=dense_out)
+        masked = masked_run(pf, torch, prob, u, stream, args, world, dev, dense_out, pass_ms)
+        del dense_out
+
     # end-to-end through the C ABI with pinned host buffers
     e2e = None
     if not args.no_e2e:
@@ -480,7 +526,7 @@ def run_ours(args, world, rank, local):
             "sweeps": sweeps, "stages_per_step": ss, "accepted": acc,
             "roofline": roof, "pass_ms": pass_ms,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
-            "time_to_solution": tts, "served": served,
+            "time_to_solution": tts, "served": served, "masked": masked,
         }
         print(json.dumps(line), flush=True)
     sim.close()
@@ -498,6 +544,7 @@ def main():
     ap.add_argument("--tma", action="store_true", help="TMA-staged kernels instead of plain loads")
     ap.add_argument("--no-tts", action="store_true", help="skip the 2D time-to-solution runs")
     ap.add_argument("--served", type=int, default=48, help="requests in the served Poisson stream (0: skip)")
+    ap.add_argument("--no-masked", action="store_true", help="skip the masked-storage run")
     args = ap.parse_args()
     world, rank, local = dist_setup(args)
     if args.impl == "reference":

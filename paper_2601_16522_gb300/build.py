@@ -1,8 +1,10 @@
 """Build libpf.so (the sm_103a engine) in-tree with nvcc.
 
-Three translation units compile in parallel: the FP64 stage pass (built with
+The translation units compile in parallel: the FP64 stage pass (built with
 ``--fmad=false`` so its arithmetic is exactly the written sequence of
-IEEE operations), the FP32 stage pass (FMA contraction on) and the host engine.
+IEEE operations), the FP32 stage passes for K = 0 and K = 1 in dense and
+masked storage (FMA contraction on), the dispatch, the allocation-free totals
+and the host engine.
 """
 import os
 import subprocess
@@ -19,6 +21,8 @@ UNITS = [
     ("pf_stage_f64.cu", ["--fmad=false"]),
     ("pf_stage_f32k0.cu", ["--fmad=true"]),
     ("pf_stage_f32k1.cu", ["--fmad=true"]),
+    ("pf_stage_m32k0.cu", ["--fmad=true"]),
+    ("pf_stage_m32k1.cu", ["--fmad=true"]),
     ("pf_dispatch.cu", ["--fmad=false"]),
     ("pf_noalloc.cu", ["--fmad=false"]),
     ("pf_engine.cu", ["--fmad=false"]),

@@ -9,9 +9,15 @@ int launch_f32k0(const Geom &, const Pass<float> &, unsigned, cudaStream_t, cons
                  const float *, const signed char *, const TmaMaps *, bool *);
 int launch_f32k1(const Geom &, const Pass<float> &, unsigned, cudaStream_t, const float *, const float *,
                  const float *, const signed char *, const TmaMaps *, bool *);
+int launch_m32k0(const Geom &, const Pass<float> &, unsigned, cudaStream_t, const float *, const float *,
+                 const float *, const signed char *, bool *);
+int launch_m32k1(const Geom &, const Pass<float> &, unsigned, cudaStream_t, const float *, const float *,
+                 const float *, const signed char *, bool *);
 int prepare_f64();
 int prepare_f32k0();
 int prepare_f32k1();
+int prepare_m32k0();
+int prepare_m32k1();
 
 template <>
 int launch_stage<double>(const Geom &g, const Pass<double> &P, cudaStream_t st, const double *A, const double *B,
@@ -28,6 +34,13 @@ int launch_stage<float>(const Geom &g, const Pass<float> &P, cudaStream_t st, co
                         const float *L, const signed char *ptype, const TmaMaps *tma)
 {
     bool done = false;
+    if (P.m_in) {
+        // masked storage: only the masked instantiations maintain the masks
+        const unsigned sig = pass_signature(P);
+        int e = g.K ? launch_m32k1(g, P, sig, st, A, B, L, ptype, &done)
+                    : launch_m32k0(g, P, sig, st, A, B, L, ptype, &done);
+        return done ? e : (int)cudaErrorInvalidValue;
+    }
     auto go = [&](unsigned sig) {
         return g.K ? launch_f32k1(g, P, sig, st, A, B, L, ptype, tma, &done)
                    : launch_f32k0(g, P, sig, st, A, B, L, ptype, tma, &done);
@@ -43,8 +56,8 @@ int prepare_stage<double>() { return prepare_f64(); }
 template <>
 int prepare_stage<float>()
 {
-    const int a = prepare_f32k0(), b = prepare_f32k1();
-    return (a > 0 && b > 0) ? a : -1;
+    const int a = prepare_f32k0(), b = prepare_f32k1(), c = prepare_m32k0(), d = prepare_m32k1();
+    return (a > 0 && b > 0 && c > 0 && d > 0) ? a : -1;
 }
 
 }  // namespace pfk

@@ -82,6 +82,18 @@ __global__ void finalize_err_kernel(const double *__restrict__ ps, const long lo
     if (threadIdx.x == 0) { *out_sum = ss[0]; *out_cnt = sc[0]; }
 }
 
+// Occupancy masks of an FP32 state (masked storage): bit a of cell i is set
+// where phase a is nonzero.
+__global__ void mask_kernel(const float *__restrict__ u, unsigned *__restrict__ m, long long V, long long Vs, int N)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < V; i += (long long)gridDim.x * blockDim.x) {
+        unsigned w = 0u;
+        for (int a = 0; a < N; ++a)
+            if (u[(long long)a * Vs + i] != 0.0f) w |= 1u << a;
+        m[i] = w;
+    }
+}
+
 // Per-field totals: block (b, f) sums / maximises field f over a fixed cell range.
 template <typename T>
 __global__ void totals_kernel(const T *__restrict__ u, long long V, long long Vs, double *psum, double *pmax)
@@ -220,6 +232,7 @@ struct pf_handle {
     int *dflag = nullptr;
     double *tot_sum = nullptr, *tot_max = nullptr;
     int tot_blocks = 0;
+    bool masked = false;               // masked storage: an occupancy-mask plane after the fields
     bool tma_ok = false;               // tensor maps built: TMA-staged kernels available
     bool tma = false;                  // TMA-staged FP32 kernels in use
     CUtensorMap m3[NBUF], m1[NBUF];    // per buffer: 3-plane and 1-plane boxes
@@ -325,6 +338,30 @@ int buf_index(const pf_handle *h, const void *p)
     return -1;
 }
 
+// Occupancy-mask plane of a state vector (masked storage): Vs words after
+// the NP fields.
+unsigned *mask_plane(const pf_handle *h, const void *vecp)
+{
+    return vecp ? (unsigned *)((char *)const_cast<void *>(vecp) + (size_t)h->Vs * h->NP * h->esize) : nullptr;
+}
+
+// Pass signatures that have a masked instantiation.
+bool masked_sig(unsigned s)
+{
+    using namespace pfk;
+    return s == SIG_PROJECT || s == (SIG_P2 | SIG_PROJECT) || s == (SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT) ||
+           s == (SIG_R0OUT | SIG_PROJECT) || s == SIG_ERR || s == (SIG_P0 | SIG_PROJECT);
+}
+
+// After a pass that wrote a state vector without maintaining its mask, mark
+// every phase of it as possibly nonzero.
+int invalidate_mask(pf_handle *h, const void *vecp)
+{
+    if (!vecp || buf_index(h, vecp) < 0) return PF_OK;
+    return cudaMemsetAsync(mask_plane(h, vecp), 0xff, sizeof(unsigned) * (size_t)h->Vs, h->stream) == cudaSuccess
+               ? PF_OK : PF_EDEVICE;
+}
+
 template <typename T>
 int run_pass(pf_handle *h, const Pass<T> &P)
 {
@@ -344,10 +381,30 @@ int run_pass(pf_handle *h, const Pass<T> &P)
             tmp = &tm;
         }
     }
+    if (h->masked && P.mode != pfk::MODE_RHS && masked_sig(pfk::pass_signature(P))) {
+        Pass<T> Q = P;
+        Q.m_in = mask_plane(h, P.in);
+        Q.m_p0 = mask_plane(h, P.p0);
+        Q.m_p2 = mask_plane(h, P.p2);
+        Q.m_r0 = mask_plane(h, P.r0in);
+        Q.m_out = P.mode == pfk::MODE_ERR ? nullptr : mask_plane(h, P.out);
+        Q.m_r0out = mask_plane(h, P.r0out);
+        int e = pfk::launch_stage<T>(h->g, Q, h->stream, (const T *)h->dA, (const T *)h->dB, (const T *)h->dL,
+                                     h->dptype, nullptr);
+        h->launches++;
+        if (e != 0) return PF_EDEVICE;
+        return prof_end(h);
+    }
     int e = pfk::launch_stage<T>(h->g, P, h->stream, (const T *)h->dA, (const T *)h->dB, (const T *)h->dL,
                                  h->dptype, tmp);
     h->launches++;
     if (e != 0) return PF_EDEVICE;
+    if (h->masked && P.mode != pfk::MODE_RHS) {
+        // a dense pass (generic kernel) wrote these vectors: their masks are stale
+        const void *outs[] = {P.out, P.r0out, P.zout, P.out2};
+        for (const void *o : outs)
+            if ((st = invalidate_mask(h, o))) return st;
+    }
     return prof_end(h);
 }
 
@@ -865,6 +922,11 @@ int set_state_t(pf_handle *h, const double *src_dev)
 {
     pack_kernel<T><<<grid_for(h->V * h->NP), 256, 0, h->stream>>>(src_dev, (T *)h->buf[h->iu], h->V, h->Vs, h->NP);
     h->launches++;
+    if (h->masked) {
+        mask_kernel<<<grid_for(h->V), 256, 0, h->stream>>>((const float *)h->buf[h->iu], mask_plane(h, h->buf[h->iu]),
+                                                           h->V, h->Vs, h->N);
+        h->launches++;
+    }
     return cuda_status(cudaGetLastError());
 }
 
@@ -1081,7 +1143,12 @@ int pf_create(const pf_params *p, void *cuda_stream, pf_handle **out)
     h->tot_blocks = (int)((h->V + 4095) / 4096 < 1024 ? (h->V + 4095) / 4096 : 1024);
     if (h->tot_blocks < 1) h->tot_blocks = 1;
 
-    h->vec_bytes = (size_t)h->Vs * NP * h->esize;
+    if (p->options & PF_OPT_MASKED) {
+        // masked storage: FP32, at most 32 phases (one mask word per cell)
+        if (p->precision != 32 || p->n_phases > 32) { delete h; return PF_EINVAL; }
+        h->masked = true;
+    }
+    h->vec_bytes = (size_t)h->Vs * NP * h->esize + (h->masked ? sizeof(unsigned) * (size_t)h->Vs : 0);
     bool ok = true;
     for (int k = 0; k < NBUF && ok; ++k) ok = dmalloc(h, &h->buf[k], h->vec_bytes);
     ok = ok && dmalloc(h, &h->dA, h->esize * N * N);
@@ -1112,10 +1179,13 @@ int pf_create(const pf_params *p, void *cuda_stream, pf_handle **out)
     st |= cudaMemcpyAsync(h->dAB64 + (size_t)N * N, h->B.data(), sizeof(double) * N * N, cudaMemcpyHostToDevice,
                           h->stream);
     st |= cudaMemsetAsync(h->dflag, 0, sizeof(int), h->stream);
+    if (h->masked)
+        for (int k = 0; k < NBUF; ++k)
+            st |= cudaMemsetAsync(mask_plane(h, h->buf[k]), 0xff, sizeof(unsigned) * (size_t)h->Vs, h->stream);
     st |= cudaStreamSynchronize(h->stream);
     if (st != 0) { free_all(h); delete h; return PF_EDEVICE; }
     // TMA-staged FP32 kernels: full 32 x 8 tiles, 3D, 5..32 phases
-    if (h->prec == 32 && p->dim == 3 && N > 4 && N <= 32 && p->nx % pfk::TX == 0 && p->ny % pfk::TY == 0 &&
+    if (h->prec == 32 && !h->masked && p->dim == 3 && N > 4 && N <= 32 && p->nx % pfk::TX == 0 && p->ny % pfk::TY == 0 &&
         p->nz >= 3 && h->Vs < 0x7fffffffLL) {
         bool ok = true;
         for (int k = 0; k < NBUF && ok; ++k)
@@ -1141,6 +1211,7 @@ int pf_footprint(const pf_params *p, long long *bytes)
     const long long tiles = (long long)((p->nx + pfk::TX - 1) / pfk::TX) * ((p->ny + pfk::TY - 1) / pfk::TY) * p->nz;
     const long long tot_blocks = (V + 4095) / 4096 < 1024 ? ((V + 4095) / 4096 > 0 ? (V + 4095) / 4096 : 1) : 1024;
     long long b = (long long)NBUF * NF * Vs * es;          // state vectors
+    if (p->options & PF_OPT_MASKED) b += (long long)NBUF * Vs * 4;   // occupancy masks
     b += NF * V * 8;                                       // ABI staging buffer (allocated on first set/get)
     b += 3LL * p->n_phases * p->n_phases * es + p->n_phases;   // coefficient tables, phase types
     b += 2LL * p->n_phases * p->n_phases * 8;              // FP64 A and B for the energy functional

@@ -72,6 +72,11 @@ struct Pass {
     double *rhs_pm;      // MODE_RHS: FP64 output, field f at rhs_pm + f * V
     unsigned char *nz_out; // MODE_RHS: N_z per cell (may be null)
     int *flag;           // device status flags
+    // Occupancy masks (masked storage, FP32 fast path, N <= 32): bit a of a
+    // cell's word is set where phase a may be nonzero; every entry whose bit
+    // is clear holds zero.  Null: dense pass.
+    const unsigned *m_in, *m_p0, *m_p2, *m_r0;
+    unsigned *m_out, *m_r0out;
 };
 
 enum { MODE_RHS = 0, MODE_STAGE = 1, MODE_ERR = 2 };
@@ -91,6 +96,10 @@ __device__ __forceinline__ T tabs(T v) { return v < (T)0 ? -v : v; }
 // Resident 256-thread blocks per SM the fast kernel's register budget targets.
 #ifndef PF_FAST_MINB
 #define PF_FAST_MINB 4
+#endif
+// ... and of its masked-storage instantiations.
+#ifndef PF_MASK_MINB
+#define PF_MASK_MINB 4
 #endif
 
 // Streaming load that does not allocate in L1 (pointwise stage inputs are
@@ -673,11 +682,11 @@ struct TmaLoader {
 // term) is final in that first loop; only the N_z listed phases receive their
 // RHS term after the pairwise sums.  Rounding order differs from the generic
 // kernel; FP32 is not compared bit for bit.
-template <int DIM, int KC, unsigned SIG, int NMAX, class LD>
+template <int DIM, int KC, unsigned SIG, int NMAX, class LD, bool MASK = false>
 __device__ __forceinline__ void fast_cell(const Geom &g, const Pass<float> &P, LD &ld, ListSmem<float> &S, int tid,
                                           long long i, const int *off, const int *ghost, const float *tabA,
                                           const float *tabB, const float *tabL, const signed char *ptype,
-                                          double &esum, long long &ecnt)
+                                          double &esum, long long &ecnt, unsigned am = 0xffffffffu)
 {
     typedef float T;
     constexpr int NFACE = 2 * DIM;
@@ -710,6 +719,28 @@ __device__ __forceinline__ void fast_cell(const Geom &g, const Pass<float> &P, L
         }
     }
 
+    // masked storage: phases that are zero at the cell, its face neighbours
+    // and the pointwise inputs are skipped (their RHS and stage value are
+    // exactly zero); entries known to be zero are not loaded
+    unsigned U = 0u, mc = 0u, mnb[NFACE], mp0 = 0u, mp2 = 0u, mr0 = 0u, mo_old = 0u, mr_old = 0u;
+    if (MASK) {
+        mc = __ldg(P.m_in + i);
+        U = mc;
+#pragma unroll
+        for (int f = 0; f < NFACE; ++f) {
+            mnb[f] = __ldg(P.m_in + i + off[f]);
+            U |= mnb[f];
+        }
+        if (HP0) { mp0 = __ldg(P.m_p0 + i); U |= mp0; }
+        if (HP2) { mp2 = __ldg(P.m_p2 + i); U |= mp2; }
+        if (HR0) { mr0 = __ldg(P.m_r0 + i); U |= mr0; }
+        if (!ERR) mo_old = P.m_out[i];
+        if (R0OUT) mr_old = P.m_r0out[i];
+        // the warp walks the union of its lanes' phases (a uniform branch);
+        // a lane whose masks lack a phase loads nothing and computes zeros
+        U = __reduce_or_sync(am, U);
+    }
+
     int nz = 0, nc = 0;
     bool changed = false;
     T best = (T)-1, ssum = (T)0;
@@ -719,11 +750,21 @@ __device__ __forceinline__ void fast_cell(const Geom &g, const Pass<float> &P, L
 #pragma unroll
     for (int a = 0; a < NMAX; ++a) {
         nv[a] = (T)0;
-        if (a < N) {
+        if (a < N && (!MASK || ((U >> a) & 1u))) {
             const long long fo = (long long)a * Vs;
             T v0, nb[NFACE], p0v = (T)0, p2v = (T)0, r0v = (T)0;
-            ld.load(a, fo, v0, nb, p0v, p2v, r0v, HP0, HP2, HR0);
-            ld.release(a);
+            if (MASK) {
+                const T *b = P.in + fo + i;
+                v0 = ((mc >> a) & 1u) ? ldg(b) : (T)0;
+#pragma unroll
+                for (int f = 0; f < NFACE; ++f) nb[f] = ((mnb[f] >> a) & 1u) ? ldg(b + off[f]) : (T)0;
+                if (HP0 && ((mp0 >> a) & 1u)) p0v = ld_stream(P.p0 + fo + i);
+                if (HP2 && ((mp2 >> a) & 1u)) p2v = ld_stream(P.p2 + fo + i);
+                if (HR0 && ((mr0 >> a) & 1u)) r0v = ld_stream(P.r0in + fo + i);
+            } else {
+                ld.load(a, fo, v0, nb, p0v, p2v, r0v, HP0, HP2, HR0);
+                ld.release(a);
+            }
             T mx = v0, mn = v0;
 #pragma unroll
             for (int f = 0; f < NFACE; ++f) {
@@ -884,9 +925,13 @@ __device__ __forceinline__ void fast_cell(const Geom &g, const Pass<float> &P, L
     const T inv = (ssum > (T)0) ? (T)1 / ssum : (T)1;
     const bool fix = R0OUT && P.fix_first && changed;
     int kr = 0;      // list cursor for the RHS of listed phases (R0OUT)
+    unsigned nmask = 0u, nrmask = 0u;
+    // masked: a phase outside U has a zero result; it is written only where
+    // the output still holds an older nonzero value
+    const unsigned touch = MASK ? __reduce_or_sync(am, U | mo_old | mr_old) : 0u;
 #pragma unroll
     for (int a = 0; a < NMAX; ++a) {
-        if (a < N) {
+        if (a < N && (!MASK || ((touch >> a) & 1u))) {
             const long long fo = (long long)a * Vs;
             T w = nv[a];
             if (PROJ) w = (bestid >= 0) ? ((a == bestid) ? (T)1 : (T)0) : w * inv;
@@ -894,10 +939,24 @@ __device__ __forceinline__ void fast_cell(const Geom &g, const Pass<float> &P, L
                 T r = (T)0;
                 if ((actmask >> a) & 1u) { r = S.lap[kr][tid]; kr++; }
                 if (fix) r = (w - ldg(P.in + fo + i)) / b1c;
-                (P.r0out + fo)[i32] = r;
+                if (!MASK) {
+                    (P.r0out + fo)[i32] = r;
+                } else {
+                    if (r != (T)0) nrmask |= 1u << a;
+                    if (r != (T)0 || ((mr_old >> a) & 1u)) (P.r0out + fo)[i32] = r;
+                }
             }
-            (P.out + fo)[i32] = w;
+            if (!MASK) {
+                (P.out + fo)[i32] = w;
+            } else {
+                if (w != (T)0) nmask |= 1u << a;
+                if (w != (T)0 || ((mo_old >> a) & 1u)) (P.out + fo)[i32] = w;
+            }
         }
+    }
+    if (MASK) {
+        P.m_out[i] = nmask;
+        if (R0OUT) P.m_r0out[i] = nrmask;
     }
     if (KC) {
         const long long o = (long long)N * Vs + i;
@@ -1172,8 +1231,8 @@ big_kernel(const Geom g, const Pass<float> P, const float *__restrict__ tabA, co
 }
 
 // FP32 fast path with plain global loads (any grid, 2D or 3D).
-template <int DIM, int KC, unsigned SIG, int NMAX>
-__global__ void __launch_bounds__(BLOCK, PF_FAST_MINB)
+template <int DIM, int KC, unsigned SIG, int NMAX, bool MASK = false>
+__global__ void __launch_bounds__(BLOCK, MASK ? PF_MASK_MINB : PF_FAST_MINB)
 fast_kernel(const Geom g, const Pass<float> P, const float *__restrict__ tabA, const float *__restrict__ tabB,
             const float *__restrict__ tabL, const signed char *__restrict__ ptype)
 {
@@ -1186,7 +1245,9 @@ fast_kernel(const Geom g, const Pass<float> P, const float *__restrict__ tabA, c
     const int z = blockIdx.z;
     double esum = 0.0;
     long long ecnt = 0;
-    if (x < g.nx && y < g.ny) {
+    const bool here = x < g.nx && y < g.ny;
+    const unsigned am = MASK ? __ballot_sync(0xffffffffu, here) : 0xffffffffu;
+    if (here) {
         const long long i = ((long long)z * g.ny + y) * g.nx + x;
         long long off64[6];
         int ghost[6];
@@ -1205,7 +1266,8 @@ fast_kernel(const Geom g, const Pass<float> P, const float *__restrict__ tabA, c
         ld.p0 = P.p0;
         ld.p2 = P.p2;
         ld.r0 = P.r0in;
-        fast_cell<DIM, KC, SIG, NMAX>(g, P, ld, S, tid, i, off, ghost, tabA, tabB, tabL, ptype, esum, ecnt);
+        fast_cell<DIM, KC, SIG, NMAX, PlainLoader<DIM>, MASK>(g, P, ld, S, tid, i, off, ghost, tabA, tabB, tabL, ptype,
+                                                              esum, ecnt, am);
     }
     if (SIG & SIG_ERR) block_partials(esum, ecnt, P.part_sum, P.part_cnt, bid);
 }

@@ -144,9 +144,9 @@ def make_params(prob, precision=64, options=0):
     return p, keep
 
 
-def footprint(prob, precision=64):
+def footprint(prob, precision=64, options=0):
     """Device bytes a Simulation of this problem holds (pf_footprint)."""
-    p, keep = make_params(prob, precision)
+    p, keep = make_params(prob, precision, options)
     b = C.c_longlong()
     _check(_lib().pf_footprint(C.byref(p), C.byref(b)), "pf_footprint")
     return b.value
@@ -156,6 +156,7 @@ class Simulation:
     """One simulation handle (pf_create .. pf_destroy)."""
 
     OPT_TMA = 1
+    OPT_MASKED = 2
 
     def __init__(self, prob, precision=64, stream=None, options=0):
         self.prob = prob

@@ -1,0 +1,103 @@
+"""Masked storage (PF_OPT_MASKED): the occupancy-masked FP32 passes against
+the dense FP32 passes and the FP64 oracle.
+
+A phase outside a cell's occupancy union has an exactly zero RHS and stage
+value, so skipping it changes nothing but the sign of some zeros: the masked
+and the dense results are equal value for value (np.array_equal treats -0
+and +0 as equal).  The dense FP32 path is itself tested against the oracle
+in test_gpu_parity.py; here the masked path is also compared with the
+oracle directly on one RKL2 step of a 32-grain 3D state.
+"""
+import numpy as np
+import pytest
+
+from oracle import ref
+from paper_2601_16522_gb300 import inputs as I
+
+from test_gpu_parity import CASES, pf  # noqa: F401  (fixture)
+
+pytestmark = pytest.mark.gpu
+
+ELIGIBLE = [c for c in CASES if c[1].n_phases <= 32]
+TOL = (1e-4, 1e-3, 1e-4, 1e-3)
+
+
+def _run(pf, prob, u, opts, integ, nsteps_dte, **kw):
+    with pf.Simulation(prob, precision=32, options=opts) as sim:
+        sim.set_state(u)
+        st = sim.step(integ, nsteps_dte * sim.dt_e(), **kw)
+        out, t = sim.get_state()
+    return out, st
+
+
+@pytest.mark.parametrize("integ,kw", [(ref.FEULER, dict(dt_mult=0.9)), (ref.SSP2, dict(dt_mult=2.0)),
+                                      (ref.RKL1, dict(dt_mult=6.0)), (ref.RKL2, dict(dt_mult=12.0)),
+                                      (ref.SSP104, dict(dt_mult=2.0))],
+                         ids=["fe", "ssp2", "rkl1", "rkl2", "ssp104"])
+@pytest.mark.parametrize("name,prob,u", ELIGIBLE, ids=[c[0] for c in ELIGIBLE])
+def test_masked_fixed_steps_equal_dense(pf, name, prob, u, integ, kw):
+    n = 10 if integ != ref.FEULER else 6
+    dense, st_d = _run(pf, prob, u, 0, integ, n, **kw)
+    masked, st_m = _run(pf, prob, u, pf.Simulation.OPT_MASKED, integ, n, **kw)
+    assert st_d["rhs_evals"] == st_m["rhs_evals"]
+    assert np.array_equal(masked, dense), np.abs(masked - dense).max()
+
+
+@pytest.mark.parametrize("integ", [ref.RKL1, ref.RKL2, ref.SSP104], ids=["rkl1", "rkl2", "ssp104"])
+@pytest.mark.parametrize("name,prob,u", [ELIGIBLE[1], ELIGIBLE[3], ELIGIBLE[-1]],
+                         ids=[ELIGIBLE[1][0], ELIGIBLE[3][0], ELIGIBLE[-1][0]])
+def test_masked_adaptive_equal_dense(pf, name, prob, u, integ):
+    dense, st_d = _run(pf, prob, u, 0, integ, 40, tol=TOL)
+    masked, st_m = _run(pf, prob, u, pf.Simulation.OPT_MASKED, integ, 40, tol=TOL)
+    for k in ("rhs_evals", "steps_accepted", "steps_rejected"):
+        assert st_d[k] == st_m[k], k
+    assert np.array_equal(masked, dense), np.abs(masked - dense).max()
+
+
+def test_masked_grains_rkl2_vs_oracle(pf):
+    # 48^3, 32 grains: one RKL2 step of 9 dt_e in masked storage, replayed
+    # by the FP64 oracle on the FP32-rounded initial state
+    prob, u = I.grains_device(n=48, n_grains=32, min_dist=9.0, seed=5, dim=3, dx=1.0, W_cells=2.5, M=1.0,
+                              device="cuda")
+    u = u.cpu().numpy()
+    with pf.Simulation(prob, precision=32, options=pf.Simulation.OPT_MASKED) as sim:
+        sim.set_state(u)
+        u32, _ = sim.get_state()
+        dt = 9.0 * sim.dt_e()
+        st = sim.step(pf.RKL2, dt, dt_mult=9.0, trace_cap=4)
+        out, _ = sim.get_state()
+    with pf.Simulation(prob, precision=32) as sim:
+        sim.set_state(u)
+        sim.step(pf.RKL2, dt, dt_mult=9.0)
+        dense, _ = sim.get_state()
+    assert np.array_equal(out, dense)
+    tr = st["trace"]
+    assert len(tr["dt"]) == 1
+    o = ref.Oracle(prob)
+    un, _, _, _ = o.step(ref.RKL2, tr["dt"][0], int(tr["s"][0]), u32)
+    scale = np.abs(un).max()
+    assert np.abs(out - un).max() <= 2e-5 * scale
+
+
+def test_masked_graph_replay_equals_launches(pf):
+    name, prob, u = ELIGIBLE[3]
+    outs = []
+    for flags in (0, pf.Simulation.STEP_NO_GRAPH):
+        with pf.Simulation(prob, precision=32, options=pf.Simulation.OPT_MASKED) as sim:
+            sim.set_state(u)
+            sim.step(ref.RKL2, 40 * sim.dt_e(), dt_mult=4.0, flags=flags)
+            outs.append(sim.get_state()[0])
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_masked_eligibility_and_footprint(pf):
+    name, prob, u = [c for c in CASES if c[1].n_phases > 32][0]
+    with pytest.raises(RuntimeError):
+        pf.Simulation(prob, precision=32, options=pf.Simulation.OPT_MASKED)
+    name, prob, u = ELIGIBLE[0]
+    with pytest.raises(RuntimeError):
+        pf.Simulation(prob, precision=64, options=pf.Simulation.OPT_MASKED)
+    d = pf.footprint(prob, 32)
+    m = pf.footprint(prob, 32, options=pf.Simulation.OPT_MASKED)
+    Vs = (prob.V + 63) // 64 * 64
+    assert m - d == 5 * Vs * 4
