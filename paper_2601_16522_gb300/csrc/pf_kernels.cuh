@@ -682,11 +682,11 @@ struct TmaLoader {
 // term) is final in that first loop; only the N_z listed phases receive their
 // RHS term after the pairwise sums.  Rounding order differs from the generic
 // kernel; FP32 is not compared bit for bit.
-template <int DIM, int KC, unsigned SIG, int NMAX, class LD, bool MASK = false>
+template <int DIM, int KC, unsigned SIG, int NMAX, class LD>
 __device__ __forceinline__ void fast_cell(const Geom &g, const Pass<float> &P, LD &ld, ListSmem<float> &S, int tid,
                                           long long i, const int *off, const int *ghost, const float *tabA,
                                           const float *tabB, const float *tabL, const signed char *ptype,
-                                          double &esum, long long &ecnt, unsigned am = 0xffffffffu)
+                                          double &esum, long long &ecnt)
 {
     typedef float T;
     constexpr int NFACE = 2 * DIM;
@@ -719,28 +719,6 @@ __device__ __forceinline__ void fast_cell(const Geom &g, const Pass<float> &P, L
         }
     }
 
-    // masked storage: phases that are zero at the cell, its face neighbours
-    // and the pointwise inputs are skipped (their RHS and stage value are
-    // exactly zero); entries known to be zero are not loaded
-    unsigned U = 0u, mc = 0u, mnb[NFACE], mp0 = 0u, mp2 = 0u, mr0 = 0u, mo_old = 0u, mr_old = 0u;
-    if (MASK) {
-        mc = __ldg(P.m_in + i);
-        U = mc;
-#pragma unroll
-        for (int f = 0; f < NFACE; ++f) {
-            mnb[f] = __ldg(P.m_in + i + off[f]);
-            U |= mnb[f];
-        }
-        if (HP0) { mp0 = __ldg(P.m_p0 + i); U |= mp0; }
-        if (HP2) { mp2 = __ldg(P.m_p2 + i); U |= mp2; }
-        if (HR0) { mr0 = __ldg(P.m_r0 + i); U |= mr0; }
-        if (!ERR) mo_old = P.m_out[i];
-        if (R0OUT) mr_old = P.m_r0out[i];
-        // the warp walks the union of its lanes' phases (a uniform branch);
-        // a lane whose masks lack a phase loads nothing and computes zeros
-        U = __reduce_or_sync(am, U);
-    }
-
     int nz = 0, nc = 0;
     bool changed = false;
     T best = (T)-1, ssum = (T)0;
@@ -750,21 +728,11 @@ __device__ __forceinline__ void fast_cell(const Geom &g, const Pass<float> &P, L
 #pragma unroll
     for (int a = 0; a < NMAX; ++a) {
         nv[a] = (T)0;
-        if (a < N && (!MASK || ((U >> a) & 1u))) {
+        if (a < N) {
             const long long fo = (long long)a * Vs;
             T v0, nb[NFACE], p0v = (T)0, p2v = (T)0, r0v = (T)0;
-            if (MASK) {
-                const T *b = P.in + fo + i;
-                v0 = ((mc >> a) & 1u) ? ldg(b) : (T)0;
-#pragma unroll
-                for (int f = 0; f < NFACE; ++f) nb[f] = ((mnb[f] >> a) & 1u) ? ldg(b + off[f]) : (T)0;
-                if (HP0 && ((mp0 >> a) & 1u)) p0v = ld_stream(P.p0 + fo + i);
-                if (HP2 && ((mp2 >> a) & 1u)) p2v = ld_stream(P.p2 + fo + i);
-                if (HR0 && ((mr0 >> a) & 1u)) r0v = ld_stream(P.r0in + fo + i);
-            } else {
-                ld.load(a, fo, v0, nb, p0v, p2v, r0v, HP0, HP2, HR0);
-                ld.release(a);
-            }
+            ld.load(a, fo, v0, nb, p0v, p2v, r0v, HP0, HP2, HR0);
+            ld.release(a);
             T mx = v0, mn = v0;
 #pragma unroll
             for (int f = 0; f < NFACE; ++f) {
@@ -925,13 +893,9 @@ __device__ __forceinline__ void fast_cell(const Geom &g, const Pass<float> &P, L
     const T inv = (ssum > (T)0) ? (T)1 / ssum : (T)1;
     const bool fix = R0OUT && P.fix_first && changed;
     int kr = 0;      // list cursor for the RHS of listed phases (R0OUT)
-    unsigned nmask = 0u, nrmask = 0u;
-    // masked: a phase outside U has a zero result; it is written only where
-    // the output still holds an older nonzero value
-    const unsigned touch = MASK ? __reduce_or_sync(am, U | mo_old | mr_old) : 0u;
 #pragma unroll
     for (int a = 0; a < NMAX; ++a) {
-        if (a < N && (!MASK || ((touch >> a) & 1u))) {
+        if (a < N) {
             const long long fo = (long long)a * Vs;
             T w = nv[a];
             if (PROJ) w = (bestid >= 0) ? ((a == bestid) ? (T)1 : (T)0) : w * inv;
@@ -939,25 +903,279 @@ __device__ __forceinline__ void fast_cell(const Geom &g, const Pass<float> &P, L
                 T r = (T)0;
                 if ((actmask >> a) & 1u) { r = S.lap[kr][tid]; kr++; }
                 if (fix) r = (w - ldg(P.in + fo + i)) / b1c;
-                if (!MASK) {
-                    (P.r0out + fo)[i32] = r;
-                } else {
-                    if (r != (T)0) nrmask |= 1u << a;
-                    if (r != (T)0 || ((mr_old >> a) & 1u)) (P.r0out + fo)[i32] = r;
+                (P.r0out + fo)[i32] = r;
+            }
+            (P.out + fo)[i32] = w;
+        }
+    }
+    if (KC) {
+        const long long o = (long long)N * Vs + i;
+        T acc = HP0 ? a0c * ldg(P.p0 + o) + a1c * cc : a1c * cc;
+        if (HP2) acc = acc + a2c * ldg(P.p2 + o);
+        acc = acc + b1c * rc;
+        if (HR0) acc = acc + b0c * ldg(P.r0in + o);
+        if (R0OUT) P.r0out[o] = rc;
+        P.out[o] = acc;
+    }
+}
+
+// Per-cell body of the FP32 fast path in masked storage (N <= 32).  The
+// arithmetic and its order are those of fast_cell; what changes is which
+// phases are visited: the warp walks the union of its lanes' occupied phases
+// (the occupancy words of the stencil input at the cell and its face
+// neighbours and of the pointwise inputs) in a rolled loop, so the code
+// stays small, and a lane loads only the entries whose bits are set (the
+// others are zero).  A phase outside the union has a zero RHS and a zero
+// stage value; it is written only where the output still holds an older
+// nonzero value.  Stage values live in a per-thread array indexed by phase
+// (local memory, of which only the visited entries are touched).
+template <int DIM, int KC, unsigned SIG>
+__device__ __forceinline__ void masked_cell(const Geom &g, const Pass<float> &P, ListSmem<float> &S, int tid,
+                                            long long i, const int *off, const int *ghost, const float *tabA,
+                                            const float *tabB, const float *tabL, const signed char *ptype,
+                                            double &esum, long long &ecnt, unsigned am)
+{
+    typedef float T;
+    constexpr int NFACE = 2 * DIM;
+    constexpr bool ERR = (SIG & SIG_ERR) != 0;
+    constexpr bool HP0 = (SIG & SIG_P0) != 0 || ERR;
+    constexpr bool HP2 = (SIG & SIG_P2) != 0;
+    constexpr bool HR0 = (SIG & SIG_R0IN) != 0 || ERR;
+    constexpr bool R0OUT = (SIG & SIG_R0OUT) != 0;
+    constexpr bool PROJ = (SIG & SIG_PROJECT) != 0;
+    const int N = g.N;
+    const int Vs = (int)g.Vs;
+    const int i32 = (int)i;
+    const T idx2 = (T)(1.0 / g.dx2);
+    const T a0c = (T)P.a0, a1c = (T)P.a1, a2c = (T)P.a2, b1c = (T)P.b1, b0c = (T)P.b0;
+    const T dt = (T)P.dt, rph = (T)P.r_phi, aph = (T)P.a_phi;
+
+    // concentration
+    T cc = (T)0, num_c = (T)0, den_c = (T)0, num_n[NFACE], den_n[NFACE], mf[NFACE];
+#pragma unroll
+    for (int f = 0; f < NFACE; ++f) { num_n[f] = (T)0; den_n[f] = (T)0; mf[f] = (T)0; }
+    if (KC) {
+        const T *cf = P.in + (long long)N * Vs + i;
+        cc = ldg(cf);
+        num_c = cc;
+#pragma unroll
+        for (int f = 0; f < NFACE; ++f) {
+            T v = ldg(cf + off[f]);
+            if (ghost[f] && g.bc_c[f] == BC_DIRICHLET) v = (T)2 * (T)g.cdir[f] - cc;
+            num_n[f] = v;
+        }
+    }
+
+    // occupancy words; U becomes the warp's union (a uniform loop bound)
+    const unsigned mc = __ldg(P.m_in + i);
+    unsigned mnb[NFACE], U = mc, mp0 = 0u, mp2 = 0u, mr0 = 0u;
+#pragma unroll
+    for (int f = 0; f < NFACE; ++f) {
+        mnb[f] = __ldg(P.m_in + i + off[f]);
+        U |= mnb[f];
+    }
+    if (HP0) { mp0 = __ldg(P.m_p0 + i); U |= mp0; }
+    if (HP2) { mp2 = __ldg(P.m_p2 + i); U |= mp2; }
+    if (HR0) { mr0 = __ldg(P.m_r0 + i); U |= mr0; }
+    const unsigned mo_old = ERR ? 0u : P.m_out[i];
+    const unsigned mr_old = R0OUT ? P.m_r0out[i] : 0u;
+    const unsigned full = N >= 32 ? 0xffffffffu : ((1u << N) - 1u);
+    U = __reduce_or_sync(am, U) & full;
+
+    int nz = 0, nc = 0;
+    bool changed = false;
+    T best = (T)-1, ssum = (T)0;
+    int bestid = -1;
+    T nv[32];
+    unsigned actmask = 0u;
+    for (unsigned m = U; m; m &= m - 1u) {
+        const int a = __ffs(m) - 1;
+        const long long fo = (long long)a * Vs;
+        const T *b = P.in + fo + i;
+        const T v0 = ((mc >> a) & 1u) ? ldg(b) : (T)0;
+        T nb[NFACE];
+#pragma unroll
+        for (int f = 0; f < NFACE; ++f) nb[f] = ((mnb[f] >> a) & 1u) ? ldg(b + off[f]) : (T)0;
+        T p0v = (T)0, p2v = (T)0, r0v = (T)0;
+        if (HP0 && ((mp0 >> a) & 1u)) p0v = ld_stream(P.p0 + fo + i);
+        if (HP2 && ((mp2 >> a) & 1u)) p2v = ld_stream(P.p2 + fo + i);
+        if (HR0 && ((mr0 >> a) & 1u)) r0v = ld_stream(P.r0in + fo + i);
+        T mx = v0, mn = v0;
+#pragma unroll
+        for (int f = 0; f < NFACE; ++f) {
+            mx = fmaxf(mx, nb[f]);
+            mn = fminf(mn, nb[f]);
+        }
+        if (KC) {
+            const int t = ptype[a];
+            const T c0t = (T)g.c0[t], ikt = (T)g.invk[t], dkt = (T)g.Dk[t];
+            num_c = num_c - v0 * c0t;
+            den_c = den_c + v0 * ikt;
+#pragma unroll
+            for (int f = 0; f < NFACE; ++f) {
+                num_n[f] = num_n[f] - nb[f] * c0t;
+                den_n[f] = den_n[f] + nb[f] * ikt;
+                mf[f] = mf[f] + dkt * ((T)0.5 * (v0 + nb[f]));
+            }
+        }
+        const bool act = mx > (T)0 && mn < (T)1;
+        if (act) {
+            T l = (T)0;
+#pragma unroll
+            for (int f = 0; f < NFACE; ++f) l = l + (nb[f] - v0);
+            if (nz < MAXACT) {
+                S.id[nz][tid] = (unsigned char)a;
+                S.lap[nz][tid] = l * idx2;
+                S.cen[nz][tid] = v0;
+                actmask |= 1u << a;
+            }
+            nz++;
+        }
+        if (ERR) {
+            if (!act) {
+                T e = ((T)12 * (p0v - v0) + ((T)6 * dt) * r0v) * ((T)1 / (T)15);
+                const T trial = p0v + (dt * (T)0.5) * r0v;
+                if (trial < (T)0 || trial > (T)1) e = (T)0;
+                if (e != (T)0) {
+                    const T w = rph * fmaxf(fabsf(p0v), fabsf(v0)) + aph;
+                    const T q = e / w;
+                    esum += (double)(q * q);
+                    nc++;
                 }
             }
-            if (!MASK) {
-                (P.out + fo)[i32] = w;
-            } else {
-                if (w != (T)0) nmask |= 1u << a;
-                if (w != (T)0 || ((mo_old >> a) & 1u)) (P.out + fo)[i32] = w;
+        } else {
+            T acc = HP0 ? a0c * p0v + a1c * v0 : a1c * v0;
+            if (HP2) acc = acc + a2c * p2v;
+            if (HR0) acc = acc + b0c * r0v;
+            if (!act && PROJ) {
+                if (acc < (T)0) { acc = (T)0; changed = true; }
+                if (acc >= (T)1 && acc > best) { best = acc; bestid = a; }
+                ssum = ssum + acc;
+            }
+            nv[a] = acc;
+        }
+    }
+    if (nz > MAXACT) {
+        atomicOr(P.flag, FLAG_NZ_OVERFLOW);
+        nz = MAXACT;
+    }
+
+    T mu = (T)0, rc = (T)0;
+    if (KC) {
+        mu = num_c / den_c;
+        T acc = (T)0;
+#pragma unroll
+        for (int f = 0; f < NFACE; ++f) acc = acc + mf[f] * (num_n[f] / den_n[f] - mu);
+        rc = acc * idx2;
+    }
+    // variational derivative and pairwise sum over the listed phases
+    for (int k = 0; k < nz; ++k) {
+        const int a = S.id[k][tid];
+        const T *Aa = tabA + a * N, *Ba = tabB + a * N;
+        T d = (T)0;
+        for (int k2 = 0; k2 < nz; ++k2) {
+            if (k2 == k) continue;
+            const int b = S.id[k2][tid];
+            d = d + (ldg(Aa + b) * S.lap[k2][tid] + ldg(Ba + b) * S.cen[k2][tid]);
+        }
+        if (KC) {
+            const int t = ptype[a];
+            d = d + (-(mu * mu) / ((T)2 * (T)g.k[t]) - mu * (T)g.c0[t]);
+        }
+        S.dl[k][tid] = d;
+    }
+    const T inz = nz > 1 ? (T)1 / (T)nz : (T)0;
+    for (int k = 0; k < nz; ++k) {
+        T rk = (T)0;
+        if (nz > 1) {
+            const int a = S.id[k][tid];
+            const T *La = tabL + a * N;
+            const T dk = S.dl[k][tid];
+            T s = (T)0;
+            for (int k2 = 0; k2 < nz; ++k2) {
+                if (k2 == k) continue;
+                s = s + ldg(La + S.id[k2][tid]) * (dk - S.dl[k2][tid]);
+            }
+            rk = -(s * inz);
+        }
+        S.lap[k][tid] = rk;                 // the list now holds the RHS
+        if (ERR) {
+            const int a = S.id[k][tid];
+            const long long fo = (long long)a * Vs;
+            const T p0v = ldg(P.p0 + fo + i), v0 = S.cen[k][tid], r0v = ldg(P.r0in + fo + i);
+            const T sr = r0v + rk;
+            T e = ((T)12 * (p0v - v0) + ((T)6 * dt) * sr) * ((T)1 / (T)15);
+            const T trial = p0v + (dt * (T)0.5) * sr;
+            if (trial < (T)0 || trial > (T)1) e = (T)0;
+            if (e != (T)0) {
+                const T w = rph * fmaxf(fabsf(p0v), fabsf(v0)) + aph;
+                const T q = e / w;
+                esum += (double)(q * q);
+                nc++;
             }
         }
     }
-    if (MASK) {
-        P.m_out[i] = nmask;
-        if (R0OUT) P.m_r0out[i] = nrmask;
+    if (ERR) {
+        ecnt += (nc > 0 ? nc : 2);
+        if (KC) {
+            const long long o = (long long)N * Vs + i;
+            const T un = ldg(P.p0 + o), un1 = cc, rn = ldg(P.r0in + o);
+            const T e = ((T)12 * (un - un1) + ((T)6 * dt) * (rn + rc)) * ((T)1 / (T)15);
+            const T w = (T)P.r_c * fmaxf(fabsf(un), fabsf(un1)) + (T)P.a_c;
+            const T q = e / w;
+            esum += (double)(q * q);
+            ecnt += 1;
+        }
+        return;
     }
+    // listed phases (ascending ids): add the RHS term, clamp, >= 1 candidates, sum
+    {
+        int kk = 0;
+        for (unsigned m = actmask; m; m &= m - 1u) {
+            const int a = __ffs(m) - 1;
+            const T rk = S.lap[kk][tid];
+            kk++;
+            T acc = nv[a] + b1c * rk;
+            if (PROJ) {
+                if (acc < (T)0) { acc = (T)0; changed = true; }
+                if (acc >= (T)1 && (acc > best || (acc == best && a < bestid))) { best = acc; bestid = a; }
+                ssum = ssum + acc;
+            }
+            nv[a] = acc;
+        }
+    }
+    if (PROJ) {
+        if (bestid >= 0) {
+            for (unsigned m = U; m; m &= m - 1u) {
+                const int a = __ffs(m) - 1;
+                if (nv[a] != ((a == bestid) ? (T)1 : (T)0)) changed = true;
+            }
+            ssum = (T)1;
+        }
+        if (!(ssum > (T)0)) atomicOr(P.flag, FLAG_SIMPLEX);
+    }
+    const T inv = (ssum > (T)0) ? (T)1 / ssum : (T)1;
+    const bool fix = R0OUT && P.fix_first && changed;
+    int kr = 0;      // list cursor for the RHS of listed phases (R0OUT)
+    unsigned nmask = 0u, nrmask = 0u;
+    const unsigned touch = __reduce_or_sync(am, U | mo_old | mr_old) & full;
+    for (unsigned m = touch; m; m &= m - 1u) {
+        const int a = __ffs(m) - 1;
+        const long long fo = (long long)a * Vs;
+        T w = ((U >> a) & 1u) ? nv[a] : (T)0;
+        if (PROJ) w = (bestid >= 0) ? ((a == bestid) ? (T)1 : (T)0) : w * inv;
+        if (R0OUT) {
+            T r = (T)0;
+            if ((actmask >> a) & 1u) { r = S.lap[kr][tid]; kr++; }
+            if (fix) r = (w - ldg(P.in + fo + i)) / b1c;
+            if (r != (T)0) nrmask |= 1u << a;
+            if (r != (T)0 || ((mr_old >> a) & 1u)) (P.r0out + fo)[i32] = r;
+        }
+        if (w != (T)0) nmask |= 1u << a;
+        if (w != (T)0 || ((mo_old >> a) & 1u)) (P.out + fo)[i32] = w;
+    }
+    P.m_out[i] = nmask;
+    if (R0OUT) P.m_r0out[i] = nrmask;
     if (KC) {
         const long long o = (long long)N * Vs + i;
         T acc = HP0 ? a0c * ldg(P.p0 + o) + a1c * cc : a1c * cc;
@@ -1266,8 +1484,10 @@ fast_kernel(const Geom g, const Pass<float> P, const float *__restrict__ tabA, c
         ld.p0 = P.p0;
         ld.p2 = P.p2;
         ld.r0 = P.r0in;
-        fast_cell<DIM, KC, SIG, NMAX, PlainLoader<DIM>, MASK>(g, P, ld, S, tid, i, off, ghost, tabA, tabB, tabL, ptype,
-                                                              esum, ecnt, am);
+        if (MASK)
+            masked_cell<DIM, KC, SIG>(g, P, S, tid, i, off, ghost, tabA, tabB, tabL, ptype, esum, ecnt, am);
+        else
+            fast_cell<DIM, KC, SIG, NMAX>(g, P, ld, S, tid, i, off, ghost, tabA, tabB, tabL, ptype, esum, ecnt);
     }
     if (SIG & SIG_ERR) block_partials(esum, ecnt, P.part_sum, P.part_cnt, bid);
 }
