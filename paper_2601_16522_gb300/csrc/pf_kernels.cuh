@@ -97,6 +97,12 @@ __device__ __forceinline__ T tabs(T v) { return v < (T)0 ? -v : v; }
 #ifndef PF_FAST_MINB
 #define PF_FAST_MINB 4
 #endif
+// Dense FP32 stage passes through the rolled phase loop (every phase
+// occupied) instead of the register-unrolled one (the error sweep, which
+// holds no stage values, always takes the rolled loop: it measured faster).
+#ifndef PF_DENSE_ROLLED
+#define PF_DENSE_ROLLED 0
+#endif
 // ... and of its masked-storage instantiations.
 #ifndef PF_MASK_MINB
 #define PF_MASK_MINB 4
@@ -929,7 +935,7 @@ __device__ __forceinline__ void fast_cell(const Geom &g, const Pass<float> &P, L
 // stage value; it is written only where the output still holds an older
 // nonzero value.  Stage values live in a per-thread array indexed by phase
 // (local memory, of which only the visited entries are touched).
-template <int DIM, int KC, unsigned SIG>
+template <int DIM, int KC, unsigned SIG, bool OCC = true>
 __device__ __forceinline__ void masked_cell(const Geom &g, const Pass<float> &P, ListSmem<float> &S, int tid,
                                             long long i, const int *off, const int *ghost, const float *tabA,
                                             const float *tabB, const float *tabL, const signed char *ptype,
@@ -966,21 +972,22 @@ __device__ __forceinline__ void masked_cell(const Geom &g, const Pass<float> &P,
         }
     }
 
-    // occupancy words; U becomes the warp's union (a uniform loop bound)
-    const unsigned mc = __ldg(P.m_in + i);
+    // occupancy words; U becomes the warp's union (a uniform loop bound).
+    // Without words (OCC false: dense storage) every phase is occupied.
+    const unsigned full = N >= 32 ? 0xffffffffu : ((1u << N) - 1u);
+    const unsigned mc = OCC ? __ldg(P.m_in + i) : full;
     unsigned mnb[NFACE], U = mc, mp0 = 0u, mp2 = 0u, mr0 = 0u;
 #pragma unroll
     for (int f = 0; f < NFACE; ++f) {
-        mnb[f] = __ldg(P.m_in + i + off[f]);
+        mnb[f] = OCC ? __ldg(P.m_in + i + off[f]) : full;
         U |= mnb[f];
     }
-    if (HP0) { mp0 = __ldg(P.m_p0 + i); U |= mp0; }
-    if (HP2) { mp2 = __ldg(P.m_p2 + i); U |= mp2; }
-    if (HR0) { mr0 = __ldg(P.m_r0 + i); U |= mr0; }
-    const unsigned mo_old = ERR ? 0u : P.m_out[i];
-    const unsigned mr_old = R0OUT ? P.m_r0out[i] : 0u;
-    const unsigned full = N >= 32 ? 0xffffffffu : ((1u << N) - 1u);
-    U = __reduce_or_sync(am, U) & full;
+    if (HP0) { mp0 = OCC ? __ldg(P.m_p0 + i) : full; U |= mp0; }
+    if (HP2) { mp2 = OCC ? __ldg(P.m_p2 + i) : full; U |= mp2; }
+    if (HR0) { mr0 = OCC ? __ldg(P.m_r0 + i) : full; U |= mr0; }
+    const unsigned mo_old = (ERR || !OCC) ? 0u : P.m_out[i];
+    const unsigned mr_old = (R0OUT && OCC) ? P.m_r0out[i] : 0u;
+    U = OCC ? (__reduce_or_sync(am, U) & full) : full;
 
     int nz = 0, nc = 0;
     bool changed = false;
@@ -992,6 +999,13 @@ __device__ __forceinline__ void masked_cell(const Geom &g, const Pass<float> &P,
         const int a = __ffs(m) - 1;
         const long long fo = (long long)a * Vs;
         const T *b = P.in + fo + i;
+        if (!OCC && PF_PREFETCH_DIST > 0 && a + PF_PREFETCH_DIST < N) {
+            const long long pa = (long long)PF_PREFETCH_DIST * Vs;
+            prefetch_l2(b + pa);
+            if (HP0) prefetch_l2(P.p0 + fo + pa + i);
+            if (HP2) prefetch_l2(P.p2 + fo + pa + i);
+            if (HR0) prefetch_l2(P.r0in + fo + pa + i);
+        }
         const T v0 = ((mc >> a) & 1u) ? ldg(b) : (T)0;
         T nb[NFACE];
 #pragma unroll
@@ -1158,7 +1172,7 @@ __device__ __forceinline__ void masked_cell(const Geom &g, const Pass<float> &P,
     const bool fix = R0OUT && P.fix_first && changed;
     int kr = 0;      // list cursor for the RHS of listed phases (R0OUT)
     unsigned nmask = 0u, nrmask = 0u;
-    const unsigned touch = __reduce_or_sync(am, U | mo_old | mr_old) & full;
+    const unsigned touch = OCC ? (__reduce_or_sync(am, U | mo_old | mr_old) & full) : full;
     for (unsigned m = touch; m; m &= m - 1u) {
         const int a = __ffs(m) - 1;
         const long long fo = (long long)a * Vs;
@@ -1169,13 +1183,15 @@ __device__ __forceinline__ void masked_cell(const Geom &g, const Pass<float> &P,
             if ((actmask >> a) & 1u) { r = S.lap[kr][tid]; kr++; }
             if (fix) r = (w - ldg(P.in + fo + i)) / b1c;
             if (r != (T)0) nrmask |= 1u << a;
-            if (r != (T)0 || ((mr_old >> a) & 1u)) (P.r0out + fo)[i32] = r;
+            if (!OCC || r != (T)0 || ((mr_old >> a) & 1u)) (P.r0out + fo)[i32] = r;
         }
         if (w != (T)0) nmask |= 1u << a;
-        if (w != (T)0 || ((mo_old >> a) & 1u)) (P.out + fo)[i32] = w;
+        if (!OCC || w != (T)0 || ((mo_old >> a) & 1u)) (P.out + fo)[i32] = w;
     }
-    P.m_out[i] = nmask;
-    if (R0OUT) P.m_r0out[i] = nrmask;
+    if (OCC) {
+        P.m_out[i] = nmask;
+        if (R0OUT) P.m_r0out[i] = nrmask;
+    }
     if (KC) {
         const long long o = (long long)N * Vs + i;
         T acc = HP0 ? a0c * ldg(P.p0 + o) + a1c * cc : a1c * cc;
@@ -1485,7 +1501,9 @@ fast_kernel(const Geom g, const Pass<float> P, const float *__restrict__ tabA, c
         ld.p2 = P.p2;
         ld.r0 = P.r0in;
         if (MASK)
-            masked_cell<DIM, KC, SIG>(g, P, S, tid, i, off, ghost, tabA, tabB, tabL, ptype, esum, ecnt, am);
+            masked_cell<DIM, KC, SIG, true>(g, P, S, tid, i, off, ghost, tabA, tabB, tabL, ptype, esum, ecnt, am);
+        else if (PF_DENSE_ROLLED || (SIG & SIG_ERR) != 0)
+            masked_cell<DIM, KC, SIG, false>(g, P, S, tid, i, off, ghost, tabA, tabB, tabL, ptype, esum, ecnt, am);
         else
             fast_cell<DIM, KC, SIG, NMAX>(g, P, ld, S, tid, i, off, ghost, tabA, tabB, tabL, ptype, esum, ecnt);
     }
