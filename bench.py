@@ -462,7 +462,7 @@ def run_ours(args, world, rank, local):
     # masked storage (the GPU form of the per-cell phase lists): the same
     # steps from the same state; its result must equal the dense one
     masked = None
-    if not args.no_masked and prec == 32 and N <= 32:
+    if not args.no_masked and prec == 32 and N <= 128:
         dense_out = torch.empty((N + prob.has_conc, V), dtype=torch.float64, device=dev)
         sim.get_state(out=dense_out)
         masked = masked_run(pf, torch, prob, u, stream, args, world, dev, dense_out, pass_ms)

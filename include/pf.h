@@ -84,18 +84,19 @@ typedef struct {
    instead of the plain-load kernel.  Results are bit-identical; which is
    faster depends on the problem (on the 256^3, 32-phase grain workload the
    plain-load kernel is). */
-/* PF_OPT_MASKED (FP32, at most 32 phases) selects masked storage, the
+/* PF_OPT_MASKED (FP32, at most 128 phases) selects masked storage, the
    GPU form of the per-cell phase lists of Sec. 3.1 (only the N_z local
    phases are loaded): the state keeps its dense phase-major layout and adds
-   one 32-bit occupancy word per cell (bit a set where phase a may be
-   nonzero; every entry whose bit is clear holds zero).  The FP32 fast passes
+   one 32-bit occupancy word per 32 phases and cell (bit b of word w set
+   where phase 32 w + b may be nonzero; every entry whose bit is clear holds
+   zero).  The FP32 fast passes
    skip the loads and the work of phases that are zero at a cell, its face
    neighbours and the pass's pointwise inputs; their RHS and stage values are
    exactly zero, so results equal the dense passes' up to the sign of zero.
    Passes without a masked form (SSP(10)4 with its embedded solution) run
    dense and mark the vectors they write as fully occupied.  The masks cost
-   4 bytes per cell per state vector (pf_footprint counts them); TMA staging
-   is not used.  PF_EINVAL for FP64 or more than 32 phases. */
+   4 bytes per word, cell and state vector (pf_footprint counts them); TMA
+   staging is not used.  PF_EINVAL for FP64. */
 enum { PF_OPT_TMA = 1, PF_OPT_MASKED = 2 };
 
 /* Error tolerances of the weighted norm (Eq. error_norm): relative r and

@@ -82,15 +82,17 @@ __global__ void finalize_err_kernel(const double *__restrict__ ps, const long lo
     if (threadIdx.x == 0) { *out_sum = ss[0]; *out_cnt = sc[0]; }
 }
 
-// Occupancy masks of an FP32 state (masked storage): bit a of cell i is set
-// where phase a is nonzero.
+// Occupancy words of an FP32 state (masked storage): bit b of word w of cell
+// i (plane w) is set where phase 32 w + b is nonzero.
 __global__ void mask_kernel(const float *__restrict__ u, unsigned *__restrict__ m, long long V, long long Vs, int N)
 {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < V; i += (long long)gridDim.x * blockDim.x) {
-        unsigned w = 0u;
-        for (int a = 0; a < N; ++a)
-            if (u[(long long)a * Vs + i] != 0.0f) w |= 1u << a;
-        m[i] = w;
+        for (int w = 0; 32 * w < N; ++w) {
+            unsigned bits = 0u;
+            for (int b = 0; b < 32 && 32 * w + b < N; ++b)
+                if (u[(long long)(32 * w + b) * Vs + i] != 0.0f) bits |= 1u << b;
+            m[(long long)w * Vs + i] = bits;
+        }
     }
 }
 
@@ -232,7 +234,8 @@ struct pf_handle {
     int *dflag = nullptr;
     double *tot_sum = nullptr, *tot_max = nullptr;
     int tot_blocks = 0;
-    bool masked = false;               // masked storage: an occupancy-mask plane after the fields
+    bool masked = false;               // masked storage: occupancy-word planes after the fields
+    int nw = 0;                        // occupancy words per cell (masked storage)
     bool tma_ok = false;               // tensor maps built: TMA-staged kernels available
     bool tma = false;                  // TMA-staged FP32 kernels in use
     CUtensorMap m3[NBUF], m1[NBUF];    // per buffer: 3-plane and 1-plane boxes
@@ -358,8 +361,8 @@ bool masked_sig(unsigned s)
 int invalidate_mask(pf_handle *h, const void *vecp)
 {
     if (!vecp || buf_index(h, vecp) < 0) return PF_OK;
-    return cudaMemsetAsync(mask_plane(h, vecp), 0xff, sizeof(unsigned) * (size_t)h->Vs, h->stream) == cudaSuccess
-               ? PF_OK : PF_EDEVICE;
+    return cudaMemsetAsync(mask_plane(h, vecp), 0xff, sizeof(unsigned) * (size_t)h->Vs * h->nw, h->stream) ==
+                   cudaSuccess ? PF_OK : PF_EDEVICE;
 }
 
 template <typename T>
@@ -1144,11 +1147,12 @@ int pf_create(const pf_params *p, void *cuda_stream, pf_handle **out)
     if (h->tot_blocks < 1) h->tot_blocks = 1;
 
     if (p->options & PF_OPT_MASKED) {
-        // masked storage: FP32, at most 32 phases (one mask word per cell)
-        if (p->precision != 32 || p->n_phases > 32) { delete h; return PF_EINVAL; }
+        // masked storage: FP32, one occupancy word per 32 phases and cell
+        if (p->precision != 32 || p->n_phases > 128) { delete h; return PF_EINVAL; }
         h->masked = true;
+        h->nw = (p->n_phases + 31) / 32;
     }
-    h->vec_bytes = (size_t)h->Vs * NP * h->esize + (h->masked ? sizeof(unsigned) * (size_t)h->Vs : 0);
+    h->vec_bytes = (size_t)h->Vs * NP * h->esize + sizeof(unsigned) * (size_t)h->Vs * h->nw;
     bool ok = true;
     for (int k = 0; k < NBUF && ok; ++k) ok = dmalloc(h, &h->buf[k], h->vec_bytes);
     ok = ok && dmalloc(h, &h->dA, h->esize * N * N);
@@ -1181,7 +1185,8 @@ int pf_create(const pf_params *p, void *cuda_stream, pf_handle **out)
     st |= cudaMemsetAsync(h->dflag, 0, sizeof(int), h->stream);
     if (h->masked)
         for (int k = 0; k < NBUF; ++k)
-            st |= cudaMemsetAsync(mask_plane(h, h->buf[k]), 0xff, sizeof(unsigned) * (size_t)h->Vs, h->stream);
+            st |= cudaMemsetAsync(mask_plane(h, h->buf[k]), 0xff, sizeof(unsigned) * (size_t)h->Vs * h->nw,
+                                  h->stream);
     st |= cudaStreamSynchronize(h->stream);
     if (st != 0) { free_all(h); delete h; return PF_EDEVICE; }
     // TMA-staged FP32 kernels: full 32 x 8 tiles, 3D, 5..32 phases
@@ -1211,7 +1216,7 @@ int pf_footprint(const pf_params *p, long long *bytes)
     const long long tiles = (long long)((p->nx + pfk::TX - 1) / pfk::TX) * ((p->ny + pfk::TY - 1) / pfk::TY) * p->nz;
     const long long tot_blocks = (V + 4095) / 4096 < 1024 ? ((V + 4095) / 4096 > 0 ? (V + 4095) / 4096 : 1) : 1024;
     long long b = (long long)NBUF * NF * Vs * es;          // state vectors
-    if (p->options & PF_OPT_MASKED) b += (long long)NBUF * Vs * 4;   // occupancy masks
+    if (p->options & PF_OPT_MASKED) b += (long long)NBUF * ((p->n_phases + 31) / 32) * Vs * 4;   // occupancy words
     b += NF * V * 8;                                       // ABI staging buffer (allocated on first set/get)
     b += 3LL * p->n_phases * p->n_phases * es + p->n_phases;   // coefficient tables, phase types
     b += 2LL * p->n_phases * p->n_phases * 8;              // FP64 A and B for the energy functional

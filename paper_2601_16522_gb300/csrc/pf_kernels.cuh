@@ -925,17 +925,26 @@ __device__ __forceinline__ void fast_cell(const Geom &g, const Pass<float> &P, L
     }
 }
 
-// Per-cell body of the FP32 fast path in masked storage (N <= 32).  The
+// Bits of occupancy word w that belong to phases below N.
+__device__ __forceinline__ unsigned word_bits(int N, int w)
+{
+    const int r = N - 32 * w;
+    return r >= 32 ? 0xffffffffu : (r <= 0 ? 0u : ((1u << r) - 1u));
+}
+
+// Per-cell body of the FP32 fast path in masked storage (N <= 32 NW).  The
 // arithmetic and its order are those of fast_cell; what changes is which
 // phases are visited: the warp walks the union of its lanes' occupied phases
 // (the occupancy words of the stencil input at the cell and its face
-// neighbours and of the pointwise inputs) in a rolled loop, so the code
-// stays small, and a lane loads only the entries whose bits are set (the
-// others are zero).  A phase outside the union has a zero RHS and a zero
-// stage value; it is written only where the output still holds an older
-// nonzero value.  Stage values live in a per-thread array indexed by phase
-// (local memory, of which only the visited entries are touched).
-template <int DIM, int KC, unsigned SIG, bool OCC = true>
+// neighbours and of the pointwise inputs), word by word, in a rolled loop,
+// so the code stays small, and a lane loads only the entries whose bits are
+// set (the others are zero).  A phase outside the union has a zero RHS and a
+// zero stage value; it is written only where the output still holds an
+// older nonzero value.  Stage values live in a per-thread array indexed by
+// phase (local memory, of which only the visited entries are touched).
+// Word w of a cell's occupancy covers phases 32w .. 32w + 31 and lives in
+// the plane at w * Vs.
+template <int DIM, int KC, unsigned SIG, bool OCC = true, int NW = 1>
 __device__ __forceinline__ void masked_cell(const Geom &g, const Pass<float> &P, ListSmem<float> &S, int tid,
                                             long long i, const int *off, const int *ghost, const float *tabA,
                                             const float *tabB, const float *tabL, const signed char *ptype,
@@ -972,31 +981,51 @@ __device__ __forceinline__ void masked_cell(const Geom &g, const Pass<float> &P,
         }
     }
 
-    // occupancy words; U becomes the warp's union (a uniform loop bound).
+    // occupancy: U[w] is the warp's union of word w (a uniform loop bound).
     // Without words (OCC false: dense storage) every phase is occupied.
-    const unsigned full = N >= 32 ? 0xffffffffu : ((1u << N) - 1u);
-    const unsigned mc = OCC ? __ldg(P.m_in + i) : full;
-    unsigned mnb[NFACE], U = mc, mp0 = 0u, mp2 = 0u, mr0 = 0u;
+    // only the words of existing phases exist in memory: w < nwr
+    const int nwr = (N + 31) / 32;
+    unsigned U[NW];
 #pragma unroll
-    for (int f = 0; f < NFACE; ++f) {
-        mnb[f] = OCC ? __ldg(P.m_in + i + off[f]) : full;
-        U |= mnb[f];
+    for (int w = 0; w < NW; ++w) {
+        const unsigned full = word_bits(N, w);
+        unsigned u = full;
+        if (OCC && w < nwr) {
+            const long long o = (long long)w * Vs + i;
+            u = __ldg(P.m_in + o);
+#pragma unroll
+            for (int f = 0; f < NFACE; ++f) u |= __ldg(P.m_in + o + off[f]);
+            if (HP0) u |= __ldg(P.m_p0 + o);
+            if (HP2) u |= __ldg(P.m_p2 + o);
+            if (HR0) u |= __ldg(P.m_r0 + o);
+            u = __reduce_or_sync(am, u) & full;
+        }
+        U[w] = u;
     }
-    if (HP0) { mp0 = OCC ? __ldg(P.m_p0 + i) : full; U |= mp0; }
-    if (HP2) { mp2 = OCC ? __ldg(P.m_p2 + i) : full; U |= mp2; }
-    if (HR0) { mr0 = OCC ? __ldg(P.m_r0 + i) : full; U |= mr0; }
-    const unsigned mo_old = (ERR || !OCC) ? 0u : P.m_out[i];
-    const unsigned mr_old = (R0OUT && OCC) ? P.m_r0out[i] : 0u;
-    U = OCC ? (__reduce_or_sync(am, U) & full) : full;
 
     int nz = 0, nc = 0;
     bool changed = false;
     T best = (T)-1, ssum = (T)0;
     int bestid = -1;
-    T nv[32];
-    unsigned actmask = 0u;
-    for (unsigned m = U; m; m &= m - 1u) {
-        const int a = __ffs(m) - 1;
+    T nv[32 * NW];
+    unsigned actmask[NW];
+#pragma unroll
+    for (int w = 0; w < NW; ++w) actmask[w] = 0u;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+      if (w >= nwr || !U[w]) continue;
+      const unsigned full = word_bits(N, w);
+      const long long ow = (long long)w * Vs + i;
+      const unsigned mc = OCC ? __ldg(P.m_in + ow) : full;
+      unsigned mnb[NFACE];
+#pragma unroll
+      for (int f = 0; f < NFACE; ++f) mnb[f] = OCC ? __ldg(P.m_in + ow + off[f]) : full;
+      const unsigned mp0 = HP0 ? (OCC ? __ldg(P.m_p0 + ow) : full) : 0u;
+      const unsigned mp2 = HP2 ? (OCC ? __ldg(P.m_p2 + ow) : full) : 0u;
+      const unsigned mr0 = HR0 ? (OCC ? __ldg(P.m_r0 + ow) : full) : 0u;
+      for (unsigned m = U[w]; m; m &= m - 1u) {
+        const int bit = __ffs(m) - 1;
+        const int a = 32 * w + bit;
         const long long fo = (long long)a * Vs;
         const T *b = P.in + fo + i;
         if (!OCC && PF_PREFETCH_DIST > 0 && a + PF_PREFETCH_DIST < N) {
@@ -1006,14 +1035,14 @@ __device__ __forceinline__ void masked_cell(const Geom &g, const Pass<float> &P,
             if (HP2) prefetch_l2(P.p2 + fo + pa + i);
             if (HR0) prefetch_l2(P.r0in + fo + pa + i);
         }
-        const T v0 = ((mc >> a) & 1u) ? ldg(b) : (T)0;
+        const T v0 = ((mc >> bit) & 1u) ? ldg(b) : (T)0;
         T nb[NFACE];
 #pragma unroll
-        for (int f = 0; f < NFACE; ++f) nb[f] = ((mnb[f] >> a) & 1u) ? ldg(b + off[f]) : (T)0;
+        for (int f = 0; f < NFACE; ++f) nb[f] = ((mnb[f] >> bit) & 1u) ? ldg(b + off[f]) : (T)0;
         T p0v = (T)0, p2v = (T)0, r0v = (T)0;
-        if (HP0 && ((mp0 >> a) & 1u)) p0v = ld_stream(P.p0 + fo + i);
-        if (HP2 && ((mp2 >> a) & 1u)) p2v = ld_stream(P.p2 + fo + i);
-        if (HR0 && ((mr0 >> a) & 1u)) r0v = ld_stream(P.r0in + fo + i);
+        if (HP0 && ((mp0 >> bit) & 1u)) p0v = ld_stream(P.p0 + fo + i);
+        if (HP2 && ((mp2 >> bit) & 1u)) p2v = ld_stream(P.p2 + fo + i);
+        if (HR0 && ((mr0 >> bit) & 1u)) r0v = ld_stream(P.r0in + fo + i);
         T mx = v0, mn = v0;
 #pragma unroll
         for (int f = 0; f < NFACE; ++f) {
@@ -1041,7 +1070,7 @@ __device__ __forceinline__ void masked_cell(const Geom &g, const Pass<float> &P,
                 S.id[nz][tid] = (unsigned char)a;
                 S.lap[nz][tid] = l * idx2;
                 S.cen[nz][tid] = v0;
-                actmask |= 1u << a;
+                actmask[w] |= 1u << bit;
             }
             nz++;
         }
@@ -1051,8 +1080,8 @@ __device__ __forceinline__ void masked_cell(const Geom &g, const Pass<float> &P,
                 const T trial = p0v + (dt * (T)0.5) * r0v;
                 if (trial < (T)0 || trial > (T)1) e = (T)0;
                 if (e != (T)0) {
-                    const T w = rph * fmaxf(fabsf(p0v), fabsf(v0)) + aph;
-                    const T q = e / w;
+                    const T wt = rph * fmaxf(fabsf(p0v), fabsf(v0)) + aph;
+                    const T q = e / wt;
                     esum += (double)(q * q);
                     nc++;
                 }
@@ -1068,6 +1097,7 @@ __device__ __forceinline__ void masked_cell(const Geom &g, const Pass<float> &P,
             }
             nv[a] = acc;
         }
+      }
     }
     if (nz > MAXACT) {
         atomicOr(P.flag, FLAG_NZ_OVERFLOW);
@@ -1122,8 +1152,8 @@ __device__ __forceinline__ void masked_cell(const Geom &g, const Pass<float> &P,
             const T trial = p0v + (dt * (T)0.5) * sr;
             if (trial < (T)0 || trial > (T)1) e = (T)0;
             if (e != (T)0) {
-                const T w = rph * fmaxf(fabsf(p0v), fabsf(v0)) + aph;
-                const T q = e / w;
+                const T wt = rph * fmaxf(fabsf(p0v), fabsf(v0)) + aph;
+                const T q = e / wt;
                 esum += (double)(q * q);
                 nc++;
             }
@@ -1135,8 +1165,8 @@ __device__ __forceinline__ void masked_cell(const Geom &g, const Pass<float> &P,
             const long long o = (long long)N * Vs + i;
             const T un = ldg(P.p0 + o), un1 = cc, rn = ldg(P.r0in + o);
             const T e = ((T)12 * (un - un1) + ((T)6 * dt) * (rn + rc)) * ((T)1 / (T)15);
-            const T w = (T)P.r_c * fmaxf(fabsf(un), fabsf(un1)) + (T)P.a_c;
-            const T q = e / w;
+            const T wt = (T)P.r_c * fmaxf(fabsf(un), fabsf(un1)) + (T)P.a_c;
+            const T q = e / wt;
             esum += (double)(q * q);
             ecnt += 1;
         }
@@ -1145,8 +1175,10 @@ __device__ __forceinline__ void masked_cell(const Geom &g, const Pass<float> &P,
     // listed phases (ascending ids): add the RHS term, clamp, >= 1 candidates, sum
     {
         int kk = 0;
-        for (unsigned m = actmask; m; m &= m - 1u) {
-            const int a = __ffs(m) - 1;
+#pragma unroll
+        for (int w = 0; w < NW; ++w)
+        for (unsigned m = actmask[w]; m; m &= m - 1u) {
+            const int a = 32 * w + __ffs(m) - 1;
             const T rk = S.lap[kk][tid];
             kk++;
             T acc = nv[a] + b1c * rk;
@@ -1160,10 +1192,12 @@ __device__ __forceinline__ void masked_cell(const Geom &g, const Pass<float> &P,
     }
     if (PROJ) {
         if (bestid >= 0) {
-            for (unsigned m = U; m; m &= m - 1u) {
-                const int a = __ffs(m) - 1;
-                if (nv[a] != ((a == bestid) ? (T)1 : (T)0)) changed = true;
-            }
+#pragma unroll
+            for (int w = 0; w < NW; ++w)
+                for (unsigned m = U[w]; m; m &= m - 1u) {
+                    const int a = 32 * w + __ffs(m) - 1;
+                    if (nv[a] != ((a == bestid) ? (T)1 : (T)0)) changed = true;
+                }
             ssum = (T)1;
         }
         if (!(ssum > (T)0)) atomicOr(P.flag, FLAG_SIMPLEX);
@@ -1171,26 +1205,35 @@ __device__ __forceinline__ void masked_cell(const Geom &g, const Pass<float> &P,
     const T inv = (ssum > (T)0) ? (T)1 / ssum : (T)1;
     const bool fix = R0OUT && P.fix_first && changed;
     int kr = 0;      // list cursor for the RHS of listed phases (R0OUT)
-    unsigned nmask = 0u, nrmask = 0u;
-    const unsigned touch = OCC ? (__reduce_or_sync(am, U | mo_old | mr_old) & full) : full;
-    for (unsigned m = touch; m; m &= m - 1u) {
-        const int a = __ffs(m) - 1;
-        const long long fo = (long long)a * Vs;
-        T w = ((U >> a) & 1u) ? nv[a] : (T)0;
-        if (PROJ) w = (bestid >= 0) ? ((a == bestid) ? (T)1 : (T)0) : w * inv;
-        if (R0OUT) {
-            T r = (T)0;
-            if ((actmask >> a) & 1u) { r = S.lap[kr][tid]; kr++; }
-            if (fix) r = (w - ldg(P.in + fo + i)) / b1c;
-            if (r != (T)0) nrmask |= 1u << a;
-            if (!OCC || r != (T)0 || ((mr_old >> a) & 1u)) (P.r0out + fo)[i32] = r;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        if (w >= nwr) break;
+        const unsigned full = word_bits(N, w);
+        const long long ow = (long long)w * Vs + i;
+        const unsigned mo_old = OCC ? P.m_out[ow] : 0u;
+        const unsigned mr_old = (R0OUT && OCC) ? P.m_r0out[ow] : 0u;
+        const unsigned touch = OCC ? (__reduce_or_sync(am, U[w] | mo_old | mr_old) & full) : full;
+        unsigned nmask = 0u, nrmask = 0u;
+        for (unsigned m = touch; m; m &= m - 1u) {
+            const int bit = __ffs(m) - 1;
+            const int a = 32 * w + bit;
+            const long long fo = (long long)a * Vs;
+            T wv = ((U[w] >> bit) & 1u) ? nv[a] : (T)0;
+            if (PROJ) wv = (bestid >= 0) ? ((a == bestid) ? (T)1 : (T)0) : wv * inv;
+            if (R0OUT) {
+                T r = (T)0;
+                if ((actmask[w] >> bit) & 1u) { r = S.lap[kr][tid]; kr++; }
+                if (fix) r = (wv - ldg(P.in + fo + i)) / b1c;
+                if (r != (T)0) nrmask |= 1u << bit;
+                if (!OCC || r != (T)0 || ((mr_old >> bit) & 1u)) (P.r0out + fo)[i32] = r;
+            }
+            if (wv != (T)0) nmask |= 1u << bit;
+            if (!OCC || wv != (T)0 || ((mo_old >> bit) & 1u)) (P.out + fo)[i32] = wv;
         }
-        if (w != (T)0) nmask |= 1u << a;
-        if (!OCC || w != (T)0 || ((mo_old >> a) & 1u)) (P.out + fo)[i32] = w;
-    }
-    if (OCC) {
-        P.m_out[i] = nmask;
-        if (R0OUT) P.m_r0out[i] = nrmask;
+        if (OCC) {
+            P.m_out[ow] = nmask;
+            if (R0OUT) P.m_r0out[ow] = nrmask;
+        }
     }
     if (KC) {
         const long long o = (long long)N * Vs + i;
@@ -1501,9 +1544,10 @@ fast_kernel(const Geom g, const Pass<float> P, const float *__restrict__ tabA, c
         ld.p2 = P.p2;
         ld.r0 = P.r0in;
         if (MASK)
-            masked_cell<DIM, KC, SIG, true>(g, P, S, tid, i, off, ghost, tabA, tabB, tabL, ptype, esum, ecnt, am);
+            masked_cell<DIM, KC, SIG, true, (NMAX + 31) / 32>(g, P, S, tid, i, off, ghost, tabA, tabB, tabL, ptype,
+                                                              esum, ecnt, am);
         else if (PF_DENSE_ROLLED || (SIG & SIG_ERR) != 0)
-            masked_cell<DIM, KC, SIG, false>(g, P, S, tid, i, off, ghost, tabA, tabB, tabL, ptype, esum, ecnt, am);
+            masked_cell<DIM, KC, SIG, false, 1>(g, P, S, tid, i, off, ghost, tabA, tabB, tabL, ptype, esum, ecnt, am);
         else
             fast_cell<DIM, KC, SIG, NMAX>(g, P, ld, S, tid, i, off, ghost, tabA, tabB, tabL, ptype, esum, ecnt);
     }

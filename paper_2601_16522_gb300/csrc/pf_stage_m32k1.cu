@@ -9,7 +9,7 @@ int launch_m32k1(const Geom &g, const Pass<float> &P, unsigned sig, cudaStream_t
     const dim3 grid(g.tiles_x, g.tiles_y, g.nz);
     const size_t smf = sizeof(ListSmem<float>);
     *done = true;
-    if (g.N <= 32 && g.Vs < 0x7fffffffLL) {
+    if (g.N <= 128 && g.Vs < 0x7fffffffLL) {
         if (g.N <= 4) {
             if (g.dim == 2 && sig == (SIG_PROJECT)) {
                 fast_kernel<2, 1, SIG_PROJECT, 4, true><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
@@ -60,7 +60,7 @@ int launch_m32k1(const Geom &g, const Pass<float> &P, unsigned sig, cudaStream_t
                 return (int)cudaGetLastError();
             }
         }
-        if (g.N > 4) {
+        if (g.N > 4 && g.N <= 32) {
             if (g.dim == 2 && sig == (SIG_PROJECT)) {
                 fast_kernel<2, 1, SIG_PROJECT, 32, true><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
                 return (int)cudaGetLastError();
@@ -110,6 +110,56 @@ int launch_m32k1(const Geom &g, const Pass<float> &P, unsigned sig, cudaStream_t
                 return (int)cudaGetLastError();
             }
         }
+        if (g.N > 32) {
+            if (g.dim == 2 && sig == (SIG_PROJECT)) {
+                fast_kernel<2, 1, SIG_PROJECT, 128, true><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 2 && sig == (SIG_P2 | SIG_PROJECT)) {
+                fast_kernel<2, 1, SIG_P2 | SIG_PROJECT, 128, true><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 2 && sig == (SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT)) {
+                fast_kernel<2, 1, SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT, 128, true><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 2 && sig == (SIG_R0OUT | SIG_PROJECT)) {
+                fast_kernel<2, 1, SIG_R0OUT | SIG_PROJECT, 128, true><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 2 && sig == (SIG_ERR)) {
+                fast_kernel<2, 1, SIG_ERR, 128, true><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 2 && sig == (SIG_P0 | SIG_PROJECT)) {
+                fast_kernel<2, 1, SIG_P0 | SIG_PROJECT, 128, true><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 3 && sig == (SIG_PROJECT)) {
+                fast_kernel<3, 1, SIG_PROJECT, 128, true><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 3 && sig == (SIG_P2 | SIG_PROJECT)) {
+                fast_kernel<3, 1, SIG_P2 | SIG_PROJECT, 128, true><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 3 && sig == (SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT)) {
+                fast_kernel<3, 1, SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT, 128, true><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 3 && sig == (SIG_R0OUT | SIG_PROJECT)) {
+                fast_kernel<3, 1, SIG_R0OUT | SIG_PROJECT, 128, true><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 3 && sig == (SIG_ERR)) {
+                fast_kernel<3, 1, SIG_ERR, 128, true><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 3 && sig == (SIG_P0 | SIG_PROJECT)) {
+                fast_kernel<3, 1, SIG_P0 | SIG_PROJECT, 128, true><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+        }
     }
     *done = false;
     return 0;
@@ -142,6 +192,18 @@ int prepare_m32k1()
     if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_R0OUT | SIG_PROJECT, 32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_ERR, 32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_P0 | SIG_PROJECT, 32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_PROJECT, 128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_P2 | SIG_PROJECT, 128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT, 128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_R0OUT | SIG_PROJECT, 128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_ERR, 128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_P0 | SIG_PROJECT, 128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_PROJECT, 128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_P2 | SIG_PROJECT, 128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT, 128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_R0OUT | SIG_PROJECT, 128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_ERR, 128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_P0 | SIG_PROJECT, 128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     return 1;
 }
 

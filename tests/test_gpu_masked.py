@@ -18,7 +18,8 @@ from test_gpu_parity import CASES, pf  # noqa: F401  (fixture)
 
 pytestmark = pytest.mark.gpu
 
-ELIGIBLE = [c for c in CASES if c[1].n_phases <= 32]
+ELIGIBLE = [c for c in CASES if c[0] != "blobs3d_N70"]
+N70 = [c for c in CASES if c[0] == "blobs3d_N70"][0]
 TOL = (1e-4, 1e-3, 1e-4, 1e-3)
 
 
@@ -40,6 +41,15 @@ def test_masked_fixed_steps_equal_dense(pf, name, prob, u, integ, kw):
     dense, st_d = _run(pf, prob, u, 0, integ, n, **kw)
     masked, st_m = _run(pf, prob, u, pf.Simulation.OPT_MASKED, integ, n, **kw)
     assert st_d["rhs_evals"] == st_m["rhs_evals"]
+    assert np.array_equal(masked, dense), np.abs(masked - dense).max()
+
+
+def test_masked_three_words_fe_equal_dense(pf):
+    # 70 phases: three occupancy words per cell; one forward Euler step (the
+    # 70-phase blob state exceeds the 12-phase list capacity after that)
+    name, prob, u = N70
+    dense, st_d = _run(pf, prob, u, 0, ref.FEULER, 0.9, dt_mult=0.9)
+    masked, st_m = _run(pf, prob, u, pf.Simulation.OPT_MASKED, ref.FEULER, 0.9, dt_mult=0.9)
     assert np.array_equal(masked, dense), np.abs(masked - dense).max()
 
 
@@ -91,13 +101,11 @@ def test_masked_graph_replay_equals_launches(pf):
 
 
 def test_masked_eligibility_and_footprint(pf):
-    name, prob, u = [c for c in CASES if c[1].n_phases > 32][0]
-    with pytest.raises(RuntimeError):
-        pf.Simulation(prob, precision=32, options=pf.Simulation.OPT_MASKED)
     name, prob, u = ELIGIBLE[0]
     with pytest.raises(RuntimeError):
         pf.Simulation(prob, precision=64, options=pf.Simulation.OPT_MASKED)
-    d = pf.footprint(prob, 32)
-    m = pf.footprint(prob, 32, options=pf.Simulation.OPT_MASKED)
-    Vs = (prob.V + 63) // 64 * 64
-    assert m - d == 5 * Vs * 4
+    for name, prob, u in (ELIGIBLE[0], N70):
+        d = pf.footprint(prob, 32)
+        m = pf.footprint(prob, 32, options=pf.Simulation.OPT_MASKED)
+        Vs = (prob.V + 63) // 64 * 64
+        assert m - d == 5 * ((prob.n_phases + 31) // 32) * Vs * 4
