@@ -336,7 +336,7 @@ def served_stream(pf, torch, n_requests, rate=50.0):
     s = serve.summary(finished, makespan)
     s.update({"arrival_rate_per_s": rate, "workers": 8, "mem_budget_bytes": srv.budget,
               "peak_admitted_bytes": srv.peak_used,
-              "mix": "circles, Stefan strips, 2D/3D Voronoi grains (N 2..32), FE/SSP2/RKL1/RKL2, FP32, "
+              "mix": "circles, Stefan strips, 2D/3D Voronoi grains (N 2..32, masked storage), FE/SSP2/RKL1/RKL2, FP32, "
                      "100 stable-Euler steps of simulated time each"})
     return s
 

@@ -34,6 +34,7 @@ class Request:
     tol: Optional[tuple] = None     # adaptive when set, else fixed dt_mult
     dt_mult: float = 0.0
     precision: int = 32
+    options: int = 0                # pf_params.options (e.g. masked storage)
     arrival: float = 0.0            # seconds after the start of the stream
     # filled in by the server
     admitted: float = float("nan")
@@ -44,7 +45,7 @@ class Request:
 
     @property
     def footprint(self):
-        return pf.footprint(self.prob, self.precision)
+        return pf.footprint(self.prob, self.precision, self.options)
 
     @property
     def latency(self):
@@ -55,7 +56,7 @@ def run_alone(req: Request, stream=None):
     """Run one request by itself (reference for the batching invariance)."""
     import torch
     stream = stream or torch.cuda.Stream()
-    with pf.Simulation(req.prob, precision=req.precision, stream=stream) as sim:
+    with pf.Simulation(req.prob, precision=req.precision, stream=stream, options=req.options) as sim:
         sim.set_state(req.u0)
         st = _advance(sim, req)
         out, _ = sim.get_state()
@@ -159,8 +160,9 @@ def poisson_stream(n, rate=50.0, seed=4, sizes2d=(64, 128, 256, 512, 1024), size
                    phases=(2, 3, 8, 16, 32), steps=100, device="cuda"):
     """Seeded mixed stream shaped like the paper's benchmarks: shrinking
     circles and Stefan strips (2D, N = 2) and Voronoi grain structures (2D/3D,
-    N up to 32); integrators and tolerances drawn uniformly.  Each request
-    runs for `steps` stable Euler steps of simulated time."""
+    N up to 32, in masked storage); integrators and tolerances drawn
+    uniformly.  Each request runs for `steps` stable Euler steps of
+    simulated time."""
     rng = np.random.default_rng(seed)
     t = 0.0
     reqs = []
@@ -184,7 +186,9 @@ def poisson_stream(n, rate=50.0, seed=4, sizes2d=(64, 128, 256, 512, 1024), size
             u = u.cpu().numpy()
         integ = int(rng.choice([pf.FEULER, pf.RKL1, pf.RKL2, pf.SSP2]))
         a_phi = float(rng.choice([1e-2, 1e-3, 1e-4]))
-        req = Request(rid=rid, prob=prob, u0=u, integ=integ, t_end=0.0, arrival=t)
+        # grain structures run in masked storage (only occupied phases are loaded)
+        opts = pf.Simulation.OPT_MASKED if kind == 2 else 0
+        req = Request(rid=rid, prob=prob, u0=u, integ=integ, t_end=0.0, arrival=t, options=opts)
         if integ in (pf.RKL1, pf.RKL2):
             req.tol = (1e-4, a_phi, 1e-4, 1e-4)
         else:
