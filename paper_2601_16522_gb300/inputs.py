@@ -124,6 +124,22 @@ def circle(n=128, R0=40.0, W=5.0 / math.pi, M=1.0, gamma=1.0, dx=1.0, ny=None):
     return prob, u
 
 
+def phase_embedding(n=128, r=32.0, W=3.0, D=100.0, k=500.0, c0=(0.02, 0.98), M=1.0, gamma=1.0, dx=1.0):
+    """Phase embedding (Sec. 5.1.1): a circle of phase 1 (type beta) of
+    radius r (distance d = r - |X - C|, Eq. centersphere) in phase 0 (type
+    alpha), both at their flat equilibrium concentrations, c = sum phi_a
+    c0_a (mu = 0); 2D periodic, K = 1, equal k (Tab. params), D = 100 as the
+    paper uses for equilibrium runs, W = 3 dx^0.4 at dx = 1."""
+    prob = Problem(dim=2, nx=n, ny=n, nz=1, dx=dx, n_phases=2, phase_type=np.array([0, 1], np.int32),
+                   gamma=uniform_pairs(2, gamma), mobility=uniform_pairs(2, M), W=W, has_conc=1,
+                   k=(k, k), c0=tuple(c0), D=(D, D), name="embedding%d" % n)
+    x, y, _ = cell_centres(n, n, 1, dx)
+    cx = cy = n * dx / 2.0
+    g = profile(r - np.sqrt((x - cx) ** 2 + (y - cy) ** 2), W)
+    u = np.stack([1.0 - g, g, (1.0 - g) * c0[0] + g * c0[1]])
+    return prob, u
+
+
 def stefan_L(W, k=1.0, dc=0.96, D=1.0, MF=0.3084251):
     """Thin-interface phase-field mobility for vanishing kinetic coefficient
     (Eq. thin-interface, Sec. 5.2.2): L = pi^2/(16 W^2) D (dc/dmu) / (dc_eq^2 (M+F)),
