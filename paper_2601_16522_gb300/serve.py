@@ -51,6 +51,13 @@ class Request:
     def latency(self):
         return self.finished - self.arrival
 
+    def describe(self):
+        p = self.prob
+        size = "x".join(str(v) for v in ((p.nx, p.ny) if p.dim == 2 else (p.nx, p.ny, p.nz)))
+        return "request %d: %s %s, %d phases%s, integrator %d, %s" % (
+            self.rid, p.name or "problem", size, p.n_phases, " + c" if p.has_conc else "", self.integ,
+            "tol %s" % (self.tol,) if self.tol is not None else "dt_mult %g" % self.dt_mult)
+
 
 def run_alone(req: Request, stream=None):
     """Run one request by itself (reference for the batching invariance)."""
@@ -117,7 +124,7 @@ class Server:
                 out, st = self.runner(req, streams[sidx])
                 req.result, req.stats = out, st
             except Exception as exc:                  # reported per request
-                req.error = str(exc)
+                req.error = "%s (%s)" % (exc, req.describe())
             req.finished = time.perf_counter() - t0
             with self.lock:
                 self.used -= fp[req.rid]
@@ -210,8 +217,8 @@ def summary(finished, makespan):
     ok = [r for r in finished if r.error is None]
     lat = np.array([r.latency for r in ok]) if ok else np.zeros(1)
     cells = sum(r.prob.V * r.stats["rhs_evals"] for r in ok)
-    errors = sorted({r.error for r in finished if r.error is not None})
+    errors = [r.error for r in finished if r.error is not None]
     return {"requests": len(finished), "completed": len(ok), "rejected": len(finished) - len(ok),
-            "errors": errors[:3],
+            "errors": errors[:5],
             "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
             "makespan_s": makespan, "gcell_updates_per_s": cells / makespan / 1e9}
