@@ -378,6 +378,39 @@ def masked_run(pf, torch, prob, u, stream, args, world, dev, dense_out, dense_pa
             "storage": "dense phase planes + one 32-bit occupancy word per cell and vector"}
 
 
+def reuse_run(pf, torch, prob, u, stream, args, world, dev, dense_out, dense_ms):
+    """The bench steps again with F(u^{n+1}) of each accepted step reused as
+    the next step's F(u^n) (PF_STEP_REUSE_RHS): time per step, RHS sweeps,
+    and the largest difference from the dense run's final state."""
+    V = prob.V
+    sim = pf.Simulation(prob, precision=32, stream=stream)
+    sim.set_state(u)
+    f = pf.Simulation.STEP_REUSE_RHS
+    for _ in range(args.warmup):
+        sim.step(pf.RKL2, 1e30, tol=TOL, max_attempts=1, flags=f)
+    torch.cuda.synchronize()
+    barrier(world)
+    sim.profile(1)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    sweeps = 0
+    for _ in range(args.steps):
+        sweeps += sim.step(pf.RKL2, 1e30, tol=TOL, max_attempts=1, flags=f)["rhs_evals"]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(ev0.elapsed_time(ev1), world, dev)
+    prof = sim.profile(0)
+    out = torch.empty_like(dense_out)
+    sim.get_state(out=out)
+    diff = float((out - dense_out).abs().max())
+    sim.close()
+    return {"ms_per_step": ms / args.steps, "dense_ms_per_step": dense_ms / args.steps, "rhs_sweeps": sweeps,
+            "value": aggregate_value(V, sweeps, ms, world), "unit": UNIT,
+            "pass_ms": {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items() if v[1] > 0},
+            "max_abs_diff_to_dense": diff}
+
+
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
@@ -462,10 +495,13 @@ def run_ours(args, world, rank, local):
     # masked storage (the GPU form of the per-cell phase lists): the same
     # steps from the same state; its result must equal the dense one
     masked = None
+    reuse = None
     if not args.no_masked and prec == 32 and N <= 128:
         dense_out = torch.empty((N + prob.has_conc, V), dtype=torch.float64, device=dev)
         sim.get_state(out=dense_out)
         masked = masked_run(pf, torch, prob, u, stream, args, world, dev, dense_out, pass_ms)
+        if not args.no_reuse:
+            reuse = reuse_run(pf, torch, prob, u, stream, args, world, dev, dense_out, ms_max)
         del dense_out
 
     # end-to-end through the C ABI with pinned host buffers
@@ -526,7 +562,7 @@ def run_ours(args, world, rank, local):
             "sweeps": sweeps, "stages_per_step": ss, "accepted": acc,
             "roofline": roof, "pass_ms": pass_ms,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
-            "time_to_solution": tts, "served": served, "masked": masked,
+            "time_to_solution": tts, "served": served, "masked": masked, "reuse_rhs": reuse,
         }
         print(json.dumps(line), flush=True)
     sim.close()
@@ -545,6 +581,7 @@ def main():
     ap.add_argument("--no-tts", action="store_true", help="skip the 2D time-to-solution runs")
     ap.add_argument("--served", type=int, default=48, help="requests in the served Poisson stream (0: skip)")
     ap.add_argument("--no-masked", action="store_true", help="skip the masked-storage run")
+    ap.add_argument("--no-reuse", action="store_true", help="skip the run that reuses F(u^{n+1})")
     args = ap.parse_args()
     world, rank, local = dist_setup(args)
     if args.impl == "reference":

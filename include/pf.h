@@ -126,8 +126,18 @@ typedef struct {
    captures the smallest group of full steps after which the buffer rotation
    repeats into a CUDA graph (cached per handle) and replays it; results are
    identical to launching the passes one by one.  PF_STEP_NO_GRAPH disables
-   that. */
-enum { PF_STEP_NO_GRAPH = 1 };
+   that.
+   PF_STEP_REUSE_RHS (adaptive RKL1/RKL2, dense storage) reuses F(u^{n+1}),
+   which the error sweep of Sec. 3.3 evaluates anyway, as the next step's
+   F(u^n) (the footnote on the Sommeijer estimate notes the paper's code
+   does not): the error sweep also stores it, and after an accepted step the
+   first stage is a pointwise pass u1 = S(u^n + mu~_1 dt F) (with the RKL2
+   first-stage fix) instead of a stencil sweep.  One RHS evaluation fewer per
+   accepted step; rhs_evals counts what was evaluated.  The trajectory is the
+   one without reuse up to rounding.  The stored RHS belongs to the state it
+   was computed from: pf_set_state, a rejected attempt or a step without the
+   flag drop it. */
+enum { PF_STEP_NO_GRAPH = 1, PF_STEP_REUSE_RHS = 2 };
 
 typedef struct {
     long long rhs_evals;       /* RHS sweeps, including rejected steps and STS error sweeps */

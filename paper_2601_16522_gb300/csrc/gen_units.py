@@ -4,7 +4,8 @@ signatures; the written files are committed, and build.py compiles them).
 
 pf_stage_f64.cu      FP64: the generic stage kernel, 2D/3D, K = 0/1
 pf_stage_f32k{0,1}   FP32, K fixed: big_kernel (32 < N <= 250), tma_kernel and
-                     fast_kernel (N <= 32, NMAX 4 or 32) per pass signature,
+                     fast_kernel (N <= 32, NMAX 4 or 32) per pass signature
+                     (fast_kernel also for the error sweep that keeps its RHS),
                      and the generic kernel as the fallback
 pf_stage_m32k{0,1}   FP32 masked storage, K fixed: fast_kernel<..., true> per
                      pass signature for N <= 4, N <= 32 and N <= 128
@@ -17,6 +18,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 # RKL1 body, RKL2 body, RKL stage 1, error sweep, SSP2 final combination
 SIGS = ["SIG_PROJECT", "SIG_P2 | SIG_PROJECT", "SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT",
         "SIG_R0OUT | SIG_PROJECT", "SIG_ERR", "SIG_P0 | SIG_PROJECT"]
+# the dense fast kernel also has the error sweep that keeps F(u^{n+1})
+FAST_SIGS = SIGS + ["SIG_ERR | SIG_R0OUT"]
 
 
 def unit(T, kcs, fast, fname):
@@ -55,7 +58,7 @@ def unit(T, kcs, fast, fname):
         for nmax in (4, 32):
             L.append("        if (%s) {" % ("g.N <= 4" if nmax == 4 else "g.N > 4"))
             for d in (2, 3):
-                for sg in SIGS:
+                for sg in FAST_SIGS:
                     L.append("            if (g.dim == %d && sig == (%s)) {" % (d, sg))
                     L.append("                fast_kernel<%d, %d, %s, %d><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);" % (d, kc, sg, nmax))
                     L.append("                return (int)cudaGetLastError();")

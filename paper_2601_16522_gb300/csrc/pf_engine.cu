@@ -128,6 +128,56 @@ __global__ void totals_kernel(const T *__restrict__ u, long long V, long long Vs
 }
 
 
+// RKL stage 1 from a stored RHS (reuse of F(u^{n+1}) of the previous error
+// sweep as F(u^n)): u1 = S(u^n + b1 F) with the simplex projection of
+// Sec. 3.1 in the stage kernels' order (clamp, largest value >= 1 with ties
+// to the lowest id, division by the sum), and the RKL2 first-stage fix
+// F <- (S(u1) - u^n) / b1 in every phase of a cell where S acted (fix != 0).
+// The stored RHS is updated in place (each thread reads and writes only its
+// own cell).  Pass 1 writes the unprojected values to out; pass 2 rereads
+// them (the same thread wrote them).
+template <typename T>
+__global__ void first_from_rhs_kernel(const T *__restrict__ in, T *out, T *r0, long long V, long long Vs, int N, int K,
+                                      double b1, int fix, int *flag)
+{
+    const T one = (T)1, b1c = (T)b1;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < V; i += (long long)gridDim.x * blockDim.x) {
+        bool changed = false;
+        T best = (T)-1, ssum = (T)0;
+        int bestid = -1, nnz = 0;
+        for (int a = 0; a < N; ++a) {
+            const long long o = (long long)a * Vs + i;
+            T acc = one * in[o];
+            acc = acc + b1c * r0[o];
+            if (acc < (T)0) { acc = (T)0; changed = true; }
+            if (acc >= (T)1 && acc > best) { best = acc; bestid = a; }
+            if (acc != (T)0) nnz++;
+            ssum = ssum + acc;
+            out[o] = acc;
+        }
+        if (bestid >= 0) {
+            if (!(best == (T)1 && nnz == 1)) changed = true;
+            ssum = (T)1;
+        }
+        if (!(ssum > (T)0)) atomicOr(flag, pfk::FLAG_SIMPLEX);
+        const bool fx = fix && changed;
+        for (int a = 0; a < N; ++a) {
+            const long long o = (long long)a * Vs + i;
+            T w = out[o];
+            if (bestid >= 0) w = (a == bestid) ? (T)1 : (T)0;
+            else if (ssum > (T)0) w = w / ssum;
+            out[o] = w;
+            if (fx) r0[o] = (w - in[o]) / b1c;
+        }
+        if (K) {
+            const long long o = (long long)N * Vs + i;
+            T acc = one * in[o];
+            acc = acc + b1c * r0[o];
+            out[o] = acc;
+        }
+    }
+}
+
 // Energy functional of Eq. energy, one cell per thread, accumulated in FP64.
 // The gradients are forward differences across the +x, +y, +z faces (a
 // zero-gradient ghost across a non-periodic face).  Only phases that are
@@ -263,6 +313,11 @@ struct pf_handle {
     double b = 0.9, E1 = 0.0, E2 = 0.0, dt1 = 0.0, dt2 = 0.0;
     int nhist = 0;
     double dt_next = 0.0;
+    // reuse of F(u^{n+1}) as the next step's F(u^n) (PF_STEP_REUSE_RHS):
+    // buffer rhs_buf holds the raw RHS of the state in buffer rhs_iu
+    bool reuse_on = false, rhs_valid = false;
+    int rhs_buf = -1, rhs_iu = -1;
+    int rhs_pending = -1;              // buffer the last error sweep wrote F(u^{n+1}) into
 };
 
 namespace {
@@ -586,6 +641,8 @@ void reset_controller(pf_handle *h)
     h->dt_next = 0.0;
 }
 
+int grid_for(long long n) { long long b = (n + 255) / 256; return (int)(b < 4096 ? (b > 0 ? b : 1) : 4096); }
+
 // ---- one step ---------------------------------------------------------------
 // Runs the stages of one step of size dt with s stages from buf[iu].  On
 // return *out is the buffer index holding the candidate u^{n+1}; when
@@ -666,12 +723,30 @@ int do_step(pf_handle *h, int integ, double dt, int s, const pf_tol *tol, bool w
     }
     // RKL1 / RKL2 (Eq. sts), ring of three stage buffers plus F(u^n)
     const bool o2 = (integ == PF_RKL2);
-    const int ring[3] = {w[0], w[1], w[2]};
-    const int r0 = w[3];
+    // F(u^n) kept by the previous accepted step's error sweep (reuse)
+    const bool reuse = h->reuse_on && h->rhs_valid && h->rhs_iu == U && h->rhs_buf >= 0 && h->rhs_buf != U;
+    int ring[3] = {w[0], w[1], w[2]};
+    int r0 = w[3];
+    if (reuse) {
+        r0 = h->rhs_buf;
+        int n = 0;
+        for (int k = 0; k < NBUF; ++k) if (k != U && k != r0) ring[n++] = k;
+    }
     const double ds = (double)s;
     const double w1 = o2 ? 4.0 / (ds * ds + ds - 2.0) : 2.0 / (ds * ds + ds);
     const double mt1 = o2 ? rkl2_b(1) * w1 : w1;
-    {
+    if (reuse) {
+        // stage 1 from the stored F(u^n): no RHS evaluation; the stored RHS is
+        // consumed (replaced by the effective one where the fix applies)
+        h->cur_kind = PF_PASS_STS_FIRST;
+        if ((st = prof_begin(h))) return st;
+        first_from_rhs_kernel<T><<<grid_for(h->V), 256, 0, h->stream>>>(B(U), B(ring[0]), B(r0), h->V, h->Vs, h->N,
+                                                                         h->K, mt1 * dt, o2 ? 1 : 0, h->dflag);
+        h->launches++;
+        if (cudaGetLastError() != cudaSuccess) return PF_EDEVICE;
+        if ((st = prof_end(h))) return st;
+        h->rhs_valid = false;
+    } else {
         h->cur_kind = PF_PASS_STS_FIRST;
         Pass<T> P = blank_pass<T>(h);
         P.in = B(U); P.a1 = 1.0; P.b1 = mt1 * dt; P.out = B(ring[0]); P.r0out = B(r0); P.fix_first = o2 ? 1 : 0;
@@ -701,14 +776,20 @@ int do_step(pf_handle *h, int integ, double dt, int s, const pf_tol *tol, bool w
         if ((st = run_pass<T>(h, P))) return st;
     }
     const int fin = ring[(s - 1) % 3];
-    *evals += s;
+    *evals += reuse ? s - 1 : s;
+    h->rhs_pending = -1;
     if (want_err) {
-        // Sommeijer estimate with F(u^{n+1}) (Sec. 3.3): one more RHS sweep
+        // Sommeijer estimate with F(u^{n+1}) (Sec. 3.3): one more RHS sweep;
+        // with reuse it also keeps F(u^{n+1}) in a stage buffer it no longer needs
         h->cur_kind = PF_PASS_STS_ERR;
         Pass<T> P = blank_pass<T>(h);
         P.mode = pfk::MODE_ERR;
         P.in = B(fin); P.p0 = B(U); P.r0in = B(r0); P.dt = dt; P.project = 0;
         P.r_phi = tol->r_phi; P.a_phi = tol->a_phi; P.r_c = tol->r_c; P.a_c = tol->a_c;
+        if (h->reuse_on) {
+            h->rhs_pending = ring[(s + 1) % 3];
+            P.r0out = B(h->rhs_pending);
+        }
         if ((st = run_pass<T>(h, P))) return st;
         *evals += 1;
     }
@@ -825,6 +906,9 @@ int step_loop(pf_handle *h, int integ, double t_end, const pf_tol *tol, const pf
         if (nfix < 1) nfix = 1;
     }
     if (cudaMemsetAsync(h->dflag, 0, sizeof(int), h->stream) != cudaSuccess) return PF_EDEVICE;
+    // reuse of F(u^{n+1}): adaptive RKL steps in dense storage only
+    h->reuse_on = (o->flags & PF_STEP_REUSE_RHS) && adaptive && sts && !h->masked;
+    if (!h->reuse_on) h->rhs_valid = false;
     const bool graphs = !adaptive && h->stream != nullptr && !h->prof_on && !(o->flags & PF_STEP_NO_GRAPH) &&
                         o->max_attempts == 0 && o->trace_cap == 0;
     while (h->t < t_end) {
@@ -896,7 +980,13 @@ int step_loop(pf_handle *h, int integ, double t_end, const pf_tol *tol, const pf
             if (!adaptive) { kfix++; h->t = last ? t_end : t0 + (double)kfix * dt; }
             else h->t = last ? t_end : h->t + hs;
             acc_n++;
+            if (h->reuse_on && h->rhs_pending >= 0) {
+                h->rhs_valid = true;
+                h->rhs_buf = h->rhs_pending;
+                h->rhs_iu = cand;
+            }
         } else {
+            h->rhs_valid = false;
             rej_n++;
             if (rej_n > 100000) { status = PF_EUNSTABLE; break; }
         }
@@ -918,7 +1008,6 @@ int step_loop(pf_handle *h, int integ, double t_end, const pf_tol *tol, const pf
     return status;
 }
 
-int grid_for(long long n) { long long b = (n + 255) / 256; return (int)(b < 4096 ? (b > 0 ? b : 1) : 4096); }
 
 template <typename T>
 int set_state_t(pf_handle *h, const double *src_dev)
@@ -1256,6 +1345,7 @@ int pf_set_state(pf_handle *h, const double *phi, const double *c, double t, int
     if (!ptr_is_device && cudaStreamSynchronize(h->stream) != cudaSuccess) return PF_EDEVICE;
     h->t = t;
     h->has_state = true;
+    h->rhs_valid = false;
     reset_controller(h);
     return PF_OK;
 }

@@ -376,6 +376,7 @@ cell_kernel(const Geom g, const Pass<T> P, const T *__restrict__ tabA, const T *
             for (int a = 0; a < N; ++a, o += Vs) {
                 T r1 = (T)0;
                 PF_NEXT_RHS(a, r1)
+                if (P.r0out) P.r0out[o] = r1;      // F(u^{n+1}) kept for reuse
                 const T un = ldg(P.p0 + o), un1 = ldg(P.in + o), rn = ldg(P.r0in + o);
                 const T sr = rn + r1;
                 T e = ((T)12 * (un - un1) + ((T)6 * dt) * sr) / (T)15;
@@ -392,6 +393,7 @@ cell_kernel(const Geom g, const Pass<T> P, const T *__restrict__ tabA, const T *
             ecnt += (nc > 0 ? nc : 2);
             if (K) {
                 const long long oc = (long long)N * Vs + i;
+                if (P.r0out) P.r0out[oc] = rc;
                 const T un = ldg(P.p0 + oc), un1 = ldg(P.in + oc), rn = ldg(P.r0in + oc);
                 const T sr = rn + rc;
                 const T e = ((T)12 * (un - un1) + ((T)6 * dt) * sr) / (T)15;
@@ -1160,6 +1162,17 @@ __device__ __forceinline__ void masked_cell(const Geom &g, const Pass<float> &P,
         }
     }
     if (ERR) {
+        if constexpr (R0OUT && !OCC) {
+            // keep F(u^{n+1}), the RHS just evaluated, for reuse as the next
+            // step's F(u^n) (listed phases in ascending order, others zero)
+            int kr = 0;
+            for (int a = 0; a < N; ++a) {
+                T r = (T)0;
+                if (kr < nz && S.id[kr][tid] == a) { r = S.lap[kr][tid]; kr++; }
+                (P.r0out + (long long)a * Vs)[i32] = r;
+            }
+            if (KC) P.r0out[(long long)N * Vs + i] = rc;
+        }
         ecnt += (nc > 0 ? nc : 2);
         if (KC) {
             const long long o = (long long)N * Vs + i;
@@ -1543,10 +1556,10 @@ fast_kernel(const Geom g, const Pass<float> P, const float *__restrict__ tabA, c
         ld.p0 = P.p0;
         ld.p2 = P.p2;
         ld.r0 = P.r0in;
-        if (MASK)
+        if constexpr (MASK)
             masked_cell<DIM, KC, SIG, true, (NMAX + 31) / 32>(g, P, S, tid, i, off, ghost, tabA, tabB, tabL, ptype,
                                                               esum, ecnt, am);
-        else if (PF_DENSE_ROLLED || (SIG & SIG_ERR) != 0)
+        else if constexpr (PF_DENSE_ROLLED || (SIG & SIG_ERR) != 0)
             masked_cell<DIM, KC, SIG, false, 1>(g, P, S, tid, i, off, ghost, tabA, tabB, tabL, ptype, esum, ecnt, am);
         else
             fast_cell<DIM, KC, SIG, NMAX>(g, P, ld, S, tid, i, off, ghost, tabA, tabB, tabL, ptype, esum, ecnt);
@@ -1638,7 +1651,7 @@ tma_kernel(const Geom g, const Pass<float> P, const __grid_constant__ TmaMaps M,
 template <typename T>
 inline unsigned pass_signature(const Pass<T> &P)
 {
-    if (P.mode == MODE_ERR) return SIG_ERR;
+    if (P.mode == MODE_ERR) return P.r0out ? (SIG_ERR | SIG_R0OUT) : SIG_ERR;
     if (P.mode == MODE_RHS) return SIG_RHS;
     if (P.zout || P.embedded_err || P.out2) return SIG_GENERIC;
     unsigned s = 0;

@@ -112,6 +112,10 @@ int launch_f32k1(const Geom &g, const Pass<float> &P, unsigned sig, cudaStream_t
                 fast_kernel<2, 1, SIG_P0 | SIG_PROJECT, 4><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
                 return (int)cudaGetLastError();
             }
+            if (g.dim == 2 && sig == (SIG_ERR | SIG_R0OUT)) {
+                fast_kernel<2, 1, SIG_ERR | SIG_R0OUT, 4><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
             if (g.dim == 3 && sig == (SIG_PROJECT)) {
                 fast_kernel<3, 1, SIG_PROJECT, 4><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
                 return (int)cudaGetLastError();
@@ -134,6 +138,10 @@ int launch_f32k1(const Geom &g, const Pass<float> &P, unsigned sig, cudaStream_t
             }
             if (g.dim == 3 && sig == (SIG_P0 | SIG_PROJECT)) {
                 fast_kernel<3, 1, SIG_P0 | SIG_PROJECT, 4><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 3 && sig == (SIG_ERR | SIG_R0OUT)) {
+                fast_kernel<3, 1, SIG_ERR | SIG_R0OUT, 4><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
                 return (int)cudaGetLastError();
             }
         }
@@ -162,6 +170,10 @@ int launch_f32k1(const Geom &g, const Pass<float> &P, unsigned sig, cudaStream_t
                 fast_kernel<2, 1, SIG_P0 | SIG_PROJECT, 32><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
                 return (int)cudaGetLastError();
             }
+            if (g.dim == 2 && sig == (SIG_ERR | SIG_R0OUT)) {
+                fast_kernel<2, 1, SIG_ERR | SIG_R0OUT, 32><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
             if (g.dim == 3 && sig == (SIG_PROJECT)) {
                 fast_kernel<3, 1, SIG_PROJECT, 32><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
                 return (int)cudaGetLastError();
@@ -184,6 +196,10 @@ int launch_f32k1(const Geom &g, const Pass<float> &P, unsigned sig, cudaStream_t
             }
             if (g.dim == 3 && sig == (SIG_P0 | SIG_PROJECT)) {
                 fast_kernel<3, 1, SIG_P0 | SIG_PROJECT, 32><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 3 && sig == (SIG_ERR | SIG_R0OUT)) {
+                fast_kernel<3, 1, SIG_ERR | SIG_R0OUT, 32><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
                 return (int)cudaGetLastError();
             }
         }
@@ -230,24 +246,28 @@ int prepare_f32k1()
     if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_R0OUT | SIG_PROJECT, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_ERR, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_P0 | SIG_PROJECT, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_ERR | SIG_R0OUT, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_PROJECT, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_P2 | SIG_PROJECT, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_R0OUT | SIG_PROJECT, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_ERR, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_P0 | SIG_PROJECT, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_ERR | SIG_R0OUT, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_PROJECT, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_P2 | SIG_PROJECT, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_R0OUT | SIG_PROJECT, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_ERR, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_P0 | SIG_PROJECT, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_ERR | SIG_R0OUT, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_PROJECT, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_P2 | SIG_PROJECT, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_R0OUT | SIG_PROJECT, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_ERR, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_P0 | SIG_PROJECT, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_ERR | SIG_R0OUT, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(cell_kernel<float, 2, 1, SIG_GENERIC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem<float>)) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(cell_kernel<float, 3, 1, SIG_GENERIC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem<float>)) != cudaSuccess) return -1;
     int nb = 0;
