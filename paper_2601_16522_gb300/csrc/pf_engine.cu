@@ -178,6 +178,60 @@ __global__ void first_from_rhs_kernel(const T *__restrict__ in, T *out, T *r0, l
     }
 }
 
+// The same stage for N <= NMAX phases with the cell's values held in
+// registers: one read of u^n and F, one write of u1, F rewritten only where
+// the fix applies.
+template <typename T, int NMAX>
+__global__ void __launch_bounds__(256)
+first_from_rhs_reg_kernel(const T *__restrict__ in, T *out, T *r0, long long V, long long Vs, int N, int K, double b1,
+                          int fix, int *flag)
+{
+    const T one = (T)1, b1c = (T)b1;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < V; i += (long long)gridDim.x * blockDim.x) {
+        T v[NMAX], acc[NMAX];
+        bool changed = false;
+        T best = (T)-1, ssum = (T)0;
+        int bestid = -1, nnz = 0;
+#pragma unroll
+        for (int a = 0; a < NMAX; ++a) {
+            if (a < N) {
+                const long long o = (long long)a * Vs + i;
+                v[a] = in[o];
+                T x = one * v[a];
+                x = x + b1c * r0[o];
+                if (x < (T)0) { x = (T)0; changed = true; }
+                if (x >= (T)1 && x > best) { best = x; bestid = a; }
+                if (x != (T)0) nnz++;
+                ssum = ssum + x;
+                acc[a] = x;
+            }
+        }
+        if (bestid >= 0) {
+            if (!(best == (T)1 && nnz == 1)) changed = true;
+            ssum = (T)1;
+        }
+        if (!(ssum > (T)0)) atomicOr(flag, pfk::FLAG_SIMPLEX);
+        const bool fx = fix && changed;
+#pragma unroll
+        for (int a = 0; a < NMAX; ++a) {
+            if (a < N) {
+                const long long o = (long long)a * Vs + i;
+                T w = acc[a];
+                if (bestid >= 0) w = (a == bestid) ? (T)1 : (T)0;
+                else if (ssum > (T)0) w = w / ssum;
+                out[o] = w;
+                if (fx) r0[o] = (w - v[a]) / b1c;
+            }
+        }
+        if (K) {
+            const long long o = (long long)N * Vs + i;
+            T x = one * in[o];
+            x = x + b1c * r0[o];
+            out[o] = x;
+        }
+    }
+}
+
 // Energy functional of Eq. energy, one cell per thread, accumulated in FP64.
 // The gradients are forward differences across the +x, +y, +z faces (a
 // zero-gradient ghost across a non-periodic face).  Only phases that are
@@ -740,8 +794,12 @@ int do_step(pf_handle *h, int integ, double dt, int s, const pf_tol *tol, bool w
         // consumed (replaced by the effective one where the fix applies)
         h->cur_kind = PF_PASS_STS_FIRST;
         if ((st = prof_begin(h))) return st;
-        first_from_rhs_kernel<T><<<grid_for(h->V), 256, 0, h->stream>>>(B(U), B(ring[0]), B(r0), h->V, h->Vs, h->N,
-                                                                         h->K, mt1 * dt, o2 ? 1 : 0, h->dflag);
+        if (sizeof(T) == 4 && h->N <= 32)
+            first_from_rhs_reg_kernel<T, 32><<<grid_for(h->V), 256, 0, h->stream>>>(
+                B(U), B(ring[0]), B(r0), h->V, h->Vs, h->N, h->K, mt1 * dt, o2 ? 1 : 0, h->dflag);
+        else
+            first_from_rhs_kernel<T><<<grid_for(h->V), 256, 0, h->stream>>>(B(U), B(ring[0]), B(r0), h->V, h->Vs,
+                                                                             h->N, h->K, mt1 * dt, o2 ? 1 : 0, h->dflag);
         h->launches++;
         if (cudaGetLastError() != cudaSuccess) return PF_EDEVICE;
         if ((st = prof_end(h))) return st;
