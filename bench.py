@@ -365,6 +365,7 @@ def masked_run(pf, torch, prob, u, stream, args, world, dev, dense_out, dense_pa
     prof = sim.profile(0)
     out = torch.empty_like(dense_out)
     sim.get_state(out=out)
+    torch.cuda.synchronize()         # the copy runs on the simulation's stream
     equal = bool(torch.equal(out, dense_out))
     sim.close()
     occ = float((u[:N] != 0).sum(0, dtype=torch.float64).mean())
@@ -394,15 +395,19 @@ def reuse_run(pf, torch, prob, u, stream, args, world, dev, dense_out, dense_ms)
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    sweeps = 0
+    sweeps, stages, accepted = 0, [], 0
     for _ in range(args.steps):
-        sweeps += sim.step(pf.RKL2, 1e30, tol=TOL, max_attempts=1, flags=f)["rhs_evals"]
+        st = sim.step(pf.RKL2, 1e30, tol=TOL, max_attempts=1, flags=f)
+        sweeps += st["rhs_evals"]
+        stages.append(st["rhs_evals"])
+        accepted += st["steps_accepted"]
     ev1.record(stream)
     torch.cuda.synchronize()
     ms = max_over_ranks(ev0.elapsed_time(ev1), world, dev)
     prof = sim.profile(0)
     out = torch.empty_like(dense_out)
     sim.get_state(out=out)
+    torch.cuda.synchronize()         # the copy runs on the simulation's stream
     d = (out - dense_out).abs()
     mean_diff = float(d.mean())
     frac = float((d.amax(0) > 1e-3).double().mean())
@@ -411,6 +416,7 @@ def reuse_run(pf, torch, prob, u, stream, args, world, dev, dense_out, dense_ms)
     # the RHS is discontinuous (activity filter, clamps), so rounding-level
     # differences flip a few cells; the bulk of the state agrees to rounding
     return {"ms_per_step": ms / args.steps, "dense_ms_per_step": dense_ms / args.steps, "rhs_sweeps": sweeps,
+            "sweeps_per_step": stages, "accepted": accepted,
             "value": aggregate_value(V, sweeps, ms, world), "unit": UNIT,
             "pass_ms": {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items() if v[1] > 0},
             "mean_abs_diff_to_dense": mean_diff, "cells_differing_over_1e-3": frac}
@@ -504,6 +510,7 @@ def run_ours(args, world, rank, local):
     if not args.no_masked and prec == 32 and N <= 128:
         dense_out = torch.empty((N + prob.has_conc, V), dtype=torch.float64, device=dev)
         sim.get_state(out=dense_out)
+        torch.cuda.synchronize()
         masked = masked_run(pf, torch, prob, u, stream, args, world, dev, dense_out, pass_ms)
         if not args.no_reuse:
             reuse = reuse_run(pf, torch, prob, u, stream, args, world, dev, dense_out, ms_max)

@@ -128,6 +128,11 @@ __global__ void totals_kernel(const T *__restrict__ u, long long V, long long Vs
 }
 
 
+// Stage 1 from a stored RHS: recompute sweep (1) or store-and-reread (0).
+#ifndef PF_FIRST_RECOMPUTE
+#define PF_FIRST_RECOMPUTE 1
+#endif
+
 // RKL stage 1 from a stored RHS (reuse of F(u^{n+1}) of the previous error
 // sweep as F(u^n)): u1 = S(u^n + b1 F) with the simplex projection of
 // Sec. 3.1 in the stage kernels' order (clamp, largest value >= 1 with ties
@@ -178,33 +183,29 @@ __global__ void first_from_rhs_kernel(const T *__restrict__ in, T *out, T *r0, l
     }
 }
 
-// The same stage for N <= NMAX phases with the cell's values held in
-// registers: one read of u^n and F, one write of u1, F rewritten only where
-// the fix applies.
-template <typename T, int NMAX>
+// The same stage without storing the unprojected values: a first sweep over
+// the phases gathers the projection's sum and decisions, a second sweep
+// recomputes each value from u^n and F and writes it (u^n and F are read
+// twice, the output once).
+template <typename T>
 __global__ void __launch_bounds__(256)
-first_from_rhs_reg_kernel(const T *__restrict__ in, T *out, T *r0, long long V, long long Vs, int N, int K, double b1,
-                          int fix, int *flag)
+first_from_rhs_recompute_kernel(const T *__restrict__ in, T *out, T *r0, long long V, long long Vs, int N, int K,
+                                double b1, int fix, int *flag)
 {
     const T one = (T)1, b1c = (T)b1;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < V; i += (long long)gridDim.x * blockDim.x) {
-        T v[NMAX], acc[NMAX];
         bool changed = false;
         T best = (T)-1, ssum = (T)0;
         int bestid = -1, nnz = 0;
-#pragma unroll
-        for (int a = 0; a < NMAX; ++a) {
-            if (a < N) {
-                const long long o = (long long)a * Vs + i;
-                v[a] = in[o];
-                T x = one * v[a];
-                x = x + b1c * r0[o];
-                if (x < (T)0) { x = (T)0; changed = true; }
-                if (x >= (T)1 && x > best) { best = x; bestid = a; }
-                if (x != (T)0) nnz++;
-                ssum = ssum + x;
-                acc[a] = x;
-            }
+#pragma unroll 8
+        for (int a = 0; a < N; ++a) {
+            const long long o = (long long)a * Vs + i;
+            T x = one * in[o];
+            x = x + b1c * r0[o];
+            if (x < (T)0) { x = (T)0; changed = true; }
+            if (x >= (T)1 && x > best) { best = x; bestid = a; }
+            if (x != (T)0) nnz++;
+            ssum = ssum + x;
         }
         if (bestid >= 0) {
             if (!(best == (T)1 && nnz == 1)) changed = true;
@@ -212,16 +213,18 @@ first_from_rhs_reg_kernel(const T *__restrict__ in, T *out, T *r0, long long V, 
         }
         if (!(ssum > (T)0)) atomicOr(flag, pfk::FLAG_SIMPLEX);
         const bool fx = fix && changed;
-#pragma unroll
-        for (int a = 0; a < NMAX; ++a) {
-            if (a < N) {
-                const long long o = (long long)a * Vs + i;
-                T w = acc[a];
-                if (bestid >= 0) w = (a == bestid) ? (T)1 : (T)0;
-                else if (ssum > (T)0) w = w / ssum;
-                out[o] = w;
-                if (fx) r0[o] = (w - v[a]) / b1c;
-            }
+#pragma unroll 8
+        for (int a = 0; a < N; ++a) {
+            const long long o = (long long)a * Vs + i;
+            const T v = in[o];
+            T x = one * v;
+            x = x + b1c * r0[o];
+            if (x < (T)0) x = (T)0;
+            T w;
+            if (bestid >= 0) w = (a == bestid) ? (T)1 : (T)0;
+            else w = (ssum > (T)0) ? x / ssum : x;
+            out[o] = w;
+            if (fx) r0[o] = (w - v) / b1c;
         }
         if (K) {
             const long long o = (long long)N * Vs + i;
@@ -794,8 +797,8 @@ int do_step(pf_handle *h, int integ, double dt, int s, const pf_tol *tol, bool w
         // consumed (replaced by the effective one where the fix applies)
         h->cur_kind = PF_PASS_STS_FIRST;
         if ((st = prof_begin(h))) return st;
-        if (sizeof(T) == 4 && h->N <= 32)
-            first_from_rhs_reg_kernel<T, 32><<<grid_for(h->V), 256, 0, h->stream>>>(
+        if (PF_FIRST_RECOMPUTE)
+            first_from_rhs_recompute_kernel<T><<<grid_for(h->V), 256, 0, h->stream>>>(
                 B(U), B(ring[0]), B(r0), h->V, h->Vs, h->N, h->K, mt1 * dt, o2 ? 1 : 0, h->dflag);
         else
             first_from_rhs_kernel<T><<<grid_for(h->V), 256, 0, h->stream>>>(B(U), B(ring[0]), B(r0), h->V, h->Vs,
