@@ -208,7 +208,9 @@ class Simulation:
         self._last_in = u
 
     def get_state(self, out=None, with_nz=False):
-        """Returns (u, t[, nz]); out may be a preallocated numpy array or CUDA tensor."""
+        """Returns (u, t[, nz]); out may be a preallocated numpy array or CUDA tensor.
+        Into a CUDA tensor the copy is ordered on the simulation's stream and
+        not waited for: synchronise before reading it from another stream."""
         if out is None:
             out = np.zeros((self.N + self.K, self.V))
         dev = _is_dev(out)
