@@ -709,6 +709,7 @@ __device__ __forceinline__ void fast_cell(const Geom &g, const Pass<float> &P, L
     const int i32 = (int)i;
     const T idx2 = (T)(1.0 / g.dx2);
     const T a0c = (T)P.a0, a1c = (T)P.a1, a2c = (T)P.a2, b1c = (T)P.b1, b0c = (T)P.b0;
+    const T ib1 = (T)(1.0 / P.b1);   // first-stage fix: F <- (S(u1) - u^n) / (mu~_1 dt)
     const T dt = (T)P.dt, rph = (T)P.r_phi, aph = (T)P.a_phi;
 
     // concentration
@@ -910,7 +911,7 @@ __device__ __forceinline__ void fast_cell(const Geom &g, const Pass<float> &P, L
             if (R0OUT) {
                 T r = (T)0;
                 if ((actmask >> a) & 1u) { r = S.lap[kr][tid]; kr++; }
-                if (fix) r = (w - ldg(P.in + fo + i)) / b1c;
+                if (fix) r = (w - ldg(P.in + fo + i)) * ib1;
                 (P.r0out + fo)[i32] = r;
             }
             (P.out + fo)[i32] = w;
@@ -965,6 +966,7 @@ __device__ __forceinline__ void masked_cell(const Geom &g, const Pass<float> &P,
     const int i32 = (int)i;
     const T idx2 = (T)(1.0 / g.dx2);
     const T a0c = (T)P.a0, a1c = (T)P.a1, a2c = (T)P.a2, b1c = (T)P.b1, b0c = (T)P.b0;
+    const T ib1 = (T)(1.0 / P.b1);   // first-stage fix: F <- (S(u1) - u^n) / (mu~_1 dt)
     const T dt = (T)P.dt, rph = (T)P.r_phi, aph = (T)P.a_phi;
 
     // concentration
@@ -1236,7 +1238,7 @@ __device__ __forceinline__ void masked_cell(const Geom &g, const Pass<float> &P,
             if (R0OUT) {
                 T r = (T)0;
                 if ((actmask[w] >> bit) & 1u) { r = S.lap[kr][tid]; kr++; }
-                if (fix) r = (wv - ldg(P.in + fo + i)) / b1c;
+                if (fix) r = (wv - ldg(P.in + fo + i)) * ib1;
                 if (r != (T)0) nrmask |= 1u << bit;
                 if (!OCC || r != (T)0 || ((mr_old >> bit) & 1u)) (P.r0out + fo)[i32] = r;
             }
@@ -1285,6 +1287,7 @@ __device__ __forceinline__ void big_cell(const Geom &g, const Pass<float> &P, Pl
     const int i32 = (int)i;
     const T idx2 = (T)(1.0 / g.dx2);
     const T a0c = (T)P.a0, a1c = (T)P.a1, a2c = (T)P.a2, b1c = (T)P.b1, b0c = (T)P.b0;
+    const T ib1 = (T)(1.0 / P.b1);   // first-stage fix: F <- (S(u1) - u^n) / (mu~_1 dt)
     const T dt = (T)P.dt, rph = (T)P.r_phi, aph = (T)P.a_phi;
     auto combo = [&](T p0v, T v0, T p2v, T r0v) {
         T acc = HP0 ? a0c * p0v + a1c * v0 : a1c * v0;
@@ -1466,7 +1469,7 @@ __device__ __forceinline__ void big_cell(const Geom &g, const Pass<float> &P, Pl
         if (R0OUT) {
             T r = (T)0;
             if (a == curid) { r = S.lap[kr][tid]; kr++; curid = kr < nz ? S.id[kr][tid] : -1; }
-            if (fix) r = (w - ldg(P.in + fo + i)) / b1c;
+            if (fix) r = (w - ldg(P.in + fo + i)) * ib1;
             (P.r0out + fo)[i32] = r;
         }
         (P.out + fo)[i32] = w;

@@ -196,12 +196,33 @@ class Simulation:
         _check(_lib().pf_dt_e(self.h, C.byref(d)), "pf_dt_e")
         return d.value
 
+    def _wait_for_torch(self, t):
+        """Order the simulation's stream after the work torch has queued on
+        its current stream (which may still be writing the tensor t)."""
+        import torch
+        cur = torch.cuda.current_stream(t.device)
+        if self._stream is not None:
+            self._stream.wait_stream(cur)
+        else:
+            cur.synchronize()
+
+    def _torch_waits(self, t):
+        """Order torch's current stream after the simulation's stream (which
+        is writing the tensor t)."""
+        import torch
+        cur = torch.cuda.current_stream(t.device)
+        cur.wait_stream(self._stream if self._stream is not None else torch.cuda.default_stream(t.device))
+
     def set_state(self, u, t=0.0):
-        """u: (N+K, V) float64 numpy array (host) or torch CUDA tensor (device)."""
+        """u: (N+K, V) float64 numpy array (host) or torch CUDA tensor (device).
+        A CUDA tensor is read on the simulation's stream after the work torch
+        has queued on its current stream."""
         dev = _is_dev(u)
         if not dev:
             u = np.ascontiguousarray(u, np.float64)
         assert tuple(u.shape) == (self.N + self.K, self.V), tuple(u.shape)
+        if dev:
+            self._wait_for_torch(u)
         phi = _ptr(u)
         c = phi + 8 * self.N * self.V if self.K else None
         _check(_lib().pf_set_state(self.h, phi, c, float(t), int(dev)), "pf_set_state")
@@ -209,8 +230,8 @@ class Simulation:
 
     def get_state(self, out=None, with_nz=False):
         """Returns (u, t[, nz]); out may be a preallocated numpy array or CUDA tensor.
-        Into a CUDA tensor the copy is ordered on the simulation's stream and
-        not waited for: synchronise before reading it from another stream."""
+        Into a CUDA tensor the copy runs on the simulation's stream, and
+        torch's current stream is made to wait for it."""
         if out is None:
             out = np.zeros((self.N + self.K, self.V))
         dev = _is_dev(out)
@@ -223,7 +244,11 @@ class Simulation:
                 import torch
                 nz = torch.zeros(self.V, dtype=torch.uint8, device=out.device)
         t = C.c_double()
+        if dev:
+            self._wait_for_torch(out)
         _check(_lib().pf_get_state(self.h, phi, c, _ptr(nz), C.byref(t), int(dev)), "pf_get_state")
+        if dev:
+            self._torch_waits(out)
         return (out, t.value, nz) if with_nz else (out, t.value)
 
     def rhs(self):

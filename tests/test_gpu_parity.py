@@ -342,3 +342,24 @@ def test_fp32_step_many_phases(pf, case, integ, mult):
         sim.step(integ, dt, dt_mult=mult)
         ug, _ = sim.get_state()
     assert relerr(ug, un_ref, prob.n_phases, prob.has_conc) < 1e-4
+
+
+def test_device_state_transfer_is_stream_ordered(pf):
+    # a state still being written on torch's stream when set_state is called
+    # (the simulation works on its own stream) arrives complete, and a
+    # device-side get_state is complete before torch reads it
+    import torch
+    prob, u = I.multiphase_blobs(64, 48, 40, 6, seed=21, has_conc=1, n_alpha=2)
+    base = torch.from_numpy(u).cuda()
+    stream = torch.cuda.Stream()
+    with pf.Simulation(prob, precision=64, stream=stream) as sim:
+        for k in range(3):
+            torch.cuda.synchronize()
+            d = torch.zeros_like(base)
+            for _ in range(40):                       # a long chain of work queued on torch's stream
+                d = d * 0.5 + base * 0.5
+            d = d + (base - d)                        # == base, written last
+            sim.set_state(d)
+            out = torch.empty_like(base)
+            sim.get_state(out=out)
+            assert torch.equal(out, base)
