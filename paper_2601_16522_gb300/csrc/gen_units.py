@@ -132,15 +132,19 @@ def munit(kc, fname):
     return "\n".join(L) + "\n"
 
 
-def main():
-    out = {
+def render():
+    """{file name: text} of every instantiation unit."""
+    return {
         "pf_stage_f64.cu": unit("double", [0, 1], False, "pf_stage_f64.cu"),
         "pf_stage_f32k0.cu": unit("float", [0], True, "pf_stage_f32k0.cu"),
         "pf_stage_f32k1.cu": unit("float", [1], True, "pf_stage_f32k1.cu"),
         "pf_stage_m32k0.cu": munit(0, "pf_stage_m32k0.cu"),
         "pf_stage_m32k1.cu": munit(1, "pf_stage_m32k1.cu"),
     }
-    for name, text in out.items():
+
+
+def main():
+    for name, text in render().items():
         with open(os.path.join(HERE, name), "w") as f:
             f.write(text)
 

@@ -51,3 +51,15 @@ def test_product_does_not_import_oracle():
             for m in re.findall(r"^\s*(?:from|import)\s+(paper_2601_16522_gb300[\w.]*)", txt, re.M):
                 assert m == "paper_2601_16522_gb300.inputs", (f, m)
             assert "pf_kernels" not in txt and "include/pf.h" not in txt, f
+
+
+def test_instantiation_units_match_their_generator():
+    # the committed pf_stage_*.cu files are what csrc/gen_units.py writes
+    import importlib.util
+    path = os.path.join(ROOT, "paper_2601_16522_gb300", "csrc", "gen_units.py")
+    spec = importlib.util.spec_from_file_location("gen_units", path)
+    gen = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(gen)
+    for name, text in gen.render().items():
+        with open(os.path.join(os.path.dirname(path), name)) as f:
+            assert f.read() == text, name
