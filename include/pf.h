@@ -136,8 +136,18 @@ typedef struct {
    accepted step; rhs_evals counts what was evaluated.  The trajectory is the
    one without reuse up to rounding.  The stored RHS belongs to the state it
    was computed from: pf_set_state, a rejected attempt or a step without the
-   flag drop it. */
-enum { PF_STEP_NO_GRAPH = 1, PF_STEP_REUSE_RHS = 2 };
+   flag drop it.
+   PF_STEP_DEVICE_LOOP (adaptive RKL1/RKL2 on a non-default stream; FP64, or
+   FP32 dense storage with at most 32 phases; not with PF_STEP_REUSE_RHS or
+   profiling; else PF_EINVAL) runs the adaptive loop device-driven: the
+   output-time clip, stage count, stage coefficients and buffers, error
+   norm, PID controller with bias and accept/reject of Sec. 3.2/3.3 are
+   computed by GPU kernels inside one CUDA graph with conditional WHILE
+   nodes, which carries up to 256 attempts per launch, so the host waits
+   once per launch instead of once per attempt.  The controller's pow/atan
+   then round as the GPU's math library does, which may differ from the
+   host loop in the last bits of the step size. */
+enum { PF_STEP_NO_GRAPH = 1, PF_STEP_REUSE_RHS = 2, PF_STEP_DEVICE_LOOP = 4 };
 
 typedef struct {
     long long rhs_evals;       /* RHS sweeps, including rejected steps and STS error sweeps */

@@ -7,6 +7,8 @@ pf_stage_f32k{0,1}   FP32, K fixed: big_kernel (32 < N <= 250), tma_kernel and
                      fast_kernel (N <= 32, NMAX 4 or 32) per pass signature
                      (fast_kernel also for the error sweep that keeps its RHS),
                      and the generic kernel as the fallback
+(each of these also holds launchd_*: the descriptor-driven passes of
+device-driven adaptive RKL steps)
 pf_stage_m32k{0,1}   FP32 masked storage, K fixed: fast_kernel<..., true> per
                      pass signature for N <= 4, N <= 32 and N <= 128
 """
@@ -20,6 +22,9 @@ SIGS = ["SIG_PROJECT", "SIG_P2 | SIG_PROJECT", "SIG_P0 | SIG_P2 | SIG_R0IN | SIG
         "SIG_R0OUT | SIG_PROJECT", "SIG_ERR", "SIG_P0 | SIG_PROJECT"]
 # the dense fast kernel also has the error sweep that keeps F(u^{n+1})
 FAST_SIGS = SIGS + ["SIG_ERR | SIG_R0OUT"]
+# passes of the device-driven adaptive RKL steps: stage 1, RKL2 body, RKL1
+# body, error sweep (descriptor-driven kernels)
+DSIGS = ["SIG_R0OUT | SIG_PROJECT", "SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT", "SIG_P2 | SIG_PROJECT", "SIG_ERR"]
 
 
 def unit(T, kcs, fast, fname):
@@ -77,6 +82,40 @@ def unit(T, kcs, fast, fname):
     L.append("    (void)tma;")
     L.append("    *done = false;")
     L.append("    return 0;")
+    L.append("}")
+    L.append("")
+    # descriptor-driven passes of device-driven adaptive RKL steps
+    L.append("int launchd_%s(const Geom &g, unsigned sig, const Pass<%s> *dP, cudaStream_t st, const %s *A, const %s *B,"
+             % (tag, T, T, T))
+    L.append("             const %s *L, const signed char *ptype)" % T)
+    L.append("{")
+    L.append("    const dim3 grid(g.tiles_x, g.tiles_y, g.nz);")
+    if fast:
+        kc = kcs[0]
+        L.append("    const size_t smf = sizeof(ListSmem<float>);")
+        L.append("    if (g.N <= 32 && g.Vs < 0x7fffffffLL) {")
+        for nmax in (4, 32):
+            L.append("        if (%s) {" % ("g.N <= 4" if nmax == 4 else "g.N > 4"))
+            for d in (2, 3):
+                for sg in DSIGS:
+                    L.append("            if (g.dim == %d && sig == (%s)) {" % (d, sg))
+                    L.append("                fast_kernel_d<%d, %d, %s, %d><<<grid, BLOCK, smf, st>>>(g, dP, A, B, L, ptype);" % (d, kc, sg, nmax))
+                    L.append("                return (int)cudaGetLastError();")
+                    L.append("            }")
+                    prep.append("    if (cudaFuncSetAttribute(fast_kernel_d<%d, %d, %s, %d>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;" % (d, kc, sg, nmax))
+            L.append("        }")
+        L.append("    }")
+    else:
+        L.append("    const size_t sm = sizeof(Smem<%s>);" % T)
+        for d in (2, 3):
+            for k in kcs:
+                L.append("    if (g.dim == %d && g.K == %d) {" % (d, k))
+                L.append("        cell_kernel_d<%s, %d, %d, SIG_GENERIC><<<grid, BLOCK, sm, st>>>(g, dP, A, B, L, ptype);" % (T, d, k))
+                L.append("        return (int)cudaGetLastError();")
+                L.append("    }")
+                prep.append("    if (cudaFuncSetAttribute(cell_kernel_d<%s, %d, %d, SIG_GENERIC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem<%s>)) != cudaSuccess) return -1;" % (T, d, k, T))
+    L.append("    (void)sig;")
+    L.append("    return (int)cudaErrorInvalidValue;")
     L.append("}")
     L.append("")
     L.append("int prepare_%s()" % tag)

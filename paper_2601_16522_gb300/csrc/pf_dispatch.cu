@@ -13,6 +13,12 @@ int launch_m32k0(const Geom &, const Pass<float> &, unsigned, cudaStream_t, cons
                  const float *, const signed char *, bool *);
 int launch_m32k1(const Geom &, const Pass<float> &, unsigned, cudaStream_t, const float *, const float *,
                  const float *, const signed char *, bool *);
+int launchd_f64(const Geom &, unsigned, const Pass<double> *, cudaStream_t, const double *, const double *,
+                const double *, const signed char *);
+int launchd_f32k0(const Geom &, unsigned, const Pass<float> *, cudaStream_t, const float *, const float *,
+                  const float *, const signed char *);
+int launchd_f32k1(const Geom &, unsigned, const Pass<float> *, cudaStream_t, const float *, const float *,
+                  const float *, const signed char *);
 int prepare_f64();
 int prepare_f32k0();
 int prepare_f32k1();
@@ -48,6 +54,20 @@ int launch_stage<float>(const Geom &g, const Pass<float> &P, cudaStream_t st, co
     int e = go(pass_signature(P));
     if (!done) e = go(SIG_GENERIC);
     return done ? e : (int)cudaErrorInvalidValue;
+}
+
+template <>
+int launch_stage_d<double>(const Geom &g, unsigned sig, const Pass<double> *dP, cudaStream_t st, const double *A,
+                           const double *B, const double *L, const signed char *ptype)
+{
+    return launchd_f64(g, sig, dP, st, A, B, L, ptype);
+}
+
+template <>
+int launch_stage_d<float>(const Geom &g, unsigned sig, const Pass<float> *dP, cudaStream_t st, const float *A,
+                          const float *B, const float *L, const signed char *ptype)
+{
+    return g.K ? launchd_f32k1(g, sig, dP, st, A, B, L, ptype) : launchd_f32k0(g, sig, dP, st, A, B, L, ptype);
 }
 
 template <>

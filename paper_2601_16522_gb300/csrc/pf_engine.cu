@@ -370,6 +370,11 @@ struct pf_handle {
     double b = 0.9, E1 = 0.0, E2 = 0.0, dt1 = 0.0, dt2 = 0.0;
     int nhist = 0;
     double dt_next = 0.0;
+    // device-driven adaptive RKL steps: control block, pass descriptions, graph
+    void *dl_ctl = nullptr, *dl_desc = nullptr;
+    cudaGraph_t dl_graph = nullptr;
+    cudaGraphExec_t dl_exec = nullptr;
+    int dl_integ = -1;
     // reuse of F(u^{n+1}) as the next step's F(u^n) (PF_STEP_REUSE_RHS):
     // buffer rhs_buf holds the raw RHS of the state in buffer rhs_iu
     bool reuse_on = false, rhs_valid = false;
@@ -571,7 +576,7 @@ double gershgorin_dt_e(const pf_handle *h, const pf_params *p)
 }
 
 // ---- RKL coefficients (Meyer et al. 2012/2014, Legendre basis) ------------
-double rkl2_b(int j)
+__host__ __device__ double rkl2_b(int j)
 {
     if (j < 2) return 1.0 / 3.0;
     const double jj = (double)j;
@@ -579,7 +584,7 @@ double rkl2_b(int j)
 }
 
 // Smallest odd stage count whose RKL stability bound with 0.9 dt_e covers dt.
-int sts_stages(int integ, double dt, double dte)
+__host__ __device__ int sts_stages(int integ, double dt, double dte)
 {
     const double dte9 = 0.9 * dte;
     for (int s = (integ == PF_RKL2) ? 3 : 1;; s += 2) {
@@ -589,7 +594,7 @@ int sts_stages(int integ, double dt, double dte)
     }
 }
 
-double sts_max_dt(int integ, int s, double dte)
+__host__ __device__ double sts_max_dt(int integ, int s, double dte)
 {
     const double ds = (double)s;
     return ((integ == PF_RKL2) ? (ds * ds + ds - 2.0) / 4.0 : (ds * ds + ds) / 2.0) * 0.9 * dte;
@@ -663,31 +668,51 @@ void ssp104_embedded(double bh[10])
 }
 
 // ---- PID controller with bias (Sec. 3.3, Soderlind 2006 form) --------------
-double controller(pf_handle *h, double err, double dt, int P, int *accept)
+struct CtrlState {
+    double b, E1, E2, dt1, dt2;
+    int nhist;
+};
+
+// One controller update on the state of the last accepted steps; the host
+// loop and the device-driven loop share it.  Returns the next step size.
+__host__ __device__ double pid_bias(CtrlState &c, double err, double dt, int P, int *accept)
 {
     const double k1 = 1.25, k2 = 0.5, k3 = -0.6, k4 = 0.25, k5 = 0.0;
     const double ex = 1.0 / (double)(P + 1);
-    double E = err / h->b;
+    double E = err / c.b;
     if (E < 1e-10) E = 1e-10;
     double F = pow(E, -k1 * ex);
-    if (h->nhist >= 1) F = F * pow(h->E1, -k2 * ex) * pow(dt / h->dt1, k4);
-    if (h->nhist >= 2) F = F * pow(h->E2, -k3 * ex) * pow(h->dt1 / h->dt2, k5);
+    if (c.nhist >= 1) F = F * pow(c.E1, -k2 * ex) * pow(dt / c.dt1, k4);
+    if (c.nhist >= 2) F = F * pow(c.E2, -k3 * ex) * pow(c.dt1 / c.dt2, k5);
     const int acc = err < 1.0;
     if (acc) {
-        h->E2 = h->E1;
-        h->E1 = E;
-        h->dt2 = h->dt1;
-        h->dt1 = dt;
-        if (h->nhist < 2) h->nhist++;
-        const double nb = sqrt(h->b);
-        h->b = nb > 0.98 ? 0.98 : nb;
+        c.E2 = c.E1;
+        c.E1 = E;
+        c.dt2 = c.dt1;
+        c.dt1 = dt;
+        if (c.nhist < 2) c.nhist++;
+        const double nb = sqrt(c.b);
+        c.b = nb > 0.98 ? 0.98 : nb;
     } else {
-        const double nb = h->b * h->b;
-        h->b = nb < 0.1 ? 0.1 : nb;
+        const double nb = c.b * c.b;
+        c.b = nb < 0.1 ? 0.1 : nb;
         if (F > 1.0) F = pow(E, -k1 * ex);
     }
     *accept = acc;
     return dt * (1.0 + 5.0 * atan((F - 1.0) / 5.0));
+}
+
+double controller(pf_handle *h, double err, double dt, int P, int *accept)
+{
+    CtrlState c{h->b, h->E1, h->E2, h->dt1, h->dt2, h->nhist};
+    const double r = pid_bias(c, err, dt, P, accept);
+    h->b = c.b;
+    h->E1 = c.E1;
+    h->E2 = c.E2;
+    h->dt1 = c.dt1;
+    h->dt2 = c.dt2;
+    h->nhist = c.nhist;
+    return r;
 }
 
 void reset_controller(pf_handle *h)
@@ -860,7 +885,7 @@ int do_step(pf_handle *h, int integ, double dt, int s, const pf_tol *tol, bool w
 
 // Device flags -> status: a non-positive simplex sum is an instability; more
 // nontrivial phases in one cell than the kernel's list holds is unsupported.
-int flag_status(int flag)
+__host__ __device__ int flag_status(int flag)
 {
     if (flag & pfk::FLAG_NZ_OVERFLOW) return PF_EINVAL;
     if (flag & pfk::FLAG_TIMEOUT) return PF_ETIMEOUT;
@@ -944,6 +969,403 @@ bool capture_fixed_steps(pf_handle *h, int integ, double dt, int s)
     return true;
 }
 
+// ---------------------------------------------------------------------------
+// Device-driven adaptive RKL steps (PF_STEP_DEVICE_LOOP).  Every decision of
+// the adaptive loop of Sec. 3.2/3.3 -- the output-time clip, the stage count,
+// each stage's buffers and coefficients, the error norm, the PID controller
+// with bias and accept/reject -- is taken on the GPU by single-thread
+// kernels, and the attempts run as one CUDA graph with two conditional WHILE
+// nodes (attempts; stages 2..s).  A launch carries up to DL_CAP attempts, so
+// the host waits once per launch instead of once per attempt.  Every WHILE
+// ends: the attempt loop after DL_CAP attempts per launch, the stage loop
+// after s <= max_stages stages.
+// ---------------------------------------------------------------------------
+constexpr int DL_CAP = 256;
+
+template <typename P>
+bool dmalloc(pf_handle *h, P **p, size_t bytes);
+
+struct DevCtl {
+    // inputs, set by the host for each pf_step call
+    double t_end, dte, tol[4];
+    int integ, max_stages, order, trace_cap;
+    long long max_attempts;          // 0: no limit
+    double *tr_dt, *tr_err;
+    int *tr_s, *tr_acc;
+    void *buf[NBUF];
+    // loop state (read back by the host after every launch)
+    double t, dt, hs, hlast, elast;
+    double b, E1, E2, dt1, dt2;
+    int nhist, iu, s, j, last, status, ntr;
+    long long evals, acc_n, rej_n, attempts, launch_attempts, launches;
+};
+
+// The four buffers other than u^n in index order: three RKL stage buffers
+// and F(u^n) (the assignment do_step uses).
+__host__ __device__ inline void dl_buffers(int iu, int w[NBUF - 1])
+{
+    int n = 0;
+    for (int k = 0; k < NBUF; ++k) if (k != iu) w[n++] = k;
+}
+
+__global__ void dl_begin(DevCtl *c, cudaGraphConditionalHandle hout)
+{
+    c->launch_attempts = 0;
+    c->launches += 1;
+    const bool go = c->status == PF_OK && c->t < c->t_end && (c->max_attempts == 0 || c->attempts < c->max_attempts);
+    cudaGraphSetConditional(hout, go ? 1u : 0u);
+}
+
+// Stage 1: step size (clipped to the output time), stage count, description.
+template <typename T>
+__global__ void dl_first(DevCtl *c, Pass<T> *d, cudaGraphConditionalHandle hin)
+{
+    const bool o2 = c->integ == PF_RKL2;
+    const double rem = c->t_end - c->t;
+    double hs = c->dt;
+    int last = 0;
+    if (hs >= rem * (1.0 - 1e-9)) { hs = rem; last = 1; }
+    int s = sts_stages(c->integ, hs, c->dte);
+    if (s > c->max_stages) {
+        s = c->max_stages | 1;
+        hs = sts_max_dt(c->integ, s, c->dte);
+        last = 0;
+    }
+    c->hs = hs;
+    c->s = s;
+    c->last = last;
+    c->j = 2;
+    int w[NBUF - 1];
+    dl_buffers(c->iu, w);
+    const double ds = (double)s;
+    const double w1 = o2 ? 4.0 / (ds * ds + ds - 2.0) : 2.0 / (ds * ds + ds);
+    const double mt1 = o2 ? rkl2_b(1) * w1 : w1;
+    Pass<T> P = d[3];
+    P.in = (const T *)c->buf[c->iu];
+    P.a1 = 1.0;
+    P.b1 = mt1 * hs;
+    P.out = (T *)c->buf[w[0]];
+    P.r0out = (T *)c->buf[w[3]];
+    P.fix_first = o2 ? 1 : 0;
+    d[0] = P;
+    cudaGraphSetConditional(hin, s >= 2 ? 1u : 0u);
+}
+
+// Stage j >= 2 of Eq. sts: coefficients and the ring of stage buffers.
+template <typename T>
+__global__ void dl_stage(DevCtl *c, Pass<T> *d, cudaGraphConditionalHandle hin)
+{
+    const bool o2 = c->integ == PF_RKL2;
+    const int j = c->j, s = c->s;
+    const double hs = c->hs, ds = (double)s, dj = (double)j;
+    const double w1 = o2 ? 4.0 / (ds * ds + ds - 2.0) : 2.0 / (ds * ds + ds);
+    double mu, nu, mt, gt;
+    if (o2) {
+        mu = ((2.0 * dj - 1.0) / dj) * (rkl2_b(j) / rkl2_b(j - 1));
+        nu = -((dj - 1.0) / dj) * (rkl2_b(j) / rkl2_b(j - 2));
+        mt = mu * w1;
+        gt = -(1.0 - rkl2_b(j - 1)) * mt;
+    } else {
+        mu = (2.0 * dj - 1.0) / dj;
+        nu = -(dj - 1.0) / dj;
+        mt = w1 * mu;
+        gt = 0.0;
+    }
+    int w[NBUF - 1];
+    dl_buffers(c->iu, w);
+    Pass<T> P = d[3];
+    P.in = (const T *)c->buf[w[(j - 2) % 3]];
+    P.p2 = (j == 2) ? (const T *)c->buf[c->iu] : (const T *)c->buf[w[(j - 3) % 3]];
+    P.a1 = mu;
+    P.a2 = nu;
+    P.b1 = mt * hs;
+    if (o2) {
+        P.p0 = (const T *)c->buf[c->iu];
+        P.a0 = (1.0 - mu) - nu;
+        P.r0in = (const T *)c->buf[w[3]];
+        P.b0 = gt * hs;
+    }
+    P.out = (T *)c->buf[w[(j - 1) % 3]];
+    d[1] = P;
+    c->j = j + 1;
+    cudaGraphSetConditional(hin, (j + 1 <= s) ? 1u : 0u);
+}
+
+// The error sweep's description (Sommeijer estimate with F(u^{n+1})).
+template <typename T>
+__global__ void dl_err(DevCtl *c, Pass<T> *d)
+{
+    int w[NBUF - 1];
+    dl_buffers(c->iu, w);
+    Pass<T> P = d[3];
+    P.mode = pfk::MODE_ERR;
+    P.in = (const T *)c->buf[w[(c->s - 1) % 3]];
+    P.p0 = (const T *)c->buf[c->iu];
+    P.r0in = (const T *)c->buf[w[3]];
+    P.dt = c->hs;
+    P.project = 0;
+    P.r_phi = c->tol[0];
+    P.a_phi = c->tol[1];
+    P.r_c = c->tol[2];
+    P.a_c = c->tol[3];
+    d[2] = P;
+}
+
+// Error norm, controller, accept/reject, trace; continue or end the launch.
+__global__ void dl_ctrl(DevCtl *c, const double *dres, const long long *dcnt, const int *dflag,
+                        cudaGraphConditionalHandle hout)
+{
+    c->attempts++;
+    c->launch_attempts++;
+    c->evals += c->s + 1;
+    c->launches += 2 * (long long)c->s + 4;
+    int st = PF_OK;
+    const int flag = *dflag;
+    double err = 0.0;
+    if (flag) {
+        st = flag_status(flag);
+    } else {
+        const long long n = *dcnt;
+        err = n > 0 ? sqrt(*dres / (double)n) : 0.0;
+        if (!isfinite(err)) st = PF_EUNSTABLE;
+    }
+    if (st == PF_OK) {
+        CtrlState cs{c->b, c->E1, c->E2, c->dt1, c->dt2, c->nhist};
+        int acc = 0;
+        const double dtn = pid_bias(cs, err, c->hs, c->order, &acc);
+        c->b = cs.b;
+        c->E1 = cs.E1;
+        c->E2 = cs.E2;
+        c->dt1 = cs.dt1;
+        c->dt2 = cs.dt2;
+        c->nhist = cs.nhist;
+        if (c->ntr < c->trace_cap) {
+            c->tr_dt[c->ntr] = c->hs;
+            c->tr_s[c->ntr] = c->s;
+            c->tr_err[c->ntr] = err;
+            c->tr_acc[c->ntr] = acc;
+            c->ntr++;
+        }
+        c->hlast = c->hs;
+        c->elast = err;
+        if (acc) {
+            int w[NBUF - 1];
+            dl_buffers(c->iu, w);
+            c->iu = w[(c->s - 1) % 3];
+            c->t = c->last ? c->t_end : c->t + c->hs;
+            c->acc_n++;
+        } else {
+            c->rej_n++;
+            if (c->rej_n > 100000) st = PF_EUNSTABLE;
+        }
+        c->dt = dtn;
+    }
+    c->status = st;
+    const bool go = st == PF_OK && c->t < c->t_end && c->launch_attempts < DL_CAP &&
+                    (c->max_attempts == 0 || c->attempts < c->max_attempts);
+    cudaGraphSetConditional(hout, go ? 1u : 0u);
+}
+
+void free_devloop(pf_handle *h)
+{
+    if (h->dl_exec) cudaGraphExecDestroy(h->dl_exec);
+    if (h->dl_graph) cudaGraphDestroy(h->dl_graph);
+    h->dl_exec = nullptr;
+    h->dl_graph = nullptr;
+    h->dl_integ = -1;
+}
+
+// Capture the launches fn() makes on the handle's stream into `graph`
+// (after the nodes deps); *leaves receives the last captured nodes.
+template <class F>
+bool capture_to(pf_handle *h, cudaGraph_t graph, const cudaGraphNode_t *deps, size_t ndeps,
+                std::vector<cudaGraphNode_t> *leaves, F fn)
+{
+    if (cudaStreamBeginCaptureToGraph(h->stream, graph, deps, nullptr, ndeps, cudaStreamCaptureModeThreadLocal) !=
+        cudaSuccess)
+        return false;
+    bool ok = fn();
+    if (ok && leaves) {
+        cudaStreamCaptureStatus cs;
+        const cudaGraphNode_t *d = nullptr;
+        size_t n = 0;
+        ok = cudaStreamGetCaptureInfo(h->stream, &cs, nullptr, nullptr, &d, nullptr, &n) == cudaSuccess && n > 0;
+        if (ok) leaves->assign(d, d + n);
+    }
+    cudaGraph_t g = nullptr;
+    const bool ended = cudaStreamEndCapture(h->stream, &g) == cudaSuccess;
+    return ok && ended;
+}
+
+bool add_while(cudaGraph_t graph, const cudaGraphNode_t *dep, size_t ndep, cudaGraphConditionalHandle hc,
+               cudaGraphNode_t *node, cudaGraph_t *body)
+{
+    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+    cp.conditional.handle = hc;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    if (cudaGraphAddNode(node, graph, dep, nullptr, ndep, &cp) != cudaSuccess) return false;
+    *body = cp.conditional.phGraph_out[0];
+    return true;
+}
+
+// Build (once per integrator) the graph: begin -> WHILE(attempts){ plan and
+// stage 1 -> WHILE(stages 2..s){ plan, stage } -> error sweep, norm,
+// controller }.  The kernels are captured straight into the conditional
+// nodes' body graphs; every body sets its own node's condition.
+template <typename T>
+int build_devloop(pf_handle *h, int integ)
+{
+    if (h->dl_exec && h->dl_integ == integ) return PF_OK;
+    free_devloop(h);
+    if (!h->dl_ctl && !dmalloc(h, &h->dl_ctl, sizeof(DevCtl))) return PF_ENOMEM;
+    if (!h->dl_desc && !dmalloc(h, &h->dl_desc, 4 * sizeof(Pass<double>))) return PF_ENOMEM;
+    DevCtl *ctl = (DevCtl *)h->dl_ctl;
+    Pass<T> *desc = (Pass<T> *)h->dl_desc;
+    const Pass<T> base = blank_pass<T>(h);
+    if (cudaMemcpyAsync(desc + 3, &base, sizeof(base), cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+        return PF_EDEVICE;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return PF_EDEVICE;
+    const unsigned body_sig = integ == PF_RKL2 ? (pfk::SIG_P0 | pfk::SIG_P2 | pfk::SIG_R0IN | pfk::SIG_PROJECT)
+                                               : (pfk::SIG_P2 | pfk::SIG_PROJECT);
+    const T *A = (const T *)h->dA, *B = (const T *)h->dB, *L = (const T *)h->dL;
+    cudaStream_t st = h->stream;
+    cudaGraph_t top = nullptr, outer = nullptr, inner = nullptr;
+    cudaGraphConditionalHandle hout = 0, hin = 0;
+    cudaGraphNode_t nw, ni;
+    std::vector<cudaGraphNode_t> lb, la;
+    bool ok = cudaGraphCreate(&top, 0) == cudaSuccess &&
+              cudaGraphConditionalHandleCreate(&hout, top, 0, cudaGraphCondAssignDefault) == cudaSuccess;
+    ok = ok && capture_to(h, top, nullptr, 0, &lb, [&] {
+        dl_begin<<<1, 1, 0, st>>>(ctl, hout);
+        return cudaGetLastError() == cudaSuccess;
+    });
+    ok = ok && add_while(top, lb.data(), lb.size(), hout, &nw, &outer);
+    ok = ok && cudaGraphConditionalHandleCreate(&hin, outer, 0, 0) == cudaSuccess;
+    ok = ok && capture_to(h, outer, nullptr, 0, &la, [&] {
+        dl_first<T><<<1, 1, 0, st>>>(ctl, desc, hin);
+        return cudaGetLastError() == cudaSuccess &&
+               pfk::launch_stage_d<T>(h->g, pfk::SIG_R0OUT | pfk::SIG_PROJECT, desc + 0, st, A, B, L, h->dptype) == 0;
+    });
+    ok = ok && add_while(outer, la.data(), la.size(), hin, &ni, &inner);
+    ok = ok && capture_to(h, inner, nullptr, 0, nullptr, [&] {
+        dl_stage<T><<<1, 1, 0, st>>>(ctl, desc, hin);
+        return cudaGetLastError() == cudaSuccess &&
+               pfk::launch_stage_d<T>(h->g, body_sig, desc + 1, st, A, B, L, h->dptype) == 0;
+    });
+    ok = ok && capture_to(h, outer, &ni, 1, nullptr, [&] {
+        dl_err<T><<<1, 1, 0, st>>>(ctl, desc);
+        if (cudaGetLastError() != cudaSuccess) return false;
+        if (pfk::launch_stage_d<T>(h->g, pfk::SIG_ERR, desc + 2, st, A, B, L, h->dptype) != 0) return false;
+        finalize_err_kernel<<<1, 256, 0, st>>>(h->part_sum, h->part_cnt, h->grid, h->dres, h->dcnt);
+        dl_ctrl<<<1, 1, 0, st>>>(ctl, h->dres, h->dcnt, h->dflag, hout);
+        return cudaGetLastError() == cudaSuccess;
+    });
+    cudaGraphExec_t exec = nullptr;
+    ok = ok && cudaGraphInstantiate(&exec, top, 0) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        if (exec) cudaGraphExecDestroy(exec);
+        if (top) cudaGraphDestroy(top);
+        return PF_EDEVICE;
+    }
+    h->dl_graph = top;
+    h->dl_exec = exec;
+    h->dl_integ = integ;
+    return PF_OK;
+}
+
+// Adaptive RKL1/RKL2 to t_end through the device-driven graph.
+template <typename T>
+int devloop(pf_handle *h, int integ, double t_end, const pf_tol *tol, const pf_step_opts *o, pf_stats *stats)
+{
+    int st = build_devloop<T>(h, integ);
+    if (st) return st;
+    DevCtl c;
+    memset(&c, 0, sizeof(c));
+    c.t_end = t_end;
+    c.dte = h->dte;
+    c.tol[0] = tol->r_phi;
+    c.tol[1] = tol->a_phi;
+    c.tol[2] = tol->r_c;
+    c.tol[3] = tol->a_c;
+    c.integ = integ;
+    c.max_stages = o->max_stages > 0 ? o->max_stages : 1001;
+    c.order = method_order(integ);
+    c.max_attempts = o->max_attempts;
+    c.trace_cap = o->trace_cap > 0 ? o->trace_cap : 0;
+    for (int k = 0; k < NBUF; ++k) c.buf[k] = h->buf[k];
+    c.t = h->t;
+    c.dt = h->dt_next > 0.0 ? h->dt_next : (o->dt0 > 0.0 ? o->dt0 : 0.9 * h->dte);
+    c.b = h->b;
+    c.E1 = h->E1;
+    c.E2 = h->E2;
+    c.dt1 = h->dt1;
+    c.dt2 = h->dt2;
+    c.nhist = h->nhist;
+    c.iu = h->iu;
+    void *trbuf = nullptr;
+    if (c.trace_cap > 0) {
+        const size_t n = (size_t)c.trace_cap;
+        if (!dmalloc(h, &trbuf, n * (2 * sizeof(double) + 2 * sizeof(int)))) return PF_ENOMEM;
+        c.tr_dt = (double *)trbuf;
+        c.tr_err = c.tr_dt + n;
+        c.tr_s = (int *)(c.tr_err + n);
+        c.tr_acc = c.tr_s + n;
+    }
+    DevCtl *dctl = (DevCtl *)h->dl_ctl;
+    st = PF_OK;
+    if (cudaMemsetAsync(h->dflag, 0, sizeof(int), h->stream) != cudaSuccess ||
+        cudaMemcpyAsync(dctl, &c, sizeof(c), cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+        st = PF_EDEVICE;
+    long long prev_attempts = -1;
+    while (st == PF_OK) {
+        if (cudaGraphLaunch(h->dl_exec, h->stream) != cudaSuccess ||
+            cudaMemcpyAsync(&c, dctl, sizeof(c), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+            cudaStreamSynchronize(h->stream) != cudaSuccess) {
+            st = PF_EDEVICE;
+            break;
+        }
+        if (c.status != PF_OK) { st = c.status; break; }
+        if (!(c.t < t_end) || (c.max_attempts > 0 && c.attempts >= c.max_attempts)) break;
+        if (c.attempts == prev_attempts) { st = PF_EDEVICE; break; }   // a launch that made no attempt
+        prev_attempts = c.attempts;
+    }
+    if (trbuf) {
+        const size_t n = (size_t)c.ntr;
+        bool okc = true;
+        if (o->trace_dt) okc = okc && cudaMemcpyAsync(o->trace_dt, c.tr_dt, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream) == cudaSuccess;
+        if (o->trace_err) okc = okc && cudaMemcpyAsync(o->trace_err, c.tr_err, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream) == cudaSuccess;
+        if (o->trace_s) okc = okc && cudaMemcpyAsync(o->trace_s, c.tr_s, n * sizeof(int), cudaMemcpyDeviceToHost, h->stream) == cudaSuccess;
+        if (o->trace_acc) okc = okc && cudaMemcpyAsync(o->trace_acc, c.tr_acc, n * sizeof(int), cudaMemcpyDeviceToHost, h->stream) == cudaSuccess;
+        cudaFreeAsync(trbuf, h->stream);
+        if (cudaStreamSynchronize(h->stream) != cudaSuccess || !okc) st = st ? st : PF_EDEVICE;
+    }
+    if (o->trace_len) *o->trace_len = c.ntr;
+    h->t = c.t;
+    h->iu = c.iu;
+    h->b = c.b;
+    h->E1 = c.E1;
+    h->E2 = c.E2;
+    h->dt1 = c.dt1;
+    h->dt2 = c.dt2;
+    h->nhist = c.nhist;
+    h->dt_next = c.dt;
+    h->launches += c.launches;
+    if (stats) {
+        stats->rhs_evals = c.evals;
+        stats->steps_accepted = c.acc_n;
+        stats->steps_rejected = c.rej_n;
+        stats->t = h->t;
+        stats->dt_last = c.hlast;
+        stats->err_last = c.elast;
+        stats->dt_e = h->dte;
+        stats->dt_next = h->dt_next;
+        stats->kernel_launches = c.launches;
+    }
+    return st;
+}
+
 template <typename T>
 int step_loop(pf_handle *h, int integ, double t_end, const pf_tol *tol, const pf_step_opts *o, pf_stats *stats)
 {
@@ -952,6 +1374,14 @@ int step_loop(pf_handle *h, int integ, double t_end, const pf_tol *tol, const pf
     if (adaptive && (integ == PF_FEULER || integ == PF_SSP2)) return PF_EINVAL;
     if (adaptive && !tol) return PF_EINVAL;
     if (integ == PF_SSP2 && o->ssp_stages < 2) return PF_EINVAL;
+    if (o->flags & PF_STEP_DEVICE_LOOP) {
+        // the descriptor-driven kernels cover FP64 and FP32 dense storage with N <= 32
+        if (!(adaptive && sts) || !h->stream || h->prof_on || (o->flags & PF_STEP_REUSE_RHS) || h->masked ||
+            !(sizeof(T) == 8 || h->N <= 32) || h->Vs >= 0x7fffffffLL)
+            return PF_EINVAL;
+        h->rhs_valid = false;
+        return devloop<T>(h, integ, t_end, tol, o, stats);
+    }
     const int max_stages = o->max_stages > 0 ? o->max_stages : 1001;
     long long evals = 0, acc_n = 0, rej_n = 0, attempts = 0;
     const long long launches0 = h->launches;
@@ -1136,11 +1566,15 @@ void free_all(pf_handle *h)
 {
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
     h->gexec = nullptr;
+    if (h->dl_exec) cudaGraphExecDestroy(h->dl_exec);
+    if (h->dl_graph) cudaGraphDestroy(h->dl_graph);
+    h->dl_exec = nullptr;
+    h->dl_graph = nullptr;
     for (cudaEvent_t ev : h->ev_pool) cudaEventDestroy(ev);
     h->ev_pool.clear();
     for (int k = 0; k < NBUF; ++k) if (h->buf[k]) cudaFreeAsync(h->buf[k], h->stream);
     void *ps[] = {h->dA, h->dB, h->dL, h->dAB64, h->dptype, h->staging, h->dnz, h->part_sum, h->part_cnt,
-                  h->dres, h->dcnt, h->dflag, h->tot_sum, h->tot_max};
+                  h->dres, h->dcnt, h->dflag, h->tot_sum, h->tot_max, h->dl_ctl, h->dl_desc};
     for (void *p : ps) if (p) cudaFreeAsync(p, h->stream);
     cudaStreamSynchronize(h->stream);
 }

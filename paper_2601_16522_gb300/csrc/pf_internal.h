@@ -14,6 +14,14 @@ template <typename T>
 int launch_stage(const Geom &g, const Pass<T> &P, cudaStream_t st, const T *A, const T *B, const T *L,
                  const signed char *ptype, const TmaMaps *tma);
 
+// Launch one pass whose description (buffers, coefficients) sits in device
+// memory at dP, written there by a planning kernel before the launch runs
+// (device-driven adaptive steps).  sig: the pass signature the description
+// will have (stage 1, RKL body or error sweep).  Returns a cudaError_t.
+template <typename T>
+int launch_stage_d(const Geom &g, unsigned sig, const Pass<T> *dP, cudaStream_t st, const T *A, const T *B,
+                   const T *L, const signed char *ptype);
+
 // Opt every instantiation into its shared memory on the current device;
 // returns the resident blocks per SM of the generic 3D kernel (<= 0: error).
 template <typename T>

@@ -195,9 +195,9 @@ struct Smem {
 };
 
 template <typename T, int DIM, int KC, unsigned SIG>
-__global__ void __launch_bounds__(BLOCK)
-cell_kernel(const Geom g, const Pass<T> P, const T *__restrict__ tabA, const T *__restrict__ tabB,
-            const T *__restrict__ tabL, const signed char *__restrict__ ptype)
+__device__ __forceinline__ void cell_body(const Geom &g, const Pass<T> &P, const T *__restrict__ tabA,
+                                          const T *__restrict__ tabB, const T *__restrict__ tabL,
+                                          const signed char *__restrict__ ptype)
 {
     constexpr int NFACE = 2 * DIM;
     constexpr bool GEN = (SIG & SIG_GENERIC) != 0;
@@ -527,6 +527,28 @@ cell_kernel(const Geom g, const Pass<T> P, const T *__restrict__ tabA, const T *
     }
 
     if (mode == MODE_ERR || emb) block_partials(esum, ecnt, P.part_sum, P.part_cnt, bid);
+}
+
+template <typename T, int DIM, int KC, unsigned SIG>
+__global__ void __launch_bounds__(BLOCK)
+cell_kernel(const Geom g, const Pass<T> P, const T *__restrict__ tabA, const T *__restrict__ tabB,
+            const T *__restrict__ tabL, const signed char *__restrict__ ptype)
+{
+    cell_body<T, DIM, KC, SIG>(g, P, tabA, tabB, tabL, ptype);
+}
+
+// The same pass with its description read from device memory: the passes
+// of device-driven adaptive steps, whose buffers and coefficients a planning
+// kernel writes before each launch runs.
+template <typename T, int DIM, int KC, unsigned SIG>
+__global__ void __launch_bounds__(BLOCK)
+cell_kernel_d(const Geom g, const Pass<T> *__restrict__ Pd, const T *__restrict__ tabA, const T *__restrict__ tabB,
+              const T *__restrict__ tabL, const signed char *__restrict__ ptype)
+{
+    __shared__ Pass<T> Ps;
+    if (threadIdx.x == 0) Ps = *Pd;
+    __syncthreads();
+    cell_body<T, DIM, KC, SIG>(g, Ps, tabA, tabB, tabL, ptype);
 }
 
 // ---------------------------------------------------------------------------
@@ -1524,10 +1546,10 @@ big_kernel(const Geom g, const Pass<float> P, const float *__restrict__ tabA, co
 }
 
 // FP32 fast path with plain global loads (any grid, 2D or 3D).
-template <int DIM, int KC, unsigned SIG, int NMAX, bool MASK = false>
-__global__ void __launch_bounds__(BLOCK, MASK ? PF_MASK_MINB : PF_FAST_MINB)
-fast_kernel(const Geom g, const Pass<float> P, const float *__restrict__ tabA, const float *__restrict__ tabB,
-            const float *__restrict__ tabL, const signed char *__restrict__ ptype)
+template <int DIM, int KC, unsigned SIG, int NMAX, bool MASK>
+__device__ __forceinline__ void fast_body(const Geom &g, const Pass<float> &P, const float *__restrict__ tabA,
+                                          const float *__restrict__ tabB, const float *__restrict__ tabL,
+                                          const signed char *__restrict__ ptype)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     ListSmem<float> &S = *reinterpret_cast<ListSmem<float> *>(smem_raw);
@@ -1568,6 +1590,27 @@ fast_kernel(const Geom g, const Pass<float> P, const float *__restrict__ tabA, c
             fast_cell<DIM, KC, SIG, NMAX>(g, P, ld, S, tid, i, off, ghost, tabA, tabB, tabL, ptype, esum, ecnt);
     }
     if (SIG & SIG_ERR) block_partials(esum, ecnt, P.part_sum, P.part_cnt, bid);
+}
+
+template <int DIM, int KC, unsigned SIG, int NMAX, bool MASK = false>
+__global__ void __launch_bounds__(BLOCK, MASK ? PF_MASK_MINB : PF_FAST_MINB)
+fast_kernel(const Geom g, const Pass<float> P, const float *__restrict__ tabA, const float *__restrict__ tabB,
+            const float *__restrict__ tabL, const signed char *__restrict__ ptype)
+{
+    fast_body<DIM, KC, SIG, NMAX, MASK>(g, P, tabA, tabB, tabL, ptype);
+}
+
+// The same pass with its description read from device memory (device-driven
+// adaptive steps; see cell_kernel_d).
+template <int DIM, int KC, unsigned SIG, int NMAX>
+__global__ void __launch_bounds__(BLOCK, PF_FAST_MINB)
+fast_kernel_d(const Geom g, const Pass<float> *__restrict__ Pd, const float *__restrict__ tabA,
+              const float *__restrict__ tabB, const float *__restrict__ tabL, const signed char *__restrict__ ptype)
+{
+    __shared__ Pass<float> Ps;
+    if (threadIdx.x == 0) Ps = *Pd;
+    __syncthreads();
+    fast_body<DIM, KC, SIG, NMAX, false>(g, Ps, tabA, tabB, tabL, ptype);
 }
 
 // FP32 fast path with TMA staging, warp-specialised: warps 0..7 compute the

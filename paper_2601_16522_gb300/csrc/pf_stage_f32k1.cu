@@ -218,6 +218,85 @@ int launch_f32k1(const Geom &g, const Pass<float> &P, unsigned sig, cudaStream_t
     return 0;
 }
 
+int launchd_f32k1(const Geom &g, unsigned sig, const Pass<float> *dP, cudaStream_t st, const float *A, const float *B,
+             const float *L, const signed char *ptype)
+{
+    const dim3 grid(g.tiles_x, g.tiles_y, g.nz);
+    const size_t smf = sizeof(ListSmem<float>);
+    if (g.N <= 32 && g.Vs < 0x7fffffffLL) {
+        if (g.N <= 4) {
+            if (g.dim == 2 && sig == (SIG_R0OUT | SIG_PROJECT)) {
+                fast_kernel_d<2, 1, SIG_R0OUT | SIG_PROJECT, 4><<<grid, BLOCK, smf, st>>>(g, dP, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 2 && sig == (SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT)) {
+                fast_kernel_d<2, 1, SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT, 4><<<grid, BLOCK, smf, st>>>(g, dP, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 2 && sig == (SIG_P2 | SIG_PROJECT)) {
+                fast_kernel_d<2, 1, SIG_P2 | SIG_PROJECT, 4><<<grid, BLOCK, smf, st>>>(g, dP, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 2 && sig == (SIG_ERR)) {
+                fast_kernel_d<2, 1, SIG_ERR, 4><<<grid, BLOCK, smf, st>>>(g, dP, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 3 && sig == (SIG_R0OUT | SIG_PROJECT)) {
+                fast_kernel_d<3, 1, SIG_R0OUT | SIG_PROJECT, 4><<<grid, BLOCK, smf, st>>>(g, dP, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 3 && sig == (SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT)) {
+                fast_kernel_d<3, 1, SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT, 4><<<grid, BLOCK, smf, st>>>(g, dP, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 3 && sig == (SIG_P2 | SIG_PROJECT)) {
+                fast_kernel_d<3, 1, SIG_P2 | SIG_PROJECT, 4><<<grid, BLOCK, smf, st>>>(g, dP, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 3 && sig == (SIG_ERR)) {
+                fast_kernel_d<3, 1, SIG_ERR, 4><<<grid, BLOCK, smf, st>>>(g, dP, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+        }
+        if (g.N > 4) {
+            if (g.dim == 2 && sig == (SIG_R0OUT | SIG_PROJECT)) {
+                fast_kernel_d<2, 1, SIG_R0OUT | SIG_PROJECT, 32><<<grid, BLOCK, smf, st>>>(g, dP, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 2 && sig == (SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT)) {
+                fast_kernel_d<2, 1, SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT, 32><<<grid, BLOCK, smf, st>>>(g, dP, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 2 && sig == (SIG_P2 | SIG_PROJECT)) {
+                fast_kernel_d<2, 1, SIG_P2 | SIG_PROJECT, 32><<<grid, BLOCK, smf, st>>>(g, dP, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 2 && sig == (SIG_ERR)) {
+                fast_kernel_d<2, 1, SIG_ERR, 32><<<grid, BLOCK, smf, st>>>(g, dP, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 3 && sig == (SIG_R0OUT | SIG_PROJECT)) {
+                fast_kernel_d<3, 1, SIG_R0OUT | SIG_PROJECT, 32><<<grid, BLOCK, smf, st>>>(g, dP, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 3 && sig == (SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT)) {
+                fast_kernel_d<3, 1, SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT, 32><<<grid, BLOCK, smf, st>>>(g, dP, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 3 && sig == (SIG_P2 | SIG_PROJECT)) {
+                fast_kernel_d<3, 1, SIG_P2 | SIG_PROJECT, 32><<<grid, BLOCK, smf, st>>>(g, dP, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 3 && sig == (SIG_ERR)) {
+                fast_kernel_d<3, 1, SIG_ERR, 32><<<grid, BLOCK, smf, st>>>(g, dP, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+        }
+    }
+    (void)sig;
+    return (int)cudaErrorInvalidValue;
+}
+
 int prepare_f32k1()
 {
     const int smf = (int)sizeof(ListSmem<float>);
@@ -270,6 +349,22 @@ int prepare_f32k1()
     if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_ERR | SIG_R0OUT, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(cell_kernel<float, 2, 1, SIG_GENERIC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem<float>)) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(cell_kernel<float, 3, 1, SIG_GENERIC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem<float>)) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel_d<2, 1, SIG_R0OUT | SIG_PROJECT, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel_d<2, 1, SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel_d<2, 1, SIG_P2 | SIG_PROJECT, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel_d<2, 1, SIG_ERR, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel_d<3, 1, SIG_R0OUT | SIG_PROJECT, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel_d<3, 1, SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel_d<3, 1, SIG_P2 | SIG_PROJECT, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel_d<3, 1, SIG_ERR, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel_d<2, 1, SIG_R0OUT | SIG_PROJECT, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel_d<2, 1, SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel_d<2, 1, SIG_P2 | SIG_PROJECT, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel_d<2, 1, SIG_ERR, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel_d<3, 1, SIG_R0OUT | SIG_PROJECT, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel_d<3, 1, SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel_d<3, 1, SIG_P2 | SIG_PROJECT, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel_d<3, 1, SIG_ERR, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cell_kernel<float, 3, 1, SIG_GENERIC>, BLOCK, sizeof(Smem<float>)) != cudaSuccess) return -1;
     return nb;

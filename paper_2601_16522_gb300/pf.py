@@ -262,6 +262,7 @@ class Simulation:
 
     STEP_NO_GRAPH = 1
     STEP_REUSE_RHS = 2
+    STEP_DEVICE_LOOP = 4
 
     def step(self, integ, t_end, tol=None, dt_mult=0.0, ssp_stages=5, dt0=0.0, max_stages=0,
              max_attempts=0, trace_cap=0, flags=0):
