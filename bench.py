@@ -19,6 +19,7 @@ on a bounded sample of the same workload and prints the same line.
 """
 import argparse
 import json
+import math
 import os
 import subprocess
 import sys
@@ -425,6 +426,52 @@ def reuse_run(pf, torch, prob, u, stream, args, world, dev, dense_out, dense_ms)
             "mean_abs_diff_to_dense": mean_diff, "cells_differing_over_1e-3": frac}
 
 
+def grains_to_half(pf, torch, dev, stream, t_max=60.0, wall_cap_s=120.0):
+    """The 256^3 grain workload run to the time at which half of the 32
+    grains are gone (alive: max phi_a >= 0.5; the configuration's run
+    length), adaptive RKL2 in FP32 with masked and with dense storage;
+    forward Euler in FP64 at 0.9 dt_e is estimated from its measured time
+    per step times the steps it would need."""
+    prob, u, _ = workload_problem("grains256", dev)
+    out = []
+    t_half = None
+    for name, opts in (("rkl2-fp32-masked", pf.Simulation.OPT_MASKED), ("rkl2-fp32-dense", 0)):
+        sim = pf.Simulation(prob, precision=32, stream=stream, options=opts)
+        sim.set_state(u)
+        dte = sim.dt_e()
+        n0 = sim.reduce()[2]
+        dt_out = 200.0 * dte
+        t, evals, alive = 0.0, 0, n0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        while alive > n0 // 2 and t < t_max and time.perf_counter() - t0 < wall_cap_s:
+            t += dt_out
+            evals += sim.step(pf.RKL2, t, tol=TOL)["rhs_evals"]
+            alive = sim.reduce()[2]
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        sim.close()
+        out.append({"variant": name, "wall_s": el, "t_reached": t, "grains_alive": alive, "grains_start": n0,
+                    "rhs_evals": evals})
+        t_half = t if alive <= n0 // 2 else t_half
+    # forward Euler, FP64, dense: 20 timed steps, extrapolated
+    sim = pf.Simulation(prob, precision=64, stream=stream)
+    sim.set_state(u)
+    dte = sim.dt_e()
+    sim.step(pf.FEULER, 2 * 0.9 * dte, dt_mult=0.9)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim.step(pf.FEULER, 22 * 0.9 * dte, dt_mult=0.9)
+    torch.cuda.synchronize()
+    per_step = (time.perf_counter() - t0) / 20.0
+    sim.close()
+    if t_half is not None:
+        n_fe = math.ceil(t_half / (0.9 * dte))
+        out.append({"variant": "feuler-fp64-dense (estimated)", "wall_s": per_step * n_fe, "rhs_evals": n_fe,
+                    "ms_per_step": 1e3 * per_step})
+    return {"t_half": t_half, "output_interval": "200 dt_e", "tol": TOL, "variants": out}
+
+
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
@@ -558,6 +605,9 @@ def run_ours(args, world, rank, local):
     served = None
     if rank == 0 and args.served > 0:
         served = served_stream(pf, torch, args.served)
+    to_half = None
+    if rank == 0 and args.grains_to_half:
+        to_half = grains_to_half(pf, torch, dev, stream)
 
     if rank == 0:
         line = {
@@ -578,6 +628,7 @@ def run_ours(args, world, rank, local):
             "roofline": roof, "pass_ms": pass_ms,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
             "time_to_solution": tts, "served": served, "masked": masked, "reuse_rhs": reuse,
+            "grains_to_half": to_half,
         }
         print(json.dumps(line), flush=True)
     sim.close()
@@ -597,6 +648,8 @@ def main():
     ap.add_argument("--served", type=int, default=48, help="requests in the served Poisson stream (0: skip)")
     ap.add_argument("--no-masked", action="store_true", help="skip the masked-storage run")
     ap.add_argument("--no-reuse", action="store_true", help="skip the run that reuses F(u^{n+1})")
+    ap.add_argument("--grains-to-half", action="store_true",
+                    help="also run the 256^3 grain workload until half of its grains are gone")
     args = ap.parse_args()
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
