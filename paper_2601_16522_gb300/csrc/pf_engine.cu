@@ -34,29 +34,35 @@ constexpr int NBUF = 5;
 // auxiliary kernels: layout conversion and reductions
 // ---------------------------------------------------------------------------
 
-// ABI layout (FP64, field stride V) -> engine layout (T, field stride Vs)
+// ABI layout (FP64: N phase fields at phi, field stride V; the concentration
+// at c) -> engine layout (T, field stride Vs).  phi and c may be device
+// memory or page-locked host memory reached through its device mapping.
 template <typename T>
-__global__ void pack_kernel(const double *__restrict__ src, T *__restrict__ dst, long long V, long long Vs, int NF)
+__global__ void pack_kernel(const double *__restrict__ phi, const double *__restrict__ c, T *__restrict__ dst,
+                            long long V, long long Vs, int N, int NF)
 {
     const long long n = V * NF;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
          k += (long long)gridDim.x * blockDim.x) {
         const long long f = k / V;
         const long long i = k - f * V;
-        dst[f * Vs + i] = (T)src[k];
+        dst[f * Vs + i] = (T)(f < N ? phi[k] : c[i]);
     }
 }
 
-// engine layout -> ABI layout
+// engine layout -> ABI layout (phi and c as for pack_kernel; c may be null)
 template <typename T>
-__global__ void unpack_kernel(const T *__restrict__ src, double *__restrict__ dst, long long V, long long Vs, int NF)
+__global__ void unpack_kernel(const T *__restrict__ src, double *__restrict__ phi, double *__restrict__ c, long long V,
+                              long long Vs, int N, int NF)
 {
     const long long n = V * NF;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
          k += (long long)gridDim.x * blockDim.x) {
         const long long f = k / V;
         const long long i = k - f * V;
-        dst[k] = (double)src[f * Vs + i];
+        const double v = (double)src[f * Vs + i];
+        if (f < N) phi[k] = v;
+        else if (c) c[i] = v;
     }
 }
 
@@ -1500,10 +1506,27 @@ int step_loop(pf_handle *h, int integ, double t_end, const pf_tol *tol, const pf
 }
 
 
-template <typename T>
-int set_state_t(pf_handle *h, const double *src_dev)
+// An address through which kernels reach p: device and managed memory as
+// is, page-locked host memory through its device mapping; null for pageable
+// host memory (whose transfers go through the staging buffer).
+const void *device_view(const void *p)
 {
-    pack_kernel<T><<<grid_for(h->V * h->NP), 256, 0, h->stream>>>(src_dev, (T *)h->buf[h->iu], h->V, h->Vs, h->NP);
+    if (!p) return nullptr;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return p;
+    if (a.type == cudaMemoryTypeHost && a.devicePointer) return a.devicePointer;
+    return nullptr;
+}
+
+template <typename T>
+int set_state_t(pf_handle *h, const double *phi_dev, const double *c_dev)
+{
+    pack_kernel<T><<<grid_for(h->V * h->NP), 256, 0, h->stream>>>(phi_dev, c_dev, (T *)h->buf[h->iu], h->V, h->Vs,
+                                                                    h->N, h->NP);
     h->launches++;
     if (h->masked) {
         mask_kernel<<<grid_for(h->V), 256, 0, h->stream>>>((const float *)h->buf[h->iu], mask_plane(h, h->buf[h->iu]),
@@ -1514,9 +1537,10 @@ int set_state_t(pf_handle *h, const double *src_dev)
 }
 
 template <typename T>
-int get_state_t(pf_handle *h, double *dst_dev)
+int get_state_t(pf_handle *h, double *phi_dev, double *c_dev)
 {
-    unpack_kernel<T><<<grid_for(h->V * h->NP), 256, 0, h->stream>>>((const T *)h->buf[h->iu], dst_dev, h->V, h->Vs, h->NP);
+    unpack_kernel<T><<<grid_for(h->V * h->NP), 256, 0, h->stream>>>((const T *)h->buf[h->iu], phi_dev, c_dev, h->V,
+                                                                      h->Vs, h->N, h->NP);
     h->launches++;
     return cuda_status(cudaGetLastError());
 }
@@ -1829,14 +1853,21 @@ int pf_set_state(pf_handle *h, const double *phi, const double *c, double t, int
 {
     if (!h || !phi || (h->K && !c)) return PF_EINVAL;
     int st;
-    if ((st = ensure_staging(h))) return st;
-    const size_t nphi = sizeof(double) * (size_t)h->N * h->V;
-    const cudaMemcpyKind kind = ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    if (cudaMemcpyAsync(h->staging, phi, nphi, kind, h->stream) != cudaSuccess) return PF_EDEVICE;
-    if (h->K && cudaMemcpyAsync(h->staging + (size_t)h->N * h->V, c, sizeof(double) * h->V, kind, h->stream) != cudaSuccess)
-        return PF_EDEVICE;
-    st = (h->prec == 64) ? set_state_t<double>(h, h->staging) : set_state_t<float>(h, h->staging);
-    if (st) return st;
+    const double *vphi = (const double *)device_view(phi), *vc = h->K ? (const double *)device_view(c) : nullptr;
+    if (vphi && (!h->K || vc)) {
+        // device or page-locked host memory: the layout conversion reads it directly
+        st = (h->prec == 64) ? set_state_t<double>(h, vphi, vc) : set_state_t<float>(h, vphi, vc);
+        if (st) return st;
+    } else {
+        if ((st = ensure_staging(h))) return st;
+        const size_t nphi = sizeof(double) * (size_t)h->N * h->V;
+        const cudaMemcpyKind kind = ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        double *sc = h->staging + (size_t)h->N * h->V;
+        if (cudaMemcpyAsync(h->staging, phi, nphi, kind, h->stream) != cudaSuccess) return PF_EDEVICE;
+        if (h->K && cudaMemcpyAsync(sc, c, sizeof(double) * h->V, kind, h->stream) != cudaSuccess) return PF_EDEVICE;
+        st = (h->prec == 64) ? set_state_t<double>(h, h->staging, sc) : set_state_t<float>(h, h->staging, sc);
+        if (st) return st;
+    }
     if (!ptr_is_device && cudaStreamSynchronize(h->stream) != cudaSuccess) return PF_EDEVICE;
     h->t = t;
     h->has_state = true;
@@ -1850,15 +1881,21 @@ int pf_get_state(pf_handle *h, double *phi, double *c, unsigned char *nz, double
     if (!h) return PF_EINVAL;
     if (!h->has_state) return PF_ESTATE;
     int st;
-    if ((st = ensure_staging(h))) return st;
     const cudaMemcpyKind kind = ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-    if (phi || c) {
-        st = (h->prec == 64) ? get_state_t<double>(h, h->staging) : get_state_t<float>(h, h->staging);
+    double *vphi = phi ? (double *)device_view(phi) : nullptr;
+    double *vc = (c && h->K) ? (double *)device_view(c) : nullptr;
+    if (phi && vphi && (!c || !h->K || vc)) {
+        // device or page-locked host memory: the layout conversion writes it directly
+        st = (h->prec == 64) ? get_state_t<double>(h, vphi, vc) : get_state_t<float>(h, vphi, vc);
+        if (st) return st;
+    } else if (phi || c) {
+        if ((st = ensure_staging(h))) return st;
+        double *sc = h->staging + (size_t)h->N * h->V;
+        st = (h->prec == 64) ? get_state_t<double>(h, h->staging, sc) : get_state_t<float>(h, h->staging, sc);
         if (st) return st;
         if (phi && cudaMemcpyAsync(phi, h->staging, sizeof(double) * (size_t)h->N * h->V, kind, h->stream) != cudaSuccess)
             return PF_EDEVICE;
-        if (c && h->K &&
-            cudaMemcpyAsync(c, h->staging + (size_t)h->N * h->V, sizeof(double) * h->V, kind, h->stream) != cudaSuccess)
+        if (c && h->K && cudaMemcpyAsync(c, sc, sizeof(double) * h->V, kind, h->stream) != cudaSuccess)
             return PF_EDEVICE;
     }
     if (nz) {
