@@ -426,6 +426,48 @@ def reuse_run(pf, torch, prob, u, stream, args, world, dev, dense_out, dense_ms)
             "mean_abs_diff_to_dense": mean_diff, "cells_differing_over_1e-3": frac}
 
 
+def stefan_sweep(pf, torch, t_end=4300.0):
+    """The Stefan strip (1024 x 256, D 1:100) with each adaptive integrator
+    at r = a in {1e-3, 1e-4, 1e-5, 1e-6}, FP32 and FP64, beside forward
+    Euler at 0.9 dt_e: wall time, RHS sweeps, steps and the error of the
+    fitted growth constant against the exact A."""
+    import numpy as np
+    from paper_2601_16522_gb300 import inputs as I
+    prob, u = I.stefan(1024, 256, 200.0)
+    A = I.stefan_growth_constant()
+    x0 = _front(u[0][:1024])
+    stream = torch.cuda.Stream()
+    times = np.linspace(0.0, t_end, 11)[1:]
+    runs = [("feuler", 64, None, dict(dt_mult=0.9)), ("feuler", 32, None, dict(dt_mult=0.9))]
+    for tol in (1e-3, 1e-4, 1e-5, 1e-6):
+        for integ in ("rkl1", "rkl2", "ssp104"):
+            for prec in (32, 64):
+                runs.append((integ, prec, tol, dict(tol=(tol, tol, tol, tol))))
+    out = []
+    host = np.zeros((3, prob.V))
+    for name, prec, tol, kw in runs:
+        integ = {"feuler": pf.FEULER, "rkl1": pf.RKL1, "rkl2": pf.RKL2, "ssp104": pf.SSP104}[name]
+        sim = pf.Simulation(prob, precision=prec, stream=stream)
+        sim.set_state(u)
+        X, evals, acc, rej = [], 0, 0, 0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for tk in times:
+            st = sim.step(integ, float(tk), **kw)
+            evals += st["rhs_evals"]
+            acc += st["steps_accepted"]
+            rej += st["steps_rejected"]
+            sim.get_state(out=host)
+            X.append(_front(host[0][:1024]) - x0)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        sim.close()
+        Afit = float((np.sqrt(times) * np.array(X)).sum() / times.sum())
+        out.append({"integrator": name, "precision": prec, "tol": tol, "wall_ms": 1e3 * el, "rhs_evals": evals,
+                    "accepted": acc, "rejected": rej, "rel_error": abs(Afit - A) / A})
+    return {"t_end": t_end, "A_exact": A, "runs": out}
+
+
 def grains_to_half(pf, torch, dev, stream, t_max=60.0, wall_cap_s=120.0):
     """The 256^3 grain workload run to the time at which half of the 32
     grains are gone (alive: max phi_a >= 0.5; the configuration's run
@@ -608,6 +650,9 @@ def run_ours(args, world, rank, local):
     to_half = None
     if rank == 0 and args.grains_to_half:
         to_half = grains_to_half(pf, torch, dev, stream)
+    sweep = None
+    if rank == 0 and args.stefan_sweep:
+        sweep = stefan_sweep(pf, torch)
 
     if rank == 0:
         line = {
@@ -628,7 +673,7 @@ def run_ours(args, world, rank, local):
             "roofline": roof, "pass_ms": pass_ms,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
             "time_to_solution": tts, "served": served, "masked": masked, "reuse_rhs": reuse,
-            "grains_to_half": to_half,
+            "grains_to_half": to_half, "stefan_sweep": sweep,
         }
         print(json.dumps(line), flush=True)
     sim.close()
@@ -648,6 +693,8 @@ def main():
     ap.add_argument("--served", type=int, default=48, help="requests in the served Poisson stream (0: skip)")
     ap.add_argument("--no-masked", action="store_true", help="skip the masked-storage run")
     ap.add_argument("--no-reuse", action="store_true", help="skip the run that reuses F(u^{n+1})")
+    ap.add_argument("--stefan-sweep", action="store_true",
+                    help="also run the Stefan strip with every adaptive integrator at tolerances 1e-3..1e-6")
     ap.add_argument("--grains-to-half", action="store_true",
                     help="also run the 256^3 grain workload until half of its grains are gone")
     args = ap.parse_args()
