@@ -33,6 +33,21 @@ constexpr int MAXACT = 12;      // nontrivial phases per cell handled by the lis
 constexpr int TX = 32, TY = 8;  // cells per block: 32 (x) by 8 (y), one z plane
 constexpr int BLOCK = TX * TY;
 
+// Stage combination a0 p0 + a1 v + a2 p2 of every pass, whose coefficients
+// sum to one (affine combinations of states, Eq. sts, Alg. ssp2, SSP(10)4),
+// evaluated as v + a0 (p0 - v) + a2 (p2 - v).  A constant field then stays
+// exactly constant whatever the rounding of the coefficients, so in FP32 the
+// solute total is not scaled by (a0 + a1 + a2 rounded) at every stage; the
+// coefficient rounding only reaches the small stage differences.
+template <bool HP0, bool HP2, typename T>
+__device__ __forceinline__ T affine(T v, T p0, T p2, T a0, T a2)
+{
+    T acc = v;
+    if (HP0) acc = acc + a0 * (p0 - v);
+    if (HP2) acc = acc + a2 * (p2 - v);
+    return acc;
+}
+
 // Problem constants shared by every pass (passed by value).
 struct Geom {
     int nx, ny, nz, dim;
@@ -63,8 +78,10 @@ struct Pass {
     const T *uw;         // u^n for the error weights (SSP(10)4 final stage)
     int project;         // apply the simplex projection to the phases
     int embedded_err;    // final SSP(10)4 stage: e = u - z into the error partials
-    double a0, a1, a2, b1, b0, bz;   // combination coefficients (dt folded into b*)
-    double m25, m925, m15, m5;       // SSP(10)4 mid-stage combination coefficients
+    double a0, a1, a2, b1, b0, bz;   // combination coefficients (dt folded into b*);
+                                     // a0 + a1 + a2 = 1, see affine()
+    double m25, m15;                 // SSP(10)4 after stage 5: q2 <- q1 + m25 (q2in - q1),
+                                     // q1 <- q1 + m15 (q2 - q1)
     double dt;                       // step size (error sweep)
     double r_phi, a_phi, r_c, a_c;   // tolerances (error partials)
     double *part_sum;    // per-block partial sums of (e/w)^2
@@ -405,7 +422,7 @@ __device__ __forceinline__ void cell_body(const Geom &g, const Pass<T> &P, const
             }
         } else {
             // ---- stage combination (Eq. sts / Alg. ssp2 / SSP(10)4) ---------
-            const T a0c = (T)P.a0, a1c = (T)P.a1, a2c = (T)P.a2, b1c = (T)P.b1, b0c = (T)P.b0, bzc = (T)P.bz;
+            const T a0c = (T)P.a0, a2c = (T)P.a2, b1c = (T)P.b1, b0c = (T)P.b0, bzc = (T)P.bz;
             const bool chunked = N > NV;
             bool changed = false;
             T best = (T)-1;
@@ -420,10 +437,9 @@ __device__ __forceinline__ void cell_body(const Geom &g, const Pass<T> &P, const
                     T r = (T)0;
                     PF_NEXT_RHS(a, r)
                     const T v = ldg(P.in + o);
-                    T acc;
-                    if (has_p0) { acc = a0c * ldg(P.p0 + o); acc = acc + a1c * v; }
-                    else acc = a1c * v;
-                    if (has_p2) acc = acc + a2c * ldg(P.p2 + o);
+                    T acc = v;
+                    if (has_p0) acc = acc + a0c * (ldg(P.p0 + o) - v);
+                    if (has_p2) acc = acc + a2c * (ldg(P.p2 + o) - v);
                     acc = acc + b1c * r;
                     if (has_r0in) acc = acc + b0c * ldg(P.r0in + o);
                     if (has_r0out) P.r0out[o] = r;      // replaced below where S acts (RKL2)
@@ -483,9 +499,9 @@ __device__ __forceinline__ void cell_body(const Geom &g, const Pass<T> &P, const
                         }
                     }
                     if (has_out2) {
-                        const T q2 = (T)P.m25 * ldg(P.q2in + o) + (T)P.m925 * w;
+                        const T q2 = w + (T)P.m25 * (ldg(P.q2in + o) - w);
                         P.out2[o] = q2;
-                        P.out[o] = (T)P.m15 * q2 + (T)P.m5 * w;
+                        P.out[o] = w + (T)P.m15 * (q2 - w);
                     } else {
                         P.out[o] = w;
                     }
@@ -495,12 +511,12 @@ __device__ __forceinline__ void cell_body(const Geom &g, const Pass<T> &P, const
             // concentration field (no projection)
             if (K) {
                 const long long o = (long long)N * Vs + i;
-                T acc;
-                if (has_p0) { acc = a0c * ldg(P.p0 + o); acc = acc + a1c * cc; }
-                else acc = a1c * cc;
-                if (has_p2) acc = acc + a2c * ldg(P.p2 + o);
-                acc = acc + b1c * rc;
-                if (has_r0in) acc = acc + b0c * ldg(P.r0in + o);
+                // the small increments are summed first: c is rounded once per stage
+                T d = b1c * rc;
+                if (has_r0in) d = d + b0c * ldg(P.r0in + o);
+                if (has_p0) d = d + a0c * (ldg(P.p0 + o) - cc);
+                if (has_p2) d = d + a2c * (ldg(P.p2 + o) - cc);
+                const T acc = cc + d;
                 if (has_r0out) P.r0out[o] = rc;
                 if (has_z) {
                     const T zv = P.zin[o] + bzc * rc;
@@ -515,9 +531,9 @@ __device__ __forceinline__ void cell_body(const Geom &g, const Pass<T> &P, const
                     }
                 }
                 if (has_out2) {
-                    const T q2 = (T)P.m25 * ldg(P.q2in + o) + (T)P.m925 * acc;
+                    const T q2 = acc + (T)P.m25 * (ldg(P.q2in + o) - acc);
                     P.out2[o] = q2;
-                    P.out[o] = (T)P.m15 * q2 + (T)P.m5 * acc;
+                    P.out[o] = acc + (T)P.m15 * (q2 - acc);
                 } else {
                     P.out[o] = acc;
                 }
@@ -730,7 +746,7 @@ __device__ __forceinline__ void fast_cell(const Geom &g, const Pass<float> &P, L
     const int Vs = (int)g.Vs;
     const int i32 = (int)i;
     const T idx2 = (T)(1.0 / g.dx2);
-    const T a0c = (T)P.a0, a1c = (T)P.a1, a2c = (T)P.a2, b1c = (T)P.b1, b0c = (T)P.b0;
+    const T a0c = (T)P.a0, a2c = (T)P.a2, b1c = (T)P.b1, b0c = (T)P.b0;
     const T ib1 = (T)(1.0 / P.b1);   // first-stage fix: F <- (S(u1) - u^n) / (mu~_1 dt)
     const T dt = (T)P.dt, rph = (T)P.r_phi, aph = (T)P.a_phi;
 
@@ -809,8 +825,7 @@ __device__ __forceinline__ void fast_cell(const Geom &g, const Pass<float> &P, L
                     }
                 }
             } else {
-                T acc = HP0 ? a0c * p0v + a1c * v0 : a1c * v0;
-                if (HP2) acc = acc + a2c * p2v;
+                T acc = affine<HP0, HP2>(v0, p0v, p2v, a0c, a2c);
                 if (HR0) acc = acc + b0c * r0v;
                 if (!act && PROJ) {
                     if (acc < (T)0) { acc = (T)0; changed = true; }
@@ -941,10 +956,12 @@ __device__ __forceinline__ void fast_cell(const Geom &g, const Pass<float> &P, L
     }
     if (KC) {
         const long long o = (long long)N * Vs + i;
-        T acc = HP0 ? a0c * ldg(P.p0 + o) + a1c * cc : a1c * cc;
-        if (HP2) acc = acc + a2c * ldg(P.p2 + o);
-        acc = acc + b1c * rc;
-        if (HR0) acc = acc + b0c * ldg(P.r0in + o);
+        // the small increments are summed first: c is rounded once per stage
+        T d = b1c * rc;
+        if (HR0) d = d + b0c * ldg(P.r0in + o);
+        if (HP0) d = d + a0c * (ldg(P.p0 + o) - cc);
+        if (HP2) d = d + a2c * (ldg(P.p2 + o) - cc);
+        const T acc = cc + d;
         if (R0OUT) P.r0out[o] = rc;
         P.out[o] = acc;
     }
@@ -987,7 +1004,7 @@ __device__ __forceinline__ void masked_cell(const Geom &g, const Pass<float> &P,
     const int Vs = (int)g.Vs;
     const int i32 = (int)i;
     const T idx2 = (T)(1.0 / g.dx2);
-    const T a0c = (T)P.a0, a1c = (T)P.a1, a2c = (T)P.a2, b1c = (T)P.b1, b0c = (T)P.b0;
+    const T a0c = (T)P.a0, a2c = (T)P.a2, b1c = (T)P.b1, b0c = (T)P.b0;
     const T ib1 = (T)(1.0 / P.b1);   // first-stage fix: F <- (S(u1) - u^n) / (mu~_1 dt)
     const T dt = (T)P.dt, rph = (T)P.r_phi, aph = (T)P.a_phi;
 
@@ -1113,8 +1130,7 @@ __device__ __forceinline__ void masked_cell(const Geom &g, const Pass<float> &P,
                 }
             }
         } else {
-            T acc = HP0 ? a0c * p0v + a1c * v0 : a1c * v0;
-            if (HP2) acc = acc + a2c * p2v;
+            T acc = affine<HP0, HP2>(v0, p0v, p2v, a0c, a2c);
             if (HR0) acc = acc + b0c * r0v;
             if (!act && PROJ) {
                 if (acc < (T)0) { acc = (T)0; changed = true; }
@@ -1274,10 +1290,12 @@ __device__ __forceinline__ void masked_cell(const Geom &g, const Pass<float> &P,
     }
     if (KC) {
         const long long o = (long long)N * Vs + i;
-        T acc = HP0 ? a0c * ldg(P.p0 + o) + a1c * cc : a1c * cc;
-        if (HP2) acc = acc + a2c * ldg(P.p2 + o);
-        acc = acc + b1c * rc;
-        if (HR0) acc = acc + b0c * ldg(P.r0in + o);
+        // the small increments are summed first: c is rounded once per stage
+        T d = b1c * rc;
+        if (HR0) d = d + b0c * ldg(P.r0in + o);
+        if (HP0) d = d + a0c * (ldg(P.p0 + o) - cc);
+        if (HP2) d = d + a2c * (ldg(P.p2 + o) - cc);
+        const T acc = cc + d;
         if (R0OUT) P.r0out[o] = rc;
         P.out[o] = acc;
     }
@@ -1308,12 +1326,11 @@ __device__ __forceinline__ void big_cell(const Geom &g, const Pass<float> &P, Pl
     const long long Vs = g.Vs;
     const int i32 = (int)i;
     const T idx2 = (T)(1.0 / g.dx2);
-    const T a0c = (T)P.a0, a1c = (T)P.a1, a2c = (T)P.a2, b1c = (T)P.b1, b0c = (T)P.b0;
+    const T a0c = (T)P.a0, a2c = (T)P.a2, b1c = (T)P.b1, b0c = (T)P.b0;
     const T ib1 = (T)(1.0 / P.b1);   // first-stage fix: F <- (S(u1) - u^n) / (mu~_1 dt)
     const T dt = (T)P.dt, rph = (T)P.r_phi, aph = (T)P.a_phi;
     auto combo = [&](T p0v, T v0, T p2v, T r0v) {
-        T acc = HP0 ? a0c * p0v + a1c * v0 : a1c * v0;
-        if (HP2) acc = acc + a2c * p2v;
+        T acc = affine<HP0, HP2>(v0, p0v, p2v, a0c, a2c);
         if (HR0) acc = acc + b0c * r0v;
         return acc;
     };
@@ -1498,10 +1515,12 @@ __device__ __forceinline__ void big_cell(const Geom &g, const Pass<float> &P, Pl
     }
     if (KC) {
         const long long o = (long long)N * Vs + i;
-        T acc = HP0 ? a0c * ldg(P.p0 + o) + a1c * cc : a1c * cc;
-        if (HP2) acc = acc + a2c * ldg(P.p2 + o);
-        acc = acc + b1c * rc;
-        if (HR0) acc = acc + b0c * ldg(P.r0in + o);
+        // the small increments are summed first: c is rounded once per stage
+        T d = b1c * rc;
+        if (HR0) d = d + b0c * ldg(P.r0in + o);
+        if (HP0) d = d + a0c * (ldg(P.p0 + o) - cc);
+        if (HP2) d = d + a2c * (ldg(P.p2 + o) - cc);
+        const T acc = cc + d;
         if (R0OUT) P.r0out[o] = rc;
         P.out[o] = acc;
     }

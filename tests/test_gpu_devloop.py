@@ -14,7 +14,7 @@ import pytest
 from oracle import ref
 from paper_2601_16522_gb300 import inputs as I
 
-from test_gpu_parity import REL64, pf, relerr  # noqa: F401  (fixture)
+from test_gpu_parity import REL64, assert_err_trace, pf, relerr  # noqa: F401  (fixture)
 
 pytestmark = pytest.mark.gpu
 
@@ -48,7 +48,7 @@ def test_devloop_replay_fp64(pf, integ):
     status, ur, t, trace = o.run(integ, u, 0.0, t_end, tol=TOL, replay=(tr["dt"], tr["s"], tr["acc"]),
                                  trace_cap=10000)
     assert status == 0 and t == t_end
-    np.testing.assert_allclose(trace["err"], tr["err"], rtol=1e-10, atol=0)
+    assert_err_trace(trace["err"], tr["err"])
     assert relerr(ug, ur, prob.n_phases, prob.has_conc) <= REL64
     assert st["rhs_evals"] == o.stats.rhs_evals
 
