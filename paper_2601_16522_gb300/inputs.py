@@ -140,6 +140,38 @@ def phase_embedding(n=128, r=32.0, W=3.0, D=100.0, k=500.0, c0=(0.02, 0.98), M=1
     return prob, u
 
 
+def double_triple_junction(nx=192, ny=96, r=32.0, W=2.5, gamma_bb=1.0, gamma_ab=2.0, D=100.0, k=500.0,
+                           c0=(0.02, 0.98), M=1.0, dx=1.0, shift=True):
+    """Double triple junction (Sec. 5.1.2): a circle of phase 0 (type alpha)
+    of radius r centred on the straight boundary y = C_y between grains 1
+    (y < C_y) and 2 (type beta), the boundary along the long side.  phi_0
+    follows d = r - |X - C| (Eq. centersphere); the grains' trial fields
+    profile(C_y - y) and its complement are rescaled to 1 - phi_0 with their
+    ratio kept (Eq. distfix).  c is at local equilibrium (mu = 0) and, with
+    shift=True, moved uniformly so that its integral equals the sharp-interface
+    amount pi r^2 c0_alpha + (area - pi r^2) c0_beta (Sec. 5.1).  Zero-gradient
+    faces for phi and c; K = 1, D = 100 and k = 500 as for the paper's
+    equilibrium runs."""
+    N = 3
+    gam = np.array([[0.0, gamma_ab, gamma_ab], [gamma_ab, 0.0, gamma_bb], [gamma_ab, gamma_bb, 0.0]])
+    nb = (BC_NEUMANN,) * 4 + (0, 0)
+    prob = Problem(dim=2, nx=nx, ny=ny, nz=1, dx=dx, n_phases=N, phase_type=np.array([0, 1, 1], np.int32),
+                   gamma=gam, mobility=uniform_pairs(N, M), W=W, has_conc=1, k=(k, k), c0=tuple(c0),
+                   D=(D, D), bc_phi=nb, bc_c=nb, name="triplejunction%dx%d_g%g" % (nx, ny, gamma_ab))
+    x, y, _ = cell_centres(nx, ny, 1, dx)
+    cx, cy = nx * dx / 2.0, ny * dx / 2.0
+    pa = profile(r - np.sqrt((x - cx) ** 2 + (y - cy) ** 2), W)
+    t1 = profile(cy - y, W)
+    u = np.stack([pa, (1.0 - pa) * t1, (1.0 - pa) * (1.0 - t1), np.zeros_like(pa)])
+    u[3] = u[0] * c0[0] + (u[1] + u[2]) * c0[1]
+    if shift:
+        area = nx * ny * dx * dx
+        inner = math.pi * r * r
+        target = inner * c0[0] + (area - inner) * c0[1]
+        u[3] += (target - u[3].sum() * dx * dx) / area
+    return prob, u
+
+
 def stefan_L(W, k=1.0, dc=0.96, D=1.0, MF=0.3084251):
     """Thin-interface phase-field mobility for vanishing kinetic coefficient
     (Eq. thin-interface, Sec. 5.2.2): L = pi^2/(16 W^2) D (dc/dmu) / (dc_eq^2 (M+F)),
