@@ -55,9 +55,9 @@ def workload_problem(name, device):
 # algorithmic vectors moved per pass kind (reads + writes of whole state vectors)
 PASS_VECTORS = {"rkl2": 5, "rkl1": 3, "sts_first": 3, "sts_err": 3, "euler": 2, "ssp": 2, "rhs": 1}
 # DRAM bytes (read + write) per cell of one RKL2 stage pass on this workload's
-# 32-phase FP32 state, from an ncu capture of the 128^3 case (1.339 GB per
+# 32-phase FP32 state, from an ncu capture of the 128^3 case (1.316 GB per
 # launch for 2,097,152 cells); traffic grows in proportion to the cells.
-RKL2_TRAFFIC_PER_CELL = {"grains256": 1.339e9 / 2097152, "grains128": 1.339e9 / 2097152}
+RKL2_TRAFFIC_PER_CELL = {"grains256": 1.316e9 / 2097152, "grains128": 1.316e9 / 2097152}
 
 
 class ClockSampler:
