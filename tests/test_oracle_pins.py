@@ -447,3 +447,51 @@ def test_energy_decreases_under_curvature_flow():
     assert all(b < a for a, b in zip(Fs, Fs[1:]))
     # a circle of radius R carries about 2 pi R gamma
     assert Fs[0] == pytest.approx(2 * math.pi * 14.0, rel=0.05)
+
+
+def test_energy_counts_each_interface_with_its_own_pair_energy():
+    # Eq. energy sums over phase pairs with gamma_ab: two parallel flat
+    # interfaces 0|1 and 1|2 carry gamma_01 + gamma_12 per unit length, and
+    # gamma_02 (a pair that never meets) does not enter.  A transposed or
+    # shifted pair index would pick up gamma_02.
+    W, dx = 4.0, 0.25
+    g01, g12, g02 = 0.7, 1.9, 3.1
+    gam = np.array([[0.0, g01, g02], [g01, 0.0, g12], [g02, g12, 0.0]])
+    n = int(round(96 * W / dx))
+    prob = I.Problem(dim=2, nx=n, ny=3, nz=1, dx=dx, n_phases=3, phase_type=np.array([0, 0, 0], np.int32),
+                     gamma=gam, mobility=I.uniform_pairs(3, 1.0), W=W, bc_phi=(1, 1, 0, 0, 0, 0))
+    x = (np.arange(n) + 0.5) * dx
+    L = n * dx
+    p1 = I.profile(x - L / 3, W) * I.profile(2 * L / 3 - x, W)
+    p0 = 1.0 - I.profile(x - L / 3, W)
+    p2 = 1.0 - I.profile(2 * L / 3 - x, W)
+    assert np.abs(p0 + p1 + p2 - 1.0).max() < 1e-14          # the profiles do not overlap
+    u = np.stack([np.tile(p, 3) for p in (p0, p1, p2)])
+    F = ref.Oracle(prob).energy(u) / (3 * dx)
+    assert F == pytest.approx(g01 + g12, rel=2e-3)
+    assert abs(F - (g01 + g02)) > 0.5 and abs(F - (g02 + g12)) > 0.5
+
+
+def test_absent_phase_leaves_the_two_phase_rhs():
+    # Eq. phieq with the n(phi) filter (Q3): a phase that is zero in a cell and
+    # its neighbours is not active, N_z counts the two present phases, and
+    # the RHS is the two-phase one with gamma_01 and M_01, whatever the
+    # absent phase's pair parameters.  (The two-phase RHS is pinned to its
+    # closed form above.)  A non-equilibrium profile makes the RHS nonzero.
+    W = 2.0
+    n = 40
+    x = (np.arange(n) + 0.5) - n / 2
+    ph = np.tile(I.profile(x, 1.6 * W), 5)                      # too wide: not stationary
+    two = I.Problem(dim=2, nx=n, ny=5, nz=1, dx=1.0, n_phases=2, phase_type=np.array([0, 0], np.int32),
+                    gamma=I.uniform_pairs(2, 0.8), mobility=I.uniform_pairs(2, 1.4), W=W,
+                    bc_phi=(1, 1, 0, 0, 0, 0))
+    gam = np.array([[0.0, 0.8, 5.0], [0.8, 0.0, 0.3], [5.0, 0.3, 0.0]])
+    mob = np.array([[0.0, 1.4, 9.0], [1.4, 0.0, 0.2], [9.0, 0.2, 0.0]])
+    three = I.Problem(dim=2, nx=n, ny=5, nz=1, dx=1.0, n_phases=3, phase_type=np.array([0, 0, 0], np.int32),
+                      gamma=gam, mobility=mob, W=W, bc_phi=(1, 1, 0, 0, 0, 0))
+    r2, nz2 = ref.Oracle(two).rhs(np.stack([1 - ph, ph]))
+    r3, nz3 = ref.Oracle(three).rhs(np.stack([1 - ph, ph, np.zeros_like(ph)]))
+    assert np.abs(r2).max() > 1e-3
+    np.testing.assert_array_equal(nz3, nz2)
+    np.testing.assert_allclose(r3[:2], r2, rtol=1e-13, atol=1e-15)
+    assert np.all(r3[2] == 0.0)
