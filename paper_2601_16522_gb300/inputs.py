@@ -489,3 +489,30 @@ def sintering_device(n=320, n_grains=64, porosity=0.05, r_range=(4.0, 8.0), gap=
     prob.pores = len(centres)
     prob.porosity = float(phip.sum().item()) / V
     return prob, u
+
+
+def zener_device(n=320, n_grains=64, fraction=0.15, r=6.0, seed=5, dx=0.005, W_cells=2.5, device="cuda"):
+    """Grain growth with immobile particles (Sec. 5.3, Zener pinning): the
+    sintering construction with particles of one radius r = 6 cells at volume
+    fraction 0.15 whose centres are at least 2 r apart, and the immobile
+    parameters M_ab = D_alpha = 5e-8 (M_bb = 5e-3, D_beta = 5e-8, k = 1e5).
+    Returns (Problem, u) with u a float64 device tensor."""
+    prob, u = sintering_device(n=n, n_grains=n_grains, porosity=fraction, r_range=(r, r), gap=0.0, seed=seed,
+                               dx=dx, W_cells=W_cells, M_gb=5e-3, M_gp=5e-8, D_pore=5e-8, D_grain=5e-8,
+                               k=1e5, device=device)
+    prob.name = "zener%d^3_N%d_particles%d" % (n, prob.n_phases, prob.pores)
+    return prob, u
+
+
+def zener_equilibration(prob):
+    """Parameters of the equilibration run that precedes the particle runs
+    (Sec. 5.3): M_bb = 5e-8, M_ab = 5e-3, D_alpha = 5e-3 (D_beta kept), run
+    for 5 time units so that the particles relax capillarily while the grains
+    barely move."""
+    pt = prob.phase_type
+    out = prob.with_(mobility=typed_pairs(pt, 5e-8, 5e-3), D=(5e-3, prob.D[1]),
+                     name=prob.name + "_equilibration")
+    for a in ("pores", "porosity"):
+        if hasattr(prob, a):
+            setattr(out, a, getattr(prob, a))
+    return out
