@@ -477,7 +477,9 @@ def grains_to_half(pf, torch, dev, stream, t_max=60.0, wall_cap_s=120.0):
     prob, u, _ = workload_problem("grains256", dev)
     out = []
     t_half = None
-    for name, opts in (("rkl2-fp32-masked", pf.Simulation.OPT_MASKED), ("rkl2-fp32-dense", 0)):
+    for name, integ, opts in (("rkl2-fp32-masked", pf.RKL2, pf.Simulation.OPT_MASKED),
+                              ("rkl2-fp32-dense", pf.RKL2, 0),
+                              ("rkl1-fp32-masked", pf.RKL1, pf.Simulation.OPT_MASKED)):
         sim = pf.Simulation(prob, precision=32, stream=stream, options=opts)
         sim.set_state(u)
         dte = sim.dt_e()
@@ -488,14 +490,33 @@ def grains_to_half(pf, torch, dev, stream, t_max=60.0, wall_cap_s=120.0):
         t0 = time.perf_counter()
         while alive > n0 // 2 and t < t_max and time.perf_counter() - t0 < wall_cap_s:
             t += dt_out
-            evals += sim.step(pf.RKL2, t, tol=TOL)["rhs_evals"]
+            evals += sim.step(integ, t, tol=TOL)["rhs_evals"]
             alive = sim.reduce()[2]
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
         sim.close()
         out.append({"variant": name, "wall_s": el, "t_reached": t, "grains_alive": alive, "grains_start": n0,
                     "rhs_evals": evals})
-        t_half = t if alive <= n0 // 2 else t_half
+        if integ == pf.RKL2:
+            t_half = t if alive <= n0 // 2 else t_half
+    # fixed-step schemes, FP32 masked: 20 timed steps each at their largest
+    # stable step (SSP(5)2 at 4 dt_e, Sec. 3.2), extrapolated to t_half
+    for name, integ, mult in (("feuler-fp32-masked (estimated)", pf.FEULER, 0.9),
+                              ("ssp52-fp32-masked (estimated)", pf.SSP2, 3.6)):
+        sim = pf.Simulation(prob, precision=32, stream=stream, options=pf.Simulation.OPT_MASKED)
+        sim.set_state(u)
+        dte = sim.dt_e()
+        sim.step(integ, 2 * mult * dte, dt_mult=mult)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = sim.step(integ, 22 * mult * dte, dt_mult=mult)
+        torch.cuda.synchronize()
+        per_step = (time.perf_counter() - t0) / 20.0
+        sim.close()
+        if t_half is not None:
+            n = math.ceil(t_half / (mult * dte))
+            out.append({"variant": name, "wall_s": per_step * n, "rhs_evals": n * st["rhs_evals"] // 20,
+                        "ms_per_step": 1e3 * per_step, "dt": "%g dt_e" % mult})
     # forward Euler, FP64, dense: 20 timed steps, extrapolated
     sim = pf.Simulation(prob, precision=64, stream=stream)
     sim.set_state(u)
@@ -512,6 +533,49 @@ def grains_to_half(pf, torch, dev, stream, t_max=60.0, wall_cap_s=120.0):
         out.append({"variant": "feuler-fp64-dense (estimated)", "wall_s": per_step * n_fe, "rhs_evals": n_fe,
                     "ms_per_step": 1e3 * per_step})
     return {"t_half": t_half, "output_interval": "200 dt_e", "tol": TOL, "variants": out}
+
+
+def sinter_horizon(pf, torch, dev, stream, t_r=0.05, wall_cap_s=150.0):
+    """The 320^3 sintering workload (64 grains + one pore phase + c) run
+    with adaptive RKL2 in FP32 masked storage at r = a = 1e-4 towards the
+    configuration's fixed horizon t_r = 0.05 (about 1.8e5 stable Euler
+    steps), in output intervals of 0.0025, until the wall-clock cap.  A
+    step that meets more than 12 local phases in a cell ends the run with
+    PF_EINVAL; the time reached is reported."""
+    prob, u, _ = workload_problem("sinter320", dev)
+    N = prob.n_phases
+    tol = (1e-4, 1e-4, 1e-4, 1e-4)
+    sim = pf.Simulation(prob, precision=32, stream=stream, options=pf.Simulation.OPT_MASKED)
+    sim.set_state(u)
+    dte = sim.dt_e()
+    m0, vol0, alive0 = sim.reduce()
+    t, evals, acc, rej, status = 0.0, 0, 0, 0, "reached t_r"
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    while t < t_r:
+        if time.perf_counter() - t0 > wall_cap_s:
+            status = "wall-clock cap"
+            break
+        try:
+            st = sim.step(pf.RKL2, min(t_r, t + 0.0025), tol=tol)
+        except pf.PfError as e:
+            status = "stopped: %s" % e
+            break
+        evals += st["rhs_evals"]
+        acc += st["steps_accepted"]
+        rej += st["steps_rejected"]
+        t = st["t"]
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    m1, vol1, alive1 = sim.reduce()
+    sim.close()
+    return {"workload": prob.name, "cells": prob.V, "phases": N, "pores": prob.pores, "porosity": prob.porosity,
+            "dt_e": dte, "tol": tol, "t_r": t_r, "t_reached": t, "status": status, "rhs_evals": evals,
+            "accepted": acc, "rejected": rej, "wall_s": wall, "fe_rhs_evals": t / dte,
+            "rhs_ratio_vs_fe": (t / dte) / max(evals, 1), "gcell_updates_per_s": prob.V * evals / wall / 1e9,
+            "grains_alive": [alive0, alive1],
+            "pore_volume_change": float((vol1[N - 1] - vol0[N - 1]) / vol0[N - 1]),
+            "solute_change": float(abs(m1 - m0) / m0)}
 
 
 def run_ours(args, world, rank, local):
@@ -653,6 +717,9 @@ def run_ours(args, world, rank, local):
     sweep = None
     if rank == 0 and args.stefan_sweep:
         sweep = stefan_sweep(pf, torch)
+    horizon = None
+    if rank == 0 and args.sinter_horizon:
+        horizon = sinter_horizon(pf, torch, dev, stream)
 
     if rank == 0:
         line = {
@@ -673,7 +740,7 @@ def run_ours(args, world, rank, local):
             "roofline": roof, "pass_ms": pass_ms,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
             "time_to_solution": tts, "served": served, "masked": masked, "reuse_rhs": reuse,
-            "grains_to_half": to_half, "stefan_sweep": sweep,
+            "grains_to_half": to_half, "stefan_sweep": sweep, "sinter_horizon": horizon,
         }
         print(json.dumps(line), flush=True)
     sim.close()
@@ -695,6 +762,8 @@ def main():
     ap.add_argument("--no-reuse", action="store_true", help="skip the run that reuses F(u^{n+1})")
     ap.add_argument("--stefan-sweep", action="store_true",
                     help="also run the Stefan strip with every adaptive integrator at tolerances 1e-3..1e-6")
+    ap.add_argument("--sinter-horizon", action="store_true",
+                    help="320^3 sintering workload towards its fixed horizon t_r = 0.05 (RKL2, masked)")
     ap.add_argument("--grains-to-half", action="store_true",
                     help="also run the 256^3 grain workload until half of its grains are gone")
     args = ap.parse_args()
