@@ -76,6 +76,11 @@ typedef struct {
     int precision;            /* 64: FP64 storage and arithmetic; 32: FP32 storage and stencil
                                  arithmetic, FP64 time, coefficients and reductions */
     int options;              /* bit set of PF_OPT_* (0: defaults) */
+    double c_ref;             /* FP32 storage only: c is kept as c - c_ref, so values near c_ref
+                                 keep FP32's relative resolution and small per-stage changes are
+                                 not rounded away (choose the concentration of the phase that fills
+                                 most of the domain; 0 stores c itself).  Results are the same up to
+                                 rounding; ignored for precision 64; must be finite. */
 } pf_params;
 
 /* pf_params.options: PF_OPT_TMA runs the FP32 3D passes (5..32 phases, nx a

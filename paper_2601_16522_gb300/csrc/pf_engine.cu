@@ -39,21 +39,21 @@ constexpr int NBUF = 5;
 // memory or page-locked host memory reached through its device mapping.
 template <typename T>
 __global__ void pack_kernel(const double *__restrict__ phi, const double *__restrict__ c, T *__restrict__ dst,
-                            long long V, long long Vs, int N, int NF)
+                            long long V, long long Vs, int N, int NF, double cref)
 {
     const long long n = V * NF;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
          k += (long long)gridDim.x * blockDim.x) {
         const long long f = k / V;
         const long long i = k - f * V;
-        dst[f * Vs + i] = (T)(f < N ? phi[k] : c[i]);
+        dst[f * Vs + i] = (T)(f < N ? phi[k] : c[i] - cref);
     }
 }
 
 // engine layout -> ABI layout (phi and c as for pack_kernel; c may be null)
 template <typename T>
 __global__ void unpack_kernel(const T *__restrict__ src, double *__restrict__ phi, double *__restrict__ c, long long V,
-                              long long Vs, int N, int NF)
+                              long long Vs, int N, int NF, double cref)
 {
     const long long n = V * NF;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
@@ -62,7 +62,7 @@ __global__ void unpack_kernel(const T *__restrict__ src, double *__restrict__ ph
         const long long i = k - f * V;
         const double v = (double)src[f * Vs + i];
         if (f < N) phi[k] = v;
-        else if (c) c[i] = v;
+        else if (c) c[i] = v + cref;
     }
 }
 
@@ -1533,7 +1533,7 @@ template <typename T>
 int set_state_t(pf_handle *h, const double *phi_dev, const double *c_dev)
 {
     pack_kernel<T><<<grid_for(h->V * h->NP), 256, 0, h->stream>>>(phi_dev, c_dev, (T *)h->buf[h->iu], h->V, h->Vs,
-                                                                    h->N, h->NP);
+                                                                    h->N, h->NP, h->g.cref);
     h->launches++;
     if (h->masked) {
         mask_kernel<<<grid_for(h->V), 256, 0, h->stream>>>((const float *)h->buf[h->iu], mask_plane(h, h->buf[h->iu]),
@@ -1547,7 +1547,7 @@ template <typename T>
 int get_state_t(pf_handle *h, double *phi_dev, double *c_dev)
 {
     unpack_kernel<T><<<grid_for(h->V * h->NP), 256, 0, h->stream>>>((const T *)h->buf[h->iu], phi_dev, c_dev, h->V,
-                                                                      h->Vs, h->N, h->NP);
+                                                                      h->Vs, h->N, h->NP, h->g.cref);
     h->launches++;
     return cuda_status(cudaGetLastError());
 }
@@ -1689,6 +1689,7 @@ int pf_create(const pf_params *p, void *cuda_stream, pf_handle **out)
     if (p->dim != 2 && p->dim != 3) return PF_EINVAL;
     if (p->nx < 1 || p->ny < 1 || p->nz < 1 || (p->dim == 2 && p->nz != 1)) return PF_EINVAL;
     if (!(p->dx > 0.0) || !(p->W > 0.0)) return PF_EINVAL;
+    if (!isfinite(p->c_ref)) return PF_EINVAL;
     if (p->n_phases < 2 || !p->phase_type || !p->gamma || (!p->mobility && !p->L_override)) return PF_EINVAL;
     if (p->has_conc != 0 && p->has_conc != 1) return PF_EINVAL;
     if (p->precision != 32 && p->precision != 64) return PF_EINVAL;
@@ -1737,17 +1738,21 @@ int pf_create(const pf_params *p, void *cuda_stream, pf_handle **out)
     g.V = h->V; g.Vs = h->Vs; g.N = N; g.K = h->K; g.NF = NP;
     g.tiles_x = (p->nx + pfk::TX - 1) / pfk::TX;
     g.tiles_y = (p->ny + pfk::TY - 1) / pfk::TY;
+    // FP32 storage keeps c - c_ref (pf_params.c_ref); c0 and the Dirichlet
+    // values are shifted with it, which leaves mu = (c - sum phi c0) / (sum phi / k)
+    // and every difference of psi unchanged
+    g.cref = (h->prec == 32 && h->K) ? p->c_ref : 0.0;
     for (int f = 0; f < 6; ++f) {
         g.bc_phi[f] = p->bc_phi[f];
         g.bc_c[f] = p->bc_c[f];
-        g.cdir[f] = p->c_dirichlet[f];
+        g.cdir[f] = p->c_dirichlet[f] - g.cref;
     }
     g.dx2 = p->dx * p->dx;
     h->dx = p->dx;
     for (int t = 0; t < 2; ++t) {
         const double k = h->K ? p->k[t] : 1.0;
         g.k[t] = k;
-        g.c0[t] = p->c0[t];
+        g.c0[t] = p->c0[t] - g.cref;
         g.invk[t] = 1.0 / k;
         g.Dk[t] = p->D[t] / k;
     }
@@ -2022,7 +2027,7 @@ int pf_reduce(pf_handle *h, double *mass_c, double *vol_phi, int *grains_alive)
             if (vol_phi) vol_phi[f] = tot * dv;
             if (mx >= 0.5) alive++;
         } else if (mass_c) {
-            *mass_c = tot * dv;
+            *mass_c = (tot + (double)h->V * h->g.cref) * dv;     // the state holds c - cref
         }
     }
     if (mass_c && !h->K) *mass_c = 0.0;

@@ -54,9 +54,12 @@ struct Geom {
     long long V, Vs;                    // cells, field stride
     int N, K, NF;
     int bc_phi[6], bc_c[6];
-    double cdir[6];
+    double cdir[6];                     // Dirichlet value of c per face, minus cref
     double dx2;                         // dx * dx
-    double k[2], c0[2], invk[2], Dk[2]; // per chemical type: k, c0, 1/k, D/k
+    double k[2], c0[2], invk[2], Dk[2]; // per chemical type: k, c0 - cref, 1/k, D/k
+    double cref;                        // FP32 storage holds c - cref (0 in FP64); c0 and cdir
+                                        // are shifted by it, so mu and the face fluxes are those
+                                        // of c, and only the error weights |c| add it back
     int tiles_x, tiles_y;               // block tiling of the x-y plane
 };
 
@@ -414,7 +417,7 @@ __device__ __forceinline__ void cell_body(const Geom &g, const Pass<T> &P, const
                 const T un = ldg(P.p0 + oc), un1 = ldg(P.in + oc), rn = ldg(P.r0in + oc);
                 const T sr = rn + rc;
                 const T e = ((T)12 * (un - un1) + ((T)6 * dt) * sr) / (T)15;
-                const T au = tabs(un), av = tabs(un1);
+                const T au = tabs(un + (T)g.cref), av = tabs(un1 + (T)g.cref);
                 const T w = (T)P.r_c * (au > av ? au : av) + (T)P.a_c;
                 const T q = e / w;
                 esum += (double)(q * q);
@@ -523,7 +526,7 @@ __device__ __forceinline__ void cell_body(const Geom &g, const Pass<T> &P, const
                     P.zout[o] = zv;
                     if (emb) {
                         const T e = acc - zv;
-                        const T au = tabs(ldg(P.uw + o)), av = tabs(acc);
+                        const T au = tabs(ldg(P.uw + o) + (T)g.cref), av = tabs(acc + (T)g.cref);
                         const T wt = (T)P.r_c * (au > av ? au : av) + (T)P.a_c;
                         const T q = e / wt;
                         esum += (double)(q * q);
@@ -902,7 +905,7 @@ __device__ __forceinline__ void fast_cell(const Geom &g, const Pass<float> &P, L
             const long long o = (long long)N * Vs + i;
             const T un = ldg(P.p0 + o), un1 = cc, rn = ldg(P.r0in + o);
             const T e = ((T)12 * (un - un1) + ((T)6 * dt) * (rn + rc)) * ((T)1 / (T)15);
-            const T w = (T)P.r_c * fmaxf(fabsf(un), fabsf(un1)) + (T)P.a_c;
+            const T w = (T)P.r_c * fmaxf(fabsf(un + (T)g.cref), fabsf(un1 + (T)g.cref)) + (T)P.a_c;
             const T q = e / w;
             esum += (double)(q * q);
             ecnt += 1;
@@ -1218,7 +1221,7 @@ __device__ __forceinline__ void masked_cell(const Geom &g, const Pass<float> &P,
             const long long o = (long long)N * Vs + i;
             const T un = ldg(P.p0 + o), un1 = cc, rn = ldg(P.r0in + o);
             const T e = ((T)12 * (un - un1) + ((T)6 * dt) * (rn + rc)) * ((T)1 / (T)15);
-            const T wt = (T)P.r_c * fmaxf(fabsf(un), fabsf(un1)) + (T)P.a_c;
+            const T wt = (T)P.r_c * fmaxf(fabsf(un + (T)g.cref), fabsf(un1 + (T)g.cref)) + (T)P.a_c;
             const T q = e / wt;
             esum += (double)(q * q);
             ecnt += 1;
@@ -1485,7 +1488,7 @@ __device__ __forceinline__ void big_cell(const Geom &g, const Pass<float> &P, Pl
             const long long o = (long long)N * Vs + i;
             const T un = ldg(P.p0 + o), un1 = cc, rn = ldg(P.r0in + o);
             const T e = ((T)12 * (un - un1) + ((T)6 * dt) * (rn + rc)) * ((T)1 / (T)15);
-            const T w = (T)P.r_c * fmaxf(fabsf(un), fabsf(un1)) + (T)P.a_c;
+            const T w = (T)P.r_c * fmaxf(fabsf(un + (T)g.cref), fabsf(un1 + (T)g.cref)) + (T)P.a_c;
             const T q = e / w;
             esum += (double)(q * q);
             ecnt += 1;

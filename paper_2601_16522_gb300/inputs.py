@@ -45,6 +45,7 @@ class Problem:
     bc_phi: tuple = (0, 0, 0, 0, 0, 0)
     bc_c: tuple = (0, 0, 0, 0, 0, 0)
     c_dirichlet: tuple = (0.0,) * 6
+    c_ref: float = 0.0              # FP32 storage keeps c - c_ref (the majority phase's c)
     name: str = ""
 
     @property
@@ -157,7 +158,7 @@ def double_triple_junction(nx=192, ny=96, r=32.0, W=2.5, gamma_bb=1.0, gamma_ab=
     nb = (BC_NEUMANN,) * 4 + (0, 0)
     prob = Problem(dim=2, nx=nx, ny=ny, nz=1, dx=dx, n_phases=N, phase_type=np.array([0, 1, 1], np.int32),
                    gamma=gam, mobility=uniform_pairs(N, M), W=W, has_conc=1, k=(k, k), c0=tuple(c0),
-                   D=(D, D), bc_phi=nb, bc_c=nb, name="triplejunction%dx%d_g%g" % (nx, ny, gamma_ab))
+                   D=(D, D), bc_phi=nb, bc_c=nb, c_ref=c0[1], name="triplejunction%dx%d_g%g" % (nx, ny, gamma_ab))
     x, y, _ = cell_centres(nx, ny, 1, dx)
     cx, cy = nx * dx / 2.0, ny * dx / 2.0
     pa = profile(r - np.sqrt((x - cx) ** 2 + (y - cy) ** 2), W)
@@ -484,7 +485,7 @@ def sintering_device(n=320, n_grains=64, porosity=0.05, r_range=(4.0, 8.0), gap=
     ptype[n_grains] = 0
     prob = Problem(dim=3, nx=n, ny=n, nz=n, dx=dx, n_phases=N, phase_type=ptype,
                    gamma=uniform_pairs(N, gamma), mobility=typed_pairs(ptype, M_gb, M_gp), W=W_cells * dx,
-                   has_conc=1, k=(k, k), c0=tuple(c0), D=(D_pore, D_grain),
+                   has_conc=1, k=(k, k), c0=tuple(c0), D=(D_pore, D_grain), c_ref=c0[1],
                    name="sinter%d^3_N%d_pores%d" % (n, N, len(centres)))
     prob.pores = len(centres)
     prob.porosity = float(phip.sum().item()) / V

@@ -36,7 +36,8 @@ class pf_params(C.Structure):
                 ("gamma", _dp), ("mobility", _dp), ("W", C.c_double), ("L_override", _dp),
                 ("has_conc", C.c_int), ("k", C.c_double * 2), ("c0", C.c_double * 2),
                 ("D", C.c_double * 2), ("bc_phi", C.c_int * 6), ("bc_c", C.c_int * 6),
-                ("c_dirichlet", C.c_double * 6), ("precision", C.c_int), ("options", C.c_int)]
+                ("c_dirichlet", C.c_double * 6), ("precision", C.c_int), ("options", C.c_int),
+                ("c_ref", C.c_double)]
 
 
 class pf_tol(C.Structure):
@@ -141,6 +142,7 @@ def make_params(prob, precision=64, options=0):
         p.bc_phi[f], p.bc_c[f], p.c_dirichlet[f] = prob.bc_phi[f], prob.bc_c[f], prob.c_dirichlet[f]
     p.precision = precision
     p.options = options
+    p.c_ref = float(getattr(prob, "c_ref", 0.0) or 0.0)
     return p, keep
 
 
