@@ -63,3 +63,33 @@ def test_instantiation_units_match_their_generator():
     for name, text in gen.render().items():
         with open(os.path.join(os.path.dirname(path), name)) as f:
             assert f.read() == text, name
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    # The ctypes mirrors of pf_params, pf_tol, pf_step_opts and pf_stats must
+    # have the C layout: compile a probe against include/pf.h and compare the
+    # size and every field offset.
+    import shutil
+    import subprocess
+    from paper_2601_16522_gb300 import pf
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"pf_params": pf.pf_params, "pf_tol": pf.pf_tol, "pf_step_opts": pf.pf_step_opts,
+               "pf_stats": pf.pf_stats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pf.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append('printf("%s size %%zu\\n", sizeof(%s));' % (name, name))
+        for fname, _ in cls._fields_:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (name, fname, name, fname))
+    lines.append("return 0; }")
+    src = tmp_path / "probe.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "probe"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for name, cls in structs.items():
+        assert got[(name, "size")] == ctypes.sizeof(cls), name
+        for fname, _ in cls._fields_:
+            assert got[(name, fname)] == getattr(cls, fname).offset, (name, fname)
