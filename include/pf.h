@@ -74,7 +74,10 @@ typedef struct {
     int bc_c[6];              /* pf_bc per face for c (periodic, Neumann or Dirichlet) */
     double c_dirichlet[6];    /* Dirichlet value of c per face */
     int precision;            /* 64: FP64 storage and arithmetic; 32: FP32 storage and stencil
-                                 arithmetic, FP64 time, coefficients and reductions */
+                                 arithmetic, FP64 time, coefficients and reductions.  Every
+                                 stage rounds each stored value once (combinations are affine,
+                                 increments summed first), so sum c dV drifts by at most 2^-24
+                                 of sum |c - c_ref| dV per stage */
     int options;              /* bit set of PF_OPT_* (0: defaults) */
     double c_ref;             /* FP32 storage only: c is kept as c - c_ref, so values near c_ref
                                  keep FP32's relative resolution and small per-stage changes are
