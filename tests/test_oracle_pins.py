@@ -495,3 +495,20 @@ def test_absent_phase_leaves_the_two_phase_rhs():
     np.testing.assert_array_equal(nz3, nz2)
     np.testing.assert_allclose(r3[:2], r2, rtol=1e-13, atol=1e-15)
     assert np.all(r3[2] == 0.0)
+
+
+def test_equilibrium_targets_match_printed_values():
+    # The targets the GPU equilibrium tests use: gamma * kappa of the embedded
+    # circle (Sec. 5.1.1) and Young's dihedral angle of the double triple
+    # junction (Sec. 5.1.2), against the values the paper prints.
+    assert 1.0 / 32.0 == pytest.approx(G["embedding_dP"], abs=0.5e-3)
+    theta = math.degrees(2.0 * math.acos(1.0 / (2.0 * 2.0)))
+    assert round(theta, 2) == G["tj_theta_eq_deg"]
+    # the lens measure of Sec. 5.1.2 (vesica piscis, theta = 4 arctan(S / L))
+    # gives 180 degrees for a circle and theta_eq for arcs meeting at theta_eq
+    assert math.degrees(4.0 * math.atan(1.0)) == pytest.approx(180.0)
+    half = math.radians(theta) / 2.0                 # half of the interior angle at the tip
+    R = 1.0
+    L = R * math.sin(half)                           # half chord of an arc of radius R
+    S = R - R * math.cos(half)                       # its sagitta
+    assert math.degrees(4.0 * math.atan(S / L)) == pytest.approx(theta, rel=1e-12)
