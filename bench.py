@@ -578,6 +578,39 @@ def sinter_horizon(pf, torch, dev, stream, t_r=0.05, wall_cap_s=150.0):
             "solute_change": float(abs(m1 - m0) / m0)}
 
 
+def precision_check(pf, torch, dev, stream, t_end=2.0):
+    """FP32 against FP64 on the 256^3 grain workload: adaptive RKL2 from the
+    same initial state to the same time t_end (about 2400 stable Euler steps)
+    in FP32 (masked storage, equal to dense) and in FP64; the largest
+    difference of any phase value, the largest relative difference of a
+    phase volume and the alive-grain counts."""
+    prob, u, _ = workload_problem("grains256", dev)
+    out = {}
+    res = {}
+    for prec, opts in ((32, pf.Simulation.OPT_MASKED), (64, 0)):
+        sim = pf.Simulation(prob, precision=prec, stream=stream, options=opts)
+        sim.set_state(u)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = sim.step(pf.RKL2, t_end, tol=TOL)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        _, vol, alive = sim.reduce()
+        v = torch.empty_like(u)
+        sim.get_state(out=v)
+        torch.cuda.synchronize()
+        sim.close()
+        res[prec] = (v, vol, alive)
+        out["fp%d" % prec] = {"rhs_evals": st["rhs_evals"], "accepted": st["steps_accepted"],
+                              "rejected": st["steps_rejected"], "wall_s": wall, "grains_alive": alive}
+    d = (res[32][0] - res[64][0]).abs()
+    vol32, vol64 = res[32][1], res[64][1]
+    out.update({"t_end": t_end, "max_abs_phi_diff": float(d.max().item()),
+                "mean_abs_phi_diff": float(d.mean().item()),
+                "max_rel_volume_diff": float(max(abs(a - b) / b for a, b in zip(vol32, vol64) if b > 0))})
+    return out
+
+
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
@@ -720,6 +753,9 @@ def run_ours(args, world, rank, local):
     horizon = None
     if rank == 0 and args.sinter_horizon:
         horizon = sinter_horizon(pf, torch, dev, stream)
+    prec_check = None
+    if rank == 0 and args.precision_check:
+        prec_check = precision_check(pf, torch, dev, stream)
 
     if rank == 0:
         line = {
@@ -740,7 +776,7 @@ def run_ours(args, world, rank, local):
             "roofline": roof, "pass_ms": pass_ms,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
             "time_to_solution": tts, "served": served, "masked": masked, "reuse_rhs": reuse,
-            "grains_to_half": to_half, "stefan_sweep": sweep, "sinter_horizon": horizon,
+            "grains_to_half": to_half, "stefan_sweep": sweep, "sinter_horizon": horizon, "precision_check": prec_check,
         }
         print(json.dumps(line), flush=True)
     sim.close()
@@ -762,6 +798,8 @@ def main():
     ap.add_argument("--no-reuse", action="store_true", help="skip the run that reuses F(u^{n+1})")
     ap.add_argument("--stefan-sweep", action="store_true",
                     help="also run the Stefan strip with every adaptive integrator at tolerances 1e-3..1e-6")
+    ap.add_argument("--precision-check", action="store_true",
+                    help="256^3 grain workload: FP32 against FP64, adaptive RKL2 to t = 2")
     ap.add_argument("--sinter-horizon", action="store_true",
                     help="320^3 sintering workload towards its fixed horizon t_r = 0.05 (RKL2, masked)")
     ap.add_argument("--grains-to-half", action="store_true",
