@@ -227,6 +227,24 @@ int pf_energy(struct pf_handle *h, double *F);
    Sec. 5.3). */
 int pf_dt_e(struct pf_handle *h, double *dt_e);
 
+/* State of the adaptive step-size controller (Sec. 3.3: PID control with
+   bias): the bias b (0.1..0.98; 0.9 after pf_set_state), the last two
+   accepted biased error norms E1, E2 and step sizes dt1, dt2, how many of
+   them are set (nhist 0..2), and the proposed next step dt_next (0: none,
+   the next adaptive call starts from opts->dt0 or 0.9 dt_e).  A checkpoint
+   of an adaptive run is pf_get_state + pf_get_controller; pf_set_state
+   followed by pf_set_controller on any handle of the same problem resumes
+   it so that the continued run takes the same steps as the uninterrupted
+   one (with PF_STEP_REUSE_RHS the first resumed step re-evaluates F(u^n)).
+   pf_set_controller returns PF_EINVAL for values outside those ranges or not
+   finite, PF_ESTATE before pf_set_state. */
+typedef struct {
+    double b, E1, E2, dt1, dt2, dt_next;
+    int nhist;
+} pf_controller;
+int pf_get_controller(struct pf_handle *h, pf_controller *out);
+int pf_set_controller(struct pf_handle *h, const pf_controller *in);
+
 /* Kinds of fused passes, for pf_profile. */
 enum {
     PF_PASS_EULER = 0,       /* forward Euler stage */

@@ -1854,6 +1854,37 @@ int pf_destroy(pf_handle *h)
     return PF_OK;
 }
 
+int pf_get_controller(pf_handle *h, pf_controller *out)
+{
+    if (!h || !out) return PF_EINVAL;
+    out->b = h->b;
+    out->E1 = h->E1;
+    out->E2 = h->E2;
+    out->dt1 = h->dt1;
+    out->dt2 = h->dt2;
+    out->dt_next = h->dt_next;
+    out->nhist = h->nhist;
+    return PF_OK;
+}
+
+int pf_set_controller(pf_handle *h, const pf_controller *in)
+{
+    if (!h || !in) return PF_EINVAL;
+    if (!h->has_state) return PF_ESTATE;
+    const double v[] = {in->b, in->E1, in->E2, in->dt1, in->dt2, in->dt_next};
+    for (double x : v)
+        if (!isfinite(x) || x < 0.0) return PF_EINVAL;
+    if (in->b < 0.1 || in->b > 0.98 || in->nhist < 0 || in->nhist > 2) return PF_EINVAL;
+    h->b = in->b;
+    h->E1 = in->E1;
+    h->E2 = in->E2;
+    h->dt1 = in->dt1;
+    h->dt2 = in->dt2;
+    h->dt_next = in->dt_next;
+    h->nhist = in->nhist;
+    return PF_OK;
+}
+
 int pf_dt_e(pf_handle *h, double *dte)
 {
     if (!h || !dte) return PF_EINVAL;

@@ -40,6 +40,11 @@ class pf_params(C.Structure):
                 ("c_ref", C.c_double)]
 
 
+class pf_controller(C.Structure):
+    _fields_ = [("b", C.c_double), ("E1", C.c_double), ("E2", C.c_double), ("dt1", C.c_double),
+                ("dt2", C.c_double), ("dt_next", C.c_double), ("nhist", C.c_int)]
+
+
 class pf_tol(C.Structure):
     _fields_ = [("r_phi", C.c_double), ("a_phi", C.c_double), ("r_c", C.c_double), ("a_c", C.c_double)]
 
@@ -80,6 +85,8 @@ def _lib():
         L.pf_reduce.argtypes = [H, _dp, _dp, _ip]
         L.pf_energy.argtypes = [H, _dp]
         L.pf_dt_e.argtypes = [H, _dp]
+        L.pf_get_controller.argtypes = [H, C.POINTER(pf_controller)]
+        L.pf_set_controller.argtypes = [H, C.POINTER(pf_controller)]
         L.pf_destroy.argtypes = [H]
         L.pf_profile.argtypes = [H, C.c_int, _dp, C.POINTER(C.c_longlong)]
         L.pf_footprint.argtypes = [C.POINTER(pf_params), C.POINTER(C.c_longlong)]
@@ -312,6 +319,17 @@ class Simulation:
 
     def launch_count(self):
         return _lib().pf_launch_count(self.h)
+
+    def get_controller(self):
+        """Adaptive controller state (bias, error/step history, next step) as a dict."""
+        c = pf_controller()
+        _check(_lib().pf_get_controller(self.h, C.byref(c)), "pf_get_controller")
+        return {k: getattr(c, k) for k, _ in pf_controller._fields_}
+
+    def set_controller(self, state):
+        """Restore a state from get_controller (after set_state)."""
+        c = pf_controller(**{k: state[k] for k, _ in pf_controller._fields_})
+        _check(_lib().pf_set_controller(self.h, C.byref(c)), "pf_set_controller")
 
     def reduce(self):
         m = C.c_double()

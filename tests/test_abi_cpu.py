@@ -76,7 +76,7 @@ def test_binding_structs_match_the_header(tmp_path):
     if cc is None:
         pytest.skip("no C compiler")
     structs = {"pf_params": pf.pf_params, "pf_tol": pf.pf_tol, "pf_step_opts": pf.pf_step_opts,
-               "pf_stats": pf.pf_stats}
+               "pf_stats": pf.pf_stats, "pf_controller": pf.pf_controller}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pf.h"', "int main(void) {"]
     for name, cls in structs.items():
         lines.append('printf("%s size %%zu\\n", sizeof(%s));' % (name, name))
