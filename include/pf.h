@@ -227,6 +227,16 @@ int pf_energy(struct pf_handle *h, double *F);
    Sec. 5.3). */
 int pf_dt_e(struct pf_handle *h, double *dt_e);
 
+/* Self-test of the bounded device waits (failure detection without a GPU
+   fault): launches one block on cuda_stream (NULL: default stream) whose
+   thread waits on a shared-memory mbarrier that nothing arrives on, with the
+   poll loop the TMA-staged kernels use and a limit of `polls` polls
+   (1 .. 2^22, the kernels' own limit).  Returns PF_ETIMEOUT when the wait gave
+   up, as it must; PF_OK if it completed (it cannot); PF_EINVAL for a limit out
+   of range; PF_EDEVICE on a CUDA error.  The context stays usable.
+   Synchronises cuda_stream. */
+int pf_selftest_wait(void *cuda_stream, unsigned polls);
+
 /* State of the adaptive step-size controller (Sec. 3.3: PID control with
    bias): the bias b (0.1..0.98; 0.9 after pf_set_state), the last two
    accepted biased error norms E1, E2 and step sizes dt1, dt2, how many of

@@ -66,6 +66,23 @@ __global__ void unpack_kernel(const T *__restrict__ src, double *__restrict__ ph
     }
 }
 
+// Self-test of the bounded device waits: one thread waits on a shared-memory
+// mbarrier that no thread arrives on, with the poll loop of the TMA kernels
+// and a caller-given limit; it must give up, raise FLAG_TIMEOUT and return.
+__global__ void wait_selftest_kernel(int *flag, unsigned polls)
+{
+    __shared__ __align__(8) unsigned long long bar;
+    if (threadIdx.x == 0) {
+        pfk::mbar_init(&bar, 1);
+        pfk::mbar_fence_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (!pfk::mbar_wait(&bar, 0u, polls)) atomicOr(flag, pfk::FLAG_TIMEOUT);
+        asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(pfk::smem_u32(&bar)) : "memory");
+    }
+}
+
 // Fixed-order sum of the per-block error partials (one block of 256 threads).
 __global__ void finalize_err_kernel(const double *__restrict__ ps, const long long *__restrict__ pc, int n,
                                     double *out_sum, long long *out_cnt)
@@ -1852,6 +1869,25 @@ int pf_destroy(pf_handle *h)
     free_all(h);
     delete h;
     return PF_OK;
+}
+
+int pf_selftest_wait(void *cuda_stream, unsigned polls)
+{
+    if (polls == 0 || polls > pfk::TMA_SPIN) return PF_EINVAL;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    int *d = nullptr;
+    if (cudaMallocAsync((void **)&d, sizeof(int), s) != cudaSuccess) return PF_ENOMEM;
+    int hflag = 0;
+    cudaError_t e = cudaMemsetAsync(d, 0, sizeof(int), s);
+    if (e == cudaSuccess) {
+        wait_selftest_kernel<<<1, 32, 0, s>>>(d, polls);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hflag, d, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFreeAsync(d, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess || e != cudaSuccess) return PF_EDEVICE;
+    return (hflag & pfk::FLAG_TIMEOUT) ? PF_ETIMEOUT : PF_OK;
 }
 
 int pf_get_controller(pf_handle *h, pf_controller *out)

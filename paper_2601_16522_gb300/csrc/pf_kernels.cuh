@@ -635,10 +635,10 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long *b, unsigned pa
     return ok != 0;
 }
 
-// Bounded wait: false after TMA_SPIN polls (the caller raises FLAG_TIMEOUT).
-__device__ __forceinline__ bool mbar_wait(unsigned long long *b, unsigned parity)
+// Bounded wait: false after `polls` polls (the caller raises FLAG_TIMEOUT).
+__device__ __forceinline__ bool mbar_wait(unsigned long long *b, unsigned parity, unsigned polls = TMA_SPIN)
 {
-    for (unsigned k = 0; k < TMA_SPIN; ++k)
+    for (unsigned k = 0; k < polls; ++k)
         if (mbar_try_wait(b, parity)) return true;
     return false;
 }

@@ -85,6 +85,7 @@ def _lib():
         L.pf_reduce.argtypes = [H, _dp, _dp, _ip]
         L.pf_energy.argtypes = [H, _dp]
         L.pf_dt_e.argtypes = [H, _dp]
+        L.pf_selftest_wait.argtypes = [C.c_void_p, C.c_uint]
         L.pf_get_controller.argtypes = [H, C.POINTER(pf_controller)]
         L.pf_set_controller.argtypes = [H, C.POINTER(pf_controller)]
         L.pf_destroy.argtypes = [H]
@@ -151,6 +152,13 @@ def make_params(prob, precision=64, options=0):
     p.options = options
     p.c_ref = float(getattr(prob, "c_ref", 0.0) or 0.0)
     return p, keep
+
+
+def selftest_wait(polls=1 << 16, stream=None):
+    """Bounded-wait self-test (pf_selftest_wait): returns the status, which is
+    PF_ETIMEOUT (4) when the device wait gave up as designed."""
+    s = None if stream is None else C.c_void_p(stream.cuda_stream)
+    return _lib().pf_selftest_wait(s, polls)
 
 
 def footprint(prob, precision=64, options=0):
