@@ -93,3 +93,19 @@ def test_binding_structs_match_the_header(tmp_path):
         assert got[(name, "size")] == ctypes.sizeof(cls), name
         for fname, _ in cls._fields_:
             assert got[(name, fname)] == getattr(cls, fname).offset, (name, fname)
+
+
+def test_argument_checks_without_gpu():
+    # Entry points reject bad arguments before any device work, so these run
+    # without a GPU: a null handle, a null output, a poll limit out of range.
+    from paper_2601_16522_gb300 import pf
+    L = pf.lib()
+    ctl = pf.pf_controller()
+    assert L.pf_get_controller(None, ctypes.byref(ctl)) == 1
+    assert L.pf_set_controller(None, ctypes.byref(ctl)) == 1
+    assert L.pf_selftest_wait(None, 0) == 1
+    assert L.pf_selftest_wait(None, (1 << 22) + 1) == 1
+    d = ctypes.c_double()
+    assert L.pf_dt_e(None, ctypes.byref(d)) == 1
+    assert L.pf_energy(None, ctypes.byref(d)) == 1
+    assert L.pf_destroy(None) == 0
