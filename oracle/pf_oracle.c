@@ -350,7 +350,8 @@ static void project(const or_sys *S, double *u, unsigned char *acted, int *bad)
    conditions, so that choice would give a zero estimate.  Reading: the
    embedding does not use the last stage (bh_10 = 0) and is the minimum-norm
    solution of the four order-3 conditions over bh_1..bh_9.  Parity unpinned
-   for this reading (its order is pinned by the Dahlquist tests). */
+   for this reading: its order is pinned (Dahlquist tests and a nonlinear
+   system), the minimum-norm choice is not. */
 static void ssp104_tableau(double Am[10][10], double b[10])
 {
     memset(Am, 0, sizeof(double) * 100);

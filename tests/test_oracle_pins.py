@@ -512,3 +512,43 @@ def test_equilibrium_targets_match_printed_values():
     L = R * math.sin(half)                           # half chord of an arc of radius R
     S = R - R * math.cos(half)                       # its sagitta
     assert math.degrees(4.0 * math.atan(S / L)) == pytest.approx(theta, rel=1e-12)
+
+
+def test_ssp104_embedded_order_three_on_a_nonlinear_system():
+    # The Dahlquist test sees only the linear order conditions; on a
+    # nonlinear system the embedded solution u^n + h sum bh_i F_i is of order
+    # three only if bh also meets sum bh_i c_i^2 = 1/3.  The stages come from
+    # the low-storage form of Ketcheson's SSP(10,4) (Sec. 3.2) written as a
+    # plain stage loop here; only the weights come from the oracle.
+    from scipy.integrate import solve_ivp
+    bh = ref.ssp104_embedded_weights()
+
+    def f(y):
+        return np.array([-y[1] * y[0] + 0.3, y[0] * y[0] - 0.5 * y[1] + np.sin(y[0])])
+
+    def step(u, h):
+        F = []
+        q1 = u.copy()
+        for _ in range(5):
+            F.append(f(q1))
+            q1 = q1 + (h / 6.0) * F[-1]
+        q2 = u / 25.0 + 9.0 * q1 / 25.0
+        q1 = 15.0 * q2 - 5.0 * q1
+        for _ in range(4):
+            F.append(f(q1))
+            q1 = q1 + (h / 6.0) * F[-1]
+        F.append(f(q1))
+        main = q2 + 0.6 * q1 + (h / 10.0) * F[-1]
+        emb = u + h * sum(b * Fi for b, Fi in zip(bh, F))
+        return main, emb
+
+    u0 = np.array([0.7, -0.4])
+    errs_main, errs_emb = [], []
+    for h in (0.04, 0.02, 0.01):
+        exact = solve_ivp(lambda t, y: f(y), (0.0, h), u0, method="DOP853", rtol=1e-13, atol=1e-15).y[:, -1]
+        m, e = step(u0, h)
+        errs_main.append(np.abs(m - exact).max())
+        errs_emb.append(np.abs(e - exact).max())
+    for k in range(2):
+        assert math.log2(errs_emb[k] / errs_emb[k + 1]) == pytest.approx(4.0, abs=0.2)   # local error h^4
+        assert math.log2(errs_main[k] / errs_main[k + 1]) == pytest.approx(5.0, abs=0.3)  # the scheme itself
