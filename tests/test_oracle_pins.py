@@ -552,3 +552,20 @@ def test_ssp104_embedded_order_three_on_a_nonlinear_system():
     for k in range(2):
         assert math.log2(errs_emb[k] / errs_emb[k + 1]) == pytest.approx(4.0, abs=0.2)   # local error h^4
         assert math.log2(errs_main[k] / errs_main[k + 1]) == pytest.approx(5.0, abs=0.3)  # the scheme itself
+
+
+def test_energy_chemical_term_closed_form():
+    # Eq. energy with the KKS chemistry of Sec. 2: in a uniform single-phase
+    # state the gradient and obstacle terms vanish and mu = k (c - c0), so the
+    # energy is the volume times mu^2 / (2k) = k (c - c0)^2 / 2.
+    for dim, (nx, ny, nz) in ((2, (6, 5, 1)), (3, (4, 3, 5))):
+        for phase, (k, c0, delta) in enumerate(((500.0, (0.02, 0.98), 3e-3), (7.0, (0.1, 0.6), -0.04))):
+            prob = I.Problem(dim=dim, nx=nx, ny=ny, nz=nz, dx=0.5, n_phases=2,
+                             phase_type=np.array([0, 1], np.int32), gamma=I.uniform_pairs(2, 1.0),
+                             mobility=I.uniform_pairs(2, 1.0), W=2.0, has_conc=1, k=(k, k), c0=c0, D=(1.0, 1.0))
+            V = prob.V
+            phi = np.zeros((2, V))
+            phi[phase] = 1.0
+            c = np.full(V, c0[phase] + delta)
+            F = ref.Oracle(prob).energy(np.vstack([phi, c[None]]))
+            assert F == pytest.approx(V * prob.dx ** dim * k * delta * delta / 2.0, rel=1e-12)
