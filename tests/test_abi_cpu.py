@@ -109,3 +109,40 @@ def test_argument_checks_without_gpu():
     assert L.pf_dt_e(None, ctypes.byref(d)) == 1
     assert L.pf_energy(None, ctypes.byref(d)) == 1
     assert L.pf_destroy(None) == 0
+
+
+def test_create_rejects_degenerate_and_invalid_problems():
+    # pf_create validates every parameter before it touches a device, so the
+    # degenerate and invalid cases run without a GPU; each must be PF_EINVAL.
+    import numpy as np
+    from paper_2601_16522_gb300 import inputs as I
+    from paper_2601_16522_gb300 import pf
+    L = pf.lib()
+    prob, _ = I.multiphase_blobs(8, 6, 1, 3, seed=1, has_conc=1, n_alpha=1)
+    cases = {
+        "empty grid": dict(nx=0),
+        "2D with nz > 1": dict(nz=2),
+        "dx = 0": dict(dx=0.0),
+        "W < 0": dict(W=-1.0),
+        "one phase": dict(n_phases=1, phase_type=np.array([0], np.int32), gamma=np.zeros((1, 1)),
+                          mobility=np.zeros((1, 1))),
+        "more than 128 fields": dict(n_phases=130, phase_type=np.ones(130, np.int32),
+                                     gamma=I.uniform_pairs(130, 1.0), mobility=I.uniform_pairs(130, 1.0)),
+        "phase type 2": dict(phase_type=np.array([0, 2, 1], np.int32)),
+        "k = 0": dict(k=(0.0, 1.0)),
+        "periodic opposite Neumann": dict(bc_phi=(0, 1, 0, 0, 0, 0)),
+        "Dirichlet phase field": dict(bc_phi=(2, 2, 0, 0, 0, 0), bc_c=(2, 2, 0, 0, 0, 0)),
+        "c periodic against phi Neumann": dict(bc_phi=(1, 1, 0, 0, 0, 0), bc_c=(0, 0, 0, 0, 0, 0)),
+        "non-finite c_ref": dict(c_ref=float("inf")),
+    }
+    for name, kw in cases.items():
+        p, keep = pf.make_params(prob.with_(**kw), precision=32)
+        h = ctypes.c_void_p()
+        assert L.pf_create(ctypes.byref(p), None, ctypes.byref(h)) == 1, name
+        assert not h.value, name
+    p, keep = pf.make_params(prob, precision=16)
+    assert L.pf_create(ctypes.byref(p), None, ctypes.byref(ctypes.c_void_p())) == 1
+    p, keep = pf.make_params(prob, precision=64)
+    p.dim = 1
+    assert L.pf_create(ctypes.byref(p), None, ctypes.byref(ctypes.c_void_p())) == 1
+    assert L.pf_create(None, None, ctypes.byref(ctypes.c_void_p())) == 1
