@@ -53,9 +53,11 @@ class Request:
 
     def describe(self):
         p = self.prob
-        size = "x".join(str(v) for v in ((p.nx, p.ny) if p.dim == 2 else (p.nx, p.ny, p.nz)))
-        return "request %d: %s %s, %d phases%s, integrator %d, %s" % (
-            self.rid, p.name or "problem", size, p.n_phases, " + c" if p.has_conc else "", self.integ,
+        dims = [getattr(p, k, None) for k in ("nx", "ny", "nz")][:2 if getattr(p, "dim", 3) == 2 else 3]
+        size = "x".join(str(v) for v in dims) if None not in dims else "V=%s" % getattr(p, "V", "?")
+        return "request %d: %s %s, %s phases%s, integrator %d, %s" % (
+            self.rid, getattr(p, "name", "") or "problem", size, getattr(p, "n_phases", "?"),
+            " + c" if getattr(p, "has_conc", 0) else "", self.integ,
             "tol %s" % (self.tol,) if self.tol is not None else "dt_mult %g" % self.dt_mult)
 
 
@@ -119,18 +121,19 @@ class Server:
         finished = []
 
         def work(req, sidx):
-            set_dev()
             try:
+                set_dev()
                 out, st = self.runner(req, streams[sidx])
                 req.result, req.stats = out, st
             except Exception as exc:                  # reported per request
                 req.error = "%s (%s)" % (exc, req.describe())
-            req.finished = time.perf_counter() - t0
-            with self.lock:
-                self.used -= fp[req.rid]
-                free_streams.append(sidx)
-                finished.append(req)
-                self.lock.notify_all()
+            finally:                                  # memory and worker come back whatever happened
+                req.finished = time.perf_counter() - t0
+                with self.lock:
+                    self.used -= fp[req.rid]
+                    free_streams.append(sidx)
+                    finished.append(req)
+                    self.lock.notify_all()
 
         while nxt < len(pending) or waiting or running:
             now = time.perf_counter() - t0

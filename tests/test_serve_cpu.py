@@ -71,3 +71,25 @@ def test_memory_freed_is_reused():
     assert len(finished) == 3 and all(r.error is None for r in finished)
     spans.sort()
     assert all(spans[i][1] <= spans[i + 1][0] + 1e-3 for i in range(2))
+
+
+def test_failing_request_releases_its_memory():
+    # A run that raises (the engine's PF_EINVAL on a list-capacity overflow,
+    # say) is reported on that request; its memory and worker are released
+    # and the requests behind it still run.
+    reqs = [Request(rid=i, prob=FakeProb(10), u0=None, integ=0, t_end=1.0, arrival=0.0) for i in range(6)]
+
+    def runner(req, stream):
+        if req.rid == 2:
+            raise RuntimeError("pf_step failed: invalid argument (status 1)")
+        time.sleep(0.002)
+        return np.zeros(1), {"rhs_evals": 1}
+
+    srv = Server(100, workers=2, runner=runner, stream_factory=lambda: None, footprint=lambda r: 60)
+    finished, makespan = srv.serve(reqs, realtime=False)
+    assert len(finished) == 6
+    bad = [r for r in finished if r.error]
+    assert [r.rid for r in bad] == [2] and "status 1" in bad[0].error
+    assert srv.used == 0 and srv.peak_used <= 100
+    s = summary(finished, makespan)
+    assert s["completed"] == 5 and s["rejected"] == 1
