@@ -52,3 +52,43 @@ def test_zener_construction_and_equilibration_parameters():
     assert eq.D == (5e-3, 5e-8)
     for f in ("gamma", "W", "k", "c0", "dx", "n_phases"):
         assert np.array_equal(np.asarray(getattr(eq, f)), np.asarray(getattr(prob, f)))
+
+
+def test_poisson_disc_seeds_keep_their_periodic_distance():
+    rng = np.random.default_rng(3)
+    pts = I.poisson_disc_seeds((40, 30, 20), 25, 7.0, 3, rng)
+    assert pts.shape == (25, 3)
+    L = np.array([40.0, 30.0, 20.0])
+    assert np.all(pts >= 0) and np.all(pts < L)
+    d = np.abs(pts[:, None, :] - pts[None, :, :])
+    d = np.minimum(d, L - d)
+    dist = np.sqrt((d * d).sum(-1)) + np.eye(25) * 1e9
+    assert dist.min() >= 7.0
+    with pytest.raises(ValueError):                      # cannot be placed: refused, not looped forever
+        I.poisson_disc_seeds((10, 10), 50, 6.0, 2, np.random.default_rng(0), max_tries=2000)
+
+
+def test_corrected_radius_gives_the_sharp_volume():
+    # Sec. 5.3: the diffuse sphere of radius r_c holds the sharp volume 4/3 pi r^3
+    # (checked here on a fine cell grid, independently of the builder's quadrature)
+    W = 2.5
+    for r in (4.0, 6.0, 8.0):
+        rc = I.corrected_radius(r, W)
+        assert rc < r
+        h = 0.25
+        n = int(np.ceil((rc + math.pi * W / 2 + 1) / h))
+        ax = (np.arange(-n, n) + 0.5) * h
+        X, Y, Z = np.meshgrid(ax, ax, ax, indexing="ij")
+        vol = I.profile(rc - np.sqrt(X * X + Y * Y + Z * Z), W).sum() * h ** 3
+        assert vol == pytest.approx(4.0 / 3.0 * math.pi * r ** 3, rel=2e-3)
+
+
+def test_diffuse_voronoi_grains_are_a_partition():
+    prob, u = I.grains(n=24, n_grains=6, min_dist=8.0, seed=4, dim=3, dx=1.0, W_cells=2.5, M=1.0)
+    np.testing.assert_allclose(u.sum(0), 1.0, atol=1e-14)
+    assert u.min() >= 0.0 and u.max() <= 1.0
+    assert (u.max(1) >= 0.5).sum() == 6                    # every grain has a bulk
+    # bulk cells (one phase at exactly 1) exist, and no cell holds more than
+    # the knn = 6 nearest grains the construction considers
+    assert (u == 1.0).any(axis=0).any()
+    assert (u > 0).sum(0).max() <= 6
