@@ -42,6 +42,7 @@ class Request:
     result: Optional[np.ndarray] = None
     stats: Optional[dict] = None
     error: Optional[str] = None
+    cancelled: bool = False         # set by Server.cancel
 
     @property
     def footprint(self):
@@ -95,6 +96,21 @@ class Server:
         self.runner = runner or run_alone
         self.stream_factory = stream_factory
         self.footprint = footprint or (lambda r: r.footprint)
+        self._by_rid = {}
+
+    def cancel(self, rid):
+        """Cancel request `rid` (from any thread).  A request that has not
+        been admitted leaves without using memory or a worker; one whose run
+        has not started yet releases them at once; an engine call that is
+        already running is not interrupted and its result is kept.  Returns
+        whether the request was still unfinished."""
+        with self.lock:
+            r = self._by_rid.get(rid)
+            if r is None or r.finished == r.finished:          # unknown or finished (not NaN)
+                return False
+            r.cancelled = True
+            self.lock.notify_all()
+            return True
 
     def serve(self, requests, realtime=True):
         """Feed the requests at their arrival times (realtime) or all at once;
@@ -108,6 +124,8 @@ class Server:
             make_stream = self.stream_factory
             set_dev = lambda: None                                      # noqa: E731
         pending = sorted(requests, key=lambda r: (r.arrival, r.rid))
+        with self.lock:
+            self._by_rid = {r.rid: r for r in pending}
         fp = {r.rid: self.footprint(r) for r in pending}
         for r in pending:
             if fp[r.rid] > self.budget:
@@ -122,6 +140,9 @@ class Server:
 
         def work(req, sidx):
             try:
+                if req.cancelled:
+                    req.error = "cancelled before its run started (%s)" % req.describe()
+                    return
                 set_dev()
                 out, st = self.runner(req, streams[sidx])
                 req.result, req.stats = out, st
@@ -140,12 +161,20 @@ class Server:
             while nxt < len(pending) and (not realtime or pending[nxt].arrival <= now):
                 r = pending[nxt]
                 nxt += 1
+                if r.cancelled and not r.error:
+                    r.error = "cancelled before admission (%s)" % r.describe()
                 if r.error:
                     r.finished = now
                     finished.append(r)
                 else:
                     waiting.append(r)
             with self.lock:
+                # requests cancelled while queued leave without memory or a worker
+                for r in [w for w in waiting if w.cancelled]:
+                    waiting.remove(r)
+                    r.error = "cancelled before admission (%s)" % r.describe()
+                    r.finished = time.perf_counter() - t0
+                    finished.append(r)
                 # admit in arrival order while memory and a worker are available
                 while waiting and free_streams and self.used + fp[waiting[0].rid] <= self.budget:
                     r = waiting.pop(0)
@@ -220,8 +249,9 @@ def summary(finished, makespan):
     ok = [r for r in finished if r.error is None]
     lat = np.array([r.latency for r in ok]) if ok else np.zeros(1)
     cells = sum(r.prob.V * r.stats["rhs_evals"] for r in ok)
-    errors = [r.error for r in finished if r.error is not None]
-    return {"requests": len(finished), "completed": len(ok), "rejected": len(finished) - len(ok),
-            "errors": errors[:5],
+    cancelled = [r for r in finished if r.error is not None and r.cancelled]
+    errors = [r.error for r in finished if r.error is not None and not r.cancelled]
+    return {"requests": len(finished), "completed": len(ok), "rejected": len(errors),
+            "cancelled": len(cancelled), "errors": errors[:5],
             "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
             "makespan_s": makespan, "gcell_updates_per_s": cells / makespan / 1e9}

@@ -93,3 +93,44 @@ def test_failing_request_releases_its_memory():
     assert srv.used == 0 and srv.peak_used <= 100
     s = summary(finished, makespan)
     assert s["completed"] == 5 and s["rejected"] == 1
+
+
+def test_cancellation_of_queued_and_running_requests():
+    # Host-side cancellation: a request cancelled while it waits for memory
+    # leaves without ever running; one cancelled while its (uninterruptible)
+    # run is in progress finishes normally; the rest are unaffected.
+    reqs = [Request(rid=i, prob=FakeProb(10), u0=None, integ=0, t_end=1.0, arrival=0.0) for i in range(5)]
+    started = {}
+    gate = threading.Event()
+    ran = []
+
+    def runner(req, stream):
+        ran.append(req.rid)
+        started[req.rid] = True
+        if req.rid == 0:
+            gate.wait(timeout=5.0)                 # holds the whole budget until released
+        return np.zeros(1), {"rhs_evals": 1}
+
+    srv = Server(100, workers=2, runner=runner, stream_factory=lambda: None, footprint=lambda r: 60)
+    out = {}
+    th = threading.Thread(target=lambda: out.update(res=srv.serve(reqs, realtime=False)))
+    th.start()
+    t0 = time.perf_counter()
+    while 0 not in started and time.perf_counter() - t0 < 5.0:
+        time.sleep(0.001)
+    assert srv.cancel(0) is True                   # running: not interrupted
+    assert srv.cancel(3) is True                   # queued behind request 0
+    assert srv.cancel(99) is False                 # unknown
+    gate.set()
+    th.join(timeout=10.0)
+    assert not th.is_alive()
+    finished, makespan = out["res"]
+    by = {r.rid: r for r in finished}
+    assert len(finished) == 5
+    assert by[0].error is None and by[0].result is not None
+    assert by[3].error.startswith("cancelled before admission") and 3 not in ran
+    assert all(by[i].error is None for i in (1, 2, 4))
+    assert srv.used == 0
+    s = summary(finished, makespan)
+    assert s["completed"] == 4 and s["cancelled"] == 1 and s["rejected"] == 0
+    assert srv.cancel(1) is False                  # finished
