@@ -33,3 +33,31 @@ def test_bounded_wait_times_out_and_context_survives(pf):
         ug, _ = sim.get_state()
     assert st["rhs_evals"] == 10 and np.isfinite(ug).all()
     assert np.abs(ug.sum(0) - 1.0).max() < 1e-12
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("field,integ,kw", [
+    ("phase", I.FEULER, dict(dt_mult=0.9)),
+    ("phase", I.RKL2, dict(tol=(1e-4, 1e-3, 1e-4, 1e-4))),
+    ("conc", I.RKL2, dict(tol=(1e-4, 1e-3, 1e-4, 1e-4))),
+], ids=["phase-fe", "phase-rkl2", "conc-rkl2"])
+def test_non_finite_state_is_reported(pf, field, integ, kw, prec):
+    # A non-finite value makes the simplex sum of its cell fail (phases: the
+    # projection checks sum > 0, false for NaN) or the error norm non-finite
+    # (adaptive steps: every concentration entry enters the norm); either way
+    # the step ends with PF_EUNSTABLE (the contract of pf_step), and the
+    # handle still answers.
+    prob, good = I.multiphase_blobs(17, 13, 1, 4, seed=3, has_conc=1, n_alpha=1)
+    u = good.copy()
+    if field == "phase":
+        u[1, 100] = np.nan
+    else:
+        u[prob.n_phases, 100] = np.nan
+    with pf.Simulation(prob, precision=prec) as sim:
+        sim.set_state(u)
+        with pytest.raises(pf.PfError) as e:
+            sim.step(integ, 5 * sim.dt_e(), **kw)
+        assert e.value.status == 3                     # PF_EUNSTABLE
+        sim.set_state(good)
+        st = sim.step(integ, 5 * sim.dt_e(), **kw)
+        assert st["t"] == pytest.approx(5 * sim.dt_e())
