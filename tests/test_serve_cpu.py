@@ -134,3 +134,33 @@ def test_cancellation_of_queued_and_running_requests():
     s = summary(finished, makespan)
     assert s["completed"] == 4 and s["cancelled"] == 1 and s["rejected"] == 0
     assert srv.cancel(1) is False                  # finished
+
+
+def test_poisson_stream_follows_its_recipe():
+    # The served stream's recipe: Poisson arrivals (mean rate 50/s, seed 4),
+    # 2D circles and Stefan strips (N = 2), 2D/3D Voronoi grain structures
+    # with 2..32 phases in masked storage, the four integrators, each request
+    # carrying its own state of the right shape; the same seed gives the same
+    # stream.
+    from paper_2601_16522_gb300 import serve
+    a = serve.poisson_stream(30, rate=50.0, seed=4, sizes3d=(64,), device="cpu")
+    b = serve.poisson_stream(30, rate=50.0, seed=4, sizes3d=(64,), device="cpu")
+    arr = np.array([r.arrival for r in a])
+    assert np.all(np.diff(arr) > 0) and 0.1 < arr[-1] < 2.0        # ~30 / 50 s
+    for r, s in zip(a, b):
+        assert r.arrival == s.arrival and r.integ == s.integ and r.prob.name == s.prob.name
+        assert np.array_equal(r.u0, s.u0)
+    kinds = set()
+    for r in a:
+        p = r.prob
+        assert r.u0.shape == (p.n_phases + p.has_conc, p.V)
+        assert np.allclose(r.u0[:p.n_phases].sum(0), 1.0, atol=1e-12)
+        assert r.integ in (0, 1, 3, 4)
+        assert (r.tol is not None) == (r.integ in (3, 4))
+        if p.name.startswith("grains"):
+            kinds.add("grains")
+            assert 2 <= p.n_phases <= 32 and r.options == 2
+        else:
+            kinds.add(p.name.rstrip("0123456789x"))
+            assert p.n_phases == 2 and p.dim == 2 and r.options == 0
+    assert kinds == {"grains", "circle", "stefan"}
