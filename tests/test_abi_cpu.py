@@ -146,3 +146,19 @@ def test_create_rejects_degenerate_and_invalid_problems():
     p.dim = 1
     assert L.pf_create(ctypes.byref(p), None, ctypes.byref(ctypes.c_void_p())) == 1
     assert L.pf_create(None, None, ctypes.byref(ctypes.c_void_p())) == 1
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    # No CPU fallback: without the compiled library every entry point raises
+    # ImportError instead of computing anything another way.
+    from paper_2601_16522_gb300 import inputs as I
+    from paper_2601_16522_gb300 import pf
+    monkeypatch.setattr(pf, "_LIB", None)
+    monkeypatch.setattr(pf, "LIB_PATH", str(tmp_path / "absent" / "libpf.so"))
+    prob, _ = I.circle(16, 4.0)
+    with pytest.raises(ImportError):
+        pf.Simulation(prob, precision=64)
+    with pytest.raises(ImportError):
+        pf.footprint(prob)
+    with pytest.raises(ImportError):
+        pf.selftest_wait(16)
