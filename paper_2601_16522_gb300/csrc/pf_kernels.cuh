@@ -667,8 +667,9 @@ struct ListSmem {
 // ring filled by the producer warp (and releases the slot afterwards).
 template <int DIM>
 struct PlainLoader {
-    // per-phase base pointers are the same for every thread (uniform); the
-    // per-thread part is a 32-bit cell index (the fast path needs NF*Vs < 2^31)
+    // per-phase base pointers (64-bit phase offsets a * Vs) are the same for
+    // every thread (uniform); the per-thread part is a 32-bit cell index
+    // (Vs < 2^31, checked at dispatch)
     const float *in, *p0, *p2, *r0;
     int Vs, nph;
     int ic, inb[6];
