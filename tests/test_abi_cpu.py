@@ -162,3 +162,45 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
         pf.footprint(prob)
     with pytest.raises(ImportError):
         pf.selftest_wait(16)
+
+
+def test_plain_c_caller_links_and_runs(tmp_path):
+    # The boundary from C itself: a C99 program includes include/pf.h, links
+    # libpf.so and calls the entry points that need no device (status text,
+    # parameter validation, argument checks).
+    import shutil
+    import subprocess
+    from paper_2601_16522_gb300 import pf
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    pf.lib()                                                  # built
+    libdir = os.path.dirname(pf.LIB_PATH)
+    src = tmp_path / "caller.c"
+    src.write_text(r"""
+#include <stdio.h>
+#include <string.h>
+#include "pf.h"
+int main(void) {
+    int ptype[2] = {0, 0};
+    double gam[4] = {0, 1, 1, 0}, mob[4] = {0, 1, 1, 0};
+    pf_params p;
+    memset(&p, 0, sizeof p);
+    p.dim = 2; p.nx = 0; p.ny = 8; p.nz = 1; p.dx = 1.0; p.n_phases = 2;   /* empty grid */
+    p.phase_type = ptype; p.gamma = gam; p.mobility = mob; p.W = 2.0; p.precision = 64;
+    struct pf_handle *h = 0;
+    int s1 = pf_create(&p, 0, &h);
+    pf_controller c;
+    int s2 = pf_get_controller(0, &c);
+    int s3 = pf_selftest_wait(0, 0);
+    int s4 = pf_destroy(0);
+    printf("%d %d %d %d %d %s\n", s1, h == 0, s2, s3, s4, pf_strerror(PF_EINVAL));
+    return 0;
+}
+""")
+    exe = tmp_path / "caller"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe),
+                    "-L", libdir, "-lpf", "-Wl,-rpath," + libdir], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
+    assert out[:5] == ["1", "1", "1", "1", "0"]
+    assert "invalid" in " ".join(out[5:])
