@@ -58,10 +58,12 @@ typedef struct {
     int dim;                  /* 2 or 3 */
     int nx, ny, nz;           /* cells; nz = 1 when dim = 2 */
     double dx;                /* grid spacing */
-    int n_phases;             /* N >= 2 phases stored densely.  At most 12 of them may be
-                                 nontrivial (the n(phi) filter of Eq. phieq) in any one cell,
-                                 the per-cell capacity N_p = 12 the paper uses (Sec. 3.1);
-                                 more is reported as PF_EINVAL by the call that meets it. */
+    int n_phases;             /* N >= 2 phases stored densely.  Up to 12 nontrivial phases
+                                 (the n(phi) filter of Eq. phieq) per cell take the fast
+                                 per-cell list; a cell with more is recomputed on a slower
+                                 path with a 64-entry list (same results); more than 64
+                                 nontrivial phases in one cell is reported as PF_EINVAL by
+                                 the call that meets it. */
     const int *phase_type;    /* N entries, chemical type 0 (alpha) or 1 (beta), Sec. 2 */
     const double *gamma;      /* N*N interface energies gamma_ab, symmetric (diag ignored) */
     const double *mobility;   /* N*N interface mobilities M_ab, symmetric (diag ignored) */
@@ -195,7 +197,12 @@ int pf_rhs(struct pf_handle *h, double *rhs_phi, double *rhs_c, unsigned char *n
    error estimate and norm of Sec. 3.3 and the PID controller with bias.  The
    simplex projection is applied to every stage.  tol may be NULL for fixed
    steps; opts may be NULL (defaults: s = 5, adaptive, dt0 = 0.9 dt_e).
-   stats may be NULL.  PF_EUNSTABLE leaves the last accepted state. */
+   stats may be NULL.  PF_EUNSTABLE (a non-positive simplex sum, a non-finite
+   concentration or error norm) and the other device-detected failures leave
+   the state and time of the last accepted step: adaptive steps are checked
+   after every attempt; in a run of fixed steps every pass after the failing
+   one does nothing and the call returns the state after the last step that
+   completed without a flag (stats->t and steps_accepted say which). */
 int pf_step(struct pf_handle *h, pf_integrator integ, double t_end, const pf_tol *tol,
             const pf_step_opts *opts, pf_stats *stats);
 
@@ -309,8 +316,9 @@ long long pf_launch_count(struct pf_handle *h);
    fields, grains alive = phases whose max is >= 0.5).
    Scratch: a fixed device array inside the library; nothing is allocated and
    nothing is freed.  The first call on each device looks up that array's
-   device address (once per device); make that first call before any CUDA
-   stream capture.  Every call shares the array and writes every entry it
+   device address (once per device and context: after cudaDeviceReset the
+   next call looks it up again); make that first call before any CUDA
+   stream capture.  A NaN in a field makes that field's sum and maximum NaN.  Every call shares the array and writes every entry it
    later reads, so nothing needs clearing, but calls whose kernels overlap on
    the GPU (different streams without ordering) race on it and must be
    serialised by the caller.  The work is enqueued on cuda_stream (NULL: the

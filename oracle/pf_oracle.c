@@ -675,6 +675,56 @@ double or_ctrl_update(or_ctrl *c, double err, double dt, int P, int *accept)
 }
 
 /* ---- driver ------------------------------------------------------------ */
+/* Size h, stage count s and "lands on t_end" flag of the next attempt, given
+   the proposed step dt and the remaining time rem (Sec. 3.2 stage rule;
+   Sec. 5 output at target times).  Adaptive: a proposal within 1e-9 of the
+   remaining time is stretched onto it.  Fixed: step kfix + 1 of nfix; the
+   last one is shortened to land on t_end.  An RKL step that needs more than
+   max_stages stages is refused for fixed steps (OR_EINVAL) and cut to the
+   largest step that max_stages (rounded up to odd) allows for adaptive ones. */
+static int plan_attempt(int integ, int adaptive, double dt, double rem, long kfix, long nfix,
+                        double dte, int ssp_stages, int max_stages, double *h, int *s, int *last)
+{
+    int sts = (integ == OR_RKL1 || integ == OR_RKL2);
+    *last = 0;
+    if (adaptive) {
+        *h = dt;
+        if (*h >= rem * (1.0 - 1e-9)) { *h = rem; *last = 1; }
+    } else {
+        *last = (kfix + 1 >= nfix);
+        *h = *last ? rem : dt;
+    }
+    *s = sts ? or_sts_stages(integ, *h, dte) : (integ == OR_SSP2 ? ssp_stages : (integ == OR_SSP104 ? 10 : 1));
+    if (sts && *s > max_stages && !adaptive) return OR_EINVAL;
+    if (sts && *s > max_stages) {
+        *s = max_stages | 1;
+        double ds = (double)*s;
+        *h = (integ == OR_RKL2 ? (ds * ds + ds - 2.0) / 4.0 : (ds * ds + ds) / 2.0) * 0.9 * dte;
+        *last = 0;
+    }
+    return OR_OK;
+}
+
+int or_drive(int integ, double dte, double t_end, double dt0, int max_stages, int n_err,
+             const double *errs, double *t, or_ctrl *ctrl, double *dt_next,
+             int cap, double *tr_dt, int *tr_s, int *tr_acc)
+{
+    if (max_stages <= 0) max_stages = 1001;
+    double dt = *dt_next > 0.0 ? *dt_next : (dt0 > 0.0 ? dt0 : 0.9 * dte);
+    int k = 0;
+    while (*t < t_end && k < n_err) {
+        double h;
+        int s, last, acc;
+        plan_attempt(integ, 1, dt, t_end - *t, 0, 0, dte, 0, max_stages, &h, &s, &last);
+        dt = or_ctrl_update(ctrl, errs[k], h, or_order(integ), &acc);
+        if (k < cap) { tr_dt[k] = h; tr_s[k] = s; tr_acc[k] = acc; }
+        k++;
+        if (acc) *t = last ? t_end : *t + h;
+    }
+    *dt_next = dt;
+    return k;
+}
+
 int or_run(const or_params *p, int integ, double t_end, const or_tol *tol,
            double dt_mult, double dt0, int ssp_stages, int max_stages,
            double *u, double *t, or_ctrl *ctrl, or_stats *st,
@@ -709,22 +759,10 @@ int or_run(const or_params *p, int integ, double t_end, const or_tol *tol,
             h = replay_dt[attempt];
             s = replay_s[attempt];
             last = (h >= rem * (1.0 - 1e-9));
-        } else {
-            if (adaptive) {
-                h = dt;
-                if (h >= rem * (1.0 - 1e-9)) { h = rem; last = 1; }
-            } else {
-                last = (kfix + 1 >= nfix);
-                h = last ? rem : dt;
-            }
-            s = sts ? or_sts_stages(integ, h, dte) : (integ == OR_SSP2 ? ssp_stages : (integ == OR_SSP104 ? 10 : 1));
-            if (sts && s > max_stages && !adaptive) { status = OR_EINVAL; break; }
-            if (sts && s > max_stages) {
-                s = max_stages | 1;
-                double ds = (double)s;
-                h = (integ == OR_RKL2 ? (ds * ds + ds - 2.0) / 4.0 : (ds * ds + ds) / 2.0) * 0.9 * dte;
-                last = 0;
-            }
+        } else if (plan_attempt(integ, adaptive, dt, rem, kfix, nfix, dte, ssp_stages, max_stages,
+                                &h, &s, &last) != OR_OK) {
+            status = OR_EINVAL;
+            break;
         }
         long ev = or_step(&S, integ, h, s, u, unew, rn, integ == OR_SSP104 ? z : NULL);
         if (ev < 0) { status = ev == -2 ? OR_EUNSTABLE : OR_EINVAL; break; }

@@ -126,6 +126,20 @@ int or_run(const or_params *p, int integ, double t_end, const or_tol *tol,
            int cap, double *tr_dt, int *tr_s, double *tr_err, int *tr_acc, int *tr_len,
            int replay_n, const double *replay_dt, const int *replay_s, const int *replay_acc);
 
+/* ---- controller-only run (Sec. 3.2-3.3) --------------------------------
+   The decisions or_run takes in adaptive mode when the error norm of attempt
+   k is errs[k]: the attempt's size (stretched onto t_end within 1e-9, capped
+   by max_stages; 0: 1001), its RKL stage count, accept/reject and the PID
+   controller update, without evaluating the model.  Starts at *t with the
+   controller state ctrl and the previous proposal *dt_next (0: dt0, or
+   0.9 dte when dt0 is 0); *t advances on acceptance, *dt_next receives the
+   last proposal.  Stops at t_end or after n_err attempts.  The attempted
+   dt, s and accept flags are written to the trace (up to cap entries);
+   returns the number of attempts. */
+int or_drive(int integ, double dte, double t_end, double dt0, int max_stages, int n_err,
+             const double *errs, double *t, or_ctrl *ctrl, double *dt_next,
+             int cap, double *tr_dt, int *tr_s, int *tr_acc);
+
 #ifdef __cplusplus
 }
 #endif

@@ -88,6 +88,9 @@ def lib():
                              C.POINTER(_Ctrl), C.POINTER(_Stats), C.c_int, _dp, _ip, _dp, _ip, _ip,
                              C.c_int, _dp, _ip, _ip]
         L.or_run.restype = C.c_int
+        L.or_drive.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_int, C.c_int, _dp,
+                               _dp, C.POINTER(_Ctrl), _dp, C.c_int, _dp, _ip, _ip]
+        L.or_drive.restype = C.c_int
         _lib = L
     return _lib
 
@@ -276,6 +279,35 @@ def ssp104_embedded_weights():
     bh = np.zeros(10)
     lib().or_ssp104_embedded_weights(_d(bh))
     return bh
+
+
+class Drive:
+    """Controller-only run (Sec. 3.2-3.3, ``or_drive``): the attempt sizes,
+    stage counts and accept flags the oracle's adaptive loop takes when the
+    error norms come from elsewhere (e.g. the GPU's trace).  The controller
+    state and the proposal for the next step carry over between calls, as
+    they do between pf_step calls."""
+
+    def __init__(self, integ, dte, dt0=0.0, max_stages=1001, t=0.0):
+        self.integ, self.dte, self.dt0, self.max_stages = integ, dte, dt0, max_stages
+        self.t = t
+        self.ctrl = _Ctrl()
+        lib().or_ctrl_init(C.byref(self.ctrl))
+        self.dt_next = 0.0
+
+    def run(self, t_end, errs):
+        errs = np.ascontiguousarray(errs, np.float64)
+        n = len(errs)
+        dt = np.zeros(max(n, 1))
+        s = np.zeros(max(n, 1), np.int32)
+        acc = np.zeros(max(n, 1), np.int32)
+        t = C.c_double(self.t)
+        dn = C.c_double(self.dt_next)
+        k = lib().or_drive(self.integ, self.dte, t_end, self.dt0, self.max_stages, n, _d(errs),
+                           C.byref(t), C.byref(self.ctrl), C.byref(dn), n, _d(dt),
+                           s.ctypes.data_as(_ip), acc.ctypes.data_as(_ip))
+        self.t, self.dt_next = t.value, dn.value
+        return dict(dt=dt[:k].copy(), s=s[:k].copy(), acc=acc[:k].copy())
 
 
 def ctrl_sequence(errs, dts, P):

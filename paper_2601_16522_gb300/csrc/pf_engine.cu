@@ -29,6 +29,7 @@ namespace {
 
 const double kPi = 3.14159265358979323846;
 constexpr int NBUF = 5;
+constexpr size_t PF_FLAG_BYTES = 4 * sizeof(int);   // device status words (pfk::raise_flag)
 
 // ---------------------------------------------------------------------------
 // auxiliary kernels: layout conversion and reductions
@@ -168,6 +169,7 @@ template <typename T>
 __global__ void first_from_rhs_kernel(const T *__restrict__ in, T *out, T *r0, long long V, long long Vs, int N, int K,
                                       double b1, int fix, int *flag)
 {
+    if (pfk::pass_skipped(flag)) return;
     const T one = (T)1, b1c = (T)b1;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < V; i += (long long)gridDim.x * blockDim.x) {
         bool changed = false;
@@ -187,7 +189,7 @@ __global__ void first_from_rhs_kernel(const T *__restrict__ in, T *out, T *r0, l
             if (!(best == (T)1 && nnz == 1)) changed = true;
             ssum = (T)1;
         }
-        if (!(ssum > (T)0)) atomicOr(flag, pfk::FLAG_SIMPLEX);
+        if (!(ssum > (T)0)) pfk::raise_flag(flag, pfk::FLAG_SIMPLEX);
         const bool fx = fix && changed;
         for (int a = 0; a < N; ++a) {
             const long long o = (long long)a * Vs + i;
@@ -201,6 +203,7 @@ __global__ void first_from_rhs_kernel(const T *__restrict__ in, T *out, T *r0, l
             const long long o = (long long)N * Vs + i;
             T acc = one * in[o];
             acc = acc + b1c * r0[o];
+            if (!isfinite(acc)) pfk::raise_flag(flag, pfk::FLAG_NONFINITE);
             out[o] = acc;
         }
     }
@@ -215,6 +218,7 @@ __global__ void __launch_bounds__(256)
 first_from_rhs_recompute_kernel(const T *__restrict__ in, T *out, T *r0, long long V, long long Vs, int N, int K,
                                 double b1, int fix, int *flag)
 {
+    if (pfk::pass_skipped(flag)) return;
     const T one = (T)1, b1c = (T)b1;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < V; i += (long long)gridDim.x * blockDim.x) {
         bool changed = false;
@@ -234,7 +238,7 @@ first_from_rhs_recompute_kernel(const T *__restrict__ in, T *out, T *r0, long lo
             if (!(best == (T)1 && nnz == 1)) changed = true;
             ssum = (T)1;
         }
-        if (!(ssum > (T)0)) atomicOr(flag, pfk::FLAG_SIMPLEX);
+        if (!(ssum > (T)0)) pfk::raise_flag(flag, pfk::FLAG_SIMPLEX);
         const bool fx = fix && changed;
 #pragma unroll 8
         for (int a = 0; a < N; ++a) {
@@ -253,6 +257,7 @@ first_from_rhs_recompute_kernel(const T *__restrict__ in, T *out, T *r0, long lo
             const long long o = (long long)N * Vs + i;
             T x = one * in[o];
             x = x + b1c * r0[o];
+            if (!isfinite(x)) pfk::raise_flag(flag, pfk::FLAG_NONFINITE);
             out[o] = x;
         }
     }
@@ -386,6 +391,7 @@ struct pf_handle {
     // stage count and buffer rotation are unchanged)
     cudaGraphExec_t gexec = nullptr;
     int g_integ = -1, g_s = -1, g_iu = -1, g_period = 0;
+    std::vector<int> g_seq;            // buffer holding u^n after each step of the period
     double g_dt = 0.0;
     long long g_evals = 0, g_launches = 0;
     long long graph_replays = 0;
@@ -769,6 +775,7 @@ int do_step(pf_handle *h, int integ, double dt, int s, const pf_tol *tol, bool w
         h->cur_kind = PF_PASS_EULER;
         Pass<T> P = blank_pass<T>(h);
         P.in = B(U); P.out = B(w[0]); P.a1 = 1.0; P.b1 = dt;
+        P.count_step = !want_err;
         if ((st = run_pass<T>(h, P))) return st;
         *out = w[0];
         *evals += 1;
@@ -791,6 +798,7 @@ int do_step(pf_handle *h, int integ, double dt, int s, const pf_tol *tol, bool w
         P.in = B(cur); P.p0 = B(U);
         P.a0 = 1.0 / (double)s; P.a1 = (double)(s - 1) / (double)s; P.b1 = dt / (double)s;
         P.out = B(q1);
+        P.count_step = !want_err;
         if ((st = run_pass<T>(h, P))) return st;
         *out = q1;
         *evals += s;
@@ -824,6 +832,7 @@ int do_step(pf_handle *h, int integ, double dt, int s, const pf_tol *tol, bool w
         Pass<T> P = blank_pass<T>(h);
         P.in = B(cur); P.p0 = B(q2); P.a0 = 0.4; P.a1 = 0.6; P.b1 = dt / 10.0;
         P.out = B(q1);
+        P.count_step = !want_err;
         if (want_err) {
             P.zin = B(zb); P.zout = B(zb); P.bz = dt * bh[9]; P.embedded_err = 1; P.uw = B(U);
             P.r_phi = tol->r_phi; P.a_phi = tol->a_phi; P.r_c = tol->r_c; P.a_c = tol->a_c;
@@ -866,6 +875,7 @@ int do_step(pf_handle *h, int integ, double dt, int s, const pf_tol *tol, bool w
         h->cur_kind = PF_PASS_STS_FIRST;
         Pass<T> P = blank_pass<T>(h);
         P.in = B(U); P.a1 = 1.0; P.b1 = mt1 * dt; P.out = B(ring[0]); P.r0out = B(r0); P.fix_first = o2 ? 1 : 0;
+        P.count_step = !want_err && s == 1;
         if ((st = run_pass<T>(h, P))) return st;
     }
     h->cur_kind = o2 ? PF_PASS_RKL2 : PF_PASS_RKL1;
@@ -889,6 +899,7 @@ int do_step(pf_handle *h, int integ, double dt, int s, const pf_tol *tol, bool w
         P.a1 = mu; P.a2 = nu; P.b1 = mt * dt;
         if (o2) { P.p0 = B(U); P.a0 = (1.0 - mu) - nu; P.r0in = B(r0); P.b0 = gt * dt; }
         P.out = B(ring[(j - 1) % 3]);
+        P.count_step = !want_err && j == s;
         if ((st = run_pass<T>(h, P))) return st;
     }
     const int fin = ring[(s - 1) % 3];
@@ -943,12 +954,13 @@ int read_error(pf_handle *h, double *err)
     return PF_OK;
 }
 
-int check_flag(pf_handle *h)
+int check_flag(pf_handle *h, int *failed_step = nullptr)
 {
-    int flag = 0;
-    if (cudaMemcpyAsync(&flag, h->dflag, sizeof(int), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess) return PF_EDEVICE;
+    int w[4] = {0, 0, 0, 0};
+    if (cudaMemcpyAsync(w, h->dflag, PF_FLAG_BYTES, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess) return PF_EDEVICE;
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return PF_EDEVICE;
-    return flag ? flag_status(flag) : PF_OK;
+    if (failed_step) *failed_step = w[3];
+    return w[0] ? flag_status(w[0]) : PF_OK;
 }
 
 // Capture full fixed steps of size dt with s stages into a graph until the
@@ -970,10 +982,12 @@ bool capture_fixed_steps(pf_handle *h, int integ, double dt, int s)
         return false;
     }
     bool ok = true;
+    std::vector<int> seq;
     do {
         int cand = -1;
         if (do_step<T>(h, integ, dt, s, nullptr, false, &cand, &ev) != PF_OK) { ok = false; break; }
         h->iu = cand;
+        seq.push_back(cand);
         period++;
     } while (h->iu != iu0 && period < 12);
     if (cudaStreamEndCapture(h->stream, &graph) != cudaSuccess) ok = false;
@@ -994,6 +1008,7 @@ bool capture_fixed_steps(pf_handle *h, int integ, double dt, int s)
     h->g_dt = dt;
     h->g_iu = iu0;
     h->g_period = period;
+    h->g_seq = seq;
     h->g_evals = ev;
     h->g_launches = nl;
     return true;
@@ -1345,7 +1360,7 @@ int devloop(pf_handle *h, int integ, double t_end, const pf_tol *tol, const pf_s
     }
     DevCtl *dctl = (DevCtl *)h->dl_ctl;
     st = PF_OK;
-    if (cudaMemsetAsync(h->dflag, 0, sizeof(int), h->stream) != cudaSuccess ||
+    if (cudaMemsetAsync(h->dflag, 0, PF_FLAG_BYTES, h->stream) != cudaSuccess ||
         cudaMemcpyAsync(dctl, &c, sizeof(c), cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
         st = PF_EDEVICE;
     long long prev_attempts = -1;
@@ -1426,12 +1441,16 @@ int step_loop(pf_handle *h, int integ, double t_end, const pf_tol *tol, const pf
         nfix = (long long)ceil((t_end - t0) / dt - 1e-9);
         if (nfix < 1) nfix = 1;
     }
-    if (cudaMemsetAsync(h->dflag, 0, sizeof(int), h->stream) != cudaSuccess) return PF_EDEVICE;
+    if (cudaMemsetAsync(h->dflag, 0, PF_FLAG_BYTES, h->stream) != cudaSuccess) return PF_EDEVICE;
     // reuse of F(u^{n+1}): adaptive RKL steps in dense storage only
     h->reuse_on = (o->flags & PF_STEP_REUSE_RHS) && adaptive && sts && !h->masked;
     if (!h->reuse_on) h->rhs_valid = false;
     const bool graphs = !adaptive && h->stream != nullptr && !h->prof_on && !(o->flags & PF_STEP_NO_GRAPH) &&
                         o->max_attempts == 0 && o->trace_cap == 0;
+    // fixed steps: the buffer holding u^n after each step, so that a failure
+    // found at the end of the call can be traced back to the last good step
+    const int iu0 = h->iu;
+    std::vector<signed char> iu_hist;
     while (h->t < t_end) {
         if (o->max_attempts > 0 && attempts >= o->max_attempts) break;
         // replay whole groups of full fixed steps from a CUDA graph
@@ -1443,6 +1462,8 @@ int step_loop(pf_handle *h, int integ, double t_end, const pf_tol *tol, const pf
                 for (long long r = 0; r < groups; ++r)
                     if (cudaGraphLaunch(h->gexec, h->stream) != cudaSuccess) { status = PF_EDEVICE; break; }
                 if (status) break;
+                for (long long r = 0; r < groups; ++r)
+                    for (int b : h->g_seq) iu_hist.push_back((signed char)b);
                 kfix += groups * h->g_period;
                 attempts += groups * h->g_period;
                 acc_n += groups * h->g_period;
@@ -1498,7 +1519,11 @@ int step_loop(pf_handle *h, int integ, double t_end, const pf_tol *tol, const pf
         elast = err;
         if (acc) {
             h->iu = cand;
-            if (!adaptive) { kfix++; h->t = last ? t_end : t0 + (double)kfix * dt; }
+            if (!adaptive) {
+                kfix++;
+                h->t = last ? t_end : t0 + (double)kfix * dt;
+                iu_hist.push_back((signed char)cand);
+            }
             else h->t = last ? t_end : h->t + hs;
             acc_n++;
             if (h->reuse_on && h->rhs_pending >= 0) {
@@ -1512,7 +1537,21 @@ int step_loop(pf_handle *h, int integ, double t_end, const pf_tol *tol, const pf
             if (rej_n > 100000) { status = PF_EUNSTABLE; break; }
         }
     }
-    if (status == PF_OK) status = check_flag(h);
+    if (status == PF_OK) {
+        int failed = 0;
+        status = check_flag(h, &failed);
+        if (status != PF_OK && !adaptive) {
+            // a pass of fixed step `failed` (1-based) raised a flag and every
+            // later pass did nothing: return the state after the last good
+            // step, which that step's passes read but did not overwrite
+            const long long good = failed > 0 ? failed - 1 : 0;
+            if (good <= (long long)iu_hist.size()) {
+                h->iu = good > 0 ? iu_hist[good - 1] : iu0;
+                h->t = good >= nfix ? t_end : t0 + (double)good * dt;
+                acc_n = good;
+            }
+        }
+    }
     if (adaptive) h->dt_next = dt;
     if (o->trace_len) *o->trace_len = ntr;
     if (stats) {
@@ -1672,7 +1711,7 @@ double time_rkl2_pass(pf_handle *h, bool use_tma, int reps)
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    cudaMemsetAsync(h->dflag, 0, sizeof(int), h->stream);
+    cudaMemsetAsync(h->dflag, 0, PF_FLAG_BYTES, h->stream);
     h->tma = keep;
     return ms;
 }
@@ -1801,7 +1840,7 @@ int pf_create(const pf_params *p, void *cuda_stream, pf_handle **out)
     ok = ok && dmalloc(h, &h->part_cnt, sizeof(long long) * h->grid);
     ok = ok && dmalloc(h, &h->dres, sizeof(double));
     ok = ok && dmalloc(h, &h->dcnt, sizeof(long long));
-    ok = ok && dmalloc(h, &h->dflag, sizeof(int));
+    ok = ok && dmalloc(h, &h->dflag, PF_FLAG_BYTES);
     ok = ok && dmalloc(h, &h->tot_sum, sizeof(double) * h->tot_blocks * NP);
     ok = ok && dmalloc(h, &h->tot_max, sizeof(double) * h->tot_blocks * NP);
     if (!ok) { cudaGetLastError(); free_all(h); delete h; return PF_ENOMEM; }
@@ -1819,7 +1858,7 @@ int pf_create(const pf_params *p, void *cuda_stream, pf_handle **out)
     st |= cudaMemcpyAsync(h->dAB64, h->A.data(), sizeof(double) * N * N, cudaMemcpyHostToDevice, h->stream);
     st |= cudaMemcpyAsync(h->dAB64 + (size_t)N * N, h->B.data(), sizeof(double) * N * N, cudaMemcpyHostToDevice,
                           h->stream);
-    st |= cudaMemsetAsync(h->dflag, 0, sizeof(int), h->stream);
+    st |= cudaMemsetAsync(h->dflag, 0, PF_FLAG_BYTES, h->stream);
     if (h->masked)
         for (int k = 0; k < NBUF; ++k)
             st |= cudaMemsetAsync(mask_plane(h, h->buf[k]), 0xff, sizeof(unsigned) * (size_t)h->Vs * h->nw,
@@ -1995,7 +2034,7 @@ int pf_rhs(pf_handle *h, double *rhs_phi, double *rhs_c, unsigned char *nz, int 
     int st;
     if ((st = ensure_staging(h))) return st;
     if (nz && !h->dnz && !dmalloc(h, &h->dnz, h->V)) return PF_ENOMEM;
-    if (cudaMemsetAsync(h->dflag, 0, sizeof(int), h->stream) != cudaSuccess) return PF_EDEVICE;
+    if (cudaMemsetAsync(h->dflag, 0, PF_FLAG_BYTES, h->stream) != cudaSuccess) return PF_EDEVICE;
     st = (h->prec == 64) ? rhs_t<double>(h, nz ? h->dnz : nullptr) : rhs_t<float>(h, nz ? h->dnz : nullptr);
     if (st) return st;
     const cudaMemcpyKind kind = ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;

@@ -29,7 +29,8 @@
 namespace pfk {
 
 enum { BC_PERIODIC = 0, BC_NEUMANN = 1, BC_DIRICHLET = 2 };
-constexpr int MAXACT = 12;      // nontrivial phases per cell handled by the list
+constexpr int MAXACT = 12;      // nontrivial phases per cell in the fast (shared-memory) list
+constexpr int WIDEACT = 64;     // ... in the per-thread fallback list of crowded cells
 constexpr int TX = 32, TY = 8;  // cells per block: 32 (x) by 8 (y), one z plane
 constexpr int BLOCK = TX * TY;
 
@@ -91,7 +92,8 @@ struct Pass {
     long long *part_cnt; // per-block partial DoF counts
     double *rhs_pm;      // MODE_RHS: FP64 output, field f at rhs_pm + f * V
     unsigned char *nz_out; // MODE_RHS: N_z per cell (may be null)
-    int *flag;           // device status flags
+    int *flag;           // device status words (see raise_flag)
+    int count_step;      // this pass completes a fixed step: count it (see count_step_done)
     // Occupancy masks (masked storage, FP32 fast path, N <= 32): bit a of a
     // cell's word is set where phase a may be nonzero; every entry whose bit
     // is clear holds zero.  Null: dense pass.
@@ -100,7 +102,44 @@ struct Pass {
 };
 
 enum { MODE_RHS = 0, MODE_STAGE = 1, MODE_ERR = 2 };
-enum { FLAG_SIMPLEX = 1, FLAG_NZ_OVERFLOW = 2 };
+
+// Device status words behind Pass::flag (four ints, cleared by the engine at
+// the start of every pf_step / pf_rhs call):
+//   [0]  FLAG_* bits raised by any pass of the call;
+//   [1]  fixed steps completed so far in the call (counted by the last pass
+//        of every fixed step, see count_step_done);
+//   [2]  blocks of the current counting pass that have finished;
+//   [3]  1 + [1] at the moment the first flag was raised (0: none), i.e. the
+//        number of the step in which the failure happened.
+// A pass that starts while [0] is non-zero does nothing, so once a step has
+// failed no state buffer is written any more: u^n of the failed step, which
+// no pass of a step overwrites, stays intact for the engine to return.
+enum { FLAG_SIMPLEX = 1, FLAG_NZ_OVERFLOW = 2, FLAG_TIMEOUT = 4, FLAG_NONFINITE = 8 };
+
+__device__ __forceinline__ bool pass_skipped(const int *flag) { return *(const volatile int *)flag != 0; }
+
+__device__ __forceinline__ void raise_flag(int *flag, int bits)
+{
+    atomicOr(flag, bits);
+    atomicCAS(flag + 3, 0, 1 + *(volatile int *)(flag + 1));
+}
+
+// End of a pass that completes a fixed step (every thread of the block calls
+// it): the last block of the grid to finish counts the step.  A flag raised
+// during the pass is recorded (raise_flag) before the raising block finishes,
+// hence before the count moves on.
+__device__ __forceinline__ void count_step_done(int *flag)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned nb = gridDim.x * gridDim.y * gridDim.z;
+        if (atomicAdd((unsigned *)(flag + 2), 1u) == nb - 1u) {
+            atomicExch(flag + 2, 0);
+            atomicAdd(flag + 1, 1);
+        }
+    }
+}
 
 template <typename T>
 __device__ __forceinline__ T ldg(const T *p) { return __ldg(p); }
@@ -214,17 +253,53 @@ struct Smem {
     T nv[NV][BLOCK];         // stage values of the current chunk
 };
 
-template <typename T, int DIM, int KC, unsigned SIG>
-__device__ __forceinline__ void cell_body(const Geom &g, const Pass<T> &P, const T *__restrict__ tabA,
+// Where the generic body keeps a cell's list of nontrivial phases.
+// SlotList: the thread's slots of the block's shared memory (MAXACT entries,
+// plus a chunk of NV stage values).  WideList: a per-thread array in local
+// memory (WIDEACT entries, no stage-value chunk: the stage values go through
+// the output buffer), the fallback for cells where more than MAXACT phases
+// are nontrivial.
+template <typename T>
+struct SlotList {
+    static constexpr int CAP = MAXACT;
+    static constexpr int NV = Smem<T>::NV;
+    Smem<T> *S;
+    int tid;
+    __device__ __forceinline__ unsigned char &id(int k) { return S->id[k][tid]; }
+    __device__ __forceinline__ T &lap(int k) { return S->lap[k][tid]; }
+    __device__ __forceinline__ T &cen(int k) { return S->cen[k][tid]; }
+    __device__ __forceinline__ T &dl(int k) { return S->dl[k][tid]; }
+    __device__ __forceinline__ T &nv(int a) { return S->nv[a][tid]; }
+};
+
+template <typename T>
+struct WideList {
+    static constexpr int CAP = WIDEACT;
+    static constexpr int NV = 0;
+    unsigned char id_[WIDEACT];
+    T lap_[WIDEACT], cen_[WIDEACT], dl_[WIDEACT];
+    __device__ __forceinline__ unsigned char &id(int k) { return id_[k]; }
+    __device__ __forceinline__ T &lap(int k) { return lap_[k]; }
+    __device__ __forceinline__ T &cen(int k) { return cen_[k]; }
+    __device__ __forceinline__ T &dl(int k) { return dl_[k]; }
+    __device__ __forceinline__ T &nv(int) { return lap_[0]; }   // never used (NV = 0)
+};
+
+// The generic per-cell body: RHS, stage combination, projection, first-stage
+// fix, SSP(10)4 accumulators and error partials of one cell (x, y, z), with
+// every option read from P at run time (SIG_GENERIC) or fixed by SIG.
+// Returns false, having written nothing and accumulated nothing, when more
+// than LST::CAP phases are nontrivial at the cell (the caller then takes the
+// wide path).
+template <typename T, int DIM, int KC, unsigned SIG, class LST>
+__device__ __forceinline__ bool cell_core(const Geom &g, const Pass<T> &P, LST &S, const T *__restrict__ tabA,
                                           const T *__restrict__ tabB, const T *__restrict__ tabL,
-                                          const signed char *__restrict__ ptype)
+                                          const signed char *__restrict__ ptype, int x, int y, int z,
+                                          double &esum, long long &ecnt)
 {
     constexpr int NFACE = 2 * DIM;
     constexpr bool GEN = (SIG & SIG_GENERIC) != 0;
-    constexpr int NV = Smem<T>::NV;
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    Smem<T> &S = *reinterpret_cast<Smem<T> *>(smem_raw);
-    const int tid = threadIdx.x;
+    constexpr int NV = LST::NV;
 
     // pass options: compile-time for the specialised signatures, run time for GENERIC
     const int mode = GEN ? P.mode : ((SIG & SIG_ERR) ? MODE_ERR : (SIG & SIG_RHS) ? MODE_RHS : MODE_STAGE);
@@ -240,318 +315,371 @@ __device__ __forceinline__ void cell_body(const Geom &g, const Pass<T> &P, const
     const int N = g.N;
     const int K = KC;
     const long long Vs = g.Vs;
+    const long long i = ((long long)z * g.ny + y) * g.nx + x;
+    const T dx2 = (T)g.dx2;
+
+    long long off[6];
+    int ghost[6];
+    face_offsets(g, x, y, z, off, ghost);
+    // a zero-gradient ghost of phi is the cell itself: offset 0
+#pragma unroll
+    for (int f = 0; f < 6; ++f) if (ghost[f]) off[f] = 0;
+
+    // ---- concentration at the cell and its face neighbours -----------------
+    T cc = (T)0, num_c = (T)0, den_c = (T)0, num_n[NFACE], den_n[NFACE], mf[NFACE];
+#pragma unroll
+    for (int f = 0; f < NFACE; ++f) { num_n[f] = (T)0; den_n[f] = (T)0; mf[f] = (T)0; }
+    if (K) {
+        const T *cf = P.in + (long long)N * Vs + i;
+        cc = ldg(cf);
+        num_c = cc;
+#pragma unroll
+        for (int f = 0; f < NFACE; ++f) {
+            T v = ldg(cf + off[f]);
+            if (ghost[f] && g.bc_c[f] == BC_DIRICHLET) v = (T)2 * (T)g.cdir[f] - cc;
+            num_n[f] = v;
+        }
+    }
+
+    // ---- pass 1: activity, Laplacian, chemistry sums (Sec. 2-3) ------------
+    int nz = 0;
+    {
+        const T *fp = P.in + i;
+#pragma unroll 4
+        for (int a = 0; a < N; ++a, fp += Vs) {
+            const T v0 = ldg(fp);
+            T nb[NFACE];
+#pragma unroll
+            for (int f = 0; f < NFACE; ++f) nb[f] = ldg(fp + off[f]);
+            T mx = v0, mn = v0;
+#pragma unroll
+            for (int f = 0; f < NFACE; ++f) {
+                mx = nb[f] > mx ? nb[f] : mx;
+                mn = nb[f] < mn ? nb[f] : mn;
+            }
+            if (K) {
+                const int t = ptype[a];
+                const T c0t = (T)g.c0[t], ikt = (T)g.invk[t], dkt = (T)g.Dk[t];
+                num_c = num_c - v0 * c0t;
+                den_c = den_c + v0 * ikt;
+#pragma unroll
+                for (int f = 0; f < NFACE; ++f) {
+                    num_n[f] = num_n[f] - nb[f] * c0t;
+                    den_n[f] = den_n[f] + nb[f] * ikt;
+                    mf[f] = mf[f] + dkt * ((T)0.5 * (v0 + nb[f]));
+                }
+            }
+            if (mx > (T)0 && mn < (T)1) {
+                T l = (T)0;
+#pragma unroll
+                for (int f = 0; f < NFACE; ++f) l = l + (nb[f] - v0);
+                if (nz < LST::CAP) {
+                    S.id(nz) = (unsigned char)a;
+                    S.lap(nz) = l / dx2;
+                    S.cen(nz) = v0;
+                }
+                nz++;
+            }
+        }
+    }
+    if (nz > LST::CAP) return false;
+
+    // ---- grand potential and concentration RHS -----------------------------
+    T mu = (T)0, rc = (T)0;
+    if (K) {
+        mu = num_c / den_c;
+        T acc = (T)0;
+#pragma unroll
+        for (int f = 0; f < NFACE; ++f) {
+            const T mun = num_n[f] / den_n[f];
+            acc = acc + mf[f] * (mun - mu);
+        }
+        rc = acc / dx2;
+    }
+
+    // ---- variational derivative and pairwise sum over the list -------------
+    for (int k = 0; k < nz; ++k) {
+        const int a = S.id(k);
+        const T *Aa = tabA + a * N, *Ba = tabB + a * N;
+        T d = (T)0;
+        for (int k2 = 0; k2 < nz; ++k2) {
+            if (k2 == k) continue;
+            const int b = S.id(k2);
+            d = d + (ldg(Aa + b) * S.lap(k2) + ldg(Ba + b) * S.cen(k2));
+        }
+        T psi = (T)0;
+        if (K) {
+            const int t = ptype[a];
+            psi = -(mu * mu) / ((T)2 * (T)g.k[t]) - mu * (T)g.c0[t];
+        }
+        S.dl(k) = d + psi;
+    }
+    for (int k = 0; k < nz; ++k) {
+        T rk = (T)0;
+        if (nz > 1) {
+            const int a = S.id(k);
+            const T *La = tabL + a * N;
+            const T dk = S.dl(k);
+            T s = (T)0;
+            for (int k2 = 0; k2 < nz; ++k2) {
+                if (k2 == k) continue;
+                s = s + ldg(La + S.id(k2)) * (dk - S.dl(k2));
+            }
+            rk = -(s / (T)nz);
+        }
+        S.lap(k) = rk;                  // the list now holds the RHS
+    }
+
+    // list cursor: phases are visited in ascending order
+    int kk = 0;
+    int curid = nz > 0 ? S.id(0) : -1;
+#define PF_NEXT_RHS(a_, r_)                                          \
+    if ((a_) == curid) {                                             \
+        r_ = S.lap(kk);                                              \
+        kk++;                                                        \
+        curid = kk < nz ? S.id(kk) : -1;                             \
+    }
+
+    if (mode == MODE_RHS) {
+        // ---- RHS only (pf_rhs) ---------------------------------------------
+        for (int a = 0; a < N; ++a) {
+            T r = (T)0;
+            PF_NEXT_RHS(a, r)
+            P.rhs_pm[(long long)a * g.V + i] = (double)r;
+        }
+        if (K) P.rhs_pm[(long long)N * g.V + i] = (double)rc;
+        if (P.nz_out) P.nz_out[i] = (unsigned char)nz;
+    } else if (mode == MODE_ERR) {
+        // ---- STS error sweep (Sec. 3.3): in = u^{n+1}, p0 = u^n, r0in = F^n
+        const T dt = (T)P.dt;
+        const T rph = (T)P.r_phi, aph = (T)P.a_phi;
+        int nc = 0;
+        long long o = i;
+#pragma unroll 4
+        for (int a = 0; a < N; ++a, o += Vs) {
+            T r1 = (T)0;
+            PF_NEXT_RHS(a, r1)
+            if (P.r0out) P.r0out[o] = r1;      // F(u^{n+1}) kept for reuse
+            const T un = ldg(P.p0 + o), un1 = ldg(P.in + o), rn = ldg(P.r0in + o);
+            const T sr = rn + r1;
+            T e = ((T)12 * (un - un1) + ((T)6 * dt) * sr) / (T)15;
+            const T trial = un + (dt / (T)2) * sr;
+            if (trial < (T)0 || trial > (T)1) e = (T)0;
+            if (e != (T)0) {
+                const T au = tabs(un), av = tabs(un1);
+                const T w = rph * (au > av ? au : av) + aph;
+                const T q = e / w;
+                esum += (double)(q * q);
+                nc++;
+            }
+        }
+        ecnt += (nc > 0 ? nc : 2);
+        if (K) {
+            const long long oc = (long long)N * Vs + i;
+            if (P.r0out) P.r0out[oc] = rc;
+            const T un = ldg(P.p0 + oc), un1 = ldg(P.in + oc), rn = ldg(P.r0in + oc);
+            const T sr = rn + rc;
+            const T e = ((T)12 * (un - un1) + ((T)6 * dt) * sr) / (T)15;
+            const T au = tabs(un + (T)g.cref), av = tabs(un1 + (T)g.cref);
+            const T w = (T)P.r_c * (au > av ? au : av) + (T)P.a_c;
+            const T q = e / w;
+            esum += (double)(q * q);
+            ecnt += 1;
+        }
+    } else {
+        // ---- stage combination (Eq. sts / Alg. ssp2 / SSP(10)4) -------------
+        const T a0c = (T)P.a0, a2c = (T)P.a2, b1c = (T)P.b1, b0c = (T)P.b0, bzc = (T)P.bz;
+        const bool chunked = N > NV;
+        bool changed = false;
+        T best = (T)-1;
+        int bestid = -1;
+        T ssum = (T)0;
+        for (int a0 = 0; a0 < N; a0 += (NV > 0 ? NV : N)) {
+            const int an = NV > 0 ? ((N - a0) < NV ? (N - a0) : NV) : N;
+            long long o = (long long)a0 * Vs + i;
+#pragma unroll 4
+            for (int aa = 0; aa < an; ++aa, o += Vs) {
+                const int a = a0 + aa;
+                T r = (T)0;
+                PF_NEXT_RHS(a, r)
+                const T v = ldg(P.in + o);
+                T acc = v;
+                if (has_p0) acc = acc + a0c * (ldg(P.p0 + o) - v);
+                if (has_p2) acc = acc + a2c * (ldg(P.p2 + o) - v);
+                acc = acc + b1c * r;
+                if (has_r0in) acc = acc + b0c * ldg(P.r0in + o);
+                if (has_r0out) P.r0out[o] = r;      // replaced below where S acts (RKL2)
+                if (has_z) P.zout[o] = P.zin[o] + bzc * r;   // zin may alias zout
+                if (project) {
+                    // S step 1: clamp negatives; step 2 candidate: largest >= 1
+                    if (acc < (T)0) { acc = (T)0; changed = true; }
+                    if (acc >= (T)1 && acc > best) { best = acc; bestid = a; }
+                }
+                if (chunked) P.out[o] = acc;
+                else S.nv(aa) = acc;
+            }
+        }
+        // S step 2 (the >= 1 rule) and the sum for step 3, ascending order
+        if (project) {
+            if (bestid >= 0) {
+                // the winner becomes 1, the others 0; the sum is then exactly 1
+                if (!chunked) {
+                    for (int aa = 0; aa < N; ++aa) {
+                        const T w = (aa == bestid) ? (T)1 : (T)0;
+                        if (S.nv(aa) != w) changed = true;
+                    }
+                } else {
+                    changed = true;
+                }
+                ssum = (T)1;
+            } else if (!chunked) {
+                for (int aa = 0; aa < N; ++aa) ssum = ssum + S.nv(aa);
+            } else {
+                for (int a = 0; a < N; ++a) ssum = ssum + P.out[(long long)a * Vs + i];
+            }
+            if (!(ssum > (T)0)) raise_flag(P.flag, FLAG_SIMPLEX);
+        }
+        const bool fix = has_r0out && P.fix_first && changed;
+        // store pass: S step 3, first-stage fix, embedded error, SSP(10)4 mid combination
+        int nc = 0;
+        {
+            long long o = i;
+#pragma unroll 4
+            for (int a = 0; a < N; ++a, o += Vs) {
+                T w = chunked ? P.out[o] : S.nv(a);
+                if (project) {
+                    if (bestid >= 0) w = (a == bestid) ? (T)1 : (T)0;
+                    else if (ssum > (T)0) w = w / ssum;
+                }
+                if (fix) P.r0out[o] = (w - ldg(P.in + o)) / b1c;
+                if (emb) {
+                    const T zv = P.zout[o];
+                    T e = w - zv;
+                    if (zv < (T)0 || zv > (T)1) e = (T)0;
+                    if (e != (T)0) {
+                        const T au = tabs(ldg(P.uw + o)), av = tabs(w);
+                        const T wt = (T)P.r_phi * (au > av ? au : av) + (T)P.a_phi;
+                        const T q = e / wt;
+                        esum += (double)(q * q);
+                        nc++;
+                    }
+                }
+                if (has_out2) {
+                    const T q2 = w + (T)P.m25 * (ldg(P.q2in + o) - w);
+                    P.out2[o] = q2;
+                    P.out[o] = w + (T)P.m15 * (q2 - w);
+                } else {
+                    P.out[o] = w;
+                }
+            }
+        }
+        if (emb) ecnt += (nc > 0 ? nc : 2);
+        // concentration field (no projection)
+        if (K) {
+            const long long o = (long long)N * Vs + i;
+            // the small increments are summed first: c is rounded once per stage
+            T d = b1c * rc;
+            if (has_r0in) d = d + b0c * ldg(P.r0in + o);
+            if (has_p0) d = d + a0c * (ldg(P.p0 + o) - cc);
+            if (has_p2) d = d + a2c * (ldg(P.p2 + o) - cc);
+            const T acc = cc + d;
+            if (!isfinite(acc)) raise_flag(P.flag, FLAG_NONFINITE);
+            if (has_r0out) P.r0out[o] = rc;
+            if (has_z) {
+                const T zv = P.zin[o] + bzc * rc;
+                P.zout[o] = zv;
+                if (emb) {
+                    const T e = acc - zv;
+                    const T au = tabs(ldg(P.uw + o) + (T)g.cref), av = tabs(acc + (T)g.cref);
+                    const T wt = (T)P.r_c * (au > av ? au : av) + (T)P.a_c;
+                    const T q = e / wt;
+                    esum += (double)(q * q);
+                    ecnt += 1;
+                }
+            }
+            if (has_out2) {
+                const T q2 = acc + (T)P.m25 * (ldg(P.q2in + o) - acc);
+                P.out2[o] = q2;
+                P.out[o] = acc + (T)P.m15 * (q2 - acc);
+            } else {
+                P.out[o] = acc;
+            }
+        }
+    }
+#undef PF_NEXT_RHS
+    return true;
+}
+
+// Occupancy words (masked storage) of the cell's outputs after the wide path
+// rewrote every phase of it: bit set where the value is nonzero.
+__device__ __forceinline__ void wide_masks(const Geom &g, const Pass<float> &P, long long i)
+{
+    const int nwr = (g.N + 31) / 32;
+    for (int w = 0; w < nwr; ++w) {
+        unsigned mo = 0u, mr = 0u;
+        for (int b = 0; b < 32 && 32 * w + b < g.N; ++b) {
+            const long long o = (long long)(32 * w + b) * g.Vs + i;
+            if (P.out[o] != 0.0f) mo |= 1u << b;
+            if (P.r0out && P.r0out[o] != 0.0f) mr |= 1u << b;
+        }
+        if (P.m_out) P.m_out[(long long)w * g.Vs + i] = mo;
+        if (P.m_r0out) P.m_r0out[(long long)w * g.Vs + i] = mr;
+    }
+}
+__device__ __forceinline__ void wide_masks(const Geom &, const Pass<double> &, long long) {}
+
+// A cell where more than MAXACT phases are nontrivial (phases crowding at
+// junctions and particle fringes; Sec. 3.1 sets no limit): the whole cell is
+// recomputed by the generic body with a WIDEACT-entry list in local memory,
+// rewriting every output of the pass for this cell (and, in masked storage,
+// its occupancy words); its error-norm contribution is added to esum/ecnt,
+// which the caller has reset.  Beyond WIDEACT phases the pass raises
+// FLAG_NZ_OVERFLOW.  Kept out of line: its local array is touched only by
+// the rare threads that take it.
+template <typename T, int DIM, int KC>
+__device__ __noinline__ void wide_cell(const Geom *g, const Pass<T> *P, const T *tabA, const T *tabB, const T *tabL,
+                                       const signed char *ptype, int x, int y, int z, double *esum, long long *ecnt)
+{
+    WideList<T> L;
+    double es = 0.0;
+    long long ec = 0;
+    if (!cell_core<T, DIM, KC, SIG_GENERIC, WideList<T>>(*g, *P, L, tabA, tabB, tabL, ptype, x, y, z, es, ec)) {
+        raise_flag(P->flag, FLAG_NZ_OVERFLOW);
+        return;
+    }
+    if (P->mode == MODE_STAGE) wide_masks(*g, *P, ((long long)z * g->ny + y) * g->nx + x);
+    *esum += es;
+    *ecnt += ec;
+}
+
+template <typename T, int DIM, int KC, unsigned SIG>
+__device__ __forceinline__ void cell_body(const Geom &g, const Pass<T> &P, const T *__restrict__ tabA,
+                                          const T *__restrict__ tabB, const T *__restrict__ tabL,
+                                          const signed char *__restrict__ ptype)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    if (pass_skipped(P.flag)) return;
+    SlotList<T> S{reinterpret_cast<Smem<T> *>(smem_raw), (int)threadIdx.x};
+    const int tid = threadIdx.x;
     const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
     const int x = blockIdx.x * TX + (tid % TX);
     const int y = blockIdx.y * TY + (tid / TX);
     const int z = blockIdx.z;
-    const bool valid = x < g.nx && y < g.ny;
-    const long long i = valid ? ((long long)z * g.ny + y) * g.nx + x : 0;
-    const T dx2 = (T)g.dx2;
-
     double esum = 0.0;
     long long ecnt = 0;
-
-    if (valid) {
-        long long off[6];
-        int ghost[6];
-        face_offsets(g, x, y, z, off, ghost);
-        // a zero-gradient ghost of phi is the cell itself: offset 0
-#pragma unroll
-        for (int f = 0; f < 6; ++f) if (ghost[f]) off[f] = 0;
-
-        // ---- concentration at the cell and its face neighbours -------------
-        T cc = (T)0, num_c = (T)0, den_c = (T)0, num_n[NFACE], den_n[NFACE], mf[NFACE];
-#pragma unroll
-        for (int f = 0; f < NFACE; ++f) { num_n[f] = (T)0; den_n[f] = (T)0; mf[f] = (T)0; }
-        if (K) {
-            const T *cf = P.in + (long long)N * Vs + i;
-            cc = ldg(cf);
-            num_c = cc;
-#pragma unroll
-            for (int f = 0; f < NFACE; ++f) {
-                T v = ldg(cf + off[f]);
-                if (ghost[f] && g.bc_c[f] == BC_DIRICHLET) v = (T)2 * (T)g.cdir[f] - cc;
-                num_n[f] = v;
-            }
-        }
-
-        // ---- pass 1: activity, Laplacian, chemistry sums (Sec. 2-3) --------
-        int nz = 0;
-        {
-            const T *fp = P.in + i;
-#pragma unroll 4
-            for (int a = 0; a < N; ++a, fp += Vs) {
-                const T v0 = ldg(fp);
-                T nb[NFACE];
-#pragma unroll
-                for (int f = 0; f < NFACE; ++f) nb[f] = ldg(fp + off[f]);
-                T mx = v0, mn = v0;
-#pragma unroll
-                for (int f = 0; f < NFACE; ++f) {
-                    mx = nb[f] > mx ? nb[f] : mx;
-                    mn = nb[f] < mn ? nb[f] : mn;
-                }
-                if (K) {
-                    const int t = ptype[a];
-                    const T c0t = (T)g.c0[t], ikt = (T)g.invk[t], dkt = (T)g.Dk[t];
-                    num_c = num_c - v0 * c0t;
-                    den_c = den_c + v0 * ikt;
-#pragma unroll
-                    for (int f = 0; f < NFACE; ++f) {
-                        num_n[f] = num_n[f] - nb[f] * c0t;
-                        den_n[f] = den_n[f] + nb[f] * ikt;
-                        mf[f] = mf[f] + dkt * ((T)0.5 * (v0 + nb[f]));
-                    }
-                }
-                if (mx > (T)0 && mn < (T)1) {
-                    T l = (T)0;
-#pragma unroll
-                    for (int f = 0; f < NFACE; ++f) l = l + (nb[f] - v0);
-                    if (nz < MAXACT) {
-                        S.id[nz][tid] = (unsigned char)a;
-                        S.lap[nz][tid] = l / dx2;
-                        S.cen[nz][tid] = v0;
-                    }
-                    nz++;
-                }
-            }
-        }
-        if (nz > MAXACT) {
-            atomicOr(P.flag, FLAG_NZ_OVERFLOW);
-            nz = MAXACT;
-        }
-
-        // ---- grand potential and concentration RHS -------------------------
-        T mu = (T)0, rc = (T)0;
-        if (K) {
-            mu = num_c / den_c;
-            T acc = (T)0;
-#pragma unroll
-            for (int f = 0; f < NFACE; ++f) {
-                const T mun = num_n[f] / den_n[f];
-                acc = acc + mf[f] * (mun - mu);
-            }
-            rc = acc / dx2;
-        }
-
-        // ---- variational derivative and pairwise sum over the list ---------
-        for (int k = 0; k < nz; ++k) {
-            const int a = S.id[k][tid];
-            const T *Aa = tabA + a * N, *Ba = tabB + a * N;
-            T d = (T)0;
-            for (int k2 = 0; k2 < nz; ++k2) {
-                if (k2 == k) continue;
-                const int b = S.id[k2][tid];
-                d = d + (ldg(Aa + b) * S.lap[k2][tid] + ldg(Ba + b) * S.cen[k2][tid]);
-            }
-            T psi = (T)0;
-            if (K) {
-                const int t = ptype[a];
-                psi = -(mu * mu) / ((T)2 * (T)g.k[t]) - mu * (T)g.c0[t];
-            }
-            S.dl[k][tid] = d + psi;
-        }
-        for (int k = 0; k < nz; ++k) {
-            T rk = (T)0;
-            if (nz > 1) {
-                const int a = S.id[k][tid];
-                const T *La = tabL + a * N;
-                const T dk = S.dl[k][tid];
-                T s = (T)0;
-                for (int k2 = 0; k2 < nz; ++k2) {
-                    if (k2 == k) continue;
-                    s = s + ldg(La + S.id[k2][tid]) * (dk - S.dl[k2][tid]);
-                }
-                rk = -(s / (T)nz);
-            }
-            S.lap[k][tid] = rk;                  // the list now holds the RHS
-        }
-
-        // list cursor: phases are visited in ascending order
-        int kk = 0;
-        int curid = nz > 0 ? S.id[0][tid] : -1;
-#define PF_NEXT_RHS(a_, r_)                                          \
-    if ((a_) == curid) {                                             \
-        r_ = S.lap[kk][tid];                                         \
-        kk++;                                                        \
-        curid = kk < nz ? S.id[kk][tid] : -1;                        \
+    if (x < g.nx && y < g.ny) {
+        if (!cell_core<T, DIM, KC, SIG, SlotList<T>>(g, P, S, tabA, tabB, tabL, ptype, x, y, z, esum, ecnt))
+            wide_cell<T, DIM, KC>(&g, &P, tabA, tabB, tabL, ptype, x, y, z, &esum, &ecnt);
     }
-
-        if (mode == MODE_RHS) {
-            // ---- RHS only (pf_rhs) -------------------------------------------
-            for (int a = 0; a < N; ++a) {
-                T r = (T)0;
-                PF_NEXT_RHS(a, r)
-                P.rhs_pm[(long long)a * g.V + i] = (double)r;
-            }
-            if (K) P.rhs_pm[(long long)N * g.V + i] = (double)rc;
-            if (P.nz_out) P.nz_out[i] = (unsigned char)nz;
-        } else if (mode == MODE_ERR) {
-            // ---- STS error sweep (Sec. 3.3): in = u^{n+1}, p0 = u^n, r0in = F^n
-            const T dt = (T)P.dt;
-            const T rph = (T)P.r_phi, aph = (T)P.a_phi;
-            int nc = 0;
-            long long o = i;
-#pragma unroll 4
-            for (int a = 0; a < N; ++a, o += Vs) {
-                T r1 = (T)0;
-                PF_NEXT_RHS(a, r1)
-                if (P.r0out) P.r0out[o] = r1;      // F(u^{n+1}) kept for reuse
-                const T un = ldg(P.p0 + o), un1 = ldg(P.in + o), rn = ldg(P.r0in + o);
-                const T sr = rn + r1;
-                T e = ((T)12 * (un - un1) + ((T)6 * dt) * sr) / (T)15;
-                const T trial = un + (dt / (T)2) * sr;
-                if (trial < (T)0 || trial > (T)1) e = (T)0;
-                if (e != (T)0) {
-                    const T au = tabs(un), av = tabs(un1);
-                    const T w = rph * (au > av ? au : av) + aph;
-                    const T q = e / w;
-                    esum += (double)(q * q);
-                    nc++;
-                }
-            }
-            ecnt += (nc > 0 ? nc : 2);
-            if (K) {
-                const long long oc = (long long)N * Vs + i;
-                if (P.r0out) P.r0out[oc] = rc;
-                const T un = ldg(P.p0 + oc), un1 = ldg(P.in + oc), rn = ldg(P.r0in + oc);
-                const T sr = rn + rc;
-                const T e = ((T)12 * (un - un1) + ((T)6 * dt) * sr) / (T)15;
-                const T au = tabs(un + (T)g.cref), av = tabs(un1 + (T)g.cref);
-                const T w = (T)P.r_c * (au > av ? au : av) + (T)P.a_c;
-                const T q = e / w;
-                esum += (double)(q * q);
-                ecnt += 1;
-            }
-        } else {
-            // ---- stage combination (Eq. sts / Alg. ssp2 / SSP(10)4) ---------
-            const T a0c = (T)P.a0, a2c = (T)P.a2, b1c = (T)P.b1, b0c = (T)P.b0, bzc = (T)P.bz;
-            const bool chunked = N > NV;
-            bool changed = false;
-            T best = (T)-1;
-            int bestid = -1;
-            T ssum = (T)0;
-            for (int a0 = 0; a0 < N; a0 += NV) {
-                const int an = (N - a0) < NV ? (N - a0) : NV;
-                long long o = (long long)a0 * Vs + i;
-#pragma unroll 4
-                for (int aa = 0; aa < an; ++aa, o += Vs) {
-                    const int a = a0 + aa;
-                    T r = (T)0;
-                    PF_NEXT_RHS(a, r)
-                    const T v = ldg(P.in + o);
-                    T acc = v;
-                    if (has_p0) acc = acc + a0c * (ldg(P.p0 + o) - v);
-                    if (has_p2) acc = acc + a2c * (ldg(P.p2 + o) - v);
-                    acc = acc + b1c * r;
-                    if (has_r0in) acc = acc + b0c * ldg(P.r0in + o);
-                    if (has_r0out) P.r0out[o] = r;      // replaced below where S acts (RKL2)
-                    if (has_z) P.zout[o] = P.zin[o] + bzc * r;   // zin may alias zout
-                    if (project) {
-                        // S step 1: clamp negatives; step 2 candidate: largest >= 1
-                        if (acc < (T)0) { acc = (T)0; changed = true; }
-                        if (acc >= (T)1 && acc > best) { best = acc; bestid = a; }
-                    }
-                    if (chunked) P.out[o] = acc;
-                    else S.nv[aa][tid] = acc;
-                }
-            }
-            // S step 2 (the >= 1 rule) and the sum for step 3, ascending order
-            if (project) {
-                if (bestid >= 0) {
-                    // the winner becomes 1, the others 0; the sum is then exactly 1
-                    if (!chunked) {
-                        for (int aa = 0; aa < N; ++aa) {
-                            const T w = (aa == bestid) ? (T)1 : (T)0;
-                            if (S.nv[aa][tid] != w) changed = true;
-                        }
-                    } else {
-                        changed = true;
-                    }
-                    ssum = (T)1;
-                } else if (!chunked) {
-                    for (int aa = 0; aa < N; ++aa) ssum = ssum + S.nv[aa][tid];
-                } else {
-                    for (int a = 0; a < N; ++a) ssum = ssum + P.out[(long long)a * Vs + i];
-                }
-                if (!(ssum > (T)0)) atomicOr(P.flag, FLAG_SIMPLEX);
-            }
-            const bool fix = has_r0out && P.fix_first && changed;
-            // store pass: S step 3, first-stage fix, embedded error, SSP(10)4 mid combination
-            int nc = 0;
-            {
-                long long o = i;
-#pragma unroll 4
-                for (int a = 0; a < N; ++a, o += Vs) {
-                    T w = chunked ? P.out[o] : S.nv[a][tid];
-                    if (project) {
-                        if (bestid >= 0) w = (a == bestid) ? (T)1 : (T)0;
-                        else if (ssum > (T)0) w = w / ssum;
-                    }
-                    if (fix) P.r0out[o] = (w - ldg(P.in + o)) / b1c;
-                    if (emb) {
-                        const T zv = P.zout[o];
-                        T e = w - zv;
-                        if (zv < (T)0 || zv > (T)1) e = (T)0;
-                        if (e != (T)0) {
-                            const T au = tabs(ldg(P.uw + o)), av = tabs(w);
-                            const T wt = (T)P.r_phi * (au > av ? au : av) + (T)P.a_phi;
-                            const T q = e / wt;
-                            esum += (double)(q * q);
-                            nc++;
-                        }
-                    }
-                    if (has_out2) {
-                        const T q2 = w + (T)P.m25 * (ldg(P.q2in + o) - w);
-                        P.out2[o] = q2;
-                        P.out[o] = w + (T)P.m15 * (q2 - w);
-                    } else {
-                        P.out[o] = w;
-                    }
-                }
-            }
-            if (emb) ecnt += (nc > 0 ? nc : 2);
-            // concentration field (no projection)
-            if (K) {
-                const long long o = (long long)N * Vs + i;
-                // the small increments are summed first: c is rounded once per stage
-                T d = b1c * rc;
-                if (has_r0in) d = d + b0c * ldg(P.r0in + o);
-                if (has_p0) d = d + a0c * (ldg(P.p0 + o) - cc);
-                if (has_p2) d = d + a2c * (ldg(P.p2 + o) - cc);
-                const T acc = cc + d;
-                if (has_r0out) P.r0out[o] = rc;
-                if (has_z) {
-                    const T zv = P.zin[o] + bzc * rc;
-                    P.zout[o] = zv;
-                    if (emb) {
-                        const T e = acc - zv;
-                        const T au = tabs(ldg(P.uw + o) + (T)g.cref), av = tabs(acc + (T)g.cref);
-                        const T wt = (T)P.r_c * (au > av ? au : av) + (T)P.a_c;
-                        const T q = e / wt;
-                        esum += (double)(q * q);
-                        ecnt += 1;
-                    }
-                }
-                if (has_out2) {
-                    const T q2 = acc + (T)P.m25 * (ldg(P.q2in + o) - acc);
-                    P.out2[o] = q2;
-                    P.out[o] = acc + (T)P.m15 * (q2 - acc);
-                } else {
-                    P.out[o] = acc;
-                }
-            }
-        }
-#undef PF_NEXT_RHS
-    }
-
-    if (mode == MODE_ERR || emb) block_partials(esum, ecnt, P.part_sum, P.part_cnt, bid);
+    const bool errp = (SIG & SIG_GENERIC) ? (P.mode == MODE_ERR || P.embedded_err != 0) : (SIG & SIG_ERR) != 0;
+    if (errp) block_partials(esum, ecnt, P.part_sum, P.part_cnt, bid);
+    if (P.count_step) count_step_done(P.flag);
 }
 
 template <typename T, int DIM, int KC, unsigned SIG>
 __global__ void __launch_bounds__(BLOCK)
-cell_kernel(const Geom g, const Pass<T> P, const T *__restrict__ tabA, const T *__restrict__ tabB,
-            const T *__restrict__ tabL, const signed char *__restrict__ ptype)
+cell_kernel(const __grid_constant__ Geom g, const __grid_constant__ Pass<T> P, const T *__restrict__ tabA,
+            const T *__restrict__ tabB, const T *__restrict__ tabL, const signed char *__restrict__ ptype)
 {
     cell_body<T, DIM, KC, SIG>(g, P, tabA, tabB, tabL, ptype);
 }
@@ -561,8 +689,8 @@ cell_kernel(const Geom g, const Pass<T> P, const T *__restrict__ tabA, const T *
 // kernel writes before each launch runs.
 template <typename T, int DIM, int KC, unsigned SIG>
 __global__ void __launch_bounds__(BLOCK)
-cell_kernel_d(const Geom g, const Pass<T> *__restrict__ Pd, const T *__restrict__ tabA, const T *__restrict__ tabB,
-              const T *__restrict__ tabL, const signed char *__restrict__ ptype)
+cell_kernel_d(const __grid_constant__ Geom g, const Pass<T> *__restrict__ Pd, const T *__restrict__ tabA,
+              const T *__restrict__ tabB, const T *__restrict__ tabL, const signed char *__restrict__ ptype)
 {
     __shared__ Pass<T> Ps;
     if (threadIdx.x == 0) Ps = *Pd;
@@ -579,7 +707,6 @@ cell_kernel_d(const Geom g, const Pass<T> *__restrict__ Pd, const T *__restrict_
 // ---------------------------------------------------------------------------
 constexpr int TMA_R = 4;
 constexpr unsigned TMA_SPIN = 1u << 22;   // bounded mbarrier polls before giving up
-enum { FLAG_TIMEOUT = 4 };
 
 struct TmaMaps {
     CUtensorMap in3;   // stencil input, box 32 x 8 x 3 planes x 1 field
@@ -705,7 +832,17 @@ struct TmaLoader {
                                          bool hp0, bool hp2, bool hr0)
     {
         const int r = a % TMA_R;
-        if (!mbar_wait(&Q->full[r], (unsigned)((a / TMA_R) & 1))) ok = false;
+        if (ok && !mbar_wait(&Q->full[r], (unsigned)((a / TMA_R) & 1))) ok = false;
+        if (!ok) {
+            // a wait gave up (the pass reports PF_ETIMEOUT): touch no slot
+            // any more; the stencil values come from global memory, the
+            // pointwise ones are zero (the results of this pass are void)
+            v0 = ldg(pin + fo);
+#pragma unroll
+            for (int f = 0; f < 6; ++f) nb[f] = ldg(pin + fo + off[f]);
+            p0v = p2v = r0v = 0.0f;
+            return;
+        }
         v0 = Q->in[r][1][ty][tx];
         nb[0] = tx > 0 ? Q->in[r][1][ty][tx - 1] : ldg(pin + fo + off[0]);
         nb[1] = tx < TX - 1 ? Q->in[r][1][ty][tx + 1] : ldg(pin + fo + off[1]);
@@ -718,10 +855,11 @@ struct TmaLoader {
         if (hr0) r0v = Q->r0[r][ty][tx];
     }
     // one arrival per consumer warp once all its lanes have read slot a
+    // (none once a wait gave up: the producer then stops issuing copies)
     __device__ __forceinline__ void release(int a)
     {
-        __syncwarp();
-        if ((threadIdx.x & 31) == 0) mbar_arrive(&Q->empty[a % TMA_R]);
+        const bool all_ok = __all_sync(0xffffffffu, ok);
+        if ((threadIdx.x & 31) == 0 && all_ok) mbar_arrive(&Q->empty[a % TMA_R]);
     }
 };
 
@@ -733,7 +871,7 @@ struct TmaLoader {
 // RHS term after the pairwise sums.  Rounding order differs from the generic
 // kernel; FP32 is not compared bit for bit.
 template <int DIM, int KC, unsigned SIG, int NMAX, class LD>
-__device__ __forceinline__ void fast_cell(const Geom &g, const Pass<float> &P, LD &ld, ListSmem<float> &S, int tid,
+__device__ __forceinline__ bool fast_cell(const Geom &g, const Pass<float> &P, LD &ld, ListSmem<float> &S, int tid,
                                           long long i, const int *off, const int *ghost, const float *tabA,
                                           const float *tabB, const float *tabL, const signed char *ptype,
                                           double &esum, long long &ecnt)
@@ -840,10 +978,7 @@ __device__ __forceinline__ void fast_cell(const Geom &g, const Pass<float> &P, L
             }
         }
     }
-    if (nz > MAXACT) {
-        atomicOr(P.flag, FLAG_NZ_OVERFLOW);
-        nz = MAXACT;
-    }
+    if (nz > MAXACT) return false;      // crowded cell: the caller takes the wide path
 
     T mu = (T)0, rc = (T)0;
     if (KC) {
@@ -911,7 +1046,7 @@ __device__ __forceinline__ void fast_cell(const Geom &g, const Pass<float> &P, L
             esum += (double)(q * q);
             ecnt += 1;
         }
-        return;
+        return true;
     }
     // listed phases: add the RHS term, clamp, >= 1 candidates, sum
     {
@@ -938,7 +1073,7 @@ __device__ __forceinline__ void fast_cell(const Geom &g, const Pass<float> &P, L
                 if (a < N && nv[a] != ((a == bestid) ? (T)1 : (T)0)) changed = true;
             ssum = (T)1;
         }
-        if (!(ssum > (T)0)) atomicOr(P.flag, FLAG_SIMPLEX);
+        if (!(ssum > (T)0)) raise_flag(P.flag, FLAG_SIMPLEX);
     }
     const T inv = (ssum > (T)0) ? (T)1 / ssum : (T)1;
     const bool fix = R0OUT && P.fix_first && changed;
@@ -966,9 +1101,11 @@ __device__ __forceinline__ void fast_cell(const Geom &g, const Pass<float> &P, L
         if (HP0) d = d + a0c * (ldg(P.p0 + o) - cc);
         if (HP2) d = d + a2c * (ldg(P.p2 + o) - cc);
         const T acc = cc + d;
+        if (!isfinite(acc)) raise_flag(P.flag, FLAG_NONFINITE);
         if (R0OUT) P.r0out[o] = rc;
         P.out[o] = acc;
     }
+    return true;
 }
 
 // Bits of occupancy word w that belong to phases below N.
@@ -994,7 +1131,7 @@ template <int DIM, int KC, unsigned SIG, bool OCC = true, int NW = 1>
 __device__ __forceinline__ void masked_cell(const Geom &g, const Pass<float> &P, ListSmem<float> &S, int tid,
                                             long long i, const int *off, const int *ghost, const float *tabA,
                                             const float *tabB, const float *tabL, const signed char *ptype,
-                                            double &esum, long long &ecnt, unsigned am)
+                                            double &esum, long long &ecnt, unsigned am, bool &over)
 {
     typedef float T;
     constexpr int NFACE = 2 * DIM;
@@ -1145,8 +1282,10 @@ __device__ __forceinline__ void masked_cell(const Geom &g, const Pass<float> &P,
         }
       }
     }
+    // a crowded cell finishes with the truncated list (the warp's collective
+    // operations below need every lane) and is then redone on the wide path
     if (nz > MAXACT) {
-        atomicOr(P.flag, FLAG_NZ_OVERFLOW);
+        over = true;
         nz = MAXACT;
     }
 
@@ -1257,7 +1396,7 @@ __device__ __forceinline__ void masked_cell(const Geom &g, const Pass<float> &P,
                 }
             ssum = (T)1;
         }
-        if (!(ssum > (T)0)) atomicOr(P.flag, FLAG_SIMPLEX);
+        if (!(ssum > (T)0)) raise_flag(P.flag, FLAG_SIMPLEX);
     }
     const T inv = (ssum > (T)0) ? (T)1 / ssum : (T)1;
     const bool fix = R0OUT && P.fix_first && changed;
@@ -1300,6 +1439,7 @@ __device__ __forceinline__ void masked_cell(const Geom &g, const Pass<float> &P,
         if (HP0) d = d + a0c * (ldg(P.p0 + o) - cc);
         if (HP2) d = d + a2c * (ldg(P.p2 + o) - cc);
         const T acc = cc + d;
+        if (!isfinite(acc)) raise_flag(P.flag, FLAG_NONFINITE);
         if (R0OUT) P.r0out[o] = rc;
         P.out[o] = acc;
     }
@@ -1312,7 +1452,7 @@ __device__ __forceinline__ void masked_cell(const Geom &g, const Pass<float> &P,
 // same thread moments before, so it is still in L2) and applies the
 // projection's normalisation.  No per-phase register array is needed.
 template <int DIM, int KC, unsigned SIG>
-__device__ __forceinline__ void big_cell(const Geom &g, const Pass<float> &P, PlainLoader<DIM> &ld,
+__device__ __forceinline__ bool big_cell(const Geom &g, const Pass<float> &P, PlainLoader<DIM> &ld,
                                          ListSmem<float> &S, int tid, long long i, const int *off, const int *ghost,
                                          const float *tabA, const float *tabB, const float *tabL,
                                          const signed char *ptype, double &esum, long long &ecnt)
@@ -1418,10 +1558,7 @@ __device__ __forceinline__ void big_cell(const Geom &g, const Pass<float> &P, Pl
             }
         }
     }
-    if (nz > MAXACT) {
-        atomicOr(P.flag, FLAG_NZ_OVERFLOW);
-        nz = MAXACT;
-    }
+    if (nz > MAXACT) return false;      // crowded cell: the caller takes the wide path
     T mu = (T)0, rc = (T)0;
     if (KC) {
         mu = num_c / den_c;
@@ -1494,11 +1631,11 @@ __device__ __forceinline__ void big_cell(const Geom &g, const Pass<float> &P, Pl
             esum += (double)(q * q);
             ecnt += 1;
         }
-        return;
+        return true;
     }
     if (PROJ) {
         if (bestid >= 0) { changed = true; ssum = (T)1; }
-        if (!(ssum > (T)0)) atomicOr(P.flag, FLAG_SIMPLEX);
+        if (!(ssum > (T)0)) raise_flag(P.flag, FLAG_SIMPLEX);
     }
     const T inv = (ssum > (T)0) ? (T)1 / ssum : (T)1;
     const bool fix = R0OUT && P.fix_first && changed;
@@ -1525,17 +1662,20 @@ __device__ __forceinline__ void big_cell(const Geom &g, const Pass<float> &P, Pl
         if (HP0) d = d + a0c * (ldg(P.p0 + o) - cc);
         if (HP2) d = d + a2c * (ldg(P.p2 + o) - cc);
         const T acc = cc + d;
+        if (!isfinite(acc)) raise_flag(P.flag, FLAG_NONFINITE);
         if (R0OUT) P.r0out[o] = rc;
         P.out[o] = acc;
     }
+    return true;
 }
 
 template <int DIM, int KC, unsigned SIG>
 __global__ void __launch_bounds__(BLOCK, 4)
-big_kernel(const Geom g, const Pass<float> P, const float *__restrict__ tabA, const float *__restrict__ tabB,
-           const float *__restrict__ tabL, const signed char *__restrict__ ptype)
+big_kernel(const __grid_constant__ Geom g, const __grid_constant__ Pass<float> P, const float *__restrict__ tabA,
+           const float *__restrict__ tabB, const float *__restrict__ tabL, const signed char *__restrict__ ptype)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
+    if (pass_skipped(P.flag)) return;
     ListSmem<float> &S = *reinterpret_cast<ListSmem<float> *>(smem_raw);
     const int tid = threadIdx.x;
     const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
@@ -1563,9 +1703,14 @@ big_kernel(const Geom g, const Pass<float> P, const float *__restrict__ tabA, co
         ld.p0 = P.p0;
         ld.p2 = P.p2;
         ld.r0 = P.r0in;
-        big_cell<DIM, KC, SIG>(g, P, ld, S, tid, i, off, ghost, tabA, tabB, tabL, ptype, esum, ecnt);
+        if (!big_cell<DIM, KC, SIG>(g, P, ld, S, tid, i, off, ghost, tabA, tabB, tabL, ptype, esum, ecnt)) {
+            esum = 0.0;
+            ecnt = 0;
+            wide_cell<float, DIM, KC>(&g, &P, tabA, tabB, tabL, ptype, x, y, z, &esum, &ecnt);
+        }
     }
     if (SIG & SIG_ERR) block_partials(esum, ecnt, P.part_sum, P.part_cnt, bid);
+    if (P.count_step) count_step_done(P.flag);
 }
 
 // FP32 fast path with plain global loads (any grid, 2D or 3D).
@@ -1575,6 +1720,7 @@ __device__ __forceinline__ void fast_body(const Geom &g, const Pass<float> &P, c
                                           const signed char *__restrict__ ptype)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
+    if (pass_skipped(P.flag)) return;
     ListSmem<float> &S = *reinterpret_cast<ListSmem<float> *>(smem_raw);
     const int tid = threadIdx.x;
     const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
@@ -1604,21 +1750,30 @@ __device__ __forceinline__ void fast_body(const Geom &g, const Pass<float> &P, c
         ld.p0 = P.p0;
         ld.p2 = P.p2;
         ld.r0 = P.r0in;
+        bool over = false;
         if constexpr (MASK)
             masked_cell<DIM, KC, SIG, true, (NMAX + 31) / 32>(g, P, S, tid, i, off, ghost, tabA, tabB, tabL, ptype,
-                                                              esum, ecnt, am);
+                                                              esum, ecnt, am, over);
         else if constexpr (PF_DENSE_ROLLED || (SIG & SIG_ERR) != 0)
-            masked_cell<DIM, KC, SIG, false, 1>(g, P, S, tid, i, off, ghost, tabA, tabB, tabL, ptype, esum, ecnt, am);
+            masked_cell<DIM, KC, SIG, false, 1>(g, P, S, tid, i, off, ghost, tabA, tabB, tabL, ptype, esum, ecnt,
+                                                am, over);
         else
-            fast_cell<DIM, KC, SIG, NMAX>(g, P, ld, S, tid, i, off, ghost, tabA, tabB, tabL, ptype, esum, ecnt);
+            over = !fast_cell<DIM, KC, SIG, NMAX>(g, P, ld, S, tid, i, off, ghost, tabA, tabB, tabL, ptype, esum,
+                                                  ecnt);
+        if (over) {
+            esum = 0.0;
+            ecnt = 0;
+            wide_cell<float, DIM, KC>(&g, &P, tabA, tabB, tabL, ptype, x, y, z, &esum, &ecnt);
+        }
     }
     if (SIG & SIG_ERR) block_partials(esum, ecnt, P.part_sum, P.part_cnt, bid);
+    if (P.count_step) count_step_done(P.flag);
 }
 
 template <int DIM, int KC, unsigned SIG, int NMAX, bool MASK = false>
 __global__ void __launch_bounds__(BLOCK, MASK ? PF_MASK_MINB : PF_FAST_MINB)
-fast_kernel(const Geom g, const Pass<float> P, const float *__restrict__ tabA, const float *__restrict__ tabB,
-            const float *__restrict__ tabL, const signed char *__restrict__ ptype)
+fast_kernel(const __grid_constant__ Geom g, const __grid_constant__ Pass<float> P, const float *__restrict__ tabA,
+            const float *__restrict__ tabB, const float *__restrict__ tabL, const signed char *__restrict__ ptype)
 {
     fast_body<DIM, KC, SIG, NMAX, MASK>(g, P, tabA, tabB, tabL, ptype);
 }
@@ -1627,7 +1782,7 @@ fast_kernel(const Geom g, const Pass<float> P, const float *__restrict__ tabA, c
 // adaptive steps; see cell_kernel_d).
 template <int DIM, int KC, unsigned SIG, int NMAX>
 __global__ void __launch_bounds__(BLOCK, PF_FAST_MINB)
-fast_kernel_d(const Geom g, const Pass<float> *__restrict__ Pd, const float *__restrict__ tabA,
+fast_kernel_d(const __grid_constant__ Geom g, const Pass<float> *__restrict__ Pd, const float *__restrict__ tabA,
               const float *__restrict__ tabB, const float *__restrict__ tabL, const signed char *__restrict__ ptype)
 {
     __shared__ Pass<float> Ps;
@@ -1645,8 +1800,9 @@ constexpr int TMA_BLOCK = BLOCK + 32;
 
 template <int KC, unsigned SIG>
 __global__ void __launch_bounds__(TMA_BLOCK, 3)
-tma_kernel(const Geom g, const Pass<float> P, const __grid_constant__ TmaMaps M, const float *__restrict__ tabA,
-           const float *__restrict__ tabB, const float *__restrict__ tabL, const signed char *__restrict__ ptype)
+tma_kernel(const __grid_constant__ Geom g, const __grid_constant__ Pass<float> P, const __grid_constant__ TmaMaps M,
+           const float *__restrict__ tabA, const float *__restrict__ tabB, const float *__restrict__ tabL,
+           const signed char *__restrict__ ptype)
 {
     constexpr bool ERR = (SIG & SIG_ERR) != 0;
     constexpr bool HP0 = (SIG & SIG_P0) != 0 || ERR;
@@ -1658,6 +1814,7 @@ tma_kernel(const Geom g, const Pass<float> P, const __grid_constant__ TmaMaps M,
     unsigned char *sbase = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     TmaSmem &Q = *reinterpret_cast<TmaSmem *>(sbase);
     ListSmem<float> &S = *reinterpret_cast<ListSmem<float> *>(sbase + sizeof(TmaSmem));
+    if (pass_skipped(P.flag)) return;
     const int tid = threadIdx.x;
     const int N = g.N;
     const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
@@ -1680,9 +1837,15 @@ tma_kernel(const Geom g, const Pass<float> P, const __grid_constant__ TmaMaps M,
         if (tid == BLOCK) {
             const unsigned pt = (unsigned)(TX * TY * sizeof(float));
             const unsigned bytes = (zin ? 3u : 1u) * pt + (HP0 ? pt : 0u) + (HP2 ? pt : 0u) + (HR0 ? pt : 0u);
+            int issued = 0;
             for (int a = 0; a < N; ++a) {
                 const int r = a % TMA_R;
-                if (a >= TMA_R && !mbar_wait(&Q.empty[r], (unsigned)(((a / TMA_R) - 1) & 1))) timeout = 1;
+                // a slot that its consumers never released: stop issuing (no
+                // copy may land in a slot that is still being read)
+                if (a >= TMA_R && !mbar_wait(&Q.empty[r], (unsigned)(((a / TMA_R) - 1) & 1))) {
+                    timeout = 1;
+                    break;
+                }
                 fence_proxy_async();
                 mbar_expect_tx(&Q.full[r], bytes);
                 if (zin) tma_load4(&Q.in[r][0][0][0], &M.in3, x0, y0, z - 1, a, &Q.full[r]);
@@ -1690,7 +1853,12 @@ tma_kernel(const Geom g, const Pass<float> P, const __grid_constant__ TmaMaps M,
                 if (HP0) tma_load4(&Q.p0[r][0][0], &M.p0, x0, y0, z, a, &Q.full[r]);
                 if (HP2) tma_load4(&Q.p2[r][0][0], &M.p2, x0, y0, z, a, &Q.full[r]);
                 if (HR0) tma_load4(&Q.r0[r][0][0], &M.r0, x0, y0, z, a, &Q.full[r]);
+                issued = a + 1;
             }
+            // the block's shared memory must outlive every copy issued into
+            // it: wait (bounded) until the last copy of each slot has landed
+            for (int a = issued - TMA_R > 0 ? issued - TMA_R : 0; a < issued; ++a)
+                if (!mbar_wait(&Q.full[a % TMA_R], (unsigned)((a / TMA_R) & 1))) timeout = 1;
         }
     } else {
         // ---- consumer warps: one cell per thread ---------------------------
@@ -1709,11 +1877,16 @@ tma_kernel(const Geom g, const Pass<float> P, const __grid_constant__ TmaMaps M,
         ld.ty = ty;
         ld.zin = zin;
         ld.ok = true;
-        fast_cell<3, KC, SIG, 32>(g, P, ld, S, tid, i, ld.off, ghost, tabA, tabB, tabL, ptype, esum, ecnt);
+        if (!fast_cell<3, KC, SIG, 32>(g, P, ld, S, tid, i, ld.off, ghost, tabA, tabB, tabL, ptype, esum, ecnt)) {
+            esum = 0.0;
+            ecnt = 0;
+            wide_cell<float, 3, KC>(&g, &P, tabA, tabB, tabL, ptype, x, y, z, &esum, &ecnt);
+        }
         if (!ld.ok) timeout = 1;
     }
-    if (timeout) atomicOr(P.flag, FLAG_TIMEOUT);
+    if (timeout) raise_flag(P.flag, FLAG_TIMEOUT);
     if (ERR) block_partials(esum, ecnt, P.part_sum, P.part_cnt, bid);
+    if (P.count_step) count_step_done(P.flag);
 }
 
 // Signature of a pass as used by the engine's dispatcher.

@@ -61,3 +61,44 @@ def test_non_finite_state_is_reported(pf, field, integ, kw, prec):
         sim.set_state(good)
         st = sim.step(integ, 5 * sim.dt_e(), **kw)
         assert st["t"] == pytest.approx(5 * sim.dt_e())
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("graph", [True, False], ids=["graph", "launched"])
+@pytest.mark.parametrize("integ,mult", [(I.FEULER, 3.0), (I.SSP2, 12.0)], ids=["fe", "ssp2"])
+def test_fixed_steps_end_at_the_last_good_step(pf, integ, mult, graph, prec):
+    # Fixed steps far beyond the stable step (3x for forward Euler, 3x the
+    # (s-1) dt_e limit of SSP(5)2) make the concentration grow without bound
+    # until a pass flags a non-finite value or simplex sum.  pf_step must then
+    # return PF_EUNSTABLE with the state and time of the last step that
+    # completed cleanly (every later pass does nothing), whether the steps
+    # were replayed from a CUDA graph or launched one by one.
+    import torch
+    prob, u = I.multiphase_blobs(17, 13, 1, 4, seed=3, has_conc=1, n_alpha=1)
+    flags = 0 if graph else pf.Simulation.STEP_NO_GRAPH
+    with pf.Simulation(prob, precision=prec, stream=torch.cuda.Stream()) as sim:
+        sim.set_state(u)
+        dt = mult * sim.dt_e()
+        t_end = 2000 * dt
+        with pytest.raises(pf.PfError) as e:
+            sim.step(integ, t_end, dt_mult=mult, ssp_stages=5, flags=flags)
+        assert e.value.status == pf.PF_EUNSTABLE
+        ug, t = sim.get_state()
+    k = int(round(t / dt))
+    assert 1 <= k < 2000 and t == k * dt
+    assert np.isfinite(ug).all()
+    assert np.abs(ug[:prob.n_phases].sum(0) - 1.0).max() < (1e-12 if prec == 64 else 1e-5)
+    with pf.Simulation(prob, precision=prec, stream=torch.cuda.Stream()) as sim:
+        sim.set_state(u)
+        # the same k steps (every one of size dt) end cleanly at the same state
+        st = sim.step(integ, t_end, dt_mult=mult, ssp_stages=5, max_attempts=k, flags=flags)
+        assert st["steps_accepted"] == k and st["t"] == t
+        u2, _ = sim.get_state()
+        np.testing.assert_array_equal(u2, ug)
+        # and the next step fails, leaving that state and time
+        with pytest.raises(pf.PfError) as e:
+            sim.step(integ, t_end, dt_mult=mult, ssp_stages=5, flags=flags)
+        assert e.value.status == pf.PF_EUNSTABLE
+        u3, t3 = sim.get_state()
+        assert t3 == t
+        np.testing.assert_array_equal(u3, ug)

@@ -247,13 +247,58 @@ def test_status_codes(pf):
     assert e.value.status == pf.PF_EINVAL
 
 
-def test_active_list_overflow_is_reported(pf):
-    # More than 12 nontrivial phases in one cell exceeds the kernel's per-cell
-    # list (the paper's own per-cell capacity is N_p = 12): PF_EINVAL, no
-    # silent truncation.
+@pytest.mark.parametrize("prec", [64, 32])
+def test_crowded_cells_match_the_oracle(pf, prec):
+    # More than 12 nontrivial phases in a cell (the fast per-cell list) send
+    # that cell through the wide path (a 64-entry list); Sec. 3.1 sets no
+    # limit, and the results are those of the oracle: N_z bit-exact, the RHS
+    # and a forward Euler and an RKL2 step at 1e-12 (FP64) or within the FP32
+    # bound (inputs rounded to FP32 on both sides).
     prob, u = I.multiphase_blobs(9, 9, 8, 40, seed=9, has_conc=0, min_dist=1.5)
-    _, nz_ref = ref.Oracle(prob).rhs(u)
-    assert nz_ref.max() > 12
+    if prec == 32:
+        u = u.astype(np.float32).astype(np.float64)
+    o = ref.Oracle(prob)
+    r_ref, nz_ref = o.rhs(u)
+    assert nz_ref.max() > 12 and (nz_ref > 12).sum() > 10
+    dte = o.dt_e()
+    fe_ref, _, _, _ = o.step(ref.FEULER, 0.5 * dte, 1, u)
+    s = ref.sts_stages(ref.RKL2, 10 * dte, dte)
+    rk_ref, _, _, _ = o.step(ref.RKL2, 10 * dte, s, u)
+    tol = REL64 if prec == 64 else 2e-5
+    with pf.Simulation(prob, precision=prec) as sim:
+        sim.set_state(u)
+        r, nz = sim.rhs()
+        np.testing.assert_array_equal(nz, nz_ref)
+        assert relerr(r, r_ref, prob.n_phases, 0) <= (REL64 if prec == 64 else 1e-4)
+        sim.step(ref.FEULER, 0.5 * dte, dt_mult=0.5)
+        assert relerr(sim.get_state()[0], fe_ref, prob.n_phases, 0) <= tol
+        sim.set_state(u)
+        sim.step(ref.RKL2, 10 * dte, dt_mult=10.0)
+        assert relerr(sim.get_state()[0], rk_ref, prob.n_phases, 0) <= tol * (1 if prec == 64 else 5)
+
+
+def test_crowded_cells_masked_equal_dense(pf):
+    # masked storage sends the same cells through the same wide path and
+    # writes their occupancy words: the results equal the dense storage's
+    prob, u = I.multiphase_blobs(9, 9, 8, 40, seed=9, has_conc=0, min_dist=1.5)
+    out = []
+    for opt in (0, 2):                                      # dense, PF_OPT_MASKED
+        with pf.Simulation(prob, precision=32, options=opt) as sim:
+            sim.set_state(u)
+            t_end = 30 * sim.dt_e()
+            st = sim.step(ref.RKL2, t_end, tol=(1e-4, 1e-3, 1e-4, 1e-4), trace_cap=1000)
+            out.append((st["trace"], sim.get_state()[0]))
+    (ta, ua), (tb, ub) = out
+    np.testing.assert_array_equal(ta["s"], tb["s"])
+    np.testing.assert_array_equal(ua, ub)
+
+
+def test_more_than_64_nontrivial_phases_is_reported(pf):
+    # 70 phases all present in every cell (beyond the 64-entry wide list):
+    # PF_EINVAL, never a silent truncation
+    N = 70
+    prob, _ = I.multiphase_blobs(6, 5, 4, N, seed=2, has_conc=0, min_dist=1.0)
+    u = np.full((N, prob.V), 1.0 / N)
     with pf.Simulation(prob, precision=64) as sim:
         sim.set_state(u)
         with pytest.raises(pf.PfError) as e:

@@ -592,3 +592,94 @@ def test_fixed_step_temporal_orders_on_the_shrinking_grain():
             errs.append(np.abs(ue - uref).max())
         orders = [math.log2(errs[k] / errs[k + 1]) for k in range(2)]
         assert min(orders) >= p - 0.25 and sum(orders) / 2 <= p + 0.5, (integ, orders)
+
+
+def test_controller_drive_matches_the_run_loop():
+    # or_drive takes the decisions of or_run's adaptive loop (Sec. 3.2 stage
+    # rule, Sec. 3.3 controller, Sec. 5 output times) from a given error
+    # sequence: fed the run's own norms it must take the run's own attempts,
+    # across two calls (controller state and proposal carried over).
+    prob, u = I.multiphase_blobs(13, 11, 1, 3, seed=2, has_conc=1, n_alpha=1)
+    tol = (1e-4, 1e-3, 1e-4, 1e-4)
+    rejected = 0
+    for integ in (ref.RKL1, ref.RKL2, ref.SSP104):
+        o = ref.Oracle(prob)
+        dte = o.dt_e()
+        t1, t2 = 17.3 * dte, 41.0 * dte
+        _, u1, ta, tr1 = o.run(integ, u, 0.0, t1, tol=tol, trace_cap=5000)
+        _, _, tb, tr2 = o.run(integ, u1, ta, t2, tol=tol, trace_cap=5000)
+        assert ta == t1 and tb == t2
+        d = ref.Drive(integ, dte)
+        for t_end, tr in ((t1, tr1), (t2, tr2)):
+            dr = d.run(t_end, tr["err"])
+            np.testing.assert_array_equal(dr["dt"], tr["dt"])
+            np.testing.assert_array_equal(dr["s"], tr["s"])
+            np.testing.assert_array_equal(dr["acc"], tr["acc"])
+            assert d.t == t_end
+        assert d.dt_next == o.stats.dt_next
+        rejected += int((tr1["acc"] == 0).sum() + (tr2["acc"] == 0).sum())
+    assert rejected > 0                              # the reject branch was exercised
+
+
+def test_controller_drive_worked_cases():
+    # Hand-worked attempts (Sec. 3.2-3.3, Sec. 5): dt_e = 1, RKL2, every error
+    # 0.5.  First attempt 0.9 dt_e with s = 3 (bound (9 + 3 - 2)/4 * 0.9 = 2.25);
+    # the next proposal is 0.9 * 1.2772233 (the worked controller step above);
+    # an attempt that would pass t_end is shortened onto it; a proposal
+    # within 1e-9 (relative) of the remaining time is stretched onto it.
+    d = ref.Drive(ref.RKL2, 1.0)
+    dr = d.run(1.5, [0.5] * 10)
+    assert dr["dt"][0] == 0.9 and dr["s"][0] == 3 and dr["acc"][0] == 1
+    assert dr["dt"][1] == pytest.approx(1.5 - 0.9, rel=1e-15)       # clipped onto t_end
+    assert len(dr["dt"]) == 2 and d.t == 1.5
+    d = ref.Drive(ref.RKL2, 1.0)
+    dr = d.run(0.9 * (1 + 5e-10), [0.5])
+    assert dr["dt"][0] == 0.9 * (1 + 5e-10) and d.t == 0.9 * (1 + 5e-10)
+    # a rejected attempt leaves t; the retry is smaller
+    d = ref.Drive(ref.RKL1, 1.0)
+    dr = d.run(100.0, [3.0, 0.5])
+    assert list(dr["acc"]) == [0, 1] and dr["dt"][1] < dr["dt"][0]
+    assert d.t == pytest.approx(dr["dt"][1], rel=1e-15)
+    # stage cap: max_stages = 3 cuts a large proposal to the largest step that
+    # 3 RKL2 stages allow, 2.25 dt_e, and the step does not land on t_end
+    d = ref.Drive(ref.RKL2, 1.0, dt0=50.0, max_stages=3)
+    dr = d.run(100.0, [0.5])
+    assert dr["s"][0] == 3 and dr["dt"][0] == pytest.approx(2.25, rel=1e-15)
+    assert d.t == pytest.approx(2.25, rel=1e-15)
+
+
+def test_reduce_on_hand_built_states():
+    # Totals of Sec. 5.2 (area by integration) on states whose sums are known
+    # by construction: volumes are cell sums times dx^dim, mass the same for
+    # c, and a phase is alive iff its maximum is >= 0.5 (0.5 itself counts).
+    nx, ny = 10, 8
+    prob = I.Problem(dim=2, nx=nx, ny=ny, nz=1, dx=0.5, n_phases=4,
+                     phase_type=np.array([0, 1, 1, 1], np.int32),
+                     gamma=I.uniform_pairs(4, 1.0), mobility=I.uniform_pairs(4, 1.0), W=1.0,
+                     has_conc=1, k=(1.0, 1.0), c0=(0.0, 1.0), D=(1.0, 1.0))
+    V = nx * ny
+    u = np.zeros((5, V))
+    disc = np.zeros(V, bool)
+    disc[[11, 12, 13, 21, 22, 23, 24, 31, 32, 33, 34, 35, 42, 43, 44, 52, 53]] = True   # 17 cells
+    u[1, disc] = 1.0
+    u[1, [60, 61, 62]] = 0.25                       # 3 cells at 0.25 -> 0.75
+    u[2, 70] = 0.5                                  # maximum exactly 0.5: alive
+    u[3, [71, 72]] = 0.4999                          # below 0.5: not alive
+    u[0] = 1.0 - u[1:4].sum(0)
+    u[4] = np.linspace(0.0, 1.0, V)
+    mass, vol, alive = ref.Oracle(prob).reduce(u)
+    dv = 0.25
+    assert vol[1] == (17 + 0.75) * dv
+    assert vol[2] == 0.5 * dv and vol[3] == pytest.approx(2 * 0.4999 * dv, rel=1e-15)
+    assert vol.sum() == pytest.approx(V * dv, rel=1e-15)
+    assert alive == 3                               # phases 0, 1, 2
+    assert mass == pytest.approx(V * 0.5 * dv, rel=1e-14)   # mean of linspace(0, 1) is 1/2
+    # 3D: dv = dx^3
+    prob3 = prob.with_(dim=3, nx=4, ny=3, nz=2, dx=2.0, has_conc=0, n_phases=2,
+                       phase_type=np.array([0, 1], np.int32),
+                       gamma=I.uniform_pairs(2, 1.0), mobility=I.uniform_pairs(2, 1.0))
+    u3 = np.zeros((2, 24))
+    u3[1, :5] = 1.0
+    u3[0] = 1.0 - u3[1]
+    mass3, vol3, alive3 = ref.Oracle(prob3).reduce(u3)
+    assert vol3[1] == 5 * 8.0 and vol3[0] == 19 * 8.0 and mass3 == 0.0 and alive3 == 2

@@ -64,3 +64,44 @@ def test_totals_noalloc_rejects_oversize(env):
     assert st == pf.PF_EINVAL
     st = L.pf_totals_noalloc(ud.data_ptr(), 4, 8, 1.0, None, None, None)
     assert st == pf.PF_EINVAL
+
+
+def test_totals_noalloc_capped_blocks_field_limit_and_nan(env):
+    torch, pf, L = env
+    rng = np.random.default_rng(7)
+    # 2.2 M cells: more than 512 blocks of 4096 cells, so the block count is
+    # capped and every block reduces a larger chunk
+    V = 2_200_001
+    u = rng.random((2, V)) - 0.25
+    ud = torch.tensor(u, dtype=torch.float64, device="cuda")
+    sums = torch.zeros(2, dtype=torch.float64, device="cuda")
+    maxes = torch.zeros(2, dtype=torch.float64, device="cuda")
+    for _ in range(2):                                  # two calls in a row
+        assert L.pf_totals_noalloc(ud.data_ptr(), 2, V, 0.5, sums.data_ptr(), maxes.data_ptr(), None) == pf.PF_OK
+        torch.cuda.synchronize()
+        np.testing.assert_allclose(sums.cpu().numpy(), 0.5 * u.sum(axis=1), rtol=1e-12)
+        np.testing.assert_array_equal(maxes.cpu().numpy(), u.max(axis=1))
+    # the largest field count, the last scratch rows in use
+    u = rng.random((130, 999)) * 2.0 - 1.0
+    u[129, 17] = -np.inf                               # a maximum below -1e300 is still exact
+    u[129, :17] = -np.inf
+    u[129, 18:] = -np.inf
+    ud = torch.tensor(u, dtype=torch.float64, device="cuda")
+    sums = torch.zeros(130, dtype=torch.float64, device="cuda")
+    maxes = torch.zeros(130, dtype=torch.float64, device="cuda")
+    assert L.pf_totals_noalloc(ud.data_ptr(), 130, 999, 1.0, sums.data_ptr(), maxes.data_ptr(), None) == pf.PF_OK
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(sums.cpu().numpy()[:129], u[:129].sum(axis=1), rtol=1e-12)
+    np.testing.assert_array_equal(maxes.cpu().numpy(), u.max(axis=1))
+    # a NaN makes that field's sum and maximum NaN, the others are unaffected
+    u = rng.random((3, 5000))
+    u[1, 4321] = np.nan
+    ud = torch.tensor(u, dtype=torch.float64, device="cuda")
+    sums = torch.zeros(3, dtype=torch.float64, device="cuda")
+    maxes = torch.zeros(3, dtype=torch.float64, device="cuda")
+    assert L.pf_totals_noalloc(ud.data_ptr(), 3, 5000, 1.0, sums.data_ptr(), maxes.data_ptr(), None) == pf.PF_OK
+    torch.cuda.synchronize()
+    s, m = sums.cpu().numpy(), maxes.cpu().numpy()
+    assert np.isnan(s[1]) and np.isnan(m[1])
+    np.testing.assert_allclose(s[[0, 2]], u[[0, 2]].sum(axis=1), rtol=1e-12)
+    np.testing.assert_array_equal(m[[0, 2]], u[[0, 2]].max(axis=1))
