@@ -706,7 +706,7 @@ static int plan_attempt(int integ, int adaptive, double dt, double rem, long kfi
 }
 
 int or_drive(int integ, double dte, double t_end, double dt0, int max_stages, int n_err,
-             const double *errs, double *t, or_ctrl *ctrl, double *dt_next,
+             const double *errs, const double *h_given, double *t, or_ctrl *ctrl, double *dt_next,
              int cap, double *tr_dt, int *tr_s, int *tr_acc)
 {
     if (max_stages <= 0) max_stages = 1001;
@@ -716,8 +716,10 @@ int or_drive(int integ, double dte, double t_end, double dt0, int max_stages, in
         double h;
         int s, last, acc;
         plan_attempt(integ, 1, dt, t_end - *t, 0, 0, dte, 0, max_stages, &h, &s, &last);
+        if (k < cap) tr_dt[k] = h;
+        if (h_given) h = h_given[k];       /* continue from the step actually taken */
         dt = or_ctrl_update(ctrl, errs[k], h, or_order(integ), &acc);
-        if (k < cap) { tr_dt[k] = h; tr_s[k] = s; tr_acc[k] = acc; }
+        if (k < cap) { tr_s[k] = s; tr_acc[k] = acc; }
         k++;
         if (acc) *t = last ? t_end : *t + h;
     }

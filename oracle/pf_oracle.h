@@ -135,9 +135,13 @@ int or_run(const or_params *p, int integ, double t_end, const or_tol *tol,
    0.9 dte when dt0 is 0); *t advances on acceptance, *dt_next receives the
    last proposal.  Stops at t_end or after n_err attempts.  The attempted
    dt, s and accept flags are written to the trace (up to cap entries);
-   returns the number of attempts. */
+   returns the number of attempts.  With h_given (may be NULL) the loop
+   continues from the step sizes h_given[k] actually taken elsewhere (the
+   controller update and the time advance use them), while the trace still
+   holds the sizes this loop would have chosen: a one-attempt-ahead check
+   that accumulates no difference between two loops. */
 int or_drive(int integ, double dte, double t_end, double dt0, int max_stages, int n_err,
-             const double *errs, double *t, or_ctrl *ctrl, double *dt_next,
+             const double *errs, const double *h_given, double *t, or_ctrl *ctrl, double *dt_next,
              int cap, double *tr_dt, int *tr_s, int *tr_acc);
 
 #ifdef __cplusplus

@@ -88,7 +88,7 @@ def lib():
                              C.POINTER(_Ctrl), C.POINTER(_Stats), C.c_int, _dp, _ip, _dp, _ip, _ip,
                              C.c_int, _dp, _ip, _ip]
         L.or_run.restype = C.c_int
-        L.or_drive.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_int, C.c_int, _dp,
+        L.or_drive.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_int, C.c_int, _dp, _dp,
                                _dp, C.POINTER(_Ctrl), _dp, C.c_int, _dp, _ip, _ip]
         L.or_drive.restype = C.c_int
         _lib = L
@@ -295,15 +295,20 @@ class Drive:
         lib().or_ctrl_init(C.byref(self.ctrl))
         self.dt_next = 0.0
 
-    def run(self, t_end, errs):
+    def run(self, t_end, errs, given=None):
+        """Attempts to t_end for the error norms errs.  given: the step sizes
+        actually taken (continue from those; see or_drive)."""
         errs = np.ascontiguousarray(errs, np.float64)
         n = len(errs)
+        hg = None if given is None else np.ascontiguousarray(given, np.float64)
+        assert hg is None or len(hg) == n
         dt = np.zeros(max(n, 1))
         s = np.zeros(max(n, 1), np.int32)
         acc = np.zeros(max(n, 1), np.int32)
         t = C.c_double(self.t)
         dn = C.c_double(self.dt_next)
         k = lib().or_drive(self.integ, self.dte, t_end, self.dt0, self.max_stages, n, _d(errs),
+                           _d(hg) if hg is not None else _dp(),
                            C.byref(t), C.byref(self.ctrl), C.byref(dn), n, _d(dt),
                            s.ctypes.data_as(_ip), acc.ctypes.data_as(_ip))
         self.t, self.dt_next = t.value, dn.value

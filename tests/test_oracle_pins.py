@@ -617,6 +617,12 @@ def test_controller_drive_matches_the_run_loop():
             np.testing.assert_array_equal(dr["acc"], tr["acc"])
             assert d.t == t_end
         assert d.dt_next == o.stats.dt_next
+        # continuing from the sizes actually taken changes nothing here
+        d = ref.Drive(integ, dte)
+        for t_end, tr in ((t1, tr1), (t2, tr2)):
+            dr = d.run(t_end, tr["err"], given=tr["dt"])
+            np.testing.assert_array_equal(dr["dt"], tr["dt"])
+            np.testing.assert_array_equal(dr["acc"], tr["acc"])
         rejected += int((tr1["acc"] == 0).sum() + (tr2["acc"] == 0).sum())
     assert rejected > 0                              # the reject branch was exercised
 
