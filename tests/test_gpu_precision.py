@@ -1,0 +1,67 @@
+"""FP32 storage with many-stage RKL steps (Sec. 3.2, Eq. sts): the rounding
+of the stage recurrence against the FP64 oracle at s = 101, 301 and 1001.
+
+In FP32 mode the stage combination v + a0 (p0 - v) + a2 (p2 - v) + b1 F(v)
++ b0 F(u^n) is evaluated in FP32 from FP64 coefficients rounded once.  The
+recurrence of Legendre-based schemes is internally stable (a rounding error
+made at stage j is carried by a ratio of Legendre-type polynomials bounded by
+one in the stability interval), so the accumulated rounding grows about
+linearly with s, not geometrically.  FP64 arithmetic in the kernels would
+cost more than the pass itself on this GPU (its FP64 rate is 1/64 of FP32);
+instead this test bounds the FP32 error of the largest steps the schemes
+take and states it beside the time-discretisation error of the same step.
+
+Workload: the solutal Stefan strip (Sec. 5.2.2; 512 x 3 cells, D 1:100),
+one fixed RKL step from an FP32-rounded state with the largest step that s
+stages allow (0.999 of the bound of Sec. 3.2), on the GPU in FP32 and in the
+oracle in FP64.  The temporal error of that step is the difference between
+the oracle's single step and eight substeps.  Both are reported per field
+block (phases, concentration) relative to the field's largest value.
+"""
+import numpy as np
+import pytest
+
+from oracle import ref
+from paper_2601_16522_gb300 import inputs as I
+
+from test_gpu_parity import pf, relerr  # noqa: F401  (fixture)
+
+pytestmark = pytest.mark.gpu
+
+
+def _bound(integ, s):
+    return ((s * s + s - 2) / 4.0 if integ == ref.RKL2 else (s * s + s) / 2.0) * 0.9
+
+
+@pytest.mark.parametrize("integ,s", [(ref.RKL2, 101), (ref.RKL2, 301), (ref.RKL2, 1001),
+                                     (ref.RKL1, 101), (ref.RKL1, 301)],
+                         ids=["rkl2-101", "rkl2-301", "rkl2-1001", "rkl1-101", "rkl1-301"])
+def test_fp32_many_stage_rounding_is_far_below_the_temporal_error(pf, integ, s):
+    prob, u = I.stefan(nx=512, ny=3, h=100.0, W=2.5)
+    u = u.astype(np.float32).astype(np.float64)
+    N, K = prob.n_phases, prob.has_conc
+    o = ref.Oracle(prob)
+    dte = o.dt_e()
+    mult = 0.999 * _bound(integ, s)
+    dt = mult * dte
+    assert ref.sts_stages(integ, dt, dte) == s
+    u64, _, _, ev = o.step(integ, dt, s, u)
+    assert ev == s
+    uref = u.copy()
+    for _ in range(8):
+        h = dt / 8.0
+        uref, _, _, _ = o.step(integ, h, ref.sts_stages(integ, h, dte), uref)
+    e_time = relerr(u64, uref, N, K)
+    with pf.Simulation(prob, precision=32) as sim:
+        sim.set_state(u)
+        st = sim.step(integ, dt, dt_mult=mult, max_stages=s)
+        u32, _ = sim.get_state()
+    assert st["rhs_evals"] == s
+    e32 = relerr(u32, u64, N, K)
+    # front position (phase volume per row) and its change over the step
+    x64, x32, x0 = u64[1].sum() / 3.0, u32[1].sum() / 3.0, u[1].sum() / 3.0
+    print("%s s=%d dt=%.4g: FP32 vs FP64 %.3g, temporal %.3g, front %.4f vs %.4f (moved %.2f)"
+          % ("RKL2" if integ == ref.RKL2 else "RKL1", s, dt, e32, e_time, x32, x64, x64 - x0))
+    assert e32 <= 0.02 * e_time
+    assert e32 <= 5e-3
+    assert abs(x32 - x64) <= 1e-3 * abs(x64 - x0)
