@@ -630,8 +630,10 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     tuned = None
     if not args.tma:
-        choice, ms_plain, ms_tma = sim.autotune()
-        tuned = {"choice": ["plain", "tma"][choice], "rkl2_pass_ms_plain": ms_plain, "rkl2_pass_ms_tma": ms_tma}
+        choice, ms = sim.autotune()
+        names = ["two_cell", "one_cell", "tma"]
+        tuned = {"choice": names[choice]}
+        tuned.update({"rkl2_pass_ms_" + names[k]: v for k, v in ms.items()})
 
     def one_step():
         return sim.step(pf.RKL2, 1e30, tol=TOL, max_attempts=1)

@@ -107,7 +107,13 @@ typedef struct {
    dense and mark the vectors they write as fully occupied.  The masks cost
    4 bytes per word, cell and state vector (pf_footprint counts them); TMA
    staging is not used.  PF_EINVAL for FP64. */
-enum { PF_OPT_TMA = 1, PF_OPT_MASKED = 2 };
+/* PF_OPT_ONE_CELL (FP32 dense storage) runs the passes through the kernel
+   with one cell per thread and stage values held in registers (N <= 32; the
+   chunked form for more phases) instead of the default kernel with two
+   x-adjacent cells per thread (float2 loads and stores, stage values written
+   through; used where nx is even).  Results agree to FP32 rounding; meant for
+   comparison and tuning (pf_autotune picks per problem shape). */
+enum { PF_OPT_TMA = 1, PF_OPT_MASKED = 2, PF_OPT_ONE_CELL = 4 };
 
 /* Error tolerances of the weighted norm (Eq. error_norm): relative r and
    absolute a per field (phase field, concentration). */
@@ -283,14 +289,21 @@ enum {
    enable = -1 keeps the totals and the current setting. */
 int pf_profile(struct pf_handle *h, int enable, double *ms, long long *launches);
 
+/* Kernel variants of the FP32 dense passes: two cells per thread (default
+   where nx is even), one cell per thread, and one cell per thread with the
+   phase planes staged into shared memory by TMA bulk tensor copies. */
+enum { PF_KVAR_TWO_CELL = 0, PF_KVAR_ONE_CELL = 1, PF_KVAR_TMA = 2, PF_KVAR_COUNT = 3 };
+
 /* Autotuner: times the RKL2 stage pass of this handle's current state with
-   each available kernel variant (plain loads; TMA-staged phase planes where
-   the problem allows it), switches the handle to the faster one and records
-   the choice for the problem's shape (precision, dims, phases, K) in a
-   process-wide table that later pf_create calls of the same shape apply.
-   *choice = 0 plain, 1 TMA; the average times in ms (or -1 when a variant
-   does not apply).  No state change.  PF_ESTATE without a state. */
-int pf_autotune(struct pf_handle *h, int *choice, double *ms_plain, double *ms_tma);
+   each kernel variant that applies (FP32 dense storage), switches the handle
+   to the fastest and records the choice for the problem's shape (precision,
+   dims, phases, K) in a process-wide table that later pf_create calls of the
+   same shape apply (unless an option forces a variant).  *choice receives
+   the PF_KVAR_* chosen (may be NULL); ms (may be NULL) receives
+   PF_KVAR_COUNT average pass times in ms, -1 where a variant does not apply.
+   FP64 and masked storage have one kernel: nothing is timed.  No state
+   change.  PF_ESTATE without a state. */
+int pf_autotune(struct pf_handle *h, int *choice, double *ms);
 
 /* Number of CUDA kernels launched by this handle since pf_create (-1 on NULL). */
 long long pf_launch_count(struct pf_handle *h);

@@ -23,6 +23,8 @@ UNITS = [
     ("pf_stage_f32k1.cu", ["--fmad=true"]),
     ("pf_stage_m32k0.cu", ["--fmad=true"]),
     ("pf_stage_m32k1.cu", ["--fmad=true"]),
+    ("pf_stage_v32k0.cu", ["--fmad=true"]),
+    ("pf_stage_v32k1.cu", ["--fmad=true"]),
     ("pf_dispatch.cu", ["--fmad=false"]),
     ("pf_noalloc.cu", ["--fmad=false"]),
     ("pf_engine.cu", ["--fmad=false"]),

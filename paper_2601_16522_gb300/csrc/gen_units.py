@@ -11,6 +11,9 @@ pf_stage_f32k{0,1}   FP32, K fixed: big_kernel (32 < N <= 250), tma_kernel and
 device-driven adaptive RKL steps)
 pf_stage_m32k{0,1}   FP32 masked storage, K fixed: fast_kernel<..., true> per
                      pass signature for N <= 4, N <= 32 and N <= 128
+pf_stage_v32k{0,1}   FP32 dense storage, K fixed: vec_kernel (two cells per
+                     thread, N <= 128, nx even) per pass signature, and
+                     vec_kernel_d for the device-driven adaptive RKL steps
 """
 import os
 
@@ -171,6 +174,56 @@ def munit(kc, fname):
     return "\n".join(L) + "\n"
 
 
+def vunit(kc, fname):
+    tag = "v32k%d" % kc
+    L = ["// %s -- two-cell FP32 instantiations of the fused stage pass (K = %d)." % (fname, kc),
+         '#include "pf_internal.h"', "", "namespace pfk {", ""]
+    L.append("int launch_%s(const Geom &g, const Pass<float> &P, unsigned sig, cudaStream_t st, const float *A," % tag)
+    L.append("             const float *B, const float *L, const signed char *ptype, bool *done)")
+    L.append("{")
+    L.append("    const dim3 grid((g.nx + 2 * VTX - 1) / (2 * VTX), (g.ny + VTY - 1) / VTY, g.nz);")
+    L.append("    const size_t smv = sizeof(VecSmem);")
+    L.append("    *done = true;")
+    prep = []
+    for d in (2, 3):
+        for sg in FAST_SIGS:
+            L.append("    if (g.dim == %d && sig == (%s)) {" % (d, sg))
+            L.append("        vec_kernel<%d, %d, %s><<<grid, VBLOCK, smv, st>>>(g, P, A, B, L, ptype);" % (d, kc, sg))
+            L.append("        return (int)cudaGetLastError();")
+            L.append("    }")
+            prep.append("    if (cudaFuncSetAttribute(vec_kernel<%d, %d, %s>, cudaFuncAttributeMaxDynamicSharedMemorySize, smv) != cudaSuccess) return -1;" % (d, kc, sg))
+    L.append("    *done = false;")
+    L.append("    return 0;")
+    L.append("}")
+    L.append("")
+    L.append("int launchd_%s(const Geom &g, unsigned sig, const Pass<float> *dP, cudaStream_t st, const float *A," % tag)
+    L.append("             const float *B, const float *L, const signed char *ptype, bool *done)")
+    L.append("{")
+    L.append("    const dim3 grid((g.nx + 2 * VTX - 1) / (2 * VTX), (g.ny + VTY - 1) / VTY, g.nz);")
+    L.append("    const size_t smv = sizeof(VecSmem);")
+    L.append("    *done = true;")
+    for d in (2, 3):
+        for sg in DSIGS:
+            L.append("    if (g.dim == %d && sig == (%s)) {" % (d, sg))
+            L.append("        vec_kernel_d<%d, %d, %s><<<grid, VBLOCK, smv, st>>>(g, dP, A, B, L, ptype);" % (d, kc, sg))
+            L.append("        return (int)cudaGetLastError();")
+            L.append("    }")
+            prep.append("    if (cudaFuncSetAttribute(vec_kernel_d<%d, %d, %s>, cudaFuncAttributeMaxDynamicSharedMemorySize, smv) != cudaSuccess) return -1;" % (d, kc, sg))
+    L.append("    *done = false;")
+    L.append("    return 0;")
+    L.append("}")
+    L.append("")
+    L.append("int prepare_%s()" % tag)
+    L.append("{")
+    L.append("    const int smv = (int)sizeof(VecSmem);")
+    L += prep
+    L.append("    return 1;")
+    L.append("}")
+    L.append("")
+    L.append("}  // namespace pfk")
+    return "\n".join(L) + "\n"
+
+
 def render():
     """{file name: text} of every instantiation unit."""
     return {
@@ -179,6 +232,8 @@ def render():
         "pf_stage_f32k1.cu": unit("float", [1], True, "pf_stage_f32k1.cu"),
         "pf_stage_m32k0.cu": munit(0, "pf_stage_m32k0.cu"),
         "pf_stage_m32k1.cu": munit(1, "pf_stage_m32k1.cu"),
+        "pf_stage_v32k0.cu": vunit(0, "pf_stage_v32k0.cu"),
+        "pf_stage_v32k1.cu": vunit(1, "pf_stage_v32k1.cu"),
     }
 
 

@@ -19,6 +19,16 @@ int launchd_f32k0(const Geom &, unsigned, const Pass<float> *, cudaStream_t, con
                   const float *, const signed char *);
 int launchd_f32k1(const Geom &, unsigned, const Pass<float> *, cudaStream_t, const float *, const float *,
                   const float *, const signed char *);
+int launch_v32k0(const Geom &, const Pass<float> &, unsigned, cudaStream_t, const float *, const float *,
+                 const float *, const signed char *, bool *);
+int launch_v32k1(const Geom &, const Pass<float> &, unsigned, cudaStream_t, const float *, const float *,
+                 const float *, const signed char *, bool *);
+int launchd_v32k0(const Geom &, unsigned, const Pass<float> *, cudaStream_t, const float *, const float *,
+                  const float *, const signed char *, bool *);
+int launchd_v32k1(const Geom &, unsigned, const Pass<float> *, cudaStream_t, const float *, const float *,
+                  const float *, const signed char *, bool *);
+int prepare_v32k0();
+int prepare_v32k1();
 int prepare_f64();
 int prepare_f32k0();
 int prepare_f32k1();
@@ -47,6 +57,13 @@ int launch_stage<float>(const Geom &g, const Pass<float> &P, cudaStream_t st, co
                     : launch_m32k0(g, P, sig, st, A, B, L, ptype, &done);
         return done ? e : (int)cudaErrorInvalidValue;
     }
+    if (!tma && g.kvar == KVAR_TWO_CELL && vec_eligible(g)) {
+        // dense storage: the two-cell kernels take every pass they have
+        const unsigned sig = pass_signature(P);
+        int e = g.K ? launch_v32k1(g, P, sig, st, A, B, L, ptype, &done)
+                    : launch_v32k0(g, P, sig, st, A, B, L, ptype, &done);
+        if (done) return e;
+    }
     auto go = [&](unsigned sig) {
         return g.K ? launch_f32k1(g, P, sig, st, A, B, L, ptype, tma, &done)
                    : launch_f32k0(g, P, sig, st, A, B, L, ptype, tma, &done);
@@ -67,6 +84,12 @@ template <>
 int launch_stage_d<float>(const Geom &g, unsigned sig, const Pass<float> *dP, cudaStream_t st, const float *A,
                           const float *B, const float *L, const signed char *ptype)
 {
+    if (g.kvar == KVAR_TWO_CELL && vec_eligible(g)) {
+        bool done = false;
+        int e = g.K ? launchd_v32k1(g, sig, dP, st, A, B, L, ptype, &done)
+                    : launchd_v32k0(g, sig, dP, st, A, B, L, ptype, &done);
+        if (done) return e;
+    }
     return g.K ? launchd_f32k1(g, sig, dP, st, A, B, L, ptype) : launchd_f32k0(g, sig, dP, st, A, B, L, ptype);
 }
 
@@ -77,7 +100,8 @@ template <>
 int prepare_stage<float>()
 {
     const int a = prepare_f32k0(), b = prepare_f32k1(), c = prepare_m32k0(), d = prepare_m32k1();
-    return (a > 0 && b > 0 && c > 0 && d > 0) ? a : -1;
+    const int e = prepare_v32k0(), f = prepare_v32k1();
+    return (a > 0 && b > 0 && c > 0 && d > 0 && e > 0 && f > 0) ? a : -1;
 }
 
 }  // namespace pfk

@@ -13,6 +13,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <new>
@@ -85,9 +86,12 @@ __global__ void wait_selftest_kernel(int *flag, unsigned polls)
 }
 
 // Fixed-order sum of the per-block error partials (one block of 256 threads).
+// n: the number of partials, or (pn non-null) at most n, the count the error
+// pass recorded (its block count depends on the kernel that ran).
 __global__ void finalize_err_kernel(const double *__restrict__ ps, const long long *__restrict__ pc, int n,
-                                    double *out_sum, long long *out_cnt)
+                                    double *out_sum, long long *out_cnt, const int *pn = nullptr)
 {
+    if (pn && *pn < n) n = *pn;
     __shared__ double ss[256];
     __shared__ long long sc[256];
     double s = 0.0;
@@ -367,6 +371,7 @@ struct pf_handle {
     double *dres = nullptr;            // [0] error sum
     long long *dcnt = nullptr;
     int *dflag = nullptr;
+    int *dpartn = nullptr;             // error partials written by the last error pass
     double *tot_sum = nullptr, *tot_max = nullptr;
     int tot_blocks = 0;
     bool masked = false;               // masked storage: occupancy-word planes after the fields
@@ -570,6 +575,7 @@ Pass<T> blank_pass(pf_handle *h)
     P.project = 1;
     P.a1 = 1.0;
     P.flag = h->dflag;
+    P.part_n = h->dpartn;
     P.part_sum = h->part_sum;
     P.part_cnt = h->part_cnt;
     return P;
@@ -938,7 +944,7 @@ int read_error(pf_handle *h, double *err)
     h->cur_kind = PF_PASS_OTHER;
     int pst = prof_begin(h);
     if (pst) return pst;
-    finalize_err_kernel<<<1, 256, 0, h->stream>>>(h->part_sum, h->part_cnt, h->grid, h->dres, h->dcnt);
+    finalize_err_kernel<<<1, 256, 0, h->stream>>>(h->part_sum, h->part_cnt, h->grid, h->dres, h->dcnt, h->dpartn);
     h->launches++;
     if (cudaGetLastError() != cudaSuccess) return PF_EDEVICE;
     if ((pst = prof_end(h))) return pst;
@@ -1302,7 +1308,7 @@ int build_devloop(pf_handle *h, int integ)
         dl_err<T><<<1, 1, 0, st>>>(ctl, desc);
         if (cudaGetLastError() != cudaSuccess) return false;
         if (pfk::launch_stage_d<T>(h->g, pfk::SIG_ERR, desc + 2, st, A, B, L, h->dptype) != 0) return false;
-        finalize_err_kernel<<<1, 256, 0, st>>>(h->part_sum, h->part_cnt, h->grid, h->dres, h->dcnt);
+        finalize_err_kernel<<<1, 256, 0, st>>>(h->part_sum, h->part_cnt, h->grid, h->dres, h->dcnt, h->dpartn);
         dl_ctrl<<<1, 1, 0, st>>>(ctl, h->dres, h->dcnt, h->dflag, hout);
         return cudaGetLastError() == cudaSuccess;
     });
@@ -1661,7 +1667,7 @@ void free_all(pf_handle *h)
     h->ev_pool.clear();
     for (int k = 0; k < NBUF; ++k) if (h->buf[k]) cudaFreeAsync(h->buf[k], h->stream);
     void *ps[] = {h->dA, h->dB, h->dL, h->dAB64, h->dptype, h->staging, h->dnz, h->part_sum, h->part_cnt,
-                  h->dres, h->dcnt, h->dflag, h->tot_sum, h->tot_max, h->dl_ctl, h->dl_desc};
+                  h->dres, h->dcnt, h->dflag, h->dpartn, h->tot_sum, h->tot_max, h->dl_ctl, h->dl_desc};
     for (void *p : ps) if (p) cudaFreeAsync(p, h->stream);
     cudaStreamSynchronize(h->stream);
 }
@@ -1684,12 +1690,25 @@ int tuned_choice(const pf_handle *h)
     return it == g_tune.end() ? -1 : it->second;
 }
 
-// Average time of the RKL2-body pass signature on the current state (inputs
-// u^n for every operand, output into a work buffer; no state change).
-double time_rkl2_pass(pf_handle *h, bool use_tma, int reps)
+// Kernel variant of the FP32 dense passes (PF_KVAR_*) applied to a handle.
+void set_variant(pf_handle *h, int v)
 {
-    const bool keep = h->tma;
-    h->tma = use_tma;
+    h->tma = h->tma_ok && v == PF_KVAR_TMA;
+    h->g.kvar = v == PF_KVAR_TWO_CELL ? pfk::KVAR_TWO_CELL : pfk::KVAR_ONE_CELL;
+}
+
+int current_variant(const pf_handle *h)
+{
+    return h->tma ? PF_KVAR_TMA : (h->g.kvar == pfk::KVAR_TWO_CELL ? PF_KVAR_TWO_CELL : PF_KVAR_ONE_CELL);
+}
+
+// Average time of the RKL2-body pass signature on the current state with
+// kernel variant v (inputs u^n for every operand, output into a work buffer;
+// no state change).
+double time_rkl2_pass(pf_handle *h, int v, int reps)
+{
+    const int keep = current_variant(h);
+    set_variant(h, v);
     const int U = h->iu, W = (h->iu + 1) % NBUF;
     Pass<float> P = blank_pass<float>(h);
     P.in = (float *)h->buf[U]; P.p0 = (float *)h->buf[U]; P.p2 = (float *)h->buf[U]; P.r0in = (float *)h->buf[U];
@@ -1712,7 +1731,7 @@ double time_rkl2_pass(pf_handle *h, bool use_tma, int reps)
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaMemsetAsync(h->dflag, 0, PF_FLAG_BYTES, h->stream);
-    h->tma = keep;
+    set_variant(h, keep);
     return ms;
 }
 
@@ -1818,7 +1837,8 @@ int pf_create(const pf_params *p, void *cuda_stream, pf_handle **out)
     int bps = (h->prec == 64) ? pfk::prepare_stage<double>() : pfk::prepare_stage<float>();
     if (bps <= 0) { delete h; return PF_EINVAL; }
     if ((long long)g.tiles_x * g.tiles_y * p->nz > 0x7fffffffLL || p->nz > 65535) { delete h; return PF_EINVAL; }
-    h->grid = g.tiles_x * g.tiles_y * p->nz;
+    // error partials: one per block of the largest tiling an error pass may use
+    h->grid = (int)std::max((long long)g.tiles_x * g.tiles_y, pfk::vec_tiles(g)) * p->nz;
     h->tot_blocks = (int)((h->V + 4095) / 4096 < 1024 ? (h->V + 4095) / 4096 : 1024);
     if (h->tot_blocks < 1) h->tot_blocks = 1;
 
@@ -1841,6 +1861,7 @@ int pf_create(const pf_params *p, void *cuda_stream, pf_handle **out)
     ok = ok && dmalloc(h, &h->dres, sizeof(double));
     ok = ok && dmalloc(h, &h->dcnt, sizeof(long long));
     ok = ok && dmalloc(h, &h->dflag, PF_FLAG_BYTES);
+    ok = ok && dmalloc(h, &h->dpartn, sizeof(int));
     ok = ok && dmalloc(h, &h->tot_sum, sizeof(double) * h->tot_blocks * NP);
     ok = ok && dmalloc(h, &h->tot_max, sizeof(double) * h->tot_blocks * NP);
     if (!ok) { cudaGetLastError(); free_all(h); delete h; return PF_ENOMEM; }
@@ -1872,10 +1893,17 @@ int pf_create(const pf_params *p, void *cuda_stream, pf_handle **out)
         for (int k = 0; k < NBUF && ok; ++k)
             ok = make_map(&h->m3[k], h->buf[k], g, 3) && make_map(&h->m1[k], h->buf[k], g, 1);
         h->tma_ok = ok;
-        int tuned = -1;
-        if (ok) tuned = tuned_choice(h);
-        h->tma = ok && ((p->options & PF_OPT_TMA) || tuned == 1);
     }
+    // kernel variant: forced by an option, else a tuned choice for this shape,
+    // else the two-cell kernel (the one-cell kernel where it does not apply)
+    int variant = PF_KVAR_TWO_CELL;
+    if (p->options & PF_OPT_ONE_CELL) variant = PF_KVAR_ONE_CELL;
+    else if ((p->options & PF_OPT_TMA) && h->tma_ok) variant = PF_KVAR_TMA;
+    else if (h->prec == 32) {
+        const int tuned = tuned_choice(h);
+        if (tuned >= 0 && (tuned != PF_KVAR_TMA || h->tma_ok)) variant = tuned;
+    }
+    set_variant(h, variant);
     *out = h;
     return PF_OK;
 }
@@ -1889,7 +1917,9 @@ int pf_footprint(const pf_params *p, long long *bytes)
     const long long Vs = (V + 63) / 64 * 64;
     const long long NF = p->n_phases + (p->has_conc ? 1 : 0);
     const long long es = p->precision == 64 ? 8 : 4;
-    const long long tiles = (long long)((p->nx + pfk::TX - 1) / pfk::TX) * ((p->ny + pfk::TY - 1) / pfk::TY) * p->nz;
+    const long long vt = (long long)((p->nx + 2 * pfk::VTX - 1) / (2 * pfk::VTX)) * ((p->ny + pfk::VTY - 1) / pfk::VTY);
+    const long long tiles = std::max((long long)((p->nx + pfk::TX - 1) / pfk::TX) * ((p->ny + pfk::TY - 1) / pfk::TY), vt) *
+                            p->nz;
     const long long tot_blocks = (V + 4095) / 4096 < 1024 ? ((V + 4095) / 4096 > 0 ? (V + 4095) / 4096 : 1) : 1024;
     long long b = (long long)NBUF * NF * Vs * es;          // state vectors
     if (p->options & PF_OPT_MASKED) b += (long long)NBUF * ((p->n_phases + 31) / 32) * Vs * 4;   // occupancy words
@@ -2087,24 +2117,27 @@ int pf_profile(pf_handle *h, int enable, double *ms, long long *launches)
 
 long long pf_launch_count(pf_handle *h) { return h ? h->launches : -1; }
 
-int pf_autotune(pf_handle *h, int *choice, double *ms_plain, double *ms_tma)
+int pf_autotune(pf_handle *h, int *choice, double *ms)
 {
     if (!h) return PF_EINVAL;
     if (!h->has_state) return PF_ESTATE;
-    if (ms_plain) *ms_plain = -1.0;
-    if (ms_tma) *ms_tma = -1.0;
-    int c = 0;
-    if (h->prec == 32 && h->tma_ok) {
-        const double a = time_rkl2_pass(h, false, 5);
-        const double b = time_rkl2_pass(h, true, 5);
-        if (a < 0.0 || b < 0.0) return PF_EDEVICE;
-        c = b < a ? 1 : 0;
-        if (ms_plain) *ms_plain = a;
-        if (ms_tma) *ms_tma = b;
+    if (ms)
+        for (int v = 0; v < PF_KVAR_COUNT; ++v) ms[v] = -1.0;
+    int c = current_variant(h);
+    if (h->prec == 32 && !h->masked) {
+        const bool ok[PF_KVAR_COUNT] = {pfk::vec_eligible(h->g), true, h->tma_ok};
+        double best = -1.0;
+        for (int v = 0; v < PF_KVAR_COUNT; ++v) {
+            if (!ok[v]) continue;
+            const double t = time_rkl2_pass(h, v, 5);
+            if (t < 0.0) return PF_EDEVICE;
+            if (ms) ms[v] = t;
+            if (best < 0.0 || t < best) { best = t; c = v; }
+        }
         std::lock_guard<std::mutex> guard(g_tune_lock);
         g_tune[tune_key(h)] = c;
     }
-    h->tma = h->tma_ok && c == 1;
+    set_variant(h, c);
     if (choice) *choice = c;
     return check_flag(h);
 }

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include "pf_kernels.cuh"
+#include "pf_vec.cuh"
 
 namespace pfk {
 

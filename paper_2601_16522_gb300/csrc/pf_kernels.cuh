@@ -61,8 +61,11 @@ struct Geom {
     double cref;                        // FP32 storage holds c - cref (0 in FP64); c0 and cdir
                                         // are shifted by it, so mu and the face fluxes are those
                                         // of c, and only the error weights |c| add it back
-    int tiles_x, tiles_y;               // block tiling of the x-y plane
+    int tiles_x, tiles_y;               // block tiling of the x-y plane (one-cell kernels)
+    int kvar;                           // FP32 dense passes: KVAR_TWO_CELL or KVAR_ONE_CELL
 };
+// Kernel variants of the FP32 dense passes (chosen per handle, pf_autotune).
+enum { KVAR_TWO_CELL = 0, KVAR_ONE_CELL = 1 };
 
 // What one pass does (passed by value).
 template <typename T>
@@ -90,6 +93,7 @@ struct Pass {
     double r_phi, a_phi, r_c, a_c;   // tolerances (error partials)
     double *part_sum;    // per-block partial sums of (e/w)^2
     long long *part_cnt; // per-block partial DoF counts
+    int *part_n;         // number of partials the pass wrote (its block count)
     double *rhs_pm;      // MODE_RHS: FP64 output, field f at rhs_pm + f * V
     unsigned char *nz_out; // MODE_RHS: N_z per cell (may be null)
     int *flag;           // device status words (see raise_flag)
@@ -213,9 +217,12 @@ __device__ __forceinline__ void face_offsets(const Geom &g, int x, int y, int z,
     }
 }
 
-// Fixed-order block reduction of (sum, count) into the per-block partials.
-__device__ __forceinline__ void block_partials(double esum, long long ecnt, double *ps, long long *pc, int bid)
+// Fixed-order block reduction of (sum, count) into the per-block partials;
+// block 0 records how many partials the launch writes (pn, may be null).
+__device__ __forceinline__ void block_partials(double esum, long long ecnt, double *ps, long long *pc, int bid,
+                                               int *pn = nullptr)
 {
+    if (pn && bid == 0 && threadIdx.x == 0) *pn = (int)(gridDim.x * gridDim.y * gridDim.z);
     constexpr int MAXW = 16;                 // blocks of up to 512 threads
     __shared__ double rs_sum[MAXW];
     __shared__ long long rs_cnt[MAXW];
@@ -672,7 +679,7 @@ __device__ __forceinline__ void cell_body(const Geom &g, const Pass<T> &P, const
             wide_cell<T, DIM, KC>(&g, &P, tabA, tabB, tabL, ptype, x, y, z, &esum, &ecnt);
     }
     const bool errp = (SIG & SIG_GENERIC) ? (P.mode == MODE_ERR || P.embedded_err != 0) : (SIG & SIG_ERR) != 0;
-    if (errp) block_partials(esum, ecnt, P.part_sum, P.part_cnt, bid);
+    if (errp) block_partials(esum, ecnt, P.part_sum, P.part_cnt, bid, P.part_n);
     if (P.count_step) count_step_done(P.flag);
 }
 
@@ -1710,7 +1717,7 @@ big_kernel(const __grid_constant__ Geom g, const __grid_constant__ Pass<float> P
             wide_cell<float, DIM, KC>(&g, &P, tabA, tabB, tabL, ptype, x, y, z, &esum, &ecnt);
         }
     }
-    if (SIG & SIG_ERR) block_partials(esum, ecnt, P.part_sum, P.part_cnt, bid);
+    if (SIG & SIG_ERR) block_partials(esum, ecnt, P.part_sum, P.part_cnt, bid, P.part_n);
     if (P.count_step) count_step_done(P.flag);
 }
 
@@ -1767,7 +1774,7 @@ __device__ __forceinline__ void fast_body(const Geom &g, const Pass<float> &P, c
             wide_cell<float, DIM, KC>(&g, &P, tabA, tabB, tabL, ptype, x, y, z, &esum, &ecnt);
         }
     }
-    if (SIG & SIG_ERR) block_partials(esum, ecnt, P.part_sum, P.part_cnt, bid);
+    if (SIG & SIG_ERR) block_partials(esum, ecnt, P.part_sum, P.part_cnt, bid, P.part_n);
     if (P.count_step) count_step_done(P.flag);
 }
 
@@ -1886,7 +1893,7 @@ tma_kernel(const __grid_constant__ Geom g, const __grid_constant__ Pass<float> P
         if (!ld.ok) timeout = 1;
     }
     if (timeout) raise_flag(P.flag, FLAG_TIMEOUT);
-    if (ERR) block_partials(esum, ecnt, P.part_sum, P.part_cnt, bid);
+    if (ERR) block_partials(esum, ecnt, P.part_sum, P.part_cnt, bid, P.part_n);
     if (P.count_step) count_step_done(P.flag);
 }
 

@@ -1,0 +1,527 @@
+// pf_vec.cuh -- the FP32 dense stage passes with two cells per thread.
+//
+// Hot passes of FP32 dense storage (N <= 128 phases, nx even; Sec. 3 finite
+// differences, Sec. 3.1 projection, Sec. 3.2 stage combinations, Sec. 3.3
+// error sweep).  Every thread owns two x-adjacent cells (x, x + 1), so each
+// load and store of a phase plane moves a float2 (a warp covers 64
+// consecutive cells, 256 B), the x neighbours inside the pair come from the
+// pair itself and across lanes from warp shuffles, and the address
+// arithmetic of a phase is shared by both cells.
+//
+// The stage value of a phase that is not nontrivial at a cell (the n(phi)
+// filter of Eq. phieq) has a zero RHS, so after the first sweep it is final
+// up to the projection's normalisation and is written at once; only the
+// nontrivial phases (at most VACT per cell, in a shared-memory list) wait for
+// the pairwise sums.  The normalisation rewrites an already written entry
+// only where it is nonzero and the cell's simplex sum is not exactly one (or
+// the >= 1 rule changed the cell): bulk cells, whose sum is exactly one, and
+// zero entries are never touched again.  No per-phase register array is
+// needed, so the phase loop is rolled and the next phase's loads are issued
+// before the current phase is processed.  A cell with more than VACT
+// nontrivial phases is recomputed on the wide path.  The arithmetic is that
+// of fast_cell (the same combination, projection, fix and error terms); the
+// concentration sums are formed per chemical type, so rounding differs from
+// the other FP32 kernels (FP32 is not compared bit for bit).
+#pragma once
+#include "pf_kernels.cuh"
+
+namespace pfk {
+
+constexpr int VTX = 32;              // threads along x: 64 cells
+constexpr int VTY = 4;               // rows per block
+constexpr int VBLOCK = VTX * VTY;    // 128 threads
+constexpr int VCELLS = 2 * VBLOCK;   // 256 cells per block
+constexpr int VACT = 8;              // nontrivial phases per cell in the shared-memory list
+
+// Blocks of the x-y plane of the two-cell kernels (one z plane per block).
+__host__ __device__ inline long long vec_tiles(const Geom &g)
+{
+    return (long long)((g.nx + 2 * VTX - 1) / (2 * VTX)) * ((g.ny + VTY - 1) / VTY);
+}
+
+// Whether the two-cell kernels can run a problem (dense FP32 storage).
+__host__ __device__ inline bool vec_eligible(const Geom &g)
+{
+    return (g.nx % 2) == 0 && g.N <= 128 && g.V < 0x7fffffffLL;
+}
+
+struct VecSmem {
+    unsigned char id[VACT][VCELLS];
+    float lap[VACT][VCELLS];   // Laplacian, later the RHS of the listed phase
+    float cen[VACT][VCELLS];   // phi at the cell
+    float dl[VACT][VCELLS];    // variational derivative
+    float val[VACT][VCELLS];   // stage value before the RHS term
+};
+
+__device__ __forceinline__ float2 ldg2(const float *p) { return __ldg(reinterpret_cast<const float2 *>(p)); }
+
+__device__ __forceinline__ float2 ld_stream2(const float *p)
+{
+    float2 v;
+    asm("ld.global.nc.L1::no_allocate.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ void st2(float *p, float a, float b) { *reinterpret_cast<float2 *>(p) = make_float2(a, b); }
+
+// three-input minimum and maximum (sm_100+ PTX)
+__device__ __forceinline__ float fmax3(float a, float b, float c)
+{
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+__device__ __forceinline__ float fmin3(float a, float b, float c)
+{
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+// Loads of one phase for the thread's two cells.
+struct VPhase {
+    float2 c, ym, yp, zm, zp;  // stencil input at the pair and its y/z neighbours
+    float el, er;              // x neighbours across the tile edge (edge lanes only)
+    float2 p0, p2, r0;         // pointwise inputs
+};
+
+// Per-cell state of the sweep over the phases.
+struct VCell {
+    int nz, bestid, nc;
+    float best, ssum;
+    bool changed, nzhi;
+    unsigned long long nzw;    // phases < 64 not listed whose written value is nonzero
+    double es;                 // error partial (MODE_ERR)
+    long long ec;
+};
+
+template <int DIM, int KC, unsigned SIG>
+__device__ __forceinline__ void vec_body(const Geom &g, const Pass<float> &P, const float *__restrict__ tabA,
+                                         const float *__restrict__ tabB, const float *__restrict__ tabL,
+                                         const signed char *__restrict__ ptype)
+{
+    typedef float T;
+    constexpr bool ERR = (SIG & SIG_ERR) != 0;
+    constexpr bool HP0 = (SIG & SIG_P0) != 0 || ERR;
+    constexpr bool HP2 = (SIG & SIG_P2) != 0;
+    constexpr bool HR0 = (SIG & SIG_R0IN) != 0 || ERR;
+    constexpr bool R0OUT = (SIG & SIG_R0OUT) != 0;
+    constexpr bool PROJ = (SIG & SIG_PROJECT) != 0;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    if (pass_skipped(P.flag)) return;
+    VecSmem &S = *reinterpret_cast<VecSmem *>(smem_raw);
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, ty = tid >> 5;
+    const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    const int x = blockIdx.x * (2 * VTX) + 2 * lane;
+    const int y = blockIdx.y * VTY + ty;
+    const int z = blockIdx.z;
+    const int N = g.N;
+    const int Vs = (int)g.Vs;
+    VCell C[2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        C[c].nz = 0; C[c].bestid = -1; C[c].nc = 0; C[c].best = (T)-1; C[c].ssum = (T)0;
+        C[c].changed = false; C[c].nzhi = false; C[c].nzw = 0ull; C[c].es = 0.0; C[c].ec = 0;
+    }
+    bool crowd[2] = {false, false};
+    if (y < g.ny) {   // warp-uniform (a warp is one row)
+        const bool here = x < g.nx;
+        const int i = (z * g.ny + y) * g.nx + x;
+        // y / z neighbour offsets (a zero-gradient ghost is the cell itself)
+        long long off64[6];
+        int ghost[6];
+        face_offsets(g, x, y, z, off64, ghost);
+        const int oym = ghost[2] ? 0 : (int)off64[2], oyp = ghost[3] ? 0 : (int)off64[3];
+        const int ozm = DIM == 3 ? (ghost[4] ? 0 : (int)off64[4]) : 0;
+        const int ozp = DIM == 3 ? (ghost[5] ? 0 : (int)off64[5]) : 0;
+        // x neighbours of the pair: left of cell x, right of cell x + 1
+        const bool lsh = lane > 0;                          // from lane - 1 (cell x - 1)
+        const bool rsh = lane < 31 && x + 2 < g.nx;         // from lane + 1 (cell x + 2)
+        const bool lself = !lsh && x == 0 && g.bc_phi[0] != BC_PERIODIC;
+        const bool rself = !rsh && x + 2 >= g.nx && g.bc_phi[1] != BC_PERIODIC;
+        const bool lneed = here && !lsh && !lself, rneed = here && !rsh && !rself;
+        const int lofs = x > 0 ? -1 : g.nx - 1;
+        const int rofs = x + 2 < g.nx ? 2 : 2 - g.nx;
+        const T idx2 = (T)(1.0 / g.dx2);
+        const T a0c = (T)P.a0, a2c = (T)P.a2, b1c = (T)P.b1, b0c = (T)P.b0;
+        const T ib1 = (T)(1.0 / P.b1);
+        const T dt = (T)P.dt, rph = (T)P.r_phi, aph = (T)P.a_phi;
+
+        // concentration: per chemical type, phase sums of the two cells, of
+        // their y/z neighbours and of the x edge cells
+        T Ph[2][2], Pn[2][4][2], Pe[2][2];
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            Ph[0][t] = Ph[1][t] = Pe[0][t] = Pe[1][t] = (T)0;
+#pragma unroll
+            for (int f = 0; f < 4; ++f) Pn[0][f][t] = Pn[1][f][t] = (T)0;
+        }
+
+        auto fetch = [&](int a, VPhase &q) {
+            const float *b = P.in + (long long)a * Vs + i;
+            q.c = q.ym = q.yp = q.zm = q.zp = make_float2(0.f, 0.f);
+            q.p0 = q.p2 = q.r0 = make_float2(0.f, 0.f);
+            q.el = q.er = 0.f;
+            if (here) {
+                if (PF_PREFETCH_DIST > 0 && a + PF_PREFETCH_DIST < N) {
+                    const long long pa = (long long)PF_PREFETCH_DIST * Vs;
+                    prefetch_l2(b + pa);
+                    if (HP0) prefetch_l2(P.p0 + (long long)a * Vs + pa + i);
+                    if (HP2) prefetch_l2(P.p2 + (long long)a * Vs + pa + i);
+                    if (HR0) prefetch_l2(P.r0in + (long long)a * Vs + pa + i);
+                }
+                q.c = ldg2(b);
+                q.ym = ldg2(b + oym);
+                q.yp = ldg2(b + oyp);
+                if (DIM == 3) {
+                    q.zm = ldg2(b + ozm);
+                    q.zp = ldg2(b + ozp);
+                }
+                if (HP0) q.p0 = ld_stream2(P.p0 + (long long)a * Vs + i);
+                if (HP2) q.p2 = ld_stream2(P.p2 + (long long)a * Vs + i);
+                if (HR0) q.r0 = ld_stream2(P.r0in + (long long)a * Vs + i);
+            }
+            if (lneed) q.el = __ldg(b + lofs);
+            if (rneed) q.er = __ldg(b + rofs);
+        };
+
+        // one phase at one cell: activity, list entry, stage value (returned)
+        auto cell_phase = [&](VCell &Cc, int slot, int a, T v, T xl, T xr, T ym, T yp, T zm, T zp, T p0v, T p2v,
+                              T r0v) -> T {
+            T mx, mn;
+            if (DIM == 3) {
+                mx = fmax3(fmax3(v, xl, xr), fmax3(ym, yp, zm), zp);
+                mn = fmin3(fmin3(v, xl, xr), fmin3(ym, yp, zm), zp);
+            } else {
+                mx = fmax3(fmax3(v, xl, xr), ym, yp);
+                mn = fmin3(fmin3(v, xl, xr), ym, yp);
+            }
+            const bool act = mx > (T)0 && mn < (T)1;
+            T acc = (T)0;
+            if (!ERR) {
+                acc = affine<HP0, HP2>(v, p0v, p2v, a0c, a2c);
+                if (HR0) acc = acc + b0c * r0v;
+            }
+            if (act) {
+                if (Cc.nz < VACT) {
+                    const T l = DIM == 3 ? (((xl + xr) + (ym + yp)) + (zm + zp)) - (T)6 * v
+                                         : ((xl + xr) + (ym + yp)) - (T)4 * v;
+                    S.id[Cc.nz][slot] = (unsigned char)a;
+                    S.lap[Cc.nz][slot] = l * idx2;
+                    S.cen[Cc.nz][slot] = v;
+                    if (!ERR) S.val[Cc.nz][slot] = acc;
+                }
+                Cc.nz++;
+            } else if (ERR) {
+                // in = u^{n+1}, p0 = u^n, r0in = F^n; a trivial phase has F^{n+1} = 0
+                T e = ((T)12 * (p0v - v) + ((T)6 * dt) * r0v) * ((T)1 / (T)15);
+                const T trial = p0v + (dt * (T)0.5) * r0v;
+                if (trial < (T)0 || trial > (T)1) e = (T)0;
+                if (e != (T)0) {
+                    const T w = rph * fmaxf(fabsf(p0v), fabsf(v)) + aph;
+                    const T q = e / w;
+                    Cc.es += (double)(q * q);
+                    Cc.nc++;
+                }
+            } else if (PROJ) {
+                if (acc < (T)0) { acc = (T)0; Cc.changed = true; }
+                if (acc >= (T)1 && acc > Cc.best) { Cc.best = acc; Cc.bestid = a; }
+                Cc.ssum = Cc.ssum + acc;
+                if (acc != (T)0) {
+                    if (a < 64) Cc.nzw |= 1ull << a;
+                    else Cc.nzhi = true;
+                }
+            }
+            return acc;
+        };
+
+        // ---- the sweep over the phases ---------------------------------------
+        VPhase cur, nxt;
+        fetch(0, cur);
+#pragma unroll 1
+        for (int a = 0; a < N; ++a) {
+            if (a + 1 < N) fetch(a + 1, nxt);
+            const float sl = __shfl_up_sync(0xffffffffu, cur.c.y, 1);
+            const float sr = __shfl_down_sync(0xffffffffu, cur.c.x, 1);
+            const T left = lsh ? sl : (lself ? cur.c.x : cur.el);
+            const T right = rsh ? sr : (rself ? cur.c.y : cur.er);
+            if (here) {
+                const T w0 = cell_phase(C[0], tid, a, cur.c.x, left, cur.c.y, cur.ym.x, cur.yp.x, cur.zm.x,
+                                        cur.zp.x, cur.p0.x, cur.p2.x, cur.r0.x);
+                const T w1 = cell_phase(C[1], VBLOCK + tid, a, cur.c.y, cur.c.x, right, cur.ym.y, cur.yp.y,
+                                        cur.zm.y, cur.zp.y, cur.p0.y, cur.p2.y, cur.r0.y);
+                const long long fo = (long long)a * Vs + i;
+                if (!ERR) st2(P.out + fo, w0, w1);
+                if (R0OUT) st2(P.r0out + fo, (T)0, (T)0);   // listed phases get theirs below
+                if (KC) {
+                    const int t = ptype[a];
+                    // per-type sums: own cells, y/z neighbours, edge cells
+                    Ph[0][t] += cur.c.x;
+                    Ph[1][t] += cur.c.y;
+                    Pn[0][0][t] += cur.ym.x; Pn[1][0][t] += cur.ym.y;
+                    Pn[0][1][t] += cur.yp.x; Pn[1][1][t] += cur.yp.y;
+                    if (DIM == 3) {
+                        Pn[0][2][t] += cur.zm.x; Pn[1][2][t] += cur.zm.y;
+                        Pn[0][3][t] += cur.zp.x; Pn[1][3][t] += cur.zp.y;
+                    }
+                    Pe[0][t] += cur.el;
+                    Pe[1][t] += cur.er;
+                }
+            }
+            cur = nxt;
+        }
+
+        // ---- concentration: mu of the cells and their neighbours, c RHS ------
+        T mu[2] = {(T)0, (T)0}, rc[2] = {(T)0, (T)0}, cc[2] = {(T)0, (T)0};
+        if (KC) {
+            const T c00 = (T)g.c0[0], c01 = (T)g.c0[1], ik0 = (T)g.invk[0], ik1 = (T)g.invk[1];
+            const T dk0 = (T)g.Dk[0], dk1 = (T)g.Dk[1];
+            const float *cf = P.in + (long long)N * Vs + i;
+            float2 c2 = make_float2(0.f, 0.f), cym = c2, cyp = c2, czm = c2, czp = c2;
+            float cel = 0.f, cer = 0.f;
+            if (here) {
+                c2 = ldg2(cf);
+                cym = ldg2(cf + oym);
+                cyp = ldg2(cf + oyp);
+                if (DIM == 3) {
+                    czm = ldg2(cf + ozm);
+                    czp = ldg2(cf + ozp);
+                }
+            }
+            if (lneed) cel = __ldg(cf + lofs);
+            if (rneed) cer = __ldg(cf + rofs);
+            cc[0] = c2.x;
+            cc[1] = c2.y;
+            auto muof = [&](T cv, const T *ph) { return (cv - (c00 * ph[0] + c01 * ph[1])) / (ph[0] * ik0 + ph[1] * ik1); };
+            auto mof = [&](const T *ph) { return ph[0] * dk0 + ph[1] * dk1; };
+            T M[2];
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                mu[c] = muof(cc[c], Ph[c]);
+                M[c] = mof(Ph[c]);
+            }
+            // x neighbours: inside the pair, across lanes, or the edge cells
+            const T mul_s = __shfl_up_sync(0xffffffffu, mu[1], 1), Ml_s = __shfl_up_sync(0xffffffffu, M[1], 1);
+            const T mur_s = __shfl_down_sync(0xffffffffu, mu[0], 1), Mr_s = __shfl_down_sync(0xffffffffu, M[0], 1);
+            T mul, Ml, mur, Mr;
+            if (lsh) { mul = mul_s; Ml = Ml_s; }
+            else if (lself) {
+                // zero-gradient phi; c Dirichlet (ghost 2 c_b - c) or zero-gradient
+                mul = g.bc_c[0] == BC_DIRICHLET ? muof((T)2 * (T)g.cdir[0] - cc[0], Ph[0]) : mu[0];
+                Ml = M[0];
+            } else { mul = muof(cel, Pe[0]); Ml = mof(Pe[0]); }
+            if (rsh) { mur = mur_s; Mr = Mr_s; }
+            else if (rself) {
+                mur = g.bc_c[1] == BC_DIRICHLET ? muof((T)2 * (T)g.cdir[1] - cc[1], Ph[1]) : mu[1];
+                Mr = M[1];
+            } else { mur = muof(cer, Pe[1]); Mr = mof(Pe[1]); }
+            const float2 cnb[4] = {cym, cyp, czm, czp};
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                T acc = (T)0;
+                // x faces
+                const T mxl = c == 0 ? mul : mu[0], Mxl = c == 0 ? Ml : M[0];
+                const T mxr = c == 0 ? mu[1] : mur, Mxr = c == 0 ? M[1] : Mr;
+                acc = acc + ((T)0.5 * (M[c] + Mxl)) * (mxl - mu[c]);
+                acc = acc + ((T)0.5 * (M[c] + Mxr)) * (mxr - mu[c]);
+                // y and z faces (face 2 + f of the cell)
+#pragma unroll
+                for (int f = 0; f < 2 * (DIM - 1); ++f) {
+                    T cv = c == 0 ? cnb[f].x : cnb[f].y;
+                    if (ghost[2 + f] && g.bc_c[2 + f] == BC_DIRICHLET) cv = (T)2 * (T)g.cdir[2 + f] - cc[c];
+                    const T mun = muof(cv, Pn[c][f]);
+                    acc = acc + ((T)0.5 * (M[c] + mof(Pn[c][f]))) * (mun - mu[c]);
+                }
+                rc[c] = acc * idx2;
+            }
+        }
+
+        // ---- pairwise sums over each cell's list ----------------------------
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            VCell &Cc = C[c];
+            const int slot = c * VBLOCK + tid;
+            if (!here) continue;
+            if (Cc.nz > VACT) { crowd[c] = true; continue; }
+            const int nz = Cc.nz;
+            for (int k = 0; k < nz; ++k) {
+                const int a = S.id[k][slot];
+                const T *Aa = tabA + a * N, *Ba = tabB + a * N;
+                T d = (T)0;
+                for (int k2 = 0; k2 < nz; ++k2) {
+                    if (k2 == k) continue;
+                    const int b = S.id[k2][slot];
+                    d = d + (__ldg(Aa + b) * S.lap[k2][slot] + __ldg(Ba + b) * S.cen[k2][slot]);
+                }
+                if (KC) {
+                    const int t = ptype[a];
+                    d = d + (-(mu[c] * mu[c]) / ((T)2 * (T)g.k[t]) - mu[c] * (T)g.c0[t]);
+                }
+                S.dl[k][slot] = d;
+            }
+            const T inz = nz > 1 ? (T)1 / (T)nz : (T)0;
+            for (int k = 0; k < nz; ++k) {
+                T rk = (T)0;
+                const int a = S.id[k][slot];
+                if (nz > 1) {
+                    const T *La = tabL + a * N;
+                    const T dk = S.dl[k][slot];
+                    T s = (T)0;
+                    for (int k2 = 0; k2 < nz; ++k2) {
+                        if (k2 == k) continue;
+                        s = s + __ldg(La + S.id[k2][slot]) * (dk - S.dl[k2][slot]);
+                    }
+                    rk = -(s * inz);
+                }
+                S.lap[k][slot] = rk;              // the list now holds the RHS
+                const long long fo = (long long)a * Vs + i + c;
+                if (ERR) {
+                    const T p0v = __ldg(P.p0 + fo), v0 = S.cen[k][slot], r0v = __ldg(P.r0in + fo);
+                    const T sr = r0v + rk;
+                    T e = ((T)12 * (p0v - v0) + ((T)6 * dt) * sr) * ((T)1 / (T)15);
+                    const T trial = p0v + (dt * (T)0.5) * sr;
+                    if (trial < (T)0 || trial > (T)1) e = (T)0;
+                    if (e != (T)0) {
+                        const T w = rph * fmaxf(fabsf(p0v), fabsf(v0)) + aph;
+                        const T q = e / w;
+                        Cc.es += (double)(q * q);
+                        Cc.nc++;
+                    }
+                    if (R0OUT) P.r0out[fo] = rk;   // F(u^{n+1}) kept for reuse
+                } else {
+                    T acc = S.val[k][slot] + b1c * rk;
+                    if (PROJ) {
+                        if (acc < (T)0) { acc = (T)0; Cc.changed = true; }
+                        if (acc >= (T)1 && (acc > Cc.best || (acc == Cc.best && a < Cc.bestid))) {
+                            Cc.best = acc;
+                            Cc.bestid = a;
+                        }
+                        Cc.ssum = Cc.ssum + acc;
+                    }
+                    S.val[k][slot] = acc;
+                }
+            }
+        }
+
+        // ---- projection, final values, concentration ------------------------
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            VCell &Cc = C[c];
+            const int slot = c * VBLOCK + tid;
+            if (!here || crowd[c]) continue;
+            const int nz = Cc.nz;
+            if (ERR) {
+                Cc.ec += (Cc.nc > 0 ? Cc.nc : 2);
+                if (KC) {
+                    const long long o = (long long)N * Vs + i + c;
+                    const T un = __ldg(P.p0 + o), un1 = cc[c], rn = __ldg(P.r0in + o);
+                    const T e = ((T)12 * (un - un1) + ((T)6 * dt) * (rn + rc[c])) * ((T)1 / (T)15);
+                    const T w = (T)P.r_c * fmaxf(fabsf(un + (T)g.cref), fabsf(un1 + (T)g.cref)) + (T)P.a_c;
+                    const T q = e / w;
+                    Cc.es += (double)(q * q);
+                    Cc.ec += 1;
+                    if (R0OUT) P.r0out[o] = rc[c];
+                }
+                continue;
+            }
+            bool rewrite = false;     // inactive nonzero entries need their final value
+            if (PROJ) {
+                if (Cc.bestid >= 0) {
+                    // the winner becomes 1, the others 0: a change unless the
+                    // winner is exactly 1 and every other phase already zero
+                    bool others = (Cc.nzw & ~(Cc.bestid < 64 ? (1ull << Cc.bestid) : 0ull)) != 0ull || Cc.nzhi;
+                    for (int k = 0; k < nz; ++k)
+                        if (S.id[k][slot] != Cc.bestid && S.val[k][slot] != (T)0) others = true;
+                    if (others || Cc.best != (T)1) { Cc.changed = true; rewrite = true; }
+                    Cc.ssum = (T)1;
+                }
+                if (!(Cc.ssum > (T)0)) raise_flag(P.flag, FLAG_SIMPLEX);
+            }
+            const T inv = (Cc.ssum > (T)0) ? (T)1 / Cc.ssum : (T)1;
+            if (PROJ && Cc.bestid < 0 && inv != (T)1) rewrite = true;
+            const bool fix = R0OUT && P.fix_first && Cc.changed;
+            // listed phases
+            for (int k = 0; k < nz; ++k) {
+                const int a = S.id[k][slot];
+                const long long fo = (long long)a * Vs + i + c;
+                T w = S.val[k][slot];
+                if (PROJ) w = (Cc.bestid >= 0) ? ((a == Cc.bestid) ? (T)1 : (T)0) : w * inv;
+                P.out[fo] = w;
+                if (R0OUT) {
+                    T r = S.lap[k][slot];
+                    if (fix) r = (w - S.cen[k][slot]) * ib1;
+                    P.r0out[fo] = r;
+                }
+            }
+            // phases not listed whose written value is nonzero (rare outside
+            // bulk cells): the >= 1 rule or the normalisation
+            if (rewrite) {
+                for (unsigned long long m = Cc.nzw; m; m &= m - 1ull) {
+                    const int a = __ffsll((long long)m) - 1;
+                    const long long fo = (long long)a * Vs + i + c;
+                    const T w = (Cc.bestid >= 0) ? ((a == Cc.bestid) ? (T)1 : (T)0) : P.out[fo] * inv;
+                    P.out[fo] = w;
+                    if (fix) P.r0out[fo] = (w - __ldg(P.in + fo)) * ib1;
+                }
+                if (Cc.nzhi)
+                    for (int a = 64; a < N; ++a) {
+                        const long long fo = (long long)a * Vs + i + c;
+                        bool listed = false;
+                        for (int k = 0; k < nz; ++k) listed = listed || S.id[k][slot] == a;
+                        if (listed) continue;
+                        const T o = P.out[fo];
+                        if (o == (T)0) continue;
+                        const T w = (Cc.bestid >= 0) ? ((a == Cc.bestid) ? (T)1 : (T)0) : o * inv;
+                        P.out[fo] = w;
+                        if (fix) P.r0out[fo] = (w - __ldg(P.in + fo)) * ib1;
+                    }
+            }
+            if (KC) {
+                const long long o = (long long)N * Vs + i + c;
+                // the small increments are summed first: c is rounded once per stage
+                T d = b1c * rc[c];
+                if (HR0) d = d + b0c * __ldg(P.r0in + o);
+                if (HP0) d = d + a0c * (__ldg(P.p0 + o) - cc[c]);
+                if (HP2) d = d + a2c * (__ldg(P.p2 + o) - cc[c]);
+                const T acc = cc[c] + d;
+                if (!isfinite(acc)) raise_flag(P.flag, FLAG_NONFINITE);
+                if (R0OUT) P.r0out[o] = rc[c];
+                P.out[o] = acc;
+            }
+        }
+        // crowded cells: the wide path rewrites every output of the cell
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+            if (crowd[c]) {
+                C[c].es = 0.0;
+                C[c].ec = 0;
+                wide_cell<float, DIM, KC>(&g, &P, tabA, tabB, tabL, ptype, x + c, y, z, &C[c].es, &C[c].ec);
+            }
+    }
+    if (ERR) block_partials(C[0].es + C[1].es, C[0].ec + C[1].ec, P.part_sum, P.part_cnt, bid, P.part_n);
+    if (P.count_step) count_step_done(P.flag);
+}
+
+template <int DIM, int KC, unsigned SIG>
+__global__ void __launch_bounds__(VBLOCK, KC ? 4 : 6)
+vec_kernel(const __grid_constant__ Geom g, const __grid_constant__ Pass<float> P, const float *__restrict__ tabA,
+           const float *__restrict__ tabB, const float *__restrict__ tabL, const signed char *__restrict__ ptype)
+{
+    vec_body<DIM, KC, SIG>(g, P, tabA, tabB, tabL, ptype);
+}
+
+// The same pass with its description read from device memory (device-driven
+// adaptive steps; see cell_kernel_d).
+template <int DIM, int KC, unsigned SIG>
+__global__ void __launch_bounds__(VBLOCK, KC ? 4 : 6)
+vec_kernel_d(const __grid_constant__ Geom g, const Pass<float> *__restrict__ Pd, const float *__restrict__ tabA,
+             const float *__restrict__ tabB, const float *__restrict__ tabL, const signed char *__restrict__ ptype)
+{
+    __shared__ Pass<float> Ps;
+    if (threadIdx.x == 0) Ps = *Pd;
+    __syncthreads();
+    vec_body<DIM, KC, SIG>(g, Ps, tabA, tabB, tabL, ptype);
+}
+
+}  // namespace pfk

@@ -91,7 +91,7 @@ def _lib():
         L.pf_destroy.argtypes = [H]
         L.pf_profile.argtypes = [H, C.c_int, _dp, C.POINTER(C.c_longlong)]
         L.pf_footprint.argtypes = [C.POINTER(pf_params), C.POINTER(C.c_longlong)]
-        L.pf_autotune.argtypes = [H, _ip, _dp, _dp]
+        L.pf_autotune.argtypes = [H, _ip, _dp]
         L.pf_launch_count.argtypes = [H]
         L.pf_launch_count.restype = C.c_longlong
         L.pf_strerror.argtypes = [C.c_int]
@@ -174,6 +174,8 @@ class Simulation:
 
     OPT_TMA = 1
     OPT_MASKED = 2
+    OPT_ONE_CELL = 4
+    KVAR_TWO_CELL, KVAR_ONE_CELL, KVAR_TMA = 0, 1, 2
 
     def __init__(self, prob, precision=64, stream=None, options=0):
         self.prob = prob
@@ -318,12 +320,13 @@ class Simulation:
         return {k: (ms[i], n[i]) for i, k in enumerate(PASS_KINDS)}
 
     def autotune(self):
-        """pf_autotune: returns (choice, ms_plain, ms_tma); choice 0 plain, 1 TMA."""
+        """pf_autotune: returns (choice, {variant: ms}) with choice one of
+        KVAR_TWO_CELL, KVAR_ONE_CELL, KVAR_TMA; variants that do not apply are
+        left out of the dict."""
         c = C.c_int()
-        a = C.c_double()
-        b = C.c_double()
-        _check(_lib().pf_autotune(self.h, C.byref(c), C.byref(a), C.byref(b)), "pf_autotune")
-        return c.value, a.value, b.value
+        ms = (C.c_double * 3)()
+        _check(_lib().pf_autotune(self.h, C.byref(c), ms), "pf_autotune")
+        return c.value, {k: ms[k] for k in range(3) if ms[k] >= 0.0}
 
     def launch_count(self):
         return _lib().pf_launch_count(self.h)
