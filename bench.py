@@ -347,8 +347,11 @@ def served_stream(pf, torch, n_requests, rate=50.0):
 
 def masked_run(pf, torch, prob, u, stream, args, world, dev, dense_out, dense_pass_ms):
     """The bench steps again in masked storage (PF_OPT_MASKED) from the same
-    initial state: GCell-updates/s, per-pass times, and whether the final
-    state equals the dense run's."""
+    initial state: GCell-updates/s, per-pass times, and the largest
+    difference from the dense run's final state (the masked kernels share the
+    one-cell kernels' arithmetic, the dense run takes the two-cell kernels:
+    FP32 rounding differences, which the discontinuous activity filter can
+    turn into O(1e-3) local ones)."""
     V, N = prob.V, prob.n_phases
     sim = pf.Simulation(prob, precision=32, stream=stream, options=pf.Simulation.OPT_MASKED)
     sim.set_state(u)
@@ -370,14 +373,16 @@ def masked_run(pf, torch, prob, u, stream, args, world, dev, dense_out, dense_pa
     out = torch.empty_like(dense_out)
     sim.get_state(out=out)
     torch.cuda.synchronize()         # the copy runs on the simulation's stream
-    equal = bool(torch.equal(out, dense_out))
+    d = (out - dense_out).abs()
+    diff = {"max": float(d.max()), "mean": float(d.mean())}
+    del d
     sim.close()
     occ = float((u[:N] != 0).sum(0, dtype=torch.float64).mean())
     pass_ms = {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items() if v[1] > 0}
     rk = pass_ms.get("rkl2")
     dk = dense_pass_ms.get("rkl2")
     return {"value": aggregate_value(V, sweeps, ms, world), "unit": UNIT, "ms_per_step": ms / args.steps,
-            "sweeps": sweeps, "pass_ms": pass_ms, "equal_to_dense": equal,
+            "sweeps": sweeps, "pass_ms": pass_ms, "abs_diff_to_dense": diff,
             "rkl2_pass_speedup": (dk["ms"] / dk["launches"]) / (rk["ms"] / rk["launches"]) if rk and dk else None,
             "mean_nonzero_phases_per_cell": occ,
             "storage": "dense phase planes + one 32-bit occupancy word per cell and vector"}

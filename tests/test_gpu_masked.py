@@ -3,8 +3,8 @@ the dense FP32 passes and the FP64 oracle.
 
 A phase outside a cell's occupancy union has an exactly zero RHS and stage
 value, so skipping it changes nothing but the sign of some zeros: the masked
-and the dense results are equal value for value (np.array_equal treats -0
-and +0 as equal).  The dense FP32 path is itself tested against the oracle
+results equal those of the dense one-cell kernels (PF_OPT_ONE_CELL, the same
+arithmetic) value for value (np.array_equal treats -0 and +0 as equal).  The dense FP32 path is itself tested against the oracle
 in test_gpu_parity.py; here the masked path is also compared with the
 oracle directly on one RKL2 step of a 32-grain 3D state.
 """
@@ -21,6 +21,7 @@ pytestmark = pytest.mark.gpu
 ELIGIBLE = [c for c in CASES if c[0] != "blobs3d_N70"]
 N70 = [c for c in CASES if c[0] == "blobs3d_N70"][0]
 TOL = (1e-4, 1e-3, 1e-4, 1e-3)
+ONE = 4          # PF_OPT_ONE_CELL: the dense kernels the masked ones are bit-equal to
 
 
 def _run(pf, prob, u, opts, integ, nsteps_dte, **kw):
@@ -38,7 +39,7 @@ def _run(pf, prob, u, opts, integ, nsteps_dte, **kw):
 @pytest.mark.parametrize("name,prob,u", ELIGIBLE, ids=[c[0] for c in ELIGIBLE])
 def test_masked_fixed_steps_equal_dense(pf, name, prob, u, integ, kw):
     n = 10 if integ != ref.FEULER else 6
-    dense, st_d = _run(pf, prob, u, 0, integ, n, **kw)
+    dense, st_d = _run(pf, prob, u, ONE, integ, n, **kw)
     masked, st_m = _run(pf, prob, u, pf.Simulation.OPT_MASKED, integ, n, **kw)
     assert st_d["rhs_evals"] == st_m["rhs_evals"]
     assert np.array_equal(masked, dense), np.abs(masked - dense).max()
@@ -48,7 +49,7 @@ def test_masked_three_words_fe_equal_dense(pf):
     # 70 phases: three occupancy words per cell; one forward Euler step (the
     # 70-phase blob state exceeds the 12-phase list capacity after that)
     name, prob, u = N70
-    dense, st_d = _run(pf, prob, u, 0, ref.FEULER, 0.9, dt_mult=0.9)
+    dense, st_d = _run(pf, prob, u, ONE, ref.FEULER, 0.9, dt_mult=0.9)
     masked, st_m = _run(pf, prob, u, pf.Simulation.OPT_MASKED, ref.FEULER, 0.9, dt_mult=0.9)
     assert np.array_equal(masked, dense), np.abs(masked - dense).max()
 
@@ -57,7 +58,7 @@ def test_masked_three_words_fe_equal_dense(pf):
 @pytest.mark.parametrize("name,prob,u", [ELIGIBLE[1], ELIGIBLE[3], ELIGIBLE[-1]],
                          ids=[ELIGIBLE[1][0], ELIGIBLE[3][0], ELIGIBLE[-1][0]])
 def test_masked_adaptive_equal_dense(pf, name, prob, u, integ):
-    dense, st_d = _run(pf, prob, u, 0, integ, 40, tol=TOL)
+    dense, st_d = _run(pf, prob, u, ONE, integ, 40, tol=TOL)
     masked, st_m = _run(pf, prob, u, pf.Simulation.OPT_MASKED, integ, 40, tol=TOL)
     for k in ("rhs_evals", "steps_accepted", "steps_rejected"):
         assert st_d[k] == st_m[k], k
@@ -76,7 +77,7 @@ def test_masked_grains_rkl2_vs_oracle(pf):
         dt = 9.0 * sim.dt_e()
         st = sim.step(pf.RKL2, dt, dt_mult=9.0, trace_cap=4)
         out, _ = sim.get_state()
-    with pf.Simulation(prob, precision=32) as sim:
+    with pf.Simulation(prob, precision=32, options=ONE) as sim:
         sim.set_state(u)
         sim.step(pf.RKL2, dt, dt_mult=9.0)
         dense, _ = sim.get_state()

@@ -331,12 +331,12 @@ def test_bulk_state_is_stationary(pf):
 @pytest.mark.parametrize("bc", ["periodic", "neumann_z"])
 def test_tma_staging_is_bitwise_equal_to_plain_loads(pf, bc):
     # The TMA-staged FP32 kernels read the same values through shared memory
-    # that the plain kernels read from global memory and do the same
+    # that the plain one-cell kernels read from global memory and do the same
     # arithmetic, so results must be identical bit for bit.
     bcs = (0, 0, 0, 0, 1, 1) if bc == "neumann_z" else (0,) * 6
     prob, u = I.multiphase_blobs(64, 32, 16, 12, seed=21, W=2.0, bc_phi=bcs, min_dist=9.0)
     outs = []
-    for opt in (pf.Simulation.OPT_TMA, 0):
+    for opt in (pf.Simulation.OPT_TMA, pf.Simulation.OPT_ONE_CELL):
         with pf.Simulation(prob, precision=32, options=opt) as sim:
             sim.set_state(u)
             dte = sim.dt_e()

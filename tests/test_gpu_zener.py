@@ -16,7 +16,8 @@ through the wide path (a 64-entry list), so no phase is dropped (the paper
 does not specify an eviction rule).  Checked here: the printed stable step
 6.26e-5; the equilibration and the immobile run with forward Euler keep
 sum(c) within the FP32 rounding bound; adaptive RKL2 on the equilibration
-runs past 12 phases per cell, with masked storage equal to dense.  (The energy is not
+runs past 12 phases per cell, with masked storage equal to dense storage
+(the one-cell kernels, whose arithmetic the masked kernels share).  (The energy is not
 asserted: with mobilities 1e5 apart and the 1/N_z prefactor the multi-phase
 evolution is not a strict gradient flow of Eq. energy.)
 """
@@ -66,7 +67,7 @@ def test_zener_equilibration_with_rkl2_runs_past_the_fast_list(pf):
     # wide path computes; masked storage equals dense storage there
     prob, u = _state()
     out = []
-    for opts in (pf.Simulation.OPT_MASKED, 0):
+    for opts in (pf.Simulation.OPT_MASKED, pf.Simulation.OPT_ONE_CELL):
         with pf.Simulation(I.zener_equilibration(prob), precision=32, options=opts) as eq:
             eq.set_state(u)
             m0 = eq.reduce()[0]
