@@ -12,8 +12,9 @@ device-driven adaptive RKL steps)
 pf_stage_m32k{0,1}   FP32 masked storage, K fixed: fast_kernel<..., true> per
                      pass signature for N <= 4, N <= 32 and N <= 128
 pf_stage_v32k{0,1}   FP32 dense storage, K fixed: vec_kernel (two cells per
-                     thread, N <= 128, nx even) per pass signature, and
-                     vec_kernel_d for the device-driven adaptive RKL steps
+                     thread, N <= 128, nx even) per pass signature followed by
+                     the wide pass of its crowded cells (wide_fix_kernel), and
+                     the _d forms for the device-driven adaptive RKL steps
 """
 import os
 
@@ -189,6 +190,7 @@ def vunit(kc, fname):
         for sg in FAST_SIGS:
             L.append("    if (g.dim == %d && sig == (%s)) {" % (d, sg))
             L.append("        vec_kernel<%d, %d, %s><<<grid, VBLOCK, smv, st>>>(g, P, A, B, L, ptype);" % (d, kc, sg))
+            L.append("        wide_fix_kernel<%d, %d><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(g, P, A, B, L, ptype);" % (d, kc))
             L.append("        return (int)cudaGetLastError();")
             L.append("    }")
             prep.append("    if (cudaFuncSetAttribute(vec_kernel<%d, %d, %s>, cudaFuncAttributeMaxDynamicSharedMemorySize, smv) != cudaSuccess) return -1;" % (d, kc, sg))
@@ -206,6 +208,7 @@ def vunit(kc, fname):
         for sg in DSIGS:
             L.append("    if (g.dim == %d && sig == (%s)) {" % (d, sg))
             L.append("        vec_kernel_d<%d, %d, %s><<<grid, VBLOCK, smv, st>>>(g, dP, A, B, L, ptype);" % (d, kc, sg))
+            L.append("        wide_fix_kernel_d<%d, %d><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(g, dP, A, B, L, ptype);" % (d, kc))
             L.append("        return (int)cudaGetLastError();")
             L.append("    }")
             prep.append("    if (cudaFuncSetAttribute(vec_kernel_d<%d, %d, %s>, cudaFuncAttributeMaxDynamicSharedMemorySize, smv) != cudaSuccess) return -1;" % (d, kc, sg))

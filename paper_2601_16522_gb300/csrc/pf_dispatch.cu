@@ -37,9 +37,10 @@ int prepare_m32k1();
 
 template <>
 int launch_stage<double>(const Geom &g, const Pass<double> &P, cudaStream_t st, const double *A, const double *B,
-                         const double *L, const signed char *ptype, const TmaMaps *)
+                         const double *L, const signed char *ptype, const TmaMaps *, int *nk)
 {
     bool done = false;
+    if (nk) *nk = 1;
     // FP64 runs every pass through the generic instantiation
     int e = launch_f64(g, P, SIG_GENERIC, st, A, B, L, ptype, nullptr, &done);
     return done ? e : (int)cudaErrorInvalidValue;
@@ -47,9 +48,10 @@ int launch_stage<double>(const Geom &g, const Pass<double> &P, cudaStream_t st, 
 
 template <>
 int launch_stage<float>(const Geom &g, const Pass<float> &P, cudaStream_t st, const float *A, const float *B,
-                        const float *L, const signed char *ptype, const TmaMaps *tma)
+                        const float *L, const signed char *ptype, const TmaMaps *tma, int *nk)
 {
     bool done = false;
+    if (nk) *nk = 1;
     if (P.m_in) {
         // masked storage: only the masked instantiations maintain the masks
         const unsigned sig = pass_signature(P);
@@ -62,7 +64,10 @@ int launch_stage<float>(const Geom &g, const Pass<float> &P, cudaStream_t st, co
         const unsigned sig = pass_signature(P);
         int e = g.K ? launch_v32k1(g, P, sig, st, A, B, L, ptype, &done)
                     : launch_v32k0(g, P, sig, st, A, B, L, ptype, &done);
-        if (done) return e;
+        if (done) {
+            if (nk) *nk = 2;     // the pass and the wide pass of its crowded cells
+            return e;
+        }
     }
     auto go = [&](unsigned sig) {
         return g.K ? launch_f32k1(g, P, sig, st, A, B, L, ptype, tma, &done)
@@ -92,6 +97,12 @@ int launch_stage_d<float>(const Geom &g, unsigned sig, const Pass<float> *dP, cu
     }
     return g.K ? launchd_f32k1(g, sig, dP, st, A, B, L, ptype) : launchd_f32k0(g, sig, dP, st, A, B, L, ptype);
 }
+
+template <>
+int kernels_per_pass_d<double>(const Geom &) { return 1; }
+
+template <>
+int kernels_per_pass_d<float>(const Geom &g) { return (g.kvar == KVAR_TWO_CELL && vec_eligible(g)) ? 2 : 1; }
 
 template <>
 int prepare_stage<double>() { return prepare_f64(); }

@@ -372,6 +372,7 @@ struct pf_handle {
     long long *dcnt = nullptr;
     int *dflag = nullptr;
     int *dpartn = nullptr;             // error partials written by the last error pass
+    int *dcrowd = nullptr;             // crowded cells recorded by a two-cell pass (FP32)
     double *tot_sum = nullptr, *tot_max = nullptr;
     int tot_blocks = 0;
     bool masked = false;               // masked storage: occupancy-word planes after the fields
@@ -553,9 +554,10 @@ int run_pass(pf_handle *h, const Pass<T> &P)
         if (e != 0) return PF_EDEVICE;
         return prof_end(h);
     }
+    int nk = 1;
     int e = pfk::launch_stage<T>(h->g, P, h->stream, (const T *)h->dA, (const T *)h->dB, (const T *)h->dL,
-                                 h->dptype, tmp);
-    h->launches++;
+                                 h->dptype, tmp, &nk);
+    h->launches += nk;
     if (e != 0) return PF_EDEVICE;
     if (h->masked && P.mode != pfk::MODE_RHS) {
         // a dense pass (generic kernel) wrote these vectors: their masks are stale
@@ -576,6 +578,7 @@ Pass<T> blank_pass(pf_handle *h)
     P.a1 = 1.0;
     P.flag = h->dflag;
     P.part_n = h->dpartn;
+    P.crowd = h->dcrowd;
     P.part_sum = h->part_sum;
     P.part_cnt = h->part_cnt;
     return P;
@@ -1040,6 +1043,7 @@ struct DevCtl {
     // inputs, set by the host for each pf_step call
     double t_end, dte, tol[4];
     int integ, max_stages, order, trace_cap;
+    int kpp;                         // kernels each pass launches
     long long max_attempts;          // 0: no limit
     double *tr_dt, *tr_err;
     int *tr_s, *tr_acc;
@@ -1169,7 +1173,9 @@ __global__ void dl_ctrl(DevCtl *c, const double *dres, const long long *dcnt, co
     c->attempts++;
     c->launch_attempts++;
     c->evals += c->s + 1;
-    c->launches += 2 * (long long)c->s + 4;
+    // planning kernels and passes of stages 1..s and the error sweep, the
+    // norm and this kernel
+    c->launches += ((long long)c->s + 1) * (1 + c->kpp) + 2;
     int st = PF_OK;
     const int flag = *dflag;
     double err = 0.0;
@@ -1343,6 +1349,7 @@ int devloop(pf_handle *h, int integ, double t_end, const pf_tol *tol, const pf_s
     c.integ = integ;
     c.max_stages = o->max_stages > 0 ? o->max_stages : 1001;
     c.order = method_order(integ);
+    c.kpp = pfk::kernels_per_pass_d<T>(h->g);
     c.max_attempts = o->max_attempts;
     c.trace_cap = o->trace_cap > 0 ? o->trace_cap : 0;
     for (int k = 0; k < NBUF; ++k) c.buf[k] = h->buf[k];
@@ -1667,7 +1674,8 @@ void free_all(pf_handle *h)
     h->ev_pool.clear();
     for (int k = 0; k < NBUF; ++k) if (h->buf[k]) cudaFreeAsync(h->buf[k], h->stream);
     void *ps[] = {h->dA, h->dB, h->dL, h->dAB64, h->dptype, h->staging, h->dnz, h->part_sum, h->part_cnt,
-                  h->dres, h->dcnt, h->dflag, h->dpartn, h->tot_sum, h->tot_max, h->dl_ctl, h->dl_desc};
+                  h->dres, h->dcnt, h->dflag, h->dpartn, h->dcrowd, h->tot_sum, h->tot_max, h->dl_ctl,
+                  h->dl_desc};
     for (void *p : ps) if (p) cudaFreeAsync(p, h->stream);
     cudaStreamSynchronize(h->stream);
 }
@@ -1862,6 +1870,8 @@ int pf_create(const pf_params *p, void *cuda_stream, pf_handle **out)
     ok = ok && dmalloc(h, &h->dcnt, sizeof(long long));
     ok = ok && dmalloc(h, &h->dflag, PF_FLAG_BYTES);
     ok = ok && dmalloc(h, &h->dpartn, sizeof(int));
+    if (h->prec == 32)   // two entries of bookkeeping + one entry (block, 256-bit mask) per block
+        ok = ok && dmalloc(h, &h->dcrowd, sizeof(int) * (2 + (size_t)h->grid * (1 + pfk::VCELLS / 32)));
     ok = ok && dmalloc(h, &h->tot_sum, sizeof(double) * h->tot_blocks * NP);
     ok = ok && dmalloc(h, &h->tot_max, sizeof(double) * h->tot_blocks * NP);
     if (!ok) { cudaGetLastError(); free_all(h); delete h; return PF_ENOMEM; }
@@ -1880,6 +1890,7 @@ int pf_create(const pf_params *p, void *cuda_stream, pf_handle **out)
     st |= cudaMemcpyAsync(h->dAB64 + (size_t)N * N, h->B.data(), sizeof(double) * N * N, cudaMemcpyHostToDevice,
                           h->stream);
     st |= cudaMemsetAsync(h->dflag, 0, PF_FLAG_BYTES, h->stream);
+    if (h->dcrowd) st |= cudaMemsetAsync(h->dcrowd, 0, 2 * sizeof(int), h->stream);
     if (h->masked)
         for (int k = 0; k < NBUF; ++k)
             st |= cudaMemsetAsync(mask_plane(h, h->buf[k]), 0xff, sizeof(unsigned) * (size_t)h->Vs * h->nw,
@@ -1927,6 +1938,7 @@ int pf_footprint(const pf_params *p, long long *bytes)
     b += 3LL * p->n_phases * p->n_phases * es + p->n_phases;   // coefficient tables, phase types
     b += 2LL * p->n_phases * p->n_phases * 8;              // FP64 A and B for the energy functional
     b += tiles * 16 + 2 * tot_blocks * NF * 8 + 64;       // reduction partials
+    if (p->precision == 32) b += 4 * (2 + tiles * (1 + pfk::VCELLS / 32));   // crowded-cell record
     *bytes = b;
     return PF_OK;
 }

@@ -11,9 +11,15 @@ namespace pfk {
 // (specialised FP32 hot passes) or the generic kernel.  Returns a cudaError_t.
 // tma: tensor maps of the pass's buffers for the TMA-staged FP32 kernels
 // (nullptr: plain loads).
+// *nk (may be null) receives the number of kernels the pass launched.
 template <typename T>
 int launch_stage(const Geom &g, const Pass<T> &P, cudaStream_t st, const T *A, const T *B, const T *L,
-                 const signed char *ptype, const TmaMaps *tma);
+                 const signed char *ptype, const TmaMaps *tma, int *nk = nullptr);
+
+// Kernels one pass of the device-driven loop launches (two-cell passes add
+// the wide pass of their crowded cells).
+template <typename T>
+int kernels_per_pass_d(const Geom &g);
 
 // Launch one pass whose description (buffers, coefficients) sits in device
 // memory at dP, written there by a planning kernel before the launch runs

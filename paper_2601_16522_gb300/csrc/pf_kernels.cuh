@@ -97,6 +97,7 @@ struct Pass {
     double *rhs_pm;      // MODE_RHS: FP64 output, field f at rhs_pm + f * V
     unsigned char *nz_out; // MODE_RHS: N_z per cell (may be null)
     int *flag;           // device status words (see raise_flag)
+    int *crowd;          // two-cell passes: record of crowded cells for the wide pass
     int count_step;      // this pass completes a fixed step: count it (see count_step_done)
     // Occupancy masks (masked storage, FP32 fast path, N <= 32): bit a of a
     // cell's word is set where phase a may be nonzero; every entry whose bit

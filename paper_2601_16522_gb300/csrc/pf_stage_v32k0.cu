@@ -11,58 +11,72 @@ int launch_v32k0(const Geom &g, const Pass<float> &P, unsigned sig, cudaStream_t
     *done = true;
     if (g.dim == 2 && sig == (SIG_PROJECT)) {
         vec_kernel<2, 0, SIG_PROJECT><<<grid, VBLOCK, smv, st>>>(g, P, A, B, L, ptype);
+        wide_fix_kernel<2, 0><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(g, P, A, B, L, ptype);
         return (int)cudaGetLastError();
     }
     if (g.dim == 2 && sig == (SIG_P2 | SIG_PROJECT)) {
         vec_kernel<2, 0, SIG_P2 | SIG_PROJECT><<<grid, VBLOCK, smv, st>>>(g, P, A, B, L, ptype);
+        wide_fix_kernel<2, 0><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(g, P, A, B, L, ptype);
         return (int)cudaGetLastError();
     }
     if (g.dim == 2 && sig == (SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT)) {
         vec_kernel<2, 0, SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT><<<grid, VBLOCK, smv, st>>>(g, P, A, B, L, ptype);
+        wide_fix_kernel<2, 0><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(g, P, A, B, L, ptype);
         return (int)cudaGetLastError();
     }
     if (g.dim == 2 && sig == (SIG_R0OUT | SIG_PROJECT)) {
         vec_kernel<2, 0, SIG_R0OUT | SIG_PROJECT><<<grid, VBLOCK, smv, st>>>(g, P, A, B, L, ptype);
+        wide_fix_kernel<2, 0><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(g, P, A, B, L, ptype);
         return (int)cudaGetLastError();
     }
     if (g.dim == 2 && sig == (SIG_ERR)) {
         vec_kernel<2, 0, SIG_ERR><<<grid, VBLOCK, smv, st>>>(g, P, A, B, L, ptype);
+        wide_fix_kernel<2, 0><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(g, P, A, B, L, ptype);
         return (int)cudaGetLastError();
     }
     if (g.dim == 2 && sig == (SIG_P0 | SIG_PROJECT)) {
         vec_kernel<2, 0, SIG_P0 | SIG_PROJECT><<<grid, VBLOCK, smv, st>>>(g, P, A, B, L, ptype);
+        wide_fix_kernel<2, 0><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(g, P, A, B, L, ptype);
         return (int)cudaGetLastError();
     }
     if (g.dim == 2 && sig == (SIG_ERR | SIG_R0OUT)) {
         vec_kernel<2, 0, SIG_ERR | SIG_R0OUT><<<grid, VBLOCK, smv, st>>>(g, P, A, B, L, ptype);
+        wide_fix_kernel<2, 0><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(g, P, A, B, L, ptype);
         return (int)cudaGetLastError();
     }
     if (g.dim == 3 && sig == (SIG_PROJECT)) {
         vec_kernel<3, 0, SIG_PROJECT><<<grid, VBLOCK, smv, st>>>(g, P, A, B, L, ptype);
+        wide_fix_kernel<3, 0><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(g, P, A, B, L, ptype);
         return (int)cudaGetLastError();
     }
     if (g.dim == 3 && sig == (SIG_P2 | SIG_PROJECT)) {
         vec_kernel<3, 0, SIG_P2 | SIG_PROJECT><<<grid, VBLOCK, smv, st>>>(g, P, A, B, L, ptype);
+        wide_fix_kernel<3, 0><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(g, P, A, B, L, ptype);
         return (int)cudaGetLastError();
     }
     if (g.dim == 3 && sig == (SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT)) {
         vec_kernel<3, 0, SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT><<<grid, VBLOCK, smv, st>>>(g, P, A, B, L, ptype);
+        wide_fix_kernel<3, 0><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(g, P, A, B, L, ptype);
         return (int)cudaGetLastError();
     }
     if (g.dim == 3 && sig == (SIG_R0OUT | SIG_PROJECT)) {
         vec_kernel<3, 0, SIG_R0OUT | SIG_PROJECT><<<grid, VBLOCK, smv, st>>>(g, P, A, B, L, ptype);
+        wide_fix_kernel<3, 0><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(g, P, A, B, L, ptype);
         return (int)cudaGetLastError();
     }
     if (g.dim == 3 && sig == (SIG_ERR)) {
         vec_kernel<3, 0, SIG_ERR><<<grid, VBLOCK, smv, st>>>(g, P, A, B, L, ptype);
+        wide_fix_kernel<3, 0><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(g, P, A, B, L, ptype);
         return (int)cudaGetLastError();
     }
     if (g.dim == 3 && sig == (SIG_P0 | SIG_PROJECT)) {
         vec_kernel<3, 0, SIG_P0 | SIG_PROJECT><<<grid, VBLOCK, smv, st>>>(g, P, A, B, L, ptype);
+        wide_fix_kernel<3, 0><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(g, P, A, B, L, ptype);
         return (int)cudaGetLastError();
     }
     if (g.dim == 3 && sig == (SIG_ERR | SIG_R0OUT)) {
         vec_kernel<3, 0, SIG_ERR | SIG_R0OUT><<<grid, VBLOCK, smv, st>>>(g, P, A, B, L, ptype);
+        wide_fix_kernel<3, 0><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(g, P, A, B, L, ptype);
         return (int)cudaGetLastError();
     }
     *done = false;
@@ -77,34 +91,42 @@ int launchd_v32k0(const Geom &g, unsigned sig, const Pass<float> *dP, cudaStream
     *done = true;
     if (g.dim == 2 && sig == (SIG_R0OUT | SIG_PROJECT)) {
         vec_kernel_d<2, 0, SIG_R0OUT | SIG_PROJECT><<<grid, VBLOCK, smv, st>>>(g, dP, A, B, L, ptype);
+        wide_fix_kernel_d<2, 0><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(g, dP, A, B, L, ptype);
         return (int)cudaGetLastError();
     }
     if (g.dim == 2 && sig == (SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT)) {
         vec_kernel_d<2, 0, SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT><<<grid, VBLOCK, smv, st>>>(g, dP, A, B, L, ptype);
+        wide_fix_kernel_d<2, 0><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(g, dP, A, B, L, ptype);
         return (int)cudaGetLastError();
     }
     if (g.dim == 2 && sig == (SIG_P2 | SIG_PROJECT)) {
         vec_kernel_d<2, 0, SIG_P2 | SIG_PROJECT><<<grid, VBLOCK, smv, st>>>(g, dP, A, B, L, ptype);
+        wide_fix_kernel_d<2, 0><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(g, dP, A, B, L, ptype);
         return (int)cudaGetLastError();
     }
     if (g.dim == 2 && sig == (SIG_ERR)) {
         vec_kernel_d<2, 0, SIG_ERR><<<grid, VBLOCK, smv, st>>>(g, dP, A, B, L, ptype);
+        wide_fix_kernel_d<2, 0><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(g, dP, A, B, L, ptype);
         return (int)cudaGetLastError();
     }
     if (g.dim == 3 && sig == (SIG_R0OUT | SIG_PROJECT)) {
         vec_kernel_d<3, 0, SIG_R0OUT | SIG_PROJECT><<<grid, VBLOCK, smv, st>>>(g, dP, A, B, L, ptype);
+        wide_fix_kernel_d<3, 0><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(g, dP, A, B, L, ptype);
         return (int)cudaGetLastError();
     }
     if (g.dim == 3 && sig == (SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT)) {
         vec_kernel_d<3, 0, SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT><<<grid, VBLOCK, smv, st>>>(g, dP, A, B, L, ptype);
+        wide_fix_kernel_d<3, 0><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(g, dP, A, B, L, ptype);
         return (int)cudaGetLastError();
     }
     if (g.dim == 3 && sig == (SIG_P2 | SIG_PROJECT)) {
         vec_kernel_d<3, 0, SIG_P2 | SIG_PROJECT><<<grid, VBLOCK, smv, st>>>(g, dP, A, B, L, ptype);
+        wide_fix_kernel_d<3, 0><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(g, dP, A, B, L, ptype);
         return (int)cudaGetLastError();
     }
     if (g.dim == 3 && sig == (SIG_ERR)) {
         vec_kernel_d<3, 0, SIG_ERR><<<grid, VBLOCK, smv, st>>>(g, dP, A, B, L, ptype);
+        wide_fix_kernel_d<3, 0><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(g, dP, A, B, L, ptype);
         return (int)cudaGetLastError();
     }
     *done = false;

@@ -31,7 +31,18 @@ constexpr int VTX = 32;              // threads along x: 64 cells
 constexpr int VTY = 4;               // rows per block
 constexpr int VBLOCK = VTX * VTY;    // 128 threads
 constexpr int VCELLS = 2 * VBLOCK;   // 256 cells per block
-constexpr int VACT = 8;              // nontrivial phases per cell in the shared-memory list
+#ifndef PF_VEC_ACT
+#define PF_VEC_ACT 8
+#endif
+// Resident blocks per SM the register budget targets.
+#ifndef PF_VEC_MINB
+#define PF_VEC_MINB 5
+#endif
+// Register double buffering of the phase loads (1) or one phase at a time (0).
+#ifndef PF_VEC_DB
+#define PF_VEC_DB 1
+#endif
+constexpr int VACT = PF_VEC_ACT;     // nontrivial phases per cell in the shared-memory list
 
 // Blocks of the x-y plane of the two-cell kernels (one z plane per block).
 __host__ __device__ inline long long vec_tiles(const Geom &g)
@@ -89,8 +100,8 @@ struct VPhase {
 struct VCell {
     int nz, bestid, nc;
     float best, ssum;
-    bool changed, nzhi;
-    unsigned long long nzw;    // phases < 64 not listed whose written value is nonzero
+    bool changed;
+    int nzcnt;                 // phases not listed written with a nonzero value
     double es;                 // error partial (MODE_ERR)
     long long ec;
 };
@@ -122,12 +133,14 @@ __device__ __forceinline__ void vec_body(const Geom &g, const Pass<float> &P, co
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
         C[c].nz = 0; C[c].bestid = -1; C[c].nc = 0; C[c].best = (T)-1; C[c].ssum = (T)0;
-        C[c].changed = false; C[c].nzhi = false; C[c].nzw = 0ull; C[c].es = 0.0; C[c].ec = 0;
+        C[c].changed = false; C[c].nzcnt = 0; C[c].es = 0.0; C[c].ec = 0;
     }
     bool crowd[2] = {false, false};
     if (y < g.ny) {   // warp-uniform (a warp is one row)
         const bool here = x < g.nx;
         const int i = (z * g.ny + y) * g.nx + x;
+        // lanes past nx load the last pair of their row (in bounds, unused)
+        const int il = here ? i : (z * g.ny + y) * g.nx + (g.nx - 2);
         // y / z neighbour offsets (a zero-gradient ghost is the cell itself)
         long long off64[6];
         int ghost[6];
@@ -159,29 +172,25 @@ __device__ __forceinline__ void vec_body(const Geom &g, const Pass<float> &P, co
         }
 
         auto fetch = [&](int a, VPhase &q) {
-            const float *b = P.in + (long long)a * Vs + i;
-            q.c = q.ym = q.yp = q.zm = q.zp = make_float2(0.f, 0.f);
-            q.p0 = q.p2 = q.r0 = make_float2(0.f, 0.f);
-            q.el = q.er = 0.f;
-            if (here) {
-                if (PF_PREFETCH_DIST > 0 && a + PF_PREFETCH_DIST < N) {
-                    const long long pa = (long long)PF_PREFETCH_DIST * Vs;
-                    prefetch_l2(b + pa);
-                    if (HP0) prefetch_l2(P.p0 + (long long)a * Vs + pa + i);
-                    if (HP2) prefetch_l2(P.p2 + (long long)a * Vs + pa + i);
-                    if (HR0) prefetch_l2(P.r0in + (long long)a * Vs + pa + i);
-                }
-                q.c = ldg2(b);
-                q.ym = ldg2(b + oym);
-                q.yp = ldg2(b + oyp);
-                if (DIM == 3) {
-                    q.zm = ldg2(b + ozm);
-                    q.zp = ldg2(b + ozp);
-                }
-                if (HP0) q.p0 = ld_stream2(P.p0 + (long long)a * Vs + i);
-                if (HP2) q.p2 = ld_stream2(P.p2 + (long long)a * Vs + i);
-                if (HR0) q.r0 = ld_stream2(P.r0in + (long long)a * Vs + i);
+            const long long fo = (long long)a * Vs + il;
+            const float *b = P.in + fo;
+            if (PF_PREFETCH_DIST > 0 && a + PF_PREFETCH_DIST < N) {
+                const long long pa = (long long)PF_PREFETCH_DIST * Vs;
+                prefetch_l2(b + pa);
+                if (HP0) prefetch_l2(P.p0 + fo + pa);
+                if (HP2) prefetch_l2(P.p2 + fo + pa);
+                if (HR0) prefetch_l2(P.r0in + fo + pa);
             }
+            q.c = ldg2(b);
+            q.ym = ldg2(b + oym);
+            q.yp = ldg2(b + oyp);
+            if (DIM == 3) {
+                q.zm = ldg2(b + ozm);
+                q.zp = ldg2(b + ozp);
+            }
+            if (HP0) q.p0 = ld_stream2(P.p0 + fo);
+            if (HP2) q.p2 = ld_stream2(P.p2 + fo);
+            if (HR0) q.r0 = ld_stream2(P.r0in + fo);
             if (lneed) q.el = __ldg(b + lofs);
             if (rneed) q.er = __ldg(b + rofs);
         };
@@ -228,48 +237,66 @@ __device__ __forceinline__ void vec_body(const Geom &g, const Pass<float> &P, co
                 if (acc < (T)0) { acc = (T)0; Cc.changed = true; }
                 if (acc >= (T)1 && acc > Cc.best) { Cc.best = acc; Cc.bestid = a; }
                 Cc.ssum = Cc.ssum + acc;
-                if (acc != (T)0) {
-                    if (a < 64) Cc.nzw |= 1ull << a;
-                    else Cc.nzhi = true;
-                }
+                if (acc != (T)0) Cc.nzcnt++;
             }
             return acc;
         };
 
         // ---- the sweep over the phases ---------------------------------------
-        VPhase cur, nxt;
-        fetch(0, cur);
-#pragma unroll 1
-        for (int a = 0; a < N; ++a) {
-            if (a + 1 < N) fetch(a + 1, nxt);
-            const float sl = __shfl_up_sync(0xffffffffu, cur.c.y, 1);
-            const float sr = __shfl_down_sync(0xffffffffu, cur.c.x, 1);
-            const T left = lsh ? sl : (lself ? cur.c.x : cur.el);
-            const T right = rsh ? sr : (rself ? cur.c.y : cur.er);
+        auto process = [&](int a, const VPhase &q) {
+            const float sl = __shfl_up_sync(0xffffffffu, q.c.y, 1);
+            const float sr = __shfl_down_sync(0xffffffffu, q.c.x, 1);
+            const T left = lsh ? sl : (lself ? q.c.x : q.el);
+            const T right = rsh ? sr : (rself ? q.c.y : q.er);
+            const T zm0 = DIM == 3 ? q.zm.x : (T)0, zm1 = DIM == 3 ? q.zm.y : (T)0;
+            const T zp0 = DIM == 3 ? q.zp.x : (T)0, zp1 = DIM == 3 ? q.zp.y : (T)0;
+            const T p00 = HP0 ? q.p0.x : (T)0, p01 = HP0 ? q.p0.y : (T)0;
+            const T p20 = HP2 ? q.p2.x : (T)0, p21 = HP2 ? q.p2.y : (T)0;
+            const T r00 = HR0 ? q.r0.x : (T)0, r01 = HR0 ? q.r0.y : (T)0;
             if (here) {
-                const T w0 = cell_phase(C[0], tid, a, cur.c.x, left, cur.c.y, cur.ym.x, cur.yp.x, cur.zm.x,
-                                        cur.zp.x, cur.p0.x, cur.p2.x, cur.r0.x);
-                const T w1 = cell_phase(C[1], VBLOCK + tid, a, cur.c.y, cur.c.x, right, cur.ym.y, cur.yp.y,
-                                        cur.zm.y, cur.zp.y, cur.p0.y, cur.p2.y, cur.r0.y);
+                const T w0 = cell_phase(C[0], tid, a, q.c.x, left, q.c.y, q.ym.x, q.yp.x, zm0, zp0, p00, p20, r00);
+                const T w1 = cell_phase(C[1], VBLOCK + tid, a, q.c.y, q.c.x, right, q.ym.y, q.yp.y, zm1, zp1, p01,
+                                        p21, r01);
                 const long long fo = (long long)a * Vs + i;
                 if (!ERR) st2(P.out + fo, w0, w1);
                 if (R0OUT) st2(P.r0out + fo, (T)0, (T)0);   // listed phases get theirs below
                 if (KC) {
                     const int t = ptype[a];
                     // per-type sums: own cells, y/z neighbours, edge cells
-                    Ph[0][t] += cur.c.x;
-                    Ph[1][t] += cur.c.y;
-                    Pn[0][0][t] += cur.ym.x; Pn[1][0][t] += cur.ym.y;
-                    Pn[0][1][t] += cur.yp.x; Pn[1][1][t] += cur.yp.y;
+                    Ph[0][t] += q.c.x;
+                    Ph[1][t] += q.c.y;
+                    Pn[0][0][t] += q.ym.x; Pn[1][0][t] += q.ym.y;
+                    Pn[0][1][t] += q.yp.x; Pn[1][1][t] += q.yp.y;
                     if (DIM == 3) {
-                        Pn[0][2][t] += cur.zm.x; Pn[1][2][t] += cur.zm.y;
-                        Pn[0][3][t] += cur.zp.x; Pn[1][3][t] += cur.zp.y;
+                        Pn[0][2][t] += zm0; Pn[1][2][t] += zm1;
+                        Pn[0][3][t] += zp0; Pn[1][3][t] += zp1;
                     }
-                    Pe[0][t] += cur.el;
-                    Pe[1][t] += cur.er;
+                    if (lneed) Pe[0][t] += q.el;
+                    if (rneed) Pe[1][t] += q.er;
                 }
             }
-            cur = nxt;
+        };
+        // two phases per iteration: the loads of the next phase are in flight
+        // while the current one is processed, without register copies
+        if (PF_VEC_DB) {
+            VPhase qa, qb;
+            fetch(0, qa);
+            int a = 0;
+#pragma unroll 1
+            for (; a + 1 < N; a += 2) {
+                fetch(a + 1, qb);
+                process(a, qa);
+                if (a + 2 < N) fetch(a + 2, qa);
+                process(a + 1, qb);
+            }
+            if (a < N) process(a, qa);
+        } else {
+#pragma unroll 1
+            for (int a = 0; a < N; ++a) {
+                VPhase q;
+                fetch(a, q);
+                process(a, q);
+            }
         }
 
         // ---- concentration: mu of the cells and their neighbours, c RHS ------
@@ -429,17 +456,23 @@ __device__ __forceinline__ void vec_body(const Geom &g, const Pass<float> &P, co
             if (PROJ) {
                 if (Cc.bestid >= 0) {
                     // the winner becomes 1, the others 0: a change unless the
-                    // winner is exactly 1 and every other phase already zero
-                    bool others = (Cc.nzw & ~(Cc.bestid < 64 ? (1ull << Cc.bestid) : 0ull)) != 0ull || Cc.nzhi;
-                    for (int k = 0; k < nz; ++k)
-                        if (S.id[k][slot] != Cc.bestid && S.val[k][slot] != (T)0) others = true;
-                    if (others || Cc.best != (T)1) { Cc.changed = true; rewrite = true; }
+                    // winner is exactly 1 and every other phase already zero.
+                    // Unlisted entries need rewriting only where nonzero
+                    // (nzcnt of them, the winner among them if unlisted).
+                    bool listed = false, others = false;
+                    for (int k = 0; k < nz; ++k) {
+                        if (S.id[k][slot] == Cc.bestid) listed = true;
+                        else if (S.val[k][slot] != (T)0) others = true;
+                    }
+                    const int unl_others = Cc.nzcnt - (listed ? 0 : 1);
+                    if (others || unl_others > 0 || Cc.best != (T)1) Cc.changed = true;
+                    rewrite = unl_others > 0 || (!listed && Cc.best != (T)1);
                     Cc.ssum = (T)1;
                 }
                 if (!(Cc.ssum > (T)0)) raise_flag(P.flag, FLAG_SIMPLEX);
             }
             const T inv = (Cc.ssum > (T)0) ? (T)1 / Cc.ssum : (T)1;
-            if (PROJ && Cc.bestid < 0 && inv != (T)1) rewrite = true;
+            if (PROJ && Cc.bestid < 0 && inv != (T)1 && Cc.nzcnt > 0) rewrite = true;
             const bool fix = R0OUT && P.fix_first && Cc.changed;
             // listed phases
             for (int k = 0; k < nz; ++k) {
@@ -457,25 +490,16 @@ __device__ __forceinline__ void vec_body(const Geom &g, const Pass<float> &P, co
             // phases not listed whose written value is nonzero (rare outside
             // bulk cells): the >= 1 rule or the normalisation
             if (rewrite) {
-                for (unsigned long long m = Cc.nzw; m; m &= m - 1ull) {
-                    const int a = __ffsll((long long)m) - 1;
+                int kk = 0;
+                for (int a = 0; a < N; ++a) {
+                    if (kk < nz && S.id[kk][slot] == a) { kk++; continue; }
                     const long long fo = (long long)a * Vs + i + c;
-                    const T w = (Cc.bestid >= 0) ? ((a == Cc.bestid) ? (T)1 : (T)0) : P.out[fo] * inv;
+                    const T o = P.out[fo];
+                    if (o == (T)0) continue;
+                    const T w = (Cc.bestid >= 0) ? ((a == Cc.bestid) ? (T)1 : (T)0) : o * inv;
                     P.out[fo] = w;
                     if (fix) P.r0out[fo] = (w - __ldg(P.in + fo)) * ib1;
                 }
-                if (Cc.nzhi)
-                    for (int a = 64; a < N; ++a) {
-                        const long long fo = (long long)a * Vs + i + c;
-                        bool listed = false;
-                        for (int k = 0; k < nz; ++k) listed = listed || S.id[k][slot] == a;
-                        if (listed) continue;
-                        const T o = P.out[fo];
-                        if (o == (T)0) continue;
-                        const T w = (Cc.bestid >= 0) ? ((a == Cc.bestid) ? (T)1 : (T)0) : o * inv;
-                        P.out[fo] = w;
-                        if (fix) P.r0out[fo] = (w - __ldg(P.in + fo)) * ib1;
-                    }
             }
             if (KC) {
                 const long long o = (long long)N * Vs + i + c;
@@ -490,21 +514,109 @@ __device__ __forceinline__ void vec_body(const Geom &g, const Pass<float> &P, co
                 P.out[o] = acc;
             }
         }
-        // crowded cells: the wide path rewrites every output of the cell
+    }
+    // crowded cells (more than VACT nontrivial phases): recorded for the wide
+    // pass that follows (wide_fix_kernel); their outputs and error terms come
+    // from there.  The block appends one entry: its index and a 256-bit mask.
+    __shared__ unsigned cmask[VCELLS / 32];
+    if (tid < VCELLS / 32) cmask[tid] = 0u;
+    if (__syncthreads_or(crowd[0] || crowd[1])) {
 #pragma unroll
         for (int c = 0; c < 2; ++c)
             if (crowd[c]) {
-                C[c].es = 0.0;
-                C[c].ec = 0;
-                wide_cell<float, DIM, KC>(&g, &P, tabA, tabB, tabL, ptype, x + c, y, z, &C[c].es, &C[c].ec);
+                const int bit = ty * (2 * VTX) + 2 * lane + c;
+                atomicOr(&cmask[bit >> 5], 1u << (bit & 31));
             }
+        __syncthreads();
+        if (tid == 0) {
+            const int e = atomicAdd(P.crowd, 1);
+            int *ent = P.crowd + 2 + e * (1 + VCELLS / 32);
+            ent[0] = bid;
+#pragma unroll
+            for (int w = 0; w < VCELLS / 32; ++w) ent[1 + w] = (int)cmask[w];
+        }
     }
     if (ERR) block_partials(C[0].es + C[1].es, C[0].ec + C[1].ec, P.part_sum, P.part_cnt, bid, P.part_n);
-    if (P.count_step) count_step_done(P.flag);
+    // the step is counted by the wide pass, after the crowded cells
+}
+
+// The wide pass after a two-cell pass: every crowded cell recorded by the
+// two-cell blocks is recomputed by the generic body with the WIDEACT-entry
+// list (wide_cell), which rewrites all of that cell's outputs; the block's
+// error terms are added to its partial in a fixed order (cells ascending),
+// so the norm stays deterministic.  Blocks take the recorded entries in a
+// grid-stride loop; the last block to finish clears the record and, for a
+// pass that completes a fixed step, counts the step.  It runs after every
+// two-cell pass (with no entries it only does the bookkeeping).
+constexpr int WIDE_FIX_BLOCKS = 152;
+
+template <int DIM, int KC>
+__device__ __forceinline__ void wide_fix_body(const Geom &g, const Pass<float> &P, const float *tabA,
+                                              const float *tabB, const float *tabL, const signed char *ptype)
+{
+    const int n = *(volatile int *)P.crowd;
+    const int tid = threadIdx.x;
+    const int tiles_x = (g.nx + 2 * VTX - 1) / (2 * VTX), tiles_y = (g.ny + VTY - 1) / VTY;
+    for (int e = blockIdx.x; e < n; e += gridDim.x) {
+        const int *ent = P.crowd + 2 + e * (1 + VCELLS / 32);
+        const int b = ent[0];
+        const unsigned m = (unsigned)ent[1 + (tid >> 5)];
+        double es = 0.0;
+        long long ec = 0;
+        if ((m >> (tid & 31)) & 1u) {
+            const int bx = b % tiles_x, by = (b / tiles_x) % tiles_y, bz = b / (tiles_x * tiles_y);
+            const int x = bx * (2 * VTX) + (tid % (2 * VTX)), y = by * VTY + tid / (2 * VTX);
+            wide_cell<float, DIM, KC>(&g, &P, tabA, tabB, tabL, ptype, x, y, bz, &es, &ec);
+        }
+        if (P.mode == MODE_ERR) {
+            __shared__ double rs[VCELLS];
+            __shared__ long long rc[VCELLS];
+            rs[tid] = es;
+            rc[tid] = ec;
+            __syncthreads();
+            if (tid == 0) {
+                double s = 0.0;
+                long long c = 0;
+                for (int k = 0; k < VCELLS; ++k) { s += rs[k]; c += rc[k]; }
+                P.part_sum[b] += s;
+                P.part_cnt[b] += c;
+            }
+            __syncthreads();
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        if (atomicAdd(P.crowd + 1, 1) == (int)gridDim.x - 1) {
+            atomicExch(P.crowd, 0);
+            atomicExch(P.crowd + 1, 0);
+            if (P.count_step && !pass_skipped(P.flag)) atomicAdd(P.flag + 1, 1);
+        }
+    }
+}
+
+template <int DIM, int KC>
+__global__ void __launch_bounds__(VCELLS)
+wide_fix_kernel(const __grid_constant__ Geom g, const __grid_constant__ Pass<float> P, const float *__restrict__ tabA,
+                const float *__restrict__ tabB, const float *__restrict__ tabL, const signed char *__restrict__ ptype)
+{
+    wide_fix_body<DIM, KC>(g, P, tabA, tabB, tabL, ptype);
+}
+
+template <int DIM, int KC>
+__global__ void __launch_bounds__(VCELLS)
+wide_fix_kernel_d(const __grid_constant__ Geom g, const Pass<float> *__restrict__ Pd, const float *__restrict__ tabA,
+                  const float *__restrict__ tabB, const float *__restrict__ tabL,
+                  const signed char *__restrict__ ptype)
+{
+    __shared__ Pass<float> Ps;
+    if (threadIdx.x == 0) Ps = *Pd;
+    __syncthreads();
+    wide_fix_body<DIM, KC>(g, Ps, tabA, tabB, tabL, ptype);
 }
 
 template <int DIM, int KC, unsigned SIG>
-__global__ void __launch_bounds__(VBLOCK, KC ? 4 : 6)
+__global__ void __launch_bounds__(VBLOCK, KC ? 4 : PF_VEC_MINB)
 vec_kernel(const __grid_constant__ Geom g, const __grid_constant__ Pass<float> P, const float *__restrict__ tabA,
            const float *__restrict__ tabB, const float *__restrict__ tabL, const signed char *__restrict__ ptype)
 {
@@ -514,7 +626,7 @@ vec_kernel(const __grid_constant__ Geom g, const __grid_constant__ Pass<float> P
 // The same pass with its description read from device memory (device-driven
 // adaptive steps; see cell_kernel_d).
 template <int DIM, int KC, unsigned SIG>
-__global__ void __launch_bounds__(VBLOCK, KC ? 4 : 6)
+__global__ void __launch_bounds__(VBLOCK, KC ? 4 : PF_VEC_MINB)
 vec_kernel_d(const __grid_constant__ Geom g, const Pass<float> *__restrict__ Pd, const float *__restrict__ tabA,
              const float *__restrict__ tabB, const float *__restrict__ tabL, const signed char *__restrict__ ptype)
 {
