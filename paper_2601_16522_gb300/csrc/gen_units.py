@@ -183,17 +183,16 @@ def vunit(kc, fname):
     L.append("             const float *B, const float *L, const signed char *ptype, bool *done)")
     L.append("{")
     L.append("    const dim3 grid((g.nx + 2 * VTX - 1) / (2 * VTX), (g.ny + VTY - 1) / VTY, g.nz);")
-    L.append("    const size_t smv = sizeof(VecSmem);")
     L.append("    *done = true;")
     prep = []
     for d in (2, 3):
         for sg in FAST_SIGS:
             L.append("    if (g.dim == %d && sig == (%s)) {" % (d, sg))
-            L.append("        vec_kernel<%d, %d, %s><<<grid, VBLOCK, smv, st>>>(g, P, A, B, L, ptype);" % (d, kc, sg))
+            L.append("        vec_kernel<%d, %d, %s><<<grid, VBLOCK, vec_smem<%s>(), st>>>(g, P, A, B, L, ptype);" % (d, kc, sg, sg))
             L.append("        wide_fix_kernel<%d, %d><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(g, P, A, B, L, ptype);" % (d, kc))
             L.append("        return (int)cudaGetLastError();")
             L.append("    }")
-            prep.append("    if (cudaFuncSetAttribute(vec_kernel<%d, %d, %s>, cudaFuncAttributeMaxDynamicSharedMemorySize, smv) != cudaSuccess) return -1;" % (d, kc, sg))
+            prep.append("    if (cudaFuncSetAttribute(vec_kernel<%d, %d, %s>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vec_smem<%s>()) != cudaSuccess) return -1;" % (d, kc, sg, sg))
     L.append("    *done = false;")
     L.append("    return 0;")
     L.append("}")
@@ -202,23 +201,21 @@ def vunit(kc, fname):
     L.append("             const float *B, const float *L, const signed char *ptype, bool *done)")
     L.append("{")
     L.append("    const dim3 grid((g.nx + 2 * VTX - 1) / (2 * VTX), (g.ny + VTY - 1) / VTY, g.nz);")
-    L.append("    const size_t smv = sizeof(VecSmem);")
     L.append("    *done = true;")
     for d in (2, 3):
         for sg in DSIGS:
             L.append("    if (g.dim == %d && sig == (%s)) {" % (d, sg))
-            L.append("        vec_kernel_d<%d, %d, %s><<<grid, VBLOCK, smv, st>>>(g, dP, A, B, L, ptype);" % (d, kc, sg))
+            L.append("        vec_kernel_d<%d, %d, %s><<<grid, VBLOCK, vec_smem<%s>(), st>>>(g, dP, A, B, L, ptype);" % (d, kc, sg, sg))
             L.append("        wide_fix_kernel_d<%d, %d><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(g, dP, A, B, L, ptype);" % (d, kc))
             L.append("        return (int)cudaGetLastError();")
             L.append("    }")
-            prep.append("    if (cudaFuncSetAttribute(vec_kernel_d<%d, %d, %s>, cudaFuncAttributeMaxDynamicSharedMemorySize, smv) != cudaSuccess) return -1;" % (d, kc, sg))
+            prep.append("    if (cudaFuncSetAttribute(vec_kernel_d<%d, %d, %s>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vec_smem<%s>()) != cudaSuccess) return -1;" % (d, kc, sg, sg))
     L.append("    *done = false;")
     L.append("    return 0;")
     L.append("}")
     L.append("")
     L.append("int prepare_%s()" % tag)
     L.append("{")
-    L.append("    const int smv = (int)sizeof(VecSmem);")
     L += prep
     L.append("    return 1;")
     L.append("}")

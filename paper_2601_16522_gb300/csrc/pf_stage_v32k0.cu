@@ -7,75 +7,74 @@ int launch_v32k0(const Geom &g, const Pass<float> &P, unsigned sig, cudaStream_t
              const float *B, const float *L, const signed char *ptype, bool *done)
 {
     const dim3 grid((g.nx + 2 * VTX - 1) / (2 * VTX), (g.ny + VTY - 1) / VTY, g.nz);
-    const size_t smv = sizeof(VecSmem);
     *done = true;
     if (g.dim == 2 && sig == (SIG_PROJECT)) {
-        vec_kernel<2, 0, SIG_PROJECT><<<grid, VBLOCK, smv, st>>>(g, P, A, B, L, ptype);
+        vec_kernel<2, 0, SIG_PROJECT><<<grid, VBLOCK, vec_smem<SIG_PROJECT>(), st>>>(g, P, A, B, L, ptype);
         wide_fix_kernel<2, 0><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(g, P, A, B, L, ptype);
         return (int)cudaGetLastError();
     }
     if (g.dim == 2 && sig == (SIG_P2 | SIG_PROJECT)) {
-        vec_kernel<2, 0, SIG_P2 | SIG_PROJECT><<<grid, VBLOCK, smv, st>>>(g, P, A, B, L, ptype);
+        vec_kernel<2, 0, SIG_P2 | SIG_PROJECT><<<grid, VBLOCK, vec_smem<SIG_P2 | SIG_PROJECT>(), st>>>(g, P, A, B, L, ptype);
         wide_fix_kernel<2, 0><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(g, P, A, B, L, ptype);
         return (int)cudaGetLastError();
     }
     if (g.dim == 2 && sig == (SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT)) {
-        vec_kernel<2, 0, SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT><<<grid, VBLOCK, smv, st>>>(g, P, A, B, L, ptype);
+        vec_kernel<2, 0, SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT><<<grid, VBLOCK, vec_smem<SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT>(), st>>>(g, P, A, B, L, ptype);
         wide_fix_kernel<2, 0><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(g, P, A, B, L, ptype);
         return (int)cudaGetLastError();
     }
     if (g.dim == 2 && sig == (SIG_R0OUT | SIG_PROJECT)) {
-        vec_kernel<2, 0, SIG_R0OUT | SIG_PROJECT><<<grid, VBLOCK, smv, st>>>(g, P, A, B, L, ptype);
+        vec_kernel<2, 0, SIG_R0OUT | SIG_PROJECT><<<grid, VBLOCK, vec_smem<SIG_R0OUT | SIG_PROJECT>(), st>>>(g, P, A, B, L, ptype);
         wide_fix_kernel<2, 0><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(g, P, A, B, L, ptype);
         return (int)cudaGetLastError();
     }
     if (g.dim == 2 && sig == (SIG_ERR)) {
-        vec_kernel<2, 0, SIG_ERR><<<grid, VBLOCK, smv, st>>>(g, P, A, B, L, ptype);
+        vec_kernel<2, 0, SIG_ERR><<<grid, VBLOCK, vec_smem<SIG_ERR>(), st>>>(g, P, A, B, L, ptype);
         wide_fix_kernel<2, 0><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(g, P, A, B, L, ptype);
         return (int)cudaGetLastError();
     }
     if (g.dim == 2 && sig == (SIG_P0 | SIG_PROJECT)) {
-        vec_kernel<2, 0, SIG_P0 | SIG_PROJECT><<<grid, VBLOCK, smv, st>>>(g, P, A, B, L, ptype);
+        vec_kernel<2, 0, SIG_P0 | SIG_PROJECT><<<grid, VBLOCK, vec_smem<SIG_P0 | SIG_PROJECT>(), st>>>(g, P, A, B, L, ptype);
         wide_fix_kernel<2, 0><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(g, P, A, B, L, ptype);
         return (int)cudaGetLastError();
     }
     if (g.dim == 2 && sig == (SIG_ERR | SIG_R0OUT)) {
-        vec_kernel<2, 0, SIG_ERR | SIG_R0OUT><<<grid, VBLOCK, smv, st>>>(g, P, A, B, L, ptype);
+        vec_kernel<2, 0, SIG_ERR | SIG_R0OUT><<<grid, VBLOCK, vec_smem<SIG_ERR | SIG_R0OUT>(), st>>>(g, P, A, B, L, ptype);
         wide_fix_kernel<2, 0><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(g, P, A, B, L, ptype);
         return (int)cudaGetLastError();
     }
     if (g.dim == 3 && sig == (SIG_PROJECT)) {
-        vec_kernel<3, 0, SIG_PROJECT><<<grid, VBLOCK, smv, st>>>(g, P, A, B, L, ptype);
+        vec_kernel<3, 0, SIG_PROJECT><<<grid, VBLOCK, vec_smem<SIG_PROJECT>(), st>>>(g, P, A, B, L, ptype);
         wide_fix_kernel<3, 0><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(g, P, A, B, L, ptype);
         return (int)cudaGetLastError();
     }
     if (g.dim == 3 && sig == (SIG_P2 | SIG_PROJECT)) {
-        vec_kernel<3, 0, SIG_P2 | SIG_PROJECT><<<grid, VBLOCK, smv, st>>>(g, P, A, B, L, ptype);
+        vec_kernel<3, 0, SIG_P2 | SIG_PROJECT><<<grid, VBLOCK, vec_smem<SIG_P2 | SIG_PROJECT>(), st>>>(g, P, A, B, L, ptype);
         wide_fix_kernel<3, 0><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(g, P, A, B, L, ptype);
         return (int)cudaGetLastError();
     }
     if (g.dim == 3 && sig == (SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT)) {
-        vec_kernel<3, 0, SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT><<<grid, VBLOCK, smv, st>>>(g, P, A, B, L, ptype);
+        vec_kernel<3, 0, SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT><<<grid, VBLOCK, vec_smem<SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT>(), st>>>(g, P, A, B, L, ptype);
         wide_fix_kernel<3, 0><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(g, P, A, B, L, ptype);
         return (int)cudaGetLastError();
     }
     if (g.dim == 3 && sig == (SIG_R0OUT | SIG_PROJECT)) {
-        vec_kernel<3, 0, SIG_R0OUT | SIG_PROJECT><<<grid, VBLOCK, smv, st>>>(g, P, A, B, L, ptype);
+        vec_kernel<3, 0, SIG_R0OUT | SIG_PROJECT><<<grid, VBLOCK, vec_smem<SIG_R0OUT | SIG_PROJECT>(), st>>>(g, P, A, B, L, ptype);
         wide_fix_kernel<3, 0><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(g, P, A, B, L, ptype);
         return (int)cudaGetLastError();
     }
     if (g.dim == 3 && sig == (SIG_ERR)) {
-        vec_kernel<3, 0, SIG_ERR><<<grid, VBLOCK, smv, st>>>(g, P, A, B, L, ptype);
+        vec_kernel<3, 0, SIG_ERR><<<grid, VBLOCK, vec_smem<SIG_ERR>(), st>>>(g, P, A, B, L, ptype);
         wide_fix_kernel<3, 0><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(g, P, A, B, L, ptype);
         return (int)cudaGetLastError();
     }
     if (g.dim == 3 && sig == (SIG_P0 | SIG_PROJECT)) {
-        vec_kernel<3, 0, SIG_P0 | SIG_PROJECT><<<grid, VBLOCK, smv, st>>>(g, P, A, B, L, ptype);
+        vec_kernel<3, 0, SIG_P0 | SIG_PROJECT><<<grid, VBLOCK, vec_smem<SIG_P0 | SIG_PROJECT>(), st>>>(g, P, A, B, L, ptype);
         wide_fix_kernel<3, 0><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(g, P, A, B, L, ptype);
         return (int)cudaGetLastError();
     }
     if (g.dim == 3 && sig == (SIG_ERR | SIG_R0OUT)) {
-        vec_kernel<3, 0, SIG_ERR | SIG_R0OUT><<<grid, VBLOCK, smv, st>>>(g, P, A, B, L, ptype);
+        vec_kernel<3, 0, SIG_ERR | SIG_R0OUT><<<grid, VBLOCK, vec_smem<SIG_ERR | SIG_R0OUT>(), st>>>(g, P, A, B, L, ptype);
         wide_fix_kernel<3, 0><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(g, P, A, B, L, ptype);
         return (int)cudaGetLastError();
     }
@@ -87,45 +86,44 @@ int launchd_v32k0(const Geom &g, unsigned sig, const Pass<float> *dP, cudaStream
              const float *B, const float *L, const signed char *ptype, bool *done)
 {
     const dim3 grid((g.nx + 2 * VTX - 1) / (2 * VTX), (g.ny + VTY - 1) / VTY, g.nz);
-    const size_t smv = sizeof(VecSmem);
     *done = true;
     if (g.dim == 2 && sig == (SIG_R0OUT | SIG_PROJECT)) {
-        vec_kernel_d<2, 0, SIG_R0OUT | SIG_PROJECT><<<grid, VBLOCK, smv, st>>>(g, dP, A, B, L, ptype);
+        vec_kernel_d<2, 0, SIG_R0OUT | SIG_PROJECT><<<grid, VBLOCK, vec_smem<SIG_R0OUT | SIG_PROJECT>(), st>>>(g, dP, A, B, L, ptype);
         wide_fix_kernel_d<2, 0><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(g, dP, A, B, L, ptype);
         return (int)cudaGetLastError();
     }
     if (g.dim == 2 && sig == (SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT)) {
-        vec_kernel_d<2, 0, SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT><<<grid, VBLOCK, smv, st>>>(g, dP, A, B, L, ptype);
+        vec_kernel_d<2, 0, SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT><<<grid, VBLOCK, vec_smem<SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT>(), st>>>(g, dP, A, B, L, ptype);
         wide_fix_kernel_d<2, 0><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(g, dP, A, B, L, ptype);
         return (int)cudaGetLastError();
     }
     if (g.dim == 2 && sig == (SIG_P2 | SIG_PROJECT)) {
-        vec_kernel_d<2, 0, SIG_P2 | SIG_PROJECT><<<grid, VBLOCK, smv, st>>>(g, dP, A, B, L, ptype);
+        vec_kernel_d<2, 0, SIG_P2 | SIG_PROJECT><<<grid, VBLOCK, vec_smem<SIG_P2 | SIG_PROJECT>(), st>>>(g, dP, A, B, L, ptype);
         wide_fix_kernel_d<2, 0><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(g, dP, A, B, L, ptype);
         return (int)cudaGetLastError();
     }
     if (g.dim == 2 && sig == (SIG_ERR)) {
-        vec_kernel_d<2, 0, SIG_ERR><<<grid, VBLOCK, smv, st>>>(g, dP, A, B, L, ptype);
+        vec_kernel_d<2, 0, SIG_ERR><<<grid, VBLOCK, vec_smem<SIG_ERR>(), st>>>(g, dP, A, B, L, ptype);
         wide_fix_kernel_d<2, 0><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(g, dP, A, B, L, ptype);
         return (int)cudaGetLastError();
     }
     if (g.dim == 3 && sig == (SIG_R0OUT | SIG_PROJECT)) {
-        vec_kernel_d<3, 0, SIG_R0OUT | SIG_PROJECT><<<grid, VBLOCK, smv, st>>>(g, dP, A, B, L, ptype);
+        vec_kernel_d<3, 0, SIG_R0OUT | SIG_PROJECT><<<grid, VBLOCK, vec_smem<SIG_R0OUT | SIG_PROJECT>(), st>>>(g, dP, A, B, L, ptype);
         wide_fix_kernel_d<3, 0><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(g, dP, A, B, L, ptype);
         return (int)cudaGetLastError();
     }
     if (g.dim == 3 && sig == (SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT)) {
-        vec_kernel_d<3, 0, SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT><<<grid, VBLOCK, smv, st>>>(g, dP, A, B, L, ptype);
+        vec_kernel_d<3, 0, SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT><<<grid, VBLOCK, vec_smem<SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT>(), st>>>(g, dP, A, B, L, ptype);
         wide_fix_kernel_d<3, 0><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(g, dP, A, B, L, ptype);
         return (int)cudaGetLastError();
     }
     if (g.dim == 3 && sig == (SIG_P2 | SIG_PROJECT)) {
-        vec_kernel_d<3, 0, SIG_P2 | SIG_PROJECT><<<grid, VBLOCK, smv, st>>>(g, dP, A, B, L, ptype);
+        vec_kernel_d<3, 0, SIG_P2 | SIG_PROJECT><<<grid, VBLOCK, vec_smem<SIG_P2 | SIG_PROJECT>(), st>>>(g, dP, A, B, L, ptype);
         wide_fix_kernel_d<3, 0><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(g, dP, A, B, L, ptype);
         return (int)cudaGetLastError();
     }
     if (g.dim == 3 && sig == (SIG_ERR)) {
-        vec_kernel_d<3, 0, SIG_ERR><<<grid, VBLOCK, smv, st>>>(g, dP, A, B, L, ptype);
+        vec_kernel_d<3, 0, SIG_ERR><<<grid, VBLOCK, vec_smem<SIG_ERR>(), st>>>(g, dP, A, B, L, ptype);
         wide_fix_kernel_d<3, 0><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(g, dP, A, B, L, ptype);
         return (int)cudaGetLastError();
     }
@@ -135,29 +133,28 @@ int launchd_v32k0(const Geom &g, unsigned sig, const Pass<float> *dP, cudaStream
 
 int prepare_v32k0()
 {
-    const int smv = (int)sizeof(VecSmem);
-    if (cudaFuncSetAttribute(vec_kernel<2, 0, SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smv) != cudaSuccess) return -1;
-    if (cudaFuncSetAttribute(vec_kernel<2, 0, SIG_P2 | SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smv) != cudaSuccess) return -1;
-    if (cudaFuncSetAttribute(vec_kernel<2, 0, SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smv) != cudaSuccess) return -1;
-    if (cudaFuncSetAttribute(vec_kernel<2, 0, SIG_R0OUT | SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smv) != cudaSuccess) return -1;
-    if (cudaFuncSetAttribute(vec_kernel<2, 0, SIG_ERR>, cudaFuncAttributeMaxDynamicSharedMemorySize, smv) != cudaSuccess) return -1;
-    if (cudaFuncSetAttribute(vec_kernel<2, 0, SIG_P0 | SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smv) != cudaSuccess) return -1;
-    if (cudaFuncSetAttribute(vec_kernel<2, 0, SIG_ERR | SIG_R0OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smv) != cudaSuccess) return -1;
-    if (cudaFuncSetAttribute(vec_kernel<3, 0, SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smv) != cudaSuccess) return -1;
-    if (cudaFuncSetAttribute(vec_kernel<3, 0, SIG_P2 | SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smv) != cudaSuccess) return -1;
-    if (cudaFuncSetAttribute(vec_kernel<3, 0, SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smv) != cudaSuccess) return -1;
-    if (cudaFuncSetAttribute(vec_kernel<3, 0, SIG_R0OUT | SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smv) != cudaSuccess) return -1;
-    if (cudaFuncSetAttribute(vec_kernel<3, 0, SIG_ERR>, cudaFuncAttributeMaxDynamicSharedMemorySize, smv) != cudaSuccess) return -1;
-    if (cudaFuncSetAttribute(vec_kernel<3, 0, SIG_P0 | SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smv) != cudaSuccess) return -1;
-    if (cudaFuncSetAttribute(vec_kernel<3, 0, SIG_ERR | SIG_R0OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smv) != cudaSuccess) return -1;
-    if (cudaFuncSetAttribute(vec_kernel_d<2, 0, SIG_R0OUT | SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smv) != cudaSuccess) return -1;
-    if (cudaFuncSetAttribute(vec_kernel_d<2, 0, SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smv) != cudaSuccess) return -1;
-    if (cudaFuncSetAttribute(vec_kernel_d<2, 0, SIG_P2 | SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smv) != cudaSuccess) return -1;
-    if (cudaFuncSetAttribute(vec_kernel_d<2, 0, SIG_ERR>, cudaFuncAttributeMaxDynamicSharedMemorySize, smv) != cudaSuccess) return -1;
-    if (cudaFuncSetAttribute(vec_kernel_d<3, 0, SIG_R0OUT | SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smv) != cudaSuccess) return -1;
-    if (cudaFuncSetAttribute(vec_kernel_d<3, 0, SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smv) != cudaSuccess) return -1;
-    if (cudaFuncSetAttribute(vec_kernel_d<3, 0, SIG_P2 | SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smv) != cudaSuccess) return -1;
-    if (cudaFuncSetAttribute(vec_kernel_d<3, 0, SIG_ERR>, cudaFuncAttributeMaxDynamicSharedMemorySize, smv) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(vec_kernel<2, 0, SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vec_smem<SIG_PROJECT>()) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(vec_kernel<2, 0, SIG_P2 | SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vec_smem<SIG_P2 | SIG_PROJECT>()) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(vec_kernel<2, 0, SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vec_smem<SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT>()) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(vec_kernel<2, 0, SIG_R0OUT | SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vec_smem<SIG_R0OUT | SIG_PROJECT>()) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(vec_kernel<2, 0, SIG_ERR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vec_smem<SIG_ERR>()) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(vec_kernel<2, 0, SIG_P0 | SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vec_smem<SIG_P0 | SIG_PROJECT>()) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(vec_kernel<2, 0, SIG_ERR | SIG_R0OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vec_smem<SIG_ERR | SIG_R0OUT>()) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(vec_kernel<3, 0, SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vec_smem<SIG_PROJECT>()) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(vec_kernel<3, 0, SIG_P2 | SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vec_smem<SIG_P2 | SIG_PROJECT>()) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(vec_kernel<3, 0, SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vec_smem<SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT>()) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(vec_kernel<3, 0, SIG_R0OUT | SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vec_smem<SIG_R0OUT | SIG_PROJECT>()) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(vec_kernel<3, 0, SIG_ERR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vec_smem<SIG_ERR>()) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(vec_kernel<3, 0, SIG_P0 | SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vec_smem<SIG_P0 | SIG_PROJECT>()) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(vec_kernel<3, 0, SIG_ERR | SIG_R0OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vec_smem<SIG_ERR | SIG_R0OUT>()) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(vec_kernel_d<2, 0, SIG_R0OUT | SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vec_smem<SIG_R0OUT | SIG_PROJECT>()) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(vec_kernel_d<2, 0, SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vec_smem<SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT>()) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(vec_kernel_d<2, 0, SIG_P2 | SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vec_smem<SIG_P2 | SIG_PROJECT>()) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(vec_kernel_d<2, 0, SIG_ERR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vec_smem<SIG_ERR>()) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(vec_kernel_d<3, 0, SIG_R0OUT | SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vec_smem<SIG_R0OUT | SIG_PROJECT>()) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(vec_kernel_d<3, 0, SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vec_smem<SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT>()) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(vec_kernel_d<3, 0, SIG_P2 | SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vec_smem<SIG_P2 | SIG_PROJECT>()) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(vec_kernel_d<3, 0, SIG_ERR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vec_smem<SIG_ERR>()) != cudaSuccess) return -1;
     return 1;
 }
 

@@ -31,18 +31,35 @@ constexpr int VTX = 32;              // threads along x: 64 cells
 constexpr int VTY = 4;               // rows per block
 constexpr int VBLOCK = VTX * VTY;    // 128 threads
 constexpr int VCELLS = 2 * VBLOCK;   // 256 cells per block
+// List capacity per cell: passes with two extra pointwise streams (RKL2 body)
+// run fewer blocks per SM and keep 8 entries; the lighter passes keep 6 so
+// that more blocks fit in shared memory (a cell with more goes to the wide
+// pass; in grain growth fewer than 0.05 % of cells have more than 6).
 #ifndef PF_VEC_ACT
 #define PF_VEC_ACT 8
+#endif
+#ifndef PF_VEC_ACT_LIGHT
+#define PF_VEC_ACT_LIGHT 6
 #endif
 // Resident blocks per SM the register budget targets.
 #ifndef PF_VEC_MINB
 #define PF_VEC_MINB 5
 #endif
+#ifndef PF_VEC_MINB_LIGHT
+#define PF_VEC_MINB_LIGHT 7
+#endif
+// Phases ahead whose planes are prefetched into L2 (0: none).
+#ifndef PF_VEC_PREFETCH
+#define PF_VEC_PREFETCH 4
+#endif
+// ... for the passes with fewer pointwise streams
+#ifndef PF_VEC_PREFETCH_LIGHT
+#define PF_VEC_PREFETCH_LIGHT 0
+#endif
 // Register double buffering of the phase loads (1) or one phase at a time (0).
 #ifndef PF_VEC_DB
 #define PF_VEC_DB 1
 #endif
-constexpr int VACT = PF_VEC_ACT;     // nontrivial phases per cell in the shared-memory list
 
 // Blocks of the x-y plane of the two-cell kernels (one z plane per block).
 __host__ __device__ inline long long vec_tiles(const Geom &g)
@@ -56,13 +73,25 @@ __host__ __device__ inline bool vec_eligible(const Geom &g)
     return (g.nx % 2) == 0 && g.N <= 128 && g.V < 0x7fffffffLL;
 }
 
+// Whether a pass is one of the heavy ones (two extra pointwise streams).
+template <unsigned SIG>
+__host__ __device__ constexpr bool vec_heavy() { return (SIG & (SIG_P0 | SIG_P2)) == (SIG_P0 | SIG_P2); }
+
+template <unsigned SIG>
+__host__ __device__ constexpr int vec_act() { return vec_heavy<SIG>() ? PF_VEC_ACT : PF_VEC_ACT_LIGHT; }
+
+template <int ACT>
 struct VecSmem {
-    unsigned char id[VACT][VCELLS];
-    float lap[VACT][VCELLS];   // Laplacian, later the RHS of the listed phase
-    float cen[VACT][VCELLS];   // phi at the cell
-    float dl[VACT][VCELLS];    // variational derivative
-    float val[VACT][VCELLS];   // stage value before the RHS term
+    unsigned char id[ACT][VCELLS];
+    float lap[ACT][VCELLS];    // Laplacian, later the RHS of the listed phase
+    float cen[ACT][VCELLS];    // phi at the cell
+    float dl[ACT][VCELLS];     // variational derivative
+    float val[ACT][VCELLS];    // stage value before the RHS term
 };
+
+// Dynamic shared memory of a two-cell pass.
+template <unsigned SIG>
+__host__ __device__ constexpr size_t vec_smem() { return sizeof(VecSmem<vec_act<SIG>()>); }
 
 __device__ __forceinline__ float2 ldg2(const float *p) { return __ldg(reinterpret_cast<const float2 *>(p)); }
 
@@ -120,7 +149,8 @@ __device__ __forceinline__ void vec_body(const Geom &g, const Pass<float> &P, co
     constexpr bool PROJ = (SIG & SIG_PROJECT) != 0;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     if (pass_skipped(P.flag)) return;
-    VecSmem &S = *reinterpret_cast<VecSmem *>(smem_raw);
+    constexpr int VACT = vec_act<SIG>();   // nontrivial phases per cell in the shared-memory list
+    VecSmem<VACT> &S = *reinterpret_cast<VecSmem<VACT> *>(smem_raw);
     const int tid = threadIdx.x;
     const int lane = tid & 31, ty = tid >> 5;
     const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
@@ -171,28 +201,33 @@ __device__ __forceinline__ void vec_body(const Geom &g, const Pass<float> &P, co
             for (int f = 0; f < 4; ++f) Pn[0][f][t] = Pn[1][f][t] = (T)0;
         }
 
+        // per-thread 32-bit element offsets inside a phase plane; the phase
+        // bases below are the same for every thread (uniform)
+        const int oc = il, oym_ = il + oym, oyp_ = il + oyp, ozm_ = il + ozm, ozp_ = il + ozp;
+        const int oel = il + lofs, oer = il + rofs;
         auto fetch = [&](int a, VPhase &q) {
-            const long long fo = (long long)a * Vs + il;
-            const float *b = P.in + fo;
-            if (PF_PREFETCH_DIST > 0 && a + PF_PREFETCH_DIST < N) {
-                const long long pa = (long long)PF_PREFETCH_DIST * Vs;
-                prefetch_l2(b + pa);
-                if (HP0) prefetch_l2(P.p0 + fo + pa);
-                if (HP2) prefetch_l2(P.p2 + fo + pa);
-                if (HR0) prefetch_l2(P.r0in + fo + pa);
+            const long long pb = (long long)a * Vs;
+            const float *b = P.in + pb;
+            constexpr int PD = (HP0 && HP2) ? PF_VEC_PREFETCH : PF_VEC_PREFETCH_LIGHT;
+            if (PD > 0 && a + PD < N) {
+                const long long pa = pb + (long long)PD * Vs;
+                prefetch_l2(P.in + pa + oc);
+                if (HP0) prefetch_l2(P.p0 + pa + oc);
+                if (HP2) prefetch_l2(P.p2 + pa + oc);
+                if (HR0) prefetch_l2(P.r0in + pa + oc);
             }
-            q.c = ldg2(b);
-            q.ym = ldg2(b + oym);
-            q.yp = ldg2(b + oyp);
+            q.c = ldg2(b + oc);
+            q.ym = ldg2(b + oym_);
+            q.yp = ldg2(b + oyp_);
             if (DIM == 3) {
-                q.zm = ldg2(b + ozm);
-                q.zp = ldg2(b + ozp);
+                q.zm = ldg2(b + ozm_);
+                q.zp = ldg2(b + ozp_);
             }
-            if (HP0) q.p0 = ld_stream2(P.p0 + fo);
-            if (HP2) q.p2 = ld_stream2(P.p2 + fo);
-            if (HR0) q.r0 = ld_stream2(P.r0in + fo);
-            if (lneed) q.el = __ldg(b + lofs);
-            if (rneed) q.er = __ldg(b + rofs);
+            if (HP0) q.p0 = ld_stream2(P.p0 + pb + oc);
+            if (HP2) q.p2 = ld_stream2(P.p2 + pb + oc);
+            if (HR0) q.r0 = ld_stream2(P.r0in + pb + oc);
+            if (lneed) q.el = __ldg(b + oel);
+            if (rneed) q.er = __ldg(b + oer);
         };
 
         // one phase at one cell: activity, list entry, stage value (returned)
@@ -257,9 +292,9 @@ __device__ __forceinline__ void vec_body(const Geom &g, const Pass<float> &P, co
                 const T w0 = cell_phase(C[0], tid, a, q.c.x, left, q.c.y, q.ym.x, q.yp.x, zm0, zp0, p00, p20, r00);
                 const T w1 = cell_phase(C[1], VBLOCK + tid, a, q.c.y, q.c.x, right, q.ym.y, q.yp.y, zm1, zp1, p01,
                                         p21, r01);
-                const long long fo = (long long)a * Vs + i;
-                if (!ERR) st2(P.out + fo, w0, w1);
-                if (R0OUT) st2(P.r0out + fo, (T)0, (T)0);   // listed phases get theirs below
+                const long long pb = (long long)a * Vs;
+                if (!ERR) st2(P.out + pb + i, w0, w1);
+                if (R0OUT) st2(P.r0out + pb + i, (T)0, (T)0);   // listed phases get theirs below
                 if (KC) {
                     const int t = ptype[a];
                     // per-type sums: own cells, y/z neighbours, edge cells
@@ -615,8 +650,16 @@ wide_fix_kernel_d(const __grid_constant__ Geom g, const Pass<float> *__restrict_
     wide_fix_body<DIM, KC>(g, Ps, tabA, tabB, tabL, ptype);
 }
 
+// Resident blocks per SM by pass: the passes with fewer pointwise streams
+// fit a smaller register budget.
+template <int KC, unsigned SIG>
+__host__ __device__ constexpr int vec_minb()
+{
+    return KC ? 4 : (vec_heavy<SIG>() ? PF_VEC_MINB : PF_VEC_MINB_LIGHT);
+}
+
 template <int DIM, int KC, unsigned SIG>
-__global__ void __launch_bounds__(VBLOCK, KC ? 4 : PF_VEC_MINB)
+__global__ void __launch_bounds__(VBLOCK, (vec_minb<KC, SIG>()))
 vec_kernel(const __grid_constant__ Geom g, const __grid_constant__ Pass<float> P, const float *__restrict__ tabA,
            const float *__restrict__ tabB, const float *__restrict__ tabL, const signed char *__restrict__ ptype)
 {
@@ -626,7 +669,7 @@ vec_kernel(const __grid_constant__ Geom g, const __grid_constant__ Pass<float> P
 // The same pass with its description read from device memory (device-driven
 // adaptive steps; see cell_kernel_d).
 template <int DIM, int KC, unsigned SIG>
-__global__ void __launch_bounds__(VBLOCK, KC ? 4 : PF_VEC_MINB)
+__global__ void __launch_bounds__(VBLOCK, (vec_minb<KC, SIG>()))
 vec_kernel_d(const __grid_constant__ Geom g, const Pass<float> *__restrict__ Pd, const float *__restrict__ tabA,
              const float *__restrict__ tabB, const float *__restrict__ tabL, const signed char *__restrict__ ptype)
 {
