@@ -25,6 +25,7 @@
  */
 #ifndef PF_H
 #define PF_H
+#include <stddef.h>
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -346,6 +347,62 @@ int pf_totals_noalloc(const double *u_dev, int n_fields, long long n_cells, doub
    tables and reduction partials), without allocating anything.  Used to
    admit simulations by memory footprint. */
 int pf_footprint(const pf_params *params, long long *bytes);
+
+/* Caller-supplied device allocator (Sec. "Ownership" of this interface: the
+   library's device buffers may come from the caller, e.g. a framework's
+   caching allocator).  alloc(bytes, cuda_stream, ctx) returns device memory
+   of the current device usable on cuda_stream (the handle's stream), or NULL
+   (pf_create then returns PF_ENOMEM); free(ptr, bytes, cuda_stream, ctx)
+   takes back exactly what alloc returned, after the library has synchronised
+   the stream.  pf_set_allocator sets the hook for the handles created after
+   it (each handle keeps the hook it was created with until pf_destroy);
+   alloc = free = NULL restores the default, CUDA's stream-ordered allocator.
+   Process-wide, thread-safe.  PF_EINVAL when only one of the two is NULL. */
+typedef void *(*pf_alloc_fn)(size_t bytes, void *cuda_stream, void *ctx);
+typedef void (*pf_free_fn)(void *ptr, size_t bytes, void *cuda_stream, void *ctx);
+int pf_set_allocator(pf_alloc_fn alloc, pf_free_fn free_fn, void *ctx);
+
+/* Batched stepping for serving (continuous batching).  A batch advances
+   many simulations together on its own CUDA stream: every round each
+   admitted request takes one step (fixed steps) or one attempt (adaptive
+   RKL1/RKL2, Sec. 3.3), and the passes of all requests are issued wave by
+   wave, the passes of one kind (dimension, concentration field, pass
+   signature) of FP32 dense problems with nx even in ONE packed launch whose
+   blocks map to the problems (each block runs exactly what the problem's own
+   launch would, so results equal those of pf_step on the handle alone).  The
+   error norms and device flags of all requests come back in one transfer per
+   round.  Requests that cannot be packed (FP64, masked or TMA storage, odd
+   nx, SSP(10)4) launch their passes on their own handle's stream in the same
+   round.  Every request keeps the bookkeeping of pf_step (fixed steps end at
+   t0 + k dt, the controller state carries over), so its result equals that
+   of pf_step on the handle alone (options of pf_step_opts other than
+   ssp_stages, dt_mult, dt0 and max_stages are ignored).  Device memory: a request holds its handle's pf_footprint against
+   the batch's budget max_bytes from admission until its result is taken.
+
+   pf_batch_create: a batch with a budget of max_bytes (> 0) working on
+   cuda_stream (NULL: the default stream).
+   pf_batch_admit: add handle h (state set, not in another batch) to step to
+   t_end with integ, tol and opts as pf_step would; *slot receives the
+   request's slot.  PF_ENOMEM when the footprint does not fit the remaining
+   budget (nothing changes: admit it later), PF_EINVAL for arguments pf_step
+   would refuse.  The handle must not be used outside the batch until its
+   result has been taken.
+   pf_batch_run: up to `rounds` rounds (>= 1); *n_active (may be NULL)
+   receives the number of requests still running.  Synchronises the batch's
+   stream once per round.
+   pf_batch_result: *done = 1 and the request's status and statistics
+   (stats may be NULL) once it has finished or failed; its slot and budget
+   are then released and the handle is free again (its stream ordered after
+   the batch's work).  *done = 0 while it runs.
+   pf_batch_destroy: drops every request (handles stay valid) and frees the
+   batch.  NULL is accepted. */
+typedef struct pf_batch pf_batch;
+int pf_batch_create(long long max_bytes, void *cuda_stream, pf_batch **out);
+int pf_batch_admit(pf_batch *b, struct pf_handle *h, pf_integrator integ, double t_end, const pf_tol *tol,
+                   const pf_step_opts *opts, int *slot);
+int pf_batch_run(pf_batch *b, int rounds, int *n_active);
+int pf_batch_result(pf_batch *b, int slot, int *done, int *status, pf_stats *stats);
+int pf_batch_destroy(pf_batch *b);
 
 /* Release every device buffer of the handle.  NULL is accepted. */
 int pf_destroy(struct pf_handle *h);

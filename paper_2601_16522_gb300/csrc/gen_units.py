@@ -214,6 +214,23 @@ def vunit(kc, fname):
     L.append("    return 0;")
     L.append("}")
     L.append("")
+    # packed launches of several problems (batched serving)
+    L.append("int launchp_%s(int dim, unsigned sig, const VecInst *tab, const int *bstart, int n, int blocks, int *done," % tag)
+    L.append("             cudaStream_t st, bool *ok)")
+    L.append("{")
+    L.append("    *ok = true;")
+    for d in (2, 3):
+        for sg in FAST_SIGS:
+            L.append("    if (dim == %d && sig == (%s)) {" % (d, sg))
+            L.append("        packed_kernel<%d, %d, %s><<<blocks, VBLOCK, vec_smem<%s>(), st>>>(tab, bstart, n);" % (d, kc, sg, sg))
+            L.append("        packed_wide_fix_kernel<%d, %d><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(tab, n, done);" % (d, kc))
+            L.append("        return (int)cudaGetLastError();")
+            L.append("    }")
+            prep.append("    if (cudaFuncSetAttribute(packed_kernel<%d, %d, %s>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vec_smem<%s>()) != cudaSuccess) return -1;" % (d, kc, sg, sg))
+    L.append("    *ok = false;")
+    L.append("    return 0;")
+    L.append("}")
+    L.append("")
     L.append("int prepare_%s()" % tag)
     L.append("{")
     L += prep

@@ -27,6 +27,8 @@ int launchd_v32k0(const Geom &, unsigned, const Pass<float> *, cudaStream_t, con
                   const float *, const signed char *, bool *);
 int launchd_v32k1(const Geom &, unsigned, const Pass<float> *, cudaStream_t, const float *, const float *,
                   const float *, const signed char *, bool *);
+int launchp_v32k0(int, unsigned, const VecInst *, const int *, int, int, int *, cudaStream_t, bool *);
+int launchp_v32k1(int, unsigned, const VecInst *, const int *, int, int, int *, cudaStream_t, bool *);
 int prepare_v32k0();
 int prepare_v32k1();
 int prepare_f64();
@@ -96,6 +98,13 @@ int launch_stage_d<float>(const Geom &g, unsigned sig, const Pass<float> *dP, cu
         if (done) return e;
     }
     return g.K ? launchd_f32k1(g, sig, dP, st, A, B, L, ptype) : launchd_f32k0(g, sig, dP, st, A, B, L, ptype);
+}
+
+int launch_packed(int dim, int K, unsigned sig, const VecInst *tab, const int *bstart, int n, int blocks, int *done,
+                  cudaStream_t st, bool *ok)
+{
+    return K ? launchp_v32k1(dim, sig, tab, bstart, n, blocks, done, st, ok)
+             : launchp_v32k0(dim, sig, tab, bstart, n, blocks, done, st, ok);
 }
 
 template <>

@@ -347,8 +347,20 @@ energy_kernel(const Geom g, const T *__restrict__ u, const double *__restrict__ 
 // handle
 // ---------------------------------------------------------------------------
 
+// Caller-supplied device allocator (pf_set_allocator).
+struct AllocHook {
+    pf_alloc_fn alloc = nullptr;
+    pf_free_fn free = nullptr;
+    void *ctx = nullptr;
+};
+
 struct pf_handle {
     int dev = 0;
+    AllocHook hook;                    // allocator captured at pf_create (empty: stream-ordered CUDA)
+    std::vector<std::pair<void *, size_t>> allocs;   // every device allocation and its size
+    long long footprint = 0;           // pf_footprint of the parameters (batch admission)
+    std::vector<Pass<float>> *collect = nullptr;   // batch mode: FP32 passes recorded, not launched
+    bool in_batch = false;
     cudaStream_t stream = nullptr;
     int prec = 64;
     size_t esize = 8;
@@ -524,6 +536,13 @@ int run_pass(pf_handle *h, const Pass<T> &P)
     if (P.mode == pfk::MODE_STAGE &&
         fabs(P.a1 + (P.p0 ? P.a0 : 0.0) + (P.p2 ? P.a2 : 0.0) - 1.0) > 1e-12)
         return PF_EINVAL;
+    if constexpr (sizeof(T) == 4) {
+        // batch mode: the pass is recorded for a packed launch
+        if (h->collect) {
+            h->collect->push_back(P);
+            return PF_OK;
+        }
+    }
     int st = prof_begin(h);
     if (st) return st;
     pfk::TmaMaps tm;
@@ -1038,6 +1057,7 @@ constexpr int DL_CAP = 256;
 
 template <typename P>
 bool dmalloc(pf_handle *h, P **p, size_t bytes);
+void dfree(pf_handle *h, void *p);
 
 struct DevCtl {
     // inputs, set by the host for each pf_step call
@@ -1396,7 +1416,7 @@ int devloop(pf_handle *h, int integ, double t_end, const pf_tol *tol, const pf_s
         if (o->trace_err) okc = okc && cudaMemcpyAsync(o->trace_err, c.tr_err, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream) == cudaSuccess;
         if (o->trace_s) okc = okc && cudaMemcpyAsync(o->trace_s, c.tr_s, n * sizeof(int), cudaMemcpyDeviceToHost, h->stream) == cudaSuccess;
         if (o->trace_acc) okc = okc && cudaMemcpyAsync(o->trace_acc, c.tr_acc, n * sizeof(int), cudaMemcpyDeviceToHost, h->stream) == cudaSuccess;
-        cudaFreeAsync(trbuf, h->stream);
+        dfree(h, trbuf);
         if (cudaStreamSynchronize(h->stream) != cudaSuccess || !okc) st = st ? st : PF_EDEVICE;
     }
     if (o->trace_len) *o->trace_len = c.ntr;
@@ -1422,6 +1442,40 @@ int devloop(pf_handle *h, int integ, double t_end, const pf_tol *tol, const pf_s
         stats->kernel_launches = c.launches;
     }
     return st;
+}
+
+// Size *hs (in: the proposal), stage count and "lands on t_end" flag of the
+// next attempt (Sec. 3.2 stage rule; Sec. 5 output times): an adaptive
+// proposal within 1e-9 of the remaining time rem is stretched onto it; fixed
+// step kfix + 1 of nfix, the last shortened onto t_end; an RKL step needing
+// more than max_stages stages is refused (fixed) or cut to the largest step
+// max_stages (rounded up to odd) allows (adaptive).
+int plan_attempt(const pf_handle *h, int integ, bool adaptive, double rem, long long kfix, long long nfix,
+                 int ssp_stages, int max_stages, double *hs, int *s, bool *last)
+{
+    const bool sts = (integ == PF_RKL1 || integ == PF_RKL2);
+    *last = false;
+    if (adaptive) {
+        if (*hs >= rem * (1.0 - 1e-9)) { *hs = rem; *last = true; }
+    } else {
+        *last = (kfix + 1 >= nfix);
+        if (*last) *hs = rem;
+    }
+    *s = 1;
+    if (sts) {
+        *s = sts_stages(integ, *hs, h->dte);
+        if (*s > max_stages && !adaptive) return PF_EINVAL;
+        if (*s > max_stages) {
+            *s = max_stages | 1;
+            *hs = sts_max_dt(integ, *s, h->dte);
+            *last = false;
+        }
+    } else if (integ == PF_SSP2) {
+        *s = ssp_stages;
+    } else if (integ == PF_SSP104) {
+        *s = 10;
+    }
+    return PF_OK;
 }
 
 template <typename T>
@@ -1488,29 +1542,12 @@ int step_loop(pf_handle *h, int integ, double t_end, const pf_tol *tol, const pf
                 continue;
             }
         }
-        const double rem = t_end - h->t;
         double hs = dt;
         bool last = false;
-        if (adaptive) {
-            if (hs >= rem * (1.0 - 1e-9)) { hs = rem; last = true; }
-        } else {
-            last = (kfix + 1 >= nfix);
-            if (last) hs = rem;
-        }
         int s = 1;
-        if (sts) {
-            s = sts_stages(integ, hs, h->dte);
-            if (s > max_stages && !adaptive) { status = PF_EINVAL; break; }
-            if (s > max_stages) {
-                s = max_stages | 1;
-                hs = sts_max_dt(integ, s, h->dte);
-                last = false;
-            }
-        } else if (integ == PF_SSP2) {
-            s = o->ssp_stages;
-        } else if (integ == PF_SSP104) {
-            s = 10;
-        }
+        if ((status = plan_attempt(h, integ, adaptive, t_end - h->t, kfix, nfix, o->ssp_stages, max_stages, &hs, &s,
+                                   &last)))
+            break;
         int cand = -1;
         if ((status = do_step<T>(h, integ, hs, s, tol, adaptive, &cand, &evals))) break;
         attempts++;
@@ -1643,16 +1680,39 @@ int totals_t(pf_handle *h)
     return cuda_status(cudaGetLastError());
 }
 
-// Device memory comes from the stream-ordered allocator on the handle's
-// stream: creating and destroying handles then does not synchronise the
-// device, so other simulations keep running while one is set up or torn down.
+// Device memory comes from the caller's allocator hook when one was set
+// (pf_set_allocator, captured at pf_create), else from the stream-ordered
+// allocator on the handle's stream: creating and destroying handles then
+// does not synchronise the device, so other simulations keep running while
+// one is set up or torn down.  Every allocation is recorded with its size
+// and released through the same route.
 template <typename P>
 bool dmalloc(pf_handle *h, P **p, size_t bytes)
 {
     void *q = nullptr;
-    if (cudaMallocAsync(&q, bytes, h->stream) != cudaSuccess) { cudaGetLastError(); return false; }
+    if (h->hook.alloc) {
+        q = h->hook.alloc(bytes, (void *)h->stream, h->hook.ctx);
+        if (!q) return false;
+    } else if (cudaMallocAsync(&q, bytes, h->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    h->allocs.push_back(std::make_pair(q, bytes));
     *p = static_cast<P *>(q);
     return true;
+}
+
+void dfree(pf_handle *h, void *p)
+{
+    if (!p) return;
+    for (size_t k = 0; k < h->allocs.size(); ++k)
+        if (h->allocs[k].first == p) {
+            const size_t bytes = h->allocs[k].second;
+            h->allocs.erase(h->allocs.begin() + k);
+            if (h->hook.free) h->hook.free(p, bytes, (void *)h->stream, h->hook.ctx);
+            else cudaFreeAsync(p, h->stream);
+            return;
+        }
 }
 
 int ensure_staging(pf_handle *h)
@@ -1672,16 +1732,17 @@ void free_all(pf_handle *h)
     h->dl_graph = nullptr;
     for (cudaEvent_t ev : h->ev_pool) cudaEventDestroy(ev);
     h->ev_pool.clear();
-    for (int k = 0; k < NBUF; ++k) if (h->buf[k]) cudaFreeAsync(h->buf[k], h->stream);
-    void *ps[] = {h->dA, h->dB, h->dL, h->dAB64, h->dptype, h->staging, h->dnz, h->part_sum, h->part_cnt,
-                  h->dres, h->dcnt, h->dflag, h->dpartn, h->dcrowd, h->tot_sum, h->tot_max, h->dl_ctl,
-                  h->dl_desc};
-    for (void *p : ps) if (p) cudaFreeAsync(p, h->stream);
+    // the stream's work must be done before a caller's allocator reuses the memory
+    cudaStreamSynchronize(h->stream);
+    while (!h->allocs.empty()) dfree(h, h->allocs.back().first);
     cudaStreamSynchronize(h->stream);
 }
 
-// Process-wide autotuning results: problem shape -> kernel variant (0 plain
-// loads, 1 TMA staging).
+// Process-wide allocator hook for the handles created next (pf_set_allocator).
+std::mutex g_hook_lock;
+AllocHook g_hook;
+
+// Process-wide autotuning results: problem shape -> kernel variant (PF_KVAR_*).
 typedef std::tuple<int, int, int, int, int, int, int> TuneKey;   // prec, dim, nx, ny, nz, N, K
 std::mutex g_tune_lock;
 std::map<TuneKey, int> g_tune;
@@ -1795,6 +1856,11 @@ int pf_create(const pf_params *p, void *cuda_stream, pf_handle **out)
     pf_handle *h = new (std::nothrow) pf_handle();
     if (!h) return PF_ENOMEM;
     if (cudaGetDevice(&h->dev) != cudaSuccess) { delete h; return PF_EDEVICE; }
+    {
+        std::lock_guard<std::mutex> guard(g_hook_lock);
+        h->hook = g_hook;
+    }
+    pf_footprint(p, &h->footprint);
     h->stream = (cudaStream_t)cuda_stream;
     h->prec = p->precision;
     h->esize = p->precision == 64 ? 8 : 4;
@@ -1946,6 +2012,7 @@ int pf_footprint(const pf_params *p, long long *bytes)
 int pf_destroy(pf_handle *h)
 {
     if (!h) return PF_OK;
+    if (h->in_batch) return PF_EINVAL;
     cudaStreamSynchronize(h->stream);
     free_all(h);
     delete h;
@@ -2011,7 +2078,7 @@ int pf_dt_e(pf_handle *h, double *dte)
 
 int pf_set_state(pf_handle *h, const double *phi, const double *c, double t, int ptr_is_device)
 {
-    if (!h || !phi || (h->K && !c)) return PF_EINVAL;
+    if (!h || !phi || (h->K && !c) || h->in_batch) return PF_EINVAL;
     int st;
     const double *vphi = (const double *)device_view(phi), *vc = h->K ? (const double *)device_view(c) : nullptr;
     if (vphi && (!h->K || vc)) {
@@ -2092,7 +2159,7 @@ int pf_rhs(pf_handle *h, double *rhs_phi, double *rhs_c, unsigned char *nz, int 
 int pf_step(pf_handle *h, pf_integrator integ, double t_end, const pf_tol *tol, const pf_step_opts *opts,
             pf_stats *stats)
 {
-    if (!h) return PF_EINVAL;
+    if (!h || h->in_batch) return PF_EINVAL;
     if (!h->has_state) return PF_ESTATE;
     if ((int)integ < PF_FEULER || (int)integ > PF_RKL2) return PF_EINVAL;
     if (!(t_end >= h->t)) return PF_EINVAL;
@@ -2213,6 +2280,431 @@ int pf_energy(pf_handle *h, double *F)
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return PF_EDEVICE;
     if (over) return PF_EINVAL;
     *F = sum * pow(h->dx, h->g.dim);
+    return PF_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched stepping (pf_batch_*): continuous batching of many simulations on
+// one stream.  Every round each running request takes one step or adaptive
+// attempt; the FP32 passes of the requests that can be packed are recorded
+// (do_step in collect mode) and issued wave by wave, one packed launch per
+// pass kind and wave; the error partials and device flags of all requests
+// are folded and read back in one transfer; the controller and the
+// bookkeeping of step_loop then run per request on the host.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct BatchReq {
+    pf_handle *h = nullptr;
+    int integ = 0;
+    double t_end = 0.0;
+    pf_tol tol{};
+    pf_step_opts o{};
+    bool adaptive = false, packed = false, done = false;
+    int status = PF_OK;
+    double dt = 0.0, t0 = 0.0;
+    long long nfix = 0, kfix = 0;
+    int max_stages = 1001;
+    long long acc_n = 0, rej_n = 0, evals = 0, launches = 0;
+    double hlast = 0.0, elast = 0.0;
+    // the attempt of the current round
+    std::vector<Pass<float>> passes;
+    int cand = -1, s = 1;
+    double hs = 0.0;
+    bool last = false;
+};
+
+// Per request: where its error partials and status words are.
+struct BatchGather {
+    const double *ps;
+    const long long *pc;
+    const int *pn;
+    int cap;
+    int *flag;
+};
+
+// One block per request: the error partials folded in the order of
+// finalize_err_kernel (so the norm equals the single-handle one bit for
+// bit), the status words read and cleared for the next round.
+__global__ void batch_gather_kernel(const BatchGather *__restrict__ gs, double *out)
+{
+    const BatchGather G = gs[blockIdx.x];
+    __shared__ double ss[256];
+    __shared__ long long sc[256];
+    int n = G.cap;
+    if (G.pn && *G.pn < n) n = *G.pn;
+    double s = 0.0;
+    long long c = 0;
+    for (int k = threadIdx.x; k < n; k += 256) { s += G.ps[k]; c += G.pc[k]; }
+    ss[threadIdx.x] = s;
+    sc[threadIdx.x] = c;
+    __syncthreads();
+    for (int o = 128; o >= 1; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            ss[threadIdx.x] += ss[threadIdx.x + o];
+            sc[threadIdx.x] += sc[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double *o = out + 4 * blockIdx.x;
+        o[0] = ss[0];
+        o[1] = (double)sc[0];
+        o[2] = (double)G.flag[0];
+        o[3] = (double)G.flag[3];
+        G.flag[0] = G.flag[1] = G.flag[2] = G.flag[3] = 0;
+    }
+}
+
+template <typename T>
+bool grow(T **dev, T **host, size_t *cap, size_t want)
+{
+    if (want <= *cap) return true;
+    size_t c = *cap ? *cap : 64;
+    while (c < want) c *= 2;
+    if (*dev) cudaFree(*dev);
+    if (*host) cudaFreeHost(*host);
+    *dev = nullptr;
+    *host = nullptr;
+    *cap = 0;
+    if (cudaMalloc((void **)dev, sizeof(T) * c) != cudaSuccess) { cudaGetLastError(); return false; }
+    if (cudaMallocHost((void **)host, sizeof(T) * c) != cudaSuccess) { cudaGetLastError(); return false; }
+    *cap = c;
+    return true;
+}
+
+bool packable(const pf_handle *h, int integ)
+{
+    return h->prec == 32 && !h->masked && !h->tma && h->g.kvar == pfk::KVAR_TWO_CELL && pfk::vec_eligible(h->g) &&
+           integ != PF_SSP104;
+}
+
+}  // namespace
+
+struct pf_batch {
+    int dev = 0;
+    cudaStream_t stream = nullptr;
+    long long max_bytes = 0, used = 0;
+    std::vector<BatchReq> slots;       // h == nullptr: free slot
+    pfk::VecInst *dtab = nullptr, *htab = nullptr;
+    size_t tcap = 0;
+    int *dstart = nullptr, *hstart = nullptr;
+    size_t scap = 0;
+    BatchGather *dg = nullptr, *hg = nullptr;
+    size_t gcap = 0;
+    double *dout = nullptr, *hout = nullptr;
+    size_t ocap = 0;
+    int *ddone = nullptr;
+};
+
+namespace {
+
+// Bookkeeping of step_loop after one attempt of a request (packed path).
+void batch_after(BatchReq &r, int flag, double sum, double cnt)
+{
+    pf_handle *h = r.h;
+    r.hlast = r.hs;
+    if (flag) {
+        r.done = true;
+        r.status = flag_status(flag);
+        return;
+    }
+    int acc = 1;
+    if (r.adaptive) {
+        const double err = cnt > 0.0 ? sqrt(sum / cnt) : 0.0;
+        r.elast = err;
+        if (!isfinite(err)) {
+            r.done = true;
+            r.status = PF_EUNSTABLE;
+            return;
+        }
+        r.dt = controller(h, err, r.hs, method_order(r.integ), &acc);
+        h->dt_next = r.dt;
+    }
+    if (acc) {
+        h->iu = r.cand;
+        if (!r.adaptive) {
+            r.kfix++;
+            h->t = r.last ? r.t_end : r.t0 + (double)r.kfix * r.dt;
+        } else {
+            h->t = r.last ? r.t_end : h->t + r.hs;
+        }
+        r.acc_n++;
+    } else {
+        r.rej_n++;
+        if (r.rej_n > 100000) {
+            r.done = true;
+            r.status = PF_EUNSTABLE;
+            return;
+        }
+    }
+    if (!(h->t < r.t_end)) r.done = true;
+}
+
+int batch_round(pf_batch *b)
+{
+    std::vector<int> act;
+    size_t npass = 0, maxw = 0;
+    for (size_t k = 0; k < b->slots.size(); ++k) {
+        BatchReq &r = b->slots[k];
+        if (!r.h || r.done) continue;
+        pf_handle *h = r.h;
+        r.hs = r.dt;
+        int st = plan_attempt(h, r.integ, r.adaptive, r.t_end - h->t, r.kfix, r.nfix, r.o.ssp_stages, r.max_stages,
+                              &r.hs, &r.s, &r.last);
+        r.passes.clear();
+        if (!st) {
+            const pf_tol *tol = r.adaptive ? &r.tol : nullptr;
+            long long ev = 0;
+            const long long l0 = h->launches;
+            if (r.packed) {
+                // the passes are recorded for the packed launches below
+                h->collect = &r.passes;
+                st = do_step<float>(h, r.integ, r.hs, r.s, tol, r.adaptive, &r.cand, &ev);
+                h->collect = nullptr;
+            } else {
+                // launched now on the handle's stream; the batch's stream waits for them
+                st = (h->prec == 64) ? do_step<double>(h, r.integ, r.hs, r.s, tol, r.adaptive, &r.cand, &ev)
+                                     : do_step<float>(h, r.integ, r.hs, r.s, tol, r.adaptive, &r.cand, &ev);
+                if (!st && h->stream != b->stream) {
+                    cudaEvent_t e;
+                    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return PF_EDEVICE;
+                    cudaEventRecord(e, h->stream);
+                    cudaStreamWaitEvent(b->stream, e, 0);
+                    cudaEventDestroy(e);
+                }
+            }
+            r.launches += h->launches - l0;
+            r.evals += ev;
+        }
+        if (st) { r.done = true; r.status = st; continue; }
+        npass += r.passes.size();
+        maxw = std::max(maxw, r.passes.size());
+        act.push_back((int)k);
+    }
+    if (act.empty()) return PF_OK;
+    if (!grow(&b->dtab, &b->htab, &b->tcap, npass) || !grow(&b->dstart, &b->hstart, &b->scap, npass) ||
+        !grow(&b->dg, &b->hg, &b->gcap, act.size()) || !grow(&b->dout, &b->hout, &b->ocap, 4 * act.size()))
+        return PF_ENOMEM;
+    // waves: the w-th pass of every request; one packed launch per pass kind
+    struct Launch { int dim, K; unsigned sig; size_t toff; int n, blocks; };
+    std::vector<Launch> launches;
+    size_t toff = 0;
+    for (size_t w = 0; w < maxw; ++w) {
+        std::map<std::tuple<int, int, unsigned>, std::vector<int>> groups;
+        for (int k : act) {
+            BatchReq &r = b->slots[k];
+            if (w < r.passes.size())
+                groups[std::make_tuple(r.h->g.dim, r.h->K, pfk::pass_signature(r.passes[w]))].push_back(k);
+        }
+        for (auto &gr : groups) {
+            Launch l{std::get<0>(gr.first), std::get<1>(gr.first), std::get<2>(gr.first), toff, 0, 0};
+            for (int k : gr.second) {
+                BatchReq &r = b->slots[k];
+                pfk::VecInst &I = b->htab[toff];
+                I.g = r.h->g;
+                I.P = r.passes[w];
+                I.A = (const float *)r.h->dA;
+                I.B = (const float *)r.h->dB;
+                I.L = (const float *)r.h->dL;
+                I.ptype = r.h->dptype;
+                I.nblk = (int)(pfk::vec_tiles(r.h->g) * r.h->g.nz);
+                b->hstart[toff] = l.blocks;
+                l.blocks += I.nblk;
+                l.n++;
+                toff++;
+                r.launches += 2;
+            }
+            launches.push_back(l);
+        }
+    }
+    if (cudaMemcpyAsync(b->dtab, b->htab, sizeof(pfk::VecInst) * toff, cudaMemcpyHostToDevice, b->stream) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(b->dstart, b->hstart, sizeof(int) * toff, cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
+        return PF_EDEVICE;
+    for (const Launch &l : launches) {
+        bool ok = false;
+        const int e = pfk::launch_packed(l.dim, l.K, l.sig, b->dtab + l.toff, b->dstart + l.toff, l.n, l.blocks,
+                                         b->ddone, b->stream, &ok);
+        if (!ok || e != 0) return PF_EDEVICE;
+    }
+    // error partials and status words of every request, one transfer
+    for (size_t j = 0; j < act.size(); ++j) {
+        const pf_handle *h = b->slots[act[j]].h;
+        b->hg[j] = BatchGather{h->part_sum, h->part_cnt, h->dpartn, h->grid, h->dflag};
+    }
+    if (cudaMemcpyAsync(b->dg, b->hg, sizeof(BatchGather) * act.size(), cudaMemcpyHostToDevice, b->stream) !=
+        cudaSuccess)
+        return PF_EDEVICE;
+    batch_gather_kernel<<<(unsigned)act.size(), 256, 0, b->stream>>>(b->dg, b->dout);
+    if (cudaGetLastError() != cudaSuccess) return PF_EDEVICE;
+    if (cudaMemcpyAsync(b->hout, b->dout, sizeof(double) * 4 * act.size(), cudaMemcpyDeviceToHost, b->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(b->stream) != cudaSuccess)
+        return PF_EDEVICE;
+    for (size_t j = 0; j < act.size(); ++j) {
+        const double *o = b->hout + 4 * j;
+        batch_after(b->slots[act[j]], (int)o[2], o[0], o[1]);
+    }
+    return PF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pf_set_allocator(pf_alloc_fn alloc, pf_free_fn free_fn, void *ctx)
+{
+    if ((alloc == nullptr) != (free_fn == nullptr)) return PF_EINVAL;
+    std::lock_guard<std::mutex> guard(g_hook_lock);
+    g_hook.alloc = alloc;
+    g_hook.free = free_fn;
+    g_hook.ctx = alloc ? ctx : nullptr;
+    return PF_OK;
+}
+
+int pf_batch_create(long long max_bytes, void *cuda_stream, pf_batch **out)
+{
+    if (!out || max_bytes <= 0) return PF_EINVAL;
+    *out = nullptr;
+    pf_batch *b = new (std::nothrow) pf_batch();
+    if (!b) return PF_ENOMEM;
+    if (cudaGetDevice(&b->dev) != cudaSuccess) { delete b; return PF_EDEVICE; }
+    b->stream = (cudaStream_t)cuda_stream;
+    b->max_bytes = max_bytes;
+    if (cudaMalloc((void **)&b->ddone, sizeof(int)) != cudaSuccess) { cudaGetLastError(); delete b; return PF_ENOMEM; }
+    if (cudaMemsetAsync(b->ddone, 0, sizeof(int), b->stream) != cudaSuccess ||
+        cudaStreamSynchronize(b->stream) != cudaSuccess) {
+        cudaFree(b->ddone);
+        delete b;
+        return PF_EDEVICE;
+    }
+    *out = b;
+    return PF_OK;
+}
+
+int pf_batch_admit(pf_batch *b, pf_handle *h, pf_integrator integ, double t_end, const pf_tol *tol,
+                   const pf_step_opts *opts, int *slot)
+{
+    if (!b || !h || !slot) return PF_EINVAL;
+    if (!h->has_state) return PF_ESTATE;
+    if (h->in_batch || h->dev != b->dev) return PF_EINVAL;
+    if ((int)integ < PF_FEULER || (int)integ > PF_RKL2) return PF_EINVAL;
+    if (!(t_end >= h->t)) return PF_EINVAL;
+    BatchReq r;
+    memset(&r.o, 0, sizeof(r.o));
+    r.o.ssp_stages = 5;
+    if (opts) r.o = *opts;
+    r.adaptive = !(r.o.dt_mult > 0.0);
+    if (r.adaptive && (integ == PF_FEULER || integ == PF_SSP2)) return PF_EINVAL;
+    if (r.adaptive && !tol) return PF_EINVAL;
+    if (integ == PF_SSP2 && r.o.ssp_stages < 2) return PF_EINVAL;
+    if (h->footprint > b->max_bytes - b->used) return PF_ENOMEM;
+    r.h = h;
+    r.integ = integ;
+    r.t_end = t_end;
+    if (tol) r.tol = *tol;
+    r.max_stages = r.o.max_stages > 0 ? r.o.max_stages : 1001;
+    r.packed = packable(h, integ);
+    if (r.adaptive) {
+        r.dt = h->dt_next > 0.0 ? h->dt_next : (r.o.dt0 > 0.0 ? r.o.dt0 : 0.9 * h->dte);
+    } else {
+        r.dt = r.o.dt_mult * h->dte;
+        r.t0 = h->t;
+        r.nfix = (long long)ceil((t_end - r.t0) / r.dt - 1e-9);
+        if (r.nfix < 1) r.nfix = 1;
+    }
+    {
+        // the batch's stream waits for the handle's earlier work
+        cudaEvent_t ev;
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return PF_EDEVICE;
+        cudaError_t e = cudaEventRecord(ev, h->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, ev, 0);
+        cudaEventDestroy(ev);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->dflag, 0, PF_FLAG_BYTES, b->stream);
+        if (e != cudaSuccess) return PF_EDEVICE;
+        h->reuse_on = false;
+        h->rhs_valid = false;
+    }
+    if (!(h->t < t_end)) r.done = true;
+    h->in_batch = true;
+    b->used += h->footprint;
+    int k = 0;
+    while (k < (int)b->slots.size() && b->slots[k].h) ++k;
+    if (k == (int)b->slots.size()) b->slots.emplace_back();
+    b->slots[k] = r;
+    *slot = k;
+    return PF_OK;
+}
+
+int pf_batch_run(pf_batch *b, int rounds, int *n_active)
+{
+    if (!b || rounds < 1) return PF_EINVAL;
+    for (int i = 0; i < rounds; ++i) {
+        bool any = false;
+        for (const BatchReq &r : b->slots) any = any || (r.h && !r.done);
+        if (!any) break;
+        const int st = batch_round(b);
+        if (st) return st;
+    }
+    if (n_active) {
+        int n = 0;
+        for (const BatchReq &r : b->slots) n += (r.h && !r.done) ? 1 : 0;
+        *n_active = n;
+    }
+    return PF_OK;
+}
+
+int pf_batch_result(pf_batch *b, int slot, int *done, int *status, pf_stats *stats)
+{
+    if (!b || !done || slot < 0 || slot >= (int)b->slots.size() || !b->slots[slot].h) return PF_EINVAL;
+    BatchReq &r = b->slots[slot];
+    *done = r.done ? 1 : 0;
+    if (!r.done) return PF_OK;
+    pf_handle *h = r.h;
+    if (status) *status = r.status;
+    if (stats) {
+        stats->rhs_evals = r.evals;
+        stats->steps_accepted = r.acc_n;
+        stats->steps_rejected = r.rej_n;
+        stats->t = h->t;
+        stats->dt_last = r.hlast;
+        stats->err_last = r.elast;
+        stats->dt_e = h->dte;
+        stats->dt_next = r.adaptive ? h->dt_next : 0.0;
+        stats->kernel_launches = r.launches;
+    }
+    // the handle's stream is ordered after the batch's work on it
+    cudaEvent_t ev;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess) {
+        cudaEventRecord(ev, b->stream);
+        cudaStreamWaitEvent(h->stream, ev, 0);
+        cudaEventDestroy(ev);
+    }
+    h->in_batch = false;
+    b->used -= h->footprint;
+    r = BatchReq();
+    return PF_OK;
+}
+
+int pf_batch_destroy(pf_batch *b)
+{
+    if (!b) return PF_OK;
+    cudaStreamSynchronize(b->stream);
+    for (BatchReq &r : b->slots)
+        if (r.h) r.h->in_batch = false;
+    if (b->dtab) cudaFree(b->dtab);
+    if (b->htab) cudaFreeHost(b->htab);
+    if (b->dstart) cudaFree(b->dstart);
+    if (b->hstart) cudaFreeHost(b->hstart);
+    if (b->dg) cudaFree(b->dg);
+    if (b->hg) cudaFreeHost(b->hg);
+    if (b->dout) cudaFree(b->dout);
+    if (b->hout) cudaFreeHost(b->hout);
+    if (b->ddone) cudaFree(b->ddone);
+    delete b;
     return PF_OK;
 }
 

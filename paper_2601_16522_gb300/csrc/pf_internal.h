@@ -29,6 +29,14 @@ template <typename T>
 int launch_stage_d(const Geom &g, unsigned sig, const Pass<T> *dP, cudaStream_t st, const T *A, const T *B,
                    const T *L, const signed char *ptype);
 
+// Packed launch of one pass kind (dimension dim, K, signature sig) over the n
+// problems of a device table (two-cell FP32 passes; see VecInst): blocks is
+// the sum of their block counts, bstart their prefix sums, done a zeroed
+// device counter of the caller.  Returns a cudaError_t; *ok false when the
+// pass kind has no packed form.
+int launch_packed(int dim, int K, unsigned sig, const VecInst *tab, const int *bstart, int n, int blocks, int *done,
+                  cudaStream_t st, bool *ok);
+
 // Opt every instantiation into its shared memory on the current device;
 // returns the resident blocks per SM of the generic 3D kernel (<= 0: error).
 template <typename T>

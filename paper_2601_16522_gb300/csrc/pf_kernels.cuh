@@ -221,9 +221,9 @@ __device__ __forceinline__ void face_offsets(const Geom &g, int x, int y, int z,
 // Fixed-order block reduction of (sum, count) into the per-block partials;
 // block 0 records how many partials the launch writes (pn, may be null).
 __device__ __forceinline__ void block_partials(double esum, long long ecnt, double *ps, long long *pc, int bid,
-                                               int *pn = nullptr)
+                                               int *pn = nullptr, int nblk = -1)
 {
-    if (pn && bid == 0 && threadIdx.x == 0) *pn = (int)(gridDim.x * gridDim.y * gridDim.z);
+    if (pn && bid == 0 && threadIdx.x == 0) *pn = nblk >= 0 ? nblk : (int)(gridDim.x * gridDim.y * gridDim.z);
     constexpr int MAXW = 16;                 // blocks of up to 512 threads
     __shared__ double rs_sum[MAXW];
     __shared__ long long rs_cnt[MAXW];

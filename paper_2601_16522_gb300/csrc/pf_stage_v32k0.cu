@@ -131,6 +131,84 @@ int launchd_v32k0(const Geom &g, unsigned sig, const Pass<float> *dP, cudaStream
     return 0;
 }
 
+int launchp_v32k0(int dim, unsigned sig, const VecInst *tab, const int *bstart, int n, int blocks, int *done,
+             cudaStream_t st, bool *ok)
+{
+    *ok = true;
+    if (dim == 2 && sig == (SIG_PROJECT)) {
+        packed_kernel<2, 0, SIG_PROJECT><<<blocks, VBLOCK, vec_smem<SIG_PROJECT>(), st>>>(tab, bstart, n);
+        packed_wide_fix_kernel<2, 0><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(tab, n, done);
+        return (int)cudaGetLastError();
+    }
+    if (dim == 2 && sig == (SIG_P2 | SIG_PROJECT)) {
+        packed_kernel<2, 0, SIG_P2 | SIG_PROJECT><<<blocks, VBLOCK, vec_smem<SIG_P2 | SIG_PROJECT>(), st>>>(tab, bstart, n);
+        packed_wide_fix_kernel<2, 0><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(tab, n, done);
+        return (int)cudaGetLastError();
+    }
+    if (dim == 2 && sig == (SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT)) {
+        packed_kernel<2, 0, SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT><<<blocks, VBLOCK, vec_smem<SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT>(), st>>>(tab, bstart, n);
+        packed_wide_fix_kernel<2, 0><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(tab, n, done);
+        return (int)cudaGetLastError();
+    }
+    if (dim == 2 && sig == (SIG_R0OUT | SIG_PROJECT)) {
+        packed_kernel<2, 0, SIG_R0OUT | SIG_PROJECT><<<blocks, VBLOCK, vec_smem<SIG_R0OUT | SIG_PROJECT>(), st>>>(tab, bstart, n);
+        packed_wide_fix_kernel<2, 0><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(tab, n, done);
+        return (int)cudaGetLastError();
+    }
+    if (dim == 2 && sig == (SIG_ERR)) {
+        packed_kernel<2, 0, SIG_ERR><<<blocks, VBLOCK, vec_smem<SIG_ERR>(), st>>>(tab, bstart, n);
+        packed_wide_fix_kernel<2, 0><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(tab, n, done);
+        return (int)cudaGetLastError();
+    }
+    if (dim == 2 && sig == (SIG_P0 | SIG_PROJECT)) {
+        packed_kernel<2, 0, SIG_P0 | SIG_PROJECT><<<blocks, VBLOCK, vec_smem<SIG_P0 | SIG_PROJECT>(), st>>>(tab, bstart, n);
+        packed_wide_fix_kernel<2, 0><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(tab, n, done);
+        return (int)cudaGetLastError();
+    }
+    if (dim == 2 && sig == (SIG_ERR | SIG_R0OUT)) {
+        packed_kernel<2, 0, SIG_ERR | SIG_R0OUT><<<blocks, VBLOCK, vec_smem<SIG_ERR | SIG_R0OUT>(), st>>>(tab, bstart, n);
+        packed_wide_fix_kernel<2, 0><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(tab, n, done);
+        return (int)cudaGetLastError();
+    }
+    if (dim == 3 && sig == (SIG_PROJECT)) {
+        packed_kernel<3, 0, SIG_PROJECT><<<blocks, VBLOCK, vec_smem<SIG_PROJECT>(), st>>>(tab, bstart, n);
+        packed_wide_fix_kernel<3, 0><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(tab, n, done);
+        return (int)cudaGetLastError();
+    }
+    if (dim == 3 && sig == (SIG_P2 | SIG_PROJECT)) {
+        packed_kernel<3, 0, SIG_P2 | SIG_PROJECT><<<blocks, VBLOCK, vec_smem<SIG_P2 | SIG_PROJECT>(), st>>>(tab, bstart, n);
+        packed_wide_fix_kernel<3, 0><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(tab, n, done);
+        return (int)cudaGetLastError();
+    }
+    if (dim == 3 && sig == (SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT)) {
+        packed_kernel<3, 0, SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT><<<blocks, VBLOCK, vec_smem<SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT>(), st>>>(tab, bstart, n);
+        packed_wide_fix_kernel<3, 0><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(tab, n, done);
+        return (int)cudaGetLastError();
+    }
+    if (dim == 3 && sig == (SIG_R0OUT | SIG_PROJECT)) {
+        packed_kernel<3, 0, SIG_R0OUT | SIG_PROJECT><<<blocks, VBLOCK, vec_smem<SIG_R0OUT | SIG_PROJECT>(), st>>>(tab, bstart, n);
+        packed_wide_fix_kernel<3, 0><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(tab, n, done);
+        return (int)cudaGetLastError();
+    }
+    if (dim == 3 && sig == (SIG_ERR)) {
+        packed_kernel<3, 0, SIG_ERR><<<blocks, VBLOCK, vec_smem<SIG_ERR>(), st>>>(tab, bstart, n);
+        packed_wide_fix_kernel<3, 0><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(tab, n, done);
+        return (int)cudaGetLastError();
+    }
+    if (dim == 3 && sig == (SIG_P0 | SIG_PROJECT)) {
+        packed_kernel<3, 0, SIG_P0 | SIG_PROJECT><<<blocks, VBLOCK, vec_smem<SIG_P0 | SIG_PROJECT>(), st>>>(tab, bstart, n);
+        packed_wide_fix_kernel<3, 0><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(tab, n, done);
+        return (int)cudaGetLastError();
+    }
+    if (dim == 3 && sig == (SIG_ERR | SIG_R0OUT)) {
+        packed_kernel<3, 0, SIG_ERR | SIG_R0OUT><<<blocks, VBLOCK, vec_smem<SIG_ERR | SIG_R0OUT>(), st>>>(tab, bstart, n);
+        packed_wide_fix_kernel<3, 0><<<WIDE_FIX_BLOCKS, VCELLS, 0, st>>>(tab, n, done);
+        return (int)cudaGetLastError();
+    }
+    *ok = false;
+    return 0;
+}
+
 int prepare_v32k0()
 {
     if (cudaFuncSetAttribute(vec_kernel<2, 0, SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vec_smem<SIG_PROJECT>()) != cudaSuccess) return -1;
@@ -155,6 +233,20 @@ int prepare_v32k0()
     if (cudaFuncSetAttribute(vec_kernel_d<3, 0, SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vec_smem<SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT>()) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(vec_kernel_d<3, 0, SIG_P2 | SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vec_smem<SIG_P2 | SIG_PROJECT>()) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(vec_kernel_d<3, 0, SIG_ERR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vec_smem<SIG_ERR>()) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(packed_kernel<2, 0, SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vec_smem<SIG_PROJECT>()) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(packed_kernel<2, 0, SIG_P2 | SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vec_smem<SIG_P2 | SIG_PROJECT>()) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(packed_kernel<2, 0, SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vec_smem<SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT>()) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(packed_kernel<2, 0, SIG_R0OUT | SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vec_smem<SIG_R0OUT | SIG_PROJECT>()) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(packed_kernel<2, 0, SIG_ERR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vec_smem<SIG_ERR>()) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(packed_kernel<2, 0, SIG_P0 | SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vec_smem<SIG_P0 | SIG_PROJECT>()) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(packed_kernel<2, 0, SIG_ERR | SIG_R0OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vec_smem<SIG_ERR | SIG_R0OUT>()) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(packed_kernel<3, 0, SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vec_smem<SIG_PROJECT>()) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(packed_kernel<3, 0, SIG_P2 | SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vec_smem<SIG_P2 | SIG_PROJECT>()) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(packed_kernel<3, 0, SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vec_smem<SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT>()) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(packed_kernel<3, 0, SIG_R0OUT | SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vec_smem<SIG_R0OUT | SIG_PROJECT>()) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(packed_kernel<3, 0, SIG_ERR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vec_smem<SIG_ERR>()) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(packed_kernel<3, 0, SIG_P0 | SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vec_smem<SIG_P0 | SIG_PROJECT>()) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(packed_kernel<3, 0, SIG_ERR | SIG_R0OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vec_smem<SIG_ERR | SIG_R0OUT>()) != cudaSuccess) return -1;
     return 1;
 }
 

@@ -135,10 +135,12 @@ struct VCell {
     long long ec;
 };
 
+// One block of a two-cell pass: tile (bx, by) of plane bz, one of nblk
+// blocks of the pass (a packed launch maps its blocks to several problems).
 template <int DIM, int KC, unsigned SIG>
 __device__ __forceinline__ void vec_body(const Geom &g, const Pass<float> &P, const float *__restrict__ tabA,
                                          const float *__restrict__ tabB, const float *__restrict__ tabL,
-                                         const signed char *__restrict__ ptype)
+                                         const signed char *__restrict__ ptype, int bx, int by, int bz, int nblk)
 {
     typedef float T;
     constexpr bool ERR = (SIG & SIG_ERR) != 0;
@@ -153,10 +155,11 @@ __device__ __forceinline__ void vec_body(const Geom &g, const Pass<float> &P, co
     VecSmem<VACT> &S = *reinterpret_cast<VecSmem<VACT> *>(smem_raw);
     const int tid = threadIdx.x;
     const int lane = tid & 31, ty = tid >> 5;
-    const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-    const int x = blockIdx.x * (2 * VTX) + 2 * lane;
-    const int y = blockIdx.y * VTY + ty;
-    const int z = blockIdx.z;
+    const int tiles_x = (g.nx + 2 * VTX - 1) / (2 * VTX), tiles_y = (g.ny + VTY - 1) / VTY;
+    const int bid = bx + tiles_x * (by + tiles_y * bz);
+    const int x = bx * (2 * VTX) + 2 * lane;
+    const int y = by * VTY + ty;
+    const int z = bz;
     const int N = g.N;
     const int Vs = (int)g.Vs;
     VCell C[2];
@@ -571,7 +574,7 @@ __device__ __forceinline__ void vec_body(const Geom &g, const Pass<float> &P, co
             for (int w = 0; w < VCELLS / 32; ++w) ent[1 + w] = (int)cmask[w];
         }
     }
-    if (ERR) block_partials(C[0].es + C[1].es, C[0].ec + C[1].ec, P.part_sum, P.part_cnt, bid, P.part_n);
+    if (ERR) block_partials(C[0].es + C[1].es, C[0].ec + C[1].ec, P.part_sum, P.part_cnt, bid, P.part_n, nblk);
     // the step is counted by the wide pass, after the crowded cells
 }
 
@@ -585,14 +588,18 @@ __device__ __forceinline__ void vec_body(const Geom &g, const Pass<float> &P, co
 // two-cell pass (with no entries it only does the bookkeeping).
 constexpr int WIDE_FIX_BLOCKS = 152;
 
+// The recorded entries e = w, w + nw, ... of one two-cell pass.
 template <int DIM, int KC>
-__device__ __forceinline__ void wide_fix_body(const Geom &g, const Pass<float> &P, const float *tabA,
-                                              const float *tabB, const float *tabL, const signed char *ptype)
+__device__ __forceinline__ void wide_fix_entries(const Geom &g, const Pass<float> &P, const float *tabA,
+                                                 const float *tabB, const float *tabL, const signed char *ptype,
+                                                 int w, int nw)
 {
+    __shared__ double rs[VCELLS];
+    __shared__ long long rc[VCELLS];
     const int n = *(volatile int *)P.crowd;
     const int tid = threadIdx.x;
     const int tiles_x = (g.nx + 2 * VTX - 1) / (2 * VTX), tiles_y = (g.ny + VTY - 1) / VTY;
-    for (int e = blockIdx.x; e < n; e += gridDim.x) {
+    for (int e = w; e < n; e += nw) {
         const int *ent = P.crowd + 2 + e * (1 + VCELLS / 32);
         const int b = ent[0];
         const unsigned m = (unsigned)ent[1 + (tid >> 5)];
@@ -604,8 +611,6 @@ __device__ __forceinline__ void wide_fix_body(const Geom &g, const Pass<float> &
             wide_cell<float, DIM, KC>(&g, &P, tabA, tabB, tabL, ptype, x, y, bz, &es, &ec);
         }
         if (P.mode == MODE_ERR) {
-            __shared__ double rs[VCELLS];
-            __shared__ long long rc[VCELLS];
             rs[tid] = es;
             rc[tid] = ec;
             __syncthreads();
@@ -619,14 +624,26 @@ __device__ __forceinline__ void wide_fix_body(const Geom &g, const Pass<float> &
             __syncthreads();
         }
     }
+}
+
+// After every block of the wide pass: clear the record and, for a pass
+// that completes a fixed step without a flag, count the step.
+__device__ __forceinline__ void wide_fix_close(const Pass<float> &P)
+{
+    atomicExch(P.crowd, 0);
+    atomicExch(P.crowd + 1, 0);
+    if (P.count_step && !pass_skipped(P.flag)) atomicAdd(P.flag + 1, 1);
+}
+
+template <int DIM, int KC>
+__device__ __forceinline__ void wide_fix_body(const Geom &g, const Pass<float> &P, const float *tabA,
+                                              const float *tabB, const float *tabL, const signed char *ptype)
+{
+    wide_fix_entries<DIM, KC>(g, P, tabA, tabB, tabL, ptype, blockIdx.x, gridDim.x);
     __syncthreads();
-    if (tid == 0) {
+    if (threadIdx.x == 0) {
         __threadfence();
-        if (atomicAdd(P.crowd + 1, 1) == (int)gridDim.x - 1) {
-            atomicExch(P.crowd, 0);
-            atomicExch(P.crowd + 1, 0);
-            if (P.count_step && !pass_skipped(P.flag)) atomicAdd(P.flag + 1, 1);
-        }
+        if (atomicAdd(P.crowd + 1, 1) == (int)gridDim.x - 1) wide_fix_close(P);
     }
 }
 
@@ -663,7 +680,8 @@ __global__ void __launch_bounds__(VBLOCK, (vec_minb<KC, SIG>()))
 vec_kernel(const __grid_constant__ Geom g, const __grid_constant__ Pass<float> P, const float *__restrict__ tabA,
            const float *__restrict__ tabB, const float *__restrict__ tabL, const signed char *__restrict__ ptype)
 {
-    vec_body<DIM, KC, SIG>(g, P, tabA, tabB, tabL, ptype);
+    vec_body<DIM, KC, SIG>(g, P, tabA, tabB, tabL, ptype, blockIdx.x, blockIdx.y, blockIdx.z,
+                           (int)(gridDim.x * gridDim.y * gridDim.z));
 }
 
 // The same pass with its description read from device memory (device-driven
@@ -676,7 +694,79 @@ vec_kernel_d(const __grid_constant__ Geom g, const Pass<float> *__restrict__ Pd,
     __shared__ Pass<float> Ps;
     if (threadIdx.x == 0) Ps = *Pd;
     __syncthreads();
-    vec_body<DIM, KC, SIG>(g, Ps, tabA, tabB, tabL, ptype);
+    vec_body<DIM, KC, SIG>(g, Ps, tabA, tabB, tabL, ptype, blockIdx.x, blockIdx.y, blockIdx.z,
+                           (int)(gridDim.x * gridDim.y * gridDim.z));
+}
+
+
+// ---------------------------------------------------------------------------
+// Packed launches (batched serving): one launch runs the same pass kind
+// (dimension, K, signature) of several problems.  The blocks of problem k
+// are blocks bstart[k] .. bstart[k + 1] - 1 of the launch; each block finds
+// its problem by binary search, copies that problem's constants and pass
+// description into shared memory and runs the two-cell body on its tile, so
+// every problem computes exactly what its own launch would.
+// ---------------------------------------------------------------------------
+struct VecInst {
+    Geom g;
+    Pass<float> P;
+    const float *A, *B, *L;
+    const signed char *ptype;
+    int nblk;                        // two-cell blocks of this problem
+};
+
+__device__ __forceinline__ int packed_find(const int *__restrict__ bstart, int n, int b)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(bstart + mid) <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int DIM, int KC, unsigned SIG>
+__global__ void __launch_bounds__(VBLOCK, (vec_minb<KC, SIG>()))
+packed_kernel(const VecInst *__restrict__ tab, const int *__restrict__ bstart, int n)
+{
+    __shared__ Geom gs;
+    __shared__ Pass<float> Ps;
+    __shared__ int ks;
+    if (threadIdx.x == 0) {
+        const int k = packed_find(bstart, n, blockIdx.x);
+        ks = k;
+        gs = tab[k].g;
+        Ps = tab[k].P;
+    }
+    __syncthreads();
+    const int k = ks;
+    const VecInst &I = tab[k];
+    const int b = blockIdx.x - __ldg(bstart + k);
+    const int tiles_x = (gs.nx + 2 * VTX - 1) / (2 * VTX), tiles_y = (gs.ny + VTY - 1) / VTY;
+    vec_body<DIM, KC, SIG>(gs, Ps, I.A, I.B, I.L, I.ptype, b % tiles_x, (b / tiles_x) % tiles_y,
+                           b / (tiles_x * tiles_y), I.nblk);
+}
+
+// The wide pass of a packed launch: the blocks share out every problem's
+// recorded entries; the last block to finish closes every problem's pass
+// (done: a counter of the batch, zero between launches).
+template <int DIM, int KC>
+__global__ void __launch_bounds__(VCELLS)
+packed_wide_fix_kernel(const VecInst *__restrict__ tab, int n, int *done)
+{
+    for (int k = 0; k < n; ++k) {
+        const VecInst &I = tab[k];
+        wide_fix_entries<DIM, KC>(I.g, I.P, I.A, I.B, I.L, I.ptype, blockIdx.x, gridDim.x);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(done, 1) == (int)gridDim.x - 1) {
+            for (int k = 0; k < n; ++k) wide_fix_close(tab[k].P);
+            atomicExch(done, 0);
+        }
+    }
 }
 
 }  // namespace pfk

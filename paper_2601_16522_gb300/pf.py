@@ -66,6 +66,9 @@ class pf_stats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+_ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+_FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+
 _LIB = None
 
 
@@ -96,6 +99,13 @@ def _lib():
         L.pf_launch_count.restype = C.c_longlong
         L.pf_strerror.argtypes = [C.c_int]
         L.pf_strerror.restype = C.c_char_p
+        L.pf_set_allocator.argtypes = [_ALLOC_FN, _FREE_FN, C.c_void_p]
+        L.pf_batch_create.argtypes = [C.c_longlong, C.c_void_p, C.POINTER(C.c_void_p)]
+        L.pf_batch_admit.argtypes = [C.c_void_p, H, C.c_int, C.c_double, C.POINTER(pf_tol),
+                                     C.POINTER(pf_step_opts), _ip]
+        L.pf_batch_run.argtypes = [C.c_void_p, C.c_int, _ip]
+        L.pf_batch_result.argtypes = [C.c_void_p, C.c_int, _ip, _ip, C.POINTER(pf_stats)]
+        L.pf_batch_destroy.argtypes = [C.c_void_p]
         _LIB = L
     return _LIB
 
@@ -354,3 +364,102 @@ class Simulation:
         F = C.c_double()
         _check(_lib().pf_energy(self.h, C.byref(F)), "pf_energy")
         return F.value
+
+
+# ---------------------------------------------------------------------------
+# Device memory from torch's caching allocator (pf_set_allocator)
+# ---------------------------------------------------------------------------
+_HOOK = None
+
+
+def use_torch_allocator(enable=True):
+    """Route the device buffers of handles created from now on through
+    torch's caching allocator (torch.cuda.caching_allocator_alloc / _delete on
+    the handle's stream), so simulations and torch share one memory pool;
+    enable=False restores CUDA's stream-ordered allocator."""
+    global _HOOK
+    L = _lib()
+    if not enable:
+        _check(L.pf_set_allocator(_ALLOC_FN(), _FREE_FN(), None), "pf_set_allocator")
+        return
+    import torch
+
+    def alloc(nbytes, stream, ctx):
+        try:
+            dev = torch.cuda.current_device()
+            s = torch.cuda.ExternalStream(stream) if stream else torch.cuda.default_stream(dev)
+            return torch.cuda.caching_allocator_alloc(int(nbytes), dev, s)
+        except Exception:
+            return None
+
+    def free(ptr, nbytes, stream, ctx):
+        try:
+            torch.cuda.caching_allocator_delete(ptr)
+        except Exception:
+            pass
+
+    _HOOK = (_ALLOC_FN(alloc), _FREE_FN(free))      # kept alive while set
+    _check(L.pf_set_allocator(_HOOK[0], _HOOK[1], None), "pf_set_allocator")
+
+
+# ---------------------------------------------------------------------------
+# Batched stepping (pf_batch_*)
+# ---------------------------------------------------------------------------
+class Batch:
+    """Continuous batching of Simulations on one stream (pf_batch_*): admit
+    requests as memory allows, run rounds, collect finished results."""
+
+    def __init__(self, max_bytes, stream=None):
+        self._stream = stream
+        b = C.c_void_p()
+        sptr = C.c_void_p(stream.cuda_stream) if stream is not None else None
+        _check(_lib().pf_batch_create(int(max_bytes), sptr, C.byref(b)), "pf_batch_create")
+        self.b = b
+        self._sims = {}
+
+    def admit(self, sim, integ, t_end, tol=None, dt_mult=0.0, ssp_stages=5, dt0=0.0, max_stages=0):
+        """Returns the slot, or None when the request does not fit the budget now."""
+        o = pf_step_opts()
+        o.ssp_stages, o.dt_mult, o.dt0, o.max_stages = ssp_stages, dt_mult, dt0, max_stages
+        tl = pf_tol(*tol) if tol is not None else None
+        slot = C.c_int()
+        st = _lib().pf_batch_admit(self.b, sim.h, int(integ), float(t_end),
+                                   C.byref(tl) if tl is not None else None, C.byref(o), C.byref(slot))
+        if st == PF_ENOMEM:
+            return None
+        _check(st, "pf_batch_admit")
+        self._sims[slot.value] = sim
+        return slot.value
+
+    def run(self, rounds=1):
+        """Runs up to `rounds` rounds; returns the number of running requests."""
+        n = C.c_int()
+        _check(_lib().pf_batch_run(self.b, int(rounds), C.byref(n)), "pf_batch_run")
+        return n.value
+
+    def result(self, slot):
+        """None while running; else (status, stats dict), releasing the slot."""
+        done, status, st = C.c_int(), C.c_int(), pf_stats()
+        _check(_lib().pf_batch_result(self.b, int(slot), C.byref(done), C.byref(status), C.byref(st)),
+               "pf_batch_result")
+        if not done.value:
+            return None
+        self._sims.pop(slot, None)
+        return status.value, st.as_dict()
+
+    def close(self):
+        if getattr(self, "b", None):
+            _lib().pf_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

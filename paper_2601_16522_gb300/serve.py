@@ -1,4 +1,8 @@
-"""Serving loop: continuous batching of simulations by device-memory footprint.
+"""Serving loops: continuous batching of simulations by device-memory footprint.
+
+BatchServer drives the library's batch (pf_batch_*: one stream, one round of
+steps at a time, the passes of FP32 dense problems packed into shared
+launches).  Server below is the thread-per-request form:
 
 Requests (a problem, an initial state, an integrator and an end time) arrive
 over time.  The scheduler admits a waiting request as soon as its footprint
@@ -193,6 +197,87 @@ class Server:
                     self.lock.wait(timeout=0.05)
         makespan = time.perf_counter() - t0
         return finished, makespan
+
+
+class BatchServer:
+    """Continuous batching through the library's batch (pf_batch_*): every
+    admitted request gets a handle on the server's one stream and is
+    admitted into the batch by its footprint; the batch advances all of them
+    a round at a time (one step or attempt each, the passes of FP32 dense
+    problems packed into shared launches, one transfer of error norms and
+    flags per round).  Arrivals are admitted between rounds as memory frees
+    up; finished requests leave with their state and statistics.  A result
+    equals the request run alone (the batch keeps pf_step's bookkeeping).
+
+    rounds: rounds per batch call between admission checks."""
+
+    def __init__(self, mem_budget_bytes: int, rounds: int = 4):
+        self.budget = int(mem_budget_bytes)
+        self.rounds = int(rounds)
+        self.peak_used = 0
+
+    def serve(self, requests, realtime=True):
+        import torch
+        stream = torch.cuda.Stream()
+        pending = sorted(requests, key=lambda r: (r.arrival, r.rid))
+        fp = {r.rid: r.footprint for r in pending}
+        waiting, running, finished = [], {}, []
+        used = 0
+        t0 = time.perf_counter()
+        nxt = 0
+        with pf.Batch(self.budget, stream=stream) as batch:
+            while nxt < len(pending) or waiting or running:
+                now = time.perf_counter() - t0
+                while nxt < len(pending) and (not realtime or pending[nxt].arrival <= now):
+                    r = pending[nxt]
+                    nxt += 1
+                    if fp[r.rid] > self.budget:
+                        r.error = "footprint %d B exceeds the memory budget %d B" % (fp[r.rid], self.budget)
+                        r.finished = now
+                        finished.append(r)
+                    else:
+                        waiting.append(r)
+                # admit in arrival order while the budget allows
+                while waiting and used + fp[waiting[0].rid] <= self.budget:
+                    r = waiting.pop(0)
+                    sim = pf.Simulation(r.prob, precision=r.precision, stream=stream, options=r.options)
+                    try:
+                        sim.set_state(r.u0)
+                        slot = batch.admit(sim, r.integ, r.t_end, tol=r.tol, dt_mult=r.dt_mult)
+                    except Exception as exc:
+                        sim.close()
+                        r.error = "%s (%s)" % (exc, r.describe())
+                        r.finished = time.perf_counter() - t0
+                        finished.append(r)
+                        continue
+                    if slot is None:                  # the library's accounting says no: later
+                        sim.close()
+                        waiting.insert(0, r)
+                        break
+                    used += fp[r.rid]
+                    self.peak_used = max(self.peak_used, used)
+                    r.admitted = time.perf_counter() - t0
+                    running[slot] = (r, sim)
+                if running:
+                    batch.run(self.rounds)
+                    for slot in list(running):
+                        res = batch.result(slot)
+                        if res is None:
+                            continue
+                        r, sim = running.pop(slot)
+                        status, st = res
+                        if status == pf.PF_OK:
+                            r.result, _ = sim.get_state()
+                            r.stats = st
+                        else:
+                            r.error = "status %d (%s)" % (status, r.describe())
+                        sim.close()
+                        used -= fp[r.rid]
+                        r.finished = time.perf_counter() - t0
+                        finished.append(r)
+                elif nxt < len(pending):
+                    time.sleep(max(0.0, min(0.05, pending[nxt].arrival - (time.perf_counter() - t0))))
+        return finished, time.perf_counter() - t0
 
 
 def poisson_stream(n, rate=50.0, seed=4, sizes2d=(64, 128, 256, 512, 1024), sizes3d=(64, 96, 128),
