@@ -141,7 +141,7 @@ def test_batch_admission_rules(pf):
         while batch.run(8):
             pass
         status, st = batch.result(sa)
-        assert status == pf.PF_OK and st["steps_accepted"] == 10
+        assert status == pf.PF_OK and st["steps_accepted"] == 12          # ceil(10 / 0.9) fixed steps
         assert batch.admit(b, pf.FEULER, 10 * b.dt_e(), dt_mult=0.9) is not None # budget freed
         while batch.run(8):
             pass
