@@ -250,10 +250,11 @@ def _front(liquid_row):
     return float(r[0]) if len(r) else float(j)
 
 
-def time_to_solution(pf, torch, stefan_t_end=4300.0):
-    """Wall time of each integrator/precision to t_end with outputs at exact
-    times, and its error against the sharp-interface law; FP64 forward Euler
-    at 0.9 dt_e sets the target error."""
+def time_to_solution(pf, torch):
+    """The shrinking circle (128^2, 2000 x 0.9 dt_e): wall time of each
+    integrator/precision to t_end with outputs at exact times, and its error
+    against the sharp-interface area law; FP64 forward Euler at 0.9 dt_e sets
+    the target error.  (The Stefan strip is the stefan_sweep section.)"""
     import numpy as np
     from paper_2601_16522_gb300 import inputs as I
     res = {}
@@ -287,35 +288,6 @@ def time_to_solution(pf, torch, stefan_t_end=4300.0):
         sim.close()
     res["circle128"] = {"t_end": "2000 x 0.9 dt_e", "error": "|<dA/dt> + 2 pi M gamma| / (2 pi M gamma)",
                         "variants": out}
-    # -- solutal Stefan strip, 1024 x 256, W = 5/pi, D 1:100 ------------------
-    prob, u = I.stefan(1024, 256, 200.0)
-    A = I.stefan_growth_constant()
-    variants = [("feuler", 64, dict(dt_mult=0.9)), ("rkl2", 32, dict(tol=(1e-4, 1e-2, 1e-4, 1e-4))),
-                ("rkl2", 64, dict(tol=(1e-4, 1e-2, 1e-4, 1e-4))), ("feuler", 32, dict(dt_mult=0.9)),
-                ("rkl2", 32, dict(tol=(1e-4, 1e-2, 1e-4, 1e-4), flags=dloop))]
-    out = []
-    x0 = _front(u[0][:1024])
-    for name, prec, kw in variants:
-        sim = pf.Simulation(prob, precision=prec, stream=stream)
-        sim.set_state(u)
-        times = np.linspace(0.0, stefan_t_end, 11)[1:]
-        integ = {"feuler": pf.FEULER, "rkl2": pf.RKL2}[name]
-        X = []
-        evals = 0
-        host = np.zeros((3, prob.V))
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for tk in times:
-            evals += sim.step(integ, float(tk), **kw)["rhs_evals"]
-            sim.get_state(out=host)
-            X.append(_front(host[0][:1024]) - x0)
-        torch.cuda.synchronize()
-        el = time.perf_counter() - t0
-        Afit = float((np.sqrt(times) * np.array(X)).sum() / times.sum())
-        out.append({"integrator": name + ("-device-loop" if kw.get("flags") else ""), "precision": prec,
-                    "wall_ms": 1e3 * el, "rhs_evals": evals, "A_fit": Afit, "rel_error": abs(Afit - A) / A})
-        sim.close()
-    res["stefan1024x256"] = {"t_end": stefan_t_end, "A_exact": A, "error": "|A* - A| / A", "variants": out}
     # speedups over FP64 FE among variants whose error is within 1.05x of its error
     for k, r in res.items():
         ref = [v for v in r["variants"] if v["integrator"] == "feuler" and v["precision"] == 64][0]
@@ -329,20 +301,51 @@ def time_to_solution(pf, torch, stefan_t_end=4300.0):
 
 def served_stream(pf, torch, n_requests, rate=50.0):
     """Poisson stream of mixed simulations through the continuous-batching
-    server; p50/p99 latency and aggregate GCell-updates/s."""
+    server on the library's batch (pf_batch_*: one stream, a round of steps
+    at a time, FP32 dense passes packed into shared launches); p50/p99
+    latency and aggregate GCell-updates/s."""
     from paper_2601_16522_gb300 import serve
     reqs = serve.poisson_stream(n_requests, rate=rate, seed=4, sizes2d=(64, 128, 256, 512, 1024),
-                                sizes3d=(64, 96), steps=100)
+                                sizes3d=(64, 96, 128, 192), steps=100, masked_grains=False)
     serve.finalize_end_times(reqs)
     free, total = torch.cuda.mem_get_info()
-    srv = serve.Server(mem_budget_bytes=int(0.5 * free), workers=8)
+    srv = serve.BatchServer(mem_budget_bytes=int(0.5 * free), rounds=4)
     finished, makespan = srv.serve(reqs, realtime=True)
     s = serve.summary(finished, makespan)
-    s.update({"arrival_rate_per_s": rate, "workers": 8, "mem_budget_bytes": srv.budget,
-              "peak_admitted_bytes": srv.peak_used,
-              "mix": "circles, Stefan strips, 2D/3D Voronoi grains (N 2..32, masked storage), FE/SSP2/RKL1/RKL2, FP32, "
+    s.update({"arrival_rate_per_s": rate, "server": "batch (pf_batch_*), 4 rounds per call",
+              "mem_budget_bytes": srv.budget, "peak_admitted_bytes": srv.peak_used,
+              "mix": "circles, Stefan strips (2D 64^2..1024^2), 2D/3D Voronoi grains (N 2..32, 3D 64^3..192^3, "
+                     "dense storage), FE/SSP(5)2 fixed and RKL1/RKL2/SSP(10)4 adaptive, FP32, "
                      "100 stable-Euler steps of simulated time each"})
     return s
+
+
+def fp64_fe_pass(pf, torch, dev, stream):
+    """Roofline of the FP64 forward Euler pass (the baseline of the
+    time-to-solution comparisons) on the 256^3 x 32 grain workload: 2 x 32
+    FP64 values per cell (read and write), timed over 3 passes."""
+    prob, u, _ = workload_problem("grains256", dev)
+    sim = pf.Simulation(prob, precision=64, stream=stream)
+    sim.set_state(u)
+    dte = sim.dt_e()
+    sim.step(pf.FEULER, 0.9 * dte, dt_mult=0.9)
+    sim.profile(1)
+    sim.step(pf.FEULER, 4 * 0.9 * dte, dt_mult=0.9, flags=pf.Simulation.STEP_NO_GRAPH)
+    prof = sim.profile(0)
+    sim.close()
+    ms, n = prof["euler"]
+    nbytes = 2 * prob.n_phases * 8 * prob.V
+    peak = _peak_gbs()
+    ach = nbytes / (ms / n * 1e-3) / 1e9
+    return {"workload": prob.name, "pass_ms": ms / n, "bytes_per_launch": nbytes, "achieved_gbs": ach,
+            "frac_of_measured_peak": ach / peak, "kernel": "cell_kernel<double,3,0,generic> (--fmad=false)"}
+
+
+def _peak_gbs():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0)
+    except (OSError, ValueError):
+        return 6800.0
 
 
 def masked_run(pf, torch, prob, u, stream, args, world, dev, dense_out, dense_pass_ms):
@@ -431,11 +434,16 @@ def reuse_run(pf, torch, prob, u, stream, args, world, dev, dense_out, dense_ms)
             "mean_abs_diff_to_dense": mean_diff, "cells_differing_over_1e-3": frac}
 
 
-def stefan_sweep(pf, torch, t_end=4300.0):
-    """The Stefan strip (1024 x 256, D 1:100) with each adaptive integrator
-    at r = a in {1e-3, 1e-4, 1e-5, 1e-6}, FP32 and FP64, beside forward
-    Euler at 0.9 dt_e: wall time, RHS sweeps, steps and the error of the
-    fitted growth constant against the exact A."""
+def stefan_sweep(pf, torch, t_end=43e3, full=False):
+    """The Stefan strip (1024 x 256, D 1:100) to the configuration's t_end
+    (43e3, front advance X ~ 50) with ten output times: forward Euler at
+    0.9 dt_e in FP64 and FP32, SSP(5)2 at 3.6 dt_e, and the adaptive schemes
+    at r = a in {1e-3 .. 1e-6}: wall time, RHS sweeps, steps, the error of the
+    fitted growth constant against the exact A, and the speed-up over FP64
+    forward Euler of every run whose error is within 1.05x of its error.
+    The default list is a bounded subset (RKL2 FP32 at every tolerance, RKL2
+    FP64, RKL1 and SSP(10)4 FP32 at 1e-3); full=True runs every integrator at
+    every tolerance in both precisions."""
     import numpy as np
     from paper_2601_16522_gb300 import inputs as I
     prob, u = I.stefan(1024, 256, 200.0)
@@ -443,15 +451,22 @@ def stefan_sweep(pf, torch, t_end=4300.0):
     x0 = _front(u[0][:1024])
     stream = torch.cuda.Stream()
     times = np.linspace(0.0, t_end, 11)[1:]
-    runs = [("feuler", 64, None, dict(dt_mult=0.9)), ("feuler", 32, None, dict(dt_mult=0.9))]
-    for tol in (1e-3, 1e-4, 1e-5, 1e-6):
-        for integ in ("rkl1", "rkl2", "ssp104"):
-            for prec in (32, 64):
-                runs.append((integ, prec, tol, dict(tol=(tol, tol, tol, tol))))
+    runs = [("feuler", 64, None, dict(dt_mult=0.9)), ("feuler", 32, None, dict(dt_mult=0.9)),
+            ("ssp2", 32, None, dict(dt_mult=3.6, ssp_stages=5))]
+    if full:
+        for tol in (1e-3, 1e-4, 1e-5, 1e-6):
+            for integ in ("rkl1", "rkl2", "ssp104"):
+                for prec in (32, 64):
+                    runs.append((integ, prec, tol, dict(tol=(tol, tol, tol, tol))))
+    else:
+        for tol in (1e-3, 1e-4, 1e-5, 1e-6):
+            runs.append(("rkl2", 32, tol, dict(tol=(tol, tol, tol, tol))))
+        for integ, prec in (("rkl2", 64), ("rkl1", 32), ("ssp104", 32)):
+            runs.append((integ, prec, 1e-3, dict(tol=(1e-3,) * 4)))
     out = []
     host = np.zeros((3, prob.V))
     for name, prec, tol, kw in runs:
-        integ = {"feuler": pf.FEULER, "rkl1": pf.RKL1, "rkl2": pf.RKL2, "ssp104": pf.SSP104}[name]
+        integ = {"feuler": pf.FEULER, "ssp2": pf.SSP2, "rkl1": pf.RKL1, "rkl2": pf.RKL2, "ssp104": pf.SSP104}[name]
         sim = pf.Simulation(prob, precision=prec, stream=stream)
         sim.set_state(u)
         X, evals, acc, rej = [], 0, 0, 0
@@ -470,10 +485,17 @@ def stefan_sweep(pf, torch, t_end=4300.0):
         Afit = float((np.sqrt(times) * np.array(X)).sum() / times.sum())
         out.append({"integrator": name, "precision": prec, "tol": tol, "wall_ms": 1e3 * el, "rhs_evals": evals,
                     "accepted": acc, "rejected": rej, "rel_error": abs(Afit - A) / A})
-    return {"t_end": t_end, "A_exact": A, "runs": out}
+    ref = out[0]
+    for r in out:
+        r["speedup_vs_fe64"] = ref["wall_ms"] / r["wall_ms"]
+        r["at_target_error"] = bool(r["rel_error"] <= 1.05 * ref["rel_error"] + 1e-12)
+    ok = [r for r in out if r["at_target_error"]]
+    best = min(ok, key=lambda r: r["wall_ms"])
+    return {"t_end": t_end, "A_exact": A, "target_error": ref["rel_error"], "runs": out,
+            "fastest_at_target": {k: best[k] for k in ("integrator", "precision", "tol", "speedup_vs_fe64")}}
 
 
-def grains_to_half(pf, torch, dev, stream, t_max=60.0, wall_cap_s=120.0):
+def grains_to_half(pf, torch, dev, stream, t_max=60.0, wall_cap_s=120.0, full=False):
     """The 256^3 grain workload run to the time at which half of the 32
     grains are gone (alive: max phi_a >= 0.5; the configuration's run
     length), adaptive RKL2 in FP32 with masked and with dense storage;
@@ -482,9 +504,11 @@ def grains_to_half(pf, torch, dev, stream, t_max=60.0, wall_cap_s=120.0):
     prob, u, _ = workload_problem("grains256", dev)
     out = []
     t_half = None
-    for name, integ, opts in (("rkl2-fp32-masked", pf.RKL2, pf.Simulation.OPT_MASKED),
-                              ("rkl2-fp32-dense", pf.RKL2, 0),
-                              ("rkl1-fp32-masked", pf.RKL1, pf.Simulation.OPT_MASKED)):
+    runs = [("rkl2-fp32-masked", pf.RKL2, pf.Simulation.OPT_MASKED)]
+    if full:
+        runs.append(("rkl2-fp32-dense", pf.RKL2, 0))
+    runs.append(("rkl1-fp32-masked", pf.RKL1, pf.Simulation.OPT_MASKED))
+    for name, integ, opts in runs:
         sim = pf.Simulation(prob, precision=32, stream=stream, options=opts)
         sim.set_state(u)
         dte = sim.dt_e()
@@ -543,10 +567,10 @@ def grains_to_half(pf, torch, dev, stream, t_max=60.0, wall_cap_s=120.0):
 def sinter_horizon(pf, torch, dev, stream, t_r=0.05, wall_cap_s=150.0):
     """The 320^3 sintering workload (64 grains + one pore phase + c) run
     with adaptive RKL2 in FP32 masked storage at r = a = 1e-4 towards the
-    configuration's fixed horizon t_r = 0.05 (about 1.8e5 stable Euler
-    steps), in output intervals of 0.0025, until the wall-clock cap.  A
-    step that meets more than 12 local phases in a cell ends the run with
-    PF_EINVAL; the time reached is reported."""
+    horizon t_r (the configuration's t_r = 0.05 is about 1.8e5 stable Euler
+    steps), in output intervals of 0.0025, until the wall-clock cap; the time
+    reached, RHS sweeps against forward Euler's and the conserved totals are
+    reported."""
     prob, u, _ = workload_problem("sinter320", dev)
     N = prob.n_phases
     tol = (1e-4, 1e-4, 1e-4, 1e-4)
@@ -739,30 +763,47 @@ def run_ours(args, world, rank, local):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        m = 48 if N <= 32 else 24
+        # the oracle on all host cores (OpenMP over the RHS rows) and on one
+        m = 64 if N <= 32 else 32
         sub, us = sub_box(prob, u, m)
-        v, el, sw = oracle_sample(us, sub)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "one RKL2 step (s=5) + error sweep on a %d^3 sub-box of the same state, %.1f s" % (m, el)}
+        from oracle import ref
+        ref.set_openmp(True)
+        try:
+            v, el, sw = oracle_sample(us, sub)
+        finally:
+            ref.set_openmp(False)
+        ms1 = 48 if N <= 32 else 24
+        sub1, us1 = sub_box(prob, u, ms1)
+        v1, el1, _ = oracle_sample(us1, sub1)
+        cores = os.cpu_count()
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "one RKL2 step (s=5) + error sweep on a %d^3 sub-box of the same state, %.1f s, "
+                         "OpenMP on all %d host cores (RHS rows shared)" % (m, el, cores),
+               "single_thread": {"value": v1, "cores": 1,
+                                 "sample": "the same step on a %d^3 sub-box, %.1f s" % (ms1, el1)}}
 
+    extras = rank == 0 and world == 1 and not args.quick
     tts = None
-    if rank == 0 and not args.no_tts:
+    if extras and not args.no_tts:
         tts = time_to_solution(pf, torch)
     served = None
-    if rank == 0 and args.served > 0:
+    if extras and args.served > 0:
         served = served_stream(pf, torch, args.served)
     to_half = None
-    if rank == 0 and args.grains_to_half:
-        to_half = grains_to_half(pf, torch, dev, stream)
+    if extras and not args.no_grains_to_half:
+        to_half = grains_to_half(pf, torch, dev, stream, full=args.full)
     sweep = None
-    if rank == 0 and args.stefan_sweep:
-        sweep = stefan_sweep(pf, torch)
+    if extras and not args.no_stefan_sweep:
+        sweep = stefan_sweep(pf, torch, full=args.full)
     horizon = None
-    if rank == 0 and args.sinter_horizon:
-        horizon = sinter_horizon(pf, torch, dev, stream)
+    if extras and not args.no_sinter:
+        horizon = sinter_horizon(pf, torch, dev, stream, t_r=0.05 if args.full else 0.01)
     prec_check = None
-    if rank == 0 and args.precision_check:
+    if extras and args.precision_check:
         prec_check = precision_check(pf, torch, dev, stream)
+    fe64 = None
+    if extras:
+        fe64 = fp64_fe_pass(pf, torch, dev, stream)
 
     if rank == 0:
         line = {
@@ -784,6 +825,7 @@ def run_ours(args, world, rank, local):
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
             "time_to_solution": tts, "served": served, "masked": masked, "reuse_rhs": reuse,
             "grains_to_half": to_half, "stefan_sweep": sweep, "sinter_horizon": horizon, "precision_check": prec_check,
+            "fp64_fe_pass": fe64,
         }
         print(json.dumps(line), flush=True)
     sim.close()
@@ -800,17 +842,18 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tma", action="store_true", help="TMA-staged kernels instead of plain loads")
     ap.add_argument("--no-tts", action="store_true", help="skip the 2D time-to-solution runs")
-    ap.add_argument("--served", type=int, default=48, help="requests in the served Poisson stream (0: skip)")
+    ap.add_argument("--served", type=int, default=2000, help="requests in the served Poisson stream (0: skip)")
+    ap.add_argument("--quick", action="store_true", help="only the headline steps (no configuration runs)")
+    ap.add_argument("--full", action="store_true",
+                    help="full configuration runs: every integrator/tolerance of the Stefan sweep, dense RKL2 "
+                         "to t_half, sintering to t_r = 0.05")
+    ap.add_argument("--no-grains-to-half", action="store_true")
+    ap.add_argument("--no-stefan-sweep", action="store_true")
+    ap.add_argument("--no-sinter", action="store_true")
     ap.add_argument("--no-masked", action="store_true", help="skip the masked-storage run")
     ap.add_argument("--no-reuse", action="store_true", help="skip the run that reuses F(u^{n+1})")
-    ap.add_argument("--stefan-sweep", action="store_true",
-                    help="also run the Stefan strip with every adaptive integrator at tolerances 1e-3..1e-6")
     ap.add_argument("--precision-check", action="store_true",
                     help="256^3 grain workload: FP32 against FP64, adaptive RKL2 to t = 2")
-    ap.add_argument("--sinter-horizon", action="store_true",
-                    help="320^3 sintering workload towards its fixed horizon t_r = 0.05 (RKL2, masked)")
-    ap.add_argument("--grains-to-half", action="store_true",
-                    help="also run the 256^3 grain workload until half of its grains are gone")
     args = ap.parse_args()
     world, rank, local = dist_setup(args)
     if args.impl == "reference":

@@ -14,6 +14,17 @@ import numpy as np
 from . import build as _build
 
 _lib = None
+_libs = {}
+_openmp = False
+
+
+def set_openmp(flag):
+    """Use the OpenMP build of the oracle (RHS loop shared among the host
+    cores; identical results) from now on: only for timing the all-core CPU
+    baseline."""
+    global _openmp, _lib
+    _openmp = bool(flag)
+    _lib = None
 
 FEULER, SSP2, SSP104, RKL1, RKL2 = 0, 1, 2, 3, 4
 _dp = C.POINTER(C.c_double)
@@ -54,8 +65,10 @@ class _Sys(C.Structure):
 
 def lib():
     global _lib
+    if _lib is None and _openmp in _libs:
+        _lib = _libs[_openmp]
     if _lib is None:
-        path = _build.build()
+        path = _build.build(openmp=_openmp)
         L = C.CDLL(path)
         L.or_rhs.argtypes = [C.POINTER(_Params), _dp, _dp, _ubp]
         L.or_project.argtypes = [C.POINTER(_Params), _dp, _ubp]
@@ -91,6 +104,7 @@ def lib():
         L.or_drive.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_int, C.c_int, _dp, _dp,
                                _dp, C.POINTER(_Ctrl), _dp, C.c_int, _dp, _ip, _ip]
         L.or_drive.restype = C.c_int
+        _libs[_openmp] = L
         _lib = L
     return _lib
 

@@ -280,11 +280,12 @@ class BatchServer:
         return finished, time.perf_counter() - t0
 
 
-def poisson_stream(n, rate=50.0, seed=4, sizes2d=(64, 128, 256, 512, 1024), sizes3d=(64, 96, 128),
-                   phases=(2, 3, 8, 16, 32), steps=100, device="cuda"):
+def poisson_stream(n, rate=50.0, seed=4, sizes2d=(64, 128, 256, 512, 1024), sizes3d=(64, 96, 128, 192),
+                   phases=(2, 3, 8, 16, 32), steps=100, device="cuda", masked_grains=True):
     """Seeded mixed stream shaped like the paper's benchmarks: shrinking
     circles and Stefan strips (2D, N = 2) and Voronoi grain structures (2D/3D,
-    N up to 32, in masked storage); integrators and tolerances drawn
+    N up to 32, in masked storage unless masked_grains is False); integrators
+    (FE, SSP(5)2, RKL1, RKL2, adaptive SSP(10)4) and tolerances drawn
     uniformly.  Each request runs for `steps` stable Euler steps of
     simulated time."""
     rng = np.random.default_rng(seed)
@@ -308,12 +309,12 @@ def poisson_stream(n, rate=50.0, seed=4, sizes2d=(64, 128, 256, 512, 1024), size
                                       seed=int(rng.integers(1 << 30)), dim=dim, dx=1.0, W_cells=2.5, M=1.0,
                                       device=device)
             u = u.cpu().numpy()
-        integ = int(rng.choice([pf.FEULER, pf.RKL1, pf.RKL2, pf.SSP2]))
+        integ = int(rng.choice([pf.FEULER, pf.RKL1, pf.RKL2, pf.SSP2, pf.SSP104]))
         a_phi = float(rng.choice([1e-2, 1e-3, 1e-4]))
         # grain structures run in masked storage (only occupied phases are loaded)
-        opts = pf.Simulation.OPT_MASKED if kind == 2 else 0
+        opts = pf.Simulation.OPT_MASKED if (kind == 2 and masked_grains) else 0
         req = Request(rid=rid, prob=prob, u0=u, integ=integ, t_end=0.0, arrival=t, options=opts)
-        if integ in (pf.RKL1, pf.RKL2):
+        if integ in (pf.RKL1, pf.RKL2, pf.SSP104):
             req.tol = (1e-4, a_phi, 1e-4, 1e-4)
         else:
             req.dt_mult = 0.9 if integ == pf.FEULER else 2.0

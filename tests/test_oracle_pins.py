@@ -689,3 +689,24 @@ def test_reduce_on_hand_built_states():
     u3[0] = 1.0 - u3[1]
     mass3, vol3, alive3 = ref.Oracle(prob3).reduce(u3)
     assert vol3[1] == 5 * 8.0 and vol3[0] == 19 * 8.0 and mass3 == 0.0 and alive3 == 2
+
+
+def test_openmp_build_gives_the_same_rhs():
+    # the all-core build shares the RHS rows among threads; every cell is
+    # computed from the input alone, so the result is bit for bit the same
+    import os
+    prob, u = I.multiphase_blobs(21, 17, 9, 6, seed=5, has_conc=1, n_alpha=2)
+    r1, nz1 = ref.Oracle(prob).rhs(u)
+    old = os.environ.get("OMP_NUM_THREADS")
+    os.environ["OMP_NUM_THREADS"] = "4"
+    try:
+        ref.set_openmp(True)
+        r2, nz2 = ref.Oracle(prob).rhs(u)
+    finally:
+        ref.set_openmp(False)
+        if old is None:
+            os.environ.pop("OMP_NUM_THREADS", None)
+        else:
+            os.environ["OMP_NUM_THREADS"] = old
+    np.testing.assert_array_equal(r1, r2)
+    np.testing.assert_array_equal(nz1, nz2)

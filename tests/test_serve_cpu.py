@@ -139,7 +139,8 @@ def test_cancellation_of_queued_and_running_requests():
 def test_poisson_stream_follows_its_recipe():
     # The served stream's recipe: Poisson arrivals (mean rate 50/s, seed 4),
     # 2D circles and Stefan strips (N = 2), 2D/3D Voronoi grain structures
-    # with 2..32 phases in masked storage, the four integrators, each request
+    # with 2..32 phases in masked storage, the five integrators (SSP(10)4 and
+    # the RKL schemes adaptive), each request
     # carrying its own state of the right shape; the same seed gives the same
     # stream.
     from paper_2601_16522_gb300 import serve
@@ -155,8 +156,8 @@ def test_poisson_stream_follows_its_recipe():
         p = r.prob
         assert r.u0.shape == (p.n_phases + p.has_conc, p.V)
         assert np.allclose(r.u0[:p.n_phases].sum(0), 1.0, atol=1e-12)
-        assert r.integ in (0, 1, 3, 4)
-        assert (r.tol is not None) == (r.integ in (3, 4))
+        assert r.integ in (0, 1, 2, 3, 4)
+        assert (r.tol is not None) == (r.integ in (2, 3, 4))
         if p.name.startswith("grains"):
             kinds.add("grains")
             assert 2 <= p.n_phases <= 32 and r.options == 2
