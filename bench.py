@@ -306,16 +306,17 @@ def served_stream(pf, torch, n_requests, rate=50.0):
     latency and aggregate GCell-updates/s."""
     from paper_2601_16522_gb300 import serve
     reqs = serve.poisson_stream(n_requests, rate=rate, seed=4, sizes2d=(64, 128, 256, 512, 1024),
-                                sizes3d=(64, 96, 128, 192), steps=100, masked_grains=False)
+                                sizes3d=(64, 96, 128, 192), steps=100, masked_grains=True)
     serve.finalize_end_times(reqs)
     free, total = torch.cuda.mem_get_info()
     srv = serve.BatchServer(mem_budget_bytes=int(0.5 * free), rounds=4)
+    lanes = "lanes by cells x fields < 2^20, < 2^24, larger (one batch, stream and thread each)"
     finished, makespan = srv.serve(reqs, realtime=True)
     s = serve.summary(finished, makespan)
-    s.update({"arrival_rate_per_s": rate, "server": "batch (pf_batch_*), 4 rounds per call",
+    s.update({"arrival_rate_per_s": rate, "server": "batch (pf_batch_*), 4 rounds per call, " + lanes,
               "mem_budget_bytes": srv.budget, "peak_admitted_bytes": srv.peak_used,
               "mix": "circles, Stefan strips (2D 64^2..1024^2), 2D/3D Voronoi grains (N 2..32, 3D 64^3..192^3, "
-                     "dense storage), FE/SSP(5)2 fixed and RKL1/RKL2/SSP(10)4 adaptive, FP32, "
+                     "masked storage), FE/SSP(5)2 fixed and RKL1/RKL2/SSP(10)4 adaptive, FP32, "
                      "100 stable-Euler steps of simulated time each"})
     return s
 

@@ -200,71 +200,67 @@ class Server:
 
 
 class BatchServer:
-    """Continuous batching through the library's batch (pf_batch_*): every
-    admitted request gets a handle on the server's one stream and is
-    admitted into the batch by its footprint; the batch advances all of them
-    a round at a time (one step or attempt each, the passes of FP32 dense
-    problems packed into shared launches, one transfer of error norms and
-    flags per round).  Arrivals are admitted between rounds as memory frees
-    up; finished requests leave with their state and statistics.  A result
-    equals the request run alone (the batch keeps pf_step's bookkeeping).
+    """Continuous batching through the library's batch (pf_batch_*).
 
+    Requests are sorted into lanes by the work of one step (cells times
+    fields); every lane is one pf.Batch on its own CUDA stream, driven by its
+    own thread (ctypes releases the GIL while the library runs), so lanes
+    overlap on the GPU and a small request is not held back by the rounds of
+    a large one.  Within a lane the batch advances all admitted requests a
+    round at a time (one step or attempt each, the passes of FP32 dense
+    problems packed into shared launches, one transfer of error norms and
+    flags per round).  Arrivals are admitted, in arrival order, while the
+    server's memory budget allows; finished requests leave with their state
+    and statistics.  A result equals the request run alone (the batch keeps
+    pf_step's bookkeeping).
+
+    lane_bounds: upper bounds of cells x fields of all lanes but the last;
     rounds: rounds per batch call between admission checks."""
 
-    def __init__(self, mem_budget_bytes: int, rounds: int = 4):
+    def __init__(self, mem_budget_bytes: int, rounds: int = 4, lane_bounds=(1 << 20, 1 << 24)):
         self.budget = int(mem_budget_bytes)
         self.rounds = int(rounds)
+        self.lane_bounds = tuple(lane_bounds)
         self.peak_used = 0
+
+    def _lane(self, r):
+        w = r.prob.V * (r.prob.n_phases + r.prob.has_conc)
+        for k, b in enumerate(self.lane_bounds):
+            if w < b:
+                return k
+        return len(self.lane_bounds)
 
     def serve(self, requests, realtime=True):
         import torch
-        stream = torch.cuda.Stream()
+        dev = torch.cuda.current_device()
+        nl = len(self.lane_bounds) + 1
+        streams = [torch.cuda.Stream(device=dev) for _ in range(nl)]
+        batches = [pf.Batch(self.budget, stream=st) for st in streams]
+        locks = [threading.Lock() for _ in range(nl)]
+        running = [dict() for _ in range(nl)]          # slot -> (request, simulation)
+        cv = threading.Condition()
+        state = {"used": 0, "stop": False}
+        finished = []
         pending = sorted(requests, key=lambda r: (r.arrival, r.rid))
         fp = {r.rid: r.footprint for r in pending}
-        waiting, running, finished = [], {}, []
-        used = 0
         t0 = time.perf_counter()
-        nxt = 0
-        with pf.Batch(self.budget, stream=stream) as batch:
-            while nxt < len(pending) or waiting or running:
-                now = time.perf_counter() - t0
-                while nxt < len(pending) and (not realtime or pending[nxt].arrival <= now):
-                    r = pending[nxt]
-                    nxt += 1
-                    if fp[r.rid] > self.budget:
-                        r.error = "footprint %d B exceeds the memory budget %d B" % (fp[r.rid], self.budget)
-                        r.finished = now
-                        finished.append(r)
-                    else:
-                        waiting.append(r)
-                # admit in arrival order while the budget allows
-                while waiting and used + fp[waiting[0].rid] <= self.budget:
-                    r = waiting.pop(0)
-                    sim = pf.Simulation(r.prob, precision=r.precision, stream=stream, options=r.options)
-                    try:
-                        sim.set_state(r.u0)
-                        slot = batch.admit(sim, r.integ, r.t_end, tol=r.tol, dt_mult=r.dt_mult)
-                    except Exception as exc:
-                        sim.close()
-                        r.error = "%s (%s)" % (exc, r.describe())
-                        r.finished = time.perf_counter() - t0
-                        finished.append(r)
-                        continue
-                    if slot is None:                  # the library's accounting says no: later
-                        sim.close()
-                        waiting.insert(0, r)
-                        break
-                    used += fp[r.rid]
-                    self.peak_used = max(self.peak_used, used)
-                    r.admitted = time.perf_counter() - t0
-                    running[slot] = (r, sim)
-                if running:
-                    batch.run(self.rounds)
-                    for slot in list(running):
-                        res = batch.result(slot)
+
+        def drive(k):
+            torch.cuda.set_device(dev)
+            while True:
+                with cv:
+                    while not running[k] and not state["stop"]:
+                        cv.wait(0.05)
+                    if state["stop"] and not running[k]:
+                        return
+                with locks[k]:
+                    batches[k].run(self.rounds)
+                    done = []
+                    for slot in list(running[k]):
+                        res = batches[k].result(slot)
                         if res is None:
                             continue
-                        r, sim = running.pop(slot)
+                        r, sim = running[k].pop(slot)
                         status, st = res
                         if status == pf.PF_OK:
                             r.result, _ = sim.get_state()
@@ -272,11 +268,80 @@ class BatchServer:
                         else:
                             r.error = "status %d (%s)" % (status, r.describe())
                         sim.close()
-                        used -= fp[r.rid]
                         r.finished = time.perf_counter() - t0
-                        finished.append(r)
-                elif nxt < len(pending):
-                    time.sleep(max(0.0, min(0.05, pending[nxt].arrival - (time.perf_counter() - t0))))
+                        done.append(r)
+                if done:
+                    with cv:
+                        for r in done:
+                            state["used"] -= fp[r.rid]
+                            finished.append(r)
+                        cv.notify_all()
+
+        threads = [threading.Thread(target=drive, args=(k,), daemon=True) for k in range(nl)]
+        for th in threads:
+            th.start()
+        waiting = []
+        nxt = 0
+        try:
+            while True:
+                now = time.perf_counter() - t0
+                while nxt < len(pending) and (not realtime or pending[nxt].arrival <= now):
+                    r = pending[nxt]
+                    nxt += 1
+                    if fp[r.rid] > self.budget:
+                        r.error = "footprint %d B exceeds the memory budget %d B" % (fp[r.rid], self.budget)
+                        r.finished = now
+                        with cv:
+                            finished.append(r)
+                    else:
+                        waiting.append(r)
+                # admit in arrival order while the budget allows
+                while waiting:
+                    r = waiting[0]
+                    with cv:
+                        if state["used"] + fp[r.rid] > self.budget:
+                            break
+                        state["used"] += fp[r.rid]
+                        self.peak_used = max(self.peak_used, state["used"])
+                    waiting.pop(0)
+                    k = self._lane(r)
+                    err = None
+                    with locks[k]:
+                        sim = pf.Simulation(r.prob, precision=r.precision, stream=streams[k], options=r.options)
+                        try:
+                            sim.set_state(r.u0)
+                            slot = batches[k].admit(sim, r.integ, r.t_end, tol=r.tol, dt_mult=r.dt_mult)
+                            if slot is None:
+                                err = "not admitted by the batch (%s)" % r.describe()
+                        except Exception as exc:
+                            err = "%s (%s)" % (exc, r.describe())
+                        if err is None:
+                            r.admitted = time.perf_counter() - t0
+                            running[k][slot] = (r, sim)
+                        else:
+                            sim.close()
+                    with cv:
+                        if err is not None:
+                            r.error = err
+                            r.finished = time.perf_counter() - t0
+                            state["used"] -= fp[r.rid]
+                            finished.append(r)
+                        cv.notify_all()
+                with cv:
+                    if nxt >= len(pending) and not waiting and len(finished) == len(pending):
+                        break
+                    wait = 0.002
+                    if nxt < len(pending) and realtime:
+                        wait = max(0.0005, min(0.01, pending[nxt].arrival - (time.perf_counter() - t0)))
+                    cv.wait(wait)
+        finally:
+            with cv:
+                state["stop"] = True
+                cv.notify_all()
+            for th in threads:
+                th.join()
+            for b in batches:
+                b.close()
         return finished, time.perf_counter() - t0
 
 

@@ -68,3 +68,29 @@ def test_tight_budget_still_completes(env):
     finished, _ = srv.serve(reqs, realtime=False)
     assert all(r.error is None for r in finished) and len(finished) == len(reqs)
     assert srv.peak_used <= biggest
+
+
+@pytest.mark.parametrize("bounds", [(1 << 20, 1 << 24), ()], ids=["three-lanes", "one-lane"])
+def test_batch_server_alone_equals_mixed(env, bounds):
+    # the batch server (pf_batch_*, packed launches, lanes on their own
+    # streams and threads) gives every request the result it has alone
+    torch, pf, serve = env
+    alone = {}
+    for r in requests(pf, serve):
+        out, st = serve.run_alone(r)
+        alone[r.rid] = (out, st["rhs_evals"])
+    reqs = requests(pf, serve)
+    srv = serve.BatchServer(mem_budget_bytes=8 << 30, rounds=3, lane_bounds=bounds)
+    finished, makespan = srv.serve(reqs, realtime=True)
+    assert len(finished) == len(reqs)
+    for r in finished:
+        assert r.error is None, r.error
+        np.testing.assert_array_equal(r.result, alone[r.rid][0])
+        assert r.stats["rhs_evals"] == alone[r.rid][1]
+    # a budget that holds only the largest request at a time
+    reqs = requests(pf, serve)
+    biggest = max(pf.footprint(r.prob, r.precision) for r in reqs)
+    srv = serve.BatchServer(mem_budget_bytes=biggest, rounds=2, lane_bounds=bounds)
+    finished, _ = srv.serve(reqs, realtime=False)
+    assert all(r.error is None for r in finished) and len(finished) == len(reqs)
+    assert srv.peak_used <= biggest
