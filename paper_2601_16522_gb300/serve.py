@@ -215,12 +215,16 @@ class BatchServer:
     pf_step's bookkeeping).
 
     lane_bounds: upper bounds of cells x fields of all lanes but the last;
-    rounds: rounds per batch call between admission checks."""
+    rounds: rounds per batch call between admission checks; lane_cap: the
+    most requests a lane runs at a time (arrivals queue per lane in arrival
+    order, so that under load the early requests finish first instead of
+    every request sharing the GPU with all later ones)."""
 
-    def __init__(self, mem_budget_bytes: int, rounds: int = 4, lane_bounds=(1 << 20, 1 << 24)):
+    def __init__(self, mem_budget_bytes: int, rounds: int = 4, lane_bounds=(1 << 20, 1 << 24), lane_cap=64):
         self.budget = int(mem_budget_bytes)
         self.rounds = int(rounds)
         self.lane_bounds = tuple(lane_bounds)
+        self.lane_cap = int(lane_cap)
         self.peak_used = 0
 
     def _lane(self, r):
@@ -280,7 +284,7 @@ class BatchServer:
         threads = [threading.Thread(target=drive, args=(k,), daemon=True) for k in range(nl)]
         for th in threads:
             th.start()
-        waiting = []
+        waiting = [[] for _ in range(nl)]              # per lane, arrival order
         nxt = 0
         try:
             while True:
@@ -294,41 +298,41 @@ class BatchServer:
                         with cv:
                             finished.append(r)
                     else:
-                        waiting.append(r)
-                # admit in arrival order while the budget allows
-                while waiting:
-                    r = waiting[0]
-                    with cv:
-                        if state["used"] + fp[r.rid] > self.budget:
-                            break
-                        state["used"] += fp[r.rid]
-                        self.peak_used = max(self.peak_used, state["used"])
-                    waiting.pop(0)
-                    k = self._lane(r)
-                    err = None
-                    with locks[k]:
-                        sim = pf.Simulation(r.prob, precision=r.precision, stream=streams[k], options=r.options)
-                        try:
-                            sim.set_state(r.u0)
-                            slot = batches[k].admit(sim, r.integ, r.t_end, tol=r.tol, dt_mult=r.dt_mult)
-                            if slot is None:
-                                err = "not admitted by the batch (%s)" % r.describe()
-                        except Exception as exc:
-                            err = "%s (%s)" % (exc, r.describe())
-                        if err is None:
-                            r.admitted = time.perf_counter() - t0
-                            running[k][slot] = (r, sim)
-                        else:
-                            sim.close()
-                    with cv:
-                        if err is not None:
-                            r.error = err
-                            r.finished = time.perf_counter() - t0
-                            state["used"] -= fp[r.rid]
-                            finished.append(r)
-                        cv.notify_all()
+                        waiting[self._lane(r)].append(r)
+                # admit in arrival order per lane while the lane has room and the budget allows
+                for k in range(nl):
+                    while waiting[k]:
+                        r = waiting[k][0]
+                        with cv:
+                            if state["used"] + fp[r.rid] > self.budget or len(running[k]) >= self.lane_cap:
+                                break
+                            state["used"] += fp[r.rid]
+                            self.peak_used = max(self.peak_used, state["used"])
+                        waiting[k].pop(0)
+                        err = None
+                        with locks[k]:
+                            sim = pf.Simulation(r.prob, precision=r.precision, stream=streams[k], options=r.options)
+                            try:
+                                sim.set_state(r.u0)
+                                slot = batches[k].admit(sim, r.integ, r.t_end, tol=r.tol, dt_mult=r.dt_mult)
+                                if slot is None:
+                                    err = "not admitted by the batch (%s)" % r.describe()
+                            except Exception as exc:
+                                err = "%s (%s)" % (exc, r.describe())
+                            if err is None:
+                                r.admitted = time.perf_counter() - t0
+                                running[k][slot] = (r, sim)
+                            else:
+                                sim.close()
+                        with cv:
+                            if err is not None:
+                                r.error = err
+                                r.finished = time.perf_counter() - t0
+                                state["used"] -= fp[r.rid]
+                                finished.append(r)
+                            cv.notify_all()
                 with cv:
-                    if nxt >= len(pending) and not waiting and len(finished) == len(pending):
+                    if nxt >= len(pending) and not any(waiting) and len(finished) == len(pending):
                         break
                     wait = 0.002
                     if nxt < len(pending) and realtime:
