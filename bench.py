@@ -608,6 +608,52 @@ def sinter_horizon(pf, torch, dev, stream, t_r=0.05, wall_cap_s=150.0):
             "solute_change": float(abs(m1 - m0) / m0)}
 
 
+def zener_sts(pf, torch, dev, stream, n=128, n_grains=32, t_eq=0.05, t_run=1.0):
+    """Grain growth with immobile particles (Sec. 5.3, Zener pinning; the
+    paper's 11.5x case, Tab. perf-ggpores, on a 400^3 domain to t_r = 884):
+    n^3 cells, particles of radius 6 at volume fraction 0.15, masked FP32
+    storage.  An equilibration segment (the equilibration parameters, RKL2
+    to t_eq) is followed by the immobile run with adaptive RKL2 over t_run
+    time units; the RHS sweeps are compared with the stable Euler steps the
+    same interval takes (t_run / dt_e).  More than 12 nontrivial phases per
+    cell appear at the particle fringes under the STS schemes; those cells
+    take the wide path."""
+    from paper_2601_16522_gb300 import inputs as I
+    prob, u = I.zener_device(n=n, n_grains=n_grains, device=dev)
+    opts = pf.Simulation.OPT_MASKED
+    eq = pf.Simulation(I.zener_equilibration(prob), precision=32, stream=stream, options=opts)
+    eq.set_state(u)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st_eq = eq.step(pf.RKL2, t_eq, tol=(1e-4, 1e-2, 1e-4, 1e-3))
+    u1 = torch.empty_like(u)
+    eq.get_state(out=u1)
+    torch.cuda.synchronize()
+    eq.close()
+    sim = pf.Simulation(prob, precision=32, stream=stream, options=opts)
+    dte = sim.dt_e()
+    sim.set_state(u1, t=0.0)
+    evals, acc, rej = 0, 0, 0
+    tol = (1e-4, 1e-2, 1e-4, 1e-3)
+    t1 = time.perf_counter()
+    for k in range(1, 11):
+        st = sim.step(pf.RKL2, k * t_run / 10, tol=tol)
+        evals += st["rhs_evals"]
+        acc += st["steps_accepted"]
+        rej += st["steps_rejected"]
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t1
+    _, _, nz = sim.get_state(out=torch.empty_like(u1), with_nz=True)
+    torch.cuda.synchronize()
+    sim.close()
+    fe = t_run / dte
+    return {"workload": prob.name, "cells": prob.V, "phases": prob.n_phases, "dt_e": dte, "tol": tol,
+            "equilibration": {"t": t_eq, "rhs_evals": st_eq["rhs_evals"], "wall_s": t1 - t0},
+            "t_run": t_run, "rhs_evals": evals, "accepted": acc, "rejected": rej, "wall_s": wall,
+            "fe_steps": fe, "rhs_ratio_vs_fe": fe / max(evals, 1), "paper_ratio": 14110453 / 1224604,
+            "max_nontrivial_phases_per_cell": int(nz.max().item())}
+
+
 def precision_check(pf, torch, dev, stream, t_end=2.0):
     """FP32 against FP64 on the 256^3 grain workload: adaptive RKL2 from the
     same initial state to the same time t_end (about 2400 stable Euler steps)
@@ -805,6 +851,9 @@ def run_ours(args, world, rank, local):
     fe64 = None
     if extras:
         fe64 = fp64_fe_pass(pf, torch, dev, stream)
+    zener = None
+    if extras and not args.no_zener:
+        zener = zener_sts(pf, torch, dev, stream)
 
     if rank == 0:
         line = {
@@ -826,7 +875,7 @@ def run_ours(args, world, rank, local):
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
             "time_to_solution": tts, "served": served, "masked": masked, "reuse_rhs": reuse,
             "grains_to_half": to_half, "stefan_sweep": sweep, "sinter_horizon": horizon, "precision_check": prec_check,
-            "fp64_fe_pass": fe64,
+            "fp64_fe_pass": fe64, "zener_sts": zener,
         }
         print(json.dumps(line), flush=True)
     sim.close()
@@ -851,6 +900,7 @@ def main():
     ap.add_argument("--no-grains-to-half", action="store_true")
     ap.add_argument("--no-stefan-sweep", action="store_true")
     ap.add_argument("--no-sinter", action="store_true")
+    ap.add_argument("--no-zener", action="store_true")
     ap.add_argument("--no-masked", action="store_true", help="skip the masked-storage run")
     ap.add_argument("--no-reuse", action="store_true", help="skip the run that reuses F(u^{n+1})")
     ap.add_argument("--precision-check", action="store_true",
