@@ -54,10 +54,9 @@ def workload_problem(name, device):
 
 # algorithmic vectors moved per pass kind (reads + writes of whole state vectors)
 PASS_VECTORS = {"rkl2": 5, "rkl1": 3, "sts_first": 3, "sts_err": 3, "euler": 2, "ssp": 2, "rhs": 1}
-# DRAM bytes (read + write) per cell of one RKL2 stage pass on this workload's
-# 32-phase FP32 state, from an ncu capture of the 128^3 case (1.316 GB per
-# launch for 2,097,152 cells); traffic grows in proportion to the cells.
-RKL2_TRAFFIC_PER_CELL = {"grains256": 1.316e9 / 2097152, "grains128": 1.316e9 / 2097152}
+# DRAM bytes (read + write) per cell of one RKL2 stage pass (two-cell kernel,
+# 32-phase FP32 state) from ncu captures of that launch on each workload
+RKL2_TRAFFIC_PER_CELL = {}
 
 
 class ClockSampler:
@@ -130,15 +129,18 @@ def barrier(world):
         dist.barrier()
 
 
-def kernel_name(prob, prec, tma):
-    """Which stage kernel the library dispatches for this problem."""
+def kernel_name(prob, prec, variant):
+    """Which stage kernel the library dispatches for this problem's RKL2
+    passes (variant: the kernel variant the handle uses)."""
     K = prob.has_conc
     if prec == 64:
         return "cell_kernel<double,%d,%d,generic>" % (prob.dim, K)
     if prob.n_phases > 32:
         return "big_kernel<%d,%d,sig>" % (prob.dim, K)
-    if tma and prob.dim == 3 and prob.n_phases > 4:
+    if variant == "tma" and prob.dim == 3 and prob.n_phases > 4:
         return "tma_kernel<%d,sig>" % K
+    if variant == "two_cell" and prob.nx % 2 == 0:
+        return "vec_kernel<%d,%d,sig> + wide_fix_kernel" % (prob.dim, K)
     return "fast_kernel<%d,%d,sig,%d>" % (prob.dim, K, 4 if prob.n_phases <= 4 else 32)
 
 
@@ -499,7 +501,8 @@ def stefan_sweep(pf, torch, t_end=43e3, full=False):
 def grains_to_half(pf, torch, dev, stream, t_max=60.0, wall_cap_s=120.0, full=False):
     """The 256^3 grain workload run to the time at which half of the 32
     grains are gone (alive: max phi_a >= 0.5; the configuration's run
-    length), adaptive RKL2 in FP32 with masked and with dense storage;
+    length), adaptive RKL2 in FP32 with masked and with dense storage,
+    adaptive RKL1 and SSP(10)4 in masked storage (each stops at the wall cap);
     forward Euler in FP64 at 0.9 dt_e is estimated from its measured time
     per step times the steps it would need."""
     prob, u, _ = workload_problem("grains256", dev)
@@ -509,6 +512,7 @@ def grains_to_half(pf, torch, dev, stream, t_max=60.0, wall_cap_s=120.0, full=Fa
     if full:
         runs.append(("rkl2-fp32-dense", pf.RKL2, 0))
     runs.append(("rkl1-fp32-masked", pf.RKL1, pf.Simulation.OPT_MASKED))
+    runs.append(("ssp104-fp32-masked", pf.SSP104, pf.Simulation.OPT_MASKED))
     for name, integ, opts in runs:
         sim = pf.Simulation(prob, precision=32, stream=stream, options=opts)
         sim.set_state(u)
@@ -608,16 +612,18 @@ def sinter_horizon(pf, torch, dev, stream, t_r=0.05, wall_cap_s=150.0):
             "solute_change": float(abs(m1 - m0) / m0)}
 
 
-def zener_sts(pf, torch, dev, stream, n=128, n_grains=32, t_eq=0.05, t_run=1.0):
+def zener_sts(pf, torch, dev, stream, n=128, n_grains=32, t_eq=5.0, t_run=10.0):
     """Grain growth with immobile particles (Sec. 5.3, Zener pinning; the
     paper's 11.5x case, Tab. perf-ggpores, on a 400^3 domain to t_r = 884):
     n^3 cells, particles of radius 6 at volume fraction 0.15, masked FP32
-    storage.  An equilibration segment (the equilibration parameters, RKL2
-    to t_eq) is followed by the immobile run with adaptive RKL2 over t_run
-    time units; the RHS sweeps are compared with the stable Euler steps the
-    same interval takes (t_run / dt_e).  More than 12 nontrivial phases per
-    cell appear at the particle fringes under the STS schemes; those cells
-    take the wide path."""
+    storage.  The equilibration run of Sec. 5.3 (its parameters, adaptive
+    RKL2 to t_eq = 5) is followed by the immobile run with adaptive RKL2 over
+    t_run time units; the RHS sweeps are compared with the stable Euler steps
+    the same interval takes (t_run / dt_e).  More than 12 nontrivial phases
+    per cell appear at the particle fringes under the STS schemes; those
+    cells take the wide path.  The same immobile run is repeated for the
+    first time unit with the mobility-weighted projection (dense storage,
+    generic passes) beside the standard one."""
     from paper_2601_16522_gb300 import inputs as I
     prob, u = I.zener_device(n=n, n_grains=n_grains, device=dev)
     opts = pf.Simulation.OPT_MASKED
@@ -637,7 +643,7 @@ def zener_sts(pf, torch, dev, stream, n=128, n_grains=32, t_eq=0.05, t_run=1.0):
     tol = (1e-4, 1e-2, 1e-4, 1e-3)
     t1 = time.perf_counter()
     for k in range(1, 11):
-        st = sim.step(pf.RKL2, k * t_run / 10, tol=tol)
+        st = sim.step(pf.RKL2, k * t_run / 10, tol=tol)    # ten output times
         evals += st["rhs_evals"]
         acc += st["steps_accepted"]
         rej += st["steps_rejected"]
@@ -646,12 +652,27 @@ def zener_sts(pf, torch, dev, stream, n=128, n_grains=32, t_eq=0.05, t_run=1.0):
     _, _, nz = sim.get_state(out=torch.empty_like(u1), with_nz=True)
     torch.cuda.synchronize()
     sim.close()
+    # the first time unit with each projection (dense storage, same state)
+    proj = {}
+    for name, p in (("standard", prob), ("mobility-weighted", prob.with_(simplex=1))):
+        sim = pf.Simulation(p, precision=32, stream=stream)
+        sim.set_state(u1, t=0.0)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        st = sim.step(pf.RKL2, 1.0, tol=tol)
+        torch.cuda.synchronize()
+        _, _, nzp = sim.get_state(out=torch.empty_like(u1), with_nz=True)
+        torch.cuda.synchronize()
+        proj[name] = {"t": 1.0, "rhs_evals": st["rhs_evals"], "accepted": st["steps_accepted"],
+                      "rejected": st["steps_rejected"], "wall_s": time.perf_counter() - t2,
+                      "max_nontrivial_phases_per_cell": int(nzp.max().item())}
+        sim.close()
     fe = t_run / dte
     return {"workload": prob.name, "cells": prob.V, "phases": prob.n_phases, "dt_e": dte, "tol": tol,
             "equilibration": {"t": t_eq, "rhs_evals": st_eq["rhs_evals"], "wall_s": t1 - t0},
             "t_run": t_run, "rhs_evals": evals, "accepted": acc, "rejected": rej, "wall_s": wall,
             "fe_steps": fe, "rhs_ratio_vs_fe": fe / max(evals, 1), "paper_ratio": 14110453 / 1224604,
-            "max_nontrivial_phases_per_cell": int(nz.max().item())}
+            "max_nontrivial_phases_per_cell": int(nz.max().item()), "projections": proj}
 
 
 def precision_check(pf, torch, dev, stream, t_end=2.0):
@@ -759,13 +780,12 @@ def run_ours(args, world, rank, local):
         ms_k, n_k = kinds[dom]
         bytes_launch = PASS_VECTORS[dom] * vec_bytes
         achieved = bytes_launch / (ms_k / n_k * 1e-3) / 1e9
+        variant = "tma" if args.tma else (tuned["choice"] if tuned else "two_cell")
         traffic = None
-        if (dom == "rkl2" and args.workload in RKL2_TRAFFIC_PER_CELL and not args.tma
-                and not (tuned and tuned["choice"] == "tma")):
+        if dom == "rkl2" and args.workload in RKL2_TRAFFIC_PER_CELL and variant == "two_cell":
             traffic = RKL2_TRAFFIC_PER_CELL[args.workload] * V
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": kernel_name(prob, prec, (tuned and tuned["choice"] == "tma") or args.tma)
-                + " (%s pass)" % dom,
+                "traffic": traffic, "kernel": kernel_name(prob, prec, variant) + " (%s pass)" % dom,
                 "bytes_per_launch": bytes_launch, "avg_launch_ms": ms_k / n_k,
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
     pass_ms = {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items() if v[1] > 0}

@@ -104,8 +104,9 @@ typedef struct {
    skip the loads and the work of phases that are zero at a cell, its face
    neighbours and the pass's pointwise inputs; their RHS and stage values are
    exactly zero, so results equal the dense passes' up to the sign of zero.
-   Passes without a masked form (SSP(10)4 with its embedded solution) run
-   dense and mark the vectors they write as fully occupied.  The masks cost
+   Every pass of every integrator has a masked form (SSP(10)4 included: its
+   embedded accumulator and its mid-stage combination keep masks of their
+   own); the pf_rhs pass runs dense.  The masks cost
    4 bytes per word, cell and state vector (pf_footprint counts them); TMA
    staging is not used.  PF_EINVAL for FP64. */
 /* PF_OPT_ONE_CELL (FP32 dense storage) runs the passes through the kernel
@@ -114,7 +115,21 @@ typedef struct {
    x-adjacent cells per thread (float2 loads and stores, stage values written
    through; used where nx is even).  Results agree to FP32 rounding; meant for
    comparison and tuning (pf_autotune picks per problem shape). */
-enum { PF_OPT_TMA = 1, PF_OPT_MASKED = 2, PF_OPT_ONE_CELL = 4 };
+/* PF_OPT_MOBILITY_SIMPLEX replaces the standard projection S after every
+   stage (clamp, >= 1 rule, divide by the sum; Sec. 3.1) by a
+   mobility-weighted one, a reading of the mobility-based simplex Sec. 3.1
+   cites for the particle cases of Sec. 5.3 (the paper does not describe
+   it): on the phases with a positive value at the cell, P, the point of the
+   simplex face spanned by P nearest to the stage value in the metric
+   sum (x_a - y_a)^2 / w_a, with w_a the mean phase-field mobility L_ab of
+   phase a towards the other phases of P; so x_a = max(y_a - tau w_a, 0) with
+   tau fixing the sum to 1, and a phase that moves slowly against its
+   neighbours (an immobile particle) takes little of the correction.  With
+   equal mobilities this is the Euclidean projection.  Runs on the generic
+   passes (both precisions); PF_EINVAL with PF_OPT_MASKED, and pf_step
+   returns PF_EINVAL for PF_STEP_REUSE_RHS and PF_STEP_DEVICE_LOOP; more than
+   64 positive phases in one cell is PF_EINVAL from the call that meets it. */
+enum { PF_OPT_TMA = 1, PF_OPT_MASKED = 2, PF_OPT_ONE_CELL = 4, PF_OPT_MOBILITY_SIMPLEX = 8 };
 
 /* Error tolerances of the weighted norm (Eq. error_norm): relative r and
    absolute a per field (phase field, concentration). */

@@ -181,11 +181,98 @@ int or_rhs(const or_params *p, const double *u, double *r, unsigned char *nzout)
 /* Simplex projection S (Sec. 3.1): clamp negatives to 0; if a component is
    >= 1 it becomes 1 and all others 0 (largest wins, ties to the lowest id);
    finally divide by the sum. */
+/* Mobility-weighted projection of one cell (a reading of the mobility-based
+   simplex that Sec. 3.1 cites for the particle cases of Sec. 5.3 without
+   describing it): the point of the simplex face spanned by the phases with a
+   positive value, P = {a : y_a > 0}, nearest to y in the metric
+   sum_a (x_a - y_a)^2 / w_a, where w_a is the mean phase-field mobility L_ab
+   of phase a towards the other phases of P.  Its optimality conditions give
+   x_a = max(y_a - tau w_a, 0) with tau fixed by sum_a x_a = 1, so a phase
+   that moves slowly against its neighbours (an immobile particle) takes a
+   small share of the correction, and with equal mobilities this is the
+   Euclidean projection.  tau by the active-set iteration (Michelot 1986, with
+   weights): start from P, set tau = (sum y - 1) / sum w over the active
+   phases, drop the phases with y_a - tau w_a <= 0, repeat until none is
+   dropped (tau only grows, so a dropped phase stays at 0).  Sums run over
+   ascending phase ids.  One phase in P becomes 1; if every weight is 0 the
+   standard S is applied instead. */
+int or_project_cell_mobility(int N, const double *L, double *y)
+{
+    int *pid = malloc(sizeof(int) * N), *on = malloc(sizeof(int) * N);
+    double *w = malloc(sizeof(double) * N), *x = malloc(sizeof(double) * N);
+    int np = 0, ret = 0;
+    for (int a = 0; a < N; ++a)
+        if (y[a] > 0.0) pid[np++] = a;
+    if (np == 0) { ret = -1; goto done; }
+    for (int a = 0; a < N; ++a) x[a] = 0.0;
+    if (np == 1) {
+        x[pid[0]] = 1.0;
+    } else {
+        double wsum = 0.0;
+        for (int k = 0; k < np; ++k) {
+            double s = 0.0;
+            for (int j = 0; j < np; ++j)
+                if (j != k) s = s + L[pid[k] * N + pid[j]];
+            w[k] = s / (double)(np - 1);
+            wsum = wsum + w[k];
+            on[k] = 1;
+        }
+        int standard = !(wsum > 0.0);
+        if (!standard) {
+            double tau = 0.0;
+            for (;;) {
+                double sy = 0.0, sw = 0.0;
+                for (int k = 0; k < np; ++k)
+                    if (on[k]) { sy = sy + y[pid[k]]; sw = sw + w[k]; }
+                if (!(sw > 0.0)) { standard = 1; break; }   /* only immobile phases left */
+                tau = (sy - 1.0) / sw;
+                int dropped = 0;
+                for (int k = 0; k < np; ++k)
+                    if (on[k] && y[pid[k]] - tau * w[k] <= 0.0) { on[k] = 0; dropped = 1; }
+                if (!dropped) break;
+            }
+            if (!standard)
+                for (int k = 0; k < np; ++k) x[pid[k]] = on[k] ? y[pid[k]] - tau * w[k] : 0.0;
+        }
+        if (standard) {
+            /* no mobility to share the correction: the standard S (>= 1 rule, divide) */
+            int amax = -1;
+            for (int k = 0; k < np; ++k)
+                if (y[pid[k]] >= 1.0 && (amax < 0 || y[pid[k]] > y[amax])) amax = pid[k];
+            double s = 0.0;
+            for (int k = 0; k < np; ++k) s = s + y[pid[k]];
+            for (int k = 0; k < np; ++k)
+                x[pid[k]] = amax >= 0 ? (pid[k] == amax ? 1.0 : 0.0) : y[pid[k]] / s;
+        }
+    }
+    for (int a = 0; a < N; ++a) {
+        if (x[a] != y[a]) ret = 1;
+        y[a] = x[a];
+    }
+done:
+    free(pid); free(on); free(w); free(x);
+    return ret;
+}
+
 int or_project(const or_params *p, double *u, unsigned char *acted)
 {
     int N = p->N;
     long V = or_ncells(p);
     int bad = 0;
+    if (p->simplex == 1) {
+        double *A = malloc(sizeof(double) * N * N), *B = malloc(sizeof(double) * N * N),
+               *L = malloc(sizeof(double) * N * N), *y = malloc(sizeof(double) * N);
+        or_coeffs(p, A, B, L);
+        for (long i = 0; i < V; ++i) {
+            for (int a = 0; a < N; ++a) y[a] = u[a * V + i];
+            int r = or_project_cell_mobility(N, L, y);
+            if (r < 0) { bad = 1; continue; }
+            for (int a = 0; a < N; ++a) u[a * V + i] = y[a];
+            if (acted) acted[i] = (unsigned char)r;
+        }
+        free(A); free(B); free(L); free(y);
+        return bad ? OR_EUNSTABLE : OR_OK;
+    }
     for (long i = 0; i < V; ++i) {
         int changed = 0;
         for (int a = 0; a < N; ++a)

@@ -13,13 +13,18 @@
  * c[V] (if K=1)], cell index i = (z*ny + y)*nx + x, x fastest.
  *
  * Pinning (see tests/test_oracle_*.py): every function here is pinned against
- * closed forms, invariants or numbers printed in the paper, except
+ * closed forms, invariants or numbers printed in the paper (the
+ * mobility-weighted projection against the optimality conditions of its own
+ * definition and the Euclidean simplex projection it reduces to), except
  *   - or_ssp104_embedded_weights (Sec. 3.3 cites external weights that the
- *     paper does not print; we use the minimum-norm order-3 embedding) and
+ *     paper does not print; we use the minimum-norm order-3 embedding),
  *   - the chemical / diffusion parts of or_dt_e (Sec. 3.2: the Gershgorin
  *     estimates live in the missing supplement; our reading reproduces the
- *     three stable steps printed in Sec. 5.3 but is fitted, not derived):
- *     parity unpinned for those two readings.
+ *     three stable steps printed in Sec. 5.3 but is fitted, not derived) and
+ *   - the mobility-based simplex of Sec. 3.1/5.3 (cited, not described):
+ *     or_project_cell_mobility is one reading of it (a projection in the
+ *     metric the mobilities define), so the paper does not fix its values:
+ *     parity unpinned for those three readings.
  */
 #ifndef PF_ORACLE_H
 #define PF_ORACLE_H
@@ -44,6 +49,7 @@ typedef struct {
     double k[2], c0[2], D[2];   /* per chemical type (Eq. gibbs-energy, Eq. ceq) */
     int bc_phi[6], bc_c[6];     /* faces x-,x+,y-,y+,z-,z+ */
     double cdir[6];             /* Dirichlet concentration per face */
+    int simplex;                /* projection S: 0 the standard one, 1 mobility-weighted */
 } or_params;
 
 typedef struct { double r_phi, a_phi, r_c, a_c; } or_tol;
@@ -68,8 +74,16 @@ void or_coeffs(const or_params *p, double *A, double *B, double *L);
 int or_rhs(const or_params *p, const double *u, double *r, unsigned char *nz);
 /* Simplex projection S (Sec. 3.1); acted[i] (per cell, may be NULL) is set to
    1 where clamping or the >=1 rule changed a value.  Returns OR_EUNSTABLE if a
-   cell sum is not positive. */
+   cell sum is not positive.  With p->simplex = 1 the mobility-weighted
+   projection (or_project_cell_mobility) replaces it. */
 int or_project(const or_params *p, double *u, unsigned char *acted);
+/* Mobility-weighted projection of one cell's N values y (in place), L the
+   N*N phase-field mobilities: on P = {a : y_a > 0}, x_a = max(y_a - tau w_a, 0)
+   with w_a the mean of L_ab over the other phases b of P and tau such that
+   the x_a sum to 1; phases outside P become 0.  Returns 1 if a value changed
+   (*acted), -1 if no value is positive (the cell cannot be projected), 0
+   otherwise. */
+int or_project_cell_mobility(int N, const double *L, double *y);
 /* Stable explicit Euler step from the Gershgorin reading (Sec. 3.2). */
 double or_dt_e(const or_params *p);
 /* Energy functional F = int a + w + f dV (Eq. energy) with forward

@@ -37,7 +37,8 @@ class _Params(C.Structure):
                 ("dx", C.c_double), ("N", C.c_int), ("ptype", _ip), ("gamma", _dp),
                 ("mob", _dp), ("W", C.c_double), ("Lover", _dp), ("K", C.c_int),
                 ("k", C.c_double * 2), ("c0", C.c_double * 2), ("D", C.c_double * 2),
-                ("bc_phi", C.c_int * 6), ("bc_c", C.c_int * 6), ("cdir", C.c_double * 6)]
+                ("bc_phi", C.c_int * 6), ("bc_c", C.c_int * 6), ("cdir", C.c_double * 6),
+                ("simplex", C.c_int)]
 
 
 class _Tol(C.Structure):
@@ -72,6 +73,8 @@ def lib():
         L = C.CDLL(path)
         L.or_rhs.argtypes = [C.POINTER(_Params), _dp, _dp, _ubp]
         L.or_project.argtypes = [C.POINTER(_Params), _dp, _ubp]
+        L.or_project_cell_mobility.argtypes = [C.c_int, _dp, _dp]
+        L.or_project_cell_mobility.restype = C.c_int
         L.or_dt_e.argtypes = [C.POINTER(_Params)]
         L.or_dt_e.restype = C.c_double
         L.or_reduce.argtypes = [C.POINTER(_Params), _dp, _dp, _dp, _ip]
@@ -138,6 +141,7 @@ class Oracle:
             p.k[t], p.c0[t], p.D[t] = prob.k[t], prob.c0[t], prob.D[t]
         for f in range(6):
             p.bc_phi[f], p.bc_c[f], p.cdir[f] = prob.bc_phi[f], prob.bc_c[f], prob.c_dirichlet[f]
+        p.simplex = int(getattr(prob, "simplex", 0))
         self.p = p
         self.sys = _Sys()
         lib().or_sys_pde(C.byref(self.sys), C.byref(self.p))
@@ -283,6 +287,16 @@ def dahlquist_solve(integ, lam, t_end, nsteps, s=1):
         lib().or_step(C.byref(sysd), integ, dt, s, _d(u), _d(un), _d(rn), _d(zz))
         u, un = un, u
     return complex(u[0], u[1])
+
+
+def project_cell_mobility(L, y):
+    """or_project_cell_mobility: the mobility-weighted projection of one
+    cell's values y (length N) with phase-field mobilities L (N x N).
+    Returns (x, code), code 1 if a value changed, -1 if none is positive."""
+    y = np.array(y, dtype=np.float64)
+    L = np.ascontiguousarray(L, dtype=np.float64).reshape(-1)
+    r = lib().or_project_cell_mobility(len(y), _d(L), _d(y))
+    return y, r
 
 
 def sts_stages(integ, dt, dte):

@@ -26,6 +26,10 @@ SIGS = ["SIG_PROJECT", "SIG_P2 | SIG_PROJECT", "SIG_P0 | SIG_P2 | SIG_R0IN | SIG
         "SIG_R0OUT | SIG_PROJECT", "SIG_ERR", "SIG_P0 | SIG_PROJECT"]
 # the dense fast kernel also has the error sweep that keeps F(u^{n+1})
 FAST_SIGS = SIGS + ["SIG_ERR | SIG_R0OUT"]
+# SSP(10)4 passes (one-cell rolled body, dense and masked): fixed-step stage 5,
+# and the stages with the embedded accumulator
+SSP_SIGS = ["SIG_O2 | SIG_PROJECT", "SIG_Z | SIG_PROJECT", "SIG_Z | SIG_O2 | SIG_PROJECT",
+            "SIG_P0 | SIG_Z | SIG_EMB | SIG_PROJECT"]
 # passes of the device-driven adaptive RKL steps: stage 1, RKL2 body, RKL1
 # body, error sweep (descriptor-driven kernels)
 DSIGS = ["SIG_R0OUT | SIG_PROJECT", "SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT", "SIG_P2 | SIG_PROJECT", "SIG_ERR"]
@@ -46,6 +50,17 @@ def unit(T, kcs, fast, fname):
         kc = kcs[0]
         L.append("    const size_t smf = sizeof(ListSmem<float>);")
         L.append("    const size_t smt = 1024 + sizeof(TmaSmem) + sizeof(ListSmem<float>);")
+        # SSP(10)4 passes with 33..128 phases: the rolled body the masked
+        # storage uses (its results are the dense ones bit for bit)
+        L.append("    if (g.N > 32 && g.N <= 128 && g.Vs < 0x7fffffffLL) {")
+        for d in (2, 3):
+            for sg in SSP_SIGS:
+                L.append("        if (g.dim == %d && sig == (%s)) {" % (d, sg))
+                L.append("            fast_kernel<%d, %d, %s, 128><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);" % (d, kc, sg))
+                L.append("            return (int)cudaGetLastError();")
+                L.append("        }")
+                prep.append("    if (cudaFuncSetAttribute(fast_kernel<%d, %d, %s, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;" % (d, kc, sg))
+        L.append("    }")
         L.append("    if (g.N > 32 && g.N <= 250 && g.Vs < 0x7fffffffLL) {")
         for d in (2, 3):
             for sg in SIGS:
@@ -67,7 +82,7 @@ def unit(T, kcs, fast, fname):
         for nmax in (4, 32):
             L.append("        if (%s) {" % ("g.N <= 4" if nmax == 4 else "g.N > 4"))
             for d in (2, 3):
-                for sg in FAST_SIGS:
+                for sg in FAST_SIGS + SSP_SIGS:
                     L.append("            if (g.dim == %d && sig == (%s)) {" % (d, sg))
                     L.append("                fast_kernel<%d, %d, %s, %d><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);" % (d, kc, sg, nmax))
                     L.append("                return (int)cudaGetLastError();")
@@ -152,7 +167,7 @@ def munit(kc, fname):
     for nmax in (4, 32, 128):
         L.append("        if (%s) {" % {4: "g.N <= 4", 32: "g.N > 4 && g.N <= 32", 128: "g.N > 32"}[nmax])
         for d in (2, 3):
-            for sg in SIGS:
+            for sg in SIGS + SSP_SIGS:
                 L.append("            if (g.dim == %d && sig == (%s)) {" % (d, sg))
                 L.append("                fast_kernel<%d, %d, %s, %d, true><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);" % (d, kc, sg, nmax))
                 L.append("                return (int)cudaGetLastError();")

@@ -54,6 +54,12 @@ int launch_stage<float>(const Geom &g, const Pass<float> &P, cudaStream_t st, co
 {
     bool done = false;
     if (nk) *nk = 1;
+    if (g.simplex != SIMPLEX_STANDARD) {
+        // the mobility-weighted projection lives in the generic body only
+        int e = g.K ? launch_f32k1(g, P, SIG_GENERIC, st, A, B, L, ptype, nullptr, &done)
+                    : launch_f32k0(g, P, SIG_GENERIC, st, A, B, L, ptype, nullptr, &done);
+        return done ? e : (int)cudaErrorInvalidValue;
+    }
     if (P.m_in) {
         // masked storage: only the masked instantiations maintain the masks
         const unsigned sig = pass_signature(P);

@@ -517,7 +517,9 @@ bool masked_sig(unsigned s)
 {
     using namespace pfk;
     return s == SIG_PROJECT || s == (SIG_P2 | SIG_PROJECT) || s == (SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT) ||
-           s == (SIG_R0OUT | SIG_PROJECT) || s == SIG_ERR || s == (SIG_P0 | SIG_PROJECT);
+           s == (SIG_R0OUT | SIG_PROJECT) || s == SIG_ERR || s == (SIG_P0 | SIG_PROJECT) ||
+           s == (SIG_O2 | SIG_PROJECT) || s == (SIG_Z | SIG_PROJECT) || s == (SIG_Z | SIG_O2 | SIG_PROJECT) ||
+           s == (SIG_P0 | SIG_Z | SIG_EMB | SIG_PROJECT);
 }
 
 // After a pass that wrote a state vector without maintaining its mask, mark
@@ -567,6 +569,11 @@ int run_pass(pf_handle *h, const Pass<T> &P)
         Q.m_r0 = mask_plane(h, P.r0in);
         Q.m_out = P.mode == pfk::MODE_ERR ? nullptr : mask_plane(h, P.out);
         Q.m_r0out = mask_plane(h, P.r0out);
+        Q.m_zin = mask_plane(h, P.zin);
+        Q.m_zout = mask_plane(h, P.zout);
+        Q.m_out2 = mask_plane(h, P.out2);
+        Q.m_q2in = mask_plane(h, P.q2in);
+        Q.m_uw = mask_plane(h, P.uw);
         int e = pfk::launch_stage<T>(h->g, Q, h->stream, (const T *)h->dA, (const T *)h->dB, (const T *)h->dL,
                                      h->dptype, nullptr);
         h->launches++;
@@ -1489,11 +1496,13 @@ int step_loop(pf_handle *h, int integ, double t_end, const pf_tol *tol, const pf
     if (o->flags & PF_STEP_DEVICE_LOOP) {
         // the descriptor-driven kernels cover FP64 and FP32 dense storage with N <= 32
         if (!(adaptive && sts) || !h->stream || h->prof_on || (o->flags & PF_STEP_REUSE_RHS) || h->masked ||
-            !(sizeof(T) == 8 || h->N <= 32) || h->Vs >= 0x7fffffffLL)
+            !(sizeof(T) == 8 || h->N <= 32) || h->Vs >= 0x7fffffffLL || h->g.simplex != pfk::SIMPLEX_STANDARD)
             return PF_EINVAL;
         h->rhs_valid = false;
         return devloop<T>(h, integ, t_end, tol, o, stats);
     }
+    // the pointwise first stage of the reuse path applies the standard S only
+    if ((o->flags & PF_STEP_REUSE_RHS) && h->g.simplex != pfk::SIMPLEX_STANDARD) return PF_EINVAL;
     const int max_stages = o->max_stages > 0 ? o->max_stages : 1001;
     long long evals = 0, acc_n = 0, rej_n = 0, attempts = 0;
     const long long launches0 = h->launches;
@@ -1658,14 +1667,17 @@ int get_state_t(pf_handle *h, double *phi_dev, double *c_dev)
     return cuda_status(cudaGetLastError());
 }
 
+// RHS of the current state into the staging buffer (rhs true; allocated by
+// the caller) and/or N_z per cell into nz_dev.
 template <typename T>
-int rhs_t(pf_handle *h, unsigned char *nz_dev)
+int rhs_t(pf_handle *h, unsigned char *nz_dev, bool rhs)
 {
+    if (rhs && !h->staging) return PF_EINVAL;
     h->cur_kind = PF_PASS_RHS;
     Pass<T> P = blank_pass<T>(h);
     P.mode = pfk::MODE_RHS;
     P.in = (const T *)h->buf[h->iu];
-    P.rhs_pm = h->staging;
+    P.rhs_pm = rhs ? h->staging : nullptr;
     P.nz_out = nz_dev;
     P.project = 0;
     return run_pass<T>(h, P);
@@ -1891,6 +1903,7 @@ int pf_create(const pf_params *p, void *cuda_stream, pf_handle **out)
     // values are shifted with it, which leaves mu = (c - sum phi c0) / (sum phi / k)
     // and every difference of psi unchanged
     g.cref = (h->prec == 32 && h->K) ? p->c_ref : 0.0;
+    g.simplex = (p->options & PF_OPT_MOBILITY_SIMPLEX) ? pfk::SIMPLEX_MOBILITY : pfk::SIMPLEX_STANDARD;
     for (int f = 0; f < 6; ++f) {
         g.bc_phi[f] = p->bc_phi[f];
         g.bc_c[f] = p->bc_c[f];
@@ -1918,7 +1931,10 @@ int pf_create(const pf_params *p, void *cuda_stream, pf_handle **out)
 
     if (p->options & PF_OPT_MASKED) {
         // masked storage: FP32, one occupancy word per 32 phases and cell
-        if (p->precision != 32 || p->n_phases > 128) { delete h; return PF_EINVAL; }
+        if (p->precision != 32 || p->n_phases > 128 || g.simplex != pfk::SIMPLEX_STANDARD) {
+            delete h;
+            return PF_EINVAL;
+        }
         h->masked = true;
         h->nw = (p->n_phases + 31) / 32;
     }
@@ -2127,7 +2143,8 @@ int pf_get_state(pf_handle *h, double *phi, double *c, unsigned char *nz, double
     }
     if (nz) {
         if (!h->dnz && !dmalloc(h, &h->dnz, h->V)) return PF_ENOMEM;
-        st = (h->prec == 64) ? rhs_t<double>(h, h->dnz) : rhs_t<float>(h, h->dnz);
+        // N_z only: the RHS values are not stored
+        st = (h->prec == 64) ? rhs_t<double>(h, h->dnz, false) : rhs_t<float>(h, h->dnz, false);
         if (st) return st;
         if (cudaMemcpyAsync(nz, h->dnz, h->V, kind, h->stream) != cudaSuccess) return PF_EDEVICE;
     }
@@ -2144,7 +2161,8 @@ int pf_rhs(pf_handle *h, double *rhs_phi, double *rhs_c, unsigned char *nz, int 
     if ((st = ensure_staging(h))) return st;
     if (nz && !h->dnz && !dmalloc(h, &h->dnz, h->V)) return PF_ENOMEM;
     if (cudaMemsetAsync(h->dflag, 0, PF_FLAG_BYTES, h->stream) != cudaSuccess) return PF_EDEVICE;
-    st = (h->prec == 64) ? rhs_t<double>(h, nz ? h->dnz : nullptr) : rhs_t<float>(h, nz ? h->dnz : nullptr);
+    st = (h->prec == 64) ? rhs_t<double>(h, nz ? h->dnz : nullptr, true)
+                         : rhs_t<float>(h, nz ? h->dnz : nullptr, true);
     if (st) return st;
     const cudaMemcpyKind kind = ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     if (cudaMemcpyAsync(rhs_phi, h->staging, sizeof(double) * (size_t)h->N * h->V, kind, h->stream) != cudaSuccess)
@@ -2378,7 +2396,7 @@ bool grow(T **dev, T **host, size_t *cap, size_t want)
 bool packable(const pf_handle *h, int integ)
 {
     return h->prec == 32 && !h->masked && !h->tma && h->g.kvar == pfk::KVAR_TWO_CELL && pfk::vec_eligible(h->g) &&
-           integ != PF_SSP104;
+           integ != PF_SSP104 && h->g.simplex == pfk::SIMPLEX_STANDARD;
 }
 
 }  // namespace

@@ -63,9 +63,14 @@ struct Geom {
                                         // of c, and only the error weights |c| add it back
     int tiles_x, tiles_y;               // block tiling of the x-y plane (one-cell kernels)
     int kvar;                           // FP32 dense passes: KVAR_TWO_CELL or KVAR_ONE_CELL
+    int simplex;                        // projection S: SIMPLEX_STANDARD or SIMPLEX_MOBILITY
 };
 // Kernel variants of the FP32 dense passes (chosen per handle, pf_autotune).
 enum { KVAR_TWO_CELL = 0, KVAR_ONE_CELL = 1 };
+// The projection onto the simplex after every stage (Sec. 3.1): the standard
+// one (clamp, >= 1 rule, divide by the sum) or the mobility-weighted one
+// (mob_project; the generic body only).
+enum { SIMPLEX_STANDARD = 0, SIMPLEX_MOBILITY = 1 };
 
 // What one pass does (passed by value).
 template <typename T>
@@ -104,6 +109,9 @@ struct Pass {
     // is clear holds zero.  Null: dense pass.
     const unsigned *m_in, *m_p0, *m_p2, *m_r0;
     unsigned *m_out, *m_r0out;
+    // the same for the SSP(10)4 vectors: z accumulator in/out, q2 in/out, u^n
+    const unsigned *m_zin, *m_q2in, *m_uw;
+    unsigned *m_zout, *m_out2;
 };
 
 enum { MODE_RHS = 0, MODE_STAGE = 1, MODE_ERR = 2 };
@@ -248,7 +256,11 @@ __device__ __forceinline__ void block_partials(double esum, long long ecnt, doub
 // SIG_GENERIC reads every option from the Pass at run time.
 enum : unsigned {
     SIG_P0 = 1u, SIG_P2 = 2u, SIG_R0IN = 4u, SIG_R0OUT = 8u, SIG_PROJECT = 16u,
-    SIG_ERR = 32u, SIG_RHS = 64u, SIG_GENERIC = 1u << 30
+    SIG_ERR = 32u, SIG_RHS = 64u,
+    // SSP(10)4 (Sec. 3.3): embedded accumulator z <- z + bz F, the q2 combination
+    // after stage 5, and the embedded error of the final stage (implies SIG_Z)
+    SIG_Z = 128u, SIG_O2 = 256u, SIG_EMB = 512u,
+    SIG_GENERIC = 1u << 30
 };
 
 template <typename T>
@@ -292,6 +304,88 @@ struct WideList {
     __device__ __forceinline__ T &dl(int k) { return dl_[k]; }
     __device__ __forceinline__ T &nv(int) { return lap_[0]; }   // never used (NV = 0)
 };
+
+// Mobility-weighted projection of one cell (a reading of the mobility-based
+// simplex Sec. 3.1 cites for the particle cases of Sec. 5.3): on the phases
+// with a positive value, P = {a : y_a > 0}, the point of the simplex face
+// they span nearest to y in the metric sum (x_a - y_a)^2 / w_a, w_a the mean
+// phase-field mobility L_ab of a towards the other phases of P:
+// x_a = max(y_a - tau w_a, 0), sum x_a = 1.  tau by the weighted active-set
+// iteration (drop the phases that reach zero, recompute, until none does);
+// sums in ascending phase order.  No mobility to share the correction: the
+// standard S on P.  The N values sit at v[a * Vs] (raw on entry, projected
+// on return).  Returns 1 if a value changed, 0 if none did, -1 if no value is
+// positive, -2 if more than MOBCAP are.  Out of line: only the generic
+// passes of a handle created with this projection call it.
+constexpr int MOBCAP = 64;
+template <typename T>
+__device__ __noinline__ int mob_project(int N, long long Vs, T *v, const T *__restrict__ tabL)
+{
+    unsigned char pid[MOBCAP];
+    T yv[MOBCAP], w[MOBCAP];
+    int np = 0;
+    bool nonpos = false;     // a nonzero value <= 0 (becomes 0)
+    for (int a = 0; a < N; ++a) {
+        const T y = v[(long long)a * Vs];
+        if (y > (T)0) {
+            if (np >= MOBCAP) return -2;
+            pid[np] = (unsigned char)a;
+            yv[np] = y;
+            np++;
+        } else if (y != (T)0) {
+            nonpos = true;
+        }
+    }
+    if (np == 0) return -1;
+    unsigned long long on = 0ull;
+    T tau = (T)0;
+    bool standard = false;
+    if (np > 1) {
+        T wsum = (T)0;
+        for (int k = 0; k < np; ++k) {
+            const T *La = tabL + pid[k] * N;
+            T s = (T)0;
+            for (int j = 0; j < np; ++j)
+                if (j != k) s = s + La[pid[j]];
+            w[k] = s / (T)(np - 1);
+            wsum = wsum + w[k];
+            on |= 1ull << k;
+        }
+        standard = !(wsum > (T)0);
+        while (!standard) {
+            T sy = (T)0, sw = (T)0;
+            for (int k = 0; k < np; ++k)
+                if ((on >> k) & 1ull) { sy = sy + yv[k]; sw = sw + w[k]; }
+            if (!(sw > (T)0)) { standard = true; break; }
+            tau = (sy - (T)1) / sw;
+            bool dropped = false;
+            for (int k = 0; k < np; ++k)
+                if (((on >> k) & 1ull) && yv[k] - tau * w[k] <= (T)0) { on &= ~(1ull << k); dropped = true; }
+            if (!dropped) break;
+        }
+    }
+    int amax = -1;
+    T s = (T)0;
+    if (standard) {
+        for (int k = 0; k < np; ++k)
+            if (yv[k] >= (T)1 && (amax < 0 || yv[k] > yv[amax])) amax = k;
+        for (int k = 0; k < np; ++k) s = s + yv[k];
+    }
+    bool changed = nonpos;
+    int k = 0;
+    for (int a = 0; a < N; ++a) {
+        T x = (T)0;
+        if (k < np && pid[k] == a) {
+            if (np == 1) x = (T)1;
+            else if (standard) x = amax >= 0 ? (k == amax ? (T)1 : (T)0) : yv[k] / s;
+            else x = ((on >> k) & 1ull) ? yv[k] - tau * w[k] : (T)0;
+            if (x != yv[k]) changed = true;
+            k++;
+        }
+        v[(long long)a * Vs] = x;
+    }
+    return changed ? 1 : 0;
+}
 
 // The generic per-cell body: RHS, stage combination, projection, first-stage
 // fix, SSP(10)4 accumulators and error partials of one cell (x, y, z), with
@@ -449,13 +543,15 @@ __device__ __forceinline__ bool cell_core(const Geom &g, const Pass<T> &P, LST &
     }
 
     if (mode == MODE_RHS) {
-        // ---- RHS only (pf_rhs) ---------------------------------------------
-        for (int a = 0; a < N; ++a) {
-            T r = (T)0;
-            PF_NEXT_RHS(a, r)
-            P.rhs_pm[(long long)a * g.V + i] = (double)r;
+        // ---- RHS only (pf_rhs); without rhs_pm only N_z (pf_get_state) -----
+        if (P.rhs_pm) {
+            for (int a = 0; a < N; ++a) {
+                T r = (T)0;
+                PF_NEXT_RHS(a, r)
+                P.rhs_pm[(long long)a * g.V + i] = (double)r;
+            }
+            if (K) P.rhs_pm[(long long)N * g.V + i] = (double)rc;
         }
-        if (K) P.rhs_pm[(long long)N * g.V + i] = (double)rc;
         if (P.nz_out) P.nz_out[i] = (unsigned char)nz;
     } else if (mode == MODE_ERR) {
         // ---- STS error sweep (Sec. 3.3): in = u^{n+1}, p0 = u^n, r0in = F^n
@@ -497,7 +593,9 @@ __device__ __forceinline__ bool cell_core(const Geom &g, const Pass<T> &P, LST &
     } else {
         // ---- stage combination (Eq. sts / Alg. ssp2 / SSP(10)4) -------------
         const T a0c = (T)P.a0, a2c = (T)P.a2, b1c = (T)P.b1, b0c = (T)P.b0, bzc = (T)P.bz;
-        const bool chunked = N > NV;
+        // the mobility-weighted projection works on the stage values in the output
+        const bool mob = GEN && project && g.simplex == SIMPLEX_MOBILITY;
+        const bool chunked = N > NV || mob;
         bool changed = false;
         T best = (T)-1;
         int bestid = -1;
@@ -518,7 +616,7 @@ __device__ __forceinline__ bool cell_core(const Geom &g, const Pass<T> &P, LST &
                 if (has_r0in) acc = acc + b0c * ldg(P.r0in + o);
                 if (has_r0out) P.r0out[o] = r;      // replaced below where S acts (RKL2)
                 if (has_z) P.zout[o] = P.zin[o] + bzc * r;   // zin may alias zout
-                if (project) {
+                if (project && !mob) {
                     // S step 1: clamp negatives; step 2 candidate: largest >= 1
                     if (acc < (T)0) { acc = (T)0; changed = true; }
                     if (acc >= (T)1 && acc > best) { best = acc; bestid = a; }
@@ -528,7 +626,12 @@ __device__ __forceinline__ bool cell_core(const Geom &g, const Pass<T> &P, LST &
             }
         }
         // S step 2 (the >= 1 rule) and the sum for step 3, ascending order
-        if (project) {
+        if (mob) {
+            const int r = mob_project<T>(N, Vs, P.out + i, tabL);
+            if (r == -1) raise_flag(P.flag, FLAG_SIMPLEX);
+            if (r == -2) raise_flag(P.flag, FLAG_NZ_OVERFLOW);
+            changed = r == 1;
+        } else if (project) {
             if (bestid >= 0) {
                 // the winner becomes 1, the others 0; the sum is then exactly 1
                 if (!chunked) {
@@ -555,7 +658,7 @@ __device__ __forceinline__ bool cell_core(const Geom &g, const Pass<T> &P, LST &
 #pragma unroll 4
             for (int a = 0; a < N; ++a, o += Vs) {
                 T w = chunked ? P.out[o] : S.nv(a);
-                if (project) {
+                if (project && !mob) {
                     if (bestid >= 0) w = (a == bestid) ? (T)1 : (T)0;
                     else if (ssum > (T)0) w = w / ssum;
                 }
@@ -624,14 +727,19 @@ __device__ __forceinline__ void wide_masks(const Geom &g, const Pass<float> &P, 
 {
     const int nwr = (g.N + 31) / 32;
     for (int w = 0; w < nwr; ++w) {
-        unsigned mo = 0u, mr = 0u;
+        unsigned mo = 0u, mr = 0u, mz = 0u, m2 = 0u;
         for (int b = 0; b < 32 && 32 * w + b < g.N; ++b) {
             const long long o = (long long)(32 * w + b) * g.Vs + i;
             if (P.out[o] != 0.0f) mo |= 1u << b;
             if (P.r0out && P.r0out[o] != 0.0f) mr |= 1u << b;
+            if (P.zout && P.zout[o] != 0.0f) mz |= 1u << b;
+            if (P.out2 && P.out2[o] != 0.0f) m2 |= 1u << b;
         }
-        if (P.m_out) P.m_out[(long long)w * g.Vs + i] = mo;
-        if (P.m_r0out) P.m_r0out[(long long)w * g.Vs + i] = mr;
+        const long long ow = (long long)w * g.Vs + i;
+        if (P.m_out) P.m_out[ow] = mo;
+        if (P.m_r0out) P.m_r0out[ow] = mr;
+        if (P.m_zout) P.m_zout[ow] = mz;
+        if (P.m_out2) P.m_out2[ow] = m2;
     }
 }
 __device__ __forceinline__ void wide_masks(const Geom &, const Pass<double> &, long long) {}
@@ -1149,6 +1257,9 @@ __device__ __forceinline__ void masked_cell(const Geom &g, const Pass<float> &P,
     constexpr bool HR0 = (SIG & SIG_R0IN) != 0 || ERR;
     constexpr bool R0OUT = (SIG & SIG_R0OUT) != 0;
     constexpr bool PROJ = (SIG & SIG_PROJECT) != 0;
+    constexpr bool EMB = (SIG & SIG_EMB) != 0;
+    constexpr bool HZ = (SIG & SIG_Z) != 0 || EMB;
+    constexpr bool HO2 = (SIG & SIG_O2) != 0;
     const int N = g.N;
     const int Vs = (int)g.Vs;
     const int i32 = (int)i;
@@ -1156,6 +1267,7 @@ __device__ __forceinline__ void masked_cell(const Geom &g, const Pass<float> &P,
     const T a0c = (T)P.a0, a2c = (T)P.a2, b1c = (T)P.b1, b0c = (T)P.b0;
     const T ib1 = (T)(1.0 / P.b1);   // first-stage fix: F <- (S(u1) - u^n) / (mu~_1 dt)
     const T dt = (T)P.dt, rph = (T)P.r_phi, aph = (T)P.a_phi;
+    const T bzc = (T)P.bz, m25 = (T)P.m25, m15 = (T)P.m15;
 
     // concentration
     T cc = (T)0, num_c = (T)0, den_c = (T)0, num_n[NFACE], den_n[NFACE], mf[NFACE];
@@ -1409,7 +1521,8 @@ __device__ __forceinline__ void masked_cell(const Geom &g, const Pass<float> &P,
     }
     const T inv = (ssum > (T)0) ? (T)1 / ssum : (T)1;
     const bool fix = R0OUT && P.fix_first && changed;
-    int kr = 0;      // list cursor for the RHS of listed phases (R0OUT)
+    int kr = 0;      // list cursor for the RHS of listed phases (R0OUT, z)
+    int nce = 0;     // entries of the SSP(10)4 embedded error
 #pragma unroll
     for (int w = 0; w < NW; ++w) {
         if (w >= nwr) break;
@@ -1417,20 +1530,60 @@ __device__ __forceinline__ void masked_cell(const Geom &g, const Pass<float> &P,
         const long long ow = (long long)w * Vs + i;
         const unsigned mo_old = OCC ? P.m_out[ow] : 0u;
         const unsigned mr_old = (R0OUT && OCC) ? P.m_r0out[ow] : 0u;
-        const unsigned touch = OCC ? (__reduce_or_sync(am, U[w] | mo_old | mr_old) & full) : full;
-        unsigned nmask = 0u, nrmask = 0u;
+        // SSP(10)4: a phase held by z or by q2in gets a z or q2 entry (and,
+        // through the q2 combination, an output entry) where its stage value
+        // is zero
+        const unsigned mzi = (HZ && OCC) ? P.m_zin[ow] : full;
+        const unsigned mz_old = (HZ && OCC) ? P.m_zout[ow] : 0u;
+        const unsigned mq2 = (HO2 && OCC) ? __ldg(P.m_q2in + ow) : full;
+        const unsigned m2_old = (HO2 && OCC) ? P.m_out2[ow] : 0u;
+        const unsigned muw = (EMB && OCC) ? __ldg(P.m_uw + ow) : full;
+        unsigned tu = U[w] | mo_old | mr_old;
+        if (HZ) tu |= mzi | mz_old;
+        if (HO2) tu |= mq2 | m2_old;
+        const unsigned touch = OCC ? (__reduce_or_sync(am, tu) & full) : full;
+        unsigned nmask = 0u, nrmask = 0u, nzmask = 0u, n2mask = 0u;
         for (unsigned m = touch; m; m &= m - 1u) {
             const int bit = __ffs(m) - 1;
             const int a = 32 * w + bit;
             const long long fo = (long long)a * Vs;
             T wv = ((U[w] >> bit) & 1u) ? nv[a] : (T)0;
             if (PROJ) wv = (bestid >= 0) ? ((a == bestid) ? (T)1 : (T)0) : wv * inv;
+            T rl = (T)0;     // RHS of the phase (zero unless listed)
+            if (R0OUT || HZ)
+                if ((actmask[w] >> bit) & 1u) { rl = S.lap[kr][tid]; kr++; }
             if (R0OUT) {
-                T r = (T)0;
-                if ((actmask[w] >> bit) & 1u) { r = S.lap[kr][tid]; kr++; }
+                T r = rl;
                 if (fix) r = (wv - ldg(P.in + fo + i)) * ib1;
                 if (r != (T)0) nrmask |= 1u << bit;
                 if (!OCC || r != (T)0 || ((mr_old >> bit) & 1u)) (P.r0out + fo)[i32] = r;
+            }
+            if (HZ) {
+                // z <- z + bz F (zin may alias zout; a crowded cell leaves z
+                // to the wide path, which reads it again)
+                const T zi = ((mzi >> bit) & 1u) ? P.zin[fo + i] : (T)0;
+                const T zv = zi + bzc * rl;
+                if (zv != (T)0) nzmask |= 1u << bit;
+                if (!over && (!OCC || zv != (T)0 || ((mz_old >> bit) & 1u))) (P.zout + fo)[i32] = zv;
+                if (EMB) {
+                    T e = wv - zv;
+                    if (zv < (T)0 || zv > (T)1) e = (T)0;
+                    if (e != (T)0) {
+                        const T uv = ((muw >> bit) & 1u) ? ldg(P.uw + fo + i) : (T)0;
+                        const T wt = rph * fmaxf(fabsf(uv), fabsf(wv)) + aph;
+                        const T q = e / wt;
+                        esum += (double)(q * q);
+                        nce++;
+                    }
+                }
+            }
+            if (HO2) {
+                // after stage 5: q2 <- q1 + m25 (u^n - q1), q1 <- q1 + m15 (q2 - q1)
+                const T qi = ((mq2 >> bit) & 1u) ? ldg(P.q2in + fo + i) : (T)0;
+                const T q2 = wv + m25 * (qi - wv);
+                if (q2 != (T)0) n2mask |= 1u << bit;
+                if (!OCC || q2 != (T)0 || ((m2_old >> bit) & 1u)) (P.out2 + fo)[i32] = q2;
+                wv = wv + m15 * (q2 - wv);
             }
             if (wv != (T)0) nmask |= 1u << bit;
             if (!OCC || wv != (T)0 || ((mo_old >> bit) & 1u)) (P.out + fo)[i32] = wv;
@@ -1438,8 +1591,11 @@ __device__ __forceinline__ void masked_cell(const Geom &g, const Pass<float> &P,
         if (OCC) {
             P.m_out[ow] = nmask;
             if (R0OUT) P.m_r0out[ow] = nrmask;
+            if (HZ && !over) P.m_zout[ow] = nzmask;
+            if (HO2) P.m_out2[ow] = n2mask;
         }
     }
+    if (EMB) ecnt += (nce > 0 ? nce : 2);
     if (KC) {
         const long long o = (long long)N * Vs + i;
         // the small increments are summed first: c is rounded once per stage
@@ -1450,7 +1606,25 @@ __device__ __forceinline__ void masked_cell(const Geom &g, const Pass<float> &P,
         const T acc = cc + d;
         if (!isfinite(acc) && !over) raise_flag(P.flag, FLAG_NONFINITE);
         if (R0OUT) P.r0out[o] = rc;
-        P.out[o] = acc;
+        T cv = acc;
+        if (HZ) {
+            const T zv = P.zin[o] + bzc * rc;
+            if (!over) P.zout[o] = zv;
+            if (EMB) {
+                const T e = acc - zv;
+                const T au = fabsf(ldg(P.uw + o) + (T)g.cref), av = fabsf(acc + (T)g.cref);
+                const T wt = (T)P.r_c * fmaxf(au, av) + (T)P.a_c;
+                const T q = e / wt;
+                esum += (double)(q * q);
+                ecnt += 1;
+            }
+        }
+        if (HO2) {
+            const T q2 = acc + m25 * (ldg(P.q2in + o) - acc);
+            P.out2[o] = q2;
+            cv = acc + m15 * (q2 - acc);
+        }
+        P.out[o] = cv;
     }
 }
 
@@ -1763,9 +1937,9 @@ __device__ __forceinline__ void fast_body(const Geom &g, const Pass<float> &P, c
         if constexpr (MASK)
             masked_cell<DIM, KC, SIG, true, (NMAX + 31) / 32>(g, P, S, tid, i, off, ghost, tabA, tabB, tabL, ptype,
                                                               esum, ecnt, am, over);
-        else if constexpr (PF_DENSE_ROLLED || (SIG & SIG_ERR) != 0)
-            masked_cell<DIM, KC, SIG, false, 1>(g, P, S, tid, i, off, ghost, tabA, tabB, tabL, ptype, esum, ecnt,
-                                                am, over);
+        else if constexpr (PF_DENSE_ROLLED || (SIG & (SIG_ERR | SIG_Z | SIG_O2 | SIG_EMB)) != 0)
+            masked_cell<DIM, KC, SIG, false, (NMAX + 31) / 32>(g, P, S, tid, i, off, ghost, tabA, tabB, tabL, ptype,
+                                                               esum, ecnt, am, over);
         else
             over = !fast_cell<DIM, KC, SIG, NMAX>(g, P, ld, S, tid, i, off, ghost, tabA, tabB, tabL, ptype, esum,
                                                   ecnt);
@@ -1775,7 +1949,7 @@ __device__ __forceinline__ void fast_body(const Geom &g, const Pass<float> &P, c
             wide_cell<float, DIM, KC>(&g, &P, tabA, tabB, tabL, ptype, x, y, z, &esum, &ecnt);
         }
     }
-    if (SIG & SIG_ERR) block_partials(esum, ecnt, P.part_sum, P.part_cnt, bid, P.part_n);
+    if (SIG & (SIG_ERR | SIG_EMB)) block_partials(esum, ecnt, P.part_sum, P.part_cnt, bid, P.part_n);
     if (P.count_step) count_step_done(P.flag);
 }
 
@@ -1904,13 +2078,18 @@ inline unsigned pass_signature(const Pass<T> &P)
 {
     if (P.mode == MODE_ERR) return P.r0out ? (SIG_ERR | SIG_R0OUT) : SIG_ERR;
     if (P.mode == MODE_RHS) return SIG_RHS;
-    if (P.zout || P.embedded_err || P.out2) return SIG_GENERIC;
     unsigned s = 0;
     if (P.p0) s |= SIG_P0;
     if (P.p2) s |= SIG_P2;
     if (P.r0in) s |= SIG_R0IN;
     if (P.r0out) s |= SIG_R0OUT;
     if (P.project) s |= SIG_PROJECT;
+    if (P.zout) s |= SIG_Z;
+    if (P.out2) s |= SIG_O2;
+    if (P.embedded_err) {
+        if (!P.zout) return SIG_GENERIC;
+        s |= SIG_EMB;
+    }
     return s;
 }
 

@@ -10,6 +10,40 @@ int launch_f32k1(const Geom &g, const Pass<float> &P, unsigned sig, cudaStream_t
     *done = true;
     const size_t smf = sizeof(ListSmem<float>);
     const size_t smt = 1024 + sizeof(TmaSmem) + sizeof(ListSmem<float>);
+    if (g.N > 32 && g.N <= 128 && g.Vs < 0x7fffffffLL) {
+        if (g.dim == 2 && sig == (SIG_O2 | SIG_PROJECT)) {
+            fast_kernel<2, 1, SIG_O2 | SIG_PROJECT, 128><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+            return (int)cudaGetLastError();
+        }
+        if (g.dim == 2 && sig == (SIG_Z | SIG_PROJECT)) {
+            fast_kernel<2, 1, SIG_Z | SIG_PROJECT, 128><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+            return (int)cudaGetLastError();
+        }
+        if (g.dim == 2 && sig == (SIG_Z | SIG_O2 | SIG_PROJECT)) {
+            fast_kernel<2, 1, SIG_Z | SIG_O2 | SIG_PROJECT, 128><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+            return (int)cudaGetLastError();
+        }
+        if (g.dim == 2 && sig == (SIG_P0 | SIG_Z | SIG_EMB | SIG_PROJECT)) {
+            fast_kernel<2, 1, SIG_P0 | SIG_Z | SIG_EMB | SIG_PROJECT, 128><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+            return (int)cudaGetLastError();
+        }
+        if (g.dim == 3 && sig == (SIG_O2 | SIG_PROJECT)) {
+            fast_kernel<3, 1, SIG_O2 | SIG_PROJECT, 128><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+            return (int)cudaGetLastError();
+        }
+        if (g.dim == 3 && sig == (SIG_Z | SIG_PROJECT)) {
+            fast_kernel<3, 1, SIG_Z | SIG_PROJECT, 128><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+            return (int)cudaGetLastError();
+        }
+        if (g.dim == 3 && sig == (SIG_Z | SIG_O2 | SIG_PROJECT)) {
+            fast_kernel<3, 1, SIG_Z | SIG_O2 | SIG_PROJECT, 128><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+            return (int)cudaGetLastError();
+        }
+        if (g.dim == 3 && sig == (SIG_P0 | SIG_Z | SIG_EMB | SIG_PROJECT)) {
+            fast_kernel<3, 1, SIG_P0 | SIG_Z | SIG_EMB | SIG_PROJECT, 128><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+            return (int)cudaGetLastError();
+        }
+    }
     if (g.N > 32 && g.N <= 250 && g.Vs < 0x7fffffffLL) {
         if (g.dim == 2 && sig == (SIG_PROJECT)) {
             big_kernel<2, 1, SIG_PROJECT><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
@@ -116,6 +150,22 @@ int launch_f32k1(const Geom &g, const Pass<float> &P, unsigned sig, cudaStream_t
                 fast_kernel<2, 1, SIG_ERR | SIG_R0OUT, 4><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
                 return (int)cudaGetLastError();
             }
+            if (g.dim == 2 && sig == (SIG_O2 | SIG_PROJECT)) {
+                fast_kernel<2, 1, SIG_O2 | SIG_PROJECT, 4><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 2 && sig == (SIG_Z | SIG_PROJECT)) {
+                fast_kernel<2, 1, SIG_Z | SIG_PROJECT, 4><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 2 && sig == (SIG_Z | SIG_O2 | SIG_PROJECT)) {
+                fast_kernel<2, 1, SIG_Z | SIG_O2 | SIG_PROJECT, 4><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 2 && sig == (SIG_P0 | SIG_Z | SIG_EMB | SIG_PROJECT)) {
+                fast_kernel<2, 1, SIG_P0 | SIG_Z | SIG_EMB | SIG_PROJECT, 4><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
             if (g.dim == 3 && sig == (SIG_PROJECT)) {
                 fast_kernel<3, 1, SIG_PROJECT, 4><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
                 return (int)cudaGetLastError();
@@ -142,6 +192,22 @@ int launch_f32k1(const Geom &g, const Pass<float> &P, unsigned sig, cudaStream_t
             }
             if (g.dim == 3 && sig == (SIG_ERR | SIG_R0OUT)) {
                 fast_kernel<3, 1, SIG_ERR | SIG_R0OUT, 4><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 3 && sig == (SIG_O2 | SIG_PROJECT)) {
+                fast_kernel<3, 1, SIG_O2 | SIG_PROJECT, 4><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 3 && sig == (SIG_Z | SIG_PROJECT)) {
+                fast_kernel<3, 1, SIG_Z | SIG_PROJECT, 4><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 3 && sig == (SIG_Z | SIG_O2 | SIG_PROJECT)) {
+                fast_kernel<3, 1, SIG_Z | SIG_O2 | SIG_PROJECT, 4><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 3 && sig == (SIG_P0 | SIG_Z | SIG_EMB | SIG_PROJECT)) {
+                fast_kernel<3, 1, SIG_P0 | SIG_Z | SIG_EMB | SIG_PROJECT, 4><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
                 return (int)cudaGetLastError();
             }
         }
@@ -174,6 +240,22 @@ int launch_f32k1(const Geom &g, const Pass<float> &P, unsigned sig, cudaStream_t
                 fast_kernel<2, 1, SIG_ERR | SIG_R0OUT, 32><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
                 return (int)cudaGetLastError();
             }
+            if (g.dim == 2 && sig == (SIG_O2 | SIG_PROJECT)) {
+                fast_kernel<2, 1, SIG_O2 | SIG_PROJECT, 32><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 2 && sig == (SIG_Z | SIG_PROJECT)) {
+                fast_kernel<2, 1, SIG_Z | SIG_PROJECT, 32><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 2 && sig == (SIG_Z | SIG_O2 | SIG_PROJECT)) {
+                fast_kernel<2, 1, SIG_Z | SIG_O2 | SIG_PROJECT, 32><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 2 && sig == (SIG_P0 | SIG_Z | SIG_EMB | SIG_PROJECT)) {
+                fast_kernel<2, 1, SIG_P0 | SIG_Z | SIG_EMB | SIG_PROJECT, 32><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
             if (g.dim == 3 && sig == (SIG_PROJECT)) {
                 fast_kernel<3, 1, SIG_PROJECT, 32><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
                 return (int)cudaGetLastError();
@@ -200,6 +282,22 @@ int launch_f32k1(const Geom &g, const Pass<float> &P, unsigned sig, cudaStream_t
             }
             if (g.dim == 3 && sig == (SIG_ERR | SIG_R0OUT)) {
                 fast_kernel<3, 1, SIG_ERR | SIG_R0OUT, 32><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 3 && sig == (SIG_O2 | SIG_PROJECT)) {
+                fast_kernel<3, 1, SIG_O2 | SIG_PROJECT, 32><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 3 && sig == (SIG_Z | SIG_PROJECT)) {
+                fast_kernel<3, 1, SIG_Z | SIG_PROJECT, 32><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 3 && sig == (SIG_Z | SIG_O2 | SIG_PROJECT)) {
+                fast_kernel<3, 1, SIG_Z | SIG_O2 | SIG_PROJECT, 32><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 3 && sig == (SIG_P0 | SIG_Z | SIG_EMB | SIG_PROJECT)) {
+                fast_kernel<3, 1, SIG_P0 | SIG_Z | SIG_EMB | SIG_PROJECT, 32><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
                 return (int)cudaGetLastError();
             }
         }
@@ -301,6 +399,14 @@ int prepare_f32k1()
 {
     const int smf = (int)sizeof(ListSmem<float>);
     const int smt = (int)(1024 + sizeof(TmaSmem) + sizeof(ListSmem<float>));
+    if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_O2 | SIG_PROJECT, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_Z | SIG_PROJECT, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_Z | SIG_O2 | SIG_PROJECT, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_P0 | SIG_Z | SIG_EMB | SIG_PROJECT, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_O2 | SIG_PROJECT, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_Z | SIG_PROJECT, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_Z | SIG_O2 | SIG_PROJECT, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_P0 | SIG_Z | SIG_EMB | SIG_PROJECT, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(big_kernel<2, 1, SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(big_kernel<2, 1, SIG_P2 | SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(big_kernel<2, 1, SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
@@ -326,6 +432,10 @@ int prepare_f32k1()
     if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_ERR, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_P0 | SIG_PROJECT, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_ERR | SIG_R0OUT, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_O2 | SIG_PROJECT, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_Z | SIG_PROJECT, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_Z | SIG_O2 | SIG_PROJECT, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_P0 | SIG_Z | SIG_EMB | SIG_PROJECT, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_PROJECT, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_P2 | SIG_PROJECT, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
@@ -333,6 +443,10 @@ int prepare_f32k1()
     if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_ERR, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_P0 | SIG_PROJECT, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_ERR | SIG_R0OUT, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_O2 | SIG_PROJECT, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_Z | SIG_PROJECT, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_Z | SIG_O2 | SIG_PROJECT, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_P0 | SIG_Z | SIG_EMB | SIG_PROJECT, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_PROJECT, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_P2 | SIG_PROJECT, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
@@ -340,6 +454,10 @@ int prepare_f32k1()
     if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_ERR, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_P0 | SIG_PROJECT, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_ERR | SIG_R0OUT, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_O2 | SIG_PROJECT, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_Z | SIG_PROJECT, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_Z | SIG_O2 | SIG_PROJECT, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_P0 | SIG_Z | SIG_EMB | SIG_PROJECT, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_PROJECT, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_P2 | SIG_PROJECT, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
@@ -347,6 +465,10 @@ int prepare_f32k1()
     if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_ERR, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_P0 | SIG_PROJECT, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_ERR | SIG_R0OUT, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_O2 | SIG_PROJECT, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_Z | SIG_PROJECT, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_Z | SIG_O2 | SIG_PROJECT, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_P0 | SIG_Z | SIG_EMB | SIG_PROJECT, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(cell_kernel<float, 2, 1, SIG_GENERIC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem<float>)) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(cell_kernel<float, 3, 1, SIG_GENERIC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem<float>)) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel_d<2, 1, SIG_R0OUT | SIG_PROJECT, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;

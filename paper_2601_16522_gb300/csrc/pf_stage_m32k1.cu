@@ -35,6 +35,22 @@ int launch_m32k1(const Geom &g, const Pass<float> &P, unsigned sig, cudaStream_t
                 fast_kernel<2, 1, SIG_P0 | SIG_PROJECT, 4, true><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
                 return (int)cudaGetLastError();
             }
+            if (g.dim == 2 && sig == (SIG_O2 | SIG_PROJECT)) {
+                fast_kernel<2, 1, SIG_O2 | SIG_PROJECT, 4, true><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 2 && sig == (SIG_Z | SIG_PROJECT)) {
+                fast_kernel<2, 1, SIG_Z | SIG_PROJECT, 4, true><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 2 && sig == (SIG_Z | SIG_O2 | SIG_PROJECT)) {
+                fast_kernel<2, 1, SIG_Z | SIG_O2 | SIG_PROJECT, 4, true><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 2 && sig == (SIG_P0 | SIG_Z | SIG_EMB | SIG_PROJECT)) {
+                fast_kernel<2, 1, SIG_P0 | SIG_Z | SIG_EMB | SIG_PROJECT, 4, true><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
             if (g.dim == 3 && sig == (SIG_PROJECT)) {
                 fast_kernel<3, 1, SIG_PROJECT, 4, true><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
                 return (int)cudaGetLastError();
@@ -57,6 +73,22 @@ int launch_m32k1(const Geom &g, const Pass<float> &P, unsigned sig, cudaStream_t
             }
             if (g.dim == 3 && sig == (SIG_P0 | SIG_PROJECT)) {
                 fast_kernel<3, 1, SIG_P0 | SIG_PROJECT, 4, true><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 3 && sig == (SIG_O2 | SIG_PROJECT)) {
+                fast_kernel<3, 1, SIG_O2 | SIG_PROJECT, 4, true><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 3 && sig == (SIG_Z | SIG_PROJECT)) {
+                fast_kernel<3, 1, SIG_Z | SIG_PROJECT, 4, true><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 3 && sig == (SIG_Z | SIG_O2 | SIG_PROJECT)) {
+                fast_kernel<3, 1, SIG_Z | SIG_O2 | SIG_PROJECT, 4, true><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 3 && sig == (SIG_P0 | SIG_Z | SIG_EMB | SIG_PROJECT)) {
+                fast_kernel<3, 1, SIG_P0 | SIG_Z | SIG_EMB | SIG_PROJECT, 4, true><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
                 return (int)cudaGetLastError();
             }
         }
@@ -85,6 +117,22 @@ int launch_m32k1(const Geom &g, const Pass<float> &P, unsigned sig, cudaStream_t
                 fast_kernel<2, 1, SIG_P0 | SIG_PROJECT, 32, true><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
                 return (int)cudaGetLastError();
             }
+            if (g.dim == 2 && sig == (SIG_O2 | SIG_PROJECT)) {
+                fast_kernel<2, 1, SIG_O2 | SIG_PROJECT, 32, true><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 2 && sig == (SIG_Z | SIG_PROJECT)) {
+                fast_kernel<2, 1, SIG_Z | SIG_PROJECT, 32, true><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 2 && sig == (SIG_Z | SIG_O2 | SIG_PROJECT)) {
+                fast_kernel<2, 1, SIG_Z | SIG_O2 | SIG_PROJECT, 32, true><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 2 && sig == (SIG_P0 | SIG_Z | SIG_EMB | SIG_PROJECT)) {
+                fast_kernel<2, 1, SIG_P0 | SIG_Z | SIG_EMB | SIG_PROJECT, 32, true><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
             if (g.dim == 3 && sig == (SIG_PROJECT)) {
                 fast_kernel<3, 1, SIG_PROJECT, 32, true><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
                 return (int)cudaGetLastError();
@@ -107,6 +155,22 @@ int launch_m32k1(const Geom &g, const Pass<float> &P, unsigned sig, cudaStream_t
             }
             if (g.dim == 3 && sig == (SIG_P0 | SIG_PROJECT)) {
                 fast_kernel<3, 1, SIG_P0 | SIG_PROJECT, 32, true><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 3 && sig == (SIG_O2 | SIG_PROJECT)) {
+                fast_kernel<3, 1, SIG_O2 | SIG_PROJECT, 32, true><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 3 && sig == (SIG_Z | SIG_PROJECT)) {
+                fast_kernel<3, 1, SIG_Z | SIG_PROJECT, 32, true><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 3 && sig == (SIG_Z | SIG_O2 | SIG_PROJECT)) {
+                fast_kernel<3, 1, SIG_Z | SIG_O2 | SIG_PROJECT, 32, true><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 3 && sig == (SIG_P0 | SIG_Z | SIG_EMB | SIG_PROJECT)) {
+                fast_kernel<3, 1, SIG_P0 | SIG_Z | SIG_EMB | SIG_PROJECT, 32, true><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
                 return (int)cudaGetLastError();
             }
         }
@@ -135,6 +199,22 @@ int launch_m32k1(const Geom &g, const Pass<float> &P, unsigned sig, cudaStream_t
                 fast_kernel<2, 1, SIG_P0 | SIG_PROJECT, 128, true><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
                 return (int)cudaGetLastError();
             }
+            if (g.dim == 2 && sig == (SIG_O2 | SIG_PROJECT)) {
+                fast_kernel<2, 1, SIG_O2 | SIG_PROJECT, 128, true><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 2 && sig == (SIG_Z | SIG_PROJECT)) {
+                fast_kernel<2, 1, SIG_Z | SIG_PROJECT, 128, true><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 2 && sig == (SIG_Z | SIG_O2 | SIG_PROJECT)) {
+                fast_kernel<2, 1, SIG_Z | SIG_O2 | SIG_PROJECT, 128, true><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 2 && sig == (SIG_P0 | SIG_Z | SIG_EMB | SIG_PROJECT)) {
+                fast_kernel<2, 1, SIG_P0 | SIG_Z | SIG_EMB | SIG_PROJECT, 128, true><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
             if (g.dim == 3 && sig == (SIG_PROJECT)) {
                 fast_kernel<3, 1, SIG_PROJECT, 128, true><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
                 return (int)cudaGetLastError();
@@ -159,6 +239,22 @@ int launch_m32k1(const Geom &g, const Pass<float> &P, unsigned sig, cudaStream_t
                 fast_kernel<3, 1, SIG_P0 | SIG_PROJECT, 128, true><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
                 return (int)cudaGetLastError();
             }
+            if (g.dim == 3 && sig == (SIG_O2 | SIG_PROJECT)) {
+                fast_kernel<3, 1, SIG_O2 | SIG_PROJECT, 128, true><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 3 && sig == (SIG_Z | SIG_PROJECT)) {
+                fast_kernel<3, 1, SIG_Z | SIG_PROJECT, 128, true><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 3 && sig == (SIG_Z | SIG_O2 | SIG_PROJECT)) {
+                fast_kernel<3, 1, SIG_Z | SIG_O2 | SIG_PROJECT, 128, true><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
+            if (g.dim == 3 && sig == (SIG_P0 | SIG_Z | SIG_EMB | SIG_PROJECT)) {
+                fast_kernel<3, 1, SIG_P0 | SIG_Z | SIG_EMB | SIG_PROJECT, 128, true><<<grid, BLOCK, smf, st>>>(g, P, A, B, L, ptype);
+                return (int)cudaGetLastError();
+            }
         }
     }
     *done = false;
@@ -174,36 +270,60 @@ int prepare_m32k1()
     if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_R0OUT | SIG_PROJECT, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_ERR, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_P0 | SIG_PROJECT, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_O2 | SIG_PROJECT, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_Z | SIG_PROJECT, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_Z | SIG_O2 | SIG_PROJECT, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_P0 | SIG_Z | SIG_EMB | SIG_PROJECT, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_PROJECT, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_P2 | SIG_PROJECT, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_R0OUT | SIG_PROJECT, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_ERR, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_P0 | SIG_PROJECT, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_O2 | SIG_PROJECT, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_Z | SIG_PROJECT, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_Z | SIG_O2 | SIG_PROJECT, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_P0 | SIG_Z | SIG_EMB | SIG_PROJECT, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_PROJECT, 32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_P2 | SIG_PROJECT, 32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT, 32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_R0OUT | SIG_PROJECT, 32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_ERR, 32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_P0 | SIG_PROJECT, 32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_O2 | SIG_PROJECT, 32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_Z | SIG_PROJECT, 32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_Z | SIG_O2 | SIG_PROJECT, 32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_P0 | SIG_Z | SIG_EMB | SIG_PROJECT, 32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_PROJECT, 32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_P2 | SIG_PROJECT, 32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT, 32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_R0OUT | SIG_PROJECT, 32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_ERR, 32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_P0 | SIG_PROJECT, 32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_O2 | SIG_PROJECT, 32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_Z | SIG_PROJECT, 32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_Z | SIG_O2 | SIG_PROJECT, 32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_P0 | SIG_Z | SIG_EMB | SIG_PROJECT, 32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_PROJECT, 128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_P2 | SIG_PROJECT, 128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT, 128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_R0OUT | SIG_PROJECT, 128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_ERR, 128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_P0 | SIG_PROJECT, 128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_O2 | SIG_PROJECT, 128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_Z | SIG_PROJECT, 128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_Z | SIG_O2 | SIG_PROJECT, 128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<2, 1, SIG_P0 | SIG_Z | SIG_EMB | SIG_PROJECT, 128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_PROJECT, 128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_P2 | SIG_PROJECT, 128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_P0 | SIG_P2 | SIG_R0IN | SIG_PROJECT, 128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_R0OUT | SIG_PROJECT, 128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_ERR, 128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_P0 | SIG_PROJECT, 128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_O2 | SIG_PROJECT, 128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_Z | SIG_PROJECT, 128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_Z | SIG_O2 | SIG_PROJECT, 128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(fast_kernel<3, 1, SIG_P0 | SIG_Z | SIG_EMB | SIG_PROJECT, 128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf) != cudaSuccess) return -1;
     return 1;
 }
 

@@ -46,6 +46,7 @@ class Problem:
     bc_c: tuple = (0, 0, 0, 0, 0, 0)
     c_dirichlet: tuple = (0.0,) * 6
     c_ref: float = 0.0              # FP32 storage keeps c - c_ref (the majority phase's c)
+    simplex: int = 0                # projection S: 0 standard (Sec. 3.1), 1 mobility-weighted
     name: str = ""
 
     @property

@@ -159,6 +159,8 @@ def make_params(prob, precision=64, options=0):
     for f in range(6):
         p.bc_phi[f], p.bc_c[f], p.c_dirichlet[f] = prob.bc_phi[f], prob.bc_c[f], prob.c_dirichlet[f]
     p.precision = precision
+    if getattr(prob, "simplex", 0) == 1:
+        options |= Simulation.OPT_MOBILITY_SIMPLEX
     p.options = options
     p.c_ref = float(getattr(prob, "c_ref", 0.0) or 0.0)
     return p, keep
@@ -185,6 +187,7 @@ class Simulation:
     OPT_TMA = 1
     OPT_MASKED = 2
     OPT_ONE_CELL = 4
+    OPT_MOBILITY_SIMPLEX = 8
     KVAR_TWO_CELL, KVAR_ONE_CELL, KVAR_TMA = 0, 1, 2
 
     def __init__(self, prob, precision=64, stream=None, options=0):

@@ -90,6 +90,36 @@ def test_masked_grains_rkl2_vs_oracle(pf):
     assert np.abs(out - un).max() <= 2e-5 * scale
 
 
+def test_masked_grains_ssp104_vs_oracle(pf):
+    # 48^3, 32 grains, K = 1: one adaptive SSP(10)4 attempt in masked storage
+    # (the z accumulator, the q2 combination and the embedded error in the
+    # masked passes) equals the dense one-cell passes, and the FP64 oracle's
+    # step and embedded error norm from the same FP32-rounded state
+    prob, u = I.sintering_device(n=48, n_grains=24, seed=3, device="cuda")
+    u = u.cpu().numpy()
+    tol = (1e-4, 1e-3, 1e-4, 1e-3)
+    res = []
+    for opts in (pf.Simulation.OPT_MASKED, ONE):
+        with pf.Simulation(prob, precision=32, options=opts) as sim:
+            sim.set_state(u)
+            u32, _ = sim.get_state()
+            dt0 = 3.0 * sim.dt_e()
+            st = sim.step(pf.SSP104, 1e30, tol=tol, dt0=dt0, max_attempts=1, trace_cap=2)
+            out, _ = sim.get_state()
+        res.append((st, out, u32))
+    (st_m, out_m, u32), (st_d, out_d, _) = res
+    assert np.array_equal(out_m, out_d)
+    assert st_m["trace"]["err"][0] == st_d["trace"]["err"][0]
+    o = ref.Oracle(prob)
+    un, err, nd = o.step_error(ref.SSP104, st_m["trace"]["dt"][0], 10, u32, tol)
+    N = prob.n_phases
+    scale = np.abs(un[:N]).max()
+    assert np.abs(out_m[:N] - un[:N]).max() <= 2e-5 * scale
+    # e = u - z of FP32 values after ten stages: a few 1e-7 absolute per entry
+    # against weights of about a_phi = 1e-3
+    assert abs(st_m["trace"]["err"][0] - err) <= 2e-2 * err + 1e-3
+
+
 def test_masked_graph_replay_equals_launches(pf):
     name, prob, u = ELIGIBLE[3]
     outs = []

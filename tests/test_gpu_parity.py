@@ -450,3 +450,28 @@ def test_state_transfer_paths_agree(pf, prec):
             outs += [a, b.numpy(), c.cpu().numpy()]
     for o in outs:
         np.testing.assert_array_equal(o, ref_u)
+
+
+@pytest.mark.parametrize("case", [3, 5], ids=["blobs3d_K1", "blobs3d_N33"])
+@pytest.mark.parametrize("prec,opts", [(64, 0), (32, 0), (32, 2)], ids=["fp64", "fp32", "fp32-masked"])
+def test_nz_into_device_memory(pf, prec, opts, case):
+    # N_z written straight into device memory by a handle that never staged a
+    # host transfer (device state in, device state out): only N_z is computed
+    torch = pytest.importorskip("torch")
+    name, prob, u = CASES[case]
+    o = ref.Oracle(prob)
+    ur = np.ascontiguousarray(u, np.float64)
+    ud = torch.from_numpy(ur).cuda()
+    with pf.Simulation(prob, precision=prec, options=opts) as sim:
+        sim.set_state(ud)
+        out = torch.empty_like(ud)
+        _, t, nz = sim.get_state(out=out, with_nz=True)
+        torch.cuda.synchronize()
+        nz = nz.cpu().numpy()
+        back = out.cpu().numpy()
+    if prec == 64:
+        np.testing.assert_array_equal(back, ur)
+        _, nz_ref = o.rhs(ur)
+    else:
+        _, nz_ref = o.rhs(back)
+    np.testing.assert_array_equal(nz, nz_ref)

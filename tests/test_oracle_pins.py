@@ -710,3 +710,124 @@ def test_openmp_build_gives_the_same_rhs():
             os.environ["OMP_NUM_THREADS"] = old
     np.testing.assert_array_equal(r1, r2)
     np.testing.assert_array_equal(nz1, nz2)
+
+
+# ---- mobility-weighted projection (reading of the Sec. 3.1 mobility-based simplex)
+
+def _euclid_simplex(y):
+    """Euclidean projection onto the probability simplex by sorting (Held,
+    Wolfe and Crowder 1974): the textbook routine the weighted projection
+    reduces to when every mobility is the same."""
+    u = np.sort(y)[::-1]
+    css = np.cumsum(u)
+    k = np.nonzero(u * np.arange(1, len(y) + 1) > css - 1.0)[0][-1]
+    theta = (css[k] - 1.0) / (k + 1)
+    return np.maximum(y - theta, 0.0)
+
+
+def _sym_mobility(rng, N, lo=0.5, hi=2.0):
+    L = rng.uniform(lo, hi, (N, N))
+    L = 0.5 * (L + L.T)
+    np.fill_diagonal(L, 0.0)
+    return L
+
+
+def test_mobility_projection_equal_mobilities_is_the_euclidean_projection():
+    rng = np.random.default_rng(11)
+    for N in (2, 3, 5, 8):
+        L = np.full((N, N), 0.7)
+        np.fill_diagonal(L, 0.0)
+        for _ in range(40):
+            y = rng.uniform(0.0, 1.0, N) * rng.uniform(0.5, 1.6)
+            x, code = ref.project_cell_mobility(L, y)
+            np.testing.assert_allclose(x, _euclid_simplex(y), atol=1e-14)
+
+
+def test_mobility_projection_satisfies_its_optimality_conditions():
+    # x minimises sum (x_a - y_a)^2 / w_a on the face of P = {y > 0}: KKT
+    # with one multiplier tau: x_a = y_a - tau w_a where x_a > 0, y_a <= tau w_a
+    # where x_a = 0 (w_a the mean L_ab over the other phases of P)
+    rng = np.random.default_rng(12)
+    for N in (3, 4, 6):
+        for _ in range(60):
+            L = _sym_mobility(rng, N, 1e-3, 1.0)
+            y = rng.uniform(-0.2, 1.0, N)
+            y[rng.integers(N)] = rng.uniform(0.05, 1.0)
+            x, code = ref.project_cell_mobility(L, y)
+            P = np.nonzero(y > 0)[0]
+            assert np.all(x >= 0.0) and abs(x.sum() - 1.0) < 1e-14
+            assert np.all(x[y <= 0] == 0.0)
+            if len(P) == 1:
+                assert x[P[0]] == 1.0
+                continue
+            w = np.array([L[a, P[P != a]].mean() for a in P])
+            pos = x[P] > 0
+            taus = (y[P][pos] - x[P][pos]) / w[pos]
+            tau = taus.mean()
+            assert np.abs(taus - tau).max() <= 1e-12 * max(1.0, abs(tau))
+            assert np.all(y[P][~pos] <= tau * w[~pos] + 1e-13)
+
+
+def test_mobility_projection_brute_force_on_three_phases():
+    # the weighted distance of the result is the smallest over a fine grid of
+    # the simplex (three phases, all positive)
+    rng = np.random.default_rng(13)
+    g = np.linspace(0.0, 1.0, 401)
+    A, B = np.meshgrid(g, g, indexing="ij")
+    keep = A + B <= 1.0
+    X = np.stack([A[keep], B[keep], 1.0 - A[keep] - B[keep]], axis=1)
+    for _ in range(10):
+        L = _sym_mobility(rng, 3, 0.05, 1.0)
+        y = rng.uniform(0.05, 0.9, 3)
+        x, _ = ref.project_cell_mobility(L, y)
+        w = np.array([L[a, [b for b in range(3) if b != a]].mean() for a in range(3)])
+        f = lambda z: (((z - y) ** 2) / w).sum(axis=-1)
+        assert f(x) <= f(X).min() + 1e-12
+
+
+def test_mobility_projection_special_cases():
+    L = np.ones((4, 4))
+    np.fill_diagonal(L, 0.0)
+    # a point of the simplex stays where it is
+    y = np.array([0.1, 0.2, 0.3, 0.4])
+    x, code = ref.project_cell_mobility(L, y)
+    np.testing.assert_array_equal(x, y)
+    assert code == 0
+    # no positive value: the cell cannot be projected
+    x, code = ref.project_cell_mobility(L, [-0.1, 0.0, -0.2, 0.0])
+    assert code == -1
+    # one positive value becomes 1
+    x, code = ref.project_cell_mobility(L, [-0.1, 0.3, 0.0, 0.0])
+    np.testing.assert_array_equal(x, [0.0, 1.0, 0.0, 0.0])
+    # an immobile phase (mobility 1e-6 of the others' towards everything)
+    # keeps its value to O(1e-6) while the mobile ones absorb the excess
+    Li = L.copy()
+    Li[3, :] = Li[:, 3] = 1e-6
+    Li[3, 3] = 0.0
+    y = np.array([0.5, 0.2, 0.0, 0.45])
+    x, code = ref.project_cell_mobility(Li, y)
+    assert abs(x[3] - 0.45) < 1e-6 and abs(x.sum() - 1.0) < 1e-15
+    np.testing.assert_allclose(x[:2], [0.5 - 0.075, 0.2 - 0.075], atol=1e-6)
+    # every mobility zero: the standard S
+    Z = np.zeros((3, 3))
+    x, code = ref.project_cell_mobility(Z, [0.5, 0.3, 0.4])
+    np.testing.assert_allclose(x, np.array([0.5, 0.3, 0.4]) / 1.2, rtol=1e-15)
+
+
+def test_step_with_mobility_simplex_keeps_simplex_and_mass():
+    prob, u = I.multiphase_blobs(14, 12, 1, 5, seed=3, has_conc=1, n_alpha=2)
+    prob = prob.with_(simplex=1)
+    o = ref.Oracle(prob)
+    dte = o.dt_e()
+    N, V = prob.n_phases, prob.V
+    for integ, s in ((ref.FEULER, 1), (ref.RKL2, 9), (ref.SSP104, 10)):
+        un, _, _, _ = o.step(integ, 0.9 * dte if integ == ref.FEULER else 20 * dte if integ == ref.RKL2 else 4 * dte,
+                             s, u)
+        ph = un[:N]
+        assert ph.min() >= 0.0
+        np.testing.assert_allclose(ph.sum(axis=0), 1.0, atol=1e-13)
+        assert abs(un[N].sum() - u[N].sum()) <= 1e-12 * abs(u[N]).sum()
+    # the standard and the weighted projection differ on this state
+    a, _, _, _ = o.step(ref.RKL2, 20 * dte, 9, u)
+    b, _, _, _ = ref.Oracle(prob.with_(simplex=0)).step(ref.RKL2, 20 * dte, 9, u)
+    assert np.abs(a - b).max() > 1e-6
