@@ -55,8 +55,10 @@ def workload_problem(name, device):
 # algorithmic vectors moved per pass kind (reads + writes of whole state vectors)
 PASS_VECTORS = {"rkl2": 5, "rkl1": 3, "sts_first": 3, "sts_err": 3, "euler": 2, "ssp": 2, "rhs": 1}
 # DRAM bytes (read + write) per cell of one RKL2 stage pass (two-cell kernel,
-# 32-phase FP32 state) from ncu captures of that launch on each workload
-RKL2_TRAFFIC_PER_CELL = {}
+# 32-phase FP32 state) from an ncu capture of that launch at full size
+# (256^3: 8.813 GB read + 2.149 GB written in the second RKL2 pass of a step;
+# the algorithmic 640 B/cell is 10.74 GB)
+RKL2_TRAFFIC_PER_CELL = {"grains256": (8813314816 + 2148658688) / 16777216}
 
 
 class ClockSampler:
@@ -726,7 +728,7 @@ def run_ours(args, world, rank, local):
     sim.set_state(u)
     torch.cuda.synchronize()
     tuned = None
-    if not args.tma:
+    if not args.tma and not args.no_autotune:
         choice, ms = sim.autotune()
         names = ["two_cell", "one_cell", "tma"]
         tuned = {"choice": names[choice]}
@@ -921,6 +923,9 @@ def main():
     ap.add_argument("--no-stefan-sweep", action="store_true")
     ap.add_argument("--no-sinter", action="store_true")
     ap.add_argument("--no-zener", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default kernel variant (two cells per thread) instead of timing the variants "
+                         "first (a profiler distorts those timings)")
     ap.add_argument("--no-masked", action="store_true", help="skip the masked-storage run")
     ap.add_argument("--no-reuse", action="store_true", help="skip the run that reuses F(u^{n+1})")
     ap.add_argument("--precision-check", action="store_true",

@@ -387,6 +387,40 @@ __device__ __noinline__ int mob_project(int N, long long Vs, T *v, const T *__re
     return changed ? 1 : 0;
 }
 
+// Whether a value is +0 (its encoding is all zero bits): integer tests that
+// let the generic body skip arithmetic whose result is exactly known.
+__device__ __forceinline__ bool zbits(double x) { return __double_as_longlong(x) == 0; }
+__device__ __forceinline__ bool zbits(float x) { return __float_as_int(x) == 0; }
+__device__ __forceinline__ bool same_bits(double a, double b) { return __double_as_longlong(a) == __double_as_longlong(b); }
+__device__ __forceinline__ bool same_bits(float a, float b) { return __float_as_int(a) == __float_as_int(b); }
+
+// The activity filter of Eq. phieq on a phase's stencil values: max > 0 and
+// min < 1.  In FP64 it runs on the encodings (for finite values x > 0 and
+// x < 1 are signed integer comparisons of the bits), off the FP64 pipe.
+template <int NFACE>
+__device__ __forceinline__ bool nontrivial(double v0, const double *nb)
+{
+    long long bx = __double_as_longlong(v0), bn = bx;
+#pragma unroll
+    for (int f = 0; f < NFACE; ++f) {
+        const long long b = __double_as_longlong(nb[f]);
+        bx = b > bx ? b : bx;
+        bn = b < bn ? b : bn;
+    }
+    return bx > 0 && bn < 0x3ff0000000000000LL;
+}
+template <int NFACE>
+__device__ __forceinline__ bool nontrivial(float v0, const float *nb)
+{
+    float mx = v0, mn = v0;
+#pragma unroll
+    for (int f = 0; f < NFACE; ++f) {
+        mx = nb[f] > mx ? nb[f] : mx;
+        mn = nb[f] < mn ? nb[f] : mn;
+    }
+    return mx > 0.0f && mn < 1.0f;
+}
+
 // The generic per-cell body: RHS, stage combination, projection, first-stage
 // fix, SSP(10)4 accumulators and error partials of one cell (x, y, z), with
 // every option read from P at run time (SIG_GENERIC) or fixed by SIG.
@@ -453,12 +487,7 @@ __device__ __forceinline__ bool cell_core(const Geom &g, const Pass<T> &P, LST &
             T nb[NFACE];
 #pragma unroll
             for (int f = 0; f < NFACE; ++f) nb[f] = ldg(fp + off[f]);
-            T mx = v0, mn = v0;
-#pragma unroll
-            for (int f = 0; f < NFACE; ++f) {
-                mx = nb[f] > mx ? nb[f] : mx;
-                mn = nb[f] < mn ? nb[f] : mn;
-            }
+            const bool act = nontrivial<NFACE>(v0, nb);
             if (K) {
                 const int t = ptype[a];
                 const T c0t = (T)g.c0[t], ikt = (T)g.invk[t], dkt = (T)g.Dk[t];
@@ -471,7 +500,7 @@ __device__ __forceinline__ bool cell_core(const Geom &g, const Pass<T> &P, LST &
                     mf[f] = mf[f] + dkt * ((T)0.5 * (v0 + nb[f]));
                 }
             }
-            if (mx > (T)0 && mn < (T)1) {
+            if (act) {
                 T l = (T)0;
 #pragma unroll
                 for (int f = 0; f < NFACE; ++f) l = l + (nb[f] - v0);
@@ -565,6 +594,8 @@ __device__ __forceinline__ bool cell_core(const Geom &g, const Pass<T> &P, LST &
             PF_NEXT_RHS(a, r1)
             if (P.r0out) P.r0out[o] = r1;      // F(u^{n+1}) kept for reuse
             const T un = ldg(P.p0 + o), un1 = ldg(P.in + o), rn = ldg(P.r0in + o);
+            // no change and no RHS: e is exactly zero (skipped like any zero e)
+            if (same_bits(un, un1) && zbits(rn) && zbits(r1)) continue;
             const T sr = rn + r1;
             T e = ((T)12 * (un - un1) + ((T)6 * dt) * sr) / (T)15;
             const T trial = un + (dt / (T)2) * sr;
@@ -609,23 +640,30 @@ __device__ __forceinline__ bool cell_core(const Geom &g, const Pass<T> &P, LST &
                 T r = (T)0;
                 PF_NEXT_RHS(a, r)
                 const T v = ldg(P.in + o);
+                const T p0v = has_p0 ? ldg(P.p0 + o) : (T)0, p2v = has_p2 ? ldg(P.p2 + o) : (T)0;
+                const T r0v = has_r0in ? ldg(P.r0in + o) : (T)0;
                 T acc = v;
-                if (has_p0) acc = acc + a0c * (ldg(P.p0 + o) - v);
-                if (has_p2) acc = acc + a2c * (ldg(P.p2 + o) - v);
-                acc = acc + b1c * r;
-                if (has_r0in) acc = acc + b0c * ldg(P.r0in + o);
+                // every input +0: the combination is exactly 0 (no arithmetic)
+                if (!(zbits(v) && zbits(p0v) && zbits(p2v) && zbits(r0v) && zbits(r))) {
+                    if (has_p0) acc = acc + a0c * (p0v - v);
+                    if (has_p2) acc = acc + a2c * (p2v - v);
+                    acc = acc + b1c * r;
+                    if (has_r0in) acc = acc + b0c * r0v;
+                }
                 if (has_r0out) P.r0out[o] = r;      // replaced below where S acts (RKL2)
                 if (has_z) P.zout[o] = P.zin[o] + bzc * r;   // zin may alias zout
-                if (project && !mob) {
-                    // S step 1: clamp negatives; step 2 candidate: largest >= 1
+                if (project && !mob && !zbits(acc)) {
+                    // S step 1: clamp negatives; step 2 candidate: largest >= 1;
+                    // the sum for step 3 in ascending order (+0 entries add nothing)
                     if (acc < (T)0) { acc = (T)0; changed = true; }
                     if (acc >= (T)1 && acc > best) { best = acc; bestid = a; }
+                    ssum = ssum + acc;
                 }
                 if (chunked) P.out[o] = acc;
                 else S.nv(aa) = acc;
             }
         }
-        // S step 2 (the >= 1 rule) and the sum for step 3, ascending order
+        // S step 2 (the >= 1 rule); the sum for step 3 is formed above
         if (mob) {
             const int r = mob_project<T>(N, Vs, P.out + i, tabL);
             if (r == -1) raise_flag(P.flag, FLAG_SIMPLEX);
@@ -643,24 +681,24 @@ __device__ __forceinline__ bool cell_core(const Geom &g, const Pass<T> &P, LST &
                     changed = true;
                 }
                 ssum = (T)1;
-            } else if (!chunked) {
-                for (int aa = 0; aa < N; ++aa) ssum = ssum + S.nv(aa);
-            } else {
-                for (int a = 0; a < N; ++a) ssum = ssum + P.out[(long long)a * Vs + i];
             }
             if (!(ssum > (T)0)) raise_flag(P.flag, FLAG_SIMPLEX);
         }
         const bool fix = has_r0out && P.fix_first && changed;
+        // a cell whose values are final as written (sum exactly 1, no >= 1 rule,
+        // nothing else to store) is not swept again: the bulk of every grain
+        const bool final_vals = chunked && !mob && bestid < 0 && (!project || ssum == (T)1) && !fix && !emb &&
+                                !has_out2;
         // store pass: S step 3, first-stage fix, embedded error, SSP(10)4 mid combination
         int nc = 0;
-        {
+        if (!final_vals) {
             long long o = i;
 #pragma unroll 4
             for (int a = 0; a < N; ++a, o += Vs) {
                 T w = chunked ? P.out[o] : S.nv(a);
                 if (project && !mob) {
                     if (bestid >= 0) w = (a == bestid) ? (T)1 : (T)0;
-                    else if (ssum > (T)0) w = w / ssum;
+                    else if (ssum > (T)0 && ssum != (T)1 && !zbits(w)) w = w / ssum;
                 }
                 if (fix) P.r0out[o] = (w - ldg(P.in + o)) / b1c;
                 if (emb) {
