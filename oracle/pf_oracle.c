@@ -254,7 +254,57 @@ done:
     return ret;
 }
 
+/* Per-cell phase slots (Sec. 3.1: each cell stores N_p phase values with
+   their phase ids): a projected cell with more than n_slots nonzero values
+   keeps the n_slots largest (equal values: the lower id first), the others
+   become 0, and the kept ones are divided by their sum (ascending ids) so
+   the cell stays on the simplex.  The paper gives no rule for a cell that
+   would need more slots; this is the reading.  Returns 1 if the cell
+   changed. */
+int or_evict_cell(int N, int n_slots, double *y)
+{
+    int cnt = 0;
+    for (int a = 0; a < N; ++a)
+        if (y[a] != 0.0) cnt++;
+    if (n_slots <= 0 || cnt <= n_slots) return 0;
+    unsigned char *keep = calloc((size_t)N, 1);
+    for (int a = 0; a < N; ++a) {
+        if (y[a] == 0.0) continue;
+        int rank = 0;   /* entries that go before a */
+        for (int b = 0; b < N; ++b)
+            if (b != a && y[b] != 0.0 && (y[b] > y[a] || (y[b] == y[a] && b < a))) rank++;
+        keep[a] = rank < n_slots;
+    }
+    double s = 0.0;
+    for (int a = 0; a < N; ++a)
+        if (keep[a]) s = s + y[a];
+    for (int a = 0; a < N; ++a) y[a] = keep[a] ? y[a] / s : 0.0;
+    free(keep);
+    return 1;
+}
+
+static int project_cells(const or_params *p, double *u, unsigned char *acted);
+
 int or_project(const or_params *p, double *u, unsigned char *acted)
+{
+    int st = project_cells(p, u, acted);
+    if (p->n_slots > 0) {
+        int N = p->N;
+        long V = or_ncells(p);
+        double *y = malloc(sizeof(double) * N);
+        for (long i = 0; i < V; ++i) {
+            for (int a = 0; a < N; ++a) y[a] = u[a * V + i];
+            if (or_evict_cell(N, p->n_slots, y)) {
+                for (int a = 0; a < N; ++a) u[a * V + i] = y[a];
+                if (acted) acted[i] = 1;
+            }
+        }
+        free(y);
+    }
+    return st;
+}
+
+static int project_cells(const or_params *p, double *u, unsigned char *acted)
 {
     int N = p->N;
     long V = or_ncells(p);

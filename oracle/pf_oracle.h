@@ -50,6 +50,7 @@ typedef struct {
     int bc_phi[6], bc_c[6];     /* faces x-,x+,y-,y+,z-,z+ */
     double cdir[6];             /* Dirichlet concentration per face */
     int simplex;                /* projection S: 0 the standard one, 1 mobility-weighted */
+    int n_slots;                /* > 0: per-cell phase slots, or_evict_cell after S */
 } or_params;
 
 typedef struct { double r_phi, a_phi, r_c, a_c; } or_tol;
@@ -84,6 +85,12 @@ int or_project(const or_params *p, double *u, unsigned char *acted);
    (*acted), -1 if no value is positive (the cell cannot be projected), 0
    otherwise. */
 int or_project_cell_mobility(int N, const double *L, double *y);
+/* Per-cell phase slots (Sec. 3.1, N_p values and ids per cell): a cell with
+   more than n_slots nonzero values keeps the n_slots largest (equal values:
+   lower id first) and divides them by their sum (ascending ids); returns 1
+   if it changed the cell.  or_project applies it after S when
+   p->n_slots > 0 ("S acted" then includes it). */
+int or_evict_cell(int N, int n_slots, double *y);
 /* Stable explicit Euler step from the Gershgorin reading (Sec. 3.2). */
 double or_dt_e(const or_params *p);
 /* Energy functional F = int a + w + f dV (Eq. energy) with forward

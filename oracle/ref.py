@@ -38,7 +38,7 @@ class _Params(C.Structure):
                 ("mob", _dp), ("W", C.c_double), ("Lover", _dp), ("K", C.c_int),
                 ("k", C.c_double * 2), ("c0", C.c_double * 2), ("D", C.c_double * 2),
                 ("bc_phi", C.c_int * 6), ("bc_c", C.c_int * 6), ("cdir", C.c_double * 6),
-                ("simplex", C.c_int)]
+                ("simplex", C.c_int), ("n_slots", C.c_int)]
 
 
 class _Tol(C.Structure):
@@ -75,6 +75,8 @@ def lib():
         L.or_project.argtypes = [C.POINTER(_Params), _dp, _ubp]
         L.or_project_cell_mobility.argtypes = [C.c_int, _dp, _dp]
         L.or_project_cell_mobility.restype = C.c_int
+        L.or_evict_cell.argtypes = [C.c_int, C.c_int, _dp]
+        L.or_evict_cell.restype = C.c_int
         L.or_dt_e.argtypes = [C.POINTER(_Params)]
         L.or_dt_e.restype = C.c_double
         L.or_reduce.argtypes = [C.POINTER(_Params), _dp, _dp, _dp, _ip]
@@ -142,6 +144,7 @@ class Oracle:
         for f in range(6):
             p.bc_phi[f], p.bc_c[f], p.cdir[f] = prob.bc_phi[f], prob.bc_c[f], prob.c_dirichlet[f]
         p.simplex = int(getattr(prob, "simplex", 0))
+        p.n_slots = int(getattr(prob, "n_slots", 0))
         self.p = p
         self.sys = _Sys()
         lib().or_sys_pde(C.byref(self.sys), C.byref(self.p))
@@ -296,6 +299,13 @@ def project_cell_mobility(L, y):
     y = np.array(y, dtype=np.float64)
     L = np.ascontiguousarray(L, dtype=np.float64).reshape(-1)
     r = lib().or_project_cell_mobility(len(y), _d(L), _d(y))
+    return y, r
+
+
+def evict_cell(y, n_slots):
+    """or_evict_cell: the per-cell slot rule on one cell's values y."""
+    y = np.array(y, dtype=np.float64)
+    r = lib().or_evict_cell(len(y), int(n_slots), _d(y))
     return y, r
 
 

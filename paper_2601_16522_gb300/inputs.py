@@ -47,6 +47,7 @@ class Problem:
     c_dirichlet: tuple = (0.0,) * 6
     c_ref: float = 0.0              # FP32 storage keeps c - c_ref (the majority phase's c)
     simplex: int = 0                # projection S: 0 standard (Sec. 3.1), 1 mobility-weighted
+    n_slots: int = 0                # > 0: per-cell phase slots (Sec. 3.1 N_p), 0: every phase stored
     name: str = ""
 
     @property

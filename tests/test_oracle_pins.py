@@ -831,3 +831,53 @@ def test_step_with_mobility_simplex_keeps_simplex_and_mass():
     a, _, _, _ = o.step(ref.RKL2, 20 * dte, 9, u)
     b, _, _, _ = ref.Oracle(prob.with_(simplex=0)).step(ref.RKL2, 20 * dte, 9, u)
     assert np.abs(a - b).max() > 1e-6
+
+
+# ---- per-cell phase slots (Sec. 3.1 N_p; the eviction rule is a reading)
+
+def test_evict_cell_keeps_the_largest_and_renormalises():
+    rng = np.random.default_rng(21)
+    for N, k in ((5, 3), (16, 12), (30, 12), (8, 1)):
+        for _ in range(50):
+            y = rng.uniform(0.0, 1.0, N) * (rng.uniform(size=N) < 0.8)
+            y[rng.integers(N)] = rng.uniform(0.1, 1.0)
+            y = y / y.sum()
+            x, code = ref.evict_cell(y, k)
+            nnz = np.count_nonzero(y)
+            if nnz <= k:
+                assert code == 0 and np.array_equal(x, y)
+                continue
+            # the kept set is the top k by (value descending, id ascending): a sort
+            order = np.lexsort((np.arange(N), -y))
+            kept = np.zeros(N, bool)
+            kept[order[:k]] = True
+            assert code == 1
+            assert np.array_equal(x != 0.0, kept)
+            np.testing.assert_allclose(x[kept], y[kept] / y[kept].sum(), rtol=1e-15)
+            assert abs(x.sum() - 1.0) < 1e-14
+
+
+def test_evict_cell_ties_go_to_the_lower_id():
+    x, code = ref.evict_cell([0.25, 0.25, 0.25, 0.25], 3)
+    np.testing.assert_array_equal(x, [1 / 3, 1 / 3, 1 / 3, 0.0])
+    x, code = ref.evict_cell([0.2, 0.3, 0.2, 0.3], 3)
+    np.testing.assert_allclose(x, [0.25, 0.375, 0.0, 0.375], rtol=1e-15)
+
+
+def test_slots_in_a_step():
+    # enough slots: the step is the unlimited one bit for bit; two slots on a
+    # state with triple junctions: no cell keeps more than two nonzero values
+    # and every cell stays on the simplex
+    prob, u = I.multiphase_blobs(20, 18, 1, 5, seed=3, has_conc=1, n_alpha=2)
+    o = ref.Oracle(prob)
+    dte = o.dt_e()
+    N = prob.n_phases
+    a, _, _, _ = o.step(ref.RKL2, 20 * dte, 9, u)
+    b, _, _, _ = ref.Oracle(prob.with_(n_slots=N)).step(ref.RKL2, 20 * dte, 9, u)
+    assert np.array_equal(a, b)
+    assert np.count_nonzero(a[:N], axis=0).max() > 2
+    c, _, _, _ = ref.Oracle(prob.with_(n_slots=2)).step(ref.RKL2, 20 * dte, 9, u)
+    assert np.count_nonzero(c[:N], axis=0).max() <= 2
+    assert c[:N].min() >= 0.0
+    np.testing.assert_allclose(c[:N].sum(axis=0), 1.0, atol=1e-13)
+    assert abs(c[N].sum() - u[N].sum()) <= 1e-12 * np.abs(u[N]).sum()
