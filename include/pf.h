@@ -129,7 +129,29 @@ typedef struct {
    passes (both precisions); PF_EINVAL with PF_OPT_MASKED, and pf_step
    returns PF_EINVAL for PF_STEP_REUSE_RHS and PF_STEP_DEVICE_LOOP; more than
    64 positive phases in one cell is PF_EINVAL from the call that meets it. */
-enum { PF_OPT_TMA = 1, PF_OPT_MASKED = 2, PF_OPT_ONE_CELL = 4, PF_OPT_MOBILITY_SIMPLEX = 8 };
+/* PF_OPT_SLOTS (FP32, up to 32768 phases) selects slot storage, the per-cell
+   phase records of Sec. 3.1: every cell holds at most N_p = 12 phase values
+   with their phase ids (ascending, 16-bit), whatever the number of phases
+   N, so a state vector costs 12 x 6 bytes (+ 4 for c) per cell: 256^3 cells
+   with 2000 grains take 1.3 GB per vector instead of 134 GB dense.  The
+   passes merge the sorted slot lists of the stencil and pointwise inputs
+   and use the arithmetic of the masked one-cell passes, so results equal
+   the dense ones bit for bit while no cell needs more than 12 slots.  A
+   projected cell with more nonzero values keeps the 12 largest (equal
+   values: the lower id) and divides them by their sum (the paper gives no
+   rule; "S acted" for the RKL2 first-stage fix includes this step); the
+   stored F(u^n) of RKL1/RKL2 keeps the 12 entries of largest magnitude
+   (equal magnitudes: the lower id).  A state given with more than 12
+   nonzero values in a cell is PF_EINVAL.  FE, SSP(s)2, RKL1 and
+   RKL2 (fixed or adaptive); PF_EINVAL for SSP(10)4, PF_STEP_REUSE_RHS,
+   PF_STEP_DEVICE_LOOP, pf_energy, and with PF_OPT_MASKED or
+   PF_OPT_MOBILITY_SIMPLEX.  pf_set_state / pf_get_state / pf_rhs still take
+   the dense layout (N x V values: for small N); pf_set_state_slots /
+   pf_get_state_slots take the slot form.  pf_reduce's phase volumes are
+   summed with atomics (their last bits depend on scheduling; the maxima,
+   the grain count and the concentration total do not). */
+enum { PF_OPT_TMA = 1, PF_OPT_MASKED = 2, PF_OPT_ONE_CELL = 4, PF_OPT_MOBILITY_SIMPLEX = 8, PF_OPT_SLOTS = 16 };
+#define PF_N_SLOTS 12
 
 /* Error tolerances of the weighted norm (Eq. error_norm): relative r and
    absolute a per field (phase field, concentration). */
@@ -227,6 +249,22 @@ int pf_rhs(struct pf_handle *h, double *rhs_phi, double *rhs_c, unsigned char *n
    completed without a flag (stats->t and steps_accepted say which). */
 int pf_step(struct pf_handle *h, pf_integrator integ, double t_end, const pf_tol *tol,
             const pf_step_opts *opts, pf_stats *stats);
+
+/* Slot storage (PF_OPT_SLOTS; PF_EINVAL for other handles).  Set the state
+   from its slot form: n_in planes of V values (vals[k * V + i]) and of
+   phase ids (ids[k * V + i], 0..N-1, or -1 for an empty slot), in any order
+   within a cell; entries whose value rounds to 0 in FP32 are dropped.  A
+   cell with more than 12 nonzero values, an id out of range or a repeated
+   id is PF_EINVAL.  c: V concentrations (K = 1).  Pointers as for
+   pf_set_state; pageable host memory goes through temporary device copies
+   freed before the call returns (Sec. 3.1: N_p values and ids per cell). */
+int pf_set_state_slots(struct pf_handle *h, const double *vals, const int *ids, int n_in, const double *c,
+                       double t, int ptr_is_device);
+
+/* Copy a slot state out: 12 planes of V values and of ids (ascending ids
+   first in every cell, then -1 with value 0), c (may be NULL) and t (may be
+   NULL). */
+int pf_get_state_slots(struct pf_handle *h, double *vals, int *ids, double *c, double *t, int ptr_is_device);
 
 /* Copy the state out (phase-major doubles; c may be NULL), N_z of the
    current state (nz, V bytes, may be NULL) and the time (t, may be NULL). */

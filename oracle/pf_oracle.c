@@ -283,6 +283,26 @@ int or_evict_cell(int N, int n_slots, double *y)
     return 1;
 }
 
+int or_keep_rhs_cell(int N, int n_slots, double *r)
+{
+    int cnt = 0;
+    for (int a = 0; a < N; ++a)
+        if (r[a] != 0.0) cnt++;
+    if (n_slots <= 0 || cnt <= n_slots) return 0;
+    unsigned char *keep = calloc((size_t)N, 1);
+    for (int a = 0; a < N; ++a) {
+        if (r[a] == 0.0) continue;
+        int rank = 0;
+        for (int b = 0; b < N; ++b)
+            if (b != a && r[b] != 0.0 && (fabs(r[b]) > fabs(r[a]) || (fabs(r[b]) == fabs(r[a]) && b < a))) rank++;
+        keep[a] = rank < n_slots;
+    }
+    for (int a = 0; a < N; ++a)
+        if (!keep[a]) r[a] = 0.0;
+    free(keep);
+    return 1;
+}
+
 static int project_cells(const or_params *p, double *u, unsigned char *acted);
 
 int or_project(const or_params *p, double *u, unsigned char *acted)
@@ -452,6 +472,20 @@ void or_reduce(const or_params *p, const double *u, double *mass, double *vol, i
 static void pde_rhs(void *ctx, const double *u, double *r) { or_rhs((const or_params *)ctx, u, r, NULL); }
 static int pde_proj(void *ctx, double *u, unsigned char *acted) { return or_project((const or_params *)ctx, u, acted); }
 
+static void pde_keep_rhs(void *ctx, double *r)
+{
+    const or_params *p = (const or_params *)ctx;
+    int N = p->N;
+    long V = or_ncells(p);
+    double *y = malloc(sizeof(double) * N);
+    for (long i = 0; i < V; ++i) {
+        for (int a = 0; a < N; ++a) y[a] = r[a * V + i];
+        if (or_keep_rhs_cell(N, p->n_slots, y))
+            for (int a = 0; a < N; ++a) r[a * V + i] = y[a];
+    }
+    free(y);
+}
+
 void or_sys_pde(or_sys *s, const or_params *p)
 {
     s->V = or_ncells(p);
@@ -461,6 +495,7 @@ void or_sys_pde(or_sys *s, const or_params *p)
     s->ctx = (void *)p;
     s->rhs = pde_rhs;
     s->proj = pde_proj;
+    s->keep_rhs = p->n_slots > 0 ? pde_keep_rhs : NULL;
 }
 
 static void dahl_rhs(void *ctx, const double *u, double *r)
@@ -477,6 +512,7 @@ void or_sys_dahlquist(or_sys *s, double *lam2)
     s->ctx = lam2;
     s->rhs = dahl_rhs;
     s->proj = NULL;
+    s->keep_rhs = NULL;
 }
 
 /* ---- integrators (Sec. 3.2) ------------------------------------------- */
@@ -653,6 +689,7 @@ long or_step(const or_sys *S, int integ, double dt, int s, const double *un,
                 for (long i = 0; i < V; ++i)
                     if (acted[i]) r0[a * V + i] = (ym1[a * V + i] - un[a * V + i]) / (mt1 * dt);
         }
+        if (S->keep_rhs) S->keep_rhs(S->ctx, r0);
         memcpy(ym2, un, sizeof(double) * n);
         for (int j = 2; j <= s; ++j) {
             double dj = (double)j, mu, nu, mt, gt;

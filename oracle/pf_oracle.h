@@ -91,6 +91,12 @@ int or_project_cell_mobility(int N, const double *L, double *y);
    if it changed the cell.  or_project applies it after S when
    p->n_slots > 0 ("S acted" then includes it). */
 int or_evict_cell(int N, int n_slots, double *y);
+/* The stored RHS F(u^n) of the STS schemes in slots: a cell with more than
+   n_slots nonzero entries keeps the n_slots largest in magnitude (equal
+   magnitudes: lower id first), the others become 0 (reading, as above).
+   Returns 1 if it changed the cell.  or_sys_pde applies it to F(u^n) after
+   the first-stage fix when p->n_slots > 0. */
+int or_keep_rhs_cell(int N, int n_slots, double *r);
 /* Stable explicit Euler step from the Gershgorin reading (Sec. 3.2). */
 double or_dt_e(const or_params *p);
 /* Energy functional F = int a + w + f dV (Eq. energy) with forward
@@ -110,6 +116,7 @@ typedef struct or_sys {
     void *ctx;
     void (*rhs)(void *ctx, const double *u, double *r);
     int (*proj)(void *ctx, double *u, unsigned char *acted_cells); /* may be NULL */
+    void (*keep_rhs)(void *ctx, double *r);   /* the stored F(u^n) of the STS schemes; may be NULL */
 } or_sys;
 
 void or_sys_pde(or_sys *s, const or_params *p);

@@ -61,7 +61,7 @@ _PROJFN = C.CFUNCTYPE(C.c_int, C.c_void_p, _dp, _ubp)
 
 class _Sys(C.Structure):
     _fields_ = [("n", C.c_long), ("N", C.c_int), ("K", C.c_int), ("V", C.c_long),
-                ("ctx", C.c_void_p), ("rhs", _RHSFN), ("proj", _PROJFN)]
+                ("ctx", C.c_void_p), ("rhs", _RHSFN), ("proj", _PROJFN), ("keep_rhs", C.c_void_p)]
 
 
 def lib():
@@ -77,6 +77,8 @@ def lib():
         L.or_project_cell_mobility.restype = C.c_int
         L.or_evict_cell.argtypes = [C.c_int, C.c_int, _dp]
         L.or_evict_cell.restype = C.c_int
+        L.or_keep_rhs_cell.argtypes = [C.c_int, C.c_int, _dp]
+        L.or_keep_rhs_cell.restype = C.c_int
         L.or_dt_e.argtypes = [C.POINTER(_Params)]
         L.or_dt_e.restype = C.c_double
         L.or_reduce.argtypes = [C.POINTER(_Params), _dp, _dp, _dp, _ip]
@@ -307,6 +309,13 @@ def evict_cell(y, n_slots):
     y = np.array(y, dtype=np.float64)
     r = lib().or_evict_cell(len(y), int(n_slots), _d(y))
     return y, r
+
+
+def keep_rhs_cell(r, n_slots):
+    """or_keep_rhs_cell: the slot rule for one cell's stored RHS r."""
+    r = np.array(r, dtype=np.float64)
+    code = lib().or_keep_rhs_cell(len(r), int(n_slots), _d(r))
+    return r, code
 
 
 def sts_stages(integ, dt, dte):

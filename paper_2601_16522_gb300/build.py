@@ -25,6 +25,8 @@ UNITS = [
     ("pf_stage_m32k1.cu", ["--fmad=true"]),
     ("pf_stage_v32k0.cu", ["--fmad=true"]),
     ("pf_stage_v32k1.cu", ["--fmad=true"]),
+    ("pf_stage_s32k0.cu", ["--fmad=true"]),
+    ("pf_stage_s32k1.cu", ["--fmad=true"]),
     ("pf_dispatch.cu", ["--fmad=false"]),
     ("pf_noalloc.cu", ["--fmad=false"]),
     ("pf_engine.cu", ["--fmad=false"]),

@@ -190,6 +190,29 @@ def munit(kc, fname):
     return "\n".join(L) + "\n"
 
 
+def sunit(kc, fname):
+    tag = "s32k%d" % kc
+    L = ["// %s -- slot-storage instantiations of the FP32 stage passes (K = %d)." % (fname, kc),
+         '#include "pf_internal.h"', "", "namespace pfk {", ""]
+    L.append("int launch_%s(const Geom &g, const Pass<float> &P, unsigned sig, cudaStream_t st, const float *A," % tag)
+    L.append("             const float *B, const float *L, const signed char *ptype, bool *done)")
+    L.append("{")
+    L.append("    const dim3 grid(g.tiles_x, g.tiles_y, g.nz);")
+    L.append("    *done = true;")
+    for d in (2, 3):
+        for sg in SIGS + ["SIG_RHS"]:
+            L.append("    if (g.dim == %d && sig == (%s)) {" % (d, sg))
+            L.append("        slot_kernel<%d, %d, %s><<<grid, BLOCK, 0, st>>>(g, P, A, B, L, ptype);" % (d, kc, sg))
+            L.append("        return (int)cudaGetLastError();")
+            L.append("    }")
+    L.append("    *done = false;")
+    L.append("    return 0;")
+    L.append("}")
+    L.append("")
+    L.append("}  // namespace pfk")
+    return "\n".join(L) + "\n"
+
+
 def vunit(kc, fname):
     tag = "v32k%d" % kc
     L = ["// %s -- two-cell FP32 instantiations of the fused stage pass (K = %d)." % (fname, kc),
@@ -266,6 +289,8 @@ def render():
         "pf_stage_m32k1.cu": munit(1, "pf_stage_m32k1.cu"),
         "pf_stage_v32k0.cu": vunit(0, "pf_stage_v32k0.cu"),
         "pf_stage_v32k1.cu": vunit(1, "pf_stage_v32k1.cu"),
+        "pf_stage_s32k0.cu": sunit(0, "pf_stage_s32k0.cu"),
+        "pf_stage_s32k1.cu": sunit(1, "pf_stage_s32k1.cu"),
     }
 
 

@@ -29,6 +29,10 @@ int launchd_v32k1(const Geom &, unsigned, const Pass<float> *, cudaStream_t, con
                   const float *, const signed char *, bool *);
 int launchp_v32k0(int, unsigned, const VecInst *, const int *, int, int, int *, cudaStream_t, bool *);
 int launchp_v32k1(int, unsigned, const VecInst *, const int *, int, int, int *, cudaStream_t, bool *);
+int launch_s32k0(const Geom &, const Pass<float> &, unsigned, cudaStream_t, const float *, const float *,
+                 const float *, const signed char *, bool *);
+int launch_s32k1(const Geom &, const Pass<float> &, unsigned, cudaStream_t, const float *, const float *,
+                 const float *, const signed char *, bool *);
 int prepare_v32k0();
 int prepare_v32k1();
 int prepare_f64();
@@ -54,6 +58,13 @@ int launch_stage<float>(const Geom &g, const Pass<float> &P, cudaStream_t st, co
 {
     bool done = false;
     if (nk) *nk = 1;
+    if (g.slots) {
+        // slot storage: only the slot instantiations read the layout; a pass
+        // kind without one is refused (cudaErrorInvalidValue)
+        int e = g.K ? launch_s32k1(g, P, pass_signature(P), st, A, B, L, ptype, &done)
+                    : launch_s32k0(g, P, pass_signature(P), st, A, B, L, ptype, &done);
+        return done ? e : (int)cudaErrorInvalidValue;
+    }
     if (g.simplex != SIMPLEX_STANDARD) {
         // the mobility-weighted projection lives in the generic body only
         int e = g.K ? launch_f32k1(g, P, SIG_GENERIC, st, A, B, L, ptype, nullptr, &done)

@@ -68,6 +68,119 @@ __global__ void unpack_kernel(const T *__restrict__ src, double *__restrict__ ph
     }
 }
 
+// Slot storage (pf_slots.cuh layout).  Dense ABI layout -> slots: a cell's
+// nonzero values (after rounding to FP32) in ascending phase order; a cell
+// with more than NSLOT raises FLAG_NZ_OVERFLOW (the state cannot be held).
+__global__ void slot_pack_dense(const double *__restrict__ phi, const double *__restrict__ c, float *__restrict__ dst,
+                                long long V, int Vs, int N, int K, double cref, int *flag)
+{
+    unsigned short *ids = reinterpret_cast<unsigned short *>(dst + (long long)pfk::NSLOT * Vs);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < V; i += (long long)gridDim.x * blockDim.x) {
+        int cnt = 0;
+        for (int a = 0; a < N; ++a) {
+            const float v = (float)phi[(long long)a * V + i];
+            if (v == 0.0f) continue;
+            if (cnt < pfk::NSLOT) {
+                dst[(long long)cnt * Vs + i] = v;
+                ids[(long long)cnt * Vs + i] = (unsigned short)a;
+            }
+            cnt++;
+        }
+        if (cnt > pfk::NSLOT) atomicOr(flag, pfk::FLAG_NZ_OVERFLOW);
+        for (int k = cnt; k < pfk::NSLOT; ++k) {
+            dst[(long long)k * Vs + i] = 0.0f;
+            ids[(long long)k * Vs + i] = (unsigned short)pfk::SLOT_EMPTY;
+        }
+        if (K) dst[(long long)pfk::SLOT_C_PLANES * Vs + i] = (float)(c[i] - cref);
+    }
+}
+
+// Slot form of the ABI (n_in planes of values and of int ids, id < 0 empty)
+// -> slots: the entries with a nonzero FP32 value, sorted by id.  More than
+// NSLOT of them, an id outside 0..N-1 or a repeated id raises
+// FLAG_NZ_OVERFLOW.
+__global__ void slot_pack_slots(const double *__restrict__ vals, const int *__restrict__ idin, int n_in,
+                                const double *__restrict__ c, float *__restrict__ dst, long long V, int Vs, int N,
+                                int K, double cref, int *flag)
+{
+    unsigned short *ids = reinterpret_cast<unsigned short *>(dst + (long long)pfk::NSLOT * Vs);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < V; i += (long long)gridDim.x * blockDim.x) {
+        float sv[pfk::NSLOT];
+        int sid[pfk::NSLOT];
+        int cnt = 0;
+        bool bad = false;
+        for (int k = 0; k < n_in; ++k) {
+            const int a = idin[(long long)k * V + i];
+            if (a < 0) continue;
+            const float v = (float)vals[(long long)k * V + i];
+            if (v == 0.0f) continue;
+            if (a >= N || cnt >= pfk::NSLOT) { bad = true; break; }
+            // insertion in ascending id order
+            int j = cnt;
+            while (j > 0 && sid[j - 1] > a) { sid[j] = sid[j - 1]; sv[j] = sv[j - 1]; --j; }
+            if (j > 0 && sid[j - 1] == a) { bad = true; break; }
+            sid[j] = a;
+            sv[j] = v;
+            cnt++;
+        }
+        if (bad) { atomicOr(flag, pfk::FLAG_NZ_OVERFLOW); cnt = 0; }
+        for (int k = 0; k < pfk::NSLOT; ++k) {
+            dst[(long long)k * Vs + i] = k < cnt ? sv[k] : 0.0f;
+            ids[(long long)k * Vs + i] = (unsigned short)(k < cnt ? sid[k] : (int)pfk::SLOT_EMPTY);
+        }
+        if (K) dst[(long long)pfk::SLOT_C_PLANES * Vs + i] = (float)(c[i] - cref);
+    }
+}
+
+// Slots -> dense ABI layout (c may be null).
+__global__ void slot_unpack_dense(const float *__restrict__ src, double *__restrict__ phi, double *__restrict__ c,
+                                  long long V, int Vs, int N, int K, double cref)
+{
+    const unsigned short *ids = reinterpret_cast<const unsigned short *>(src + (long long)pfk::NSLOT * Vs);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < V; i += (long long)gridDim.x * blockDim.x) {
+        for (int a = 0; a < N; ++a) phi[(long long)a * V + i] = 0.0;
+        for (int k = 0; k < pfk::NSLOT; ++k) {
+            const unsigned a = ids[(long long)k * Vs + i];
+            if (a >= (unsigned)N) break;
+            phi[(long long)a * V + i] = (double)src[(long long)k * Vs + i];
+        }
+        if (K && c) c[i] = (double)src[(long long)pfk::SLOT_C_PLANES * Vs + i] + cref;
+    }
+}
+
+// Slots -> slot form of the ABI (NSLOT planes of values and ids, -1 empty).
+__global__ void slot_unpack_slots(const float *__restrict__ src, double *__restrict__ vals, int *__restrict__ idout,
+                                  double *__restrict__ c, long long V, int Vs, int N, int K, double cref)
+{
+    const unsigned short *ids = reinterpret_cast<const unsigned short *>(src + (long long)pfk::NSLOT * Vs);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < V; i += (long long)gridDim.x * blockDim.x) {
+        for (int k = 0; k < pfk::NSLOT; ++k) {
+            const unsigned a = ids[(long long)k * Vs + i];
+            const bool used = a < (unsigned)N;
+            vals[(long long)k * V + i] = used ? (double)src[(long long)k * Vs + i] : 0.0;
+            idout[(long long)k * V + i] = used ? (int)a : -1;
+        }
+        if (K && c) c[i] = (double)src[(long long)pfk::SLOT_C_PLANES * Vs + i] + cref;
+    }
+}
+
+// Per-phase totals of a slot state: sum (FP64 atomics, so the last bits
+// depend on the order the blocks run in) and maximum (on the encodings of
+// the nonnegative values, exact) of every phase.
+__global__ void slot_phase_totals(const float *__restrict__ src, long long V, int Vs, int N, double *vol,
+                                  unsigned long long *mx)
+{
+    const unsigned short *ids = reinterpret_cast<const unsigned short *>(src + (long long)pfk::NSLOT * Vs);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < V; i += (long long)gridDim.x * blockDim.x)
+        for (int k = 0; k < pfk::NSLOT; ++k) {
+            const unsigned a = ids[(long long)k * Vs + i];
+            if (a >= (unsigned)N) break;
+            const double v = (double)src[(long long)k * Vs + i];
+            atomicAdd(vol + a, v);
+            if (v > 0.0) atomicMax(mx + a, (unsigned long long)__double_as_longlong(v));
+        }
+}
+
 // Self-test of the bounded device waits: one thread waits on a shared-memory
 // mbarrier that no thread arrives on, with the poll loop of the TMA kernels
 // and a caller-given limit; it must give up, raise FLAG_TIMEOUT and return.
@@ -387,6 +500,7 @@ struct pf_handle {
     int *dcrowd = nullptr;             // crowded cells recorded by a two-cell pass (FP32)
     double *tot_sum = nullptr, *tot_max = nullptr;
     int tot_blocks = 0;
+    bool slots = false;                // per-cell phase slots (pf_slots.cuh layout)
     bool masked = false;               // masked storage: occupancy-word planes after the fields
     int nw = 0;                        // occupancy words per cell (masked storage)
     bool tma_ok = false;               // tensor maps built: TMA-staged kernels available
@@ -1496,13 +1610,16 @@ int step_loop(pf_handle *h, int integ, double t_end, const pf_tol *tol, const pf
     if (o->flags & PF_STEP_DEVICE_LOOP) {
         // the descriptor-driven kernels cover FP64 and FP32 dense storage with N <= 32
         if (!(adaptive && sts) || !h->stream || h->prof_on || (o->flags & PF_STEP_REUSE_RHS) || h->masked ||
-            !(sizeof(T) == 8 || h->N <= 32) || h->Vs >= 0x7fffffffLL || h->g.simplex != pfk::SIMPLEX_STANDARD)
+            !(sizeof(T) == 8 || h->N <= 32) || h->Vs >= 0x7fffffffLL || h->g.simplex != pfk::SIMPLEX_STANDARD ||
+            h->slots)
             return PF_EINVAL;
         h->rhs_valid = false;
         return devloop<T>(h, integ, t_end, tol, o, stats);
     }
     // the pointwise first stage of the reuse path applies the standard S only
-    if ((o->flags & PF_STEP_REUSE_RHS) && h->g.simplex != pfk::SIMPLEX_STANDARD) return PF_EINVAL;
+    if ((o->flags & PF_STEP_REUSE_RHS) && (h->g.simplex != pfk::SIMPLEX_STANDARD || h->slots)) return PF_EINVAL;
+    // slot storage: the passes of FE, SSP(s)2, RKL1 and RKL2
+    if (h->slots && integ == PF_SSP104) return PF_EINVAL;
     const int max_stages = o->max_stages > 0 ? o->max_stages : 1001;
     long long evals = 0, acc_n = 0, rej_n = 0, attempts = 0;
     const long long launches0 = h->launches;
@@ -1647,6 +1764,14 @@ const void *device_view(const void *p)
 template <typename T>
 int set_state_t(pf_handle *h, const double *phi_dev, const double *c_dev)
 {
+    if (h->slots) {
+        if (cudaMemsetAsync(h->dflag, 0, PF_FLAG_BYTES, h->stream) != cudaSuccess) return PF_EDEVICE;
+        slot_pack_dense<<<grid_for(h->V), 256, 0, h->stream>>>(phi_dev, c_dev, (float *)h->buf[h->iu], h->V,
+                                                              (int)h->Vs, h->N, h->K, h->g.cref, h->dflag);
+        h->launches++;
+        if (cudaGetLastError() != cudaSuccess) return PF_EDEVICE;
+        return check_flag(h);
+    }
     pack_kernel<T><<<grid_for(h->V * h->NP), 256, 0, h->stream>>>(phi_dev, c_dev, (T *)h->buf[h->iu], h->V, h->Vs,
                                                                     h->N, h->NP, h->g.cref);
     h->launches++;
@@ -1661,6 +1786,12 @@ int set_state_t(pf_handle *h, const double *phi_dev, const double *c_dev)
 template <typename T>
 int get_state_t(pf_handle *h, double *phi_dev, double *c_dev)
 {
+    if (h->slots) {
+        slot_unpack_dense<<<grid_for(h->V), 256, 0, h->stream>>>((const float *)h->buf[h->iu], phi_dev, c_dev, h->V,
+                                                                (int)h->Vs, h->N, h->K, h->g.cref);
+        h->launches++;
+        return cuda_status(cudaGetLastError());
+    }
     unpack_kernel<T><<<grid_for(h->V * h->NP), 256, 0, h->stream>>>((const T *)h->buf[h->iu], phi_dev, c_dev, h->V,
                                                                       h->Vs, h->N, h->NP, h->g.cref);
     h->launches++;
@@ -1673,6 +1804,10 @@ template <typename T>
 int rhs_t(pf_handle *h, unsigned char *nz_dev, bool rhs)
 {
     if (rhs && !h->staging) return PF_EINVAL;
+    // slot passes write only the listed phases' entries
+    if (rhs && h->slots &&
+        cudaMemsetAsync(h->staging, 0, sizeof(double) * (size_t)h->NP * h->V, h->stream) != cudaSuccess)
+        return PF_EDEVICE;
     h->cur_kind = PF_PASS_RHS;
     Pass<T> P = blank_pass<T>(h);
     P.mode = pfk::MODE_RHS;
@@ -1850,7 +1985,9 @@ int pf_create(const pf_params *p, void *cuda_stream, pf_handle **out)
     if (p->has_conc != 0 && p->has_conc != 1) return PF_EINVAL;
     if (p->precision != 32 && p->precision != 64) return PF_EINVAL;
     const int NP = p->n_phases + p->has_conc;
-    if (NP > 128) return PF_EINVAL;
+    const bool slots = (p->options & PF_OPT_SLOTS) != 0;
+    if (slots ? p->n_phases > pfk::SLOT_MAXN : NP > 128) return PF_EINVAL;
+    if (slots && (p->precision != 32 || (p->options & (PF_OPT_MASKED | PF_OPT_MOBILITY_SIMPLEX)))) return PF_EINVAL;
     for (int f = 0; f < 6; ++f) {
         if (f >= 2 * p->dim) break;
         const int o = f ^ 1;
@@ -1904,6 +2041,10 @@ int pf_create(const pf_params *p, void *cuda_stream, pf_handle **out)
     // and every difference of psi unchanged
     g.cref = (h->prec == 32 && h->K) ? p->c_ref : 0.0;
     g.simplex = (p->options & PF_OPT_MOBILITY_SIMPLEX) ? pfk::SIMPLEX_MOBILITY : pfk::SIMPLEX_STANDARD;
+    g.slots = slots ? 1 : 0;
+    h->slots = slots;
+    // slot passes index a slot plane with 32-bit offsets
+    if (slots && (long long)pfk::NSLOT * h->Vs >= 0x7fffffffLL) { delete h; return PF_EINVAL; }
     for (int f = 0; f < 6; ++f) {
         g.bc_phi[f] = p->bc_phi[f];
         g.bc_c[f] = p->bc_c[f];
@@ -1938,14 +2079,15 @@ int pf_create(const pf_params *p, void *cuda_stream, pf_handle **out)
         h->masked = true;
         h->nw = (p->n_phases + 31) / 32;
     }
-    h->vec_bytes = (size_t)h->Vs * NP * h->esize + sizeof(unsigned) * (size_t)h->Vs * h->nw;
+    h->vec_bytes = slots ? sizeof(float) * (size_t)h->Vs * pfk::slot_planes(h->K)
+                         : (size_t)h->Vs * NP * h->esize + sizeof(unsigned) * (size_t)h->Vs * h->nw;
     bool ok = true;
     for (int k = 0; k < NBUF && ok; ++k) ok = dmalloc(h, &h->buf[k], h->vec_bytes);
     ok = ok && dmalloc(h, &h->dA, h->esize * N * N);
     ok = ok && dmalloc(h, &h->dB, h->esize * N * N);
     ok = ok && dmalloc(h, &h->dL, h->esize * N * N);
     ok = ok && dmalloc(h, &h->dptype, N);
-    ok = ok && dmalloc(h, &h->dAB64, sizeof(double) * 2 * N * N);
+    if (!slots) ok = ok && dmalloc(h, &h->dAB64, sizeof(double) * 2 * N * N);   // energy (dense storage)
     ok = ok && dmalloc(h, &h->part_sum, sizeof(double) * h->grid);
     ok = ok && dmalloc(h, &h->part_cnt, sizeof(long long) * h->grid);
     ok = ok && dmalloc(h, &h->dres, sizeof(double));
@@ -1968,9 +2110,11 @@ int pf_create(const pf_params *p, void *cuda_stream, pf_handle **out)
     st |= cudaMemcpyAsync(h->dB, tb, h->esize * N * N, cudaMemcpyHostToDevice, h->stream);
     st |= cudaMemcpyAsync(h->dL, tl, h->esize * N * N, cudaMemcpyHostToDevice, h->stream);
     st |= cudaMemcpyAsync(h->dptype, pt.data(), N, cudaMemcpyHostToDevice, h->stream);
-    st |= cudaMemcpyAsync(h->dAB64, h->A.data(), sizeof(double) * N * N, cudaMemcpyHostToDevice, h->stream);
-    st |= cudaMemcpyAsync(h->dAB64 + (size_t)N * N, h->B.data(), sizeof(double) * N * N, cudaMemcpyHostToDevice,
-                          h->stream);
+    if (h->dAB64) {
+        st |= cudaMemcpyAsync(h->dAB64, h->A.data(), sizeof(double) * N * N, cudaMemcpyHostToDevice, h->stream);
+        st |= cudaMemcpyAsync(h->dAB64 + (size_t)N * N, h->B.data(), sizeof(double) * N * N, cudaMemcpyHostToDevice,
+                              h->stream);
+    }
     st |= cudaMemsetAsync(h->dflag, 0, PF_FLAG_BYTES, h->stream);
     if (h->dcrowd) st |= cudaMemsetAsync(h->dcrowd, 0, 2 * sizeof(int), h->stream);
     if (h->masked)
@@ -1980,7 +2124,8 @@ int pf_create(const pf_params *p, void *cuda_stream, pf_handle **out)
     st |= cudaStreamSynchronize(h->stream);
     if (st != 0) { free_all(h); delete h; return PF_EDEVICE; }
     // TMA-staged FP32 kernels: full 32 x 8 tiles, 3D, 5..32 phases
-    if (h->prec == 32 && !h->masked && p->dim == 3 && N > 4 && N <= 32 && p->nx % pfk::TX == 0 && p->ny % pfk::TY == 0 &&
+    if (h->prec == 32 && !h->masked && !slots && p->dim == 3 && N > 4 && N <= 32 && p->nx % pfk::TX == 0 &&
+        p->ny % pfk::TY == 0 &&
         p->nz >= 3 && h->Vs < 0x7fffffffLL) {
         bool ok = true;
         for (int k = 0; k < NBUF && ok; ++k)
@@ -2014,11 +2159,13 @@ int pf_footprint(const pf_params *p, long long *bytes)
     const long long tiles = std::max((long long)((p->nx + pfk::TX - 1) / pfk::TX) * ((p->ny + pfk::TY - 1) / pfk::TY), vt) *
                             p->nz;
     const long long tot_blocks = (V + 4095) / 4096 < 1024 ? ((V + 4095) / 4096 > 0 ? (V + 4095) / 4096 : 1) : 1024;
-    long long b = (long long)NBUF * NF * Vs * es;          // state vectors
+    const bool slots = (p->options & PF_OPT_SLOTS) != 0;
+    long long b = slots ? (long long)NBUF * pfk::slot_planes(p->has_conc ? 1 : 0) * Vs * 4   // slot vectors
+                        : (long long)NBUF * NF * Vs * es;                                    // state vectors
     if (p->options & PF_OPT_MASKED) b += (long long)NBUF * ((p->n_phases + 31) / 32) * Vs * 4;   // occupancy words
-    b += NF * V * 8;                                       // ABI staging buffer (allocated on first set/get)
+    if (!slots) b += NF * V * 8;                           // ABI staging buffer (allocated on first set/get)
     b += 3LL * p->n_phases * p->n_phases * es + p->n_phases;   // coefficient tables, phase types
-    b += 2LL * p->n_phases * p->n_phases * 8;              // FP64 A and B for the energy functional
+    if (!slots) b += 2LL * p->n_phases * p->n_phases * 8;  // FP64 A and B for the energy functional
     b += tiles * 16 + 2 * tot_blocks * NF * 8 + 64;       // reduction partials
     if (p->precision == 32) b += 4 * (2 + tiles * (1 + pfk::VCELLS / 32));   // crowded-cell record
     *bytes = b;
@@ -2117,6 +2264,77 @@ int pf_set_state(pf_handle *h, const double *phi, const double *c, double t, int
     h->rhs_valid = false;
     reset_controller(h);
     return PF_OK;
+}
+
+int pf_set_state_slots(pf_handle *h, const double *vals, const int *ids, int n_in, const double *c, double t,
+                       int ptr_is_device)
+{
+    if (!h || !h->slots || !vals || !ids || n_in < 1 || (h->K && !c) || h->in_batch) return PF_EINVAL;
+    const double *dv = (const double *)device_view(vals), *dc = h->K ? (const double *)device_view(c) : nullptr;
+    const int *di = (const int *)device_view(ids);
+    std::vector<void *> tmp;
+    auto stage = [&](const void *src, size_t bytes) -> const void * {
+        void *q = nullptr;
+        if (!dmalloc(h, &q, bytes)) return nullptr;
+        tmp.push_back(q);
+        if (cudaMemcpyAsync(q, src, bytes, ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                            h->stream) != cudaSuccess)
+            return nullptr;
+        return q;
+    };
+    int st = PF_OK;
+    // pageable host memory goes through temporary device copies
+    if (!dv) dv = (const double *)stage(vals, sizeof(double) * (size_t)n_in * h->V);
+    if (!di) di = (const int *)stage(ids, sizeof(int) * (size_t)n_in * h->V);
+    if (h->K && !dc) dc = (const double *)stage(c, sizeof(double) * (size_t)h->V);
+    if (!dv || !di || (h->K && !dc)) st = PF_ENOMEM;
+    if (!st && cudaMemsetAsync(h->dflag, 0, PF_FLAG_BYTES, h->stream) != cudaSuccess) st = PF_EDEVICE;
+    if (!st) {
+        slot_pack_slots<<<grid_for(h->V), 256, 0, h->stream>>>(dv, di, n_in, dc, (float *)h->buf[h->iu], h->V,
+                                                              (int)h->Vs, h->N, h->K, h->g.cref, h->dflag);
+        h->launches++;
+        st = cudaGetLastError() == cudaSuccess ? check_flag(h) : PF_EDEVICE;
+    }
+    cudaStreamSynchronize(h->stream);
+    for (void *q : tmp) dfree(h, q);
+    if (st) return st;
+    h->t = t;
+    h->has_state = true;
+    h->rhs_valid = false;
+    reset_controller(h);
+    return PF_OK;
+}
+
+int pf_get_state_slots(pf_handle *h, double *vals, int *ids, double *c, double *t, int ptr_is_device)
+{
+    if (!h || !h->slots || !vals || !ids) return PF_EINVAL;
+    if (!h->has_state) return PF_ESTATE;
+    double *dv = (double *)device_view(vals), *dc = (c && h->K) ? (double *)device_view(c) : nullptr;
+    int *di = (int *)device_view(ids);
+    const size_t nv = sizeof(double) * (size_t)pfk::NSLOT * h->V, ni = sizeof(int) * (size_t)pfk::NSLOT * h->V;
+    double *tv = nullptr, *tc = nullptr;
+    int *ti = nullptr;
+    int st = PF_OK;
+    if (!dv && !dmalloc(h, &tv, nv)) st = PF_ENOMEM;
+    if (!st && !di && !dmalloc(h, &ti, ni)) st = PF_ENOMEM;
+    if (!st && c && h->K && !dc && !dmalloc(h, &tc, sizeof(double) * h->V)) st = PF_ENOMEM;
+    if (!st) {
+        slot_unpack_slots<<<grid_for(h->V), 256, 0, h->stream>>>((const float *)h->buf[h->iu], dv ? dv : tv,
+                                                                di ? di : ti, (c && h->K) ? (dc ? dc : tc) : nullptr,
+                                                                h->V, (int)h->Vs, h->N, h->K, h->g.cref);
+        h->launches++;
+        if (cudaGetLastError() != cudaSuccess) st = PF_EDEVICE;
+    }
+    const cudaMemcpyKind kind = ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (!st && tv && cudaMemcpyAsync(vals, tv, nv, kind, h->stream) != cudaSuccess) st = PF_EDEVICE;
+    if (!st && ti && cudaMemcpyAsync(ids, ti, ni, kind, h->stream) != cudaSuccess) st = PF_EDEVICE;
+    if (!st && tc && cudaMemcpyAsync(c, tc, sizeof(double) * h->V, kind, h->stream) != cudaSuccess) st = PF_EDEVICE;
+    if (t) *t = h->t;
+    if ((tv || ti || tc || !ptr_is_device) && cudaStreamSynchronize(h->stream) != cudaSuccess && !st) st = PF_EDEVICE;
+    if (tv) dfree(h, tv);
+    if (ti) dfree(h, ti);
+    if (tc) dfree(h, tc);
+    return st;
 }
 
 int pf_get_state(pf_handle *h, double *phi, double *c, unsigned char *nz, double *t, int ptr_is_device)
@@ -2221,7 +2439,7 @@ int pf_autotune(pf_handle *h, int *choice, double *ms)
     if (ms)
         for (int v = 0; v < PF_KVAR_COUNT; ++v) ms[v] = -1.0;
     int c = current_variant(h);
-    if (h->prec == 32 && !h->masked) {
+    if (h->prec == 32 && !h->masked && !h->slots) {
         const bool ok[PF_KVAR_COUNT] = {pfk::vec_eligible(h->g), true, h->tma_ok};
         double best = -1.0;
         for (int v = 0; v < PF_KVAR_COUNT; ++v) {
@@ -2239,10 +2457,57 @@ int pf_autotune(pf_handle *h, int *choice, double *ms)
     return check_flag(h);
 }
 
+// pf_reduce on slot storage: per-phase sums and maxima by atomics over the
+// slots (N doubles each), the concentration by the fixed-order partials.
+int reduce_slots(pf_handle *h, double *mass_c, double *vol_phi, int *grains_alive)
+{
+    const int N = h->N;
+    double *vol = h->tot_sum;
+    unsigned long long *mx = reinterpret_cast<unsigned long long *>(h->tot_max);
+    double *cs = h->tot_sum + N, *cm = h->tot_max + N;      // N + tot_blocks <= tot_blocks * NP
+    if (cudaMemsetAsync(vol, 0, sizeof(double) * N, h->stream) != cudaSuccess) return PF_EDEVICE;
+    if (cudaMemsetAsync(mx, 0, sizeof(double) * N, h->stream) != cudaSuccess) return PF_EDEVICE;
+    const float *u = (const float *)h->buf[h->iu];
+    slot_phase_totals<<<grid_for(h->V), 256, 0, h->stream>>>(u, h->V, (int)h->Vs, N, vol, mx);
+    h->launches++;
+    if (h->K) {
+        dim3 grid(h->tot_blocks, 1);
+        totals_kernel<float><<<grid, 256, 0, h->stream>>>(u + (size_t)pfk::SLOT_C_PLANES * h->Vs, h->V, h->Vs, cs, cm);
+        h->launches++;
+    }
+    if (cudaGetLastError() != cudaSuccess) return PF_EDEVICE;
+    std::vector<double> v(N), c(h->tot_blocks);
+    std::vector<unsigned long long> m(N);
+    if (cudaMemcpyAsync(v.data(), vol, sizeof(double) * N, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+        return PF_EDEVICE;
+    if (cudaMemcpyAsync(m.data(), mx, sizeof(double) * N, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+        return PF_EDEVICE;
+    if (h->K && cudaMemcpyAsync(c.data(), cs, sizeof(double) * h->tot_blocks, cudaMemcpyDeviceToHost, h->stream) !=
+                    cudaSuccess)
+        return PF_EDEVICE;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return PF_EDEVICE;
+    const double dv = pow(h->dx, h->g.dim);
+    int alive = 0;
+    for (int a = 0; a < N; ++a) {
+        if (vol_phi) vol_phi[a] = v[a] * dv;
+        double mv;
+        memcpy(&mv, &m[a], sizeof(double));
+        if (mv >= 0.5) alive++;
+    }
+    if (mass_c) {
+        double tot = 0.0;
+        for (int b = 0; b < h->tot_blocks; ++b) tot += c[b];
+        *mass_c = h->K ? (tot + (double)h->V * h->g.cref) * dv : 0.0;
+    }
+    if (grains_alive) *grains_alive = alive;
+    return PF_OK;
+}
+
 int pf_reduce(pf_handle *h, double *mass_c, double *vol_phi, int *grains_alive)
 {
     if (!h) return PF_EINVAL;
     if (!h->has_state) return PF_ESTATE;
+    if (h->slots) return reduce_slots(h, mass_c, vol_phi, grains_alive);
     int st = (h->prec == 64) ? totals_t<double>(h) : totals_t<float>(h);
     if (st) return st;
     std::vector<double> s((size_t)h->tot_blocks * h->NP), m((size_t)h->tot_blocks * h->NP);
@@ -2273,7 +2538,7 @@ int pf_reduce(pf_handle *h, double *mass_c, double *vol_phi, int *grains_alive)
 
 int pf_energy(pf_handle *h, double *F)
 {
-    if (!h || !F) return PF_EINVAL;
+    if (!h || !F || h->slots) return PF_EINVAL;
     if (!h->has_state) return PF_ESTATE;
     const long long want = (h->V + 255) / 256;
     const int nblk = (int)(want < h->grid ? want : h->grid);
@@ -2395,8 +2660,8 @@ bool grow(T **dev, T **host, size_t *cap, size_t want)
 
 bool packable(const pf_handle *h, int integ)
 {
-    return h->prec == 32 && !h->masked && !h->tma && h->g.kvar == pfk::KVAR_TWO_CELL && pfk::vec_eligible(h->g) &&
-           integ != PF_SSP104 && h->g.simplex == pfk::SIMPLEX_STANDARD;
+    return h->prec == 32 && !h->masked && !h->slots && !h->tma && h->g.kvar == pfk::KVAR_TWO_CELL &&
+           pfk::vec_eligible(h->g) && integ != PF_SSP104 && h->g.simplex == pfk::SIMPLEX_STANDARD;
 }
 
 }  // namespace

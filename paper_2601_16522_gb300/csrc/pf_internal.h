@@ -4,6 +4,7 @@
 #include <stddef.h>
 #include "pf_kernels.cuh"
 #include "pf_vec.cuh"
+#include "pf_slots.cuh"
 
 namespace pfk {
 

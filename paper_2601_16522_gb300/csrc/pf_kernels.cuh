@@ -64,6 +64,7 @@ struct Geom {
     int tiles_x, tiles_y;               // block tiling of the x-y plane (one-cell kernels)
     int kvar;                           // FP32 dense passes: KVAR_TWO_CELL or KVAR_ONE_CELL
     int simplex;                        // projection S: SIMPLEX_STANDARD or SIMPLEX_MOBILITY
+    int slots;                          // 1: per-cell phase slots (FP32; see pf_slots.cuh)
 };
 // Kernel variants of the FP32 dense passes (chosen per handle, pf_autotune).
 enum { KVAR_TWO_CELL = 0, KVAR_ONE_CELL = 1 };

@@ -228,24 +228,21 @@ def stefan_growth_constant(D=1.0, c_a=0.2, c_ab=0.02, c_ba=0.98, c_b=0.98):
 
 def poisson_disc_seeds(n_cells, count, min_dist, dim, rng, max_tries=200000):
     """Seeded random points in a periodic box with a minimum (periodic) distance."""
-    pts = []
+    pts = np.zeros((count, dim))
+    n = 0
     tries = 0
     L = np.array(n_cells, dtype=np.float64)
-    while len(pts) < count:
+    while n < count:
         tries += 1
         if tries > max_tries:
             raise ValueError("could not place %d seeds with min distance %g" % (count, min_dist))
         p = rng.random(dim) * L
-        ok = True
-        for q in pts:
-            dd = np.abs(p - q)
-            dd = np.minimum(dd, L - dd)
-            if np.sqrt((dd * dd).sum()) < min_dist:
-                ok = False
-                break
-        if ok:
-            pts.append(p)
-    return np.array(pts)
+        dd = np.abs(p - pts[:n])
+        dd = np.minimum(dd, L - dd)
+        if n == 0 or not (np.sqrt((dd * dd).sum(axis=1)) < min_dist).any():
+            pts[n] = p
+            n += 1
+    return pts
 
 
 def _diffuse_voronoi(shape, seeds, W, knn=6, chunk=1 << 17):
@@ -370,10 +367,22 @@ def grains_device(n=256, n_grains=32, min_dist=40.0, seed=2, dim=3, dx=0.005, W_
                    name="grains%d^%d_N%d" % (n, dim, n_grains))
     m = n if region is None else region
     V = m ** dim
+    u = torch.zeros((n_grains, V), dtype=torch.float64, device=device)
+    for idx, nn, tr in _voronoi_chunks(seeds, n, m, dim, W_cells, knn, device, chunk):
+        for j in range(nn.shape[1]):
+            u.index_put_((nn[:, j], idx), tr[:, j], accumulate=True)
+    return prob, u
+
+
+def _voronoi_chunks(seeds, n, m, dim, W_cells, knn, device, chunk):
+    """The diffuse periodic Voronoi structure of grains_device, chunk by
+    chunk of cells: yields (cell indices, the k nearest seeds per cell, their
+    trial values rescaled to sum 1)."""
+    import torch
+    V = m ** dim
     S = torch.tensor(seeds, dtype=torch.float64, device=device)
     box = torch.full((dim,), float(n), dtype=torch.float64, device=device)
-    u = torch.zeros((n_grains, V), dtype=torch.float64, device=device)
-    k = min(knn, n_grains)
+    k = min(knn, len(seeds))
     eye = torch.eye(k, dtype=torch.bool, device=device)
     h = math.pi * W_cells / 2.0
     for s0 in range(0, V, chunk):
@@ -395,9 +404,44 @@ def grains_device(n=256, n_grains=32, min_dist=40.0, seed=2, dim=3, dx=0.005, W_
         tr = torch.where(dist <= -h, torch.zeros_like(tr), tr)
         tr = torch.where(dist >= h, torch.ones_like(tr), tr)
         tr /= tr.sum(1, keepdim=True)
-        for j in range(k):
-            u.index_put_((nn[:, j], idx), tr[:, j], accumulate=True)
-    return prob, u
+        yield idx, nn, tr
+
+
+N_SLOTS = 12    # per-cell phase slots of the slot storage (Sec. 3.1: N_p = 12)
+
+
+def grains_slots_device(n=256, n_grains=2000, min_dist=None, seed=2, dim=3, dx=0.005, W_cells=2.5, M=5e-3,
+                        gamma=1.0, knn=6, device="cuda"):
+    """The grain structure of grains_device with many grains, returned in
+    per-cell slot form (Sec. 3.1: each cell holds its nonzero phase values
+    with their phase ids, at most N_SLOTS): (Problem, vals, ids, None) with
+    vals a (N_SLOTS, V) float64 tensor and ids a (N_SLOTS, V) int32 tensor,
+    slots in ascending id order, -1 (value 0) where empty.  min_dist defaults
+    to 0.6 of the mean grain spacing."""
+    import torch
+    rng = np.random.default_rng(seed)
+    shape = (n,) * dim
+    if min_dist is None:
+        min_dist = 0.6 * (n ** dim / n_grains) ** (1.0 / dim)
+    seeds = poisson_disc_seeds(shape, n_grains, min_dist, dim, rng, max_tries=50 * n_grains + 200000)
+    W = W_cells * dx
+    prob = Problem(dim=dim, nx=n, ny=n, nz=n if dim == 3 else 1, dx=dx, n_phases=n_grains,
+                   phase_type=np.ones(n_grains, np.int32),
+                   gamma=uniform_pairs(n_grains, gamma), mobility=uniform_pairs(n_grains, M), W=W,
+                   n_slots=N_SLOTS, name="grains%d^%d_N%d_slots" % (n, dim, n_grains))
+    V = n ** dim
+    vals = torch.zeros((N_SLOTS, V), dtype=torch.float64, device=device)
+    ids = torch.full((N_SLOTS, V), -1, dtype=torch.int32, device=device)
+    chunk = max(1024, (1 << 25) // n_grains)
+    for idx, nn, tr in _voronoi_chunks(seeds, n, n, dim, W_cells, knn, device, chunk):
+        # ascending ids, zero trial values left out (they sort after the others)
+        key = torch.where(tr > 0, nn, torch.full_like(nn, 1 << 30))
+        key, order = torch.sort(key, dim=1)
+        tv = torch.gather(tr, 1, order)
+        k = nn.shape[1]
+        vals[:k, idx] = torch.where(key < (1 << 30), tv, torch.zeros_like(tv)).T
+        ids[:k, idx] = torch.where(key < (1 << 30), key, torch.full_like(key, -1)).to(torch.int32).T
+    return prob, vals, ids, None
 
 
 def corrected_radius(r, W, tol=1e-10):

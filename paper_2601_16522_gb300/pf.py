@@ -85,6 +85,8 @@ def _lib():
         L.pf_step.argtypes = [H, C.c_int, C.c_double, C.POINTER(pf_tol), C.POINTER(pf_step_opts),
                               C.POINTER(pf_stats)]
         L.pf_get_state.argtypes = [H, C.c_void_p, C.c_void_p, C.c_void_p, _dp, C.c_int]
+        L.pf_set_state_slots.argtypes = [H, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_double, C.c_int]
+        L.pf_get_state_slots.argtypes = [H, C.c_void_p, C.c_void_p, C.c_void_p, _dp, C.c_int]
         L.pf_reduce.argtypes = [H, _dp, _dp, _ip]
         L.pf_energy.argtypes = [H, _dp]
         L.pf_dt_e.argtypes = [H, _dp]
@@ -161,6 +163,10 @@ def make_params(prob, precision=64, options=0):
     p.precision = precision
     if getattr(prob, "simplex", 0) == 1:
         options |= Simulation.OPT_MOBILITY_SIMPLEX
+    if getattr(prob, "n_slots", 0):
+        if prob.n_slots != Simulation.N_SLOTS:
+            raise ValueError("slot storage holds %d phases per cell" % Simulation.N_SLOTS)
+        options |= Simulation.OPT_SLOTS
     p.options = options
     p.c_ref = float(getattr(prob, "c_ref", 0.0) or 0.0)
     return p, keep
@@ -188,6 +194,8 @@ class Simulation:
     OPT_MASKED = 2
     OPT_ONE_CELL = 4
     OPT_MOBILITY_SIMPLEX = 8
+    OPT_SLOTS = 16
+    N_SLOTS = 12
     KVAR_TWO_CELL, KVAR_ONE_CELL, KVAR_TMA = 0, 1, 2
 
     def __init__(self, prob, precision=64, stream=None, options=0):
@@ -282,6 +290,44 @@ class Simulation:
         if dev:
             self._torch_waits(out)
         return (out, t.value, nz) if with_nz else (out, t.value)
+
+    def set_state_slots(self, vals, ids, c=None, t=0.0):
+        """Slot form (slot storage): vals (n_in, V) float64 and ids (n_in, V)
+        int32 (-1: empty), c (V,) float64 when K = 1; numpy arrays or CUDA
+        tensors (all of one kind)."""
+        dev = _is_dev(vals)
+        if not dev:
+            vals = np.ascontiguousarray(vals, np.float64)
+            ids = np.ascontiguousarray(ids, np.int32)
+            c = None if c is None else np.ascontiguousarray(c, np.float64)
+        assert vals.shape == ids.shape and vals.shape[1] == self.V, (vals.shape, ids.shape)
+        if dev:
+            self._wait_for_torch(vals)
+        _check(_lib().pf_set_state_slots(self.h, _ptr(vals), _ptr(ids), int(vals.shape[0]),
+                                         _ptr(c) if c is not None else None, float(t), int(dev)),
+               "pf_set_state_slots")
+        self._last_in = (vals, ids, c)
+
+    def get_state_slots(self, device=None):
+        """Returns (vals (12, V) float64, ids (12, V) int32, c or None, t):
+        numpy arrays, or CUDA tensors on `device`."""
+        n = self.N_SLOTS
+        if device is None:
+            vals = np.zeros((n, self.V))
+            ids = np.zeros((n, self.V), np.int32)
+            c = np.zeros(self.V) if self.K else None
+        else:
+            import torch
+            vals = torch.empty((n, self.V), dtype=torch.float64, device=device)
+            ids = torch.empty((n, self.V), dtype=torch.int32, device=device)
+            c = torch.empty(self.V, dtype=torch.float64, device=device) if self.K else None
+            self._wait_for_torch(vals)
+        t = C.c_double()
+        _check(_lib().pf_get_state_slots(self.h, _ptr(vals), _ptr(ids), _ptr(c) if c is not None else None,
+                                         C.byref(t), int(device is not None)), "pf_get_state_slots")
+        if device is not None:
+            self._torch_waits(vals)
+        return vals, ids, c, t.value
 
     def rhs(self):
         """RHS of the current state -> ((N+K, V) float64, nz uint8) on the host."""

@@ -881,3 +881,35 @@ def test_slots_in_a_step():
     assert c[:N].min() >= 0.0
     np.testing.assert_allclose(c[:N].sum(axis=0), 1.0, atol=1e-13)
     assert abs(c[N].sum() - u[N].sum()) <= 1e-12 * np.abs(u[N]).sum()
+
+
+def test_keep_rhs_cell_keeps_the_largest_magnitudes():
+    rng = np.random.default_rng(22)
+    for N, k in ((20, 12), (6, 3)):
+        for _ in range(50):
+            r = rng.normal(size=N) * (rng.uniform(size=N) < 0.9)
+            x, code = ref.keep_rhs_cell(r, k)
+            if np.count_nonzero(r) <= k:
+                assert code == 0 and np.array_equal(x, r)
+                continue
+            order = np.lexsort((np.arange(N), -np.abs(r)))
+            kept = np.zeros(N, bool)
+            kept[order[:k]] = True
+            kept &= r != 0
+            assert code == 1
+            np.testing.assert_array_equal(x, np.where(kept, r, 0.0))
+    x, _ = ref.keep_rhs_cell([0.5, -0.5, 0.1], 1)
+    np.testing.assert_array_equal(x, [0.5, 0.0, 0.0])
+
+
+def test_slots_keep_the_stored_rhs():
+    # RKL2 with two slots: F(u^n) keeps two entries per cell, so the step
+    # differs from the one with the full F but stays on the simplex
+    prob, u = I.multiphase_blobs(20, 18, 1, 5, seed=3, has_conc=1, n_alpha=2)
+    o = ref.Oracle(prob.with_(n_slots=2))
+    dte = o.dt_e()
+    un, rn, _, _ = o.step(ref.RKL2, 20 * dte, 9, u)
+    N = prob.n_phases
+    assert np.count_nonzero(rn[:N], axis=0).max() <= 2
+    assert np.count_nonzero(un[:N], axis=0).max() <= 2
+    np.testing.assert_allclose(un[:N].sum(axis=0), 1.0, atol=1e-13)
