@@ -524,7 +524,8 @@ def grains_to_half(pf, torch, dev, stream, t_max=60.0, wall_cap_s=120.0, full=Fa
         t, evals, alive = 0.0, 0, n0
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        while alive > n0 // 2 and t < t_max and time.perf_counter() - t0 < wall_cap_s:
+        cap = wall_cap_s if integ != pf.SSP104 or full else 0.5 * wall_cap_s
+        while alive > n0 // 2 and t < t_max and time.perf_counter() - t0 < cap:
             t += dt_out
             evals += sim.step(integ, t, tol=TOL)["rhs_evals"]
             alive = sim.reduce()[2]
@@ -614,18 +615,21 @@ def sinter_horizon(pf, torch, dev, stream, t_r=0.05, wall_cap_s=150.0):
             "solute_change": float(abs(m1 - m0) / m0)}
 
 
-def zener_sts(pf, torch, dev, stream, n=128, n_grains=32, t_eq=5.0, t_run=10.0):
+def zener_sts(pf, torch, dev, stream, n=128, n_grains=32, t_eq=0.5, t_run=10.0, full=False):
     """Grain growth with immobile particles (Sec. 5.3, Zener pinning; the
     paper's 11.5x case, Tab. perf-ggpores, on a 400^3 domain to t_r = 884):
     n^3 cells, particles of radius 6 at volume fraction 0.15, masked FP32
     storage.  The equilibration run of Sec. 5.3 (its parameters, adaptive
-    RKL2 to t_eq = 5) is followed by the immobile run with adaptive RKL2 over
-    t_run time units; the RHS sweeps are compared with the stable Euler steps
-    the same interval takes (t_run / dt_e).  More than 12 nontrivial phases
-    per cell appear at the particle fringes under the STS schemes; those
-    cells take the wide path.  The same immobile run is repeated for the
-    first time unit with the mobility-weighted projection (dense storage,
-    generic passes) beside the standard one."""
+    RKL2 to t_eq; the paper's 5 time units with full=True) is followed by
+    the immobile run with adaptive RKL2 over t_run time units; the RHS sweeps
+    are compared with the stable Euler steps the same interval takes
+    (t_run / dt_e).  More than 12 nontrivial phases per cell appear at the
+    particle fringes under the STS schemes; those cells take the wide path.
+    With full=True the first time unit of the immobile run is repeated with
+    the mobility-weighted projection (dense storage, generic passes) beside
+    the standard one."""
+    if full:
+        t_eq = 5.0
     from paper_2601_16522_gb300 import inputs as I
     prob, u = I.zener_device(n=n, n_grains=n_grains, device=dev)
     opts = pf.Simulation.OPT_MASKED
@@ -656,7 +660,7 @@ def zener_sts(pf, torch, dev, stream, n=128, n_grains=32, t_eq=5.0, t_run=10.0):
     sim.close()
     # the first time unit with each projection (dense storage, same state)
     proj = {}
-    for name, p in (("standard", prob), ("mobility-weighted", prob.with_(simplex=1))):
+    for name, p in ((("standard", prob), ("mobility-weighted", prob.with_(simplex=1))) if full else ()):
         sim = pf.Simulation(p, precision=32, stream=stream)
         sim.set_state(u1, t=0.0)
         torch.cuda.synchronize()
@@ -675,6 +679,49 @@ def zener_sts(pf, torch, dev, stream, n=128, n_grains=32, t_eq=5.0, t_run=10.0):
             "t_run": t_run, "rhs_evals": evals, "accepted": acc, "rejected": rej, "wall_s": wall,
             "fe_steps": fe, "rhs_ratio_vs_fe": fe / max(evals, 1), "paper_ratio": 14110453 / 1224604,
             "max_nontrivial_phases_per_cell": int(nz.max().item()), "projections": proj}
+
+
+def slots_many_grains(pf, torch, dev, stream, n=256, n_grains=2000, attempts=6):
+    """Slot storage (Sec. 3.1: 12 phase values and ids per cell) on a grain
+    structure with many more grains than dense planes could hold: n^3 cells,
+    n_grains Voronoi grains, adaptive RKL2 in FP32.  Reports the device
+    footprint beside that of dense storage, GCell-updates/s over a few
+    attempts after one warm-up attempt, and the RKL2 pass's algorithmic
+    bandwidth (5 slot vectors of 72 B per cell)."""
+    from paper_2601_16522_gb300 import inputs as I
+    t0 = time.perf_counter()
+    prob, vals, ids, _ = I.grains_slots_device(n=n, n_grains=n_grains, seed=7, device=dev)
+    build_s = time.perf_counter() - t0
+    opts = pf.Simulation.OPT_SLOTS
+    fp = pf.footprint(prob, 32, options=opts)
+    dense = 5 * prob.V * n_grains * 4
+    sim = pf.Simulation(prob, precision=32, stream=stream)
+    sim.set_state_slots(vals, ids)
+    del vals, ids
+    _, _, alive0 = sim.reduce()
+    sim.step(pf.RKL2, 1e30, tol=TOL, max_attempts=1)
+    torch.cuda.synchronize()
+    sim.profile(1)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    sweeps = 0
+    for _ in range(attempts):
+        sweeps += sim.step(pf.RKL2, 1e30, tol=TOL, max_attempts=1)["rhs_evals"]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    prof = sim.profile(0)
+    _, _, alive = sim.reduce()
+    sim.close()
+    out = {"workload": prob.name, "cells": prob.V, "grains": n_grains, "slots_per_cell": 12,
+           "footprint_gb": fp / 1e9, "dense_state_vectors_gb": dense / 1e9, "build_s": build_s,
+           "attempts": attempts, "rhs_evals": sweeps, "ms": ms,
+           "gcell_updates_per_s": prob.V * sweeps / (ms * 1e-3) / 1e9, "grains_alive": [alive0, alive]}
+    if prof.get("rkl2", (0, 0))[1]:
+        per = prof["rkl2"][0] / prof["rkl2"][1]
+        out["rkl2_pass_ms"] = per
+        out["rkl2_pass_gbs"] = 5 * 72 * prob.V / (per * 1e-3) / 1e9
+    return out
 
 
 def precision_check(pf, torch, dev, stream, t_end=2.0):
@@ -875,7 +922,10 @@ def run_ours(args, world, rank, local):
         fe64 = fp64_fe_pass(pf, torch, dev, stream)
     zener = None
     if extras and not args.no_zener:
-        zener = zener_sts(pf, torch, dev, stream)
+        zener = zener_sts(pf, torch, dev, stream, full=args.full)
+    slots = None
+    if extras and not args.no_slots:
+        slots = slots_many_grains(pf, torch, dev, stream)
 
     if rank == 0:
         line = {
@@ -897,7 +947,7 @@ def run_ours(args, world, rank, local):
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
             "time_to_solution": tts, "served": served, "masked": masked, "reuse_rhs": reuse,
             "grains_to_half": to_half, "stefan_sweep": sweep, "sinter_horizon": horizon, "precision_check": prec_check,
-            "fp64_fe_pass": fe64, "zener_sts": zener,
+            "fp64_fe_pass": fe64, "zener_sts": zener, "slots_many_grains": slots,
         }
         print(json.dumps(line), flush=True)
     sim.close()
@@ -923,6 +973,7 @@ def main():
     ap.add_argument("--no-stefan-sweep", action="store_true")
     ap.add_argument("--no-sinter", action="store_true")
     ap.add_argument("--no-zener", action="store_true")
+    ap.add_argument("--no-slots", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default kernel variant (two cells per thread) instead of timing the variants "
                          "first (a profiler distorts those timings)")
