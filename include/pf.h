@@ -396,12 +396,13 @@ int pf_totals_noalloc(const double *u_dev, int n_fields, long long n_cells, doub
                       double *max_dev, void *cuda_stream);
 
 /* Device bytes a handle for these parameters holds once it has been
-   created and a state has been set (state vectors, ABI staging buffer,
+   created and a state has been set (state vectors, ABI staging buffer --
+   none for slot storage, whose dense transfers allocate it on first use --,
    tables and reduction partials), without allocating anything.  Used to
    admit simulations by memory footprint. */
 int pf_footprint(const pf_params *params, long long *bytes);
 
-/* Caller-supplied device allocator (Sec. "Ownership" of this interface: the
+/* Caller-supplied device allocator (the paper has no counterpart: the
    library's device buffers may come from the caller, e.g. a framework's
    caching allocator).  alloc(bytes, cuda_stream, ctx) returns device memory
    of the current device usable on cuda_stream (the handle's stream), or NULL
