@@ -166,6 +166,50 @@ def aggregate_value(cells, sweeps_per_rank, ms_max, world):
     return world * cells * sweeps_per_rank / (ms_max * 1e-3) / 1e9
 
 
+def oracle_configs():
+    """The CPU oracle on the configurations beside the GPU runs: the
+    shrinking circle (128^2, 2000 FE steps of 0.9 dt_e, FP64) in full, the
+    Stefan strip (1024 x 256) for a
+    fixed number of forward Euler steps (the Stefan count extrapolated to
+    its run length, t = 43e3); the sintering recipe (65 phases + c) on a
+    48^3 box; OpenMP on all host cores, and one thread on a tenth of the
+    circle run."""
+    from oracle import ref
+    from paper_2601_16522_gb300 import inputs as I
+    cores = os.cpu_count()
+    out = {"cores": cores}
+
+    def fe(prob, u, n_steps):
+        o = ref.Oracle(prob)
+        dte = o.dt_e()
+        t0 = time.perf_counter()
+        st, _, t, _ = o.run(ref.FEULER, u, 0.0, n_steps * 0.9 * dte, dt_mult=0.9)
+        el = time.perf_counter() - t0
+        return el, dte
+
+    ref.set_openmp(True)
+    try:
+        prob, u = I.circle(128, 40.0)
+        el, dte = fe(prob, u, 2000)
+        out["circle128_fe64_full"] = {"steps": 2000, "wall_s": el, "gcell_updates_per_s": prob.V * 2000 / el / 1e9}
+        prob, u = I.stefan(nx=1024, ny=256, h=200.0)
+        el, dte = fe(prob, u, 20)
+        n_full = math.ceil(43e3 / (0.9 * dte))
+        out["stefan1024x256_fe64"] = {"steps_timed": 20, "wall_s": el, "gcell_updates_per_s": prob.V * 20 / el / 1e9,
+                                      "steps_to_t43e3": n_full, "estimated_wall_s_to_t43e3": el / 20 * n_full}
+        # the sintering recipe (64 grains + pore phase + c) on a 48^3 box
+        sp, su = I.sintering_device(n=48, n_grains=64, seed=3, device="cpu")
+        el, dte = fe(sp, su.numpy(), 2)
+        out["sinter_recipe48_fe64"] = {"steps_timed": 2, "cells": sp.V, "phases": sp.n_phases, "wall_s": el,
+                                       "gcell_updates_per_s": sp.V * 2 / el / 1e9}
+    finally:
+        ref.set_openmp(False)
+    prob, u = I.circle(128, 40.0)
+    el, dte = fe(prob, u, 200)
+    out["circle128_fe64_single_thread"] = {"steps": 200, "wall_s": el, "gcell_updates_per_s": prob.V * 200 / el / 1e9}
+    return out
+
+
 def oracle_sample(u_host_sub, prob_sub, s=5):
     """Time the CPU oracle on one RKL2 step (s stages + error sweep) of a sub-box."""
     from oracle import ref
@@ -836,6 +880,7 @@ def run_ours(args, world, rank, local):
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": kernel_name(prob, prec, variant) + " (%s pass)" % dom,
                 "bytes_per_launch": bytes_launch, "avg_launch_ms": ms_k / n_k,
+                "frac_of_spec_8tbs": achieved / 8000.0,
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
     pass_ms = {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items() if v[1] > 0}
 
@@ -926,6 +971,9 @@ def run_ours(args, world, rank, local):
     slots = None
     if extras and not args.no_slots:
         slots = slots_many_grains(pf, torch, dev, stream)
+    oracle_cfg = None
+    if extras and not args.no_cpu_baseline:
+        oracle_cfg = oracle_configs()
 
     if rank == 0:
         line = {
@@ -947,7 +995,7 @@ def run_ours(args, world, rank, local):
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
             "time_to_solution": tts, "served": served, "masked": masked, "reuse_rhs": reuse,
             "grains_to_half": to_half, "stefan_sweep": sweep, "sinter_horizon": horizon, "precision_check": prec_check,
-            "fp64_fe_pass": fe64, "zener_sts": zener, "slots_many_grains": slots,
+            "fp64_fe_pass": fe64, "zener_sts": zener, "slots_many_grains": slots, "oracle_configs": oracle_cfg,
         }
         print(json.dumps(line), flush=True)
     sim.close()
