@@ -236,6 +236,16 @@ __device__ __forceinline__ void vec_body(const Geom &g, const Pass<float> &P, co
         // one phase at one cell: activity, list entry, stage value (returned)
         auto cell_phase = [&](VCell &Cc, int slot, int a, T v, T xl, T xr, T ym, T yp, T zm, T zp, T p0v, T p2v,
                               T r0v) -> T {
+            // every input +0 (most phases of most cells): the phase is not
+            // nontrivial, its stage value is exactly +0, it adds nothing to the
+            // sum, the count or the error -- the result of the steps below
+            unsigned bits = __float_as_uint(v) | __float_as_uint(xl) | __float_as_uint(xr) | __float_as_uint(ym) |
+                            __float_as_uint(yp);
+            if (DIM == 3) bits |= __float_as_uint(zm) | __float_as_uint(zp);
+            if (HP0) bits |= __float_as_uint(p0v);
+            if (HP2) bits |= __float_as_uint(p2v);
+            if (HR0) bits |= __float_as_uint(r0v);
+            if (bits == 0u) return (T)0;
             T mx, mn;
             if (DIM == 3) {
                 mx = fmax3(fmax3(v, xl, xr), fmax3(ym, yp, zm), zp);
