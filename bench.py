@@ -56,9 +56,9 @@ def workload_problem(name, device):
 PASS_VECTORS = {"rkl2": 5, "rkl1": 3, "sts_first": 3, "sts_err": 3, "euler": 2, "ssp": 2, "rhs": 1}
 # DRAM bytes (read + write) per cell of one RKL2 stage pass (two-cell kernel,
 # 32-phase FP32 state) from an ncu capture of that launch at full size
-# (256^3: 8.813 GB read + 2.149 GB written in the second RKL2 pass of a step;
+# (256^3: 8.822 GB read + 2.148 GB written in the second RKL2 pass of a step;
 # the algorithmic 640 B/cell is 10.74 GB)
-RKL2_TRAFFIC_PER_CELL = {"grains256": (8813314816 + 2148658688) / 16777216}
+RKL2_TRAFFIC_PER_CELL = {"grains256": (8821829632 + 2148446464) / 16777216}
 
 
 class ClockSampler:
