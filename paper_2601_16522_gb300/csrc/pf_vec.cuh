@@ -28,7 +28,12 @@
 namespace pfk {
 
 constexpr int VTX = 32;              // threads along x: 64 cells
-constexpr int VTY = 4;               // rows per block
+// Rows per block (4; measured at 256^3 x 32: 2 rows at 10/14 blocks per SM
+// and 8 rows at 2/3 give RKL2 passes of 2.13 and 2.43 ms against 2.11 ms).
+#ifndef PF_VEC_TY
+#define PF_VEC_TY 4
+#endif
+constexpr int VTY = PF_VEC_TY;       // rows per block
 constexpr int VBLOCK = VTX * VTY;    // 128 threads
 constexpr int VCELLS = 2 * VBLOCK;   // 256 cells per block
 // List capacity per cell: passes with two extra pointwise streams (RKL2 body)
