@@ -92,3 +92,24 @@ def test_diffuse_voronoi_grains_are_a_partition():
     # the knn = 6 nearest grains the construction considers
     assert (u == 1.0).any(axis=0).any()
     assert (u > 0).sum(0).max() <= 6
+
+
+def test_slot_form_grains_are_the_dense_grains():
+    # the slot form lists, per cell, the nonzero values of the dense builder's
+    # state in ascending phase order (the same seeds and profiles)
+    pytest.importorskip("torch")
+    prob_d, u = I.grains_device(n=20, n_grains=12, min_dist=5.0, seed=3, dim=3, device="cpu")
+    prob_s, vals, ids, _ = I.grains_slots_device(n=20, n_grains=12, min_dist=5.0, seed=3, dim=3, device="cpu")
+    u, vals, ids = u.numpy(), vals.numpy(), ids.numpy()
+    assert prob_s.n_slots == I.N_SLOTS and prob_s.n_phases == prob_d.n_phases
+    dense = np.zeros_like(u)
+    for k in range(I.N_SLOTS):
+        m = ids[k] >= 0
+        dense[ids[k][m], np.nonzero(m)[0]] = vals[k][m]
+        assert np.all(vals[k][~m] == 0.0)
+    np.testing.assert_array_equal(dense, u)
+    used = ids >= 0
+    assert np.all(used[:-1] | ~used[1:])                      # used slots come first
+    d = np.diff(np.where(used, ids, 1 << 30), axis=0)
+    assert np.all((d > 0) | ~used[1:])                        # ascending ids
+    assert np.count_nonzero(u, axis=0).max() == used.sum(axis=0).max()
