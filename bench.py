@@ -390,6 +390,64 @@ def fp64_fe_pass(pf, torch, dev, stream):
             "frac_of_measured_peak": ach / peak, "kernel": "cell_kernel<double,3,0,generic> (--fmad=false)"}
 
 
+def kernel_families(pf, torch, dev, stream):
+    """The stage-pass kernel of every storage form, precision and projection
+    on one workload (128^3 cells x 32 grains, vectors of 268 MB > L2): per
+    launch time of the pass kind that dominates each run, its algorithmic
+    bytes (state vectors read + written, dense-equivalent for masked storage)
+    and their rate against the measured copy bandwidth; and the energy
+    functional's pass (one vector read)."""
+    prob, u, _ = workload_problem("grains128", dev)
+    V, N = prob.V, prob.n_phases
+    peak = _peak_gbs()
+    O = pf.Simulation
+    runs = [("rkl2 two-cell FP32", 32, 0, prob, pf.RKL2, "rkl2", 5),
+            ("rkl2 one-cell FP32", 32, O.OPT_ONE_CELL, prob, pf.RKL2, "rkl2", 5),
+            ("rkl2 masked FP32 (dense-equivalent bytes)", 32, O.OPT_MASKED, prob, pf.RKL2, "rkl2", 5),
+            ("rkl2 mobility-weighted projection FP32 (generic)", 32, 0, prob.with_(simplex=1), pf.RKL2, "rkl2", 5),
+            ("rkl2 FP64 (generic)", 64, 0, prob, pf.RKL2, "rkl2", 5),
+            ("ssp(10)4 stage FP32 (one-cell rolled, with z)", 32, 0, prob, pf.SSP104, "ssp", 4),
+            ("ssp(10)4 stage FP32 masked", 32, O.OPT_MASKED, prob, pf.SSP104, "ssp", 4)]
+    out = {"workload": prob.name, "peak_gbs": peak, "passes": []}
+    for name, prec, opts, p, integ, kind, nvec in runs:
+        sim = pf.Simulation(p, precision=prec, stream=stream, options=opts)
+        sim.set_state(u)
+        sim.step(integ, 1e30, tol=TOL, max_attempts=1)
+        torch.cuda.synchronize()
+        sim.profile(1)
+        for _ in range(2):
+            sim.step(integ, 1e30, tol=TOL, max_attempts=1)
+        prof = sim.profile(0)
+        sim.close()
+        ms, n = prof.get(kind, (0.0, 0))
+        if not n:
+            continue
+        nbytes = nvec * N * (prec // 8) * V
+        ach = nbytes / (ms / n * 1e-3) / 1e9
+        row = {"pass": name, "ms": ms / n, "launches": n, "bytes": nbytes}
+        if opts & O.OPT_MASKED:
+            # masked storage moves fewer bytes than the dense ones counted here:
+            # a rate, not a fraction of the memory bandwidth
+            row["dense_equivalent_gbs"] = ach
+        else:
+            row.update({"gbs": ach, "frac_of_measured_peak": ach / peak})
+        out["passes"].append(row)
+    # the energy functional (Eq. energy): one FP32 state read per evaluation
+    sim = pf.Simulation(prob, precision=32, stream=stream)
+    sim.set_state(u)
+    sim.energy()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(3):
+        sim.energy()
+    el = (time.perf_counter() - t0) / 3
+    sim.close()
+    nbytes = N * 4 * V
+    out["passes"].append({"pass": "energy functional FP32 (one call, host round trip included)", "ms": 1e3 * el,
+                          "bytes": nbytes, "gbs": nbytes / el / 1e9, "frac_of_measured_peak": nbytes / el / 1e9 / peak})
+    return out
+
+
 def _peak_gbs():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0)
@@ -974,6 +1032,9 @@ def run_ours(args, world, rank, local):
     oracle_cfg = None
     if extras and not args.no_cpu_baseline:
         oracle_cfg = oracle_configs()
+    families = None
+    if extras:
+        families = kernel_families(pf, torch, dev, stream)
 
     if rank == 0:
         line = {
@@ -996,6 +1057,7 @@ def run_ours(args, world, rank, local):
             "time_to_solution": tts, "served": served, "masked": masked, "reuse_rhs": reuse,
             "grains_to_half": to_half, "stefan_sweep": sweep, "sinter_horizon": horizon, "precision_check": prec_check,
             "fp64_fe_pass": fe64, "zener_sts": zener, "slots_many_grains": slots, "oracle_configs": oracle_cfg,
+            "kernel_families": families,
         }
         print(json.dumps(line), flush=True)
     sim.close()

@@ -390,6 +390,12 @@ first_from_rhs_recompute_kernel(const T *__restrict__ in, T *out, T *r0, long lo
 //     + sum_a phi_a mu^2 / (2 k_a)                     (K = 1, KKS, Sec. 2)
 constexpr int EMAX = 32;
 
+// x != 0 taken without the FP64 pipe (GB300's FP64 rate is a small fraction
+// of its FP32 rate): FP32 values are compared in FP32, FP64 values by their
+// encoding with the sign bit dropped (the same answer for every value).
+__device__ __forceinline__ bool nonzero_value(float x) { return x != 0.0f; }
+__device__ __forceinline__ bool nonzero_value(double x) { return (__double_as_longlong(x) << 1) != 0; }
+
 template <typename T>
 __global__ void __launch_bounds__(256)
 energy_kernel(const Geom g, const T *__restrict__ u, const double *__restrict__ A, const double *__restrict__ B,
@@ -411,15 +417,19 @@ energy_kernel(const Geom g, const T *__restrict__ u, const double *__restrict__ 
         bool full = false;
         for (int a = 0; a < g.N; ++a) {
             const T *f = u + (long long)a * g.Vs + i;
-            const double v = (double)f[0];
-            double d[3] = {0.0, 0.0, 0.0};
-            bool any = v != 0.0;
+            const T vt = f[0];
+            T wt[3] = {vt, vt, vt};
+            bool any = nonzero_value(vt);
             for (int ax = 0; ax < g.dim; ++ax) {
-                const double w = ghost[2 * ax + 1] ? v : (double)f[off[2 * ax + 1]];
-                any = any || w != 0.0;
-                d[ax] = __dsub_rn(w, v) / dx;
+                if (!ghost[2 * ax + 1]) wt[ax] = f[off[2 * ax + 1]];
+                any = any || nonzero_value(wt[ax]);
             }
             if (!any) continue;
+            // equal values have a zero difference: no FP64 division for them
+            const double v = (double)vt;
+            double d[3] = {0.0, 0.0, 0.0};
+            for (int ax = 0; ax < g.dim; ++ax)
+                if (wt[ax] != vt) d[ax] = __dsub_rn((double)wt[ax], v) / dx;
             if (n == EMAX) { full = true; break; }
             id[n] = (unsigned char)a;
             ph[n] = v;
