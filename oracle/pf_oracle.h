@@ -20,11 +20,15 @@
  *     paper does not print; we use the minimum-norm order-3 embedding),
  *   - the chemical / diffusion parts of or_dt_e (Sec. 3.2: the Gershgorin
  *     estimates live in the missing supplement; our reading reproduces the
- *     three stable steps printed in Sec. 5.3 but is fitted, not derived) and
+ *     three stable steps printed in Sec. 5.3 but is fitted, not derived),
  *   - the mobility-based simplex of Sec. 3.1/5.3 (cited, not described):
  *     or_project_cell_mobility is one reading of it (a projection in the
- *     metric the mobilities define), so the paper does not fix its values:
- *     parity unpinned for those three readings.
+ *     metric the mobilities define), so the paper does not fix its values,
+ *     and
+ *   - the rule for a cell that needs more than N_p slots (Sec. 3.1 gives
+ *     none): or_evict_cell / or_keep_rhs_cell are pinned against a sort of
+ *     their own definition, not against the paper:
+ *     parity unpinned for those four readings.
  */
 #ifndef PF_ORACLE_H
 #define PF_ORACLE_H
