@@ -2113,6 +2113,22 @@ int pf_create(const pf_params *p, void *cuda_stream, pf_handle **out)
     std::vector<signed char> pt(N);
     for (int a = 0; a < N; ++a) pt[a] = (signed char)h->ptype[a];
     std::vector<float> fa(h->A.begin(), h->A.end()), fb(h->B.begin(), h->B.end()), fl(h->L.begin(), h->L.end());
+    if (slots && N >= 2) {
+        // one value off the diagonal of every table (grain growth with equal
+        // gamma and M): the slot passes read it from the constants, which is
+        // the same FP32 value (same bits) the gather would return
+        bool same = true;
+        for (int a = 0; a < N && same; ++a)
+            for (int b = 0; b < N && same; ++b)
+                if (a != b)
+                    same = memcmp(&fa[a * N + b], &fa[1], sizeof(float)) == 0 &&
+                           memcmp(&fb[a * N + b], &fb[1], sizeof(float)) == 0 &&
+                           memcmp(&fl[a * N + b], &fl[1], sizeof(float)) == 0;
+        h->g.uni = same ? 1 : 0;
+        h->g.uA = fa[1];
+        h->g.uB = fb[1];
+        h->g.uL = fl[1];
+    }
     const void *ta = h->prec == 64 ? (const void *)h->A.data() : (const void *)fa.data();
     const void *tb = h->prec == 64 ? (const void *)h->B.data() : (const void *)fb.data();
     const void *tl = h->prec == 64 ? (const void *)h->L.data() : (const void *)fl.data();

@@ -65,6 +65,9 @@ struct Geom {
     int kvar;                           // FP32 dense passes: KVAR_TWO_CELL or KVAR_ONE_CELL
     int simplex;                        // projection S: SIMPLEX_STANDARD or SIMPLEX_MOBILITY
     int slots;                          // 1: per-cell phase slots (FP32; see pf_slots.cuh)
+    int uni;                            // slot passes: 1 if every off-diagonal entry of each
+    float uA, uB, uL;                   // FP32 table A, B, L is the same value (these), which
+                                        // the pairwise sums then use instead of gathers
 };
 // Kernel variants of the FP32 dense passes (chosen per handle, pf_autotune).
 enum { KVAR_TWO_CELL = 0, KVAR_ONE_CELL = 1 };

@@ -252,7 +252,9 @@ __device__ __forceinline__ bool slot_cell(const Geom &g, const Pass<float> &P, L
         for (int f = 0; f < NFACE; ++f) acc = acc + mf[f] * (num_n[f] / den_n[f] - mu);
         rc = acc * idx2;
     }
-    // variational derivative and pairwise sum over the listed phases
+    // variational derivative and pairwise sum over the listed phases (with
+    // uniform tables the coefficients come from the constants: same values)
+    const bool uni = g.uni != 0;
     for (int k = 0; k < nz; ++k) {
         const long long a = S.id(k);
         const T *Aa = tabA + a * N, *Ba = tabB + a * N;
@@ -260,7 +262,8 @@ __device__ __forceinline__ bool slot_cell(const Geom &g, const Pass<float> &P, L
         for (int k2 = 0; k2 < nz; ++k2) {
             if (k2 == k) continue;
             const int b = S.id(k2);
-            d = d + (ldg(Aa + b) * S.lap(k2) + ldg(Ba + b) * S.cen(k2));
+            const T Aab = uni ? g.uA : ldg(Aa + b), Bab = uni ? g.uB : ldg(Ba + b);
+            d = d + (Aab * S.lap(k2) + Bab * S.cen(k2));
         }
         if (KC) {
             const int t = ptype[a];
@@ -277,7 +280,8 @@ __device__ __forceinline__ bool slot_cell(const Geom &g, const Pass<float> &P, L
             T s = (T)0;
             for (int k2 = 0; k2 < nz; ++k2) {
                 if (k2 == k) continue;
-                s = s + ldg(La + S.id(k2)) * (dk - S.dl(k2));
+                const T Lab = uni ? g.uL : ldg(La + S.id(k2));
+                s = s + Lab * (dk - S.dl(k2));
             }
             rk = -(s * inz);
         }
