@@ -453,8 +453,10 @@ __device__ __noinline__ void slot_wide(const Geom *g, const Pass<float> *P, int 
 }
 
 // Resident blocks per SM (register budget): 4 for the RKL2 body, 3 for the
-// other passes (measured on 256^3 x 2000 grains: the RKL2 pass takes 6.6 ms
-// at 2 resident blocks, 3.2 ms at 3, 2.9 ms at 4).
+// other passes (measured on 256^3 x 2000 grains with table gathers: the RKL2
+// pass takes 6.6 ms at 2 resident blocks, 3.2 ms at 3, 2.9 ms at 4; with the
+// uniform coefficients 2.46 ms at 4 and 4.2 ms at 5, where 48 registers
+// spill).
 template <unsigned SIG>
 constexpr int slot_minb() { return (SIG & (SIG_P0 | SIG_P2)) == (SIG_P0 | SIG_P2) ? 4 : 3; }
 
